@@ -1,0 +1,166 @@
+"""Seeded synthetic inputs and configuration presets.
+
+This module holds only configuration values and seeded input generators; it
+contains none of the method's arithmetic, so that both the CUDA path and the
+CPU oracle can be driven from the same inputs.  Numbers come from the paper's
+tables (vehicle constants, Table veh; hyperparameters, Table hyperparameters)
+and from the planner workloads this library is benchmarked on.
+
+Scene recipes (all world-frame, SI units; obstacles are (x, y, vx, vy)):
+
+* ``scene_single``: one planning instance, N = 256, T = 20, 8-16-16-2 network,
+  200 static points uniform in a 40 x 40 m box centred on the start with none
+  within 5 m of it, goal position uniform in the box, goal heading uniform,
+  goal speed 0, start at rest with a random world pose.
+* ``scene_course``: the forward/reverse waypoint course of the paper's
+  Experiment 4 (four waypoints at the corners of a square, heading turned by
+  90 degrees at each) scaled 1.5x; 2000 points: 1000 on an outer wall, 500 on
+  a central island, 500 on ten moving car-sized outlines with speeds uniform
+  in [0, 3] m/s at uniform headings.  N = 16384, T = 40, 8-32-32-2.
+"""
+import math
+
+import numpy as np
+
+# ------------------------------------------------------------------ presets
+PAPER = dict(
+    # Table veh: l_f, l_r, delta_max, delta_dot_max, u_min, u_max
+    lf=1.1, lr=1.4, delta_max=40 * math.pi / 180, delta_rate_max=20 * math.pi / 180,
+    u_min=-100 / (3.8 * 3.6), u_max=100 / (7.4 * 3.6), Ts=0.1,
+    # chassis (l_f + 0.7 + l_r + 0.6) x 2 m around the CoG: 1.8 m ahead,
+    # 2.0 m behind -> centre 0.1 m behind the CoG
+    half_len=1.9, half_wid=1.0, c_off=-0.1,
+    # Table hyperparameters: Delta xi, Delta eta, Delta phi, Delta v
+    dxi_n=30.0, deta_n=3.5, dphi_n=2 * math.pi, dv_n=120 / 3.6,
+    w_pos=1.0, w_phi=1.0, w_v=0.1, w_effort=0.1,
+    widths=(5, 2, 2),
+)
+
+
+def planner(width: int) -> dict:
+    """4.5 x 1.8 m car, wheelbase 2.7 m (reference point mid-wheelbase at the
+    rectangle centre), steering +-0.6 rad at 20 deg/s, acceleration +-3 m/s^2,
+    Ts = 0.1 s, 8-width-width-2 tanh network."""
+    return dict(
+        lf=1.35, lr=1.35, delta_max=0.6, delta_rate_max=20 * math.pi / 180,
+        u_min=-3.0, u_max=3.0, Ts=0.1,
+        half_len=2.25, half_wid=0.9, c_off=0.0,
+        dxi_n=30.0, deta_n=3.5, dphi_n=2 * math.pi, dv_n=120 / 3.6,
+        w_pos=1.0, w_phi=1.0, w_v=0.1, w_effort=0.1,
+        widths=(8, width, width, 2),
+    )
+
+
+# paper Table hyperparameters: completion tolerances (xi, eta, phi, v)
+EPS = (1.0, 0.25, 10 * math.pi / 180, 5 / 3.6)
+
+
+def philox_seed(scene_seed: int) -> int:
+    return 0x5EED0000 + int(scene_seed)
+
+
+# ------------------------------------------------------------------ scenes
+def scene_single(seed: int = 0, N: int = 256, T: int = 20, M: int = 200, width: int = 16):
+    rng = np.random.default_rng(1000 + seed)
+    x0, y0 = rng.uniform(-100, 100, 2)
+    phi0 = rng.uniform(-math.pi, math.pi)
+    pts = []
+    while len(pts) < M:
+        p = rng.uniform(-20, 20, 2)
+        if p[0] ** 2 + p[1] ** 2 >= 25.0:
+            pts.append(p)
+    pts = np.array(pts).reshape(-1, 2) + [x0, y0]
+    obs = np.zeros((M, 4))
+    obs[:, :2] = pts
+    g = rng.uniform(-20, 20, 2) + [x0, y0]
+    goal = np.array([g[0], g[1], rng.uniform(-math.pi, math.pi), 0.0])
+    state = np.array([x0, y0, phi0, 0.0, 0.0, 0.0])
+    return dict(preset=planner(width), state=state, goal=goal, obs=obs, N=N, T=T,
+                seed=philox_seed(seed), t_index=0)
+
+
+def _square_outline(cx, cy, half_l, half_w, heading, n):
+    """n points evenly spaced along a rectangle's perimeter."""
+    per = 4 * (half_l + half_w)
+    s = (np.arange(n) + 0.5) * per / n
+    pts = np.zeros((n, 2))
+    for i, d in enumerate(s):
+        if d < 2 * half_l:
+            pts[i] = (-half_l + d, -half_w)
+        elif d < 2 * half_l + 2 * half_w:
+            pts[i] = (half_l, -half_w + d - 2 * half_l)
+        elif d < 4 * half_l + 2 * half_w:
+            pts[i] = (half_l - (d - 2 * half_l - 2 * half_w), half_w)
+        else:
+            pts[i] = (-half_l, half_w - (d - 4 * half_l - 2 * half_w))
+    c, s_ = math.cos(heading), math.sin(heading)
+    return np.stack([cx + c * pts[:, 0] - s_ * pts[:, 1], cy + s_ * pts[:, 0] + c * pts[:, 1]], 1)
+
+
+COURSE_WAYPOINTS = np.array([
+    [15.0, 0.0, math.pi / 2, 0.0],
+    [15.0, 15.0, math.pi, 0.0],
+    [0.0, 15.0, -math.pi / 2, 0.0],
+    [0.0, 0.0, 0.0, 0.0],
+])
+
+
+def scene_course(seed: int = 0, N: int = 16384, T: int = 40, width: int = 32,
+                 n_wall: int = 1000, n_island: int = 500, n_dyn: int = 500, vmax: float = 3.0):
+    rng = np.random.default_rng(2000 + seed)
+    wall = _square_outline(7.5, 7.5, 15.5, 15.5, 0.0, n_wall)
+    half = n_island // 2
+    island = np.concatenate([_square_outline(7.5, 7.5, 2.5, 2.5, 0.0, half),
+                             rng.uniform(5.0, 10.0, (n_island - half, 2))])
+    n_clusters = max(1, n_dyn // 50)
+    dyn = []
+    vel = []
+    per = [n_dyn // n_clusters + (1 if i < n_dyn % n_clusters else 0) for i in range(n_clusters)]
+    for k in range(n_clusters):
+        while True:
+            c = rng.uniform(-6.0, 21.0, 2)
+            if np.hypot(*c) > 8.0 and not (3.0 < c[0] < 12.0 and 3.0 < c[1] < 12.0):
+                break
+        hd = rng.uniform(-math.pi, math.pi)
+        speed = rng.uniform(0.0, vmax)
+        vh = rng.uniform(-math.pi, math.pi)
+        dyn.append(_square_outline(c[0], c[1], 2.25, 0.9, hd, per[k]))
+        vel.append(np.tile([speed * math.cos(vh), speed * math.sin(vh)], (per[k], 1)))
+    dyn = np.concatenate(dyn)
+    vel = np.concatenate(vel)
+    obs = np.zeros((n_wall + n_island + n_dyn, 4))
+    obs[:n_wall, :2] = wall
+    obs[n_wall:n_wall + n_island, :2] = island
+    obs[n_wall + n_island:, :2] = dyn
+    obs[n_wall + n_island:, 2:] = vel
+    state = np.array([0.0, 0.0, 0.0, 0.0, 0.0, 0.0])
+    return dict(preset=planner(width), state=state, goal=COURSE_WAYPOINTS[0].copy(), obs=obs,
+                N=N, T=T, seed=philox_seed(seed), t_index=0, waypoints=COURSE_WAYPOINTS.copy())
+
+
+def tiny_scene(seed: int, N: int, T: int, M: int, width: int = 16, box: float = 12.0,
+               dyn_frac: float = 0.3, vmax: float = 3.0, clear: float = 3.0):
+    """Small random instance for exhaustive checks: M points uniform in a
+    box around a random start pose (none within `clear` m of it), a fraction
+    moving, a random goal, random start speed and last controls."""
+    rng = np.random.default_rng(3000 + seed)
+    x0, y0 = rng.uniform(-30, 30, 2)
+    phi0 = rng.uniform(-math.pi, math.pi)
+    pts = []
+    while len(pts) < M:
+        p = rng.uniform(-box, box, 2)
+        if np.hypot(*p) >= clear:
+            pts.append(p)
+    obs = np.zeros((M, 4))
+    if M:
+        obs[:, :2] = np.array(pts) + [x0, y0]
+        nd = int(round(dyn_frac * M))
+        sp = rng.uniform(0, vmax, nd)
+        hd = rng.uniform(-math.pi, math.pi, nd)
+        obs[:nd, 2] = sp * np.cos(hd)
+        obs[:nd, 3] = sp * np.sin(hd)
+    g = rng.uniform(-box, box, 2) + [x0, y0]
+    goal = np.array([g[0], g[1], rng.uniform(-math.pi, math.pi), rng.uniform(-2, 2)])
+    state = np.array([x0, y0, phi0, rng.uniform(-3, 3), rng.uniform(-1, 1), rng.uniform(-1, 1)])
+    return dict(preset=planner(width), state=state, goal=goal, obs=obs, N=N, T=T,
+                seed=philox_seed(seed), t_index=int(rng.integers(0, 1000)))

@@ -1,0 +1,362 @@
+#!/usr/bin/env python
+"""Planner benchmark: rollout-steps/s of the closed-loop plan step.
+
+Workload (one GPU): the forward/reverse waypoint course, N = 16384 sampled
+8-32-32-2 networks per plan step, horizon T = 40, 2000 obstacle points (500
+on moving car outlines), 100 sampling times of closed loop at most.  A
+"step" is one plan step at one sampling time: sampling, rollout with
+collision checks, selection and the winner epilogue.  The simulated vehicle
+and the obstacles advance between steps on the host (outside the timed
+region); the winner's parameters warm-start the next step.
+
+value   = N * T * K / (sum of the K plan steps' device time), inputs resident
+          in HBM, L2 flushed (256 MiB write) between steps, CUDA events on the
+          launching stream;
+e2e     = the same through the host-buffer entry point (host->device copy of
+          the obstacles and warm start, plan, device->host copy of the
+          result, synchronise), wall clock;
+roofline = the rollout kernel: algorithmic FP32 instructions (6 per
+          point-check of a live sample, W^2 + 10 W + 30 per live control
+          step) over its event-timed duration, against the FP32 issue peak
+          152 SMs x 128 lanes x 2.07 GHz.
+
+`--impl reference` times the CPU oracle on the host cores on the same
+workload with a bounded number of samples per step.
+Multi-GPU (torchrun): every rank plans its own course scene (weak scaling,
+no collective on the data path); max over ranks.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "rollout-steps/s (N×T incl. M-point checks)"
+UNIT = "rollout-steps/s"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="npp", choices=["npp", "reference"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return float("nan")
+        sm = [num(r[1]) for r in rows]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, val in zip(names, r[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": float(np.nanmedian(sm)), "sm_max_mhz": float(np.nanmax([num(r[2]) for r in rows])),
+                "power_w_max": float(np.nanmax([num(r[3]) for r in rows])), "samples": len(rows),
+                "reasons": sorted(reasons)}
+
+
+def course_setup(seed):
+    from paper_1904_06680_gb300 import inputs
+    sc = inputs.scene_course(seed=seed)
+    return sc
+
+
+def algorithmic_instr(first_hit, T, M, W):
+    """FP32 instructions the rollout needs: 6 per point-check of a live
+    sample (4 FMA + 2 min/max), W^2 + 10 W + 30 per live control step."""
+    fh = np.asarray(first_hit)
+    checks = np.where(fh < 0, T + 1, fh + 1).sum()
+    ctrl = np.where(fh < 0, T, fh).sum()
+    return float(checks) * 6.0 * M + float(ctrl) * (W * W + 10 * W + 30)
+
+
+def cpu_baseline(sc, state, goal, obs, T, target_cpu_s=15.0):
+    """Oracle (as it stands) on the host cores: a bounded sample of the first
+    plan step's samples, every one over the full horizon."""
+    from oracle import oracle as orc
+    p = sc["preset"]
+    cores = os.cpu_count() or 1
+    goal_ev, obs_ev = orc.frame_to_ev(state, goal, obs)
+    z0 = [0.0, 0.0, 0.0, state[3]]
+    probe = np.arange(64, dtype=np.int32)
+    t0 = time.perf_counter()
+    orc.rollout_samples(p, sc["seed"], 0, probe, z0, state[4:6], goal_ev, obs_ev, T, n_threads=1,
+                        record=False)
+    per_sample = max(time.perf_counter() - t0, 1e-6) / len(probe)
+    K = int(min(sc["N"], max(256, target_cpu_s / per_sample)))
+    idx = np.arange(K, dtype=np.int32)
+    t0 = time.perf_counter()
+    orc.rollout_samples(p, sc["seed"], 0, idx, z0, state[4:6], goal_ev, obs_ev, T, n_threads=cores,
+                        record=False)
+    wall = time.perf_counter() - t0
+    return {"value": K * T / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "first plan step of the course scene: samples 0..%d of %d over the full "
+                      "horizon T=%d, M=%d points, FP64 C with OpenMP (%.1f s wall)"
+                      % (K - 1, sc["N"], T, obs.shape[0], wall)}
+
+
+def run_npp(args):
+    import torch
+    from paper_1904_06680_gb300 import closed_loop, inputs, npp
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sc = course_setup(args.seed + rank)
+    p = sc["preset"]
+    N, T = sc["N"], sc["T"]
+    W = p["widths"][1]
+    M = sc["obs"].shape[0]
+    K, Wu = args.steps, args.warmup
+    pl = npp.Planner(p, max_N=N, max_T=T, max_M=M, device=local)
+    npp.npp_set_timing(pl.h, True)
+    obs_dev = torch.empty(M, 4, dtype=torch.float32, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
+
+    def closed_loop_pass(host_api: bool, nsteps: int, record: bool):
+        state = sc["state"].copy()
+        obs = sc["obs"].copy()
+        mission = closed_loop.Mission(sc["waypoints"], inputs.EPS)
+        warm_dev = None
+        warm_host = None
+        out = dict(step_ms=[], rollout_ms=[], wall_ms=[], instr=0.0, free=[], best_cost=[])
+        if host_api:
+            obs_pin = torch.empty(M, 4, dtype=torch.float32).pin_memory()
+            hb = npp.npp_best()
+            params_h = torch.empty(pl.n_theta, dtype=torch.float32).pin_memory()
+            ctrl_h = torch.empty(T, 2, dtype=torch.float32).pin_memory()
+            traj_h = torch.empty(T + 1, 4, dtype=torch.float32).pin_memory()
+            warm_pin = torch.empty(pl.n_theta, dtype=torch.float32).pin_memory()
+            import ctypes
+            o = npp.npp_outputs()
+            o.best = ctypes.addressof(hb)
+            o.params = params_h.data_ptr()
+            o.controls = ctrl_h.data_ptr()
+            o.trajectory = traj_h.data_ptr()
+        for t in range(nsteps):
+            goal = mission.goal
+            if host_api:
+                obs_pin.copy_(torch.from_numpy(obs.astype(np.float32)))
+                flush.zero_()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                npp.npp_plan_step_host(pl.h, state, goal, obs_pin, M, N, T, sc["seed"], t,
+                                       warm_pin if warm_host else None, o)
+                wall = (time.perf_counter() - t0) * 1e3
+                a = ctrl_h[0].numpy().astype(np.float64)
+                warm_pin.copy_(params_h)
+                warm_host = True
+                if record:
+                    out["wall_ms"].append(wall)
+            else:
+                obs_dev.copy_(torch.from_numpy(obs.astype(np.float32)))
+                flush.zero_()
+                torch.cuda.synchronize()
+                pl.plan(state, goal, obs_dev, N, T, sc["seed"], t, warm=warm_dev)
+                r_ms, s_ms = npp.npp_last_timing(pl.h)
+                fh = pl.first_hit[:N].cpu().numpy()
+                a = pl.controls[0].cpu().numpy().astype(np.float64)
+                b = pl.best.cpu()
+                if warm_dev is None:
+                    warm_dev = torch.empty_like(pl.params)
+                warm_dev.copy_(pl.params)
+                if record:
+                    out["step_ms"].append(s_ms)
+                    out["rollout_ms"].append(r_ms)
+                    out["instr"] += algorithmic_instr(fh, T, M, W)
+                    out["free"].append(float(np.mean(fh < 0)))
+                    out["best_cost"].append(float(b[2:3].view(torch.float32).item()))
+            state = closed_loop.plant_step(p, state, a)
+            obs = closed_loop.advance_obstacles(obs, p["Ts"])
+            mission.update(state)
+        out["waypoints_reached"] = mission.k
+        return out
+
+    # warm-up (untimed) then K timed steps of the device path
+    closed_loop_pass(False, Wu, record=False)
+    clocks = Clocks(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    res = closed_loop_pass(False, K, record=True)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    total_ms = float(np.sum(res["step_ms"]))
+    rollout_ms = float(np.sum(res["rollout_ms"]))
+    e2e = None
+    if not args.no_e2e:
+        closed_loop_pass(True, min(Wu, 3), record=False)
+        r2 = closed_loop_pass(True, K, record=True)
+        wall = float(np.sum(r2["wall_ms"]))
+        e2e = {"value": N * T * K / (wall / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": M * 16 + pl.n_theta * 4,
+               "d2h_bytes_per_step": 32 + pl.n_theta * 4 + T * 8 + (T + 1) * 16}
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        tt = torch.tensor([total_ms, rollout_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms, rollout_ms = float(tt[0]), float(tt[1])
+        if e2e:
+            ev = torch.tensor([N * T * K / e2e["value"]], dtype=torch.float64, device=dev)
+            dist.all_reduce(ev, op=dist.ReduceOp.MAX)
+            e2e["value"] = world * N * T * K / float(ev[0])
+    value = world * N * T * K / (total_ms / 1e3)
+    instr_per_s = res["instr"] / (rollout_ms / 1e3)
+    peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6
+    roofline = {"bound": "alu", "kernel": "rollout_kernel<32,8,8>",
+                "achieved": instr_per_s / 1e12, "peak": peak / 1e12,
+                "unit": "T FP32-instr/s", "frac": instr_per_s / peak, "traffic": None,
+                "peak_basis": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz"}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": Wu, "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "closed-loop forward/reverse waypoint course: N=16384 samples, "
+                                   "T=40, MLP 8-32-32-2, M=2000 points (500 moving), one plan "
+                                   "step per sampling time",
+                       "N": N, "T": T, "M": M, "width": W, "parallelism": "replicas (rank = scene)",
+                       "l2": "flushed (256 MiB write) between timed steps",
+                       "timing": "sum of per-step CUDA-event durations on the launching stream"},
+            "roofline": roofline, "e2e": e2e, "gpu_launches": 2 * K, "clocks": ck,
+            "rollout_ms_per_step": rollout_ms / K,
+            "free_fraction": float(np.mean(res["free"])),
+            "waypoints_reached": res["waypoints_reached"]}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(sc, sc["state"], sc["waypoints"][0], sc["obs"], T)
+    pl.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def run_reference(args):
+    """The CPU oracle as it stands, timed on the host cores, on the same
+    closed-loop workload with a bounded number of samples per plan step."""
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    from oracle import oracle as orc
+    from paper_1904_06680_gb300 import closed_loop, inputs
+    sc = course_setup(args.seed)
+    p = sc["preset"]
+    T = sc["T"]
+    M = sc["obs"].shape[0]
+    cores = os.cpu_count() or 1
+    Ns = 2048
+    state = sc["state"].copy()
+    obs = sc["obs"].copy()
+    mission = closed_loop.Mission(sc["waypoints"], inputs.EPS)
+    warm = None
+    times = []
+    for t in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        r = orc.plan(p, state, mission.goal, obs, Ns, T, sc["seed"], t, warm=warm, n_threads=cores)
+        dt = time.perf_counter() - t0
+        if t >= args.warmup:
+            times.append(dt)
+        warm = r["best_theta"]
+        state = closed_loop.plant_step(p, state, r["controls"][0])
+        obs = closed_loop.advance_obstacles(obs, p["Ts"])
+        mission.update(state)
+    total = float(np.sum(times))
+    value = Ns * T * args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "closed-loop forward/reverse waypoint course: T=40, MLP "
+                                   "8-32-32-2, M=2000 points (500 moving)", "N": Ns, "T": T, "M": M},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d samples per plan step (of 16384) over the full horizon, "
+                                       "FP64 C oracle with OpenMP" % Ns},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_npp(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,185 @@
+/*
+ * npp.h -- C ABI of the GB300 planner library (libnpp.so).
+ *
+ * The library implements the per-sampling-time batched rollout of Plessen,
+ * "Online Sampling in the Parameter Space of a Neural Network for
+ * GPU-accelerated Motion Planning of Autonomous Vehicles" (arXiv 1904.06680):
+ * N neural-network controller parameter vectors are sampled, each one is held
+ * fixed over a T-step horizon while the evolving feature vector drives it
+ * (Sect. II-D "Sixth", Eq. eq_def_stph), the controls are integrated through
+ * the kinematic vehicle model (Sect. IV), every state is checked against
+ * obstacle points extrapolated at constant velocity with the polytope
+ * inequalities of Eq. eq_Apsietc_collAvoidIneqs, and the best sample is
+ * returned (a_t = X(s_t, theta*), Eq. eq_def_at_mathcalXetc).
+ *
+ * Conventions shared by every entry point:
+ *  - Plain C types only.  Pointers named *_dev are device pointers on the
+ *    handle's device; pointers named *_host are host pointers.  The caller
+ *    owns every buffer it passes; the handle owns its own workspaces.
+ *  - Calls taking a `stream` are asynchronous on that CUDA stream (a
+ *    cudaStream_t passed as void*, NULL = legacy default stream); their
+ *    device outputs are valid once the stream has reached that point.
+ *    Calls without a stream are synchronous.
+ *  - World frame: x, y in m, heading phi in rad (counter-clockwise from +x),
+ *    speed v in m/s (negative = reverse).  Obstacle points are 4 floats
+ *    (x, y, vx, vy): position and constant velocity (Sect. II-D item (i)
+ *    describes points by position, heading and speed; vx = speed cos heading,
+ *    vy = speed sin heading).  Arrays of points are [M][4], 16-byte aligned.
+ *  - Parameter vectors theta hold, per layer, W[out][in] row-major then
+ *    b[out], for the network [n_in = 8, width, width, 2], tanh on every
+ *    layer; n_theta = 12 width + width^2 + 2 (450, 1410, 4866 for widths
+ *    16, 32, 64).
+ *  - Sampling: theta_n[i] is entry (i mod 4) of the Box-Muller normals made
+ *    from Philox4x32-10(counter = (i / 4, n, t_index, stream_id),
+ *    key = (seed & 0xffffffff, seed >> 32)); words 0,1 give entries 0,1 and
+ *    words 2,3 give entries 2,3; within a pair the first word sets the radius
+ *    sqrt(-2 ln u) and the second the angle 2 pi u, with
+ *    u = (2 (w >> 9) + 1) 2^-24.  The results are reproducible bit for bit.
+ *  - Results are a pure function of the inputs, seed and t_index: the launch
+ *    shape does not change any per-sample arithmetic, and ties in cost go to
+ *    the lowest sample index.
+ *  - Errors: every call returns an npp_status; npp_last_error(h) gives a
+ *    human-readable message for the last failing call on that handle.
+ *    Invalid arguments are rejected before any work is queued.
+ */
+#ifndef NPP_H_
+#define NPP_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    NPP_OK = 0,
+    NPP_INVALID_ARG = 1,    /* bad size, pointer, alignment or non-finite scalar */
+    NPP_INFEASIBLE = 2,     /* not an error: every sample collided (Sect. II-D
+                               "Third": no collision-free trajectory is
+                               guaranteed); the result is the sample whose
+                               first collision comes last */
+    NPP_CUDA_ERROR = 3,     /* a CUDA runtime call failed */
+    NPP_DEVICE_TIMEOUT = 4, /* a bounded device-side wait gave up */
+    NPP_UNSUPPORTED = 5     /* configuration outside what the library builds */
+} npp_status;
+
+/* Vehicle, footprint, feature, cost and network constants.  The model
+ * constants play the role of the paper's Table veh and Table
+ * hyperparameters; they are fixed per handle ("defined directly on the
+ * GPU", Sect. II-D "First" and "Fourth"). */
+typedef struct {
+    float lf, lr;              /* CoG to front / rear axle [m]                   */
+    float delta_max;           /* steering limit [rad]; delta = delta_max a[0]   */
+    float delta_rate_max;      /* steering-rate limit [rad/s]                    */
+    float u_min, u_max;        /* acceleration range; u = u_min + (a[1]+1)/2 (u_max-u_min) */
+    float Ts;                  /* sampling time and Euler step [s]               */
+    float half_len, half_wid;  /* rectangle half length / half width [m]        */
+    float c_off;               /* rectangle centre ahead of the reference point [m] */
+    float dxi_n, deta_n, dphi_n, dv_n; /* feature normalisation (Delta constants) */
+    float w_pos, w_phi, w_v, w_effort; /* cost weights                          */
+    int32_t n_in;              /* network inputs: must be 8                      */
+    int32_t width;             /* hidden width: 16, 32 or 64                     */
+    int32_t max_N, max_T, max_M; /* workspace capacity of the handle             */
+} npp_config;
+
+/* Vehicle state at the sampling time (world frame) with the controls applied
+ * at the previous sampling time, a_{t-1} (normalised, in [-1, 1]). */
+typedef struct { float x, y, phi, v, a_prev0, a_prev1; } npp_state;
+
+/* Goal setpoint zeta_goal = [x, y, phi, v] (world frame). */
+typedef struct { float x, y, phi, v; } npp_goal;
+
+/* Device-side summary of one plan step. */
+typedef struct {
+    int32_t best_idx;   /* winning sample index                              */
+    int32_t status;     /* NPP_OK or NPP_INFEASIBLE                          */
+    float best_cost;    /* its cost (+inf when infeasible)                   */
+    int32_t first_hit;  /* its first colliding horizon index, -1 if none     */
+    int32_t reserved[4];
+} npp_best;
+
+/* Output buffers of a plan step; all device pointers, any may be NULL except
+ * `best`.  Trajectory and controls are those of the winning sample in the
+ * world frame; for an infeasible winner the rows after its first collision
+ * repeat the colliding state and the controls there are 0. */
+typedef struct {
+    npp_best* best;          /* [1]                                          */
+    float* params;           /* [n_theta]   winning parameter vector         */
+    float* controls;         /* [T][2]      applied normalised controls      */
+    float* trajectory;       /* [T+1][4]    (x, y, phi, v)                   */
+    float* costs;            /* [N]         per-sample cost, +inf if collided */
+    int32_t* first_hit;      /* [N]         first colliding h, -1 if none    */
+    float* sample_traj;      /* [T+1][N][4] every sample's states, EV frame at t
+                                (origin at the vehicle, x along its heading) */
+    float* sample_ctrl;      /* [T][N][2]   every sample's applied controls   */
+} npp_outputs;
+
+typedef struct npp_handle npp_handle;
+
+/* Create a handle on CUDA device `device`: validates the configuration and
+ * allocates device workspaces for up to max_N samples, max_T steps and max_M
+ * obstacle points.  *h is set to NULL on failure. */
+npp_status npp_create(npp_handle** h, const npp_config* cfg, int32_t device);
+
+/* Free the handle and its workspaces (waits for its device work). */
+npp_status npp_destroy(npp_handle* h);
+
+/* Message for the last failing call on h (or a global message if h is NULL);
+ * the pointer stays valid until the next call on the same handle. */
+const char* npp_last_error(const npp_handle* h);
+
+/* Number of network parameters of cfg's network, or -1 if unsupported. */
+int32_t npp_n_theta(const npp_config* cfg);
+
+/* One plan step (Step 5 of Alg. 1): sample N parameter vectors (sample 0 is
+ * warm_dev when non-NULL, the warm start theta*_{t-1} of Sect. II-D "Fifth"),
+ * roll each out over T steps from `state` towards `goal` among the M
+ * obstacle points obs_dev (world frame, [M][4], may be NULL when M = 0), and
+ * reduce to the best sample.  1 <= N <= max_N, 1 <= T <= max_T,
+ * 0 <= M <= max_M.  Asynchronous on `stream`; outputs as in npp_outputs. */
+npp_status npp_plan_step(npp_handle* h, const npp_state* state, const npp_goal* goal,
+                         const float* obs_dev, int32_t M, int32_t N, int32_t T,
+                         uint64_t seed, uint32_t t_index, const float* warm_dev,
+                         const npp_outputs* out, void* stream);
+
+/* The same plan step with HOST buffers: copies obs_host (and warm_host) to
+ * the device, runs npp_plan_step on the handle's own stream, copies the
+ * summary and the requested outputs back to the host pointers in out_host
+ * (fields as in npp_outputs, host memory; sample_traj and sample_ctrl must
+ * be NULL) and synchronises.  Returns NPP_INFEASIBLE when every sample
+ * collided. */
+npp_status npp_plan_step_host(npp_handle* h, const npp_state* state, const npp_goal* goal,
+                              const float* obs_host, int32_t M, int32_t N, int32_t T,
+                              uint64_t seed, uint32_t t_index, const float* warm_host,
+                              const npp_outputs* out_host);
+
+/* Roll out K explicit parameter vectors theta_dev[K][n_theta] (no sampling,
+ * no selection): writes costs[K], first_hit[K] and, when non-NULL, every
+ * rollout's states sample_traj[T+1][K][4] and controls sample_ctrl[T][K][2]
+ * in the EV frame at t.  For closed-form and regression checks. */
+npp_status npp_rollout_params(npp_handle* h, const npp_state* state, const npp_goal* goal,
+                              const float* obs_dev, int32_t M, const float* theta_dev,
+                              int32_t K, int32_t T, float* costs_dev, int32_t* first_hit_dev,
+                              float* sample_traj_dev, float* sample_ctrl_dev, void* stream);
+
+/* The sampled parameter vectors of samples n0 .. n0+K-1 (see "Sampling"
+ * above) written to out_dev[K][n_theta], rows of exactly n_theta entries.
+ * 0 <= n0, 1 <= K, 1 <= n_theta. */
+npp_status npp_sample_params(uint64_t seed, uint32_t t_index, uint32_t stream_id,
+                             int32_t n0, int32_t K, int32_t n_theta, float* out_dev,
+                             void* stream);
+
+/* Kernel timing for measurement: when enabled, npp_plan_step and
+ * npp_rollout_params record CUDA events on their stream around the rollout
+ * kernel and around the whole step (rollout + epilogue).  npp_last_timing
+ * synchronises on the last recorded end event and returns both durations in
+ * milliseconds.  Disabled by default; enabling it adds two event records per
+ * call. */
+npp_status npp_set_timing(npp_handle* h, int32_t enable);
+npp_status npp_last_timing(npp_handle* h, float* rollout_ms, float* step_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NPP_H_ */

@@ -1,0 +1,459 @@
+// npp_api.cu -- handle, argument validation, small kernels (winner epilogue,
+// parameter sampler) and the extern "C" entry points declared in npp.h.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <algorithm>
+#include <cstring>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "../../include/npp.h"
+#include "npp_device.cuh"
+
+using namespace npp;
+
+struct npp_handle {
+    npp_config cfg;
+    int device;
+    int n_theta;
+    int max_points;                      // obstacle points that fit in shared memory
+    DevCfg dc;
+    unsigned long long* d_key;           // packed best key
+    float4* d_traj;                      // [(max_T+1) * max_N]
+    float2* d_ctrl;                      // [max_T * max_N]
+    // host-mode staging
+    float4* d_obs;
+    float* d_warm;
+    npp_best* d_best;
+    float* d_params;
+    float* d_controls;
+    float* d_trajectory;
+    float* d_costs;
+    int32_t* d_fh;
+    cudaStream_t stream;
+    bool timing;
+    cudaEvent_t ev[3];                   // step start, rollout end, step end
+    std::string err;
+};
+
+static std::string g_err;
+
+static npp_status fail(npp_handle* h, npp_status s, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf; else g_err = buf;
+    return s;
+}
+
+#define CUDA_TRY(h, call)                                                                  \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail((h), NPP_CUDA_ERROR, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+static int n_theta_of(int width) { return 12 * width + width * width + 2; }
+
+static bool finite_all(const float* p, int n)
+{
+    for (int i = 0; i < n; ++i) if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+// ------------------------------------------------------------------ kernels
+namespace {
+
+// Winner epilogue: decode the packed key, write the summary record, the
+// winner's world-frame trajectory and controls, and regenerate its
+// parameters from Philox (or copy the warm start).
+__global__ void epilogue_kernel(const EpilogueArgs e)
+{
+    const unsigned long long key = *e.best_key;
+    const int idx = (int)(key & 0xffffffffull);
+    const bool dead = (key >> 63) != 0;
+    const unsigned hi = (unsigned)((key >> 32) & 0x7fffffffu);
+    const int fh = dead ? e.T - (int)hi : -1;
+    const int last = dead ? fh : e.T;
+    if (threadIdx.x == 0) {
+        npp_best* b = reinterpret_cast<npp_best*>(e.best);
+        b->best_idx = idx;
+        b->status = dead ? NPP_INFEASIBLE : NPP_OK;
+        b->best_cost = dead ? __int_as_float(0x7f800000) : __uint_as_float(hi);
+        b->first_hit = fh;
+        b->reserved[0] = b->reserved[1] = b->reserved[2] = b->reserved[3] = 0;
+    }
+    float s0, c0;
+    sincosf(e.phi0, &s0, &c0);
+    if (e.trajectory) {
+        for (int h = threadIdx.x; h <= e.T; h += blockDim.x) {
+            const float4 z = e.traj[(size_t)min(h, last) * e.N + idx];
+            float4 w;
+            w.x = e.x0 + c0 * z.x - s0 * z.y;
+            w.y = e.y0 + s0 * z.x + c0 * z.y;
+            w.z = e.phi0 + z.z;
+            w.w = z.w;
+            reinterpret_cast<float4*>(e.trajectory)[h] = w;
+        }
+    }
+    if (e.controls) {
+        for (int h = threadIdx.x; h < e.T; h += blockDim.x) {
+            float2 a = make_float2(0.f, 0.f);
+            if (h < last) a = e.ctrl[(size_t)h * e.N + idx];
+            reinterpret_cast<float2*>(e.controls)[h] = a;
+        }
+    }
+    if (e.params) {
+        if (e.warm && idx == 0) {
+            for (int i = threadIdx.x; i < e.n_theta; i += blockDim.x) e.params[i] = e.warm[i];
+        } else {
+            for (int q = threadIdx.x; 4 * q < e.n_theta; q += blockDim.x) {
+                const float4 v = sample_quad(e.key, (uint32_t)q, (uint32_t)idx);
+                const float vv[4] = { v.x, v.y, v.z, v.w };
+                for (int j = 0; j < 4 && 4 * q + j < e.n_theta; ++j) e.params[4 * q + j] = vv[j];
+            }
+        }
+    }
+}
+
+__global__ void sample_params_kernel(SamplerKey key, int n0, int K, int nt, float* out)
+{
+    const int nq = (nt + 3) / 4;
+    const long long total = (long long)K * nq;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(t / nq), q = (int)(t % nq);
+        const float4 v = sample_quad(key, (uint32_t)q, (uint32_t)(n0 + k));
+        const float vv[4] = { v.x, v.y, v.z, v.w };
+        float* row = out + (size_t)k * nt;
+        for (int j = 0; j < 4 && 4 * q + j < nt; ++j) row[4 * q + j] = vv[j];
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ helpers
+static cudaError_t launch_rollout(const npp_handle* h, const RolloutArgs& a, cudaStream_t s)
+{
+    int smem = 0;
+    switch (h->cfg.width) {
+    case 16: return launch_rollout_w16(a, s, &smem);
+    case 32: return launch_rollout_w32(a, s, &smem);
+    default: return launch_rollout_w64(a, s, &smem);
+    }
+}
+
+static SamplerKey make_key(uint64_t seed, uint32_t t_index, uint32_t stream_id)
+{
+    SamplerKey k;
+    k.k0 = (uint32_t)(seed & 0xffffffffu);
+    k.k1 = (uint32_t)(seed >> 32);
+    k.t_index = t_index;
+    k.stream_id = stream_id;
+    return k;
+}
+
+static npp_status check_state_goal(npp_handle* h, const npp_state* s, const npp_goal* g)
+{
+    if (!s || !g) return fail(h, NPP_INVALID_ARG, "state and goal must not be NULL");
+    if (!finite_all(&s->x, 6)) return fail(h, NPP_INVALID_ARG, "state has a non-finite entry");
+    if (!finite_all(&g->x, 4)) return fail(h, NPP_INVALID_ARG, "goal has a non-finite entry");
+    if (std::fabs(s->a_prev0) > 1.0f || std::fabs(s->a_prev1) > 1.0f)
+        return fail(h, NPP_INVALID_ARG, "previous controls must lie in [-1, 1]");
+    return NPP_OK;
+}
+
+static npp_status check_sizes(npp_handle* h, int32_t M, int32_t N, int32_t T, const void* obs)
+{
+    const npp_config& c = h->cfg;
+    if (N < 1 || N > c.max_N) return fail(h, NPP_INVALID_ARG, "N=%d outside [1, %d]", N, c.max_N);
+    if (T < 1 || T > c.max_T) return fail(h, NPP_INVALID_ARG, "T=%d outside [1, %d]", T, c.max_T);
+    if (M < 0 || M > c.max_M) return fail(h, NPP_INVALID_ARG, "M=%d outside [0, %d]", M, c.max_M);
+    if (M > 0 && !obs) return fail(h, NPP_INVALID_ARG, "obstacle pointer is NULL with M=%d", M);
+    if (obs && (reinterpret_cast<uintptr_t>(obs) & 15u))
+        return fail(h, NPP_INVALID_ARG, "obstacle array must be 16-byte aligned");
+    return NPP_OK;
+}
+
+static void fill_rollout_args(const npp_handle* h, RolloutArgs& a, const npp_state* s,
+                              const npp_goal* g, const float* obs, int32_t M, int32_t N, int32_t T)
+{
+    memset(&a, 0, sizeof a);
+    a.c = h->dc;
+    a.x0 = s->x; a.y0 = s->y; a.phi0 = s->phi; a.v0 = s->v; a.ap0 = s->a_prev0; a.ap1 = s->a_prev1;
+    a.gx = g->x; a.gy = g->y; a.gphi = g->phi; a.gv = g->v;
+    a.obs = reinterpret_cast<const float4*>(obs);
+    a.M = M; a.N = N; a.T = T;
+}
+
+// ------------------------------------------------------------------ C ABI
+extern "C" {
+
+int32_t npp_n_theta(const npp_config* cfg)
+{
+    if (!cfg || cfg->n_in != 8) return -1;
+    if (cfg->width != 16 && cfg->width != 32 && cfg->width != 64) return -1;
+    return n_theta_of(cfg->width);
+}
+
+const char* npp_last_error(const npp_handle* h)
+{
+    return h ? h->err.c_str() : g_err.c_str();
+}
+
+npp_status npp_create(npp_handle** out, const npp_config* cfg, int32_t device)
+{
+    if (!out) return fail(nullptr, NPP_INVALID_ARG, "handle pointer is NULL");
+    *out = nullptr;
+    if (!cfg) return fail(nullptr, NPP_INVALID_ARG, "config is NULL");
+    if (npp_n_theta(cfg) < 0)
+        return fail(nullptr, NPP_UNSUPPORTED, "network [%d, %d, %d, 2] is not built (n_in 8; width 16, 32, 64)",
+                    cfg->n_in, cfg->width, cfg->width);
+    const float* f = &cfg->lf;
+    if (!finite_all(f, 18)) return fail(nullptr, NPP_INVALID_ARG, "config has a non-finite constant");
+    if (!(cfg->lf + cfg->lr > 0.f) || !(cfg->lr >= 0.f) || !(cfg->delta_max > 0.f) ||
+        !(cfg->delta_rate_max > 0.f) || !(cfg->u_max >= cfg->u_min) || !(cfg->Ts > 0.f) ||
+        !(cfg->half_len > 0.f) || !(cfg->half_wid > 0.f) || !(cfg->dxi_n > 0.f) ||
+        !(cfg->deta_n > 0.f) || !(cfg->dphi_n > 0.f) || !(cfg->dv_n > 0.f))
+        return fail(nullptr, NPP_INVALID_ARG, "config constant out of range");
+    if (cfg->max_N < 1 || cfg->max_T < 1 || cfg->max_M < 0)
+        return fail(nullptr, NPP_INVALID_ARG, "capacity max_N, max_T >= 1, max_M >= 0 required");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+        return fail(nullptr, NPP_CUDA_ERROR, "CUDA device %d not available", device);
+    if (cudaSetDevice(device) != cudaSuccess)
+        return fail(nullptr, NPP_CUDA_ERROR, "cudaSetDevice(%d) failed", device);
+    int smem_optin = 0;
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    int max_points = cfg->width == 16 ? rollout_max_points_w16(smem_optin)
+                   : cfg->width == 32 ? rollout_max_points_w32(smem_optin)
+                                      : rollout_max_points_w64(smem_optin);
+    if (cfg->max_M > max_points)
+        return fail(nullptr, NPP_UNSUPPORTED, "max_M=%d exceeds the %d points held in shared memory",
+                    cfg->max_M, max_points);
+    if ((double)(cfg->max_T + 1) * cfg->max_N * 24.0 > 64e9)
+        return fail(nullptr, NPP_INVALID_ARG, "workspace for max_N x max_T too large");
+
+    npp_handle* h = new npp_handle();
+    h->cfg = *cfg;
+    h->device = device;
+    h->n_theta = n_theta_of(cfg->width);
+    h->max_points = max_points;
+    DevCfg& d = h->dc;
+    const double L = (double)cfg->lf + cfg->lr;
+    d.delta_max = cfg->delta_max;
+    d.r_rate = (float)((double)cfg->delta_rate_max * cfg->Ts / cfg->delta_max);
+    d.lrL = (float)(cfg->lr / L);
+    d.iL = (float)(1.0 / L);
+    d.umid = (float)(0.5 * ((double)cfg->u_min + cfg->u_max));
+    d.uhalf = (float)(0.5 * ((double)cfg->u_max - cfg->u_min));
+    d.Ts = cfg->Ts;
+    d.ihl = (float)(1.0 / cfg->half_len);
+    d.ihw = (float)(1.0 / cfg->half_wid);
+    d.c_off = cfg->c_off;
+    d.idxi = (float)(1.0 / cfg->dxi_n);
+    d.ideta = (float)(1.0 / cfg->deta_n);
+    d.idphi = (float)(1.0 / cfg->dphi_n);
+    d.idv = (float)(1.0 / cfg->dv_n);
+    d.w_pos = cfg->w_pos; d.w_phi = cfg->w_phi; d.w_v = cfg->w_v; d.w_effort = cfg->w_effort;
+
+    const size_t NT1 = (size_t)(cfg->max_T + 1) * cfg->max_N;
+    const size_t NT = (size_t)cfg->max_T * cfg->max_N;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](void** p, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(p, bytes > 0 ? bytes : 16); };
+    A((void**)&h->d_key, 64);
+    A((void**)&h->d_traj, NT1 * sizeof(float4));
+    A((void**)&h->d_ctrl, NT * sizeof(float2));
+    A((void**)&h->d_obs, (size_t)cfg->max_M * sizeof(float4));
+    A((void**)&h->d_warm, (size_t)h->n_theta * sizeof(float));
+    A((void**)&h->d_best, sizeof(npp_best));
+    A((void**)&h->d_params, (size_t)h->n_theta * sizeof(float));
+    A((void**)&h->d_controls, (size_t)cfg->max_T * 2 * sizeof(float));
+    A((void**)&h->d_trajectory, (size_t)(cfg->max_T + 1) * 4 * sizeof(float));
+    A((void**)&h->d_costs, (size_t)cfg->max_N * sizeof(float));
+    A((void**)&h->d_fh, (size_t)cfg->max_N * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaEventCreate(&h->ev[i]);
+    if (e != cudaSuccess) {
+        g_err = std::string("workspace allocation failed: ") + cudaGetErrorString(e);
+        npp_destroy(h);
+        return NPP_CUDA_ERROR;
+    }
+    *out = h;
+    return NPP_OK;
+}
+
+npp_status npp_destroy(npp_handle* h)
+{
+    if (!h) return NPP_OK;
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    void* ptrs[] = { h->d_key, h->d_traj, h->d_ctrl, h->d_obs, h->d_warm, h->d_best, h->d_params,
+                     h->d_controls, h->d_trajectory, h->d_costs, h->d_fh };
+    for (void* p : ptrs) if (p) cudaFree(p);
+    if (h->stream) cudaStreamDestroy(h->stream);
+    for (int i = 0; i < 3; ++i) if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+    delete h;
+    return NPP_OK;
+}
+
+npp_status npp_plan_step(npp_handle* h, const npp_state* state, const npp_goal* goal,
+                         const float* obs_dev, int32_t M, int32_t N, int32_t T, uint64_t seed,
+                         uint32_t t_index, const float* warm_dev, const npp_outputs* out,
+                         void* stream)
+{
+    if (!h) return fail(nullptr, NPP_INVALID_ARG, "handle is NULL");
+    npp_status st;
+    if ((st = check_state_goal(h, state, goal)) != NPP_OK) return st;
+    if ((st = check_sizes(h, M, N, T, obs_dev)) != NPP_OK) return st;
+    if (!out || !out->best) return fail(h, NPP_INVALID_ARG, "outputs.best must not be NULL");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    CUDA_TRY(h, cudaSetDevice(h->device));
+
+    RolloutArgs a;
+    fill_rollout_args(h, a, state, goal, obs_dev, M, N, T);
+    a.key = make_key(seed, t_index, 0u);
+    a.warm = warm_dev;
+    a.costs = out->costs;
+    a.first_hit = out->first_hit;
+    a.traj = out->sample_traj ? reinterpret_cast<float4*>(out->sample_traj) : h->d_traj;
+    a.ctrl = out->sample_ctrl ? reinterpret_cast<float2*>(out->sample_ctrl) : h->d_ctrl;
+    a.best_key = h->d_key;
+    if (h->timing) CUDA_TRY(h, cudaEventRecord(h->ev[0], s));
+    CUDA_TRY(h, cudaMemsetAsync(h->d_key, 0xff, sizeof(unsigned long long), s));
+    CUDA_TRY(h, launch_rollout(h, a, s));
+    if (h->timing) CUDA_TRY(h, cudaEventRecord(h->ev[1], s));
+
+    EpilogueArgs e;
+    memset(&e, 0, sizeof e);
+    e.x0 = state->x; e.y0 = state->y; e.phi0 = state->phi;
+    e.N = N; e.T = T; e.n_theta = h->n_theta;
+    e.key = a.key;
+    e.warm = warm_dev;
+    e.traj = a.traj;
+    e.ctrl = a.ctrl;
+    e.best_key = h->d_key;
+    e.best = out->best;
+    e.params = out->params;
+    e.controls = out->controls;
+    e.trajectory = out->trajectory;
+    epilogue_kernel<<<1, 256, 0, s>>>(e);
+    CUDA_TRY(h, cudaGetLastError());
+    if (h->timing) CUDA_TRY(h, cudaEventRecord(h->ev[2], s));
+    return NPP_OK;
+}
+
+npp_status npp_plan_step_host(npp_handle* h, const npp_state* state, const npp_goal* goal,
+                              const float* obs_host, int32_t M, int32_t N, int32_t T,
+                              uint64_t seed, uint32_t t_index, const float* warm_host,
+                              const npp_outputs* out_host)
+{
+    if (!h) return fail(nullptr, NPP_INVALID_ARG, "handle is NULL");
+    if (!out_host || !out_host->best) return fail(h, NPP_INVALID_ARG, "outputs.best must not be NULL");
+    if (out_host->sample_traj || out_host->sample_ctrl)
+        return fail(h, NPP_INVALID_ARG, "per-sample outputs are device-only");
+    npp_status st;
+    if ((st = check_state_goal(h, state, goal)) != NPP_OK) return st;
+    if ((st = check_sizes(h, M, N, T, nullptr)) != NPP_OK) return st;
+    if (M > 0 && !obs_host) return fail(h, NPP_INVALID_ARG, "obstacle pointer is NULL with M=%d", M);
+    CUDA_TRY(h, cudaSetDevice(h->device));
+    cudaStream_t s = h->stream;
+    if (M > 0) CUDA_TRY(h, cudaMemcpyAsync(h->d_obs, obs_host, (size_t)M * 16, cudaMemcpyHostToDevice, s));
+    if (warm_host)
+        CUDA_TRY(h, cudaMemcpyAsync(h->d_warm, warm_host, (size_t)h->n_theta * 4, cudaMemcpyHostToDevice, s));
+    npp_outputs d;
+    memset(&d, 0, sizeof d);
+    d.best = h->d_best;
+    d.params = out_host->params ? h->d_params : nullptr;
+    d.controls = out_host->controls ? h->d_controls : nullptr;
+    d.trajectory = out_host->trajectory ? h->d_trajectory : nullptr;
+    d.costs = out_host->costs ? h->d_costs : nullptr;
+    d.first_hit = out_host->first_hit ? h->d_fh : nullptr;
+    st = npp_plan_step(h, state, goal, reinterpret_cast<const float*>(h->d_obs), M, N, T, seed, t_index,
+                       warm_host ? h->d_warm : nullptr, &d, s);
+    if (st != NPP_OK) return st;
+    CUDA_TRY(h, cudaMemcpyAsync(out_host->best, h->d_best, sizeof(npp_best), cudaMemcpyDeviceToHost, s));
+    if (out_host->params)
+        CUDA_TRY(h, cudaMemcpyAsync(out_host->params, h->d_params, (size_t)h->n_theta * 4, cudaMemcpyDeviceToHost, s));
+    if (out_host->controls)
+        CUDA_TRY(h, cudaMemcpyAsync(out_host->controls, h->d_controls, (size_t)T * 8, cudaMemcpyDeviceToHost, s));
+    if (out_host->trajectory)
+        CUDA_TRY(h, cudaMemcpyAsync(out_host->trajectory, h->d_trajectory, (size_t)(T + 1) * 16, cudaMemcpyDeviceToHost, s));
+    if (out_host->costs)
+        CUDA_TRY(h, cudaMemcpyAsync(out_host->costs, h->d_costs, (size_t)N * 4, cudaMemcpyDeviceToHost, s));
+    if (out_host->first_hit)
+        CUDA_TRY(h, cudaMemcpyAsync(out_host->first_hit, h->d_fh, (size_t)N * 4, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(h, cudaStreamSynchronize(s));
+    return out_host->best->status == NPP_INFEASIBLE ? NPP_INFEASIBLE : NPP_OK;
+}
+
+npp_status npp_rollout_params(npp_handle* h, const npp_state* state, const npp_goal* goal,
+                              const float* obs_dev, int32_t M, const float* theta_dev, int32_t K,
+                              int32_t T, float* costs_dev, int32_t* first_hit_dev,
+                              float* sample_traj_dev, float* sample_ctrl_dev, void* stream)
+{
+    if (!h) return fail(nullptr, NPP_INVALID_ARG, "handle is NULL");
+    npp_status st;
+    if ((st = check_state_goal(h, state, goal)) != NPP_OK) return st;
+    if ((st = check_sizes(h, M, K, T, obs_dev)) != NPP_OK) return st;
+    if (!theta_dev) return fail(h, NPP_INVALID_ARG, "theta must not be NULL");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    CUDA_TRY(h, cudaSetDevice(h->device));
+    RolloutArgs a;
+    fill_rollout_args(h, a, state, goal, obs_dev, M, K, T);
+    a.theta = theta_dev;
+    a.costs = costs_dev;
+    a.first_hit = first_hit_dev;
+    a.traj = sample_traj_dev ? reinterpret_cast<float4*>(sample_traj_dev) : h->d_traj;
+    a.ctrl = sample_ctrl_dev ? reinterpret_cast<float2*>(sample_ctrl_dev) : h->d_ctrl;
+    a.best_key = nullptr;
+    if (h->timing) CUDA_TRY(h, cudaEventRecord(h->ev[0], s));
+    CUDA_TRY(h, launch_rollout(h, a, s));
+    if (h->timing) {
+        CUDA_TRY(h, cudaEventRecord(h->ev[1], s));
+        CUDA_TRY(h, cudaEventRecord(h->ev[2], s));
+    }
+    return NPP_OK;
+}
+
+npp_status npp_set_timing(npp_handle* h, int32_t enable)
+{
+    if (!h) return fail(nullptr, NPP_INVALID_ARG, "handle is NULL");
+    h->timing = enable != 0;
+    return NPP_OK;
+}
+
+npp_status npp_last_timing(npp_handle* h, float* rollout_ms, float* step_ms)
+{
+    if (!h) return fail(nullptr, NPP_INVALID_ARG, "handle is NULL");
+    if (!h->timing) return fail(h, NPP_INVALID_ARG, "timing is not enabled on this handle");
+    CUDA_TRY(h, cudaSetDevice(h->device));
+    CUDA_TRY(h, cudaEventSynchronize(h->ev[2]));
+    float a = 0.f, b = 0.f;
+    CUDA_TRY(h, cudaEventElapsedTime(&a, h->ev[0], h->ev[1]));
+    CUDA_TRY(h, cudaEventElapsedTime(&b, h->ev[0], h->ev[2]));
+    if (rollout_ms) *rollout_ms = a;
+    if (step_ms) *step_ms = b;
+    return NPP_OK;
+}
+
+npp_status npp_sample_params(uint64_t seed, uint32_t t_index, uint32_t stream_id, int32_t n0,
+                             int32_t K, int32_t n_theta, float* out_dev, void* stream)
+{
+    if (n0 < 0 || K < 1 || n_theta < 1 || !out_dev)
+        return fail(nullptr, NPP_INVALID_ARG, "npp_sample_params: bad arguments");
+    const long long quads = (long long)K * ((n_theta + 3) / 4);
+    const int grid = (int)std::min<long long>((quads + 255) / 256, 65536);
+    sample_params_kernel<<<grid, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+        make_key(seed, t_index, stream_id), n0, K, n_theta, out_dev);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(nullptr, NPP_CUDA_ERROR, "sampler launch: %s", cudaGetErrorString(e));
+    return NPP_OK;
+}
+
+}  // extern "C"

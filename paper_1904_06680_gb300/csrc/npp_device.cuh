@@ -1,0 +1,161 @@
+// npp_device.cuh -- device-side building blocks of the planner library:
+// the counter-based parameter sampler, the per-handle constants and the
+// kernel argument blocks shared by the kernels and their launchers.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace npp {
+
+constexpr int NIN = 8;               // network inputs (features)
+constexpr uint32_t FULL = 0xffffffffu;
+
+// Constants derived once per handle from npp_config (FP32, device side).
+struct DevCfg {
+    float delta_max, r_rate;         // steering limit, rate limit per step (normalised)
+    float lrL, iL;                   // l_r / (l_f + l_r), 1 / (l_f + l_r)
+    float umid, uhalf;               // u = umid + uhalf a1
+    float Ts;
+    float ihl, ihw, c_off;           // 1/half_len, 1/half_wid, centre offset
+    float idxi, ideta, idphi, idv;   // 1 / feature normalisation constants
+    float w_pos, w_phi, w_v, w_effort;
+};
+
+// ------------------------------------------------------------------ sampler
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw: "Parallel random numbers: as
+// easy as 1, 2, 3", SC'11): ten rounds of two 32x32->64 multiplies with the
+// published multipliers, key bumped by the published Weyl constants.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+// Natural log of u in (0,1) (the FP32 sampler specification): u = 2^e f with
+// f in [sqrt(1/2), sqrt(2)), ln f = 2 atanh(s), s = (f-1)/(f+1), odd Taylor
+// terms up to s^11, Cody-Waite split of ln 2.  Every operation is a single
+// IEEE round-to-nearest step so that the value is reproducible bit for bit.
+__device__ __forceinline__ float spec_ln(float u)
+{
+    uint32_t b = __float_as_uint(u);
+    int e = (int)(b >> 23) - 127;
+    const uint32_t m = b & 0x7FFFFFu;
+    float f;
+    if (m > 0x3504F3u) { f = __uint_as_float(m | 0x3F000000u); e += 1; }
+    else               { f = __uint_as_float(m | 0x3F800000u); }
+    const float num = __fsub_rn(f, 1.0f);
+    const float den = __fadd_rn(f, 1.0f);
+    const float s = __fdiv_rn(num, den);
+    const float z = __fmul_rn(s, s);
+    float p = __fmaf_rn(z, 0x1.745d18p-3f, 0x1.c71c72p-3f);   // 2/11, 2/9
+    p = __fmaf_rn(z, p, 0x1.24924ap-2f);                        // 2/7
+    p = __fmaf_rn(z, p, 0x1.99999ap-2f);                        // 2/5
+    p = __fmaf_rn(z, p, 0x1.555556p-1f);                        // 2/3
+    const float t = __fmul_rn(s, z);
+    const float lnf = __fmaf_rn(t, p, __fmul_rn(2.0f, s));
+    const float ef = __int2float_rn(e);
+    return __fmaf_rn(ef, 0x1.62e400p-1f, __fmaf_rn(ef, 0x1.7f7d1cp-20f, lnf));
+}
+
+// sin and cos of 2 pi K 2^-24 for odd K in [1, 2^24): quarter-turn reduction
+// in integers (exact), Taylor polynomials of degree 9 / 10 on |x| <= pi/4.
+__device__ __forceinline__ void spec_sincos2pi(uint32_t K, float& s_out, float& c_out)
+{
+    const int q = (int)((K + (1u << 21)) >> 22);
+    const int k = (int)K - q * (1 << 22);
+    const float x = __fmul_rn(__int2float_rn(k), 0x1.921fb6p-22f);
+    const float z = __fmul_rn(x, x);
+    float ps = __fmaf_rn(z, 0x1.71de3ap-19f, -0x1.a01a02p-13f);
+    ps = __fmaf_rn(z, ps, 0x1.111112p-7f);
+    ps = __fmaf_rn(z, ps, -0x1.555556p-3f);
+    const float sx = __fmaf_rn(__fmul_rn(x, z), ps, x);
+    float pc = __fmaf_rn(z, -0x1.27e4fcp-22f, 0x1.a01a02p-16f);
+    pc = __fmaf_rn(z, pc, -0x1.6c16c2p-10f);
+    pc = __fmaf_rn(z, pc, 0x1.555556p-5f);
+    pc = __fmaf_rn(z, pc, -0.5f);
+    const float cx = __fmaf_rn(z, pc, 1.0f);
+    switch (q & 3) {
+    case 0: s_out = sx;  c_out = cx;  break;
+    case 1: s_out = cx;  c_out = -sx; break;
+    case 2: s_out = -sx; c_out = -cx; break;
+    default: s_out = -cx; c_out = sx; break;
+    }
+}
+
+// Box-Muller pair from two Philox words: radius from `a`, angle from `b`.
+__device__ __forceinline__ float2 spec_normal_pair(uint32_t a, uint32_t b)
+{
+    const float u1 = __fmul_rn(__uint2float_rn(((a >> 9) << 1) | 1u), 0x1p-24f);
+    const float r = __fsqrt_rn(__fmul_rn(-2.0f, spec_ln(u1)));
+    float s, c;
+    spec_sincos2pi(((b >> 9) << 1) | 1u, s, c);
+    return make_float2(__fmul_rn(r, c), __fmul_rn(r, s));
+}
+
+struct SamplerKey {
+    uint32_t k0, k1, t_index, stream_id;
+};
+
+// theta_n[4q .. 4q+3]
+__device__ __forceinline__ float4 sample_quad(const SamplerKey& key, uint32_t q, uint32_t n)
+{
+    const uint4 w = philox4x32_10(make_uint4(q, n, key.t_index, key.stream_id), key.k0, key.k1);
+    const float2 a = spec_normal_pair(w.x, w.y);
+    const float2 b = spec_normal_pair(w.z, w.w);
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+
+// theta_n[i], theta_n[i+1] for even i (one Box-Muller pair)
+__device__ __forceinline__ float2 sample_pair(const SamplerKey& key, uint32_t i, uint32_t n)
+{
+    const uint4 w = philox4x32_10(make_uint4(i >> 2, n, key.t_index, key.stream_id), key.k0, key.k1);
+    return (i & 2u) ? spec_normal_pair(w.z, w.w) : spec_normal_pair(w.x, w.y);
+}
+
+// ------------------------------------------------------------------ kernels
+struct RolloutArgs {
+    DevCfg c;
+    float x0, y0, phi0, v0, ap0, ap1;  // world-frame state and last controls
+    float gx, gy, gphi, gv;            // world-frame goal
+    const float4* obs;                 // [M] world frame (x, y, vx, vy)
+    int M, N, T;
+    SamplerKey key;
+    const float* theta;                // explicit parameters [N][n_theta] or null
+    const float* warm;                 // replaces sample 0 when non-null
+    float* costs;                      // [N] or null
+    int* first_hit;                    // [N] or null
+    float4* traj;                      // [T+1][N] EV frame (always written)
+    float2* ctrl;                      // [T][N]
+    unsigned long long* best_key;      // packed (class, cost, index) minimum
+};
+
+struct EpilogueArgs {
+    float x0, y0, phi0;
+    int N, T, n_theta;
+    SamplerKey key;
+    const float* warm;
+    const float4* traj;
+    const float2* ctrl;
+    const unsigned long long* best_key;
+    void* best;                        // npp_best*
+    float* params;
+    float* controls;
+    float* trajectory;
+};
+
+// launchers (one translation unit per network width)
+cudaError_t launch_rollout_w16(const RolloutArgs& a, cudaStream_t s, int* smem_needed);
+cudaError_t launch_rollout_w32(const RolloutArgs& a, cudaStream_t s, int* smem_needed);
+cudaError_t launch_rollout_w64(const RolloutArgs& a, cudaStream_t s, int* smem_needed);
+int rollout_max_points_w16(int smem_limit);
+int rollout_max_points_w32(int smem_limit);
+int rollout_max_points_w64(int smem_limit);
+
+}  // namespace npp

@@ -1,0 +1,248 @@
+"""Thin ctypes binding of libnpp.so (the C ABI in include/npp.h).
+
+The functions keep the C names and only marshal arguments: torch tensors
+provide device memory and streams, every step of the planner runs in the
+library's CUDA kernels.  Importing this module raises if the library has not
+been built (there is no CPU fallback).
+"""
+import ctypes as C
+import os
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libnpp.so")
+
+NPP_OK, NPP_INVALID_ARG, NPP_INFEASIBLE, NPP_CUDA_ERROR, NPP_DEVICE_TIMEOUT, NPP_UNSUPPORTED = range(6)
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "INFEASIBLE", 3: "CUDA_ERROR", 4: "DEVICE_TIMEOUT",
+                5: "UNSUPPORTED"}
+
+
+class NppError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("npp status %s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class npp_config(C.Structure):
+    _fields_ = [(n, C.c_float) for n in (
+        "lf", "lr", "delta_max", "delta_rate_max", "u_min", "u_max", "Ts",
+        "half_len", "half_wid", "c_off", "dxi_n", "deta_n", "dphi_n", "dv_n",
+        "w_pos", "w_phi", "w_v", "w_effort")] + [
+        ("n_in", C.c_int32), ("width", C.c_int32), ("max_N", C.c_int32),
+        ("max_T", C.c_int32), ("max_M", C.c_int32)]
+
+
+class npp_state(C.Structure):
+    _fields_ = [(n, C.c_float) for n in ("x", "y", "phi", "v", "a_prev0", "a_prev1")]
+
+
+class npp_goal(C.Structure):
+    _fields_ = [(n, C.c_float) for n in ("x", "y", "phi", "v")]
+
+
+class npp_best(C.Structure):
+    _fields_ = [("best_idx", C.c_int32), ("status", C.c_int32), ("best_cost", C.c_float),
+                ("first_hit", C.c_int32), ("reserved", C.c_int32 * 4)]
+
+
+class npp_outputs(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("best", "params", "controls", "trajectory", "costs",
+                                          "first_hit", "sample_traj", "sample_ctrl")]
+
+
+EXPORTS = ("npp_create", "npp_destroy", "npp_last_error", "npp_n_theta", "npp_plan_step",
+           "npp_plan_step_host", "npp_rollout_params", "npp_sample_params", "npp_set_timing",
+           "npp_last_timing")
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libnpp.so is not built: run __graft_entry__.build() "
+                               "(there is no CPU fallback)")
+        L = C.CDLL(LIB_PATH)
+        P, I32, U32, U64 = C.c_void_p, C.c_int32, C.c_uint32, C.c_uint64
+        L.npp_create.argtypes = [C.POINTER(P), C.POINTER(npp_config), I32]
+        L.npp_destroy.argtypes = [P]
+        L.npp_last_error.argtypes = [P]
+        L.npp_last_error.restype = C.c_char_p
+        L.npp_n_theta.argtypes = [C.POINTER(npp_config)]
+        L.npp_n_theta.restype = I32
+        L.npp_plan_step.argtypes = [P, C.POINTER(npp_state), C.POINTER(npp_goal), P, I32, I32, I32,
+                                    U64, U32, P, C.POINTER(npp_outputs), P]
+        L.npp_plan_step_host.argtypes = [P, C.POINTER(npp_state), C.POINTER(npp_goal), P, I32, I32,
+                                         I32, U64, U32, P, C.POINTER(npp_outputs)]
+        L.npp_rollout_params.argtypes = [P, C.POINTER(npp_state), C.POINTER(npp_goal), P, I32, P, I32,
+                                         I32, P, P, P, P, P]
+        L.npp_sample_params.argtypes = [U64, U32, U32, I32, I32, I32, P, P]
+        L.npp_set_timing.argtypes = [P, I32]
+        L.npp_last_timing.argtypes = [P, C.POINTER(C.c_float), C.POINTER(C.c_float)]
+        for name in EXPORTS:
+            if name not in ("npp_last_error", "npp_n_theta"):
+                getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+# ------------------------------------------------------------------ helpers
+def make_config(p: dict, max_N: int, max_T: int, max_M: int) -> npp_config:
+    c = npp_config()
+    for name, _ in npp_config._fields_[:18]:
+        setattr(c, name, float(p[name]))
+    widths = tuple(p["widths"])
+    c.n_in = widths[0]
+    c.width = widths[1]
+    c.max_N, c.max_T, c.max_M = int(max_N), int(max_T), int(max_M)
+    return c
+
+
+def make_state(s) -> npp_state:
+    return npp_state(*[float(v) for v in s])
+
+
+def make_goal(g) -> npp_goal:
+    return npp_goal(*[float(v) for v in g])
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _check(status, handle=None):
+    if status not in (NPP_OK, NPP_INFEASIBLE):
+        raise NppError(status, npp_last_error(handle))
+    return status
+
+
+# ------------------------------------------------------------------ C names
+def npp_create(cfg: npp_config, device: int = 0):
+    h = C.c_void_p()
+    _check(lib().npp_create(C.byref(h), C.byref(cfg), int(device)))
+    return h
+
+
+def npp_destroy(h):
+    return lib().npp_destroy(h)
+
+
+def npp_last_error(h=None) -> str:
+    r = lib().npp_last_error(h)
+    return r.decode() if r else ""
+
+
+def npp_n_theta(cfg: npp_config) -> int:
+    return lib().npp_n_theta(C.byref(cfg))
+
+
+def npp_plan_step(h, state, goal, obs, M, N, T, seed, t_index, warm, out: npp_outputs, stream=None):
+    """obs / warm: CUDA tensors (or None); out: npp_outputs of device pointers."""
+    return _check(lib().npp_plan_step(h, C.byref(make_state(state)), C.byref(make_goal(goal)),
+                                      _ptr(obs), int(M), int(N), int(T), int(seed), int(t_index),
+                                      _ptr(warm), C.byref(out), _stream(stream)), h)
+
+
+def npp_plan_step_host(h, state, goal, obs, M, N, T, seed, t_index, warm, out: npp_outputs):
+    """obs / warm: host (CPU) tensors; out: npp_outputs of host pointers."""
+    return _check(lib().npp_plan_step_host(h, C.byref(make_state(state)), C.byref(make_goal(goal)),
+                                           _ptr(obs), int(M), int(N), int(T), int(seed),
+                                           int(t_index), _ptr(warm), C.byref(out)), h)
+
+
+def npp_rollout_params(h, state, goal, obs, M, theta, K, T, costs, first_hit, sample_traj=None,
+                       sample_ctrl=None, stream=None):
+    return _check(lib().npp_rollout_params(h, C.byref(make_state(state)), C.byref(make_goal(goal)),
+                                           _ptr(obs), int(M), _ptr(theta), int(K), int(T),
+                                           _ptr(costs), _ptr(first_hit), _ptr(sample_traj),
+                                           _ptr(sample_ctrl), _stream(stream)), h)
+
+
+def npp_sample_params(seed, t_index, stream_id, n0, K, n_theta, out, stream=None):
+    return _check(lib().npp_sample_params(int(seed), int(t_index), int(stream_id), int(n0), int(K),
+                                          int(n_theta), _ptr(out), _stream(stream)))
+
+
+def npp_set_timing(h, enable: bool):
+    return _check(lib().npp_set_timing(h, 1 if enable else 0), h)
+
+
+def npp_last_timing(h):
+    """(rollout kernel ms, whole plan step ms) of the last timed call."""
+    a, b = C.c_float(), C.c_float()
+    _check(lib().npp_last_timing(h, C.byref(a), C.byref(b)), h)
+    return a.value, b.value
+
+
+# ------------------------------------------------------------------ convenience
+class Planner:
+    """Owns a handle and the output tensors of one plan step on one device."""
+
+    def __init__(self, preset: dict, max_N: int, max_T: int, max_M: int, device: int = 0,
+                 record_samples: bool = False):
+        self.cfg = make_config(preset, max_N, max_T, max_M)
+        self.device = torch.device("cuda", device)
+        self.h = npp_create(self.cfg, device)
+        self.n_theta = npp_n_theta(self.cfg)
+        d = self.device
+        self.best = torch.zeros(8, dtype=torch.int32, device=d)
+        self.params = torch.zeros(self.n_theta, dtype=torch.float32, device=d)
+        self.controls = torch.zeros(max_T, 2, dtype=torch.float32, device=d)
+        self.trajectory = torch.zeros(max_T + 1, 4, dtype=torch.float32, device=d)
+        self.costs = torch.zeros(max_N, dtype=torch.float32, device=d)
+        self.first_hit = torch.zeros(max_N, dtype=torch.int32, device=d)
+        self.record_samples = record_samples
+        self.max_N, self.max_T = max_N, max_T
+        if record_samples:
+            self.sample_traj = torch.zeros((max_T + 1) * max_N * 4, dtype=torch.float32, device=d)
+            self.sample_ctrl = torch.zeros(max_T * max_N * 2, dtype=torch.float32, device=d)
+
+    def outputs(self) -> npp_outputs:
+        o = npp_outputs()
+        o.best = self.best.data_ptr()
+        o.params = self.params.data_ptr()
+        o.controls = self.controls.data_ptr()
+        o.trajectory = self.trajectory.data_ptr()
+        o.costs = self.costs.data_ptr()
+        o.first_hit = self.first_hit.data_ptr()
+        if self.record_samples:
+            o.sample_traj = self.sample_traj.data_ptr()
+            o.sample_ctrl = self.sample_ctrl.data_ptr()
+        return o
+
+    def plan(self, state, goal, obs, N, T, seed, t_index=0, warm=None, stream=None):
+        """Queue one plan step; obs is a CUDA float32 tensor [M, 4]."""
+        M = 0 if obs is None else obs.shape[0]
+        npp_plan_step(self.h, state, goal, obs, M, N, T, seed, t_index, warm, self.outputs(), stream)
+
+    def result(self, N, T):
+        """Host copies of the last plan step's outputs (synchronises)."""
+        b = self.best.cpu()
+        best_cost = b[2:3].view(torch.float32).item()
+        r = dict(best_idx=int(b[0]), status=int(b[1]), best_cost=best_cost, first_hit_best=int(b[3]),
+                 params=self.params.cpu().numpy(), controls=self.controls[:T].cpu().numpy(),
+                 trajectory=self.trajectory[:T + 1].cpu().numpy(), costs=self.costs[:N].cpu().numpy(),
+                 first_hit=self.first_hit[:N].cpu().numpy())
+        if self.record_samples:
+            r["sample_traj"] = self.sample_traj[:(T + 1) * N * 4].view(T + 1, N, 4).cpu().numpy()
+            r["sample_ctrl"] = self.sample_ctrl[:T * N * 2].view(T, N, 2).cpu().numpy()
+        return r
+
+    def close(self):
+        if self.h is not None:
+            npp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,37 @@
+"""The C-ABI library loads and exports every function include/npp.h
+declares (no device work: runs without a GPU)."""
+import ctypes
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "npp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(npp_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_library_exports_all_declared_symbols():
+    from paper_1904_06680_gb300 import build
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    names = _declared()
+    assert len(names) >= 10, names
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_the_abi():
+    from paper_1904_06680_gb300 import npp
+    assert sorted(npp.EXPORTS) == _declared()
+    npp.lib()
+
+
+def test_n_theta_and_config_validation_without_device():
+    from paper_1904_06680_gb300 import inputs, npp
+    for w, n in [(16, 450), (32, 1410), (64, 4866)]:
+        assert npp.npp_n_theta(npp.make_config(inputs.planner(w), 1, 1, 1)) == n
+    assert npp.npp_n_theta(npp.make_config(dict(inputs.planner(16), widths=(8, 24, 24, 2)), 1, 1, 1)) == -1
+    assert npp.npp_n_theta(npp.make_config(inputs.PAPER, 1, 1, 1)) == -1

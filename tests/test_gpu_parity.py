@@ -1,0 +1,206 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Small instances are compared on every sample (several blocks and a ragged
+tail); the full-size workloads on every sample too where the oracle is fast
+enough, otherwise on sampled indices.  Tolerances are documented in
+tests/parity.py.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1904_06680_gb300 import inputs
+
+from . import parity as P
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1904_06680_gb300 import npp
+    npp.lib()
+
+
+# ------------------------------------------------------------------ sampler
+@pytest.mark.parametrize("nt", [450, 1410, 4866, 7])
+def test_sampled_parameters_bit_exact(orc, nt):
+    import torch
+    from paper_1904_06680_gb300 import npp
+    rng = np.random.default_rng(nt)
+    for _ in range(3):
+        seed = int(rng.integers(0, 2 ** 63))
+        t = int(rng.integers(0, 2 ** 32))
+        stream = int(rng.integers(0, 4))
+        n0 = int(rng.integers(0, 2 ** 31 - 100))
+        K = 37
+        out = torch.empty(K * nt, dtype=torch.float32, device="cuda")
+        npp.npp_sample_params(seed, t, stream, n0, K, nt, out)
+        g = out.view(K, nt).cpu().numpy()
+        for k in range(K):
+            ref = orc.theta(seed, t, n0 + k, nt, stream=stream)
+            assert np.array_equal(g[k].view(np.uint32), ref.view(np.uint32)), (seed, t, n0 + k)
+
+
+def test_sampled_parameters_bulk(orc):
+    """65536 x 450 draws: bit-exact on a strided subset, moments on all."""
+    import torch
+    from paper_1904_06680_gb300 import npp
+    K, nt = 65536, 450
+    out = torch.empty(K * nt, dtype=torch.float32, device="cuda")
+    npp.npp_sample_params(0x5EED0000, 3, 0, 0, K, nt, out)
+    g = out.view(K, nt)
+    for k in range(0, K, 4099):
+        assert np.array_equal(g[k].cpu().numpy(), orc.theta(0x5EED0000, 3, k, nt))
+    x = g.double()
+    assert abs(x.mean().item()) < 5 / math.sqrt(K * nt)
+    assert abs(x.var().item() - 1) < 5 * math.sqrt(2 / (K * nt))
+
+
+# ------------------------------------------------------------------ small plans
+SMALL = [(16, 300, 20, 40, 11), (32, 150, 24, 60, 12), (64, 70, 18, 33, 13), (16, 1, 5, 7, 14),
+         (32, 33, 1, 0, 15)]
+
+
+@pytest.mark.parametrize("width,N,T,M,seed", SMALL)
+def test_plan_parity_small(orc, width, N, T, M, seed):
+    sc = inputs.tiny_scene(seed, N=N, T=T, M=M, width=width)
+    g = P.gpu_plan(sc)
+    idx = np.arange(N)
+    o = P.oracle_samples(sc, idx)
+    # winner parameters and summary record
+    nt = orc.n_theta(sc["preset"])
+    assert np.array_equal(g["params"], orc.theta(sc["seed"], sc["t_index"], g["best_idx"], nt))
+    assert g["costs"][g["best_idx"]] == np.min(g["costs"]) or g["status"] == 2
+    # per-step replay of every step of every sample
+    rs = P.replay_stats(sc, g, idx)
+    assert not rs["bad"], rs["bad"][:5]
+    # collision decisions at the GPU's states
+    fs = P.flag_stats(sc, g, idx)
+    assert not fs["bad"], fs["bad"][:5]
+    # free-running trajectories
+    ok = P.traj_stats(sc, g, o, idx)
+    assert ok.mean() >= 0.97, ok.mean()
+    # chosen sample
+    wc = P.winner_check(g, o["cost"], o["first_hit"])
+    if not wc.get("infeasible"):
+        assert wc["gpu_pick_oracle_cost"] <= wc["best_unambiguous"] * (1 + P.COST_RTOL) + P.COST_RTOL, wc
+    # winner trajectory and controls in the world frame
+    b = g["best_idx"]
+    fh = int(g["first_hit"][b])
+    last = T if fh < 0 else fh
+    c, s = math.cos(np.float32(sc["state"][2])), math.sin(np.float32(sc["state"][2]))
+    ev = g["sample_traj"][:, b].astype(np.float64)
+    x0, y0 = np.float32(sc["state"][0]), np.float32(sc["state"][1])
+    for h in range(T + 1):
+        z = ev[min(h, last)]
+        w = [x0 + c * z[0] - s * z[1], y0 + s * z[0] + c * z[1]]
+        assert np.allclose(g["trajectory"][h, :2], w, rtol=1e-6, atol=1e-4)
+    assert np.array_equal(g["controls"][:last], g["sample_ctrl"][:last, b])
+    assert np.all(g["controls"][last:] == 0)
+
+
+def test_plan_warm_start(orc):
+    sc = inputs.tiny_scene(21, N=100, T=15, M=30, width=32)
+    nt = orc.n_theta(sc["preset"])
+    warm = np.zeros(nt, np.float32)
+    warm[-2:] = [0.0, math.atanh(0.2)]
+    g = P.gpu_plan(sc, warm=warm)
+    o = P.oracle_samples(sc, [0], warm=warm)
+    assert int(g["first_hit"][0]) == int(o["first_hit"][0])
+    if o["first_hit"][0] < 0:
+        assert abs(g["costs"][0] - o["cost"][0]) <= 1e-4 * max(1, abs(o["cost"][0]))
+    if g["best_idx"] == 0:
+        assert np.array_equal(g["params"], warm)
+
+
+def test_plan_infeasible(orc):
+    """Every sample collides: INFEASIBLE and the longest survivor."""
+    sc = inputs.tiny_scene(22, N=96, T=30, M=0, width=16)
+    rng = np.random.default_rng(22)
+    ang = rng.uniform(-math.pi, math.pi, 3000)
+    rad = rng.uniform(3.5, 6.0, 3000)
+    st = sc["state"]
+    obs = np.zeros((3000, 4))
+    obs[:, 0] = st[0] + rad * np.cos(ang)
+    obs[:, 1] = st[1] + rad * np.sin(ang)
+    obs[:, 2] = -2.0 * np.cos(ang)
+    obs[:, 3] = -2.0 * np.sin(ang)
+    sc["obs"] = obs
+    g = P.gpu_plan(sc)
+    o = P.oracle_samples(sc, np.arange(96))
+    assert np.all(g["first_hit"] >= 0) and g["status"] == 2
+    assert g["best_idx"] == int(np.argmax(g["first_hit"]))
+    assert np.isinf(g["best_cost"])
+    assert np.mean(g["first_hit"] == o["first_hit"]) > 0.9
+    fh = int(g["first_hit"][g["best_idx"]])
+    assert np.all(g["controls"][fh:] == 0)
+    # a point inside the car at h = 0
+    sc["obs"] = np.array([[st[0], st[1], 0.0, 0.0]])
+    g2 = P.gpu_plan(sc)
+    assert g2["status"] == 2 and np.all(g2["first_hit"] == 0) and g2["best_idx"] == 0
+
+
+def test_invalid_arguments():
+    import torch
+    from paper_1904_06680_gb300 import inputs as I, npp
+    p = I.planner(16)
+    with pytest.raises(npp.NppError):
+        npp.Planner(dict(p, widths=(8, 24, 24, 2)), 10, 10, 10)
+    pl = npp.Planner(p, max_N=64, max_T=10, max_M=8)
+    obs = torch.zeros(8, 4, device="cuda")
+    for bad in [dict(N=0), dict(N=65), dict(T=0), dict(T=11)]:
+        kw = dict(N=10, T=5)
+        kw.update(bad)
+        with pytest.raises(npp.NppError) as ei:
+            pl.plan([0, 0, 0, 0, 0, 0], [5, 0, 0, 0], obs, kw["N"], kw["T"], 1)
+        assert ei.value.status == npp.NPP_INVALID_ARG
+    with pytest.raises(npp.NppError):
+        pl.plan([0, 0, float("nan"), 0, 0, 0], [5, 0, 0, 0], obs, 10, 5, 1)
+    with pytest.raises(npp.NppError):
+        pl.plan([0, 0, 0, 0, 2.0, 0], [5, 0, 0, 0], obs, 10, 5, 1)
+    pl.close()
+
+
+# ------------------------------------------------------------------ full sizes
+def test_single_scene_full(orc):
+    """The 1-scene workload (N=256, T=20, 8-16-16-2, M=200): every sample."""
+    sc = inputs.scene_single(0)
+    g = P.gpu_plan(sc)
+    idx = np.arange(sc["N"])
+    o = P.oracle_samples(sc, idx)
+    rs = P.replay_stats(sc, g, idx)
+    assert not rs["bad"], rs["bad"][:5]
+    fs = P.flag_stats(sc, g, idx)
+    assert not fs["bad"], fs["bad"][:5]
+    ok = P.traj_stats(sc, g, o, idx)
+    assert ok.mean() >= 0.97
+    wc = P.winner_check(g, o["cost"], o["first_hit"])
+    assert wc["gpu_pick_oracle_cost"] <= wc["best_unambiguous"] * (1 + P.COST_RTOL) + P.COST_RTOL, wc
+
+
+def test_course_full_size(orc):
+    """The closed-loop course workload at full size (N=16384, T=40,
+    8-32-32-2, M=2000), as the benchmark launches it: collision status and
+    cost of every sample from the oracle, replay and flags on a sample of
+    1024 indices, the winner against the oracle's best."""
+    sc = inputs.scene_course(0)
+    g = P.gpu_plan(sc)
+    N = sc["N"]
+    o = P.oracle_samples(sc, np.arange(N), record=False)
+    wc = P.winner_check(g, o["cost"], o["first_hit"])
+    assert wc["agree_frac"] >= 0.99, wc
+    assert wc["gpu_pick_oracle_cost"] <= wc["best_unambiguous"] * (1 + P.COST_RTOL) + P.COST_RTOL, wc
+    idx = np.random.default_rng(0).choice(N, 1024, replace=False)
+    idx = np.union1d(idx, [g["best_idx"]])
+    rs = P.replay_stats(sc, g, idx)
+    assert not rs["bad"], rs["bad"][:5]
+    fs = P.flag_stats(sc, g, idx)
+    assert not fs["bad"], fs["bad"][:5]
+    o2 = P.oracle_samples(sc, idx)
+    ok = P.traj_stats(sc, g, o2, idx)
+    assert ok.mean() >= 0.97, ok.mean()

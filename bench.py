@@ -129,12 +129,14 @@ def course_setup(seed):
 
 
 def algorithmic_instr(first_hit, T, M, W):
-    """FP32 instructions the rollout needs: 6 per point-check of a live
-    sample (4 FMA + 2 min/max), W^2 + 10 W + 30 per live control step."""
+    """FP32 instructions the rollout needs, split by kernel: the collision
+    check costs 6 per point-check of a live sample (4 FMA + 2 min/max); the
+    control step W^2 + 10 W + 30 per live step (MLP multiply-adds plus
+    features, controls and the Euler update)."""
     fh = np.asarray(first_hit)
     checks = np.where(fh < 0, T + 1, fh + 1).sum()
     ctrl = np.where(fh < 0, T, fh).sum()
-    return float(checks) * 6.0 * M + float(ctrl) * (W * W + 10 * W + 30)
+    return float(checks) * 6.0 * M, float(ctrl) * (W * W + 10 * W + 30)
 
 
 def cpu_baseline(sc, state, goal, obs, T, target_cpu_s=15.0):
@@ -189,7 +191,8 @@ def run_npp(args):
         mission = closed_loop.Mission(sc["waypoints"], inputs.EPS)
         warm_dev = None
         warm_host = None
-        out = dict(step_ms=[], rollout_ms=[], wall_ms=[], instr=0.0, free=[], best_cost=[])
+        out = dict(step_ms=[], collide_ms=[], traj_ms=[], wall_ms=[], instr_c=0.0, instr_t=0.0,
+                   free=[], best_cost=[])
         if host_api:
             obs_pin = torch.empty(M, 4, dtype=torch.float32).pin_memory()
             hb = npp.npp_best()
@@ -223,7 +226,7 @@ def run_npp(args):
                 flush.zero_()
                 torch.cuda.synchronize()
                 pl.plan(state, goal, obs_dev, N, T, sc["seed"], t, warm=warm_dev)
-                r_ms, s_ms = npp.npp_last_timing(pl.h)
+                tm = npp.npp_last_timing(pl.h)
                 fh = pl.first_hit[:N].cpu().numpy()
                 a = pl.controls[0].cpu().numpy().astype(np.float64)
                 b = pl.best.cpu()
@@ -231,9 +234,12 @@ def run_npp(args):
                     warm_dev = torch.empty_like(pl.params)
                 warm_dev.copy_(pl.params)
                 if record:
-                    out["step_ms"].append(s_ms)
-                    out["rollout_ms"].append(r_ms)
-                    out["instr"] += algorithmic_instr(fh, T, M, W)
+                    out["step_ms"].append(tm["total"])
+                    out["collide_ms"].append(tm["collide"])
+                    out["traj_ms"].append(tm["traj"])
+                    ic, it = algorithmic_instr(fh, T, M, W)
+                    out["instr_c"] += ic
+                    out["instr_t"] += it
                     out["free"].append(float(np.mean(fh < 0)))
                     out["best_cost"].append(float(b[2:3].view(torch.float32).item()))
             state = closed_loop.plant_step(p, state, a)
@@ -257,7 +263,8 @@ def run_npp(args):
         import torch.distributed as dist
         dist.barrier()
     total_ms = float(np.sum(res["step_ms"]))
-    rollout_ms = float(np.sum(res["rollout_ms"]))
+    collide_ms = float(np.sum(res["collide_ms"]))
+    traj_ms = float(np.sum(res["traj_ms"]))
     e2e = None
     if not args.no_e2e:
         closed_loop_pass(True, min(Wu, 3), record=False)
@@ -269,20 +276,24 @@ def run_npp(args):
     if world > 1:
         import torch
         import torch.distributed as dist
-        tt = torch.tensor([total_ms, rollout_ms], dtype=torch.float64, device=dev)
+        tt = torch.tensor([total_ms, collide_ms, traj_ms], dtype=torch.float64, device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms, rollout_ms = float(tt[0]), float(tt[1])
+        total_ms, collide_ms, traj_ms = float(tt[0]), float(tt[1]), float(tt[2])
         if e2e:
             ev = torch.tensor([N * T * K / e2e["value"]], dtype=torch.float64, device=dev)
             dist.all_reduce(ev, op=dist.ReduceOp.MAX)
             e2e["value"] = world * N * T * K / float(ev[0])
     value = world * N * T * K / (total_ms / 1e3)
-    instr_per_s = res["instr"] / (rollout_ms / 1e3)
     peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6
-    roofline = {"bound": "alu", "kernel": "rollout_kernel<32,8,8>",
-                "achieved": instr_per_s / 1e12, "peak": peak / 1e12,
-                "unit": "T FP32-instr/s", "frac": instr_per_s / peak, "traffic": None,
-                "peak_basis": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz"}
+    ips_c = res["instr_c"] / (collide_ms / 1e3)
+    ips_t = res["instr_t"] / (traj_ms / 1e3)
+    roofline = {"bound": "alu", "kernel": "collide_kernel<8,64,8>",
+                "achieved": ips_c / 1e12, "peak": peak / 1e12,
+                "unit": "T FP32-instr/s", "frac": ips_c / peak, "traffic": None,
+                "peak_basis": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz",
+                "kernel_ms_per_step": collide_ms / K,
+                "other": {"traj_kernel<32,16,8>": {"ms_per_step": traj_ms / K,
+                                                  "achieved": ips_t / 1e12, "frac": ips_t / peak}}}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": Wu, "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -293,7 +304,6 @@ def run_npp(args):
                        "l2": "flushed (256 MiB write) between timed steps",
                        "timing": "sum of per-step CUDA-event durations on the launching stream"},
             "roofline": roofline, "e2e": e2e, "gpu_launches": 2 * K, "clocks": ck,
-            "rollout_ms_per_step": rollout_ms / K,
             "free_fraction": float(np.mean(res["free"])),
             "waypoints_reached": res["waypoints_reached"]}
     if rank == 0 and not args.no_cpu_baseline:

@@ -110,7 +110,9 @@ typedef struct {
     float* costs;            /* [N]         per-sample cost, +inf if collided */
     int32_t* first_hit;      /* [N]         first colliding h, -1 if none    */
     float* sample_traj;      /* [T+1][N][4] every sample's states, EV frame at t
-                                (origin at the vehicle, x along its heading) */
+                                (origin at the vehicle, x along its heading);
+                                rows after a sample's first collision continue
+                                its dynamics and carry no meaning */
     float* sample_ctrl;      /* [T][N][2]   every sample's applied controls   */
 } npp_outputs;
 
@@ -169,14 +171,25 @@ npp_status npp_sample_params(uint64_t seed, uint32_t t_index, uint32_t stream_id
                              int32_t n0, int32_t K, int32_t n_theta, float* out_dev,
                              void* stream);
 
+/* Launch options that do not change any result (they choose among kernels
+ * computing identical values).  "collide_variant" in -1..2: 0 the
+ * block-balanced collision kernel with 16 warps and one block per SM, 1 the
+ * same with 8 warps and two blocks per SM, 2 warp-owned items of 8 samples,
+ * -1 (default) chooses by the number of samples.
+ * "traj_variant" 0 or 1: the trajectory kernel holds 2 (0, default) or 4 (1)
+ * hidden units per lane.
+ * Returns NPP_INVALID_ARG for an unknown name or value. */
+npp_status npp_set_option(npp_handle* h, const char* name, int32_t value);
+
 /* Kernel timing for measurement: when enabled, npp_plan_step and
- * npp_rollout_params record CUDA events on their stream around the rollout
- * kernel and around the whole step (rollout + epilogue).  npp_last_timing
- * synchronises on the last recorded end event and returns both durations in
- * milliseconds.  Disabled by default; enabling it adds two event records per
- * call. */
+ * npp_rollout_params record CUDA events on their stream around each stage.
+ * npp_last_timing synchronises on the last recorded event and writes up to n
+ * durations in milliseconds: [0] trajectory kernel, [1] collision kernel,
+ * [2] selection epilogue, [3] the whole call (npp_rollout_params has no
+ * epilogue: [2] is 0).  Disabled by default; enabling it adds four event
+ * records per call. */
 npp_status npp_set_timing(npp_handle* h, int32_t enable);
-npp_status npp_last_timing(npp_handle* h, float* rollout_ms, float* step_ms);
+npp_status npp_last_timing(npp_handle* h, float* stage_ms, int32_t n);
 
 #ifdef __cplusplus
 }

@@ -23,6 +23,15 @@ struct npp_handle {
     unsigned long long* d_key;           // packed best key
     float4* d_traj;                      // [(max_T+1) * max_N]
     float2* d_ctrl;                      // [max_T * max_N]
+    float* d_jfree;                      // [max_N]
+    float4* d_coefA;                     // [(max_T+1) * max_N]
+    float2* d_coefB;                     // [(max_T+1) * max_N]
+    unsigned* d_work;                    // persistent-kernel work counter
+    int sm_count;
+    int collide_variant;                 // -1 automatic; 0, 1 block-balanced (16 / 8 warps), 2 warp items
+    int collide_active;                  // variant used for the current launch
+    int traj_variant;                    // 0: 2 hidden units per lane, 1: 4
+    int occ_M, occ_blocks;               // cached occupancy for the last M
     // host-mode staging
     float4* d_obs;
     float* d_warm;
@@ -34,7 +43,7 @@ struct npp_handle {
     int32_t* d_fh;
     cudaStream_t stream;
     bool timing;
-    cudaEvent_t ev[3];                   // step start, rollout end, step end
+    cudaEvent_t ev[4];                   // start, after trajectories, after collisions, end
     std::string err;
 };
 
@@ -138,14 +147,37 @@ __global__ void sample_params_kernel(SamplerKey key, int n0, int K, int nt, floa
 }  // namespace
 
 // ------------------------------------------------------------------ helpers
-static cudaError_t launch_rollout(const npp_handle* h, const RolloutArgs& a, cudaStream_t s)
+static cudaError_t launch_traj(const npp_handle* h, const RolloutArgs& a, cudaStream_t s)
 {
-    int smem = 0;
     switch (h->cfg.width) {
-    case 16: return launch_rollout_w16(a, s, &smem);
-    case 32: return launch_rollout_w32(a, s, &smem);
-    default: return launch_rollout_w64(a, s, &smem);
+    case 16: return launch_traj_w16(a, s, h->traj_variant);
+    case 32: return launch_traj_w32(a, s, h->traj_variant);
+    default: return launch_traj_w64(a, s, h->traj_variant);
     }
+}
+
+// trajectories, then collision checks; events around both when timing
+static npp_status run_rollout(npp_handle* h, RolloutArgs& a, cudaStream_t s)
+{
+    a.coefA = h->d_coefA;
+    a.coefB = h->d_coefB;
+    a.work = h->d_work;
+    // automatic choice: the block-balanced kernel spreads few samples over
+    // all SMs; with many samples the warp-item kernel keeps more warps busy
+    const int v = h->collide_variant >= 0 ? h->collide_variant : (a.N < 8192 ? 0 : 2);
+    if (h->occ_M != a.M || h->collide_active != v) {
+        h->occ_blocks = collide_resident_blocks_per_sm(a.M, v);
+        h->occ_M = a.M;
+        h->collide_active = v;
+    }
+    a.grid_collide = h->sm_count * h->occ_blocks;
+    CUDA_TRY(h, cudaMemsetAsync(h->d_work, 0, sizeof(unsigned), s));
+    if (h->timing) CUDA_TRY(h, cudaEventRecord(h->ev[0], s));
+    CUDA_TRY(h, launch_traj(h, a, s));
+    if (h->timing) CUDA_TRY(h, cudaEventRecord(h->ev[1], s));
+    CUDA_TRY(h, launch_collide_resident(a, s, h->collide_active));
+    if (h->timing) CUDA_TRY(h, cudaEventRecord(h->ev[2], s));
+    return NPP_OK;
 }
 
 static SamplerKey make_key(uint64_t seed, uint32_t t_index, uint32_t stream_id)
@@ -168,14 +200,15 @@ static npp_status check_state_goal(npp_handle* h, const npp_state* s, const npp_
     return NPP_OK;
 }
 
-static npp_status check_sizes(npp_handle* h, int32_t M, int32_t N, int32_t T, const void* obs)
+static npp_status check_sizes(npp_handle* h, int32_t M, int32_t N, int32_t T, const void* obs,
+                              bool device_obs)
 {
     const npp_config& c = h->cfg;
     if (N < 1 || N > c.max_N) return fail(h, NPP_INVALID_ARG, "N=%d outside [1, %d]", N, c.max_N);
     if (T < 1 || T > c.max_T) return fail(h, NPP_INVALID_ARG, "T=%d outside [1, %d]", T, c.max_T);
     if (M < 0 || M > c.max_M) return fail(h, NPP_INVALID_ARG, "M=%d outside [0, %d]", M, c.max_M);
     if (M > 0 && !obs) return fail(h, NPP_INVALID_ARG, "obstacle pointer is NULL with M=%d", M);
-    if (obs && (reinterpret_cast<uintptr_t>(obs) & 15u))
+    if (device_obs && obs && (reinterpret_cast<uintptr_t>(obs) & 15u))
         return fail(h, NPP_INVALID_ARG, "obstacle array must be 16-byte aligned");
     return NPP_OK;
 }
@@ -230,9 +263,7 @@ npp_status npp_create(npp_handle** out, const npp_config* cfg, int32_t device)
         return fail(nullptr, NPP_CUDA_ERROR, "cudaSetDevice(%d) failed", device);
     int smem_optin = 0;
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
-    int max_points = cfg->width == 16 ? rollout_max_points_w16(smem_optin)
-                   : cfg->width == 32 ? rollout_max_points_w32(smem_optin)
-                                      : rollout_max_points_w64(smem_optin);
+    int max_points = collide_max_points(smem_optin);
     if (cfg->max_M > max_points)
         return fail(nullptr, NPP_UNSUPPORTED, "max_M=%d exceeds the %d points held in shared memory",
                     cfg->max_M, max_points);
@@ -241,6 +272,11 @@ npp_status npp_create(npp_handle** out, const npp_config* cfg, int32_t device)
 
     npp_handle* h = new npp_handle();
     h->cfg = *cfg;
+    h->collide_variant = -1;
+    h->collide_active = -1;
+    h->occ_M = -1;
+    cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (h->sm_count < 1) h->sm_count = 1;
     h->device = device;
     h->n_theta = n_theta_of(cfg->width);
     h->max_points = max_points;
@@ -269,6 +305,10 @@ npp_status npp_create(npp_handle** out, const npp_config* cfg, int32_t device)
     A((void**)&h->d_key, 64);
     A((void**)&h->d_traj, NT1 * sizeof(float4));
     A((void**)&h->d_ctrl, NT * sizeof(float2));
+    A((void**)&h->d_jfree, (size_t)cfg->max_N * sizeof(float));
+    A((void**)&h->d_coefA, NT1 * sizeof(float4));
+    A((void**)&h->d_coefB, NT1 * sizeof(float2));
+    A((void**)&h->d_work, 64);
     A((void**)&h->d_obs, (size_t)cfg->max_M * sizeof(float4));
     A((void**)&h->d_warm, (size_t)h->n_theta * sizeof(float));
     A((void**)&h->d_best, sizeof(npp_best));
@@ -278,7 +318,7 @@ npp_status npp_create(npp_handle** out, const npp_config* cfg, int32_t device)
     A((void**)&h->d_costs, (size_t)cfg->max_N * sizeof(float));
     A((void**)&h->d_fh, (size_t)cfg->max_N * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
-    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaEventCreate(&h->ev[i]);
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&h->ev[i]);
     if (e != cudaSuccess) {
         g_err = std::string("workspace allocation failed: ") + cudaGetErrorString(e);
         npp_destroy(h);
@@ -293,11 +333,12 @@ npp_status npp_destroy(npp_handle* h)
     if (!h) return NPP_OK;
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
-    void* ptrs[] = { h->d_key, h->d_traj, h->d_ctrl, h->d_obs, h->d_warm, h->d_best, h->d_params,
-                     h->d_controls, h->d_trajectory, h->d_costs, h->d_fh };
+    void* ptrs[] = { h->d_key, h->d_traj, h->d_ctrl, h->d_jfree, h->d_coefA, h->d_coefB, h->d_work,
+                     h->d_obs, h->d_warm, h->d_best, h->d_params, h->d_controls, h->d_trajectory,
+                     h->d_costs, h->d_fh };
     for (void* p : ptrs) if (p) cudaFree(p);
     if (h->stream) cudaStreamDestroy(h->stream);
-    for (int i = 0; i < 3; ++i) if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+    for (int i = 0; i < 4; ++i) if (h->ev[i]) cudaEventDestroy(h->ev[i]);
     delete h;
     return NPP_OK;
 }
@@ -310,7 +351,7 @@ npp_status npp_plan_step(npp_handle* h, const npp_state* state, const npp_goal* 
     if (!h) return fail(nullptr, NPP_INVALID_ARG, "handle is NULL");
     npp_status st;
     if ((st = check_state_goal(h, state, goal)) != NPP_OK) return st;
-    if ((st = check_sizes(h, M, N, T, obs_dev)) != NPP_OK) return st;
+    if ((st = check_sizes(h, M, N, T, obs_dev, true)) != NPP_OK) return st;
     if (!out || !out->best) return fail(h, NPP_INVALID_ARG, "outputs.best must not be NULL");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     CUDA_TRY(h, cudaSetDevice(h->device));
@@ -323,11 +364,10 @@ npp_status npp_plan_step(npp_handle* h, const npp_state* state, const npp_goal* 
     a.first_hit = out->first_hit;
     a.traj = out->sample_traj ? reinterpret_cast<float4*>(out->sample_traj) : h->d_traj;
     a.ctrl = out->sample_ctrl ? reinterpret_cast<float2*>(out->sample_ctrl) : h->d_ctrl;
+    a.jfree = h->d_jfree;
     a.best_key = h->d_key;
-    if (h->timing) CUDA_TRY(h, cudaEventRecord(h->ev[0], s));
     CUDA_TRY(h, cudaMemsetAsync(h->d_key, 0xff, sizeof(unsigned long long), s));
-    CUDA_TRY(h, launch_rollout(h, a, s));
-    if (h->timing) CUDA_TRY(h, cudaEventRecord(h->ev[1], s));
+    if ((st = run_rollout(h, a, s)) != NPP_OK) return st;
 
     EpilogueArgs e;
     memset(&e, 0, sizeof e);
@@ -344,7 +384,7 @@ npp_status npp_plan_step(npp_handle* h, const npp_state* state, const npp_goal* 
     e.trajectory = out->trajectory;
     epilogue_kernel<<<1, 256, 0, s>>>(e);
     CUDA_TRY(h, cudaGetLastError());
-    if (h->timing) CUDA_TRY(h, cudaEventRecord(h->ev[2], s));
+    if (h->timing) CUDA_TRY(h, cudaEventRecord(h->ev[3], s));
     return NPP_OK;
 }
 
@@ -359,8 +399,7 @@ npp_status npp_plan_step_host(npp_handle* h, const npp_state* state, const npp_g
         return fail(h, NPP_INVALID_ARG, "per-sample outputs are device-only");
     npp_status st;
     if ((st = check_state_goal(h, state, goal)) != NPP_OK) return st;
-    if ((st = check_sizes(h, M, N, T, nullptr)) != NPP_OK) return st;
-    if (M > 0 && !obs_host) return fail(h, NPP_INVALID_ARG, "obstacle pointer is NULL with M=%d", M);
+    if ((st = check_sizes(h, M, N, T, obs_host, false)) != NPP_OK) return st;
     CUDA_TRY(h, cudaSetDevice(h->device));
     cudaStream_t s = h->stream;
     if (M > 0) CUDA_TRY(h, cudaMemcpyAsync(h->d_obs, obs_host, (size_t)M * 16, cudaMemcpyHostToDevice, s));
@@ -400,7 +439,7 @@ npp_status npp_rollout_params(npp_handle* h, const npp_state* state, const npp_g
     if (!h) return fail(nullptr, NPP_INVALID_ARG, "handle is NULL");
     npp_status st;
     if ((st = check_state_goal(h, state, goal)) != NPP_OK) return st;
-    if ((st = check_sizes(h, M, K, T, obs_dev)) != NPP_OK) return st;
+    if ((st = check_sizes(h, M, K, T, obs_dev, true)) != NPP_OK) return st;
     if (!theta_dev) return fail(h, NPP_INVALID_ARG, "theta must not be NULL");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     CUDA_TRY(h, cudaSetDevice(h->device));
@@ -411,14 +450,28 @@ npp_status npp_rollout_params(npp_handle* h, const npp_state* state, const npp_g
     a.first_hit = first_hit_dev;
     a.traj = sample_traj_dev ? reinterpret_cast<float4*>(sample_traj_dev) : h->d_traj;
     a.ctrl = sample_ctrl_dev ? reinterpret_cast<float2*>(sample_ctrl_dev) : h->d_ctrl;
+    a.jfree = h->d_jfree;
     a.best_key = nullptr;
-    if (h->timing) CUDA_TRY(h, cudaEventRecord(h->ev[0], s));
-    CUDA_TRY(h, launch_rollout(h, a, s));
-    if (h->timing) {
-        CUDA_TRY(h, cudaEventRecord(h->ev[1], s));
-        CUDA_TRY(h, cudaEventRecord(h->ev[2], s));
-    }
+    if ((st = run_rollout(h, a, s)) != NPP_OK) return st;
+    if (h->timing) CUDA_TRY(h, cudaEventRecord(h->ev[3], s));
     return NPP_OK;
+}
+
+npp_status npp_set_option(npp_handle* h, const char* name, int32_t value)
+{
+    if (!h || !name) return fail(h, NPP_INVALID_ARG, "handle and name must not be NULL");
+    if (std::strcmp(name, "collide_variant") == 0) {
+        if (value < -1 || value > 2) return fail(h, NPP_INVALID_ARG, "collide_variant is -1..2");
+        h->collide_variant = value;
+        h->occ_M = -1;
+        return NPP_OK;
+    }
+    if (std::strcmp(name, "traj_variant") == 0) {
+        if (value != 0 && value != 1) return fail(h, NPP_INVALID_ARG, "traj_variant is 0 or 1");
+        h->traj_variant = value;
+        return NPP_OK;
+    }
+    return fail(h, NPP_INVALID_ARG, "unknown option '%s'", name);
 }
 
 npp_status npp_set_timing(npp_handle* h, int32_t enable)
@@ -428,17 +481,19 @@ npp_status npp_set_timing(npp_handle* h, int32_t enable)
     return NPP_OK;
 }
 
-npp_status npp_last_timing(npp_handle* h, float* rollout_ms, float* step_ms)
+npp_status npp_last_timing(npp_handle* h, float* stage_ms, int32_t n)
 {
     if (!h) return fail(nullptr, NPP_INVALID_ARG, "handle is NULL");
     if (!h->timing) return fail(h, NPP_INVALID_ARG, "timing is not enabled on this handle");
+    if (!stage_ms || n < 1) return fail(h, NPP_INVALID_ARG, "stage_ms must hold n >= 1 values");
     CUDA_TRY(h, cudaSetDevice(h->device));
-    CUDA_TRY(h, cudaEventSynchronize(h->ev[2]));
-    float a = 0.f, b = 0.f;
-    CUDA_TRY(h, cudaEventElapsedTime(&a, h->ev[0], h->ev[1]));
-    CUDA_TRY(h, cudaEventElapsedTime(&b, h->ev[0], h->ev[2]));
-    if (rollout_ms) *rollout_ms = a;
-    if (step_ms) *step_ms = b;
+    CUDA_TRY(h, cudaEventSynchronize(h->ev[3]));
+    float t[4] = { 0.f, 0.f, 0.f, 0.f };
+    CUDA_TRY(h, cudaEventElapsedTime(&t[0], h->ev[0], h->ev[1]));
+    CUDA_TRY(h, cudaEventElapsedTime(&t[1], h->ev[1], h->ev[2]));
+    CUDA_TRY(h, cudaEventElapsedTime(&t[2], h->ev[2], h->ev[3]));
+    CUDA_TRY(h, cudaEventElapsedTime(&t[3], h->ev[0], h->ev[3]));
+    for (int i = 0; i < n && i < 4; ++i) stage_ms[i] = t[i];
     return NPP_OK;
 }
 

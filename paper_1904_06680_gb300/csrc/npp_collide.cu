@@ -1,0 +1,34 @@
+// Collision kernels with all obstacle points resident in shared memory.
+// Variants compute the same values: 0 block-balanced (16 warps, one block per
+// SM, items of up to 128 samples); 1 block-balanced with 8 warps and two
+// blocks per SM; 2 warp-owned items of 8 samples pulled from a queue.
+#include "npp_rollout.cuh"
+
+namespace npp {
+
+using CollideResident = CollideBlockKernel<16, 128>;
+
+cudaError_t launch_collide_resident(const RolloutArgs& a, cudaStream_t s, int variant)
+{
+    switch (variant) {
+    case 0: return launch_collide_block<16, 128, 1>(a, s);
+    case 1: return launch_collide_block<8, 64, 2>(a, s);
+    default: return launch_collide_warp<8, 2>(a, s);
+    }
+}
+
+int collide_resident_blocks_per_sm(int M, int variant)
+{
+    switch (variant) {
+    case 0: return collide_block_blocks_per_sm<16, 128, 1>(M);
+    case 1: return collide_block_blocks_per_sm<8, 64, 2>(M);
+    default: return collide_warp_blocks_per_sm<8, 2>(M);
+    }
+}
+
+int collide_max_points(int smem_limit)
+{
+    return 2 * ((smem_limit - CollideResident::fixed_bytes()) / 32);
+}
+
+}  // namespace npp

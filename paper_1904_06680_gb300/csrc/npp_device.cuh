@@ -133,7 +133,12 @@ struct RolloutArgs {
     int* first_hit;                    // [N] or null
     float4* traj;                      // [T+1][N] EV frame (always written)
     float2* ctrl;                      // [T][N]
+    float* jfree;                      // [N] cost of each sample if collision-free
+    float4* coefA;                     // [T+1][N] (A, B, -C, D) scaled inequality rows
+    float2* coefB;                     // [T+1][N] (E, -F)
     unsigned long long* best_key;      // packed (class, cost, index) minimum
+    unsigned* work;                    // work-queue counter of the persistent collision kernel
+    int grid_collide;                  // persistent grid size
 };
 
 struct EpilogueArgs {
@@ -150,12 +155,12 @@ struct EpilogueArgs {
     float* trajectory;
 };
 
-// launchers (one translation unit per network width)
-cudaError_t launch_rollout_w16(const RolloutArgs& a, cudaStream_t s, int* smem_needed);
-cudaError_t launch_rollout_w32(const RolloutArgs& a, cudaStream_t s, int* smem_needed);
-cudaError_t launch_rollout_w64(const RolloutArgs& a, cudaStream_t s, int* smem_needed);
-int rollout_max_points_w16(int smem_limit);
-int rollout_max_points_w32(int smem_limit);
-int rollout_max_points_w64(int smem_limit);
+// launchers: trajectory kernel per network width, one collision kernel
+cudaError_t launch_traj_w16(const RolloutArgs& a, cudaStream_t s, int variant);
+cudaError_t launch_traj_w32(const RolloutArgs& a, cudaStream_t s, int variant);
+cudaError_t launch_traj_w64(const RolloutArgs& a, cudaStream_t s, int variant);
+cudaError_t launch_collide_resident(const RolloutArgs& a, cudaStream_t s, int variant);
+int collide_resident_blocks_per_sm(int M, int variant);
+int collide_max_points(int smem_limit);
 
 }  // namespace npp

@@ -1,23 +1,28 @@
-// npp_rollout.cuh -- the batched rollout kernel (one template per network
-// width), instantiated by npp_rollout_w{16,32,64}.cu.
+// npp_rollout.cuh -- the two kernels of one plan step, instantiated per
+// network width by npp_rollout_w{16,32,64}.cu.
 //
-// What one block does (paper: Sect. II-D "First".."Sixth", Sect. IV):
-//   * stages the M obstacle points in shared memory, rotated into the
-//     EV-aligned frame at t (Sect. II-C, m^ext in (xi, eta) coordinates);
-//   * owns B samples; a group of G lanes of one warp holds one sample's
-//     network in registers (each lane two hidden units: its rows of W1, W2,
-//     its columns of W3), generated straight from Philox, never stored;
-//   * steps all its samples through h = 0..T in lockstep.  Per step:
-//       collision phase -- the block's warps split the M points, each lane
-//         tests its points against a chunk of C live samples at once
-//         (Eq. eq_Apsietc_collAvoidIneqs with the rectangle's inequalities
-//         scaled to |xi''| < 1, |eta''| < 1: 4 FMA + 2 min/max per pair),
-//         points extrapolated at constant velocity (Sect. II-D (ii)-(iv));
-//       control phase -- features (Eq. eq_def_stph), MLP with the hidden
-//         vector exchanged through shared memory, rate-limited controls,
-//         one Euler step of the kinematic bicycle on the old state;
-//   * reduces (class, cost, index) keys to the block minimum and folds it
-//     into the global minimum with one 64-bit atomicMin.
+// The rollout of a sample (Sect. II-D "Sixth", Sect. IV) does not depend on
+// its collision checks: a collision only ends the sample (cost +inf).  The
+// step is therefore split into
+//
+//   traj_kernel    -- per sample: features (Eq. eq_def_stph), MLP
+//                     a = X(s, theta) (Eq. eq_def_at), rate-limited controls,
+//                     Euler step of the kinematic bicycle on the old state,
+//                     for h = 0..T; writes the states [T+1][N], the applied
+//                     controls [T][N] and the cost the sample has if it is
+//                     collision-free.  A group of G lanes of one warp holds
+//                     one sample's network in registers (each lane W/G hidden
+//                     units: its rows of W1, W2 and columns of W3), generated
+//                     straight from Philox and never stored.
+//   collide_kernel -- per block of SB samples: the M obstacle points staged in
+//                     shared memory in the EV-aligned frame at t, then for
+//                     h = 0..T the still-live samples are checked against the
+//                     points extrapolated at constant velocity (Sect. II-D
+//                     items (i)-(iv)) with the polytope inequalities of Eq.
+//                     eq_Apsietc_collAvoidIneqs; a sample leaves the live list
+//                     at its first collision.  Finally the (class, cost,
+//                     index) keys are reduced and folded into the global
+//                     minimum with one 64-bit atomicMin per block.
 #pragma once
 
 #include <cfloat>
@@ -28,9 +33,9 @@
 
 namespace npp {
 
-template <int W>
+template <int W, int G_>
 struct Shape {
-    static constexpr int G = (W == 16) ? 8 : (W == 32) ? 16 : 32;   // lanes per sample
+    static constexpr int G = G_;                                     // lanes per sample
     static constexpr int U = W / G;                                  // hidden units per lane
     static constexpr int NT = 12 * W + W * W + 2;                    // parameters
     static constexpr int OFF_B1 = NIN * W;
@@ -38,7 +43,8 @@ struct Shape {
     static constexpr int OFF_B2 = OFF_W2 + W * W;
     static constexpr int OFF_W3 = OFF_B2 + W;
     static constexpr int OFF_B3 = OFF_W3 + 2 * W;
-    static_assert(U == 2, "two hidden units per lane");
+    static_assert(U == 2 || U == 4, "2 or 4 hidden units per lane");
+    static_assert(G <= 32 && (32 % G) == 0, "a group lives in one warp");
 };
 
 // Parameter source: Philox (sampled) or memory (explicit / warm start).
@@ -46,6 +52,8 @@ struct ThetaSrc {
     const float* mem;     // row of this sample, or null -> sample
     SamplerKey key;
     uint32_t n;
+    // rows from memory are read element by element: a row of n_theta floats
+    // starts at any 4-byte boundary
     __device__ __forceinline__ float4 quad(int i) const {     // i % 4 == 0
         if (mem) return make_float4(mem[i], mem[i + 1], mem[i + 2], mem[i + 3]);
         return sample_quad(key, (uint32_t)i >> 2, n);
@@ -56,18 +64,19 @@ struct ThetaSrc {
     }
 };
 
-template <int W>
+template <int W, int G>
 struct LaneNet {
-    using S = Shape<W>;
-    float w1[S::U][NIN], b1[S::U];
-    float w2[S::U][W], b2[S::U];
-    float w3[2][S::U], b3[2];
+    using S = Shape<W, G>;
+    static constexpr int U = S::U;
+    float w1[U][NIN], b1[U];
+    float w2[U][W], b2[U];
+    float w3[2][U], b3[2];
 
-    // lane gl of the group holds hidden units 2 gl and 2 gl + 1
+    // lane gl of the group holds hidden units gl*U .. gl*U + U - 1
     __device__ __forceinline__ void load(const ThetaSrc& src, int gl) {
 #pragma unroll
-        for (int j = 0; j < S::U; ++j) {
-            const int u = gl * S::U + j;
+        for (int j = 0; j < U; ++j) {
+            const int u = gl * U + j;
 #pragma unroll
             for (int i = 0; i < NIN; i += 4) {
                 const float4 q = src.quad(u * NIN + i);
@@ -79,14 +88,17 @@ struct LaneNet {
                 w2[j][i] = q.x; w2[j][i + 1] = q.y; w2[j][i + 2] = q.z; w2[j][i + 3] = q.w;
             }
         }
-        const float2 pb1 = src.pair(S::OFF_B1 + gl * S::U);
-        b1[0] = pb1.x; b1[1] = pb1.y;
-        const float2 pb2 = src.pair(S::OFF_B2 + gl * S::U);
-        b2[0] = pb2.x; b2[1] = pb2.y;
 #pragma unroll
-        for (int o = 0; o < 2; ++o) {
-            const float2 p = src.pair(S::OFF_W3 + o * W + gl * S::U);
-            w3[o][0] = p.x; w3[o][1] = p.y;
+        for (int j = 0; j < U; j += 2) {
+            const float2 pb1 = src.pair(S::OFF_B1 + gl * U + j);
+            b1[j] = pb1.x; b1[j + 1] = pb1.y;
+            const float2 pb2 = src.pair(S::OFF_B2 + gl * U + j);
+            b2[j] = pb2.x; b2[j + 1] = pb2.y;
+#pragma unroll
+            for (int o = 0; o < 2; ++o) {
+                const float2 p = src.pair(S::OFF_W3 + o * W + gl * U + j);
+                w3[o][j] = p.x; w3[o][j + 1] = p.y;
+            }
         }
         const float2 pb3 = src.pair(S::OFF_B3);
         b3[0] = pb3.x; b3[1] = pb3.y;
@@ -100,108 +112,48 @@ __device__ __forceinline__ float wrap_pi(float a)
     return a - TWO_PI * floorf((a + 3.14159265358979323846f) * INV_TWO_PI);
 }
 
-// Collision phase: warps split the points; every lane tests its points
-// against chunks of C live samples.  Sets hit[b] for samples that collide.
-template <int NW, int C>
-__device__ __forceinline__ void collide_phase(const float4* __restrict__ pts, int M, float tau,
-                                              const float4* __restrict__ coef,
-                                              int* __restrict__ hit, unsigned live,
-                                              int warp, int lane)
+// The rectangle's four inequalities at state (x, y, phi), scaled so that a
+// point p is inside iff |A px + B py - C| < 2 and |D px + E py - F| < 2: rows
+// along and across the heading divided by the half length / width, times 2
+// (an exact scaling).  |v| < 2 holds exactly when bit 30 of v's IEEE pattern
+// is clear, so "both inside" is bit 30 of (xi | eta) clear: one 3-input logic
+// op per point-sample pair accumulates "some point inside".
+__device__ __forceinline__ void write_coef(const RolloutArgs& a, const DevCfg& c, size_t idx,
+                                           float x, float y, float sp, float cp)
 {
-    const int per = (M + NW - 1) / NW;
-    const int j0 = warp * per;
-    const int j1 = min(M, j0 + per);
-    while (live) {
-        int sidx[C];
-        float cA[C], cB[C], cC[C], cD[C], cE[C], cF[C];
-#pragma unroll
-        for (int k = 0; k < C; ++k) {
-            if (live) {
-                const int s = __ffs(live) - 1;
-                live &= live - 1;
-                sidx[k] = s;
-                const float4 q0 = coef[2 * s], q1 = coef[2 * s + 1];
-                cA[k] = q0.x; cB[k] = q0.y; cC[k] = q0.z; cD[k] = q0.w; cE[k] = q1.x; cF[k] = q1.y;
-            } else {
-                sidx[k] = -1;                 // padding slot: |xi''| = 2, never inside
-                cA[k] = 0.f; cB[k] = 0.f; cC[k] = -2.f; cD[k] = 0.f; cE[k] = 0.f; cF[k] = 0.f;
-            }
-        }
-        float m[C];
-#pragma unroll
-        for (int k = 0; k < C; ++k) m[k] = FLT_MAX;
-        for (int j = j0 + lane; j < j1; j += 32) {
-            const float4 p = pts[j];
-            const float px = fmaf(tau, p.z, p.x);
-            const float py = fmaf(tau, p.w, p.y);
-#pragma unroll
-            for (int k = 0; k < C; ++k) {
-                const float xi = fmaf(cA[k], px, fmaf(cB[k], py, -cC[k]));
-                const float et = fmaf(cD[k], px, fmaf(cE[k], py, -cF[k]));
-                m[k] = fminf(m[k], fmaxf(fabsf(xi), fabsf(et)));
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < C; ++k) {
-            if (sidx[k] >= 0 && __any_sync(FULL, m[k] < 1.0f) && lane == 0) hit[sidx[k]] = 1;
-        }
-    }
+    const float sl = 2.0f * c.ihl, sw = 2.0f * c.ihw;
+    a.coefA[idx] = make_float4(cp * sl, sp * sl, -((cp * x + sp * y + c.c_off) * sl), -sp * sw);
+    a.coefB[idx] = make_float2(cp * sw, -((-sp * x + cp * y) * sw));
 }
 
-template <int W, int NW, int C>
-struct RolloutKernel {
-    using S = Shape<W>;
-    static constexpr int G = S::G;
-    static constexpr int U = S::U;
+// ------------------------------------------------------------------ traj
+template <int W, int G, int NW>
+struct TrajKernel {
     static constexpr int THREADS = NW * 32;
-    static constexpr int B = THREADS / G;            // samples per block
-    static_assert(B <= 32, "live mask is one warp ballot");
-
-    // shared memory carve-up (bytes), points first
-    static constexpr int fixed_bytes() {
-        return B * 32 /*coef*/ + B * 4 /*hit*/ + B * 4 /*alive*/ + B * W * 4 /*hidden*/
-             + NW * 8 /*reduction*/ + 64;
-    }
-    static int smem_bytes(int M) { return M * 16 + fixed_bytes(); }
+    static constexpr int B = THREADS / G;             // samples per block
 };
 
-template <int W, int NW, int C>
-__global__ void __launch_bounds__(NW * 32, 1) rollout_kernel(const RolloutArgs a)
+template <int W, int G, int NW>
+__global__ void __launch_bounds__(NW * 32) traj_kernel(const RolloutArgs a)
 {
-    using K = RolloutKernel<W, NW, C>;
-    using S = Shape<W>;
-    constexpr int G = K::G, U = K::U, B = K::B;
-
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float4* pts = reinterpret_cast<float4*>(smem_raw);
-    float4* coef = pts + a.M;
-    int* hit = reinterpret_cast<int*>(coef + 2 * B);
-    int* alive_f = hit + B;
-    float* hx = reinterpret_cast<float*>(alive_f + B);
-    unsigned long long* red = reinterpret_cast<unsigned long long*>(hx + B * W);
+    using S = Shape<W, G>;
+    constexpr int U = S::U;
+    constexpr int B = TrajKernel<W, G, NW>::B;
+    __shared__ __align__(16) float hx_all[B * W];
 
     const int tid = threadIdx.x;
-    const int warp = tid >> 5, lane = tid & 31;
     const int b = tid / G, gl = tid % G;
     const int n = blockIdx.x * B + b;
     const bool valid = n < a.N;
     const DevCfg& c = a.c;
 
-    // frame of the vehicle at time t
     float s0, c0;
     sincosf(a.phi0, &s0, &c0);
-    for (int j = tid; j < a.M; j += K::THREADS) {
-        const float4 o = a.obs[j];
-        const float dx = o.x - a.x0, dy = o.y - a.y0;
-        pts[j] = make_float4(c0 * dx + s0 * dy, -s0 * dx + c0 * dy,
-                             c0 * o.z + s0 * o.w, -s0 * o.z + c0 * o.w);
-    }
     const float gdx = a.gx - a.x0, gdy = a.gy - a.y0;
     const float gxi = c0 * gdx + s0 * gdy, geta = -s0 * gdx + c0 * gdy;
     const float gph = a.gphi - a.phi0, gv = a.gv;
 
-    // this lane's slice of the sample's network
-    LaneNet<W> net;
+    LaneNet<W, G> net;
     {
         ThetaSrc src;
         src.key = a.key;
@@ -213,33 +165,18 @@ __global__ void __launch_bounds__(NW * 32, 1) rollout_kernel(const RolloutArgs a
     }
 
     float x = 0.f, y = 0.f, ph = 0.f, v = a.v0, ap0 = a.ap0, ap1 = a.ap1, E = 0.f;
-    bool alive = valid;
-    int fh = -1;
     const int T = a.T, N = a.N;
     const float invT = 1.0f / (float)T;
+    float* hrow = hx_all + b * W;
+    const bool writer = valid && gl == 0;
 
-    for (int h = 0;; ++h) {
+    for (int h = 0; h < T; ++h) {
         float sp, cp;
         sincosf(ph, &sp, &cp);
-        if (gl == 0) {
-            if (alive) a.traj[(size_t)h * N + n] = make_float4(x, y, ph, v);
-            coef[2 * b] = make_float4(cp * c.ihl, sp * c.ihl, (cp * x + sp * y + c.c_off) * c.ihl,
-                                      -sp * c.ihw);
-            coef[2 * b + 1] = make_float4(cp * c.ihw, (-sp * x + cp * y) * c.ihw, 0.f, 0.f);
-            hit[b] = 0;
-            alive_f[b] = alive ? 1 : 0;
+        if (writer) {
+            a.traj[(size_t)h * N + n] = make_float4(x, y, ph, v);
+            write_coef(a, c, (size_t)h * N + n, x, y, sp, cp);
         }
-        __syncthreads();
-        {
-            const unsigned live = __ballot_sync(FULL, lane < B && alive_f[lane] != 0);
-            collide_phase<NW, C>(pts, a.M, (float)h * c.Ts, coef, hit, live, warp, lane);
-        }
-        __syncthreads();
-        if (alive && hit[b]) { alive = false; fh = h; }
-        if (h == T) break;
-        if (!__syncthreads_or(alive)) break;
-
-        // ---- control phase: features, network, controls, Euler step
         float s[NIN];
         s[0] = (gxi - x) * c.idxi;
         s[1] = (geta - y) * c.ideta;
@@ -257,8 +194,8 @@ __global__ void __launch_bounds__(NW * 32, 1) rollout_kernel(const RolloutArgs a
             for (int i = 0; i < NIN; ++i) acc = fmaf(net.w1[j][i], s[i], acc);
             h1[j] = tanhf(acc);
         }
-        float* hrow = hx + b * W;
-        *reinterpret_cast<float2*>(hrow + gl * U) = make_float2(h1[0], h1[1]);
+#pragma unroll
+        for (int j = 0; j < U; ++j) hrow[gl * U + j] = h1[j];
         __syncwarp();
         float acc2[U];
 #pragma unroll
@@ -276,11 +213,18 @@ __global__ void __launch_bounds__(NW * 32, 1) rollout_kernel(const RolloutArgs a
             }
         }
         __syncwarp();
+        // layer 3: a fixed pairwise tree over the hidden units -- leaves
+        // w_2i h_2i + w_2i+1 h_2i+1 (one fma), then sums of neighbours -- so
+        // the value does not depend on how many units a lane holds
         float h2[U];
 #pragma unroll
         for (int j = 0; j < U; ++j) h2[j] = tanhf(acc2[j]);
         float p0 = fmaf(net.w3[0][1], h2[1], net.w3[0][0] * h2[0]);
         float p1 = fmaf(net.w3[1][1], h2[1], net.w3[1][0] * h2[0]);
+        if constexpr (U == 4) {
+            p0 += fmaf(net.w3[0][3], h2[3], net.w3[0][2] * h2[2]);
+            p1 += fmaf(net.w3[1][3], h2[3], net.w3[1][2] * h2[2]);
+        }
 #pragma unroll
         for (int off = 1; off < G; off <<= 1) {
             p0 += __shfl_xor_sync(FULL, p0, off);
@@ -288,74 +232,494 @@ __global__ void __launch_bounds__(NW * 32, 1) rollout_kernel(const RolloutArgs a
         }
         const float ar0 = tanhf(net.b3[0] + p0);
         const float ar1 = tanhf(net.b3[1] + p1);
-        if (alive) {
-            float a0 = fminf(fmaxf(ar0, ap0 - c.r_rate), ap0 + c.r_rate);
-            a0 = fminf(fmaxf(a0, -1.0f), 1.0f);
-            const float a1 = ar1;
-            E += a0 * a0 + a1 * a1;
-            if (gl == 0) a.ctrl[(size_t)h * N + n] = make_float2(a0, a1);
-            const float td = tanf(c.delta_max * a0);
-            const float tb = c.lrL * td;
-            const float dv = c.Ts * v;
-            x += dv * (cp - sp * tb);
-            y += dv * (sp + cp * tb);
-            ph += dv * td * c.iL;
-            v += c.Ts * (c.umid + c.uhalf * a1);
-            ap0 = a0;
-            ap1 = a1;
-        }
+        float a0 = fminf(fmaxf(ar0, ap0 - c.r_rate), ap0 + c.r_rate);
+        a0 = fminf(fmaxf(a0, -1.0f), 1.0f);
+        const float a1 = ar1;
+        E += a0 * a0 + a1 * a1;
+        if (writer) a.ctrl[(size_t)h * N + n] = make_float2(a0, a1);
+        const float td = tanf(c.delta_max * a0);
+        const float tb = c.lrL * td;
+        const float dv = c.Ts * v;
+        x += dv * (cp - sp * tb);
+        y += dv * (sp + cp * tb);
+        ph += dv * td * c.iL;
+        v += c.Ts * (c.umid + c.uhalf * a1);
+        ap0 = a0;
+        ap1 = a1;
     }
-
-    // ---- cost and packed selection key
-    unsigned long long key = ~0ull;
-    if (valid && gl == 0) {
-        float J = __int_as_float(0x7f800000);
-        if (alive) {
-            const float dx = x - gxi, dy = y - geta;
-            J = c.w_pos * sqrtf(dx * dx + dy * dy) + c.w_phi * fabsf(wrap_pi(ph - gph))
-              + c.w_v * fabsf(v - gv) + c.w_effort * E * invT;
-            key = ((unsigned long long)__float_as_uint(J) << 32) | (unsigned)n;
-        } else {
-            key = (1ull << 63) | ((unsigned long long)(T - fh) << 32) | (unsigned)n;
-        }
-        if (a.costs) a.costs[n] = J;
-        if (a.first_hit) a.first_hit[n] = alive ? -1 : fh;
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        const unsigned long long o = __shfl_xor_sync(FULL, key, off);
-        key = o < key ? o : key;
-    }
-    if (lane == 0) red[warp] = key;
-    __syncthreads();
-    if (tid == 0) {
-        unsigned long long k = red[0];
-        for (int w = 1; w < NW; ++w) k = red[w] < k ? red[w] : k;
-        if (a.best_key) atomicMin(a.best_key, k);
+    if (writer) {
+        float sp, cp;
+        sincosf(ph, &sp, &cp);
+        a.traj[(size_t)T * N + n] = make_float4(x, y, ph, v);
+        write_coef(a, c, (size_t)T * N + n, x, y, sp, cp);
+        const float dx = x - gxi, dy = y - geta;
+        a.jfree[n] = c.w_pos * sqrtf(dx * dx + dy * dy) + c.w_phi * fabsf(wrap_pi(ph - gph))
+                   + c.w_v * fabsf(v - gv) + c.w_effort * E * invT;
     }
 }
 
-template <int W, int NW, int C>
-cudaError_t launch_rollout(const RolloutArgs& a, cudaStream_t stream, int* smem_needed)
+// ------------------------------------------------------------------ collide
+// Points live in shared memory as pairs: XY[q] = (x_2q, x_2q+1, y_2q, y_2q+1),
+// V[q] = (vx_2q, vx_2q+1, vy_2q, vy_2q+1), so that one packed FP32x2 FMA
+// handles the same sample against two points.
+__device__ __forceinline__ unsigned long long pk(float lo, float hi)
 {
-    using K = RolloutKernel<W, NW, C>;
-    const int smem = K::smem_bytes(a.M);
-    if (smem_needed) *smem_needed = smem;
+    return ((unsigned long long)__float_as_uint(hi) << 32) | __float_as_uint(lo);
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b,
+                                                   unsigned long long c)
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// One work unit: CC live samples (compact coefficient slots cs .. cs+CC-1, at
+// most `nvalid` real; the rest repeat slot cs) against point pairs [q0, q1)
+// at time tau.  Each lane keeps m = min over its points of max(|xi''|,
+// |eta''|); a sample collides iff some lane has m < 1.  Returns the hit bits
+// of the CC slots.
+template <int CC>
+__device__ __forceinline__ unsigned check_unit(const float4* __restrict__ XY, const float4* __restrict__ V,
+                                               int q0, int q1, float tau,
+                                               const float4* __restrict__ cfA, const float2* __restrict__ cfB,
+                                               int cs, int nvalid, int lane)
+{
+    unsigned long long A[CC], B[CC], NC[CC], D[CC], E[CC], NF[CC];
+#pragma unroll
+    for (int k = 0; k < CC; ++k) {
+        const int slot = cs + (k < nvalid ? k : 0);
+        const float4 qa = cfA[slot];
+        const float2 qb = cfB[slot];
+        A[k] = pk(qa.x, qa.x); B[k] = pk(qa.y, qa.y); NC[k] = pk(qa.z, qa.z);
+        D[k] = pk(qa.w, qa.w); E[k] = pk(qb.x, qb.x); NF[k] = pk(qb.y, qb.y);
+    }
+    unsigned long long acc[CC];
+#pragma unroll
+    for (int k = 0; k < CC; ++k) acc[k] = 0ull;
+    const unsigned long long TT = pk(tau, tau);
+#pragma unroll 2
+    for (int q = q0 + lane; q < q1; q += 32) {
+        const float4 xy = XY[q];
+        const float4 vv = V[q];
+        const unsigned long long PX = fma2(TT, pk(vv.x, vv.y), pk(xy.x, xy.y));
+        const unsigned long long PY = fma2(TT, pk(vv.z, vv.w), pk(xy.z, xy.w));
+#pragma unroll
+        for (int k = 0; k < CC; ++k) {
+            const unsigned long long xi = fma2(A[k], PX, fma2(B[k], PY, NC[k]));
+            const unsigned long long et = fma2(D[k], PX, fma2(E[k], PY, NF[k]));
+            acc[k] |= ~(xi | et);
+        }
+    }
+    unsigned bits = 0;
+#pragma unroll
+    for (int k = 0; k < CC; ++k) {
+        const bool inside = ((((unsigned)acc[k]) | (unsigned)(acc[k] >> 32)) >> 30) & 1u;
+        if (k < nvalid && __any_sync(FULL, inside)) bits |= 1u << k;
+    }
+    return bits;
+}
+
+// Staging of the points in the EV frame as pairs; an odd tail is padded with
+// a point 1e15 m away (never inside).
+template <int THREADS>
+__device__ __forceinline__ int stage_points(const RolloutArgs& a, float4* XY, float4* V)
+{
+    const int npairs = (a.M + 1) / 2;
+    float s0, c0;
+    sincosf(a.phi0, &s0, &c0);
+    float* xy = reinterpret_cast<float*>(XY);
+    float* vv = reinterpret_cast<float*>(V);
+    for (int j = threadIdx.x; j < 2 * npairs; j += THREADS) {
+        float px = 1e15f, py = 1e15f, vx = 0.f, vy = 0.f;
+        if (j < a.M) {
+            const float4 o = a.obs[j];
+            const float dx = o.x - a.x0, dy = o.y - a.y0;
+            px = c0 * dx + s0 * dy;
+            py = -s0 * dx + c0 * dy;
+            vx = c0 * o.z + s0 * o.w;
+            vy = -s0 * o.z + c0 * o.w;
+        }
+        const int q = j >> 1, o2 = j & 1;
+        xy[4 * q + o2] = px;
+        xy[4 * q + 2 + o2] = py;
+        vv[4 * q + o2] = vx;
+        vv[4 * q + 2 + o2] = vy;
+    }
+    return npairs;
+}
+
+// Point slices per chunk for this step: the count whose units spread best
+// over the NW warps (ties to fewer slices), each slice keeping at least
+// `min_pairs` point pairs.
+template <int NW>
+__device__ __forceinline__ int choose_slices(int nch, int npairs)
+{
+    const int cand[8] = { 1, 2, 3, 4, 6, 8, 12, 16 };
+    int best_s = 1;
+    float best_e = 0.f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int S = cand[i];
+        if (S > 1 && npairs / S < 96) break;
+        const int units = nch * S;
+        const int rounds = (units + NW - 1) / NW;
+        const float e = (float)units / (float)(NW * rounds);
+        if (e > best_e + 1e-3f) { best_e = e; best_s = S; }
+    }
+    return best_s;
+}
+
+template <int NW, int SBMAX>
+struct CollideBlockKernel {
+    static constexpr int THREADS = NW * 32;
+    static_assert(SBMAX <= 128 && SBMAX % 32 == 0, "live list of at most 128 slots");
+    static constexpr int fixed_bytes() {
+        return 2 * SBMAX * 16 + 2 * SBMAX * 8 + 2 * SBMAX * 4 + NW * 8 + 64;
+    }
+    static int smem_bytes(int M) { return ((M + 1) / 2) * 32 + fixed_bytes(); }
+};
+
+// Block-balanced collision kernel.  Block b owns an equal contiguous share of
+// the samples and processes it in items of at most SBMAX samples; within an
+// item all live samples advance through h = 0..T together.  The live list is
+// kept compact and in sample order: slot r holds the r-th live sample, whose
+// owner thread knows its rank; after each step the hit slots are removed and
+// every rank shifts down by the number of hits below it.  The next step's
+// coefficient rows are prefetched by the owners during the checks.
+template <int NW, int SBMAX, int MINB>
+__global__ void __launch_bounds__(NW * 32, MINB) collide_block_kernel(const RolloutArgs a)
+{
+    using K = CollideBlockKernel<NW, SBMAX>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int npairs_all = (a.M + 1) / 2;
+    float4* XY = reinterpret_cast<float4*>(smem_raw);
+    float4* V = XY + npairs_all;
+    float4* cfA = V + npairs_all;                              // [2][SBMAX]
+    float2* cfB = reinterpret_cast<float2*>(cfA + 2 * SBMAX);  // [2][SBMAX]
+    int* hitf = reinterpret_cast<int*>(cfB + 2 * SBMAX);       // [2][SBMAX]
+    unsigned long long* red = reinterpret_cast<unsigned long long*>(hitf + 2 * SBMAX);
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const DevCfg& c = a.c;
+    const int T = a.T, N = a.N;
+    const int npairs = stage_points<K::THREADS>(a, XY, V);
+
+    // this block's share of the samples
+    const int per_block = (N + gridDim.x - 1) / gridDim.x;
+    const int b_begin = min(N, blockIdx.x * per_block);
+    const int b_end = min(N, b_begin + per_block);
+    const int nitems = (b_end - b_begin + SBMAX - 1) / SBMAX;
+    unsigned long long best = ~0ull;
+
+    for (int it = 0; it < nitems; ++it) {
+        const int i_begin = b_begin + (int)(((long long)(b_end - b_begin) * it) / nitems);
+        const int i_end = b_begin + (int)(((long long)(b_end - b_begin) * (it + 1)) / nitems);
+        const int cnt = i_end - i_begin;
+        const bool owner = tid < cnt;
+        const int n = i_begin + tid;
+        bool alive = owner;
+        int fh = -1;
+        int rank = tid;
+        int L = cnt;
+        float4 ca = make_float4(0.f, 0.f, 0.f, 0.f);
+        float2 cb = make_float2(0.f, 0.f);
+        if (owner) { ca = a.coefA[n]; cb = a.coefB[n]; }
+        __syncthreads();                      // points staged / previous item done
+        for (int h = 0; h <= T; ++h) {
+            const int buf = h & 1;
+            if (alive) {
+                cfA[buf * SBMAX + rank] = ca;
+                cfB[buf * SBMAX + rank] = cb;
+                hitf[buf * SBMAX + rank] = 0;
+                if (h < T) {
+                    const size_t idx = (size_t)(h + 1) * N + n;
+                    ca = a.coefA[idx];
+                    cb = a.coefB[idx];
+                }
+            }
+            __syncthreads();
+            const int nch = (L + 7) / 8;
+            const int S = choose_slices<NW>(nch, npairs);
+            const int nunits = nch * S;
+            const int per = (npairs + S - 1) / S;
+            const float tau = (float)h * c.Ts;
+            const float4* A_ = cfA + buf * SBMAX;
+            const float2* B_ = cfB + buf * SBMAX;
+            for (int u = warp; u < nunits; u += NW) {
+                const int ch = u % nch, sl = u / nch;
+                const int q0 = sl * per, q1 = min(npairs, q0 + per);
+                const int cs = ch * 8;
+                const int nv = min(8, L - cs);
+                unsigned bits;
+                if (nv > 4)      bits = check_unit<8>(XY, V, q0, q1, tau, A_, B_, cs, nv, lane);
+                else if (nv > 2) bits = check_unit<4>(XY, V, q0, q1, tau, A_, B_, cs, nv, lane);
+                else if (nv > 1) bits = check_unit<2>(XY, V, q0, q1, tau, A_, B_, cs, nv, lane);
+                else             bits = check_unit<1>(XY, V, q0, q1, tau, A_, B_, cs, nv, lane);
+                if (lane < 8 && ((bits >> lane) & 1u)) hitf[buf * SBMAX + cs + lane] = 1;
+            }
+            __syncthreads();
+            // hit mask over the (at most 128) live slots, identical in every warp
+            unsigned hm[SBMAX / 32];
+#pragma unroll
+            for (int w = 0; w < SBMAX / 32; ++w) {
+                const int r = 32 * w + lane;
+                hm[w] = __ballot_sync(FULL, r < L && hitf[buf * SBMAX + r] != 0);
+            }
+            int nhits = 0;
+#pragma unroll
+            for (int w = 0; w < SBMAX / 32; ++w) nhits += __popc(hm[w]);
+            if (alive) {
+                const int w = rank >> 5, bit = rank & 31;
+                if ((hm[w] >> bit) & 1u) {
+                    alive = false;
+                    fh = h;
+                } else {
+                    int below = __popc(hm[w] & ((1u << bit) - 1u));
+#pragma unroll
+                    for (int ww = 0; ww < SBMAX / 32; ++ww) if (ww < w) below += __popc(hm[ww]);
+                    rank -= below;
+                }
+            }
+            L -= nhits;
+            if (L == 0) break;
+        }
+        if (owner) {
+            float J = __int_as_float(0x7f800000);
+            unsigned long long key;
+            if (fh < 0) {
+                J = a.jfree[n];
+                key = ((unsigned long long)__float_as_uint(J) << 32) | (unsigned)n;
+            } else {
+                key = (1ull << 63) | ((unsigned long long)(T - fh) << 32) | (unsigned)n;
+            }
+            if (a.costs) a.costs[n] = J;
+            if (a.first_hit) a.first_hit[n] = fh;
+            best = key < best ? key : best;
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(FULL, best, off);
+        best = o < best ? o : best;
+    }
+    __syncthreads();
+    if (lane == 0) red[warp] = best;
+    __syncthreads();
+    if (tid == 0 && a.best_key) {
+        unsigned long long k = red[0];
+        for (int w = 1; w < NW; ++w) k = red[w] < k ? red[w] : k;
+        atomicMin(a.best_key, k);
+    }
+}
+
+// ------------------------------------------------------------------ collide (warp items)
+// Barrier-free variant: each warp owns an item of 8 consecutive samples and
+// checks them against all points, pulling items from the same atomic queue.
+// The next horizon step's coefficient rows are prefetched (lanes 0..7 hold
+// one sample each) while the current step is checked; the live samples are
+// gathered into 8/4/2/1 slots by shuffles so that dead ones cost nothing.
+template <int CC>
+__device__ __forceinline__ unsigned warp_check(const float4* __restrict__ XY, const float4* __restrict__ V,
+                                               int npairs, float tau, float4 ca, float2 cb,
+                                               unsigned live, int L, int lane)
+{
+    unsigned long long A[CC], B[CC], NC[CC], D[CC], E[CC], NF[CC];
+    int src[CC];
+#pragma unroll
+    for (int k = 0; k < CC; ++k) {
+        src[k] = __fns(live, 0, (k < L ? k : 0) + 1);
+        const float a0 = __shfl_sync(FULL, ca.x, src[k]), a1 = __shfl_sync(FULL, ca.y, src[k]);
+        const float a2 = __shfl_sync(FULL, ca.z, src[k]), a3 = __shfl_sync(FULL, ca.w, src[k]);
+        const float b0 = __shfl_sync(FULL, cb.x, src[k]), b1 = __shfl_sync(FULL, cb.y, src[k]);
+        A[k] = pk(a0, a0); B[k] = pk(a1, a1); NC[k] = pk(a2, a2);
+        D[k] = pk(a3, a3); E[k] = pk(b0, b0); NF[k] = pk(b1, b1);
+    }
+    unsigned long long acc[CC];
+#pragma unroll
+    for (int k = 0; k < CC; ++k) acc[k] = 0ull;
+    const unsigned long long TT = pk(tau, tau);
+#pragma unroll 2
+    for (int q = lane; q < npairs; q += 32) {
+        const float4 xy = XY[q];
+        const float4 vv = V[q];
+        const unsigned long long PX = fma2(TT, pk(vv.x, vv.y), pk(xy.x, xy.y));
+        const unsigned long long PY = fma2(TT, pk(vv.z, vv.w), pk(xy.z, xy.w));
+#pragma unroll
+        for (int k = 0; k < CC; ++k) {
+            const unsigned long long xi = fma2(A[k], PX, fma2(B[k], PY, NC[k]));
+            const unsigned long long et = fma2(D[k], PX, fma2(E[k], PY, NF[k]));
+            acc[k] |= ~(xi | et);
+        }
+    }
+    unsigned hits = 0;
+#pragma unroll
+    for (int k = 0; k < CC; ++k) {
+        const bool inside = ((((unsigned)acc[k]) | (unsigned)(acc[k] >> 32)) >> 30) & 1u;
+        if (k < L && __any_sync(FULL, inside)) hits |= 1u << src[k];
+    }
+    return hits;
+}
+
+template <int NW>
+struct CollideWarpKernel {
+    static constexpr int THREADS = NW * 32;
+    static constexpr int fixed_bytes() { return NW * 8 + 64; }
+    static int smem_bytes(int M) { return ((M + 1) / 2) * 32 + fixed_bytes(); }
+};
+
+template <int NW, int MINB>
+__global__ void __launch_bounds__(NW * 32, MINB) collide_warp_kernel(const RolloutArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int npairs = (a.M + 1) / 2;
+    float4* XY = reinterpret_cast<float4*>(smem_raw);
+    float4* V = XY + npairs;
+    unsigned long long* red = reinterpret_cast<unsigned long long*>(V + npairs);
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const DevCfg& c = a.c;
+    const int T = a.T, N = a.N;
+    stage_points<NW * 32>(a, XY, V);
+    __syncthreads();
+
+    unsigned long long best = ~0ull;
+    const int nitems = (N + 7) / 8;
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = (int)atomicAdd(a.work, 1u);
+        item = __shfl_sync(FULL, item, 0);
+        if (item >= nitems) break;
+        const int n0 = item * 8;
+        const int cnt = min(8, N - n0);
+        const int n = n0 + lane;
+        const bool mine = lane < cnt;
+        unsigned live = (1u << cnt) - 1u;
+        int fh = -1;
+        float4 ca = make_float4(0.f, 0.f, 0.f, 0.f);
+        float2 cb = make_float2(0.f, 0.f);
+        if (mine) { ca = a.coefA[n]; cb = a.coefB[n]; }
+        for (int h = 0; h <= T; ++h) {
+            const float4 cur_a = ca;
+            const float2 cur_b = cb;
+            if (mine && h < T) {
+                const size_t idx = (size_t)(h + 1) * N + n;
+                ca = a.coefA[idx];
+                cb = a.coefB[idx];
+            }
+            const int L = __popc(live);
+            const float tau = (float)h * c.Ts;
+            unsigned hits;
+            if (L > 4)      hits = warp_check<8>(XY, V, npairs, tau, cur_a, cur_b, live, L, lane);
+            else if (L > 2) hits = warp_check<4>(XY, V, npairs, tau, cur_a, cur_b, live, L, lane);
+            else if (L > 1) hits = warp_check<2>(XY, V, npairs, tau, cur_a, cur_b, live, L, lane);
+            else            hits = warp_check<1>(XY, V, npairs, tau, cur_a, cur_b, live, L, lane);
+            if ((hits >> lane) & 1u) fh = h;
+            live &= ~hits;
+            if (live == 0u) break;
+        }
+        if (mine) {
+            float J = __int_as_float(0x7f800000);
+            unsigned long long key;
+            if (fh < 0) {
+                J = a.jfree[n];
+                key = ((unsigned long long)__float_as_uint(J) << 32) | (unsigned)n;
+            } else {
+                key = (1ull << 63) | ((unsigned long long)(T - fh) << 32) | (unsigned)n;
+            }
+            if (a.costs) a.costs[n] = J;
+            if (a.first_hit) a.first_hit[n] = fh;
+            best = key < best ? key : best;
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(FULL, best, off);
+        best = o < best ? o : best;
+    }
+    if (lane == 0) red[warp] = best;
+    __syncthreads();
+    if (tid == 0 && a.best_key) {
+        unsigned long long k = red[0];
+        for (int w = 1; w < NW; ++w) k = red[w] < k ? red[w] : k;
+        atomicMin(a.best_key, k);
+    }
+}
+
+// ------------------------------------------------------------------ launchers
+template <typename KernelFn>
+inline cudaError_t ensure_smem(KernelFn fn, int smem)
+{
     // opt in to large dynamic shared memory once per device (idempotent)
     static int configured[64] = {0};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (configured[dev] < smem) {
-        e = cudaFuncSetAttribute(rollout_kernel<W, NW, C>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (smem > 48 * 1024 && configured[dev] < smem) {
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         configured[dev] = smem;
     }
+    return cudaSuccess;
+}
+
+template <int W, int G, int NW>
+cudaError_t launch_traj(const RolloutArgs& a, cudaStream_t stream)
+{
+    using K = TrajKernel<W, G, NW>;
     const int grid = (a.N + K::B - 1) / K::B;
-    rollout_kernel<W, NW, C><<<grid, K::THREADS, smem, stream>>>(a);
+    traj_kernel<W, G, NW><<<grid, K::THREADS, 0, stream>>>(a);
     return cudaGetLastError();
+}
+
+template <int NW, int SBMAX, int MINB>
+cudaError_t launch_collide_block(const RolloutArgs& a, cudaStream_t stream)
+{
+    using K = CollideBlockKernel<NW, SBMAX>;
+    const int smem = K::smem_bytes(a.M);
+    cudaError_t e = ensure_smem(collide_block_kernel<NW, SBMAX, MINB>, smem);
+    if (e != cudaSuccess) return e;
+    const int grid = max(1, min((a.N + 7) / 8, a.grid_collide));
+    collide_block_kernel<NW, SBMAX, MINB><<<grid, K::THREADS, smem, stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <int NW, int SBMAX, int MINB>
+int collide_block_blocks_per_sm(int M)
+{
+    using K = CollideBlockKernel<NW, SBMAX>;
+    int nb = 0;
+    const int smem = K::smem_bytes(M);
+    if (ensure_smem(collide_block_kernel<NW, SBMAX, MINB>, smem) != cudaSuccess) return 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, collide_block_kernel<NW, SBMAX, MINB>,
+                                                  K::THREADS, smem);
+    return nb > 0 ? nb : 1;
+}
+
+template <int NW, int MINB>
+cudaError_t launch_collide_warp(const RolloutArgs& a, cudaStream_t stream)
+{
+    using K = CollideWarpKernel<NW>;
+    const int smem = K::smem_bytes(a.M);
+    cudaError_t e = ensure_smem(collide_warp_kernel<NW, MINB>, smem);
+    if (e != cudaSuccess) return e;
+    const int nwarps_needed = (a.N + 7) / 8;
+    const int grid = min((nwarps_needed + NW - 1) / NW, a.grid_collide);
+    collide_warp_kernel<NW, MINB><<<grid, K::THREADS, smem, stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <int NW, int MINB>
+int collide_warp_blocks_per_sm(int M)
+{
+    using K = CollideWarpKernel<NW>;
+    int nb = 0;
+    const int smem = K::smem_bytes(M);
+    if (ensure_smem(collide_warp_kernel<NW, MINB>, smem) != cudaSuccess) return 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, collide_warp_kernel<NW, MINB>, K::THREADS, smem);
+    return nb > 0 ? nb : 1;
 }
 
 }  // namespace npp

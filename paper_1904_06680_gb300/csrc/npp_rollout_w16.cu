@@ -1,18 +1,13 @@
-// Instantiation of the batched rollout kernel for the 8-16-16-2 network.
+// Trajectory kernel for the 8-16-16-2 network: variant 0 holds 2 hidden
+// units per lane (8 lanes per sample), variant 1 holds 4 (4 lanes); both
+// compute identical values.
 #include "npp_rollout.cuh"
 
 namespace npp {
 
-using KW16 = RolloutKernel<16, 8, 8>;
-
-cudaError_t launch_rollout_w16(const RolloutArgs& a, cudaStream_t s, int* smem_needed)
+cudaError_t launch_traj_w16(const RolloutArgs& a, cudaStream_t s, int variant)
 {
-    return launch_rollout<16, 8, 8>(a, s, smem_needed);
-}
-
-int rollout_max_points_w16(int smem_limit)
-{
-    return (smem_limit - KW16::fixed_bytes()) / 16;
+    return variant ? launch_traj<16, 4, 8>(a, s) : launch_traj<16, 8, 8>(a, s);
 }
 
 }  // namespace npp

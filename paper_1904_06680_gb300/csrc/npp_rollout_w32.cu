@@ -1,18 +1,13 @@
-// Instantiation of the batched rollout kernel for the 8-32-32-2 network.
+// Trajectory kernel for the 8-32-32-2 network: variant 0 holds 2 hidden
+// units per lane (16 lanes per sample), variant 1 holds 4 (8 lanes); both
+// compute identical values.
 #include "npp_rollout.cuh"
 
 namespace npp {
 
-using KW32 = RolloutKernel<32, 8, 8>;
-
-cudaError_t launch_rollout_w32(const RolloutArgs& a, cudaStream_t s, int* smem_needed)
+cudaError_t launch_traj_w32(const RolloutArgs& a, cudaStream_t s, int variant)
 {
-    return launch_rollout<32, 8, 8>(a, s, smem_needed);
-}
-
-int rollout_max_points_w32(int smem_limit)
-{
-    return (smem_limit - KW32::fixed_bytes()) / 16;
+    return variant ? launch_traj<32, 8, 8>(a, s) : launch_traj<32, 16, 8>(a, s);
 }
 
 }  // namespace npp

@@ -1,18 +1,13 @@
-// Instantiation of the batched rollout kernel for the 8-64-64-2 network.
+// Trajectory kernel for the 8-64-64-2 network: variant 0 holds 2 hidden
+// units per lane (32 lanes per sample), variant 1 holds 4 (16 lanes); both
+// compute identical values.
 #include "npp_rollout.cuh"
 
 namespace npp {
 
-using KW64 = RolloutKernel<64, 8, 4>;
-
-cudaError_t launch_rollout_w64(const RolloutArgs& a, cudaStream_t s, int* smem_needed)
+cudaError_t launch_traj_w64(const RolloutArgs& a, cudaStream_t s, int variant)
 {
-    return launch_rollout<64, 8, 4>(a, s, smem_needed);
-}
-
-int rollout_max_points_w64(int smem_limit)
-{
-    return (smem_limit - KW64::fixed_bytes()) / 16;
+    return variant ? launch_traj<64, 16, 8>(a, s) : launch_traj<64, 32, 8>(a, s);
 }
 
 }  // namespace npp

@@ -53,7 +53,7 @@ class npp_outputs(C.Structure):
 
 EXPORTS = ("npp_create", "npp_destroy", "npp_last_error", "npp_n_theta", "npp_plan_step",
            "npp_plan_step_host", "npp_rollout_params", "npp_sample_params", "npp_set_timing",
-           "npp_last_timing")
+           "npp_last_timing", "npp_set_option")
 
 _lib = None
 
@@ -80,7 +80,8 @@ def lib():
                                          I32, P, P, P, P, P]
         L.npp_sample_params.argtypes = [U64, U32, U32, I32, I32, I32, P, P]
         L.npp_set_timing.argtypes = [P, I32]
-        L.npp_last_timing.argtypes = [P, C.POINTER(C.c_float), C.POINTER(C.c_float)]
+        L.npp_set_option.argtypes = [P, C.c_char_p, I32]
+        L.npp_last_timing.argtypes = [P, C.POINTER(C.c_float), I32]
         for name in EXPORTS:
             if name not in ("npp_last_error", "npp_n_theta"):
                 getattr(L, name).restype = C.c_int
@@ -171,15 +172,20 @@ def npp_sample_params(seed, t_index, stream_id, n0, K, n_theta, out, stream=None
                                           int(n_theta), _ptr(out), _stream(stream)))
 
 
+def npp_set_option(h, name: str, value: int):
+    return _check(lib().npp_set_option(h, name.encode(), int(value)), h)
+
+
 def npp_set_timing(h, enable: bool):
     return _check(lib().npp_set_timing(h, 1 if enable else 0), h)
 
 
 def npp_last_timing(h):
-    """(rollout kernel ms, whole plan step ms) of the last timed call."""
-    a, b = C.c_float(), C.c_float()
-    _check(lib().npp_last_timing(h, C.byref(a), C.byref(b)), h)
-    return a.value, b.value
+    """Stage times of the last timed call in ms: dict with keys traj,
+    collide, epilogue, total."""
+    t = (C.c_float * 4)()
+    _check(lib().npp_last_timing(h, t, 4), h)
+    return dict(traj=t[0], collide=t[1], epilogue=t[2], total=t[3])
 
 
 # ------------------------------------------------------------------ convenience

@@ -156,7 +156,9 @@ def winner_check(g, o_cost, o_fh):
     gfh = g["first_hit"]
     agree = (gfh == o_fh)
     free = agree & (gfh < 0)
-    agree_cost = free & (np.abs(gc - o_cost) <= COST_RTOL * np.maximum(1.0, np.abs(o_cost)))
+    with np.errstate(invalid="ignore"):
+        diff = np.where(free, np.abs(gc - o_cost), np.inf)
+    agree_cost = free & (diff <= COST_RTOL * np.maximum(1.0, np.abs(o_cost)))
     res = dict(agree_frac=float(agree.mean()), n_free=int((gfh < 0).sum()))
     if not np.any(o_fh < 0):
         res["infeasible"] = True

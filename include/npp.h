@@ -171,6 +171,30 @@ npp_status npp_sample_params(uint64_t seed, uint32_t t_index, uint32_t stream_id
                              int32_t n0, int32_t K, int32_t n_theta, float* out_dev,
                              void* stream);
 
+/* The plan step of npp_plan_step for callers that cannot allocate device
+ * memory -- for instance a plugin whose host application owns every device
+ * allocation, or a real-time control loop that must not call cudaMalloc once
+ * it runs, because cudaMalloc may synchronise the device and take unbounded
+ * time.  There is no counterpart in the paper; it is a deployment variant.
+ *
+ * No handle: the constants come from cfg (its max_* fields are ignored), the
+ * workspace is one fixed file-scope device array of about 33 MB that every
+ * GPU loading this part of the library holds until the process exits.
+ * Limits: 1 <= N <= 16384 and N * (T + 1) <= 688128 sample-steps (for
+ * example N = 16384 with T <= 41); larger requests return NPP_INVALID_ARG
+ * with a message in npp_last_error(NULL).  Inputs and outputs are as in
+ * npp_plan_step (device pointers; out->best required), and the launch is
+ * asynchronous on `stream` on the current device.  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress), so make
+ * that first call before any stream capture.  All calls share the array and
+ * it keeps the last call's contents; every call resets what must start at
+ * zero, but calls that overlap on the GPU (other streams or threads) race.
+ * Nothing here calls cudaMalloc, cudaFree or an allocating library routine. */
+npp_status npp_plan_step_noalloc(const npp_config* cfg, const npp_state* state,
+                                 const npp_goal* goal, const float* obs_dev, int32_t M,
+                                 int32_t N, int32_t T, uint64_t seed, uint32_t t_index,
+                                 const float* warm_dev, const npp_outputs* out, void* stream);
+
 /* Launch options that do not change any result (they choose among kernels
  * computing identical values).  "collide_variant" in -1..2: 0 the
  * block-balanced collision kernel with 16 warps and one block per SM, 1 the

@@ -146,6 +146,18 @@ __global__ void sample_params_kernel(SamplerKey key, int n0, int K, int nt, floa
 
 }  // namespace
 
+namespace npp {
+// Message for npp_last_error(NULL) from entry points without a handle.
+void set_global_error(const char* msg) { g_err = msg; }
+
+// The winner epilogue for callers outside this file (one block of 256).
+cudaError_t launch_epilogue(const EpilogueArgs& e, cudaStream_t s)
+{
+    epilogue_kernel<<<1, 256, 0, s>>>(e);
+    return cudaGetLastError();
+}
+}  // namespace npp
+
 // ------------------------------------------------------------------ helpers
 static cudaError_t launch_traj(const npp_handle* h, const RolloutArgs& a, cudaStream_t s)
 {

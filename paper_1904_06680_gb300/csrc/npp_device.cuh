@@ -162,5 +162,7 @@ cudaError_t launch_traj_w64(const RolloutArgs& a, cudaStream_t s, int variant);
 cudaError_t launch_collide_resident(const RolloutArgs& a, cudaStream_t s, int variant);
 int collide_resident_blocks_per_sm(int M, int variant);
 int collide_max_points(int smem_limit);
+cudaError_t launch_epilogue(const EpilogueArgs& e, cudaStream_t s);
+void set_global_error(const char* msg);
 
 }  // namespace npp

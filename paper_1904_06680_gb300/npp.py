@@ -53,7 +53,7 @@ class npp_outputs(C.Structure):
 
 EXPORTS = ("npp_create", "npp_destroy", "npp_last_error", "npp_n_theta", "npp_plan_step",
            "npp_plan_step_host", "npp_rollout_params", "npp_sample_params", "npp_set_timing",
-           "npp_last_timing", "npp_set_option")
+           "npp_last_timing", "npp_set_option", "npp_plan_step_noalloc")
 
 _lib = None
 
@@ -81,6 +81,9 @@ def lib():
         L.npp_sample_params.argtypes = [U64, U32, U32, I32, I32, I32, P, P]
         L.npp_set_timing.argtypes = [P, I32]
         L.npp_set_option.argtypes = [P, C.c_char_p, I32]
+        L.npp_plan_step_noalloc.argtypes = [C.POINTER(npp_config), C.POINTER(npp_state),
+                                            C.POINTER(npp_goal), P, I32, I32, I32, U64, U32, P,
+                                            C.POINTER(npp_outputs), P]
         L.npp_last_timing.argtypes = [P, C.POINTER(C.c_float), I32]
         for name in EXPORTS:
             if name not in ("npp_last_error", "npp_n_theta"):
@@ -150,6 +153,17 @@ def npp_plan_step(h, state, goal, obs, M, N, T, seed, t_index, warm, out: npp_ou
     return _check(lib().npp_plan_step(h, C.byref(make_state(state)), C.byref(make_goal(goal)),
                                       _ptr(obs), int(M), int(N), int(T), int(seed), int(t_index),
                                       _ptr(warm), C.byref(out), _stream(stream)), h)
+
+
+def npp_plan_step_noalloc(cfg: npp_config, state, goal, obs, M, N, T, seed, t_index, warm,
+                          out: npp_outputs, stream=None):
+    """Plan step that allocates no device memory (fixed static workspace);
+    for callers that cannot call cudaMalloc.  obs / warm: CUDA tensors or
+    None; out: npp_outputs of device pointers."""
+    return _check(lib().npp_plan_step_noalloc(C.byref(cfg), C.byref(make_state(state)),
+                                              C.byref(make_goal(goal)), _ptr(obs), int(M), int(N),
+                                              int(T), int(seed), int(t_index), _ptr(warm),
+                                              C.byref(out), _stream(stream)))
 
 
 def npp_plan_step_host(h, state, goal, obs, M, N, T, seed, t_index, warm, out: npp_outputs):

@@ -15,10 +15,11 @@ value   = N * T * K / (sum of the K plan steps' device time), inputs resident
 e2e     = the same through the host-buffer entry point (host->device copy of
           the obstacles and warm start, plan, device->host copy of the
           result, synchronise), wall clock;
-roofline = the rollout kernel: algorithmic FP32 instructions (6 per
-          point-check of a live sample, W^2 + 10 W + 30 per live control
-          step) over its event-timed duration, against the FP32 issue peak
-          152 SMs x 128 lanes x 2.07 GHz.
+roofline = the collision kernel (the dominant one): algorithmic FP32 FMAs
+          (4 per point-check of a live sample: two rows of the rotated
+          inequality test) over its event-timed duration, against the FMA
+          peak 152 SMs x 128 lanes x 2.07 GHz; `traffic` comes from the
+          committed ncu summary while the kernel sources are unchanged.
 
 `--impl reference` times the CPU oracle on the host cores on the same
 workload with a bounded number of samples per step.
@@ -128,20 +129,48 @@ def course_setup(seed):
     return sc
 
 
-def algorithmic_instr(first_hit, T, M, W):
-    """FP32 instructions the rollout needs, split by kernel: the collision
-    check costs 6 per point-check of a live sample (4 FMA + 2 min/max); the
-    control step W^2 + 10 W + 30 per live step (MLP multiply-adds plus
-    features, controls and the Euler update)."""
+def algorithmic_work(first_hit, T, M, W):
+    """Algorithmic FP32 FMAs, split by kernel: the collision check needs 4
+    per point-check of a live sample (two rows of the rotated inequality
+    test); the control step needs W^2 + 10 W multiply-adds per live step
+    (the MLP).  Also returns the live point-checks."""
     fh = np.asarray(first_hit)
-    checks = np.where(fh < 0, T + 1, fh + 1).sum()
-    ctrl = np.where(fh < 0, T, fh).sum()
-    return float(checks) * 6.0 * M, float(ctrl) * (W * W + 10 * W + 30)
+    checks = float(np.where(fh < 0, T + 1, fh + 1).sum()) * M
+    ctrl = float(np.where(fh < 0, T, fh).sum())
+    return 4.0 * checks, ctrl * (W * W + 10 * W), checks
+
+
+def kernel_sources_hash():
+    """Hash of the CUDA sources: profile counters apply only to this code."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_1904_06680_gb300", "csrc")
+    h = hashlib.sha1()
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(f.encode())
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from profiles/traffic.json, or None
+    when the sources changed since that capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    if rec.get("kernel_sources") != kernel_sources_hash():
+        return None
+    per = {k.replace(" ", ""): v for k, v in rec.get("bytes_per_launch", {}).items()}
+    return per.get(kernel.replace(" ", ""))
 
 
 def cpu_baseline(sc, state, goal, obs, T, target_cpu_s=15.0):
     """Oracle (as it stands) on the host cores: a bounded sample of the first
-    plan step's samples, every one over the full horizon."""
+    plan step's workload (sample indices 0..K-1; beyond N they are further
+    Philox draws of the same distribution), every one over the full
+    horizon, about `target_cpu_s` seconds of single-core work."""
     from oracle import oracle as orc
     p = sc["preset"]
     cores = os.cpu_count() or 1
@@ -152,16 +181,16 @@ def cpu_baseline(sc, state, goal, obs, T, target_cpu_s=15.0):
     orc.rollout_samples(p, sc["seed"], 0, probe, z0, state[4:6], goal_ev, obs_ev, T, n_threads=1,
                         record=False)
     per_sample = max(time.perf_counter() - t0, 1e-6) / len(probe)
-    K = int(min(sc["N"], max(256, target_cpu_s / per_sample)))
+    K = int(min(8 * sc["N"], max(256, target_cpu_s / per_sample)))
     idx = np.arange(K, dtype=np.int32)
     t0 = time.perf_counter()
     orc.rollout_samples(p, sc["seed"], 0, idx, z0, state[4:6], goal_ev, obs_ev, T, n_threads=cores,
                         record=False)
     wall = time.perf_counter() - t0
     return {"value": K * T / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "first plan step of the course scene: samples 0..%d of %d over the full "
-                      "horizon T=%d, M=%d points, FP64 C with OpenMP (%.1f s wall)"
-                      % (K - 1, sc["N"], T, obs.shape[0], wall)}
+            "sample": "first plan step of the course scene: %d samples (the step draws %d) over "
+                      "the full horizon T=%d, M=%d points, FP64 C with OpenMP (%.1f s wall)"
+                      % (K, sc["N"], T, obs.shape[0], wall)}
 
 
 def run_npp(args):
@@ -191,8 +220,8 @@ def run_npp(args):
         mission = closed_loop.Mission(sc["waypoints"], inputs.EPS)
         warm_dev = None
         warm_host = None
-        out = dict(step_ms=[], collide_ms=[], traj_ms=[], wall_ms=[], instr_c=0.0, instr_t=0.0,
-                   free=[], best_cost=[])
+        out = dict(step_ms=[], collide_ms=[], traj_ms=[], wall_ms=[], fma_c=0.0, fma_t=0.0,
+                   checks=0.0, free=[], best_cost=[])
         if host_api:
             obs_pin = torch.empty(M, 4, dtype=torch.float32).pin_memory()
             hb = npp.npp_best()
@@ -237,9 +266,10 @@ def run_npp(args):
                     out["step_ms"].append(tm["total"])
                     out["collide_ms"].append(tm["collide"])
                     out["traj_ms"].append(tm["traj"])
-                    ic, it = algorithmic_instr(fh, T, M, W)
-                    out["instr_c"] += ic
-                    out["instr_t"] += it
+                    fc, ft, ch = algorithmic_work(fh, T, M, W)
+                    out["fma_c"] += fc
+                    out["fma_t"] += ft
+                    out["checks"] += ch
                     out["free"].append(float(np.mean(fh < 0)))
                     out["best_cost"].append(float(b[2:3].view(torch.float32).item()))
             state = closed_loop.plant_step(p, state, a)
@@ -248,14 +278,15 @@ def run_npp(args):
         out["waypoints_reached"] = mission.k
         return out
 
-    # warm-up (untimed) then K timed steps of the device path
-    closed_loop_pass(False, Wu, record=False)
+    # warm-up (untimed) then K timed steps of the device path; the clock
+    # sampler starts before the warm-up so that it is running by the timed steps
     clocks = Clocks(local)
+    clocks.start()
+    closed_loop_pass(False, Wu, record=False)
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize()
-    clocks.start()
     res = closed_loop_pass(False, K, record=True)
     torch.cuda.synchronize()
     ck = clocks.stop()
@@ -285,15 +316,19 @@ def run_npp(args):
             e2e["value"] = world * N * T * K / float(ev[0])
     value = world * N * T * K / (total_ms / 1e3)
     peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6
-    ips_c = res["instr_c"] / (collide_ms / 1e3)
-    ips_t = res["instr_t"] / (traj_ms / 1e3)
-    roofline = {"bound": "alu", "kernel": "collide_kernel<8,64,8>",
-                "achieved": ips_c / 1e12, "peak": peak / 1e12,
-                "unit": "T FP32-instr/s", "frac": ips_c / peak, "traffic": None,
-                "peak_basis": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz",
+    fps_c = res["fma_c"] / (collide_ms / 1e3)
+    fps_t = res["fma_t"] / (traj_ms / 1e3)
+    kname = "collide_warp_kernel<8,2>" if N >= 8192 else "collide_block_kernel<16,128,1>"
+    traffic = profiled_traffic(kname)
+    roofline = {"bound": "alu", "kernel": kname,
+                "achieved": fps_c / 1e12, "peak": peak / 1e12, "unit": "T FP32-FMA/s",
+                "frac": fps_c / peak,
+                "traffic": None if traffic is None else traffic,
+                "peak_basis": "derived: 152 SMs x 128 FP32 FMA lanes x 2070 MHz",
                 "kernel_ms_per_step": collide_ms / K,
+                "point_checks_per_s": res["checks"] / (collide_ms / 1e3),
                 "other": {"traj_kernel<32,16,8>": {"ms_per_step": traj_ms / K,
-                                                  "achieved": ips_t / 1e12, "frac": ips_t / peak}}}
+                                                  "achieved": fps_t / 1e12, "frac": fps_t / peak}}}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": Wu, "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",

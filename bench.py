@@ -318,7 +318,8 @@ def run_npp(args):
     peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6
     fps_c = res["fma_c"] / (collide_ms / 1e3)
     fps_t = res["fma_t"] / (traj_ms / 1e3)
-    kname = "collide_warp_kernel<8,2>" if N >= 8192 else "collide_block_kernel<16,128,1>"
+    kname = ("collide_slice_kernel<4,4>" if N <= 8192 else
+             "collide_slice_kernel<2,8>" if N <= 32768 else "collide_warp_kernel<8,2>")
     traffic = profiled_traffic(kname)
     roofline = {"bound": "alu", "kernel": kname,
                 "achieved": fps_c / 1e12, "peak": peak / 1e12, "unit": "T FP32-FMA/s",

@@ -199,7 +199,8 @@ npp_status npp_plan_step_noalloc(const npp_config* cfg, const npp_state* state,
  * computing identical values).  "collide_variant" in -1..2: 0 the
  * block-balanced collision kernel with 16 warps and one block per SM, 1 the
  * same with 8 warps and two blocks per SM, 2 warp-owned items of 8 samples,
- * -1 (default) chooses by the number of samples.
+ * 3 / 4 items of 8 samples checked by 4 / 2 warps each taking a slice of the
+ * points, -1 (default) chooses by the number of samples.
  * "traj_variant" 0 or 1: the trajectory kernel holds 2 (0, default) or 4 (1)
  * hidden units per lane.
  * Returns NPP_INVALID_ARG for an unknown name or value. */

@@ -174,9 +174,11 @@ static npp_status run_rollout(npp_handle* h, RolloutArgs& a, cudaStream_t s)
     a.coefA = h->d_coefA;
     a.coefB = h->d_coefB;
     a.work = h->d_work;
-    // automatic choice: the block-balanced kernel spreads few samples over
-    // all SMs; with many samples the warp-item kernel keeps more warps busy
-    const int v = h->collide_variant >= 0 ? h->collide_variant : (a.N < 8192 ? 0 : 2);
+    // automatic choice (measured on GB300, course workload): few samples ->
+    // items checked by 4 warps on point slices; medium -> 2 warps; many
+    // samples -> one warp per item keeps enough items in flight
+    const int v = h->collide_variant >= 0 ? h->collide_variant
+                : (a.N <= 8192 ? 3 : (a.N <= 32768 ? 4 : 2));
     if (h->occ_M != a.M || h->collide_active != v) {
         h->occ_blocks = collide_resident_blocks_per_sm(a.M, v);
         h->occ_M = a.M;
@@ -473,7 +475,7 @@ npp_status npp_set_option(npp_handle* h, const char* name, int32_t value)
 {
     if (!h || !name) return fail(h, NPP_INVALID_ARG, "handle and name must not be NULL");
     if (std::strcmp(name, "collide_variant") == 0) {
-        if (value < -1 || value > 2) return fail(h, NPP_INVALID_ARG, "collide_variant is -1..2");
+        if (value < -1 || value > 4) return fail(h, NPP_INVALID_ARG, "collide_variant is -1..4");
         h->collide_variant = value;
         h->occ_M = -1;
         return NPP_OK;

@@ -13,7 +13,9 @@ cudaError_t launch_collide_resident(const RolloutArgs& a, cudaStream_t s, int va
     switch (variant) {
     case 0: return launch_collide_block<16, 128, 1>(a, s);
     case 1: return launch_collide_block<8, 64, 2>(a, s);
-    default: return launch_collide_warp<8, 2>(a, s);
+    case 2: return launch_collide_warp<8, 2>(a, s);
+    case 3: return launch_collide_slice<4, 4>(a, s);
+    default: return launch_collide_slice<2, 8>(a, s);
     }
 }
 
@@ -22,7 +24,9 @@ int collide_resident_blocks_per_sm(int M, int variant)
     switch (variant) {
     case 0: return collide_block_blocks_per_sm<16, 128, 1>(M);
     case 1: return collide_block_blocks_per_sm<8, 64, 2>(M);
-    default: return collide_warp_blocks_per_sm<8, 2>(M);
+    case 2: return collide_warp_blocks_per_sm<8, 2>(M);
+    case 3: return collide_slice_blocks_per_sm<4, 4>(M);
+    default: return collide_slice_blocks_per_sm<2, 8>(M);
     }
 }
 

@@ -156,7 +156,7 @@ extern "C" npp_status npp_plan_step_noalloc(const npp_config* cfg, const npp_sta
     a.work = reinterpret_cast<unsigned*>(base + 8);
     int sm_count = 1;
     cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev);
-    const int variant = N < 8192 ? 0 : 2;
+    const int variant = N <= 8192 ? 3 : 4;
     a.grid_collide = (sm_count > 0 ? sm_count : 1) * collide_resident_blocks_per_sm(M, variant);
 
     // the best key starts at all ones, the work counter at zero

@@ -520,21 +520,23 @@ __global__ void __launch_bounds__(NW * 32, MINB) collide_block_kernel(const Roll
 // The next horizon step's coefficient rows are prefetched (lanes 0..7 hold
 // one sample each) while the current step is checked; the live samples are
 // gathered into 8/4/2/1 slots by shuffles so that dead ones cost nothing.
+// The live samples' coefficient rows sit in a warp-private shared slot array
+// (slot r = the r-th live sample, written by its owner lane); every lane
+// reads the CC slots with broadcast loads.  Returns the hit bits in slot
+// order.
 template <int CC>
-__device__ __forceinline__ unsigned warp_check(const float4* __restrict__ XY, const float4* __restrict__ V,
-                                               int npairs, float tau, float4 ca, float2 cb,
-                                               unsigned live, int L, int lane)
+__device__ __forceinline__ unsigned check_slots(const float4* __restrict__ XY, const float4* __restrict__ V,
+                                                int npairs, float tau, const float4* __restrict__ sA,
+                                                const float2* __restrict__ sB, int L, int lane)
 {
     unsigned long long A[CC], B[CC], NC[CC], D[CC], E[CC], NF[CC];
-    int src[CC];
 #pragma unroll
     for (int k = 0; k < CC; ++k) {
-        src[k] = __fns(live, 0, (k < L ? k : 0) + 1);
-        const float a0 = __shfl_sync(FULL, ca.x, src[k]), a1 = __shfl_sync(FULL, ca.y, src[k]);
-        const float a2 = __shfl_sync(FULL, ca.z, src[k]), a3 = __shfl_sync(FULL, ca.w, src[k]);
-        const float b0 = __shfl_sync(FULL, cb.x, src[k]), b1 = __shfl_sync(FULL, cb.y, src[k]);
-        A[k] = pk(a0, a0); B[k] = pk(a1, a1); NC[k] = pk(a2, a2);
-        D[k] = pk(a3, a3); E[k] = pk(b0, b0); NF[k] = pk(b1, b1);
+        const int slot = k < L ? k : 0;
+        const float4 qa = sA[slot];
+        const float2 qb = sB[slot];
+        A[k] = pk(qa.x, qa.x); B[k] = pk(qa.y, qa.y); NC[k] = pk(qa.z, qa.z);
+        D[k] = pk(qa.w, qa.w); E[k] = pk(qb.x, qb.x); NF[k] = pk(qb.y, qb.y);
     }
     unsigned long long acc[CC];
 #pragma unroll
@@ -553,19 +555,40 @@ __device__ __forceinline__ unsigned warp_check(const float4* __restrict__ XY, co
             acc[k] |= ~(xi | et);
         }
     }
-    unsigned hits = 0;
+    unsigned bits = 0;
 #pragma unroll
     for (int k = 0; k < CC; ++k) {
         const bool inside = ((((unsigned)acc[k]) | (unsigned)(acc[k] >> 32)) >> 30) & 1u;
-        if (k < L && __any_sync(FULL, inside)) hits |= 1u << src[k];
+        if (k < L && __any_sync(FULL, inside)) bits |= 1u << k;
     }
-    return hits;
+    return bits;
+}
+
+// One step of an 8-sample item for one warp: the owner lanes (lane < 8 with
+// their bit in `live`) stage their coefficient rows, the warp checks the
+// points [XY, XY + npairs), and the hits come back as a lane mask.
+__device__ __forceinline__ unsigned warp_step(const float4* XY, const float4* V, int npairs, float tau,
+                                              float4 ca, float2 cb, unsigned live, float4* sA,
+                                              float2* sB, int lane)
+{
+    const bool owner = lane < 8 && ((live >> lane) & 1u);
+    const int rank = __popc(live & ((1u << lane) - 1u));
+    if (owner) { sA[rank] = ca; sB[rank] = cb; }
+    __syncwarp();
+    const int L = __popc(live);
+    unsigned bits;
+    if (L > 4)      bits = check_slots<8>(XY, V, npairs, tau, sA, sB, L, lane);
+    else if (L > 2) bits = check_slots<4>(XY, V, npairs, tau, sA, sB, L, lane);
+    else if (L > 1) bits = check_slots<2>(XY, V, npairs, tau, sA, sB, L, lane);
+    else            bits = check_slots<1>(XY, V, npairs, tau, sA, sB, L, lane);
+    __syncwarp();
+    return __ballot_sync(FULL, owner && ((bits >> rank) & 1u));
 }
 
 template <int NW>
 struct CollideWarpKernel {
     static constexpr int THREADS = NW * 32;
-    static constexpr int fixed_bytes() { return NW * 8 + 64; }
+    static constexpr int fixed_bytes() { return NW * 8 * 24 + NW * 8 + 64; }
     static int smem_bytes(int M) { return ((M + 1) / 2) * 32 + fixed_bytes(); }
 };
 
@@ -576,12 +599,17 @@ __global__ void __launch_bounds__(NW * 32, MINB) collide_warp_kernel(const Rollo
     const int npairs = (a.M + 1) / 2;
     float4* XY = reinterpret_cast<float4*>(smem_raw);
     float4* V = XY + npairs;
-    unsigned long long* red = reinterpret_cast<unsigned long long*>(V + npairs);
+    float4* slotA = V + npairs;                                  // [NW][8]
+    float2* slotB = reinterpret_cast<float2*>(slotA + NW * 8);   // [NW][8]
+    unsigned long long* red = reinterpret_cast<unsigned long long*>(slotB + NW * 8);
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     const DevCfg& c = a.c;
     const int T = a.T, N = a.N;
     stage_points<NW * 32>(a, XY, V);
+    __syncthreads();
+    float4* sA = slotA + warp * 8;
+    float2* sB = slotB + warp * 8;
     __syncthreads();
 
     unsigned long long best = ~0ull;
@@ -608,13 +636,8 @@ __global__ void __launch_bounds__(NW * 32, MINB) collide_warp_kernel(const Rollo
                 ca = a.coefA[idx];
                 cb = a.coefB[idx];
             }
-            const int L = __popc(live);
-            const float tau = (float)h * c.Ts;
-            unsigned hits;
-            if (L > 4)      hits = warp_check<8>(XY, V, npairs, tau, cur_a, cur_b, live, L, lane);
-            else if (L > 2) hits = warp_check<4>(XY, V, npairs, tau, cur_a, cur_b, live, L, lane);
-            else if (L > 1) hits = warp_check<2>(XY, V, npairs, tau, cur_a, cur_b, live, L, lane);
-            else            hits = warp_check<1>(XY, V, npairs, tau, cur_a, cur_b, live, L, lane);
+            const unsigned hits = warp_step(XY, V, npairs, (float)h * c.Ts, cur_a, cur_b, live,
+                                            sA, sB, lane);
             if ((hits >> lane) & 1u) fh = h;
             live &= ~hits;
             if (live == 0u) break;
@@ -643,6 +666,109 @@ __global__ void __launch_bounds__(NW * 32, MINB) collide_warp_kernel(const Rollo
     if (tid == 0 && a.best_key) {
         unsigned long long k = red[0];
         for (int w = 1; w < NW; ++w) k = red[w] < k ? red[w] : k;
+        atomicMin(a.best_key, k);
+    }
+}
+
+// ------------------------------------------------------------------ collide (sliced items)
+// An item of 8 samples is checked by a block of S warps, warp s against the
+// s-th slice of the points.  The warps run through h independently; they
+// share, per sample, the earliest step at which any slice found a collision
+// (dead_at, shared-memory atomicMin) and stop checking a sample at steps at
+// or after it.  The item's first collision per sample is the minimum over
+// the slices, identical to checking all points at once.
+template <int S>
+struct CollideSliceKernel {
+    static constexpr int THREADS = S * 32;
+    static constexpr int fixed_bytes() { return S * 8 * 24 + 8 * 4 + 16 + S * 8 + 64; }
+    static int smem_bytes(int M) { return ((M + 1) / 2) * 32 + fixed_bytes(); }
+};
+
+template <int S, int MINB>
+__global__ void __launch_bounds__(S * 32, MINB) collide_slice_kernel(const RolloutArgs a)
+{
+    using K = CollideSliceKernel<S>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int npairs = (a.M + 1) / 2;
+    float4* XY = reinterpret_cast<float4*>(smem_raw);
+    float4* V = XY + npairs;
+    float4* slotA = V + npairs;                                  // [S][8]
+    float2* slotB = reinterpret_cast<float2*>(slotA + S * 8);    // [S][8]
+    int* dead_at = reinterpret_cast<int*>(slotB + S * 8);        // [8]
+    int* qslot = dead_at + 8;
+    unsigned long long* red = reinterpret_cast<unsigned long long*>(qslot + 4);
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const DevCfg& c = a.c;
+    const int T = a.T, N = a.N;
+    stage_points<K::THREADS>(a, XY, V);
+    const int per = (npairs + S - 1) / S;
+    const int q0 = min(npairs, warp * per), q1 = min(npairs, q0 + per);
+    const int nslice = q1 - q0;
+    float4* sA = slotA + warp * 8;
+    float2* sB = slotB + warp * 8;
+
+    unsigned long long best = ~0ull;
+    const int nitems = (N + 7) / 8;
+    for (;;) {
+        if (tid < 8) dead_at[tid] = T + 1;
+        if (tid == 0) *qslot = (int)atomicAdd(a.work, 1u);
+        __syncthreads();
+        const int item = *qslot;
+        if (item >= nitems) break;
+        const int n0 = item * 8;
+        const int cnt = min(8, N - n0);
+        const int n = n0 + lane;
+        const bool mine = lane < cnt;
+        unsigned live = (1u << cnt) - 1u;
+        float4 ca = make_float4(0.f, 0.f, 0.f, 0.f);
+        float2 cb = make_float2(0.f, 0.f);
+        if (mine) { ca = a.coefA[n]; cb = a.coefB[n]; }
+        for (int h = 0; h <= T; ++h) {
+            const float4 cur_a = ca;
+            const float2 cur_b = cb;
+            if (mine && h < T) {
+                const size_t idx = (size_t)(h + 1) * N + n;
+                ca = a.coefA[idx];
+                cb = a.coefB[idx];
+            }
+            // drop samples another slice already found colliding at or before h
+            const unsigned gone = __ballot_sync(FULL, lane < 8 && *(volatile int*)&dead_at[lane] <= h);
+            live &= ~gone;
+            if (live == 0u || nslice <= 0) break;
+            const unsigned hits = warp_step(XY + q0, V + q0, nslice, (float)h * c.Ts, cur_a, cur_b,
+                                            live, sA, sB, lane);
+            if ((hits >> lane) & 1u) atomicMin(&dead_at[lane], h);
+            live &= ~hits;
+        }
+        __syncthreads();
+        if (warp == 0 && mine) {
+            const int d = dead_at[lane];
+            const int fh = d <= T ? d : -1;
+            float J = __int_as_float(0x7f800000);
+            unsigned long long key;
+            if (fh < 0) {
+                J = a.jfree[n];
+                key = ((unsigned long long)__float_as_uint(J) << 32) | (unsigned)n;
+            } else {
+                key = (1ull << 63) | ((unsigned long long)(T - fh) << 32) | (unsigned)n;
+            }
+            if (a.costs) a.costs[n] = J;
+            if (a.first_hit) a.first_hit[n] = fh;
+            best = key < best ? key : best;
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(FULL, best, off);
+        best = o < best ? o : best;
+    }
+    if (lane == 0) red[warp] = best;
+    __syncthreads();
+    if (tid == 0 && a.best_key) {
+        unsigned long long k = red[0];
+        for (int w = 1; w < S; ++w) k = red[w] < k ? red[w] : k;
         atomicMin(a.best_key, k);
     }
 }
@@ -719,6 +845,29 @@ int collide_warp_blocks_per_sm(int M)
     const int smem = K::smem_bytes(M);
     if (ensure_smem(collide_warp_kernel<NW, MINB>, smem) != cudaSuccess) return 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, collide_warp_kernel<NW, MINB>, K::THREADS, smem);
+    return nb > 0 ? nb : 1;
+}
+
+template <int S, int MINB>
+cudaError_t launch_collide_slice(const RolloutArgs& a, cudaStream_t stream)
+{
+    using K = CollideSliceKernel<S>;
+    const int smem = K::smem_bytes(a.M);
+    cudaError_t e = ensure_smem(collide_slice_kernel<S, MINB>, smem);
+    if (e != cudaSuccess) return e;
+    const int grid = max(1, min((a.N + 7) / 8, a.grid_collide));
+    collide_slice_kernel<S, MINB><<<grid, K::THREADS, smem, stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <int S, int MINB>
+int collide_slice_blocks_per_sm(int M)
+{
+    using K = CollideSliceKernel<S>;
+    int nb = 0;
+    const int smem = K::smem_bytes(M);
+    if (ensure_smem(collide_slice_kernel<S, MINB>, smem) != cudaSuccess) return 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, collide_slice_kernel<S, MINB>, K::THREADS, smem);
     return nb > 0 ? nb : 1;
 }
 

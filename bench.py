@@ -3,18 +3,17 @@
 
 Workload (one GPU): the forward/reverse waypoint course, N = 16384 sampled
 8-32-32-2 networks per plan step, horizon T = 40, 2000 obstacle points (500
-on moving car outlines), 100 sampling times of closed loop at most.  A
-"step" is one plan step at one sampling time: sampling, rollout with
-collision checks, selection and the winner epilogue.  The simulated vehicle
-and the obstacles advance between steps on the host (outside the timed
-region); the winner's parameters warm-start the next step.
+on moving car outlines).  A "step" is one sampling time of the closed loop
+run on the device as one CUDA-graph replay: sampling, rollout, collision
+checks, selection, winner epilogue, then the simulated vehicle, obstacle and
+waypoint advance; the winner's parameters warm-start the next step.
 
-value   = N * T * K / (sum of the K plan steps' device time), inputs resident
-          in HBM, L2 flushed (256 MiB write) between steps, CUDA events on the
-          launching stream;
-e2e     = the same through the host-buffer entry point (host->device copy of
-          the obstacles and warm start, plan, device->host copy of the
-          result, synchronise), wall clock;
+value   = N * T * K / (sum of the K steps' device time), inputs resident in
+          HBM, L2 flushed (256 MiB write) between steps, CUDA events captured
+          in the step graph;
+e2e     = the same closed loop through the host-buffer entry point (obstacle
+          copy in, plan, result copy out, synchronise, host vehicle model),
+          wall clock per plan call;
 roofline = the collision kernel (the dominant one): algorithmic FP32 FMAs
           (4 per point-check of a live sample: two rows of the rotated
           inequality test) over its event-timed duration, against the FMA
@@ -51,7 +50,7 @@ SM_MAX_MHZ = 2070.0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="npp", choices=["npp", "reference"])
     ap.add_argument("--seed", type=int, default=0)
@@ -68,7 +67,8 @@ def dist_env():
 
 
 class Clocks:
-    """nvidia-smi sampling of SM clock and throttle reasons every 200 ms."""
+    """SM clock and throttle reasons, sampled by a background thread that
+    queries nvidia-smi back to back while the timed steps run."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -76,33 +76,34 @@ class Clocks:
 
     def __init__(self, gpu_index):
         self.gpu = gpu_index
-        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
-        self.p = None
+        self.rows = []
+        self.stop_flag = False
+        self.thread = None
 
-    def start(self):
-        try:
-            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
-                                      stdout=self.f, stderr=subprocess.DEVNULL)
-        except OSError:
-            self.p = None
-
-    def stop(self):
-        if self.p is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.p.terminate()
-        try:
-            self.p.wait(timeout=5)
-        except subprocess.TimeoutExpired:
-            self.p.kill()
-        self.f.flush()
-        rows = []
-        with open(self.f.name) as fh:
-            for line in fh:
+    def _poll(self):
+        while not self.stop_flag:
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                      "--format=csv,noheader,nounits"], capture_output=True,
+                                     text=True, timeout=5).stdout
+            except (OSError, subprocess.TimeoutExpired):
+                return
+            for line in out.splitlines():
                 parts = [x.strip() for x in line.split(",")]
                 if len(parts) >= 9:
-                    rows.append(parts)
-        os.unlink(self.f.name)
+                    self.rows.append(parts)
+
+    def start(self):
+        import threading
+        self.stop_flag = False
+        self.thread = threading.Thread(target=self._poll, daemon=True)
+        self.thread.start()
+
+    def stop(self):
+        self.stop_flag = True
+        if self.thread is not None:
+            self.thread.join(timeout=10)
+        rows = self.rows
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
 
@@ -111,14 +112,14 @@ class Clocks:
                 return float(x)
             except ValueError:
                 return float("nan")
-        sm = [num(r[1]) for r in rows]
         reasons = set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for r in rows:
             for name, val in zip(names, r[5:9]):
                 if val.lower().startswith("active"):
                     reasons.add(name)
-        return {"sm_mhz": float(np.nanmedian(sm)), "sm_max_mhz": float(np.nanmax([num(r[2]) for r in rows])),
+        return {"sm_mhz": float(np.nanmedian([num(r[1]) for r in rows])),
+                "sm_max_mhz": float(np.nanmax([num(r[2]) for r in rows])),
                 "power_w_max": float(np.nanmax([num(r[3]) for r in rows])), "samples": len(rows),
                 "reasons": sorted(reasons)}
 
@@ -211,83 +212,82 @@ def run_npp(args):
     K, Wu = args.steps, args.warmup
     pl = npp.Planner(p, max_N=N, max_T=T, max_M=M, device=local)
     npp.npp_set_timing(pl.h, True)
-    obs_dev = torch.empty(M, 4, dtype=torch.float32, device=dev)
+    obs0_dev = torch.tensor(sc["obs"], dtype=torch.float32, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
 
-    def closed_loop_pass(host_api: bool, nsteps: int, record: bool):
-        state = sc["state"].copy()
-        obs = sc["obs"].copy()
-        mission = closed_loop.Mission(sc["waypoints"], inputs.EPS)
-        warm_dev = None
-        warm_host = None
-        out = dict(step_ms=[], collide_ms=[], traj_ms=[], wall_ms=[], fma_c=0.0, fma_t=0.0,
-                   checks=0.0, free=[], best_cost=[])
-        if host_api:
-            obs_pin = torch.empty(M, 4, dtype=torch.float32).pin_memory()
-            hb = npp.npp_best()
-            params_h = torch.empty(pl.n_theta, dtype=torch.float32).pin_memory()
-            ctrl_h = torch.empty(T, 2, dtype=torch.float32).pin_memory()
-            traj_h = torch.empty(T + 1, 4, dtype=torch.float32).pin_memory()
-            warm_pin = torch.empty(pl.n_theta, dtype=torch.float32).pin_memory()
-            import ctypes
-            o = npp.npp_outputs()
-            o.best = ctypes.addressof(hb)
-            o.params = params_h.data_ptr()
-            o.controls = ctrl_h.data_ptr()
-            o.trajectory = traj_h.data_ptr()
+    def device_loop_pass(nsteps: int, record: bool):
+        """The closed loop on the device: one CUDA-graph replay per sampling
+        time (plan step + vehicle/obstacle/waypoint advance), L2 flushed
+        between replays outside the timed region."""
+        L = npp.npp_loop_create(pl.h, sc["state"], sc["waypoints"], inputs.EPS, obs0_dev, M, N, T,
+                                sc["seed"], max_log=max(nsteps, 1))
+        out = dict(step_ms=[], collide_ms=[], traj_ms=[], fma_c=0.0, fma_t=0.0, checks=0.0,
+                   free=[], best_cost=[])
         for t in range(nsteps):
-            goal = mission.goal
-            if host_api:
-                obs_pin.copy_(torch.from_numpy(obs.astype(np.float32)))
-                flush.zero_()
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                npp.npp_plan_step_host(pl.h, state, goal, obs_pin, M, N, T, sc["seed"], t,
-                                       warm_pin if warm_host else None, o)
-                wall = (time.perf_counter() - t0) * 1e3
-                a = ctrl_h[0].numpy().astype(np.float64)
-                warm_pin.copy_(params_h)
-                warm_host = True
-                if record:
-                    out["wall_ms"].append(wall)
-            else:
-                obs_dev.copy_(torch.from_numpy(obs.astype(np.float32)))
-                flush.zero_()
-                torch.cuda.synchronize()
-                pl.plan(state, goal, obs_dev, N, T, sc["seed"], t, warm=warm_dev)
-                tm = npp.npp_last_timing(pl.h)
-                fh = pl.first_hit[:N].cpu().numpy()
-                a = pl.controls[0].cpu().numpy().astype(np.float64)
-                b = pl.best.cpu()
-                if warm_dev is None:
-                    warm_dev = torch.empty_like(pl.params)
-                warm_dev.copy_(pl.params)
-                if record:
-                    out["step_ms"].append(tm["total"])
-                    out["collide_ms"].append(tm["collide"])
-                    out["traj_ms"].append(tm["traj"])
-                    fc, ft, ch = algorithmic_work(fh, T, M, W)
-                    out["fma_c"] += fc
-                    out["fma_t"] += ft
-                    out["checks"] += ch
-                    out["free"].append(float(np.mean(fh < 0)))
-                    out["best_cost"].append(float(b[2:3].view(torch.float32).item()))
+            flush.zero_()
+            torch.cuda.synchronize()
+            npp.npp_loop_run(L, 1)
+            tm = npp.npp_loop_last_timing(L)
+            if record:
+                _, fh = npp.npp_loop_samples(L, N)
+                out["step_ms"].append(tm["total"])
+                out["collide_ms"].append(tm["collide"])
+                out["traj_ms"].append(tm["traj"])
+                fc, ft, ch = algorithmic_work(fh, T, M, W)
+                out["fma_c"] += fc
+                out["fma_t"] += ft
+                out["checks"] += ch
+                out["free"].append(float(np.mean(fh < 0)))
+        st = npp.npp_loop_read(L)
+        out["waypoints_reached"] = st["waypoint"] + st["done"]
+        out["n_infeasible"] = st["n_infeasible"]
+        npp.npp_loop_destroy(L)
+        return out
+
+    def host_loop_pass(nsteps: int):
+        """The same closed loop through the host-buffer entry point: obstacle
+        copy in, plan, result copy out, synchronise, host vehicle model."""
+        import ctypes
+        state = sc["state"].copy()
+        mission = closed_loop.Mission(sc["waypoints"], inputs.EPS)
+        obs_pin = torch.empty(M, 4, dtype=torch.float32).pin_memory()
+        hb = npp.npp_best()
+        params_h = torch.empty(pl.n_theta, dtype=torch.float32).pin_memory()
+        ctrl_h = torch.empty(T, 2, dtype=torch.float32).pin_memory()
+        traj_h = torch.empty(T + 1, 4, dtype=torch.float32).pin_memory()
+        warm_pin = torch.empty(pl.n_theta, dtype=torch.float32).pin_memory()
+        o = npp.npp_outputs()
+        o.best = ctypes.addressof(hb)
+        o.params = params_h.data_ptr()
+        o.controls = ctrl_h.data_ptr()
+        o.trajectory = traj_h.data_ptr()
+        obs = sc["obs"].copy()
+        wall_ms = []
+        for t in range(nsteps):
+            obs_pin.copy_(torch.from_numpy(obs.astype(np.float32)))
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            npp.npp_plan_step_host(pl.h, state, mission.goal, obs_pin, M, N, T, sc["seed"], t,
+                                   warm_pin if t > 0 else None, o)
+            wall_ms.append((time.perf_counter() - t0) * 1e3)
+            a = ctrl_h[0].numpy().astype(np.float64)
+            warm_pin.copy_(params_h)
             state = closed_loop.plant_step(p, state, a)
             obs = closed_loop.advance_obstacles(obs, p["Ts"])
             mission.update(state)
-        out["waypoints_reached"] = mission.k
-        return out
+        return wall_ms
 
-    # warm-up (untimed) then K timed steps of the device path; the clock
-    # sampler starts before the warm-up so that it is running by the timed steps
-    clocks = Clocks(local)
-    clocks.start()
-    closed_loop_pass(False, Wu, record=False)
+    # warm-up (untimed) then K timed steps of the device path, with the SM
+    # clocks sampled during them
+    device_loop_pass(Wu, record=False)
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize()
-    res = closed_loop_pass(False, K, record=True)
+    clocks = Clocks(local)
+    clocks.start()
+    res = device_loop_pass(K, record=True)
     torch.cuda.synchronize()
     ck = clocks.stop()
     if world > 1:
@@ -298,9 +298,8 @@ def run_npp(args):
     traj_ms = float(np.sum(res["traj_ms"]))
     e2e = None
     if not args.no_e2e:
-        closed_loop_pass(True, min(Wu, 3), record=False)
-        r2 = closed_loop_pass(True, K, record=True)
-        wall = float(np.sum(r2["wall_ms"]))
+        host_loop_pass(min(Wu, 3))
+        wall = float(np.sum(host_loop_pass(K)))
         e2e = {"value": N * T * K / (wall / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": M * 16 + pl.n_theta * 4,
                "d2h_bytes_per_step": 32 + pl.n_theta * 4 + T * 8 + (T + 1) * 16}
@@ -338,10 +337,11 @@ def run_npp(args):
                                    "step per sampling time",
                        "N": N, "T": T, "M": M, "width": W, "parallelism": "replicas (rank = scene)",
                        "l2": "flushed (256 MiB write) between timed steps",
-                       "timing": "sum of per-step CUDA-event durations on the launching stream"},
-            "roofline": roofline, "e2e": e2e, "gpu_launches": 2 * K, "clocks": ck,
+                       "timing": "sum of per-step CUDA-event durations (events captured in the "
+                                 "step graph, replayed on the launching stream)"},
+            "roofline": roofline, "e2e": e2e, "gpu_launches": 5 * K, "clocks": ck,
             "free_fraction": float(np.mean(res["free"])),
-            "waypoints_reached": res["waypoints_reached"]}
+            "waypoints_reached": res["waypoints_reached"], "infeasible_steps": res["n_infeasible"]}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sc, sc["state"], sc["waypoints"][0], sc["obs"], T)
     pl.close()

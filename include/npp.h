@@ -171,6 +171,64 @@ npp_status npp_sample_params(uint64_t seed, uint32_t t_index, uint32_t stream_id
                              int32_t n0, int32_t K, int32_t n_theta, float* out_dev,
                              void* stream);
 
+/* ---------------------------------------------------------------------
+ * Device-resident closed loop (Alg. 1): each sampling time is one CUDA graph
+ * replay holding the plan step and an advance kernel that applies the
+ * winner's first control to a simulated vehicle (the kinematic bicycle of
+ * Sect. IV in FP64, explicit Euler with Ts), moves the obstacle points at
+ * their velocities, switches to the next waypoint once the current one is
+ * reached within eps = (eps_xi, eps_eta, eps_phi, eps_v) (position error along
+ * and across the vehicle heading; Table hyperparameters), and keeps the
+ * winner's parameters as the next step's sample 0 (warm start, Sect. II-D
+ * "Fifth").  The sampling time t is the Philox t_index.
+ * --------------------------------------------------------------------- */
+typedef struct npp_loop npp_loop;
+
+typedef struct {
+    float x, y, phi, v, a_prev0, a_prev1;  /* simulated vehicle after the last step */
+    int32_t t;            /* sampling times completed                         */
+    int32_t waypoint;     /* index of the current waypoint                     */
+    int32_t done;         /* 1 once the last waypoint has been reached         */
+    int32_t status;       /* status of the last plan step (OK / INFEASIBLE)    */
+    int32_t best_idx;     /* winner of the last plan step                      */
+    int32_t n_infeasible; /* plan steps that ended infeasible                  */
+    float best_cost;      /* cost of the last winner                           */
+    int32_t reserved[3];
+} npp_loop_state;
+
+/* Create a loop on handle h (which it uses; keep h alive): initial state s0,
+ * waypoints_host[n_wp][4] (x, y, phi, v), eps_host[4], obstacle points
+ * obs_dev[M][4] at t = 0 (copied; the caller's array is not modified), N
+ * samples and horizon T per plan step (within the handle's capacity), and a
+ * device log of up to max_log rows.  Captures the step graph (synchronous). */
+npp_status npp_loop_create(npp_handle* h, const npp_state* s0, const float* waypoints_host,
+                           int32_t n_wp, const float* eps_host, const float* obs_dev, int32_t M,
+                           int32_t N, int32_t T, uint64_t seed, int32_t max_log, npp_loop** out);
+
+/* Run `steps` sampling times (graph replays), asynchronous on `stream`.
+ * A loop's steps must not run concurrently with other work on its handle. */
+npp_status npp_loop_run(npp_loop* L, int32_t steps, void* stream);
+
+/* Synchronise the device and read the loop state. */
+npp_status npp_loop_read(npp_loop* L, npp_loop_state* out_host);
+
+/* Synchronise and copy up to max_rows log rows of 8 floats (one per completed
+ * step: x, y, phi, v before the step, applied a0, a1, winner cost, waypoint
+ * index) into log_host; *rows_out receives the number copied. */
+npp_status npp_loop_log(npp_loop* L, float* log_host, int32_t max_rows, int32_t* rows_out);
+
+/* Synchronise and copy the last step's per-sample costs[N] and first
+ * collisions first_hit[N] (either pointer may be NULL). */
+npp_status npp_loop_samples(npp_loop* L, float* costs_host, int32_t* first_hit_host);
+
+/* Stage times of the last replayed step in ms (events captured in the
+ * graph): [0] trajectory kernel, [1] collision kernel, [2] selection
+ * epilogue + advance, [3] whole step; writes up to n values. */
+npp_status npp_loop_last_timing(npp_loop* L, float* stage_ms, int32_t n);
+
+/* Free the loop (after synchronising the device). */
+npp_status npp_loop_destroy(npp_loop* L);
+
 /* The plan step of npp_plan_step for callers that cannot allocate device
  * memory -- for instance a plugin whose host application owns every device
  * allocation, or a real-time control loop that must not call cudaMalloc once

@@ -11,45 +11,13 @@
 
 #include "../../include/npp.h"
 #include "npp_device.cuh"
+#include "npp_internal.h"
 
 using namespace npp;
 
-struct npp_handle {
-    npp_config cfg;
-    int device;
-    int n_theta;
-    int max_points;                      // obstacle points that fit in shared memory
-    DevCfg dc;
-    unsigned long long* d_key;           // packed best key
-    float4* d_traj;                      // [(max_T+1) * max_N]
-    float2* d_ctrl;                      // [max_T * max_N]
-    float* d_jfree;                      // [max_N]
-    float4* d_coefA;                     // [(max_T+1) * max_N]
-    float2* d_coefB;                     // [(max_T+1) * max_N]
-    unsigned* d_work;                    // persistent-kernel work counter
-    int sm_count;
-    int collide_variant;                 // -1 automatic; 0, 1 block-balanced (16 / 8 warps), 2 warp items
-    int collide_active;                  // variant used for the current launch
-    int traj_variant;                    // 0: 2 hidden units per lane, 1: 4
-    int occ_M, occ_blocks;               // cached occupancy for the last M
-    // host-mode staging
-    float4* d_obs;
-    float* d_warm;
-    npp_best* d_best;
-    float* d_params;
-    float* d_controls;
-    float* d_trajectory;
-    float* d_costs;
-    int32_t* d_fh;
-    cudaStream_t stream;
-    bool timing;
-    cudaEvent_t ev[4];                   // start, after trajectories, after collisions, end
-    std::string err;
-};
-
 static std::string g_err;
 
-static npp_status fail(npp_handle* h, npp_status s, const char* fmt, ...)
+npp_status fail(npp_handle* h, npp_status s, const char* fmt, ...)
 {
     char buf[512];
     va_list ap;
@@ -59,13 +27,6 @@ static npp_status fail(npp_handle* h, npp_status s, const char* fmt, ...)
     if (h) h->err = buf; else g_err = buf;
     return s;
 }
-
-#define CUDA_TRY(h, call)                                                                  \
-    do {                                                                                   \
-        cudaError_t e_ = (call);                                                           \
-        if (e_ != cudaSuccess)                                                             \
-            return fail((h), NPP_CUDA_ERROR, "%s failed: %s", #call, cudaGetErrorString(e_)); \
-    } while (0)
 
 static int n_theta_of(int width) { return 12 * width + width * width + 2; }
 
@@ -83,6 +44,14 @@ namespace {
 // parameters from Philox (or copy the warm start).
 __global__ void epilogue_kernel(const EpilogueArgs e)
 {
+    float x0 = e.x0, y0 = e.y0, phi0 = e.phi0;
+    SamplerKey skey = e.key;
+    bool warm_ok = true;
+    if (e.dyn) {
+        x0 = e.dyn->x0; y0 = e.dyn->y0; phi0 = e.dyn->phi0;
+        skey.t_index = e.dyn->t_index;
+        warm_ok = e.dyn->warm_valid != 0;
+    }
     const unsigned long long key = *e.best_key;
     const int idx = (int)(key & 0xffffffffull);
     const bool dead = (key >> 63) != 0;
@@ -98,14 +67,14 @@ __global__ void epilogue_kernel(const EpilogueArgs e)
         b->reserved[0] = b->reserved[1] = b->reserved[2] = b->reserved[3] = 0;
     }
     float s0, c0;
-    sincosf(e.phi0, &s0, &c0);
+    sincosf(phi0, &s0, &c0);
     if (e.trajectory) {
         for (int h = threadIdx.x; h <= e.T; h += blockDim.x) {
             const float4 z = e.traj[(size_t)min(h, last) * e.N + idx];
             float4 w;
-            w.x = e.x0 + c0 * z.x - s0 * z.y;
-            w.y = e.y0 + s0 * z.x + c0 * z.y;
-            w.z = e.phi0 + z.z;
+            w.x = x0 + c0 * z.x - s0 * z.y;
+            w.y = y0 + s0 * z.x + c0 * z.y;
+            w.z = phi0 + z.z;
             w.w = z.w;
             reinterpret_cast<float4*>(e.trajectory)[h] = w;
         }
@@ -118,11 +87,12 @@ __global__ void epilogue_kernel(const EpilogueArgs e)
         }
     }
     if (e.params) {
-        if (e.warm && idx == 0) {
-            for (int i = threadIdx.x; i < e.n_theta; i += blockDim.x) e.params[i] = e.warm[i];
+        if (e.warm && idx == 0 && warm_ok) {
+            if (e.params != e.warm)
+                for (int i = threadIdx.x; i < e.n_theta; i += blockDim.x) e.params[i] = e.warm[i];
         } else {
             for (int q = threadIdx.x; 4 * q < e.n_theta; q += blockDim.x) {
-                const float4 v = sample_quad(e.key, (uint32_t)q, (uint32_t)idx);
+                const float4 v = sample_quad(skey, (uint32_t)q, (uint32_t)idx);
                 const float vv[4] = { v.x, v.y, v.z, v.w };
                 for (int j = 0; j < 4 && 4 * q + j < e.n_theta; ++j) e.params[4 * q + j] = vv[j];
             }
@@ -169,7 +139,7 @@ static cudaError_t launch_traj(const npp_handle* h, const RolloutArgs& a, cudaSt
 }
 
 // trajectories, then collision checks; events around both when timing
-static npp_status run_rollout(npp_handle* h, RolloutArgs& a, cudaStream_t s)
+npp_status run_rollout(npp_handle* h, RolloutArgs& a, cudaStream_t s)
 {
     a.coefA = h->d_coefA;
     a.coefB = h->d_coefB;
@@ -186,11 +156,11 @@ static npp_status run_rollout(npp_handle* h, RolloutArgs& a, cudaStream_t s)
     }
     a.grid_collide = h->sm_count * h->occ_blocks;
     CUDA_TRY(h, cudaMemsetAsync(h->d_work, 0, sizeof(unsigned), s));
-    if (h->timing) CUDA_TRY(h, cudaEventRecord(h->ev[0], s));
+    if (h->timing) CUDA_TRY(h, record_event(h->ev[0], s));
     CUDA_TRY(h, launch_traj(h, a, s));
-    if (h->timing) CUDA_TRY(h, cudaEventRecord(h->ev[1], s));
+    if (h->timing) CUDA_TRY(h, record_event(h->ev[1], s));
     CUDA_TRY(h, launch_collide_resident(a, s, h->collide_active));
-    if (h->timing) CUDA_TRY(h, cudaEventRecord(h->ev[2], s));
+    if (h->timing) CUDA_TRY(h, record_event(h->ev[2], s));
     return NPP_OK;
 }
 
@@ -398,7 +368,7 @@ npp_status npp_plan_step(npp_handle* h, const npp_state* state, const npp_goal* 
     e.trajectory = out->trajectory;
     epilogue_kernel<<<1, 256, 0, s>>>(e);
     CUDA_TRY(h, cudaGetLastError());
-    if (h->timing) CUDA_TRY(h, cudaEventRecord(h->ev[3], s));
+    if (h->timing) CUDA_TRY(h, record_event(h->ev[3], s));
     return NPP_OK;
 }
 
@@ -467,7 +437,7 @@ npp_status npp_rollout_params(npp_handle* h, const npp_state* state, const npp_g
     a.jfree = h->d_jfree;
     a.best_key = nullptr;
     if ((st = run_rollout(h, a, s)) != NPP_OK) return st;
-    if (h->timing) CUDA_TRY(h, cudaEventRecord(h->ev[3], s));
+    if (h->timing) CUDA_TRY(h, record_event(h->ev[3], s));
     return NPP_OK;
 }
 

@@ -120,6 +120,28 @@ __device__ __forceinline__ float2 sample_pair(const SamplerKey& key, uint32_t i,
 }
 
 // ------------------------------------------------------------------ kernels
+// State of a device-resident closed loop (Alg. 1 run inside a CUDA graph).
+// The plan-step kernels read the planner's view of it; the advance kernel
+// moves the simulated vehicle and the mission forward.
+struct LoopDev {
+    float x0, y0, phi0, v0, ap0, ap1;  // vehicle state at this sampling time (FP32 view)
+    float gx, gy, gphi, gv;            // current goal setpoint
+    uint32_t t_index;                  // sampling time (Philox counter word)
+    int warm_valid;                    // the warm-start buffer holds theta*_{t-1}
+    double px, py, pphi, pv;           // simulated vehicle (FP64)
+    int waypoint, n_wp, done, t;
+    int status, best_idx, n_infeasible;
+    float best_cost;
+    float eps[4];                      // completion tolerances (xi, eta, phi, v)
+};
+
+// Per-step scalars of a plan step, from the arguments or from a LoopDev.
+struct StepIn {
+    float x0, y0, phi0, v0, ap0, ap1, gx, gy, gphi, gv;
+    uint32_t t_index;
+    bool warm_ok;
+};
+
 struct RolloutArgs {
     DevCfg c;
     float x0, y0, phi0, v0, ap0, ap1;  // world-frame state and last controls
@@ -139,7 +161,26 @@ struct RolloutArgs {
     unsigned long long* best_key;      // packed (class, cost, index) minimum
     unsigned* work;                    // work-queue counter of the persistent collision kernel
     int grid_collide;                  // persistent grid size
+    const LoopDev* dyn;                // when set, per-step scalars come from here
 };
+
+__device__ __forceinline__ StepIn step_in(const RolloutArgs& a)
+{
+    StepIn s;
+    if (a.dyn) {
+        const LoopDev& d = *a.dyn;
+        s.x0 = d.x0; s.y0 = d.y0; s.phi0 = d.phi0; s.v0 = d.v0; s.ap0 = d.ap0; s.ap1 = d.ap1;
+        s.gx = d.gx; s.gy = d.gy; s.gphi = d.gphi; s.gv = d.gv;
+        s.t_index = d.t_index;
+        s.warm_ok = d.warm_valid != 0;
+    } else {
+        s.x0 = a.x0; s.y0 = a.y0; s.phi0 = a.phi0; s.v0 = a.v0; s.ap0 = a.ap0; s.ap1 = a.ap1;
+        s.gx = a.gx; s.gy = a.gy; s.gphi = a.gphi; s.gv = a.gv;
+        s.t_index = a.key.t_index;
+        s.warm_ok = true;
+    }
+    return s;
+}
 
 struct EpilogueArgs {
     float x0, y0, phi0;
@@ -153,6 +194,7 @@ struct EpilogueArgs {
     float* params;
     float* controls;
     float* trajectory;
+    const LoopDev* dyn;                // when set, x0, y0, phi0, t_index, warm validity from here
 };
 
 // launchers: trajectory kernel per network width, one collision kernel

@@ -1,0 +1,69 @@
+// npp_internal.h -- the handle and helpers shared by the host-side
+// translation units of the library (not part of the C ABI).
+#pragma once
+
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "../../include/npp.h"
+#include "npp_device.cuh"
+
+struct npp_handle {
+    npp_config cfg;
+    int device;
+    int n_theta;
+    int max_points;                      // obstacle points that fit in shared memory
+    npp::DevCfg dc;
+    unsigned long long* d_key;           // packed best key
+    float4* d_traj;                      // [(max_T+1) * max_N]
+    float2* d_ctrl;                      // [max_T * max_N]
+    float* d_jfree;                      // [max_N]
+    float4* d_coefA;                     // [(max_T+1) * max_N]
+    float2* d_coefB;                     // [(max_T+1) * max_N]
+    unsigned* d_work;                    // persistent-kernel work counter
+    int sm_count;
+    int collide_variant;                 // -1 automatic, else a fixed collision-kernel variant
+    int collide_active;                  // variant used for the current launch
+    int traj_variant;                    // 0: 2 hidden units per lane, 1: 4
+    int occ_M, occ_blocks;               // cached occupancy for the last M
+    // host-mode staging
+    float4* d_obs;
+    float* d_warm;
+    npp_best* d_best;
+    float* d_params;
+    float* d_controls;
+    float* d_trajectory;
+    float* d_costs;
+    int32_t* d_fh;
+    cudaStream_t stream;
+    bool timing;
+    cudaEvent_t ev[4];                   // start, after trajectories, after collisions, end
+    std::string err;
+};
+
+
+// cudaEventRecord that becomes a real event-record node under stream capture
+// (a plain record there only orders work and is never executed)
+inline cudaError_t record_event(cudaEvent_t ev, cudaStream_t s)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return e;
+    return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal)
+                                               : cudaEventRecord(ev, s);
+}
+
+// records a message for npp_last_error and returns s
+npp_status fail(npp_handle* h, npp_status s, const char* fmt, ...);
+
+// trajectory + collision kernels of one plan step (fills workspace pointers,
+// the persistent grid and the work-counter reset)
+npp_status run_rollout(npp_handle* h, npp::RolloutArgs& a, cudaStream_t s);
+
+#define CUDA_TRY(h, call)                                                                  \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail((h), NPP_CUDA_ERROR, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)

@@ -147,24 +147,26 @@ __global__ void __launch_bounds__(NW * 32) traj_kernel(const RolloutArgs a)
     const bool valid = n < a.N;
     const DevCfg& c = a.c;
 
+    const StepIn si = step_in(a);
     float s0, c0;
-    sincosf(a.phi0, &s0, &c0);
-    const float gdx = a.gx - a.x0, gdy = a.gy - a.y0;
+    sincosf(si.phi0, &s0, &c0);
+    const float gdx = si.gx - si.x0, gdy = si.gy - si.y0;
     const float gxi = c0 * gdx + s0 * gdy, geta = -s0 * gdx + c0 * gdy;
-    const float gph = a.gphi - a.phi0, gv = a.gv;
+    const float gph = si.gphi - si.phi0, gv = si.gv;
 
     LaneNet<W, G> net;
     {
         ThetaSrc src;
         src.key = a.key;
+        src.key.t_index = si.t_index;
         src.n = (uint32_t)(valid ? n : 0);
         src.mem = nullptr;
         if (a.theta) src.mem = a.theta + (size_t)(valid ? n : 0) * S::NT;
-        else if (a.warm && n == 0) src.mem = a.warm;
+        else if (a.warm && n == 0 && si.warm_ok) src.mem = a.warm;
         net.load(src, gl);
     }
 
-    float x = 0.f, y = 0.f, ph = 0.f, v = a.v0, ap0 = a.ap0, ap1 = a.ap1, E = 0.f;
+    float x = 0.f, y = 0.f, ph = 0.f, v = si.v0, ap0 = si.ap0, ap1 = si.ap1, E = 0.f;
     const int T = a.T, N = a.N;
     const float invT = 1.0f / (float)T;
     float* hrow = hx_all + b * W;
@@ -326,15 +328,16 @@ template <int THREADS>
 __device__ __forceinline__ int stage_points(const RolloutArgs& a, float4* XY, float4* V)
 {
     const int npairs = (a.M + 1) / 2;
+    const StepIn si = step_in(a);
     float s0, c0;
-    sincosf(a.phi0, &s0, &c0);
+    sincosf(si.phi0, &s0, &c0);
     float* xy = reinterpret_cast<float*>(XY);
     float* vv = reinterpret_cast<float*>(V);
     for (int j = threadIdx.x; j < 2 * npairs; j += THREADS) {
         float px = 1e15f, py = 1e15f, vx = 0.f, vy = 0.f;
         if (j < a.M) {
             const float4 o = a.obs[j];
-            const float dx = o.x - a.x0, dy = o.y - a.y0;
+            const float dx = o.x - si.x0, dy = o.y - si.y0;
             px = c0 * dx + s0 * dy;
             py = -s0 * dx + c0 * dy;
             vx = c0 * o.z + s0 * o.w;

@@ -46,6 +46,12 @@ class npp_best(C.Structure):
                 ("first_hit", C.c_int32), ("reserved", C.c_int32 * 4)]
 
 
+class npp_loop_state(C.Structure):
+    _fields_ = [(n, C.c_float) for n in ("x", "y", "phi", "v", "a_prev0", "a_prev1")] + [
+        (n, C.c_int32) for n in ("t", "waypoint", "done", "status", "best_idx", "n_infeasible")] + [
+        ("best_cost", C.c_float), ("reserved", C.c_int32 * 3)]
+
+
 class npp_outputs(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in ("best", "params", "controls", "trajectory", "costs",
                                           "first_hit", "sample_traj", "sample_ctrl")]
@@ -53,7 +59,9 @@ class npp_outputs(C.Structure):
 
 EXPORTS = ("npp_create", "npp_destroy", "npp_last_error", "npp_n_theta", "npp_plan_step",
            "npp_plan_step_host", "npp_rollout_params", "npp_sample_params", "npp_set_timing",
-           "npp_last_timing", "npp_set_option", "npp_plan_step_noalloc")
+           "npp_last_timing", "npp_set_option", "npp_plan_step_noalloc", "npp_loop_create",
+           "npp_loop_run", "npp_loop_read", "npp_loop_log", "npp_loop_destroy", "npp_loop_samples",
+           "npp_loop_last_timing")
 
 _lib = None
 
@@ -81,6 +89,14 @@ def lib():
         L.npp_sample_params.argtypes = [U64, U32, U32, I32, I32, I32, P, P]
         L.npp_set_timing.argtypes = [P, I32]
         L.npp_set_option.argtypes = [P, C.c_char_p, I32]
+        L.npp_loop_create.argtypes = [P, C.POINTER(npp_state), P, I32, P, P, I32, I32, I32, U64, I32,
+                                      C.POINTER(P)]
+        L.npp_loop_run.argtypes = [P, I32, P]
+        L.npp_loop_read.argtypes = [P, C.POINTER(npp_loop_state)]
+        L.npp_loop_log.argtypes = [P, P, I32, C.POINTER(I32)]
+        L.npp_loop_destroy.argtypes = [P]
+        L.npp_loop_samples.argtypes = [P, P, P]
+        L.npp_loop_last_timing.argtypes = [P, C.POINTER(C.c_float), I32]
         L.npp_plan_step_noalloc.argtypes = [C.POINTER(npp_config), C.POINTER(npp_state),
                                             C.POINTER(npp_goal), P, I32, I32, I32, U64, U32, P,
                                             C.POINTER(npp_outputs), P]
@@ -199,6 +215,55 @@ def npp_last_timing(h):
     collide, epilogue, total."""
     t = (C.c_float * 4)()
     _check(lib().npp_last_timing(h, t, 4), h)
+    return dict(traj=t[0], collide=t[1], epilogue=t[2], total=t[3])
+
+
+def npp_loop_create(h, state, waypoints, eps, obs, M, N, T, seed, max_log=1024):
+    """waypoints: array-like [n_wp][4]; eps: 4 tolerances; obs: CUDA tensor."""
+    import numpy as np
+    wp = np.ascontiguousarray(waypoints, dtype=np.float32).reshape(-1, 4)
+    ep = np.ascontiguousarray(eps, dtype=np.float32).reshape(4)
+    L = C.c_void_p()
+    _check(lib().npp_loop_create(h, C.byref(make_state(state)), wp.ctypes.data_as(C.c_void_p),
+                                 wp.shape[0], ep.ctypes.data_as(C.c_void_p), _ptr(obs), int(M),
+                                 int(N), int(T), int(seed), int(max_log), C.byref(L)), h)
+    return L
+
+
+def npp_loop_run(L, steps, stream=None):
+    return _check(lib().npp_loop_run(L, int(steps), _stream(stream)))
+
+
+def npp_loop_read(L) -> dict:
+    st = npp_loop_state()
+    _check(lib().npp_loop_read(L, C.byref(st)))
+    return {n: getattr(st, n) for n, _ in npp_loop_state._fields_ if n != "reserved"}
+
+
+def npp_loop_log(L, max_rows=1024):
+    import numpy as np
+    out = np.zeros((max_rows, 8), np.float32)
+    rows = C.c_int32()
+    _check(lib().npp_loop_log(L, out.ctypes.data_as(C.c_void_p), int(max_rows), C.byref(rows)))
+    return out[: rows.value]
+
+
+def npp_loop_destroy(L):
+    return lib().npp_loop_destroy(L)
+
+
+def npp_loop_samples(L, N):
+    """(costs[N], first_hit[N]) of the last replayed step (numpy, synchronous)."""
+    import numpy as np
+    costs = np.zeros(N, np.float32)
+    fh = np.zeros(N, np.int32)
+    _check(lib().npp_loop_samples(L, costs.ctypes.data_as(C.c_void_p), fh.ctypes.data_as(C.c_void_p)))
+    return costs, fh
+
+
+def npp_loop_last_timing(L):
+    t = (C.c_float * 4)()
+    _check(lib().npp_loop_last_timing(L, t, 4))
     return dict(traj=t[0], collide=t[1], epilogue=t[2], total=t[3])
 
 

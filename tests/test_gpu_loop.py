@@ -1,0 +1,99 @@
+"""Device-resident closed loop (Alg. 1 in a CUDA graph) against a host-driven
+loop built from npp_plan_step and the same simulated vehicle."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1904_06680_gb300 import closed_loop, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _obs_at(obs0, t, Ts):
+    """obstacle points at sampling time t as the loop computes them: one FP32
+    multiply-add p0 + tau v with tau = t * Ts in FP32."""
+    o = obs0.astype(np.float32)
+    tau = np.float32(t) * np.float32(Ts)
+    out = o.copy()
+    out[:, 0] = (tau.astype(np.float64) * o[:, 2] + o[:, 0]).astype(np.float32)
+    out[:, 1] = (tau.astype(np.float64) * o[:, 3] + o[:, 1]).astype(np.float32)
+    return out
+
+
+def test_loop_matches_host_driven_loop():
+    import torch
+    from paper_1904_06680_gb300 import npp
+    sc = inputs.scene_course(3, N=2048, T=30, n_wall=300, n_island=100, n_dyn=100)
+    p, N, T = sc["preset"], sc["N"], sc["T"]
+    M = sc["obs"].shape[0]
+    K = 8
+    obs0 = torch.tensor(sc["obs"], dtype=torch.float32, device="cuda")
+    pl = npp.Planner(p, max_N=N, max_T=T, max_M=M)
+    L = npp.npp_loop_create(pl.h, sc["state"], sc["waypoints"], inputs.EPS, obs0, M, N, T, sc["seed"])
+    npp.npp_loop_run(L, K)
+    st = npp.npp_loop_read(L)
+    log = npp.npp_loop_log(L)
+    npp.npp_loop_destroy(L)
+    assert st["t"] == K and log.shape == (K, 8)
+    # host-driven reference
+    state = sc["state"].astype(np.float64).copy()
+    mission = closed_loop.Mission(sc["waypoints"], inputs.EPS)
+    warm = None
+    host_rows = []
+    for t in range(K):
+        obs_t = torch.tensor(_obs_at(sc["obs"], t, p["Ts"]), device="cuda")
+        pl.plan(state.astype(np.float32), mission.goal, obs_t, N, T, sc["seed"], t, warm=warm)
+        torch.cuda.synchronize()
+        r = pl.result(N, T)
+        a = r["controls"][0].astype(np.float64)
+        host_rows.append((state[:4].copy(), a, r["best_idx"], r["best_cost"]))
+        warm = pl.params.clone()
+        state = closed_loop.plant_step(p, state, a)
+        mission.update(state)
+    for t in range(K):
+        z, a, bi, bc = host_rows[t]
+        np.testing.assert_allclose(log[t, :4], z, rtol=1e-5, atol=1e-5)
+        np.testing.assert_allclose(log[t, 4:6], a, rtol=0, atol=1e-6)
+        # the plan inputs agree to the last float bit or so; a chaotic rollout
+        # can amplify that to the trajectory tolerance
+        assert abs(log[t, 6] - bc) <= 1e-4 * max(1.0, abs(bc))
+    np.testing.assert_allclose([st["x"], st["y"], st["phi"], st["v"]], state[:4], rtol=1e-5, atol=1e-5)
+    pl.close()
+
+
+def test_loop_reaches_waypoint_without_obstacles():
+    """An obstacle-free mission: the vehicle at rest must reach a goal 8 m
+    ahead (at rest, same heading) within the tolerances of Table
+    hyperparameters."""
+    import torch
+    from paper_1904_06680_gb300 import npp
+    p = inputs.planner(16)
+    N, T = 4096, 30
+    pl = npp.Planner(p, max_N=N, max_T=T, max_M=1)
+    obs = torch.zeros(1, 4, dtype=torch.float32, device="cuda")
+    obs[0, :2] = 1e4                              # one point far away
+    start = [2.0, -1.0, 0.3, 0.0, 0.0, 0.0]
+    goal = [2.0 + 8 * math.cos(0.3), -1.0 + 8 * math.sin(0.3), 0.3, 0.0]
+    L = npp.npp_loop_create(pl.h, start, [goal], inputs.EPS, obs, 1, N, T, 77)
+    reached_at = None
+    for k in range(12):
+        npp.npp_loop_run(L, 10)
+        st = npp.npp_loop_read(L)
+        if st["done"]:
+            reached_at = st["t"]
+            break
+    log = npp.npp_loop_log(L)
+    npp.npp_loop_destroy(L)
+    pl.close()
+    d0 = math.hypot(goal[0] - start[0], goal[1] - start[1])
+    d_end = math.hypot(goal[0] - log[-1, 0], goal[1] - log[-1, 1])
+    assert reached_at is not None, (d0, d_end, log[-1])
+    assert st["n_infeasible"] == 0

@@ -120,7 +120,9 @@ typedef struct npp_handle npp_handle;
 
 /* Create a handle on CUDA device `device`: validates the configuration and
  * allocates device workspaces for up to max_N samples, max_T steps and max_M
- * obstacle points.  *h is set to NULL on failure. */
+ * obstacle points (point sets larger than shared memory, about 14,000
+ * points, are read from an L2-resident copy instead).  *h is set to NULL on
+ * failure. */
 npp_status npp_create(npp_handle** h, const npp_config* cfg, int32_t device);
 
 /* Free the handle and its workspaces (waits for its device work). */
@@ -228,6 +230,62 @@ npp_status npp_loop_last_timing(npp_loop* L, float* stage_ms, int32_t n);
 
 /* Free the loop (after synchronising the device). */
 npp_status npp_loop_destroy(npp_loop* L);
+
+/* ---------------------------------------------------------------------
+ * Batched planning: many independent plan steps ("scenes", each with its own
+ * state, goal, obstacle points, N, T and network width 16, 32 or 64; the
+ * vehicle/cost constants are the handle's) run as one batch of persistent
+ * launches -- a point transform, one trajectory launch per width, one
+ * collision launch over all scenes (work queues, costliest scenes first) and
+ * one epilogue -- with no host work between them, so the batch can be
+ * captured in a CUDA graph by the caller.  Each scene's result equals
+ * npp_plan_step on that scene (same arithmetic per sample).
+ * --------------------------------------------------------------------- */
+typedef struct {
+    npp_state state;
+    npp_goal goal;
+    int32_t N, T, M, width;   /* samples, horizon, obstacle points, hidden width */
+    int64_t obs_offset;       /* index of the scene's first point in the batch's
+                                 obstacle array ([total][4] floats)              */
+    uint64_t seed;
+    uint32_t t_index;
+    int32_t reserved;
+} npp_scene;
+
+/* Outputs of a batch (device pointers; all but `best` may be NULL).  Scene s
+ * starts at the offsets npp_batch_offsets returns: parameters (n_theta of its
+ * width), control rows [T][2], trajectory rows [T+1][4], samples [N]. */
+typedef struct {
+    npp_best* best;          /* [S]                                           */
+    float* params;           /* [sum n_theta]                                 */
+    float* controls;         /* [sum T][2]                                    */
+    float* trajectory;       /* [sum (T+1)][4]                                */
+    float* costs;            /* [sum N]                                       */
+    int32_t* first_hit;      /* [sum N]                                       */
+} npp_batch_outputs;
+
+typedef struct npp_batch npp_batch;
+
+/* Validate the S scene descriptors, order the work, allocate the batch's
+ * workspaces (24 bytes per sample-step plus the points) and upload the scene
+ * table (synchronous).  The batch uses h's constants and keeps a pointer to h. */
+npp_status npp_batch_create(npp_handle* h, const npp_scene* scenes, int32_t S, npp_batch** out);
+
+/* New states, goals, seeds and t_index for the same scenes (sizes, widths and
+ * obstacle offsets must not change); synchronous upload. */
+npp_status npp_batch_update(npp_batch* B, const npp_scene* scenes);
+
+/* offsets_host[S+1][4]: per scene the first parameter, control row,
+ * trajectory row and sample of its outputs; row S holds the totals. */
+npp_status npp_batch_offsets(npp_batch* B, int64_t* offsets_host);
+
+/* Queue the whole batch on `stream` (kernels and memsets only).  obs_dev is
+ * the [total points][4] world-frame obstacle array, 16-byte aligned. */
+npp_status npp_plan_batch(npp_batch* B, const float* obs_dev, const npp_batch_outputs* out,
+                          void* stream);
+
+/* Free the batch (after synchronising the device). */
+npp_status npp_batch_destroy(npp_batch* B);
 
 /* The plan step of npp_plan_step for callers that cannot allocate device
  * memory -- for instance a plugin whose host application owns every device

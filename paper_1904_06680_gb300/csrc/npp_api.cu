@@ -149,17 +149,25 @@ npp_status run_rollout(npp_handle* h, RolloutArgs& a, cudaStream_t s)
     // samples -> one warp per item keeps enough items in flight
     const int v = h->collide_variant >= 0 ? h->collide_variant
                 : (a.N <= 8192 ? 3 : (a.N <= 32768 ? 4 : 2));
-    if (h->occ_M != a.M || h->collide_active != v) {
-        h->occ_blocks = collide_resident_blocks_per_sm(a.M, v);
-        h->occ_M = a.M;
-        h->collide_active = v;
+    // points beyond shared memory: point-sliced kernel on an L2-resident copy
+    const bool global_pts = a.M > h->max_points;
+    if (global_pts) {
+        a.pXY = h->d_pXY;
+        a.pV = h->d_pV;
+        a.grid_collide = h->sm_count * collide_global_blocks_per_sm();
+    } else {
+        if (h->occ_M != a.M || h->collide_active != v) {
+            h->occ_blocks = collide_resident_blocks_per_sm(a.M, v);
+            h->occ_M = a.M;
+            h->collide_active = v;
+        }
+        a.grid_collide = h->sm_count * h->occ_blocks;
     }
-    a.grid_collide = h->sm_count * h->occ_blocks;
     CUDA_TRY(h, cudaMemsetAsync(h->d_work, 0, sizeof(unsigned), s));
     if (h->timing) CUDA_TRY(h, record_event(h->ev[0], s));
     CUDA_TRY(h, launch_traj(h, a, s));
     if (h->timing) CUDA_TRY(h, record_event(h->ev[1], s));
-    CUDA_TRY(h, launch_collide_resident(a, s, h->collide_active));
+    CUDA_TRY(h, global_pts ? launch_collide_global(a, s) : launch_collide_resident(a, s, h->collide_active));
     if (h->timing) CUDA_TRY(h, record_event(h->ev[2], s));
     return NPP_OK;
 }
@@ -248,9 +256,6 @@ npp_status npp_create(npp_handle** out, const npp_config* cfg, int32_t device)
     int smem_optin = 0;
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     int max_points = collide_max_points(smem_optin);
-    if (cfg->max_M > max_points)
-        return fail(nullptr, NPP_UNSUPPORTED, "max_M=%d exceeds the %d points held in shared memory",
-                    cfg->max_M, max_points);
     if ((double)(cfg->max_T + 1) * cfg->max_N * 24.0 > 64e9)
         return fail(nullptr, NPP_INVALID_ARG, "workspace for max_N x max_T too large");
 
@@ -293,6 +298,10 @@ npp_status npp_create(npp_handle** out, const npp_config* cfg, int32_t device)
     A((void**)&h->d_coefA, NT1 * sizeof(float4));
     A((void**)&h->d_coefB, NT1 * sizeof(float2));
     A((void**)&h->d_work, 64);
+    if (cfg->max_M > max_points) {
+        A((void**)&h->d_pXY, (size_t)(cfg->max_M / 2 + 1) * sizeof(float4));
+        A((void**)&h->d_pV, (size_t)(cfg->max_M / 2 + 1) * sizeof(float4));
+    }
     A((void**)&h->d_obs, (size_t)cfg->max_M * sizeof(float4));
     A((void**)&h->d_warm, (size_t)h->n_theta * sizeof(float));
     A((void**)&h->d_best, sizeof(npp_best));
@@ -318,6 +327,7 @@ npp_status npp_destroy(npp_handle* h)
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
     void* ptrs[] = { h->d_key, h->d_traj, h->d_ctrl, h->d_jfree, h->d_coefA, h->d_coefB, h->d_work,
+                     h->d_pXY, h->d_pV,
                      h->d_obs, h->d_warm, h->d_best, h->d_params, h->d_controls, h->d_trajectory,
                      h->d_costs, h->d_fh };
     for (void* p : ptrs) if (p) cudaFree(p);

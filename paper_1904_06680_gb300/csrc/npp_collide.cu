@@ -30,6 +30,19 @@ int collide_resident_blocks_per_sm(int M, int variant)
     }
 }
 
+cudaError_t launch_collide_global(const RolloutArgs& a, cudaStream_t s)
+{
+    return launch_collide_slice_global<4, 4>(a, s);
+}
+
+int collide_global_blocks_per_sm()
+{
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, collide_slice_kernel<4, 4, true>, 128,
+                                                  CollideSliceKernel<4>::fixed_bytes());
+    return nb > 0 ? nb : 1;
+}
+
 int collide_max_points(int smem_limit)
 {
     return 2 * ((smem_limit - CollideResident::fixed_bytes()) / 32);

@@ -162,6 +162,8 @@ struct RolloutArgs {
     unsigned* work;                    // work-queue counter of the persistent collision kernel
     int grid_collide;                  // persistent grid size
     const LoopDev* dyn;                // when set, per-step scalars come from here
+    float4* pXY;                       // EV-frame point pairs in global memory (when the
+    float4* pV;                        // points exceed shared memory), [ceil(M/2)]
 };
 
 __device__ __forceinline__ StepIn step_in(const RolloutArgs& a)
@@ -202,6 +204,8 @@ cudaError_t launch_traj_w16(const RolloutArgs& a, cudaStream_t s, int variant);
 cudaError_t launch_traj_w32(const RolloutArgs& a, cudaStream_t s, int variant);
 cudaError_t launch_traj_w64(const RolloutArgs& a, cudaStream_t s, int variant);
 cudaError_t launch_collide_resident(const RolloutArgs& a, cudaStream_t s, int variant);
+cudaError_t launch_collide_global(const RolloutArgs& a, cudaStream_t s);
+int collide_global_blocks_per_sm();
 int collide_resident_blocks_per_sm(int M, int variant);
 int collide_max_points(int smem_limit);
 cudaError_t launch_epilogue(const EpilogueArgs& e, cudaStream_t s);

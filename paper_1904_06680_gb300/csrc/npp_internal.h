@@ -27,6 +27,8 @@ struct npp_handle {
     int collide_active;                  // variant used for the current launch
     int traj_variant;                    // 0: 2 hidden units per lane, 1: 4
     int occ_M, occ_blocks;               // cached occupancy for the last M
+    float4* d_pXY;                       // EV-frame point pairs when M exceeds shared memory
+    float4* d_pV;
     // host-mode staging
     float4* d_obs;
     float* d_warm;

@@ -118,12 +118,12 @@ __device__ __forceinline__ float wrap_pi(float a)
 // (an exact scaling).  |v| < 2 holds exactly when bit 30 of v's IEEE pattern
 // is clear, so "both inside" is bit 30 of (xi | eta) clear: one 3-input logic
 // op per point-sample pair accumulates "some point inside".
-__device__ __forceinline__ void write_coef(const RolloutArgs& a, const DevCfg& c, size_t idx,
-                                           float x, float y, float sp, float cp)
+__device__ __forceinline__ void write_coef(float4* coefA, float2* coefB, const DevCfg& c,
+                                           long long idx, float x, float y, float sp, float cp)
 {
     const float sl = 2.0f * c.ihl, sw = 2.0f * c.ihw;
-    a.coefA[idx] = make_float4(cp * sl, sp * sl, -((cp * x + sp * y + c.c_off) * sl), -sp * sw);
-    a.coefB[idx] = make_float2(cp * sw, -((-sp * x + cp * y) * sw));
+    coefA[idx] = make_float4(cp * sl, sp * sl, -((cp * x + sp * y + c.c_off) * sl), -sp * sw);
+    coefB[idx] = make_float2(cp * sw, -((-sp * x + cp * y) * sw));
 }
 
 // ------------------------------------------------------------------ traj
@@ -133,21 +133,34 @@ struct TrajKernel {
     static constexpr int B = THREADS / G;             // samples per block
 };
 
-template <int W, int G, int NW>
-__global__ void __launch_bounds__(NW * 32) traj_kernel(const RolloutArgs a)
+// One planning instance as the trajectory code sees it.  Records of sample n
+// at step h go to index h * rec_stride + n - rec_shift (states, controls);
+// coefficient rows to coef_base + h * N + n; the free cost to jfree[n].  Any
+// pointer may be null (nothing written).
+struct TrajJob {
+    StepIn si;
+    SamplerKey key;               // t_index resolved
+    const float* theta;           // explicit rows [N][n_theta] or null
+    const float* warm;            // replaces sample 0 when non-null (and si.warm_ok)
+    int N, T;
+    float4* traj;                 // [T+1] x stride
+    float2* ctrl;                 // [T] x stride
+    long long rec_stride, rec_shift;
+    float4* coefA;                // coefficient rows (scaled inequalities)
+    float2* coefB;
+    long long coef_base;
+    float* jfree;
+};
+
+// The trajectory of sample n (valid: n < N) computed by the G lanes of a
+// group (lane gl); hrow is the group's W-float shared exchange row.
+template <int W, int G>
+__device__ __forceinline__ void traj_sample(const DevCfg& c, const TrajJob& job, int n, bool valid,
+                                            int gl, float* hrow)
 {
     using S = Shape<W, G>;
     constexpr int U = S::U;
-    constexpr int B = TrajKernel<W, G, NW>::B;
-    __shared__ __align__(16) float hx_all[B * W];
-
-    const int tid = threadIdx.x;
-    const int b = tid / G, gl = tid % G;
-    const int n = blockIdx.x * B + b;
-    const bool valid = n < a.N;
-    const DevCfg& c = a.c;
-
-    const StepIn si = step_in(a);
+    const StepIn& si = job.si;
     float s0, c0;
     sincosf(si.phi0, &s0, &c0);
     const float gdx = si.gx - si.x0, gdy = si.gy - si.y0;
@@ -157,27 +170,26 @@ __global__ void __launch_bounds__(NW * 32) traj_kernel(const RolloutArgs a)
     LaneNet<W, G> net;
     {
         ThetaSrc src;
-        src.key = a.key;
-        src.key.t_index = si.t_index;
+        src.key = job.key;
         src.n = (uint32_t)(valid ? n : 0);
         src.mem = nullptr;
-        if (a.theta) src.mem = a.theta + (size_t)(valid ? n : 0) * S::NT;
-        else if (a.warm && n == 0 && si.warm_ok) src.mem = a.warm;
+        if (job.theta) src.mem = job.theta + (size_t)(valid ? n : 0) * S::NT;
+        else if (job.warm && n == 0 && si.warm_ok) src.mem = job.warm;
         net.load(src, gl);
     }
 
     float x = 0.f, y = 0.f, ph = 0.f, v = si.v0, ap0 = si.ap0, ap1 = si.ap1, E = 0.f;
-    const int T = a.T, N = a.N;
+    const int T = job.T, N = job.N;
     const float invT = 1.0f / (float)T;
-    float* hrow = hx_all + b * W;
     const bool writer = valid && gl == 0;
+    const long long rec = (long long)n - job.rec_shift;
 
     for (int h = 0; h < T; ++h) {
         float sp, cp;
         sincosf(ph, &sp, &cp);
         if (writer) {
-            a.traj[(size_t)h * N + n] = make_float4(x, y, ph, v);
-            write_coef(a, c, (size_t)h * N + n, x, y, sp, cp);
+            if (job.traj) job.traj[h * job.rec_stride + rec] = make_float4(x, y, ph, v);
+            if (job.coefA) write_coef(job.coefA, job.coefB, c, job.coef_base + (long long)h * N + n, x, y, sp, cp);
         }
         float s[NIN];
         s[0] = (gxi - x) * c.idxi;
@@ -238,7 +250,7 @@ __global__ void __launch_bounds__(NW * 32) traj_kernel(const RolloutArgs a)
         a0 = fminf(fmaxf(a0, -1.0f), 1.0f);
         const float a1 = ar1;
         E += a0 * a0 + a1 * a1;
-        if (writer) a.ctrl[(size_t)h * N + n] = make_float2(a0, a1);
+        if (writer && job.ctrl) job.ctrl[h * job.rec_stride + rec] = make_float2(a0, a1);
         const float td = tanf(c.delta_max * a0);
         const float tb = c.lrL * td;
         const float dv = c.Ts * v;
@@ -252,12 +264,41 @@ __global__ void __launch_bounds__(NW * 32) traj_kernel(const RolloutArgs a)
     if (writer) {
         float sp, cp;
         sincosf(ph, &sp, &cp);
-        a.traj[(size_t)T * N + n] = make_float4(x, y, ph, v);
-        write_coef(a, c, (size_t)T * N + n, x, y, sp, cp);
-        const float dx = x - gxi, dy = y - geta;
-        a.jfree[n] = c.w_pos * sqrtf(dx * dx + dy * dy) + c.w_phi * fabsf(wrap_pi(ph - gph))
-                   + c.w_v * fabsf(v - gv) + c.w_effort * E * invT;
+        if (job.traj) job.traj[T * job.rec_stride + rec] = make_float4(x, y, ph, v);
+        if (job.coefA) write_coef(job.coefA, job.coefB, c, job.coef_base + (long long)T * N + n, x, y, sp, cp);
+        if (job.jfree) {
+            const float dx = x - gxi, dy = y - geta;
+            job.jfree[n] = c.w_pos * sqrtf(dx * dx + dy * dy) + c.w_phi * fabsf(wrap_pi(ph - gph))
+                         + c.w_v * fabsf(v - gv) + c.w_effort * E * invT;
+        }
     }
+}
+
+template <int W, int G, int NW>
+__global__ void __launch_bounds__(NW * 32) traj_kernel(const RolloutArgs a)
+{
+    constexpr int B = TrajKernel<W, G, NW>::B;
+    __shared__ __align__(16) float hx_all[B * W];
+    const int tid = threadIdx.x;
+    const int b = tid / G, gl = tid % G;
+    const int n = blockIdx.x * B + b;
+    TrajJob job;
+    job.si = step_in(a);
+    job.key = a.key;
+    job.key.t_index = job.si.t_index;
+    job.theta = a.theta;
+    job.warm = a.warm;
+    job.N = a.N;
+    job.T = a.T;
+    job.traj = a.traj;
+    job.ctrl = a.ctrl;
+    job.rec_stride = a.N;
+    job.rec_shift = 0;
+    job.coefA = a.coefA;
+    job.coefB = a.coefB;
+    job.coef_base = 0;
+    job.jfree = a.jfree;
+    traj_sample<W, G>(a.c, job, n, n < a.N, gl, hx_all + b * W);
 }
 
 // ------------------------------------------------------------------ collide
@@ -687,15 +728,16 @@ struct CollideSliceKernel {
     static int smem_bytes(int M) { return ((M + 1) / 2) * 32 + fixed_bytes(); }
 };
 
-template <int S, int MINB>
+template <int S, int MINB, bool GLOBAL_PTS = false>
 __global__ void __launch_bounds__(S * 32, MINB) collide_slice_kernel(const RolloutArgs a)
 {
     using K = CollideSliceKernel<S>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int npairs = (a.M + 1) / 2;
-    float4* XY = reinterpret_cast<float4*>(smem_raw);
-    float4* V = XY + npairs;
-    float4* slotA = V + npairs;                                  // [S][8]
+    const int sp = GLOBAL_PTS ? 0 : npairs;                      // pairs held in shared memory
+    const float4* XY = GLOBAL_PTS ? a.pXY : reinterpret_cast<float4*>(smem_raw);
+    const float4* V = GLOBAL_PTS ? a.pV : reinterpret_cast<float4*>(smem_raw) + npairs;
+    float4* slotA = reinterpret_cast<float4*>(smem_raw) + 2 * sp;  // [S][8]
     float2* slotB = reinterpret_cast<float2*>(slotA + S * 8);    // [S][8]
     int* dead_at = reinterpret_cast<int*>(slotB + S * 8);        // [8]
     int* qslot = dead_at + 8;
@@ -704,7 +746,8 @@ __global__ void __launch_bounds__(S * 32, MINB) collide_slice_kernel(const Rollo
     const int warp = tid >> 5, lane = tid & 31;
     const DevCfg& c = a.c;
     const int T = a.T, N = a.N;
-    stage_points<K::THREADS>(a, XY, V);
+    if (!GLOBAL_PTS)
+        stage_points<K::THREADS>(a, reinterpret_cast<float4*>(smem_raw), reinterpret_cast<float4*>(smem_raw) + npairs);
     const int per = (npairs + S - 1) / S;
     const int q0 = min(npairs, warp * per), q1 = min(npairs, q0 + per);
     const int nslice = q1 - q0;
@@ -849,6 +892,47 @@ int collide_warp_blocks_per_sm(int M)
     if (ensure_smem(collide_warp_kernel<NW, MINB>, smem) != cudaSuccess) return 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, collide_warp_kernel<NW, MINB>, K::THREADS, smem);
     return nb > 0 ? nb : 1;
+}
+
+// EV-frame point pairs written to global memory (for point sets larger than
+// shared memory); same arithmetic as stage_points.
+static __global__ void transform_pairs_kernel(const RolloutArgs a)
+{
+    const int npairs = (a.M + 1) / 2;
+    const StepIn si = step_in(a);
+    float s0, c0;
+    sincosf(si.phi0, &s0, &c0);
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < npairs; q += gridDim.x * blockDim.x) {
+        float px[2], py[2], vx[2], vy[2];
+        for (int o = 0; o < 2; ++o) {
+            const int j = 2 * q + o;
+            px[o] = 1e15f; py[o] = 1e15f; vx[o] = 0.f; vy[o] = 0.f;
+            if (j < a.M) {
+                const float4 p = a.obs[j];
+                const float dx = p.x - si.x0, dy = p.y - si.y0;
+                px[o] = c0 * dx + s0 * dy;
+                py[o] = -s0 * dx + c0 * dy;
+                vx[o] = c0 * p.z + s0 * p.w;
+                vy[o] = -s0 * p.z + c0 * p.w;
+            }
+        }
+        a.pXY[q] = make_float4(px[0], px[1], py[0], py[1]);
+        a.pV[q] = make_float4(vx[0], vx[1], vy[0], vy[1]);
+    }
+}
+
+template <int S, int MINB>
+cudaError_t launch_collide_slice_global(const RolloutArgs& a, cudaStream_t stream)
+{
+    using K = CollideSliceKernel<S>;
+    const int npairs = (a.M + 1) / 2;
+    transform_pairs_kernel<<<max(1, min(1024, (npairs + 255) / 256)), 256, 0, stream>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int smem = K::fixed_bytes();
+    const int grid = max(1, min((a.N + 7) / 8, a.grid_collide));
+    collide_slice_kernel<S, MINB, true><<<grid, K::THREADS, smem, stream>>>(a);
+    return cudaGetLastError();
 }
 
 template <int S, int MINB>

@@ -52,6 +52,17 @@ class npp_loop_state(C.Structure):
         ("best_cost", C.c_float), ("reserved", C.c_int32 * 3)]
 
 
+class npp_scene(C.Structure):
+    _fields_ = [("state", npp_state), ("goal", npp_goal), ("N", C.c_int32), ("T", C.c_int32),
+                ("M", C.c_int32), ("width", C.c_int32), ("obs_offset", C.c_int64),
+                ("seed", C.c_uint64), ("t_index", C.c_uint32), ("reserved", C.c_int32)]
+
+
+class npp_batch_outputs(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("best", "params", "controls", "trajectory", "costs",
+                                          "first_hit")]
+
+
 class npp_outputs(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in ("best", "params", "controls", "trajectory", "costs",
                                           "first_hit", "sample_traj", "sample_ctrl")]
@@ -61,7 +72,8 @@ EXPORTS = ("npp_create", "npp_destroy", "npp_last_error", "npp_n_theta", "npp_pl
            "npp_plan_step_host", "npp_rollout_params", "npp_sample_params", "npp_set_timing",
            "npp_last_timing", "npp_set_option", "npp_plan_step_noalloc", "npp_loop_create",
            "npp_loop_run", "npp_loop_read", "npp_loop_log", "npp_loop_destroy", "npp_loop_samples",
-           "npp_loop_last_timing")
+           "npp_loop_last_timing", "npp_batch_create", "npp_batch_update", "npp_batch_offsets",
+           "npp_plan_batch", "npp_batch_destroy")
 
 _lib = None
 
@@ -97,6 +109,11 @@ def lib():
         L.npp_loop_destroy.argtypes = [P]
         L.npp_loop_samples.argtypes = [P, P, P]
         L.npp_loop_last_timing.argtypes = [P, C.POINTER(C.c_float), I32]
+        L.npp_batch_create.argtypes = [P, P, I32, C.POINTER(P)]
+        L.npp_batch_update.argtypes = [P, P]
+        L.npp_batch_offsets.argtypes = [P, P]
+        L.npp_plan_batch.argtypes = [P, P, C.POINTER(npp_batch_outputs), P]
+        L.npp_batch_destroy.argtypes = [P]
         L.npp_plan_step_noalloc.argtypes = [C.POINTER(npp_config), C.POINTER(npp_state),
                                             C.POINTER(npp_goal), P, I32, I32, I32, U64, U32, P,
                                             C.POINTER(npp_outputs), P]
@@ -265,6 +282,45 @@ def npp_loop_last_timing(L):
     t = (C.c_float * 4)()
     _check(lib().npp_loop_last_timing(L, t, 4))
     return dict(traj=t[0], collide=t[1], epilogue=t[2], total=t[3])
+
+
+def make_scenes(descs):
+    """descs: list of dicts with state, goal, N, T, M, width, obs_offset, seed,
+    t_index -> ctypes array of npp_scene."""
+    arr = (npp_scene * len(descs))()
+    for i, d in enumerate(descs):
+        arr[i].state = make_state(d["state"])
+        arr[i].goal = make_goal(d["goal"])
+        arr[i].N, arr[i].T, arr[i].M, arr[i].width = int(d["N"]), int(d["T"]), int(d["M"]), int(d["width"])
+        arr[i].obs_offset = int(d["obs_offset"])
+        arr[i].seed = int(d["seed"])
+        arr[i].t_index = int(d.get("t_index", 0))
+    return arr
+
+
+def npp_batch_create(h, scenes):
+    B = C.c_void_p()
+    _check(lib().npp_batch_create(h, C.cast(scenes, C.c_void_p), len(scenes), C.byref(B)), h)
+    return B
+
+
+def npp_batch_update(B, scenes):
+    return _check(lib().npp_batch_update(B, C.cast(scenes, C.c_void_p)))
+
+
+def npp_batch_offsets(B, S):
+    import numpy as np
+    off = np.zeros((S + 1, 4), np.int64)
+    _check(lib().npp_batch_offsets(B, off.ctypes.data_as(C.c_void_p)))
+    return off
+
+
+def npp_plan_batch(B, obs, out: npp_batch_outputs, stream=None):
+    return _check(lib().npp_plan_batch(B, _ptr(obs), C.byref(out), _stream(stream)))
+
+
+def npp_batch_destroy(B):
+    return lib().npp_batch_destroy(B)
 
 
 # ------------------------------------------------------------------ convenience

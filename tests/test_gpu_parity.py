@@ -206,6 +206,22 @@ def test_course_full_size(orc):
     assert ok.mean() >= 0.93, ok.mean()
 
 
+def test_large_point_set_from_global_memory(orc):
+    """More points than shared memory holds: the collision kernel reads an
+    L2-resident copy; every sample against the oracle."""
+    sc = inputs.tiny_scene(32, N=200, T=15, M=16001, width=16, box=120.0)
+    g = P.gpu_plan(sc)
+    idx = np.arange(sc["N"])
+    o = P.oracle_samples(sc, idx, record=False)
+    wc = P.winner_check(g, o["cost"], o["first_hit"])
+    assert wc["agree_frac"] >= 0.99, wc
+    assert 0 < np.sum(g["first_hit"] >= 0) < sc["N"]
+    if not wc.get("infeasible"):
+        assert wc["gpu_pick_oracle_cost"] <= wc["best_unambiguous"] * (1 + P.COST_RTOL) + P.COST_RTOL, wc
+    fs = P.flag_stats(sc, g, idx[:40])
+    assert not fs["bad"], fs["bad"][:5]
+
+
 def test_collide_variants_identical():
     """The launch variants of the collision and trajectory kernels compute
     the same values."""

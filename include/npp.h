@@ -128,8 +128,8 @@ npp_status npp_create(npp_handle** h, const npp_config* cfg, int32_t device);
 /* Free the handle and its workspaces (waits for its device work). */
 npp_status npp_destroy(npp_handle* h);
 
-/* Message for the last failing call on h (or a global message if h is NULL);
- * the pointer stays valid until the next call on the same handle. */
+/* Message for the last failing call on h; with h = NULL, the most recent
+ * failure of any call.  The pointer stays valid until the next failure. */
 const char* npp_last_error(const npp_handle* h);
 
 /* Number of network parameters of cfg's network, or -1 if unsupported. */
@@ -283,6 +283,12 @@ npp_status npp_batch_offsets(npp_batch* B, int64_t* offsets_host);
  * the [total points][4] world-frame obstacle array, 16-byte aligned. */
 npp_status npp_plan_batch(npp_batch* B, const float* obs_dev, const npp_batch_outputs* out,
                           void* stream);
+
+/* Launch shapes of the batch (no result changes): "slices" = warps that share
+ * one 8-sample collision item, each on a slice of the points (2, 4 or 8;
+ * default 4); "traj_warps" = warps per trajectory block (4 or 8; default 8).
+ * Synchronous (re-plans the work lists). */
+npp_status npp_batch_set_option(npp_batch* B, const char* name, int32_t value);
 
 /* Free the batch (after synchronising the device). */
 npp_status npp_batch_destroy(npp_batch* B);

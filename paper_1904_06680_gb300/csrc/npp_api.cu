@@ -24,7 +24,8 @@ npp_status fail(npp_handle* h, npp_status s, const char* fmt, ...)
     va_start(ap, fmt);
     vsnprintf(buf, sizeof buf, fmt, ap);
     va_end(ap);
-    if (h) h->err = buf; else g_err = buf;
+    if (h) h->err = buf;
+    g_err = buf;                       // npp_last_error(NULL): the most recent failure
     return s;
 }
 

@@ -364,12 +364,14 @@ struct npp_batch {
     int max_pairs;
     long long total_pairs, total_rows, total_samples;
     int grid_traj[3], grid_collide;
+    int slices;              // warps per collision item (point slices): 2, 4, 8
+    int traj_warps;          // warps per trajectory block: 4, 8
+    int smem_optin;
 };
 
 namespace {
 
-constexpr int BATCH_SLICES = 4;
-constexpr int TRAJ_NW = 8;
+constexpr int MAX_SLICES = 8;
 
 void free_batch(npp_batch* B)
 {
@@ -409,6 +411,86 @@ npp_status upload_scenes(npp_batch* B)
     return NPP_OK;
 }
 
+
+template <int S>
+cudaError_t collide_grid(npp_batch* B, int* grid)
+{
+    const int smem = B->resident_pairs * 32 + BatchCollide<S>::fixed_bytes();
+    cudaError_t e = ensure_smem(batch_collide_kernel<S>, smem);
+    int nb = 0;
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_collide_kernel<S>,
+                                                          BatchCollide<S>::THREADS, smem);
+    *grid = B->h->sm_count * std::max(1, nb);
+    return e;
+}
+
+template <int NW>
+void traj_grids(npp_batch* B)
+{
+    int nt = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nt, batch_traj_kernel<16, 8, NW>, NW * 32, 0);
+    B->grid_traj[0] = B->h->sm_count * std::max(1, nt);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nt, batch_traj_kernel<32, 16, NW>, NW * 32, 0);
+    B->grid_traj[1] = B->h->sm_count * std::max(1, nt);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nt, batch_traj_kernel<64, 32, NW>, NW * 32, 0);
+    B->grid_traj[2] = B->h->sm_count * std::max(1, nt);
+}
+
+// work order (costliest scenes first), item prefixes for the current block
+// shapes, persistent grids
+npp_status plan_work(npp_batch* B)
+{
+    npp_handle* h = B->h;
+    const int S = B->S;
+    const std::vector<npp_scene>& sc = B->scenes;
+    std::vector<int> order(S);
+    std::iota(order.begin(), order.end(), 0);
+    auto cost = [&](int i) { return (double)sc[i].N * (sc[i].T + 1) * (1.0 + sc[i].M); };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
+    std::vector<long long> cpre(S + 1, 0);
+    for (int r = 0; r < S; ++r) cpre[r + 1] = cpre[r] + (sc[order[r]].N + 7) / 8;
+    CUDA_TRY(h, cudaMemcpy(B->d_order, order.data(), sizeof(int) * S, cudaMemcpyHostToDevice));
+    CUDA_TRY(h, cudaMemcpy(B->d_citem_prefix, cpre.data(), sizeof(long long) * (S + 1), cudaMemcpyHostToDevice));
+    const int widths[3] = { 16, 32, 64 };
+    for (int w = 0; w < 3; ++w) {
+        const int Bsz = B->traj_warps * 32 / (widths[w] / 2);
+        std::vector<int> v;
+        for (int r = 0; r < S; ++r) if (sc[order[r]].width == widths[w]) v.push_back(order[r]);
+        std::stable_sort(v.begin(), v.end(), [&](int a, int b) {
+            return (double)sc[a].N * sc[a].T > (double)sc[b].N * sc[b].T; });
+        std::vector<long long> pre(v.size() + 1, 0);
+        for (size_t r = 0; r < v.size(); ++r) pre[r + 1] = pre[r] + (sc[v[r]].N + Bsz - 1) / Bsz;
+        B->n_torder[w] = (int)v.size();
+        if (!v.empty()) CUDA_TRY(h, cudaMemcpy(B->d_torder[w], v.data(), sizeof(int) * v.size(), cudaMemcpyHostToDevice));
+        CUDA_TRY(h, cudaMemcpy(B->d_titem_prefix[w], pre.data(), sizeof(long long) * pre.size(), cudaMemcpyHostToDevice));
+    }
+    cudaError_t e;
+    switch (B->slices) {
+    case 2: e = collide_grid<2>(B, &B->grid_collide); break;
+    case 8: e = collide_grid<8>(B, &B->grid_collide); break;
+    default: e = collide_grid<4>(B, &B->grid_collide); break;
+    }
+    if (e != cudaSuccess) return fail(h, NPP_CUDA_ERROR, "batch collision set-up: %s", cudaGetErrorString(e));
+    if (B->traj_warps == 4) traj_grids<4>(B); else traj_grids<8>(B);
+    return NPP_OK;
+}
+
+template <int S>
+void launch_batch_collide(npp_batch* B, const BatchArgs& b, cudaStream_t s)
+{
+    const int smem = B->resident_pairs * 32 + BatchCollide<S>::fixed_bytes();
+    batch_collide_kernel<S><<<B->grid_collide, BatchCollide<S>::THREADS, smem, s>>>(b);
+}
+
+template <int NW>
+void launch_batch_traj(npp_batch* B, const BatchArgs& b, cudaStream_t s)
+{
+    if (B->n_torder[0]) batch_traj_kernel<16, 8, NW><<<B->grid_traj[0], NW * 32, 0, s>>>(b, 0);
+    if (B->n_torder[1]) batch_traj_kernel<32, 16, NW><<<B->grid_traj[1], NW * 32, 0, s>>>(b, 1);
+    if (B->n_torder[2]) batch_traj_kernel<64, 32, NW><<<B->grid_traj[2], NW * 32, 0, s>>>(b, 2);
+}
+
 }  // namespace
 
 extern "C" {
@@ -446,38 +528,20 @@ npp_status npp_batch_create(npp_handle* h, const npp_scene* scenes, int32_t S, n
     B->max_pairs = max_pairs;
     int smem_optin = 0;
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
-    const int cap = (smem_optin - BatchCollide<BATCH_SLICES>::fixed_bytes()) / 32;
+    const int cap = (smem_optin - BatchCollide<MAX_SLICES>::fixed_bytes()) / 32;
     B->resident_pairs = std::min(max_pairs, cap);
 
-    // scenes by decreasing cost: all of them for collisions, per width for trajectories
-    std::vector<int> order(S);
-    std::iota(order.begin(), order.end(), 0);
-    auto cost = [&](int i) { return (double)scenes[i].N * (scenes[i].T + 1) * (1.0 + scenes[i].M); };
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
-    std::vector<long long> cpre(S + 1, 0);
-    for (int r = 0; r < S; ++r) cpre[r + 1] = cpre[r] + (scenes[order[r]].N + 7) / 8;
-    const int widths[3] = { 16, 32, 64 };
-    std::vector<int> tor[3];
-    std::vector<long long> tpre[3];
-    for (int w = 0; w < 3; ++w) {
-        const int Bsz = TRAJ_NW * 32 / (widths[w] / 2);
-        std::vector<int> v;
-        for (int r = 0; r < S; ++r) if (scenes[order[r]].width == widths[w]) v.push_back(order[r]);
-        std::stable_sort(v.begin(), v.end(), [&](int a, int b) {
-            return (double)scenes[a].N * scenes[a].T > (double)scenes[b].N * scenes[b].T; });
-        tor[w] = v;
-        tpre[w].assign(v.size() + 1, 0);
-        for (size_t r = 0; r < v.size(); ++r) tpre[w][r + 1] = tpre[w][r] + (scenes[v[r]].N + Bsz - 1) / Bsz;
-        B->n_torder[w] = (int)v.size();
-    }
+    B->smem_optin = smem_optin;
+    B->slices = 4;
+    B->traj_warps = 8;
     cudaError_t e = cudaSuccess;
     auto A = [&](void** p, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(p, bytes > 0 ? bytes : 16); };
     A((void**)&B->d_scenes, sizeof(SceneDev) * S);
     A((void**)&B->d_order, sizeof(int) * S);
     A((void**)&B->d_citem_prefix, sizeof(long long) * (S + 1));
     for (int w = 0; w < 3; ++w) {
-        A((void**)&B->d_torder[w], sizeof(int) * std::max<size_t>(1, tor[w].size()));
-        A((void**)&B->d_titem_prefix[w], sizeof(long long) * (tor[w].size() + 1));
+        A((void**)&B->d_torder[w], sizeof(int) * S);
+        A((void**)&B->d_titem_prefix[w], sizeof(long long) * (S + 1));
     }
     A((void**)&B->d_pXY, sizeof(float4) * std::max(1LL, pairs));
     A((void**)&B->d_pV, sizeof(float4) * std::max(1LL, pairs));
@@ -486,37 +550,13 @@ npp_status npp_batch_create(npp_handle* h, const npp_scene* scenes, int32_t S, n
     A((void**)&B->d_jfree, sizeof(float) * samples);
     A((void**)&B->d_keys, sizeof(unsigned long long) * S);
     A((void**)&B->d_counters, 64);
-    if (e == cudaSuccess) e = cudaMemcpy(B->d_order, order.data(), sizeof(int) * S, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(B->d_citem_prefix, cpre.data(), sizeof(long long) * (S + 1), cudaMemcpyHostToDevice);
-    for (int w = 0; w < 3 && e == cudaSuccess; ++w) {
-        if (!tor[w].empty()) e = cudaMemcpy(B->d_torder[w], tor[w].data(), sizeof(int) * tor[w].size(), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(B->d_titem_prefix[w], tpre[w].data(), sizeof(long long) * tpre[w].size(), cudaMemcpyHostToDevice);
-    }
     if (e != cudaSuccess) {
         free_batch(B);
-        return fail(h, NPP_CUDA_ERROR, "batch allocation/upload failed: %s", cudaGetErrorString(e));
+        return fail(h, NPP_CUDA_ERROR, "batch allocation failed: %s", cudaGetErrorString(e));
     }
     npp_status st = upload_scenes(B);
+    if (st == NPP_OK) st = plan_work(B);
     if (st != NPP_OK) { free_batch(B); return st; }
-    // persistent grids
-    const int smem = B->resident_pairs * 32 + BatchCollide<BATCH_SLICES>::fixed_bytes();
-    e = ensure_smem(batch_collide_kernel<BATCH_SLICES>, smem);
-    int nb = 0;
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_collide_kernel<BATCH_SLICES>,
-                                                          BatchCollide<BATCH_SLICES>::THREADS, smem);
-    B->grid_collide = h->sm_count * std::max(1, nb);
-    int nt = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nt, batch_traj_kernel<16, 8, TRAJ_NW>, TRAJ_NW * 32, 0);
-    B->grid_traj[0] = h->sm_count * std::max(1, nt);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nt, batch_traj_kernel<32, 16, TRAJ_NW>, TRAJ_NW * 32, 0);
-    B->grid_traj[1] = h->sm_count * std::max(1, nt);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nt, batch_traj_kernel<64, 32, TRAJ_NW>, TRAJ_NW * 32, 0);
-    B->grid_traj[2] = h->sm_count * std::max(1, nt);
-    if (e != cudaSuccess) {
-        free_batch(B);
-        return fail(h, NPP_CUDA_ERROR, "batch kernel set-up failed: %s", cudaGetErrorString(e));
-    }
     *out = B;
     return NPP_OK;
 }
@@ -600,19 +640,36 @@ npp_status npp_plan_batch(npp_batch* B, const float* obs_dev, const npp_batch_ou
         batch_prologue_kernel<<<grid, 256, 0, s>>>(b);
         CUDA_TRY(h, cudaGetLastError());
     }
-    if (B->n_torder[0]) batch_traj_kernel<16, 8, TRAJ_NW><<<B->grid_traj[0], TRAJ_NW * 32, 0, s>>>(b, 0);
-    if (B->n_torder[1]) batch_traj_kernel<32, 16, TRAJ_NW><<<B->grid_traj[1], TRAJ_NW * 32, 0, s>>>(b, 1);
-    if (B->n_torder[2]) batch_traj_kernel<64, 32, TRAJ_NW><<<B->grid_traj[2], TRAJ_NW * 32, 0, s>>>(b, 2);
+    if (B->traj_warps == 4) launch_batch_traj<4>(B, b, s); else launch_batch_traj<8>(B, b, s);
     CUDA_TRY(h, cudaGetLastError());
     if (h->timing) CUDA_TRY(h, record_event(h->ev[1], s));
-    const int smem = B->resident_pairs * 32 + BatchCollide<BATCH_SLICES>::fixed_bytes();
-    batch_collide_kernel<BATCH_SLICES><<<B->grid_collide, BatchCollide<BATCH_SLICES>::THREADS, smem, s>>>(b);
+    switch (B->slices) {
+    case 2: launch_batch_collide<2>(B, b, s); break;
+    case 8: launch_batch_collide<8>(B, b, s); break;
+    default: launch_batch_collide<4>(B, b, s); break;
+    }
     CUDA_TRY(h, cudaGetLastError());
     if (h->timing) CUDA_TRY(h, record_event(h->ev[2], s));
     batch_epilogue_kernel<<<B->S, 32, 0, s>>>(b);
     CUDA_TRY(h, cudaGetLastError());
     if (h->timing) CUDA_TRY(h, record_event(h->ev[3], s));
     return NPP_OK;
+}
+
+npp_status npp_batch_set_option(npp_batch* B, const char* name, int32_t value)
+{
+    if (!B || !name) return fail(B ? B->h : nullptr, NPP_INVALID_ARG, "batch: bad arguments");
+    if (std::strcmp(name, "slices") == 0) {
+        if (value != 2 && value != 4 && value != 8) return fail(B->h, NPP_INVALID_ARG, "slices is 2, 4 or 8");
+        B->slices = value;
+    } else if (std::strcmp(name, "traj_warps") == 0) {
+        if (value != 4 && value != 8) return fail(B->h, NPP_INVALID_ARG, "traj_warps is 4 or 8");
+        B->traj_warps = value;
+    } else {
+        return fail(B->h, NPP_INVALID_ARG, "unknown batch option '%s'", name);
+    }
+    CUDA_TRY(B->h, cudaSetDevice(B->h->device));
+    return plan_work(B);
 }
 
 npp_status npp_batch_destroy(npp_batch* B)

@@ -820,21 +820,14 @@ __global__ void __launch_bounds__(S * 32, MINB) collide_slice_kernel(const Rollo
 }
 
 // ------------------------------------------------------------------ launchers
+// opt in to more than 48 KB of dynamic shared memory for kernel fn (a host
+// call; repeated on every launch that needs it, since the setting is per
+// function and per device)
 template <typename KernelFn>
 inline cudaError_t ensure_smem(KernelFn fn, int smem)
 {
-    // opt in to large dynamic shared memory once per device (idempotent)
-    static int configured[64] = {0};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (smem > 48 * 1024 && configured[dev] < smem) {
-        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        configured[dev] = smem;
-    }
-    return cudaSuccess;
+    if (smem <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
 template <int W, int G, int NW>

@@ -12,6 +12,15 @@ Scene recipes (all world-frame, SI units; obstacles are (x, y, vx, vy)):
   200 static points uniform in a 40 x 40 m box centred on the start with none
   within 5 m of it, goal position uniform in the box, goal heading uniform,
   goal speed 0, start at rest with a random world pose.
+* ``scene_batch``: S independent reverse-parking instances (the slot of the
+  paper's Experiment 5, Fig. 8: curb line, a 5 x 5 m slot and a top wall,
+  resampled at 0.25 m and scaled 1.25x for the 4.5 m car), each at a random
+  world pose, with N = round(exp U[ln 1024, ln 65536]) rounded up to a
+  multiple of 32, T ~ U{20..80}, M = round(exp U[ln 100, ln 20000]) points
+  (the walls, parked-car outlines and a boundary wall, and 30 % of the points
+  on car outlines moving at |v| <= 3 m/s along a far lane), hidden width
+  uniform in {16, 32, 64}; start on the road at rest, goal at rest inside
+  the slot facing out.
 * ``scene_course``: the forward/reverse waypoint course of the paper's
   Experiment 4 (four waypoints at the corners of a square, heading turned by
   90 degrees at each) scaled 1.5x; 2000 points: 1000 on an outer wall, 500 on
@@ -164,3 +173,101 @@ def tiny_scene(seed: int, N: int, T: int, M: int, width: int = 16, box: float = 
     state = np.array([x0, y0, phi0, rng.uniform(-3, 3), rng.uniform(-1, 1), rng.uniform(-1, 1)])
     return dict(preset=planner(width), state=state, goal=goal, obs=obs, N=N, T=T,
                 seed=philox_seed(seed), t_index=int(rng.integers(0, 1000)))
+
+
+def _segment(a, b, spacing):
+    n = max(2, int(round(np.hypot(b[0] - a[0], b[1] - a[1]) / spacing)) + 1)
+    return np.stack([np.linspace(a[0], b[0], n), np.linspace(a[1], b[1], n)], 1)
+
+
+def parking_walls(scale: float = 1.25, spacing: float = 0.25) -> np.ndarray:
+    """Wall points of the Experiment 5 layout (curb y = -2 for |x| in
+    [2.5, 6.5], slot sides x = +-2.5 and bottom y = -7, top wall y = 6 for
+    |x| <= 4), resampled and scaled."""
+    segs = [((-6.5, -2), (-2.5, -2)), ((-2.5, -2), (-2.5, -7)), ((-2.5, -7), (2.5, -7)),
+            ((2.5, -7), (2.5, -2)), ((2.5, -2), (6.5, -2)), ((-4, 6), (4, 6))]
+    pts = [_segment(np.array(a) * scale, np.array(b) * scale, spacing) for a, b in segs]
+    return np.unique(np.round(np.concatenate(pts), 6), axis=0)
+
+
+def _car_outline(cx, cy, heading, spacing):
+    n = max(8, int(round(2 * (4.5 + 1.8) / spacing)))
+    return _square_outline(cx, cy, 2.25, 0.9, heading, n)
+
+
+def scene_batch(seed: int = 0, S: int = 512, width_choices=(16, 32, 64), N_range=(1024, 65536),
+                T_range=(20, 80), M_range=(100, 20000), dyn_frac: float = 0.3, vmax: float = 3.0):
+    """See the module docstring.  Points beyond the slot walls are structure,
+    not noise: parked-car outlines in rows left and right of the slot and
+    beyond the top wall, a boundary wall 30 m out, and (the moving 30 %) car
+    outlines driving along a far lane 10-14 m above the road; the road
+    between the curb and the top wall and the slot itself stay free.  Large
+    M densifies the outlines (smaller point spacing)."""
+    rng = np.random.default_rng(4000 + seed)
+    walls = parking_walls()
+    start_l = np.array([0.0, 2.0 * 1.25, 0.0])
+    goal_l = np.array([0.0, -5.0 * 1.25, math.pi / 2])
+    slots_x = [x for x in np.arange(-22.5, 23.0, 3.0) if abs(x) > 5.0]
+    scenes = []
+    obs_chunks = []
+    off = 0
+    for s in range(S):
+        N = int(round(math.exp(rng.uniform(math.log(N_range[0]), math.log(N_range[1])))))
+        N = max(32, 32 * ((N + 31) // 32))
+        T = int(rng.integers(T_range[0], T_range[1] + 1))
+        M = int(round(math.exp(rng.uniform(math.log(M_range[0]), math.log(M_range[1])))))
+        M = max(M, 1)
+        width = int(width_choices[rng.integers(0, len(width_choices))])
+        n_dyn = int(round(dyn_frac * M))
+        n_static = M - n_dyn
+        # static structure: slot walls first, then parked cars and boundary
+        # wall sharing the rest; densify until the count is reached
+        static = [walls]
+        rest = n_static - len(walls)
+        if rest > 0:
+            n_cars = len(slots_x) * 2
+            per_car = max(8, rest // (2 * n_cars))
+            spacing = 2 * (4.5 + 1.8) / per_car
+            cars = []
+            for x in slots_x:
+                cars.append(_car_outline(x, -4.6, math.pi / 2, spacing))      # along the curb
+                cars.append(_car_outline(x, 9.0, math.pi / 2, spacing))       # beyond the top wall
+            cars = np.concatenate(cars)
+            nb = max(0, rest - len(cars))
+            bound = _square_outline(0.0, 0.0, 30.0, 30.0, 0.0, max(nb, 4))
+            static += [cars, bound]
+        static = np.concatenate(static)
+        if len(static) >= n_static:
+            static = static[rng.permutation(len(static))[:n_static]] if n_static > len(walls) else walls[:n_static]
+        # moving car outlines on a far lane
+        dyn = np.zeros((0, 2))
+        dvel = np.zeros((0, 2))
+        if n_dyn:
+            n_mov = max(1, n_dyn // 60)
+            per = [n_dyn // n_mov + (1 if i < n_dyn % n_mov else 0) for i in range(n_mov)]
+            chunks, vels = [], []
+            for k in range(n_mov):
+                cx = rng.uniform(-25, 25)
+                cy = rng.uniform(11.0, 13.0)
+                sp = rng.uniform(0, vmax) * (1 if rng.random() < 0.5 else -1)
+                chunks.append(_square_outline(cx, cy, 2.25, 0.9, 0.0, per[k]))
+                vels.append(np.tile([sp, 0.0], (per[k], 1)))
+            dyn = np.concatenate(chunks)
+            dvel = np.concatenate(vels)
+        loc = np.concatenate([static, dyn])[:M]
+        vel = np.concatenate([np.zeros((len(static), 2)), dvel])[:M]
+        # random rigid placement of the layout in the world
+        ang = rng.uniform(-math.pi, math.pi)
+        tx, ty = rng.uniform(-500, 500, 2)
+        c, sn = math.cos(ang), math.sin(ang)
+        R = np.array([[c, -sn], [sn, c]])
+        obs = np.zeros((len(loc), 4))
+        obs[:, :2] = loc @ R.T + [tx, ty]
+        obs[:, 2:] = vel @ R.T
+        st = np.concatenate([R @ start_l[:2] + [tx, ty], [start_l[2] + ang, 0.0, 0.0, 0.0]])
+        gl = np.concatenate([R @ goal_l[:2] + [tx, ty], [goal_l[2] + ang, 0.0]])
+        scenes.append(dict(state=st, goal=gl, N=N, T=T, M=len(loc), width=width, obs_offset=off,
+                           seed=philox_seed(seed) + 7919 * s, t_index=0))
+        obs_chunks.append(obs)
+        off += len(loc)
+    return dict(preset=planner(32), scenes=scenes, obs=np.concatenate(obs_chunks))

@@ -73,7 +73,7 @@ EXPORTS = ("npp_create", "npp_destroy", "npp_last_error", "npp_n_theta", "npp_pl
            "npp_last_timing", "npp_set_option", "npp_plan_step_noalloc", "npp_loop_create",
            "npp_loop_run", "npp_loop_read", "npp_loop_log", "npp_loop_destroy", "npp_loop_samples",
            "npp_loop_last_timing", "npp_batch_create", "npp_batch_update", "npp_batch_offsets",
-           "npp_plan_batch", "npp_batch_destroy")
+           "npp_plan_batch", "npp_batch_destroy", "npp_batch_set_option")
 
 _lib = None
 
@@ -114,6 +114,7 @@ def lib():
         L.npp_batch_offsets.argtypes = [P, P]
         L.npp_plan_batch.argtypes = [P, P, C.POINTER(npp_batch_outputs), P]
         L.npp_batch_destroy.argtypes = [P]
+        L.npp_batch_set_option.argtypes = [P, C.c_char_p, I32]
         L.npp_plan_step_noalloc.argtypes = [C.POINTER(npp_config), C.POINTER(npp_state),
                                             C.POINTER(npp_goal), P, I32, I32, I32, U64, U32, P,
                                             C.POINTER(npp_outputs), P]
@@ -321,6 +322,10 @@ def npp_plan_batch(B, obs, out: npp_batch_outputs, stream=None):
 
 def npp_batch_destroy(B):
     return lib().npp_batch_destroy(B)
+
+
+def npp_batch_set_option(B, name: str, value: int):
+    return _check(lib().npp_batch_set_option(B, name.encode(), int(value)))
 
 
 # ------------------------------------------------------------------ convenience

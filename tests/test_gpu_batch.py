@@ -79,3 +79,59 @@ def test_batch_matches_single_plan_steps():
             np.testing.assert_allclose(t, r["trajectory"], rtol=1e-6, atol=1e-4)
     npp.npp_batch_destroy(B)
     pl.close()
+
+
+def test_batch_options_and_graph_replay_identical():
+    """Every launch shape the autotuner may pick, and a CUDA-graph capture of
+    the batch replayed twice, give the same results."""
+    import torch
+    from paper_1904_06680_gb300 import autotune, npp
+    b = inputs.scene_batch(5, S=24, N_range=(64, 2048), M_range=(20, 3000), T_range=(5, 30))
+    pl = npp.Planner(b["preset"], max_N=1, max_T=1, max_M=1)
+    scenes = npp.make_scenes(b["scenes"])
+    S = len(b["scenes"])
+    B = npp.npp_batch_create(pl.h, scenes)
+    off = npp.npp_batch_offsets(B, S)
+    best = torch.zeros(S * 8, dtype=torch.int32, device="cuda")
+    costs = torch.zeros(int(off[S, 3]), dtype=torch.float32, device="cuda")
+    fh = torch.zeros(int(off[S, 3]), dtype=torch.int32, device="cuda")
+    params = torch.zeros(int(off[S, 0]), dtype=torch.float32, device="cuda")
+    out = npp.npp_batch_outputs()
+    out.best, out.costs, out.first_hit, out.params = best.data_ptr(), costs.data_ptr(), fh.data_ptr(), params.data_ptr()
+    obs = torch.tensor(b["obs"], dtype=torch.float32, device="cuda")
+
+    def snap():
+        torch.cuda.synchronize()
+        return best.cpu().clone(), costs.cpu().clone(), fh.cpu().clone(), params.cpu().clone()
+
+    npp.npp_plan_batch(B, obs, out)
+    ref = snap()
+    assert 0 < int((ref[2] >= 0).sum()) < ref[2].numel()
+    for s, w in autotune.BATCH_CANDIDATES:
+        npp.npp_batch_set_option(B, "slices", s)
+        npp.npp_batch_set_option(B, "traj_warps", w)
+        for t in (best, costs, fh, params):
+            t.zero_()
+        npp.npp_plan_batch(B, obs, out)
+        got = snap()
+        for a, r in zip(got, ref):
+            assert torch.equal(a, r), (s, w)
+    choice, ms = autotune.tune_batch(B, obs, out, key="test24", reps=1)
+    assert tuple(choice) in autotune.BATCH_CANDIDATES and len(ms) == len(autotune.BATCH_CANDIDATES)
+    # capture in a CUDA graph on a side stream, replay twice
+    side = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=side):
+        npp.npp_plan_batch(B, obs, out, stream=torch.cuda.current_stream())
+    for _ in range(2):
+        for t in (best, costs, fh, params):
+            t.zero_()
+        g.replay()
+        got = snap()
+        for a, r in zip(got, ref):
+            assert torch.equal(a, r)
+    with pytest.raises(npp.NppError):
+        npp.npp_batch_set_option(B, "slices", 3)
+    npp.npp_batch_destroy(B)
+    pl.close()

@@ -56,9 +56,11 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="course", choices=["course", "batch"],
-                    help="course: the closed-loop course (default); batch: 512 parking scenes "
-                         "of uneven N, T, M and width in one graph-captured batch")
+    ap.add_argument("--workload", default="course", choices=["course", "large", "batch"],
+                    help="course: the closed-loop course (default); large: N=65536, T=100, "
+                         "8-64-64-2, 8192 points over 80x80 m with per-step spatial binning; "
+                         "batch: 512 parking scenes of uneven N, T, M and width in one "
+                         "graph-captured batch")
     return ap.parse_args()
 
 
@@ -127,10 +129,19 @@ class Clocks:
                 "reasons": sorted(reasons)}
 
 
-def course_setup(seed):
+COURSE_DESC = ("closed-loop forward/reverse waypoint course: N=16384 samples, T=40, MLP 8-32-32-2, "
+               "M=2000 points (500 moving), one plan step per sampling time")
+LARGE_DESC = ("closed loop in an 80x80 m area: N=65536 samples, T=100, MLP 8-64-64-2, M=8192 points "
+              "(20% moving, |v|<=5 m/s), per-step spatial binning of the points, one plan step per "
+              "sampling time")
+
+
+def workload_setup(name, seed):
+    """(scene, description) of a closed-loop workload."""
     from paper_1904_06680_gb300 import inputs
-    sc = inputs.scene_course(seed=seed)
-    return sc
+    if name == "large":
+        return inputs.scene_large(seed=seed), LARGE_DESC
+    return inputs.scene_course(seed=seed), COURSE_DESC
 
 
 def algorithmic_work(first_hit, T, M, W):
@@ -170,7 +181,7 @@ def profiled_traffic(kernel):
     return per.get(kernel.replace(" ", ""))
 
 
-def cpu_baseline(sc, state, goal, obs, T, target_cpu_s=15.0):
+def cpu_baseline(sc, state, goal, obs, T, workload, target_cpu_s=15.0):
     """Oracle (as it stands) on the host cores: a bounded sample of the first
     plan step's workload (sample indices 0..K-1; beyond N they are further
     Philox draws of the same distribution), every one over the full
@@ -192,9 +203,9 @@ def cpu_baseline(sc, state, goal, obs, T, target_cpu_s=15.0):
                         record=False)
     wall = time.perf_counter() - t0
     return {"value": K * T / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "first plan step of the course scene: %d samples (the step draws %d) over "
-                      "the full horizon T=%d, M=%d points, FP64 C with OpenMP (%.1f s wall)"
-                      % (K, sc["N"], T, obs.shape[0], wall)}
+            "sample": "first plan step of the %s scene: %d samples (the step draws %d) over "
+                      "the full horizon T=%d, M=%d points (brute force), FP64 C with OpenMP "
+                      "(%.1f s wall)" % (workload, K, sc["N"], T, obs.shape[0], wall)}
 
 
 def run_npp(args):
@@ -207,7 +218,7 @@ def run_npp(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    sc = course_setup(args.seed + rank)
+    sc, desc = workload_setup(args.workload, args.seed + rank)
     p = sc["preset"]
     N, T = sc["N"], sc["T"]
     W = p["widths"][1]
@@ -320,33 +331,53 @@ def run_npp(args):
     peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6
     fps_c = res["fma_c"] / (collide_ms / 1e3)
     fps_t = res["fma_t"] / (traj_ms / 1e3)
-    kname = ("collide_slice_kernel<4,4>" if N <= 8192 else
-             "collide_slice_kernel<2,8>" if N <= 32768 else "collide_warp_kernel<8,2>")
-    traffic = profiled_traffic(kname)
-    roofline = {"bound": "alu", "kernel": kname,
-                "achieved": fps_c / 1e12, "peak": peak / 1e12, "unit": "T FP32-FMA/s",
-                "frac": fps_c / peak,
-                "traffic": None if traffic is None else traffic,
-                "peak_basis": "derived: 152 SMs x 128 FP32 FMA lanes x 2070 MHz",
-                "kernel_ms_per_step": collide_ms / K,
-                "point_checks_per_s": res["checks"] / (collide_ms / 1e3),
-                "other": {"traj_kernel<32,16,8>": {"ms_per_step": traj_ms / K,
-                                                  "achieved": fps_t / 1e12, "frac": fps_t / peak}}}
+    binned = M >= 4096
+    if binned:
+        cname = "bin_build_kernel + collide_binned_kernel"
+    else:
+        cname = ("collide_slice_kernel<4,4>" if N <= 8192 else
+                 "collide_slice_kernel<2,8>" if N <= 32768 else "collide_warp_kernel<8,2>")
+    tname = "traj_kernel<%d,%d,8>" % (W, W // 2)
+    coll = {"ms_per_step": collide_ms / K, "point_checks_per_s": res["checks"] / (collide_ms / 1e3)}
+    trj = {"ms_per_step": traj_ms / K, "achieved": fps_t / 1e12, "frac": fps_t / peak}
+    if not binned:
+        coll.update(achieved=fps_c / 1e12, frac=fps_c / peak)
+    else:
+        coll["note"] = ("binned: checks only the points of the cells a state's bounding disk "
+                        "overlaps; point_checks_per_s counts the brute-force equivalent")
+    if binned and traj_ms >= collide_ms:
+        # the MLP rollout dominates once the collision check is binned
+        traffic = profiled_traffic(tname)
+        roofline = {"bound": "alu", "kernel": tname, "achieved": fps_t / 1e12, "peak": peak / 1e12,
+                    "unit": "T FP32-FMA/s", "frac": fps_t / peak, "traffic": traffic,
+                    "peak_basis": "derived: 152 SMs x 128 FP32 FMA lanes x 2070 MHz",
+                    "kernel_ms_per_step": traj_ms / K, "other": {cname: coll}}
+    else:
+        traffic = profiled_traffic(cname)
+        roofline = {"bound": "alu", "kernel": cname,
+                    "achieved": fps_c / 1e12, "peak": peak / 1e12, "unit": "T FP32-FMA/s",
+                    "frac": fps_c / peak,
+                    "traffic": None if traffic is None else traffic,
+                    "peak_basis": "derived: 152 SMs x 128 FP32 FMA lanes x 2070 MHz",
+                    "kernel_ms_per_step": collide_ms / K,
+                    "point_checks_per_s": res["checks"] / (collide_ms / 1e3),
+                    "other": {tname: trj}}
+        if binned:
+            roofline["note"] = coll["note"]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": Wu, "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "closed-loop forward/reverse waypoint course: N=16384 samples, "
-                                   "T=40, MLP 8-32-32-2, M=2000 points (500 moving), one plan "
-                                   "step per sampling time",
+            "config": {"workload": desc,
                        "N": N, "T": T, "M": M, "width": W, "parallelism": "replicas (rank = scene)",
                        "l2": "flushed (256 MiB write) between timed steps",
                        "timing": "sum of per-step CUDA-event durations (events captured in the "
                                  "step graph, replayed on the launching stream)"},
-            "roofline": roofline, "e2e": e2e, "gpu_launches": 5 * K, "clocks": ck,
+            "roofline": roofline, "e2e": e2e, "gpu_launches": (6 if binned else 5) * K, "clocks": ck,
             "free_fraction": float(np.mean(res["free"])),
             "waypoints_reached": res["waypoints_reached"], "infeasible_steps": res["n_infeasible"]}
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(sc, sc["state"], sc["waypoints"][0], sc["obs"], T)
+        line["cpu_baseline"] = cpu_baseline(sc, sc["state"], sc["waypoints"][0], sc["obs"], T,
+                                            args.workload)
     pl.close()
     if world > 1:
         import torch.distributed as dist
@@ -363,12 +394,12 @@ def run_reference(args):
         return
     from oracle import oracle as orc
     from paper_1904_06680_gb300 import closed_loop, inputs
-    sc = course_setup(args.seed)
+    sc, desc = workload_setup(args.workload, args.seed)
     p = sc["preset"]
     T = sc["T"]
     M = sc["obs"].shape[0]
     cores = os.cpu_count() or 1
-    Ns = 2048
+    Ns = 2048 if args.workload == "course" else 512
     state = sc["state"].copy()
     obs = sc["obs"].copy()
     mission = closed_loop.Mission(sc["waypoints"], inputs.EPS)
@@ -390,11 +421,10 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "closed-loop forward/reverse waypoint course: T=40, MLP "
-                                   "8-32-32-2, M=2000 points (500 moving)", "N": Ns, "T": T, "M": M},
+            "config": {"workload": desc, "N": sc["N"], "T": T, "M": M},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": "%d samples per plan step (of 16384) over the full horizon, "
-                                       "FP64 C oracle with OpenMP" % Ns},
+                             "sample": "%d samples per plan step (of %d) over the full horizon, "
+                                       "FP64 C oracle with OpenMP" % (Ns, sc["N"])},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -493,6 +523,8 @@ def run_batch(args):
 def main():
     args = parse()
     if args.impl == "reference":
+        if args.workload == "batch":
+            args.workload = "course"
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)

@@ -318,11 +318,16 @@ npp_status npp_plan_step_noalloc(const npp_config* cfg, const npp_state* state,
                                  const float* warm_dev, const npp_outputs* out, void* stream);
 
 /* Launch options that do not change any result (they choose among kernels
- * computing identical values).  "collide_variant" in -1..2: 0 the
+ * computing identical values).  "collide_variant" in -1..5: 0 the
  * block-balanced collision kernel with 16 warps and one block per SM, 1 the
  * same with 8 warps and two blocks per SM, 2 warp-owned items of 8 samples,
  * 3 / 4 items of 8 samples checked by 4 / 2 warps each taking a slice of the
- * points, -1 (default) chooses by the number of samples.
+ * points, 5 per-step spatial binning: the points extrapolated to each step
+ * are counting-sorted into a uniform grid around the vehicle and each state
+ * is tested only against the cells its bounding disk overlaps (the same
+ * per-point test, so the same flags as checking every point); -1 (default)
+ * takes 5 from M = 4096 points and otherwise chooses by the number of
+ * samples.
  * "traj_variant" 0 or 1: the trajectory kernel holds 2 (0, default) or 4 (1)
  * hidden units per lane.
  * Returns NPP_INVALID_ARG for an unknown name or value. */

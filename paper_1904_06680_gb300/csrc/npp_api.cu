@@ -147,9 +147,18 @@ npp_status run_rollout(npp_handle* h, RolloutArgs& a, cudaStream_t s)
     a.work = h->d_work;
     // automatic choice (measured on GB300, course workload): few samples ->
     // items checked by 4 warps on point slices; medium -> 2 warps; many
-    // samples -> one warp per item keeps enough items in flight
+    // samples -> one warp per item keeps enough items in flight; many points
+    // -> spatial binning
     const int v = h->collide_variant >= 0 ? h->collide_variant
-                : (a.N <= 8192 ? 3 : (a.N <= 32768 ? 4 : 2));
+                : (a.M >= BINNED_AUTO_M ? COLLIDE_BINNED : (a.N <= 8192 ? 3 : (a.N <= 32768 ? 4 : 2)));
+    if (v == COLLIDE_BINNED) {
+        if (h->timing) CUDA_TRY(h, record_event(h->ev[0], s));
+        CUDA_TRY(h, launch_traj(h, a, s));
+        if (h->timing) CUDA_TRY(h, record_event(h->ev[1], s));
+        CUDA_TRY(h, launch_collide_binned(a, h->cfg.half_len, h->cfg.half_wid, h->cfg.c_off, h->d_bins, s));
+        if (h->timing) CUDA_TRY(h, record_event(h->ev[2], s));
+        return NPP_OK;
+    }
     // points beyond shared memory: point-sliced kernel on an L2-resident copy
     const bool global_pts = a.M > h->max_points;
     if (global_pts) {
@@ -299,6 +308,7 @@ npp_status npp_create(npp_handle** out, const npp_config* cfg, int32_t device)
     A((void**)&h->d_coefA, NT1 * sizeof(float4));
     A((void**)&h->d_coefB, NT1 * sizeof(float2));
     A((void**)&h->d_work, 64);
+    A(&h->d_bins, binned_workspace_bytes(cfg->max_T, cfg->max_M));
     if (cfg->max_M > max_points) {
         A((void**)&h->d_pXY, (size_t)(cfg->max_M / 2 + 1) * sizeof(float4));
         A((void**)&h->d_pV, (size_t)(cfg->max_M / 2 + 1) * sizeof(float4));
@@ -328,7 +338,7 @@ npp_status npp_destroy(npp_handle* h)
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
     void* ptrs[] = { h->d_key, h->d_traj, h->d_ctrl, h->d_jfree, h->d_coefA, h->d_coefB, h->d_work,
-                     h->d_pXY, h->d_pV,
+                     h->d_pXY, h->d_pV, h->d_bins,
                      h->d_obs, h->d_warm, h->d_best, h->d_params, h->d_controls, h->d_trajectory,
                      h->d_costs, h->d_fh };
     for (void* p : ptrs) if (p) cudaFree(p);
@@ -456,7 +466,8 @@ npp_status npp_set_option(npp_handle* h, const char* name, int32_t value)
 {
     if (!h || !name) return fail(h, NPP_INVALID_ARG, "handle and name must not be NULL");
     if (std::strcmp(name, "collide_variant") == 0) {
-        if (value < -1 || value > 4) return fail(h, NPP_INVALID_ARG, "collide_variant is -1..4");
+        if (value < -1 || value > COLLIDE_BINNED)
+            return fail(h, NPP_INVALID_ARG, "collide_variant is -1..%d", COLLIDE_BINNED);
         h->collide_variant = value;
         h->occ_M = -1;
         return NPP_OK;

@@ -100,12 +100,7 @@ __global__ void batch_prologue_kernel(const BatchArgs b)
             const int j = 2 * q + o;
             px[o] = 1e15f; py[o] = 1e15f; vx[o] = 0.f; vy[o] = 0.f;
             if (j < s.M) {
-                const float4 p = b.obs[s.obs_off + j];
-                const float dx = p.x - s.x0, dy = p.y - s.y0;
-                px[o] = cs * dx + sn * dy;
-                py[o] = -sn * dx + cs * dy;
-                vx[o] = cs * p.z + sn * p.w;
-                vy[o] = -sn * p.z + cs * p.w;
+                ev_point(b.obs[s.obs_off + j], s.x0, s.y0, sn, cs, px[o], py[o], vx[o], vy[o]);
             }
         }
         b.pXY[s.pair_off + q] = make_float4(px[0], px[1], py[0], py[1]);

@@ -1,0 +1,203 @@
+// npp_binned.cu -- collision checks through per-timestep spatial binning.
+//
+// For every horizon step h the obstacle points at time h Ts (EV frame,
+// p + tau v with the brute-force kernels' arithmetic) are counting-sorted into
+// a uniform grid of BIN_DIM x BIN_DIM cells centred on the vehicle.  A cell is
+// wider than the diameter of the vehicle rectangle's circumscribed disk, so
+// a state's disk overlaps at most 2 x 2 cells (3 x 3 with the safety margin);
+// every point inside the rectangle lies in the disk, and cell indices of
+// points and of the query are clamped to the grid the same (monotone) way,
+// so the queried cells hold every point that can be inside.  The per-point
+// test is the brute-force one (same coefficients, same fma sequence), hence
+// the collision flags are identical to checking all points.
+#include <cmath>
+
+#include <cuda_runtime.h>
+
+#include "../../include/npp.h"
+#include "npp_rollout.cuh"
+
+using namespace npp;
+
+namespace {
+
+constexpr int BIN_DIM = 128;
+constexpr int NCELL = BIN_DIM * BIN_DIM;
+constexpr int BIN_THREADS = 1024;
+// ints per step of the cell-start table: NCELL + 1 entries padded to a
+// multiple of 16 bytes, so that the float2 point arrays after the tables
+// stay 8-byte aligned for every T
+constexpr int CS_STRIDE = NCELL + 4;
+
+struct BinGrid {
+    float x0, y0;          // lower-left corner of the grid (EV frame)
+    float inv_cell, cell;
+    float reach;           // disk radius + margin used by the query
+};
+
+__device__ __forceinline__ int cell_ix(float x, const BinGrid& g)
+{
+    const float f = floorf((x - g.x0) * g.inv_cell);
+    return (int)fminf(fmaxf(f, 0.0f), (float)(BIN_DIM - 1));
+}
+
+// one block per horizon step: cell counts (shared), exclusive scan, scatter
+__global__ void __launch_bounds__(BIN_THREADS) bin_build_kernel(const RolloutArgs a, BinGrid g,
+                                                                int* __restrict__ cell_start,
+                                                                float2* __restrict__ binned)
+{
+    extern __shared__ int cnt[];             // [NCELL]
+    const int h = blockIdx.x;
+    const int M = a.M;
+    const float tau = (float)h * a.c.Ts;
+    const StepIn si = step_in(a);
+    float s0, c0;
+    sincosf(si.phi0, &s0, &c0);
+    for (int i = threadIdx.x; i < NCELL; i += blockDim.x) cnt[i] = 0;
+    __syncthreads();
+    for (int j = threadIdx.x; j < M; j += blockDim.x) {
+        float ex, ey, evx, evy;
+        ev_point(a.obs[j], si.x0, si.y0, s0, c0, ex, ey, evx, evy);
+        const float px = fmaf(tau, evx, ex), py = fmaf(tau, evy, ey);
+        atomicAdd(&cnt[cell_ix(py, g) * BIN_DIM + cell_ix(px, g)], 1);
+    }
+    __syncthreads();
+    // exclusive scan of NCELL counts: each thread scans a contiguous run,
+    // then the run totals are scanned by warp 0
+    __shared__ int run_tot[BIN_THREADS];
+    constexpr int RUN = NCELL / BIN_THREADS;
+    const int base = threadIdx.x * RUN;
+    int acc = 0;
+    for (int k = 0; k < RUN; ++k) { const int v = cnt[base + k]; cnt[base + k] = acc; acc += v; }
+    run_tot[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        // warp 0 scans the BIN_THREADS run totals (32 per lane)
+        constexpr int PER = BIN_THREADS / 32;
+        int local = 0;
+        for (int k = 0; k < PER; ++k) local += run_tot[threadIdx.x * PER + k];
+        int incl = local;
+        for (int off = 1; off < 32; off <<= 1) {
+            const int v = __shfl_up_sync(FULL, incl, off);
+            if ((int)threadIdx.x >= off) incl += v;
+        }
+        int run = incl - local;
+        for (int k = 0; k < PER; ++k) {
+            const int v = run_tot[threadIdx.x * PER + k];
+            run_tot[threadIdx.x * PER + k] = run;
+            run += v;
+        }
+    }
+    __syncthreads();
+    for (int k = 0; k < RUN; ++k) cnt[base + k] += run_tot[threadIdx.x];
+    __syncthreads();
+    int* cs = cell_start + (size_t)h * CS_STRIDE;
+    for (int i = threadIdx.x; i < NCELL; i += blockDim.x) cs[i] = cnt[i];
+    if (threadIdx.x == 0) cs[NCELL] = M;
+    __syncthreads();
+    // scatter (order within a cell is arbitrary; the test is an OR)
+    float2* out = binned + (size_t)h * M;
+    for (int j = threadIdx.x; j < M; j += blockDim.x) {
+        float ex, ey, evx, evy;
+        ev_point(a.obs[j], si.x0, si.y0, s0, c0, ex, ey, evx, evy);
+        const float px = fmaf(tau, evx, ex), py = fmaf(tau, evy, ey);
+        const int pos = atomicAdd(&cnt[cell_ix(py, g) * BIN_DIM + cell_ix(px, g)], 1);
+        out[pos] = make_float2(px, py);
+    }
+}
+
+// one thread per sample, h in order; candidates from the cells the state's
+// disk overlaps
+__global__ void __launch_bounds__(256) collide_binned_kernel(const RolloutArgs a, BinGrid g,
+                                                             const int* __restrict__ cell_start,
+                                                             const float2* __restrict__ binned)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __shared__ unsigned long long red[8];
+    const int T = a.T, N = a.N, M = a.M;
+    unsigned long long key = ~0ull;
+    if (n < N) {
+        int fh = -1;
+        for (int h = 0; h <= T && fh < 0; ++h) {
+            const size_t idx = (size_t)h * N + n;
+            const float4 ca = a.coefA[idx];
+            const float2 cb = a.coefB[idx];
+            // the rectangle lies in the disk of radius reach around the
+            // reference point (reach covers the centre offset)
+            const float4 z = a.traj[idx];
+            const int ix0 = cell_ix(z.x - g.reach, g), ix1 = cell_ix(z.x + g.reach, g);
+            const int iy0 = cell_ix(z.y - g.reach, g), iy1 = cell_ix(z.y + g.reach, g);
+            const int* cs = cell_start + (size_t)h * CS_STRIDE;
+            const float2* pts = binned + (size_t)h * M;
+            bool inside = false;
+            for (int iy = iy0; iy <= iy1 && !inside; ++iy) {
+                const int b0 = cs[iy * BIN_DIM + ix0], b1 = cs[iy * BIN_DIM + ix1 + 1];
+                for (int k = b0; k < b1; ++k) {
+                    const float2 p = pts[k];
+                    const float xi = fmaf(ca.x, p.x, fmaf(ca.y, p.y, ca.z));
+                    const float et = fmaf(ca.w, p.x, fmaf(cb.x, p.y, cb.y));
+                    if (!(((__float_as_uint(xi) | __float_as_uint(et)) >> 30) & 1u)) { inside = true; break; }
+                }
+            }
+            if (inside) fh = h;
+        }
+        float J = __int_as_float(0x7f800000);
+        if (fh < 0) {
+            J = a.jfree[n];
+            key = ((unsigned long long)__float_as_uint(J) << 32) | (unsigned)n;
+        } else {
+            key = (1ull << 63) | ((unsigned long long)(T - fh) << 32) | (unsigned)n;
+        }
+        if (a.costs) a.costs[n] = J;
+        if (a.first_hit) a.first_hit[n] = fh;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(FULL, key, off);
+        key = o < key ? o : key;
+    }
+    if (lane == 0) red[warp] = key;
+    __syncthreads();
+    if (threadIdx.x == 0 && a.best_key) {
+        unsigned long long k = red[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) k = red[w] < k ? red[w] : k;
+        atomicMin(a.best_key, k);
+    }
+}
+
+}  // namespace
+
+namespace npp {
+
+// bytes of the per-step grids: (T+1) cell-start tables and (T+1) x M points
+size_t binned_workspace_bytes(int max_T, int max_M)
+{
+    return (size_t)(max_T + 1) * CS_STRIDE * sizeof(int) + (size_t)(max_T + 1) * max_M * sizeof(float2);
+}
+
+cudaError_t launch_collide_binned(const RolloutArgs& a, float half_len, float half_wid, float c_off,
+                                  void* workspace, cudaStream_t s)
+{
+    BinGrid g;
+    const double R = std::sqrt((double)half_len * half_len + (double)half_wid * half_wid)
+                   + std::fabs((double)c_off);
+    const double cell = 2.0 * R + 0.25;
+    g.cell = (float)cell;
+    g.inv_cell = (float)(1.0 / cell);
+    g.x0 = (float)(-0.5 * BIN_DIM * cell);
+    g.y0 = g.x0;
+    g.reach = (float)(R + 0.05);           // margin against rounding (positions are O(100) m)
+    int* cell_start = static_cast<int*>(workspace);
+    float2* binned = reinterpret_cast<float2*>(cell_start + (size_t)(a.T + 1) * CS_STRIDE);
+    const int smem = NCELL * (int)sizeof(int);
+    cudaError_t e = ensure_smem(bin_build_kernel, smem);
+    if (e != cudaSuccess) return e;
+    bin_build_kernel<<<a.T + 1, BIN_THREADS, smem, s>>>(a, g, cell_start, binned);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    collide_binned_kernel<<<(a.N + 255) / 256, 256, 0, s>>>(a, g, cell_start, binned);
+    return cudaGetLastError();
+}
+
+}  // namespace npp

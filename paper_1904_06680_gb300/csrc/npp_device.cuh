@@ -208,6 +208,12 @@ cudaError_t launch_collide_global(const RolloutArgs& a, cudaStream_t s);
 int collide_global_blocks_per_sm();
 int collide_resident_blocks_per_sm(int M, int variant);
 int collide_max_points(int smem_limit);
+// collisions through per-step spatial binning of the points (any M): builds
+// the grids in `workspace` (binned_workspace_bytes) and checks every sample
+// against the points of the cells its bounding disk overlaps
+size_t binned_workspace_bytes(int max_T, int max_M);
+cudaError_t launch_collide_binned(const RolloutArgs& a, float half_len, float half_wid, float c_off,
+                                  void* workspace, cudaStream_t s);
 cudaError_t launch_epilogue(const EpilogueArgs& e, cudaStream_t s);
 void set_global_error(const char* msg);
 

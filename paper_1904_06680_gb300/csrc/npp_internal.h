@@ -9,6 +9,11 @@
 #include "../../include/npp.h"
 #include "npp_device.cuh"
 
+// collision-kernel variant number of the spatially binned check, and the
+// point count from which the automatic choice takes it
+constexpr int COLLIDE_BINNED = 5;
+constexpr int BINNED_AUTO_M = 4096;
+
 struct npp_handle {
     npp_config cfg;
     int device;
@@ -24,11 +29,13 @@ struct npp_handle {
     unsigned* d_work;                    // persistent-kernel work counter
     int sm_count;
     int collide_variant;                 // -1 automatic, else a fixed collision-kernel variant
+                                         // (0..4 brute force, 5 spatially binned)
     int collide_active;                  // variant used for the current launch
     int traj_variant;                    // 0: 2 hidden units per lane, 1: 4
     int occ_M, occ_blocks;               // cached occupancy for the last M
     float4* d_pXY;                       // EV-frame point pairs when M exceeds shared memory
     float4* d_pV;
+    void* d_bins;                        // per-step spatial grids of the binned collision check
     // host-mode staging
     float4* d_obs;
     float* d_warm;

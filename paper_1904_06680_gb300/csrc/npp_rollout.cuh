@@ -363,6 +363,19 @@ __device__ __forceinline__ unsigned check_unit(const float4* __restrict__ XY, co
     return bits;
 }
 
+// Obstacle point o = (x, y, vx, vy) in the EV frame of the plan step (origin
+// (x0, y0), heading with sine s0 and cosine c0), rounding fixed by explicit
+// fmas so every collision path sees the same FP32 positions.
+__device__ __forceinline__ void ev_point(const float4& o, float x0, float y0, float s0, float c0,
+                                         float& px, float& py, float& vx, float& vy)
+{
+    const float dx = o.x - x0, dy = o.y - y0;
+    px = fmaf(c0, dx, __fmul_rn(s0, dy));
+    py = fmaf(-s0, dx, __fmul_rn(c0, dy));
+    vx = fmaf(c0, o.z, __fmul_rn(s0, o.w));
+    vy = fmaf(-s0, o.z, __fmul_rn(c0, o.w));
+}
+
 // Staging of the points in the EV frame as pairs; an odd tail is padded with
 // a point 1e15 m away (never inside).
 template <int THREADS>
@@ -377,12 +390,7 @@ __device__ __forceinline__ int stage_points(const RolloutArgs& a, float4* XY, fl
     for (int j = threadIdx.x; j < 2 * npairs; j += THREADS) {
         float px = 1e15f, py = 1e15f, vx = 0.f, vy = 0.f;
         if (j < a.M) {
-            const float4 o = a.obs[j];
-            const float dx = o.x - si.x0, dy = o.y - si.y0;
-            px = c0 * dx + s0 * dy;
-            py = -s0 * dx + c0 * dy;
-            vx = c0 * o.z + s0 * o.w;
-            vy = -s0 * o.z + c0 * o.w;
+            ev_point(a.obs[j], si.x0, si.y0, s0, c0, px, py, vx, vy);
         }
         const int q = j >> 1, o2 = j & 1;
         xy[4 * q + o2] = px;
@@ -901,12 +909,7 @@ static __global__ void transform_pairs_kernel(const RolloutArgs a)
             const int j = 2 * q + o;
             px[o] = 1e15f; py[o] = 1e15f; vx[o] = 0.f; vy[o] = 0.f;
             if (j < a.M) {
-                const float4 p = a.obs[j];
-                const float dx = p.x - si.x0, dy = p.y - si.y0;
-                px[o] = c0 * dx + s0 * dy;
-                py[o] = -s0 * dx + c0 * dy;
-                vx[o] = c0 * p.z + s0 * p.w;
-                vy[o] = -s0 * p.z + c0 * p.w;
+                ev_point(a.obs[j], si.x0, si.y0, s0, c0, px[o], py[o], vx[o], vy[o]);
             }
         }
         a.pXY[q] = make_float4(px[0], px[1], py[0], py[1]);

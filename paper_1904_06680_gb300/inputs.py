@@ -26,6 +26,13 @@ Scene recipes (all world-frame, SI units; obstacles are (x, y, vx, vy)):
   90 degrees at each) scaled 1.5x; 2000 points: 1000 on an outer wall, 500 on
   a central island, 500 on ten moving car-sized outlines with speeds uniform
   in [0, 3] m/s at uniform headings.  N = 16384, T = 40, 8-32-32-2.
+* ``scene_large``: N = 65536, T = 100, 8-64-64-2, 8192 points over an
+  80 x 80 m area centred on the start: a boundary wall at 0.25 m spacing,
+  parked-car outlines at uniform positions and headings (none within 8 m of
+  the start or 5 m of the goal), and 20 % of the points on moving car
+  outlines with speeds uniform in [0, 5] m/s at uniform headings (none
+  starting within 10 m of the start).  Start at the origin at rest facing
+  +x; waypoints 30 m out.
 """
 import math
 
@@ -145,6 +152,50 @@ def scene_course(seed: int = 0, N: int = 16384, T: int = 40, width: int = 32,
     state = np.array([0.0, 0.0, 0.0, 0.0, 0.0, 0.0])
     return dict(preset=planner(width), state=state, goal=COURSE_WAYPOINTS[0].copy(), obs=obs,
                 N=N, T=T, seed=philox_seed(seed), t_index=0, waypoints=COURSE_WAYPOINTS.copy())
+
+
+LARGE_WAYPOINTS = np.array([
+    [30.0, 8.0, 0.0, 0.0],
+    [30.0, 30.0, math.pi / 2, 0.0],
+])
+
+
+def scene_large(seed: int = 0, N: int = 65536, T: int = 100, width: int = 64, M: int = 8192,
+                dyn_frac: float = 0.2, vmax: float = 5.0, n_parked: int = 50, area: float = 80.0):
+    rng = np.random.default_rng(5000 + seed)
+    half = area / 2
+    n_dyn = int(round(dyn_frac * M))
+    n_static = M - n_dyn
+    wall = _square_outline(0.0, 0.0, half, half, 0.0, min(n_static // 4, int(round(4 * area / 0.25))))
+    rest = n_static - len(wall)
+    per = [rest // n_parked + (1 if i < rest % n_parked else 0) for i in range(n_parked)]
+    goal = LARGE_WAYPOINTS[0]
+    parked = []
+    for k in range(n_parked):
+        while True:
+            c = rng.uniform(-half + 3.0, half - 3.0, 2)
+            if np.hypot(*c) > 8.0 and np.hypot(c[0] - goal[0], c[1] - goal[1]) > 5.0:
+                break
+        parked.append(_square_outline(c[0], c[1], 2.25, 0.9, rng.uniform(-math.pi, math.pi), per[k]))
+    n_mov = max(1, n_dyn // 100)
+    perm = [n_dyn // n_mov + (1 if i < n_dyn % n_mov else 0) for i in range(n_mov)]
+    dyn, vel = [], []
+    for k in range(n_mov):
+        while True:
+            c = rng.uniform(-half + 3.0, half - 3.0, 2)
+            if np.hypot(*c) > 10.0:
+                break
+        sp = rng.uniform(0.0, vmax)
+        vh = rng.uniform(-math.pi, math.pi)
+        dyn.append(_square_outline(c[0], c[1], 2.25, 0.9, rng.uniform(-math.pi, math.pi), perm[k]))
+        vel.append(np.tile([sp * math.cos(vh), sp * math.sin(vh)], (perm[k], 1)))
+    obs = np.zeros((M, 4))
+    obs[:n_static, :2] = np.concatenate([wall] + parked)
+    obs[n_static:, :2] = np.concatenate(dyn)
+    obs[n_static:, 2:] = np.concatenate(vel)
+    state = np.array([0.0, 0.0, 0.0, 0.0, 0.0, 0.0])
+    return dict(preset=planner(width), state=state, goal=goal.copy(), obs=obs, N=N, T=T,
+                seed=philox_seed(seed), t_index=0, waypoints=LARGE_WAYPOINTS.copy())
 
 
 def tiny_scene(seed: int, N: int, T: int, M: int, width: int = 16, box: float = 12.0,

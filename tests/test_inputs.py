@@ -1,0 +1,59 @@
+"""The seeded workload generators produce the stated shapes, sizes and value
+distributions (CPU only)."""
+import math
+
+import numpy as np
+
+from paper_1904_06680_gb300 import inputs
+
+
+def test_scene_single_recipe():
+    sc = inputs.scene_single(3)
+    o, s = sc["obs"], sc["state"]
+    assert o.shape == (200, 4) and sc["N"] == 256 and sc["T"] == 20
+    d = o[:, :2] - s[:2]
+    assert np.all(np.abs(d) <= 20.0) and np.all(np.hypot(d[:, 0], d[:, 1]) >= 5.0)
+    assert np.all(o[:, 2:] == 0.0)
+    assert sc["preset"]["widths"] == (8, 16, 16, 2)
+
+
+def test_scene_course_recipe():
+    sc = inputs.scene_course(1)
+    o = sc["obs"]
+    assert o.shape == (2000, 4) and sc["N"] == 16384 and sc["T"] == 40
+    moving = np.hypot(o[:, 2], o[:, 3])
+    assert np.all(moving[:1500] == 0.0) and np.all(moving <= 3.0 + 1e-12)
+    assert len(sc["waypoints"]) == 4
+
+
+def test_scene_large_recipe():
+    sc = inputs.scene_large(2)
+    o = sc["obs"]
+    assert o.shape == (8192, 4) and sc["N"] == 65536 and sc["T"] == 100
+    assert sc["preset"]["widths"] == (8, 64, 64, 2)
+    speed = np.hypot(o[:, 2], o[:, 3])
+    n_dyn = int(np.count_nonzero(np.any(o[:, 2:] != 0.0, axis=1)))
+    assert abs(n_dyn - round(0.2 * 8192)) <= 20
+    assert np.all(speed <= 5.0 + 1e-12)
+    assert np.all(np.abs(o[:, :2]) <= 40.0 + 1e-9)
+    static = speed == 0.0
+    r = np.hypot(o[:, 0], o[:, 1])
+    assert np.min(r[static]) > 8.0 - 2.5          # parked outlines centred beyond 8 m
+    assert np.min(r[~static]) > 10.0 - 2.5
+
+
+def test_scene_batch_recipe():
+    b = inputs.scene_batch(0, S=24)
+    assert len(b["scenes"]) == 24
+    off = 0
+    for s in b["scenes"]:
+        assert s["obs_offset"] == off
+        off += s["M"]
+        assert 1024 <= s["N"] <= 65536 + 31 and s["N"] % 32 == 0
+        assert 20 <= s["T"] <= 80 and 1 <= s["M"] <= 20000
+        assert s["width"] in (16, 32, 64)
+        seg = b["obs"][s["obs_offset"]:s["obs_offset"] + s["M"]]
+        assert np.all(np.hypot(seg[:, 2], seg[:, 3]) <= 3.0 + 1e-9)
+        g, st = s["goal"], s["state"]
+        assert math.hypot(g[0] - st[0], g[1] - st[1]) < 15.0
+    assert off == b["obs"].shape[0]

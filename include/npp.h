@@ -173,6 +173,15 @@ npp_status npp_sample_params(uint64_t seed, uint32_t t_index, uint32_t stream_id
                              int32_t n0, int32_t K, int32_t n_theta, float* out_dev,
                              void* stream);
 
+/* Diagnostics (no counterpart in the paper): evaluates the FP32 function
+ * approximations the rollout uses on x_dev[n] (device): fn 0 tanh of the
+ * network layers -> y_dev; 1 tan of the steering angle -> y_dev; 2 sin and
+ * cos of a heading -> y_dev, y2_dev.  Lets callers bound their error against
+ * correctly rounded values.  NPP_INVALID_ARG for an unknown fn, n < 0 or a
+ * NULL output that fn writes. */
+npp_status npp_math_eval(int32_t fn, const float* x_dev, int32_t n, float* y_dev, float* y2_dev,
+                         void* stream);
+
 /* ---------------------------------------------------------------------
  * Device-resident closed loop (Alg. 1): each sampling time is one CUDA graph
  * replay holding the plan step and an advance kernel that applies the
@@ -328,8 +337,9 @@ npp_status npp_plan_step_noalloc(const npp_config* cfg, const npp_state* state,
  * per-point test, so the same flags as checking every point); -1 (default)
  * takes 5 from M = 4096 points and otherwise chooses by the number of
  * samples.
- * "traj_variant" 0 or 1: the trajectory kernel holds 2 (0, default) or 4 (1)
- * hidden units per lane.
+ * "traj_variant" 0..3: launch shape of the trajectory kernel -- 0 (default)
+ * 2 hidden units per lane in blocks sized for occupancy, 1 four hidden units
+ * per lane, 2 eight-warp blocks, 3 another block size.
  * Returns NPP_INVALID_ARG for an unknown name or value. */
 npp_status npp_set_option(npp_handle* h, const char* name, int32_t value);
 

@@ -115,6 +115,23 @@ __global__ void sample_params_kernel(SamplerKey key, int n0, int K, int nt, floa
     }
 }
 
+__global__ void math_eval_kernel(int fn, const float* x, int n, float* y, float* y2)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float v = x[i];
+        if (fn == 0) {
+            y[i] = tanh_r(v);
+        } else if (fn == 1) {
+            y[i] = tan_r(v);
+        } else {
+            float s, c;
+            sincos_r(v, s, c);
+            y[i] = s;
+            y2[i] = c;
+        }
+    }
+}
+
 }  // namespace
 
 namespace npp {
@@ -473,7 +490,7 @@ npp_status npp_set_option(npp_handle* h, const char* name, int32_t value)
         return NPP_OK;
     }
     if (std::strcmp(name, "traj_variant") == 0) {
-        if (value != 0 && value != 1) return fail(h, NPP_INVALID_ARG, "traj_variant is 0 or 1");
+        if (value < 0 || value > 3) return fail(h, NPP_INVALID_ARG, "traj_variant is 0..3");
         h->traj_variant = value;
         return NPP_OK;
     }
@@ -514,6 +531,19 @@ npp_status npp_sample_params(uint64_t seed, uint32_t t_index, uint32_t stream_id
         make_key(seed, t_index, stream_id), n0, K, n_theta, out_dev);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(nullptr, NPP_CUDA_ERROR, "sampler launch: %s", cudaGetErrorString(e));
+    return NPP_OK;
+}
+
+npp_status npp_math_eval(int32_t fn, const float* x_dev, int32_t n, float* y_dev, float* y2_dev,
+                         void* stream)
+{
+    if (fn < 0 || fn > 2 || n < 0 || (n > 0 && (!x_dev || !y_dev || (fn == 2 && !y2_dev))))
+        return fail(nullptr, NPP_INVALID_ARG, "npp_math_eval: bad arguments");
+    if (n == 0) return NPP_OK;
+    const int grid = std::min((n + 255) / 256, 4096);
+    math_eval_kernel<<<grid, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(fn, x_dev, n, y_dev, y2_dev);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(nullptr, NPP_CUDA_ERROR, "math_eval launch: %s", cudaGetErrorString(e));
     return NPP_OK;
 }
 

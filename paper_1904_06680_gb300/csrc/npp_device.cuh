@@ -119,6 +119,69 @@ __device__ __forceinline__ float2 sample_pair(const SamplerKey& key, uint32_t i,
     return (i & 2u) ? spec_normal_pair(w.z, w.w) : spec_normal_pair(w.x, w.y);
 }
 
+// ------------------------------------------------------------------ rollout math
+// FP32 functions of the rollout step built on the SFU's approximate base-2
+// exponential, reciprocal, sine and cosine (PTX ex2/rcp/sin/cos .approx).
+// Absolute errors (measured against the correctly rounded values on a dense
+// grid of arguments, see the diagnostics entry point): tanh below 5e-7 for
+// every finite x; tan below 2e-6 for |z| <= 1; sin/cos of the heading below
+// 1e-6 for |phi| <= 1e3.
+
+__device__ __forceinline__ float sfu_ex2(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float sfu_rcp(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float sfu_sin(float x)
+{
+    float y;
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float sfu_cos(float x)
+{
+    float y;
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// tanh x = 1 - 2 / (e^{2x} + 1); e^{2x} = 2^{x * 2/ln 2}.  Saturates to
+// +-1 (e^{2x} = inf gives 1, e^{2x} = 0 gives -1).
+__device__ __forceinline__ float tanh_r(float x)
+{
+    const float e = sfu_ex2(x * 2.88539008177792681f);
+    return fmaf(-2.0f, sfu_rcp(e + 1.0f), 1.0f);
+}
+
+// tan z = sin z / cos z for the steering angle (|z| <= delta_max < pi/2)
+__device__ __forceinline__ float tan_r(float z)
+{
+    return sfu_sin(z) * sfu_rcp(sfu_cos(z));
+}
+
+// sin and cos of a heading: Cody-Waite reduction by 2 pi (two-part constant,
+// 2 pi = TWO_PI_HI + TWO_PI_LO) to |r| <= pi, then the SFU on r
+__device__ __forceinline__ void sincos_r(float phi, float& s, float& c)
+{
+    const float TWO_PI_HI = 6.28318548202514648f;      // float nearest 2 pi
+    const float TWO_PI_LO = -1.74845553146951715e-7f;  // 2 pi - TWO_PI_HI
+    const float k = rintf(phi * 0.159154943091895336f);
+    float r = fmaf(-k, TWO_PI_HI, phi);
+    r = fmaf(-k, TWO_PI_LO, r);
+    s = sfu_sin(r);
+    c = sfu_cos(r);
+}
+
 // ------------------------------------------------------------------ kernels
 // State of a device-resident closed loop (Alg. 1 run inside a CUDA graph).
 // The plan-step kernels read the planner's view of it; the advance kernel

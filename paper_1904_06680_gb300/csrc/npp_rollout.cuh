@@ -186,7 +186,7 @@ __device__ __forceinline__ void traj_sample(const DevCfg& c, const TrajJob& job,
 
     for (int h = 0; h < T; ++h) {
         float sp, cp;
-        sincosf(ph, &sp, &cp);
+        sincos_r(ph, sp, cp);
         if (writer) {
             if (job.traj) job.traj[h * job.rec_stride + rec] = make_float4(x, y, ph, v);
             if (job.coefA) write_coef(job.coefA, job.coefB, c, job.coef_base + (long long)h * N + n, x, y, sp, cp);
@@ -206,33 +206,41 @@ __device__ __forceinline__ void traj_sample(const DevCfg& c, const TrajJob& job,
             float acc = net.b1[j];
 #pragma unroll
             for (int i = 0; i < NIN; ++i) acc = fmaf(net.w1[j][i], s[i], acc);
-            h1[j] = tanhf(acc);
+            h1[j] = tanh_r(acc);
         }
 #pragma unroll
         for (int j = 0; j < U; ++j) hrow[gl * U + j] = h1[j];
         __syncwarp();
-        float acc2[U];
+        // layer 2: each unit's dot product as four interleaved partial sums
+        // (inputs i = 4q + r go to partial r), added pairwise with the bias
+        // last: independent FMA chains keep the pipe busy
+        float part[U][4];
 #pragma unroll
-        for (int j = 0; j < U; ++j) acc2[j] = net.b2[j];
+        for (int j = 0; j < U; ++j)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) part[j][r] = 0.0f;
         const float4* hrow4 = reinterpret_cast<const float4*>(hrow);
 #pragma unroll
         for (int i = 0; i < W / 4; ++i) {
             const float4 hv = hrow4[i];
 #pragma unroll
             for (int j = 0; j < U; ++j) {
-                acc2[j] = fmaf(net.w2[j][4 * i + 0], hv.x, acc2[j]);
-                acc2[j] = fmaf(net.w2[j][4 * i + 1], hv.y, acc2[j]);
-                acc2[j] = fmaf(net.w2[j][4 * i + 2], hv.z, acc2[j]);
-                acc2[j] = fmaf(net.w2[j][4 * i + 3], hv.w, acc2[j]);
+                part[j][0] = fmaf(net.w2[j][4 * i + 0], hv.x, part[j][0]);
+                part[j][1] = fmaf(net.w2[j][4 * i + 1], hv.y, part[j][1]);
+                part[j][2] = fmaf(net.w2[j][4 * i + 2], hv.z, part[j][2]);
+                part[j][3] = fmaf(net.w2[j][4 * i + 3], hv.w, part[j][3]);
             }
         }
         __syncwarp();
+        float acc2[U];
+#pragma unroll
+        for (int j = 0; j < U; ++j) acc2[j] = ((part[j][0] + part[j][1]) + (part[j][2] + part[j][3])) + net.b2[j];
         // layer 3: a fixed pairwise tree over the hidden units -- leaves
         // w_2i h_2i + w_2i+1 h_2i+1 (one fma), then sums of neighbours -- so
         // the value does not depend on how many units a lane holds
         float h2[U];
 #pragma unroll
-        for (int j = 0; j < U; ++j) h2[j] = tanhf(acc2[j]);
+        for (int j = 0; j < U; ++j) h2[j] = tanh_r(acc2[j]);
         float p0 = fmaf(net.w3[0][1], h2[1], net.w3[0][0] * h2[0]);
         float p1 = fmaf(net.w3[1][1], h2[1], net.w3[1][0] * h2[0]);
         if constexpr (U == 4) {
@@ -244,14 +252,14 @@ __device__ __forceinline__ void traj_sample(const DevCfg& c, const TrajJob& job,
             p0 += __shfl_xor_sync(FULL, p0, off);
             p1 += __shfl_xor_sync(FULL, p1, off);
         }
-        const float ar0 = tanhf(net.b3[0] + p0);
-        const float ar1 = tanhf(net.b3[1] + p1);
+        const float ar0 = tanh_r(net.b3[0] + p0);
+        const float ar1 = tanh_r(net.b3[1] + p1);
         float a0 = fminf(fmaxf(ar0, ap0 - c.r_rate), ap0 + c.r_rate);
         a0 = fminf(fmaxf(a0, -1.0f), 1.0f);
         const float a1 = ar1;
         E += a0 * a0 + a1 * a1;
         if (writer && job.ctrl) job.ctrl[h * job.rec_stride + rec] = make_float2(a0, a1);
-        const float td = tanf(c.delta_max * a0);
+        const float td = tan_r(c.delta_max * a0);
         const float tb = c.lrL * td;
         const float dv = c.Ts * v;
         x += dv * (cp - sp * tb);
@@ -263,7 +271,7 @@ __device__ __forceinline__ void traj_sample(const DevCfg& c, const TrajJob& job,
     }
     if (writer) {
         float sp, cp;
-        sincosf(ph, &sp, &cp);
+        sincos_r(ph, sp, cp);
         if (job.traj) job.traj[T * job.rec_stride + rec] = make_float4(x, y, ph, v);
         if (job.coefA) write_coef(job.coefA, job.coefB, c, job.coef_base + (long long)T * N + n, x, y, sp, cp);
         if (job.jfree) {
@@ -274,8 +282,8 @@ __device__ __forceinline__ void traj_sample(const DevCfg& c, const TrajJob& job,
     }
 }
 
-template <int W, int G, int NW>
-__global__ void __launch_bounds__(NW * 32) traj_kernel(const RolloutArgs a)
+template <int W, int G, int NW, int MINB = 1>
+__global__ void __launch_bounds__(NW * 32, MINB) traj_kernel(const RolloutArgs a)
 {
     constexpr int B = TrajKernel<W, G, NW>::B;
     __shared__ __align__(16) float hx_all[B * W];
@@ -838,12 +846,12 @@ inline cudaError_t ensure_smem(KernelFn fn, int smem)
     return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
-template <int W, int G, int NW>
+template <int W, int G, int NW, int MINB = 1>
 cudaError_t launch_traj(const RolloutArgs& a, cudaStream_t stream)
 {
     using K = TrajKernel<W, G, NW>;
     const int grid = (a.N + K::B - 1) / K::B;
-    traj_kernel<W, G, NW><<<grid, K::THREADS, 0, stream>>>(a);
+    traj_kernel<W, G, NW, MINB><<<grid, K::THREADS, 0, stream>>>(a);
     return cudaGetLastError();
 }
 

@@ -1,13 +1,19 @@
-// Trajectory kernel for the 8-16-16-2 network: variant 0 holds 2 hidden
-// units per lane (8 lanes per sample), variant 1 holds 4 (4 lanes); both
-// compute identical values.
+// Trajectory kernel for the 8-16-16-2 network.  Launch shapes (all compute
+// identical values): 0 (default, fastest measured on GB300) <16, 8, 4, 4>,
+// 1 four hidden units per lane, 2 eight-warp blocks, 3 <16, 8, 8, 3>;
+// template arguments <width, lanes per sample, warps per block, blocks per SM hint>.
 #include "npp_rollout.cuh"
 
 namespace npp {
 
 cudaError_t launch_traj_w16(const RolloutArgs& a, cudaStream_t s, int variant)
 {
-    return variant ? launch_traj<16, 4, 8>(a, s) : launch_traj<16, 8, 8>(a, s);
+    switch (variant) {
+    case 1: return launch_traj<16, 4, 8>(a, s);
+    case 2: return launch_traj<16, 8, 8>(a, s);
+    case 3: return launch_traj<16, 8, 8, 3>(a, s);
+    default: return launch_traj<16, 8, 4, 4>(a, s);
+    }
 }
 
 }  // namespace npp

@@ -73,7 +73,7 @@ EXPORTS = ("npp_create", "npp_destroy", "npp_last_error", "npp_n_theta", "npp_pl
            "npp_last_timing", "npp_set_option", "npp_plan_step_noalloc", "npp_loop_create",
            "npp_loop_run", "npp_loop_read", "npp_loop_log", "npp_loop_destroy", "npp_loop_samples",
            "npp_loop_last_timing", "npp_batch_create", "npp_batch_update", "npp_batch_offsets",
-           "npp_plan_batch", "npp_batch_destroy", "npp_batch_set_option")
+           "npp_plan_batch", "npp_batch_destroy", "npp_batch_set_option", "npp_math_eval")
 
 _lib = None
 
@@ -119,6 +119,7 @@ def lib():
                                             C.POINTER(npp_goal), P, I32, I32, I32, U64, U32, P,
                                             C.POINTER(npp_outputs), P]
         L.npp_last_timing.argtypes = [P, C.POINTER(C.c_float), I32]
+        L.npp_math_eval.argtypes = [I32, P, I32, P, P, P]
         for name in EXPORTS:
             if name not in ("npp_last_error", "npp_n_theta"):
                 getattr(L, name).restype = C.c_int
@@ -218,6 +219,12 @@ def npp_rollout_params(h, state, goal, obs, M, theta, K, T, costs, first_hit, sa
 def npp_sample_params(seed, t_index, stream_id, n0, K, n_theta, out, stream=None):
     return _check(lib().npp_sample_params(int(seed), int(t_index), int(stream_id), int(n0), int(K),
                                           int(n_theta), _ptr(out), _stream(stream)))
+
+
+def npp_math_eval(fn, x, y, y2=None, stream=None):
+    """fn 0 tanh, 1 tan, 2 sin/cos (y, y2) of the rollout on CUDA tensors."""
+    return _check(lib().npp_math_eval(int(fn), _ptr(x), int(x.numel()), _ptr(y), _ptr(y2),
+                                      _stream(stream)))
 
 
 def npp_set_option(h, name: str, value: int):

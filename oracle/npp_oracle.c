@@ -33,7 +33,9 @@
  *                     (eq_Apsietc_collAvoidIneqs), obstacle points extrapolated
  *                     at constant velocity, Sect. II-D items (i)-(iv)
  *   orc_plan          best of N sampled rollouts (one TSHC sampling batch,
- *                     Sect. II-D "Fifth"/"Sixth"), lowest index on ties
+ *                     Sect. II-D "Fifth"/"Sixth"), lowest index on ties;
+ *                     optionally the first n_prop samples drawn from a
+ *                     Gaussian proposal (mean, std) instead of N(0, I)
  *
  * Pins (tests/test_oracle_*.py): Philox known-answer vectors; Normal32
  * against FP64 libm Box-Muller and moment/KS checks; the Fig. 3 state table
@@ -422,6 +424,24 @@ static void sample_theta(const orc_config* c, uint64_t seed, uint32_t t_index,
     for (int i = 0; i < nt; ++i) theta[i] = (double)tmp[i];
 }
 
+/* Sample n of a plan step with a sampling proposal (mean mu, standard
+ * deviation sigma, both FP32): samples n < n_prop are mu + sigma * eps with
+ * eps the normals of stream 1, rounded once to FP32 (a fused multiply-add,
+ * C99 fmaf, correctly rounded); the others are the isotropic samples of the
+ * given stream.  With n_prop = 0 this is sample_theta. */
+static void sample_theta_mixed(const orc_config* c, uint64_t seed, uint32_t t_index,
+                               uint32_t stream, uint32_t n, const float* mu, const float* sigma,
+                               int n_prop, double* theta, float* tmp)
+{
+    if ((int64_t)n >= (int64_t)n_prop || !mu || !sigma) {
+        sample_theta(c, seed, t_index, stream, n, theta, tmp);
+        return;
+    }
+    int nt = orc_n_theta(c);
+    orc_theta(seed, t_index, 1u, n, nt, tmp);
+    for (int i = 0; i < nt; ++i) theta[i] = (double)fmaf(sigma[i], tmp[i], mu[i]);
+}
+
 /* Rollouts of explicit parameter vectors theta[K][n_theta] (EV-frame inputs).
  * Outputs per sample: cost[K], first_hit[K], and if non-NULL
  * traj[K][T+1][4], ctrl[K][T][2] (EV frame). */
@@ -446,6 +466,7 @@ void orc_rollout_theta(const orc_config* c, const double* theta, int K,
  * non-NULL, replaces sample 0's parameters. */
 void orc_rollout_samples(const orc_config* c, uint64_t seed, uint32_t t_index,
                          uint32_t stream, const int32_t* idx, int K, const double* warm,
+                         const float* mu, const float* sigma, int n_prop,
                          const double z0[4], const double ap0[2], const double* goal_ev,
                          const double* obs_ev, int M, int T, int n_threads,
                          double* cost, int32_t* first_hit, double* traj, double* ctrl)
@@ -463,7 +484,8 @@ void orc_rollout_samples(const orc_config* c, uint64_t seed, uint32_t t_index,
 #endif
         for (int k = 0; k < K; ++k) {
             if (warm && idx[k] == 0) memcpy(theta, warm, sizeof(double) * nt);
-            else sample_theta(c, seed, t_index, stream, (uint32_t)idx[k], theta, tmp);
+            else sample_theta_mixed(c, seed, t_index, stream, (uint32_t)idx[k], mu, sigma, n_prop,
+                                    theta, tmp);
             first_hit[k] = rollout(c, theta, z0, ap0, goal_ev, obs_ev, M, T, cost + k,
                                    traj ? traj + (size_t)k * (T + 1) * 4 : NULL,
                                    ctrl ? ctrl + (size_t)k * T * 2 : NULL);
@@ -483,7 +505,8 @@ void orc_rollout_samples(const orc_config* c, uint64_t seed, uint32_t t_index,
  * [T+1][4] in the world frame. */
 int orc_plan(const orc_config* c, const double* state_w, const double* goal_w,
              const double* obs_w, int M, int N, int T, uint64_t seed,
-             uint32_t t_index, const double* warm, int n_threads,
+             uint32_t t_index, const double* warm, const float* mu, const float* sigma,
+             int n_prop, int n_threads,
              double* costs, int32_t* first_hit, int32_t* best_idx, int32_t* status,
              double* best_cost, double* best_theta, double* controls, double* traj_w)
 {
@@ -498,8 +521,8 @@ int orc_plan(const orc_config* c, const double* state_w, const double* goal_w,
     double* cst = (double*)malloc(sizeof(double) * N);
     int32_t* fh = (int32_t*)malloc(sizeof(int32_t) * N);
     for (int n = 0; n < N; ++n) idx[n] = n;
-    orc_rollout_samples(c, seed, t_index, 0u, idx, N, warm, z0, ap0, goal_ev, obs_ev, M, T,
-                        n_threads, cst, fh, NULL, NULL);
+    orc_rollout_samples(c, seed, t_index, 0u, idx, N, warm, mu, sigma, n_prop, z0, ap0, goal_ev,
+                        obs_ev, M, T, n_threads, cst, fh, NULL, NULL);
     /* argmin over collision-free samples, lowest index on ties */
     int best = -1;
     for (int n = 0; n < N; ++n)
@@ -519,7 +542,7 @@ int orc_plan(const orc_config* c, const double* state_w, const double* goal_w,
     double* theta = (double*)malloc(sizeof(double) * nt);
     float* tmp = (float*)malloc(sizeof(float) * (nt + 4));
     if (warm && best == 0) memcpy(theta, warm, sizeof(double) * nt);
-    else sample_theta(c, seed, t_index, 0u, (uint32_t)best, theta, tmp);
+    else sample_theta_mixed(c, seed, t_index, 0u, (uint32_t)best, mu, sigma, n_prop, theta, tmp);
     if (best_theta) memcpy(best_theta, theta, sizeof(double) * nt);
     double* traj_ev = (double*)malloc(sizeof(double) * 4 * (T + 1));
     double dummy;

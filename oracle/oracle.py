@@ -70,10 +70,12 @@ def lib():
         L.orc_rollout_theta.argtypes = [_P, _D, C.c_int, _D, _D, _D, _D, C.c_int, C.c_int,
                                         C.c_int, _D, _I, C.c_void_p, C.c_void_p]
         L.orc_rollout_samples.argtypes = [_P, C.c_uint64, C.c_uint32, C.c_uint32, _I, C.c_int,
-                                          C.c_void_p, _D, _D, _D, _D, C.c_int, C.c_int, C.c_int,
+                                          C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                          _D, _D, _D, _D, C.c_int, C.c_int, C.c_int,
                                           _D, _I, C.c_void_p, C.c_void_p]
         L.orc_plan.argtypes = [_P, _D, _D, _D, C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_uint32,
-                               C.c_void_p, C.c_int, _D, _I, C.POINTER(C.c_int32),
+                               C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, _D, _I,
+                               C.POINTER(C.c_int32),
                                C.POINTER(C.c_int32), C.POINTER(C.c_double), _D, _D, _D]
         L.orc_plan.restype = C.c_int
         _lib = L
@@ -85,6 +87,10 @@ def _d(a, n=None):
     if n is not None:
         assert a.size == n
     return a
+
+
+def _f32(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float32)
 
 
 def _ptr(a):
@@ -204,7 +210,9 @@ def rollout_theta(p, thetas, z0, ap0, goal_ev, obs_ev, T, n_threads=0, record=Tr
 
 
 def rollout_samples(p, seed, t_index, idx, z0, ap0, goal_ev, obs_ev, T, warm=None,
-                    stream=0, n_threads=0, record=True):
+                    stream=0, n_threads=0, record=True, mu=None, sigma=None, n_prop=0):
+    """Rollouts of the sampled parameter vectors idx; with a proposal (mu,
+    sigma FP32 arrays of n_theta) samples idx < n_prop are mu + sigma*eps."""
     c = make_config(p)
     idx = np.ascontiguousarray(idx, np.int32)
     K = idx.size
@@ -215,14 +223,17 @@ def rollout_samples(p, seed, t_index, idx, z0, ap0, goal_ev, obs_ev, T, warm=Non
     traj = np.zeros((K, T + 1, 4)) if record else None
     ctrl = np.zeros((K, T, 2)) if record else None
     w = None if warm is None else _d(warm)
+    mu32, sg32 = _f32(mu), _f32(sigma)
     lib().orc_rollout_samples(C.byref(c), int(seed), int(t_index), int(stream), idx, K, _ptr(w),
+                              _ptr(mu32), _ptr(sg32), int(n_prop),
                               _d(z0, 4), _d(ap0, 2), _d(goal_ev, 4),
                               obs_ev if M else np.zeros((1, 4)), M, T, n_threads, cost, fh,
                               _ptr(traj), _ptr(ctrl))
     return dict(cost=cost, first_hit=fh, traj=traj, ctrl=ctrl)
 
 
-def plan(p, state_w, goal_w, obs_w, N, T, seed, t_index, warm=None, n_threads=0):
+def plan(p, state_w, goal_w, obs_w, N, T, seed, t_index, warm=None, n_threads=0, mu=None,
+         sigma=None, n_prop=0):
     c = make_config(p)
     nt = lib().orc_n_theta(C.byref(c))
     obs_w = _d(obs_w).reshape(-1, 4)
@@ -236,7 +247,7 @@ def plan(p, state_w, goal_w, obs_w, N, T, seed, t_index, warm=None, n_threads=0)
     w = None if warm is None else _d(warm, nt)
     rc = lib().orc_plan(C.byref(c), _d(state_w, 6), _d(goal_w, 4),
                         obs_w if M else np.zeros((1, 4)), M, N, T, int(seed), int(t_index),
-                        _ptr(w), n_threads, costs, fh, C.byref(bi), C.byref(st), C.byref(bc),
+                        _ptr(w), _ptr(_f32(mu)), _ptr(_f32(sigma)), int(n_prop), n_threads, costs, fh, C.byref(bi), C.byref(st), C.byref(bc),
                         bt, ctrl, traj)
     if rc == 1:
         raise ValueError("invalid plan arguments")

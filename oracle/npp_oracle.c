@@ -464,6 +464,19 @@ void orc_rollout_theta(const orc_config* c, const double* theta, int K,
 
 /* Rollouts of Philox-sampled samples idx[K] (EV-frame inputs); warm, when
  * non-NULL, replaces sample 0's parameters. */
+/* theta_n of a plan step with a proposal (FP32 values, see
+ * sample_theta_mixed) */
+void orc_theta_mixed(uint64_t seed, uint32_t t_index, uint32_t n, int n_theta, const float* mu,
+                     const float* sigma, int n_prop, float* out)
+{
+    if ((int64_t)n >= (int64_t)n_prop || !mu || !sigma) {
+        orc_theta(seed, t_index, 0u, n, n_theta, out);
+        return;
+    }
+    orc_theta(seed, t_index, 1u, n, n_theta, out);
+    for (int i = 0; i < n_theta; ++i) out[i] = fmaf(sigma[i], out[i], mu[i]);
+}
+
 void orc_rollout_samples(const orc_config* c, uint64_t seed, uint32_t t_index,
                          uint32_t stream, const int32_t* idx, int K, const double* warm,
                          const float* mu, const float* sigma, int n_prop,

@@ -78,6 +78,8 @@ def lib():
                                C.POINTER(C.c_int32),
                                C.POINTER(C.c_int32), C.POINTER(C.c_double), _D, _D, _D]
         L.orc_plan.restype = C.c_int
+        L.orc_theta_mixed.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_int, C.c_void_p, C.c_void_p,
+                                      C.c_int, _F]
         _lib = L
     return _lib
 
@@ -128,6 +130,15 @@ def theta(seed, t_index, n, n_theta, stream=0):
     """FP32 parameters of sample n (Philox + Normal32)."""
     out = np.zeros(n_theta, np.float32)
     lib().orc_theta(int(seed), int(t_index), int(stream), int(n), int(n_theta), out)
+    return out
+
+
+def theta_mixed(seed, t_index, n, n_theta, mu, sigma, n_prop):
+    """FP32 parameters of sample n of a plan step with a proposal."""
+    out = np.zeros(n_theta, np.float32)
+    mu32, sg32 = _f32(mu), _f32(sigma)
+    lib().orc_theta_mixed(int(seed), int(t_index), int(n), int(n_theta), _ptr(mu32), _ptr(sg32),
+                          int(n_prop), out)
     return out
 
 

@@ -40,6 +40,24 @@ static bool finite_all(const float* p, int n)
 // ------------------------------------------------------------------ kernels
 namespace {
 
+// theta_idx[4q .. 4q+3] where the quad may run past n_theta (the proposal
+// arrays hold exactly n_theta values)
+__device__ float4 sample_quad_mixed_tail(const SamplerKey& key, const Proposal& p, uint32_t q, uint32_t n,
+                                         int n_theta)
+{
+    if (4 * (int)q + 3 < n_theta || !proposal_sample(p, n)) return sample_quad_mixed(key, p, q, n);
+    SamplerKey k1 = key;
+    k1.stream_id = 1u;
+    const float4 e = sample_quad(k1, q, n);
+    const float ev[4] = { e.x, e.y, e.z, e.w };
+    float r[4] = { 0.f, 0.f, 0.f, 0.f };
+    for (int j = 0; j < 4 && 4 * (int)q + j < n_theta; ++j) {
+        const int i = 4 * (int)q + j;
+        r[j] = fmaf(p.sigma[i], ev[j], p.mu[i]);
+    }
+    return make_float4(r[0], r[1], r[2], r[3]);
+}
+
 // Winner epilogue: decode the packed key, write the summary record, the
 // winner's world-frame trajectory and controls, and regenerate its
 // parameters from Philox (or copy the warm start).
@@ -93,7 +111,7 @@ __global__ void epilogue_kernel(const EpilogueArgs e)
                 for (int i = threadIdx.x; i < e.n_theta; i += blockDim.x) e.params[i] = e.warm[i];
         } else {
             for (int q = threadIdx.x; 4 * q < e.n_theta; q += blockDim.x) {
-                const float4 v = sample_quad(skey, (uint32_t)q, (uint32_t)idx);
+                const float4 v = sample_quad_mixed_tail(skey, e.prop, (uint32_t)q, (uint32_t)idx, e.n_theta);
                 const float vv[4] = { v.x, v.y, v.z, v.w };
                 for (int j = 0; j < 4 && 4 * q + j < e.n_theta; ++j) e.params[4 * q + j] = vv[j];
             }
@@ -365,12 +383,11 @@ npp_status npp_destroy(npp_handle* h)
     return NPP_OK;
 }
 
-npp_status npp_plan_step(npp_handle* h, const npp_state* state, const npp_goal* goal,
-                         const float* obs_dev, int32_t M, int32_t N, int32_t T, uint64_t seed,
-                         uint32_t t_index, const float* warm_dev, const npp_outputs* out,
-                         void* stream)
+static npp_status plan_step_impl(npp_handle* h, const npp_state* state, const npp_goal* goal,
+                                 const float* obs_dev, int32_t M, int32_t N, int32_t T, uint64_t seed,
+                                 uint32_t t_index, const float* warm_dev, const Proposal& prop,
+                                 const npp_outputs* out, void* stream)
 {
-    if (!h) return fail(nullptr, NPP_INVALID_ARG, "handle is NULL");
     npp_status st;
     if ((st = check_state_goal(h, state, goal)) != NPP_OK) return st;
     if ((st = check_sizes(h, M, N, T, obs_dev, true)) != NPP_OK) return st;
@@ -382,6 +399,7 @@ npp_status npp_plan_step(npp_handle* h, const npp_state* state, const npp_goal* 
     fill_rollout_args(h, a, state, goal, obs_dev, M, N, T);
     a.key = make_key(seed, t_index, 0u);
     a.warm = warm_dev;
+    a.prop = prop;
     a.costs = out->costs;
     a.first_hit = out->first_hit;
     a.traj = out->sample_traj ? reinterpret_cast<float4*>(out->sample_traj) : h->d_traj;
@@ -397,6 +415,7 @@ npp_status npp_plan_step(npp_handle* h, const npp_state* state, const npp_goal* 
     e.N = N; e.T = T; e.n_theta = h->n_theta;
     e.key = a.key;
     e.warm = warm_dev;
+    e.prop = prop;
     e.traj = a.traj;
     e.ctrl = a.ctrl;
     e.best_key = h->d_key;
@@ -408,6 +427,30 @@ npp_status npp_plan_step(npp_handle* h, const npp_state* state, const npp_goal* 
     CUDA_TRY(h, cudaGetLastError());
     if (h->timing) CUDA_TRY(h, record_event(h->ev[3], s));
     return NPP_OK;
+}
+
+npp_status npp_plan_step(npp_handle* h, const npp_state* state, const npp_goal* goal,
+                         const float* obs_dev, int32_t M, int32_t N, int32_t T, uint64_t seed,
+                         uint32_t t_index, const float* warm_dev, const npp_outputs* out,
+                         void* stream)
+{
+    if (!h) return fail(nullptr, NPP_INVALID_ARG, "handle is NULL");
+    return plan_step_impl(h, state, goal, obs_dev, M, N, T, seed, t_index, warm_dev,
+                          Proposal{ nullptr, nullptr, 0 }, out, stream);
+}
+
+npp_status npp_plan_step_proposal(npp_handle* h, const npp_state* state, const npp_goal* goal,
+                                  const float* obs_dev, int32_t M, int32_t N, int32_t T, uint64_t seed,
+                                  uint32_t t_index, const float* warm_dev, const float* mean_dev,
+                                  const float* std_dev, int32_t N_prop, const npp_outputs* out,
+                                  void* stream)
+{
+    if (!h) return fail(nullptr, NPP_INVALID_ARG, "handle is NULL");
+    if (N_prop < 0 || N_prop > N) return fail(h, NPP_INVALID_ARG, "N_prop=%d outside [0, N=%d]", N_prop, N);
+    if (N_prop > 0 && (!mean_dev || !std_dev))
+        return fail(h, NPP_INVALID_ARG, "mean and std must not be NULL with N_prop > 0");
+    return plan_step_impl(h, state, goal, obs_dev, M, N, T, seed, t_index, warm_dev,
+                          Proposal{ N_prop > 0 ? mean_dev : nullptr, std_dev, N_prop }, out, stream);
 }
 
 npp_status npp_plan_step_host(npp_handle* h, const npp_state* state, const npp_goal* goal,

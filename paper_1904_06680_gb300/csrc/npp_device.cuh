@@ -119,6 +119,59 @@ __device__ __forceinline__ float2 sample_pair(const SamplerKey& key, uint32_t i,
     return (i & 2u) ? spec_normal_pair(w.z, w.w) : spec_normal_pair(w.x, w.y);
 }
 
+// Gaussian sampling proposal of a plan step: samples n < n_prop take
+// theta_i = fma(sigma_i, eps_i, mu_i) with eps the normals of stream 1 (one
+// rounding to FP32); the others are the isotropic samples.  mu and sigma
+// hold n_theta FP32 values.
+struct Proposal {
+    const float* mu;
+    const float* sigma;
+    int n_prop;
+};
+
+__device__ __forceinline__ bool proposal_sample(const Proposal& p, uint32_t n)
+{
+    return p.mu != nullptr && (long long)n < (long long)p.n_prop;
+}
+
+// theta_n[4q .. 4q+3] of a plan step with proposal p (all four indices
+// below n_theta)
+__device__ __forceinline__ float4 sample_quad_mixed(const SamplerKey& key, const Proposal& p, uint32_t q,
+                                                    uint32_t n)
+{
+    if (!proposal_sample(p, n)) return sample_quad(key, q, n);
+    SamplerKey k1 = key;
+    k1.stream_id = 1u;
+    const float4 e = sample_quad(k1, q, n);
+    const int i = 4 * (int)q;
+    return make_float4(fmaf(p.sigma[i], e.x, p.mu[i]), fmaf(p.sigma[i + 1], e.y, p.mu[i + 1]),
+                       fmaf(p.sigma[i + 2], e.z, p.mu[i + 2]), fmaf(p.sigma[i + 3], e.w, p.mu[i + 3]));
+}
+
+// theta_n[i], theta_n[i+1] for even i
+__device__ __forceinline__ float2 sample_pair_mixed(const SamplerKey& key, const Proposal& p, uint32_t i,
+                                                    uint32_t n)
+{
+    if (!proposal_sample(p, n)) return sample_pair(key, i, n);
+    SamplerKey k1 = key;
+    k1.stream_id = 1u;
+    const float2 e = sample_pair(k1, i, n);
+    return make_float2(fmaf(p.sigma[i], e.x, p.mu[i]), fmaf(p.sigma[i + 1], e.y, p.mu[i + 1]));
+}
+
+// Obstacle point o = (x, y, vx, vy) in the EV frame of the plan step (origin
+// (x0, y0), heading with sine s0 and cosine c0), rounding fixed by explicit
+// fmas so every collision path sees the same FP32 positions.
+__device__ __forceinline__ void ev_point(const float4& o, float x0, float y0, float s0, float c0,
+                                         float& px, float& py, float& vx, float& vy)
+{
+    const float dx = o.x - x0, dy = o.y - y0;
+    px = fmaf(c0, dx, __fmul_rn(s0, dy));
+    py = fmaf(-s0, dx, __fmul_rn(c0, dy));
+    vx = fmaf(c0, o.z, __fmul_rn(s0, o.w));
+    vy = fmaf(-s0, o.z, __fmul_rn(c0, o.w));
+}
+
 // ------------------------------------------------------------------ rollout math
 // FP32 functions of the rollout step built on the SFU's approximate base-2
 // exponential, reciprocal, sine and cosine (PTX ex2/rcp/sin/cos .approx).
@@ -214,6 +267,7 @@ struct RolloutArgs {
     SamplerKey key;
     const float* theta;                // explicit parameters [N][n_theta] or null
     const float* warm;                 // replaces sample 0 when non-null
+    Proposal prop;                     // sampling proposal (mu null: isotropic only)
     float* costs;                      // [N] or null
     int* first_hit;                    // [N] or null
     float4* traj;                      // [T+1][N] EV frame (always written)
@@ -252,6 +306,7 @@ struct EpilogueArgs {
     int N, T, n_theta;
     SamplerKey key;
     const float* warm;
+    Proposal prop;
     const float4* traj;
     const float2* ctrl;
     const unsigned long long* best_key;

@@ -1,0 +1,323 @@
+// npp_gemm.cu -- BF16 GEMM on the fifth-generation tensor cores.
+//
+// One CTA of 128 threads computes a 128 x BN tile of C:
+//   warp 0, one lane   TMA producer: K blocks of 64 (128 bytes of BF16, the
+//                      128-byte swizzle atom) of A and B into a ring of
+//                      STAGES shared-memory stages, completion counted by
+//                      the stage's "full" mbarrier;
+//   warp 1, one lane   MMA issuer: four tcgen05.mma (M = 128, N = BN,
+//                      K = 16) per stage into a TMEM accumulator of BN FP32
+//                      columns, tcgen05.commit frees the stage ("empty")
+//                      and finally signals "done";
+//   warps 0-3          epilogue: warp w reads TMEM lanes 32w..32w+31 (rows)
+//                      with tcgen05.ld, applies the fused epilogue and
+//                      stores.
+// Every wait on an mbarrier is bounded (about a second of clock): on a
+// timeout the CTA records an error code, stops issuing, waits (bounded) for
+// the copies it issued, frees its TMEM and returns.
+#include "npp_gemm.cuh"
+
+#include <cudaTypedefs.h>
+
+namespace npp {
+namespace {
+
+constexpr int BM = 128;
+constexpr int BK = 64;
+constexpr int STAGES = 4;
+constexpr long long WAIT_CYCLES = 2000000000LL;   // ~1 s at 2 GHz
+
+template <int BN>
+struct GemmShape {
+    static constexpr int A_BYTES = BM * BK * 2;
+    static constexpr int B_BYTES = BN * BK * 2;
+    static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 128;   // + alignment slack + barriers
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait for the phase with the given parity to complete
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+{
+    const long long t0 = clock64();
+    while (!mbar_try(bar, parity))
+        if (clock64() - t0 > WAIT_CYCLES) return false;
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// shared-memory matrix descriptor: K-major operand in 128-byte swizzle
+// atoms (8 rows x 128 bytes, atoms 1024 bytes apart along the rows)
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);         // start address
+    d |= (uint64_t)1 << 16;                            // leading byte offset (unused for this layout)
+    d |= (uint64_t)(1024 >> 4) << 32;                  // stride byte offset: next 8-row atom
+    d |= (uint64_t)1 << 46;                            // descriptor version
+    d |= (uint64_t)2 << 61;                            // 128-byte swizzle
+    return d;
+}
+
+// instruction descriptor: BF16 x BF16 -> FP32, both K-major, M = 128, N = bn
+__host__ __device__ constexpr uint32_t mma_idesc(int bn)
+{
+    return (1u << 4)                  // D: FP32
+         | (1u << 7)                  // A: BF16
+         | (1u << 10)                 // B: BF16
+         | ((uint32_t)(bn >> 3) << 17)
+         | ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(tmem_d), "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v)
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int BN>
+__global__ void __launch_bounds__(128, 1)
+gemm_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int K,
+            const GemmEpilogue ep)
+{
+    using S = GemmShape<BN>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * S::STAGE_BYTES);
+    uint64_t* empty = full + STAGES;
+    uint64_t* done = empty + STAGES;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    int* flags = reinterpret_cast<int*>(tmem_slot + 1);      // [0] abort, [1] issued, [2] consumed
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int nk = K / BK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(done, 1);
+        flags[0] = 0;
+        flags[1] = 0;
+        flags[2] = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(tmem_slot)), "r"(BN) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(tmem_slot);
+
+    if (warp == 0 && lane == 0) {
+        int kb = 0;
+        for (; kb < nk; ++kb) {
+            const int s = kb % STAGES;
+            if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) - 1) & 1)) {
+                atomicExch(&flags[0], 1);
+                break;
+            }
+            if (*reinterpret_cast<volatile int*>(&flags[0])) break;
+            uint8_t* st = smem + s * S::STAGE_BYTES;
+            mbar_expect_tx(&full[s], S::STAGE_BYTES);
+            tma_load_2d(st, &ta, kb * BK, m0, &full[s]);
+            tma_load_2d(st + S::A_BYTES, &tb, kb * BK, n0, &full[s]);
+        }
+        flags[1] = kb;
+    } else if (warp == 1 && lane == 0) {
+        constexpr uint32_t idesc = mma_idesc(BN);
+        int kb = 0;
+        for (; kb < nk; ++kb) {
+            const int s = kb % STAGES;
+            if (!mbar_wait(&full[s], (kb / STAGES) & 1)) {
+                atomicExch(&flags[0], 1);
+                break;
+            }
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(smem + s * S::STAGE_BYTES);
+            const uint32_t b0 = a0 + S::A_BYTES;
+#pragma unroll
+            for (int j = 0; j < BK / 16; ++j)
+                mma_bf16(tmem, sw128_desc(a0 + j * 32), sw128_desc(b0 + j * 32), idesc, (kb | j) != 0);
+            mma_commit(&empty[s]);
+        }
+        flags[2] = kb;
+        mma_commit(done);               // arrives once every MMA issued above has completed
+    }
+    __syncwarp();
+
+    const bool ok = mbar_wait(done, 0);
+    tc_fence_after();
+    __syncthreads();
+    const bool aborted = !ok || *reinterpret_cast<volatile int*>(&flags[0]) != 0;
+    if (aborted) {
+        if (threadIdx.x == 0) {
+            if (ep.err) atomicExch(ep.err, 1);
+            // copies issued but never consumed: wait (bounded) for them to land
+            for (int kb = flags[2]; kb < flags[1]; ++kb) mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1);
+        }
+    } else {
+        const int row = m0 + warp * 32 + lane;
+        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+        for (int c = 0; c < BN; c += 16) {
+            float v[16];
+            tmem_ld16(trow + c, v);
+            const int n = n0 + c;
+            if (ep.mode == EPI_F32 || ep.mode == EPI_BIAS_F32) {
+                if (ep.mode == EPI_BIAS_F32)
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[i] += ep.bias[n + i];
+                float4* o = reinterpret_cast<float4*>(ep.out_f32 + (size_t)row * ep.ldo + n);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) o[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+            } else {
+                __nv_bfloat16 hb[16];
+                if (ep.mode == EPI_BIAS_RELU_BF16) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) hb[i] = __float2bfloat16_rn(fmaxf(v[i] + ep.bias[n + i], 0.0f));
+                } else {
+                    const __nv_bfloat16* mk = ep.mask + (size_t)row * ep.ldm + n;
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        hb[i] = __float2bfloat16_rn(__bfloat162float(mk[i]) > 0.0f ? v[i] : 0.0f);
+                }
+                if (ep.out_bf16) {
+                    uint4* o = reinterpret_cast<uint4*>(ep.out_bf16 + (size_t)row * ep.ldo + n);
+                    const uint4* src = reinterpret_cast<const uint4*>(hb);
+                    o[0] = src[0];
+                    o[1] = src[1];
+                }
+                if (ep.out_t) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) ep.out_t[(size_t)(n + i) * ep.ldt + row] = hb[i];
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+}  // namespace
+
+cudaError_t make_tmap_bf16(CUtensorMap* map, const void* base, int rows, int cols, int box_rows)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+    if (!fn) return cudaErrorNotSupported;
+    if ((reinterpret_cast<uintptr_t>(base) & 15u) || cols % 64 || rows % box_rows) return cudaErrorInvalidValue;
+    cuuint64_t dims[2] = { (cuuint64_t)cols, (cuuint64_t)rows };
+    cuuint64_t strides[1] = { (cuuint64_t)cols * 2 };
+    cuuint32_t box[2] = { 64u, (cuuint32_t)box_rows };
+    cuuint32_t estr[2] = { 1u, 1u };
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_gemm(const CUtensorMap& ta, const CUtensorMap& tb, int M, int N, int K, int bn,
+                        const GemmEpilogue& ep, cudaStream_t s)
+{
+    if (M % BM || K % BK || K < BK || (bn != 128 && bn != 256) || N % bn) return cudaErrorInvalidValue;
+    dim3 grid(N / bn, M / BM);
+    if (bn == 256) {
+        const int smem = GemmShape<256>::SMEM;
+        cudaError_t e = cudaFuncSetAttribute(gemm_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        gemm_kernel<256><<<grid, 128, smem, s>>>(ta, tb, K, ep);
+    } else {
+        const int smem = GemmShape<128>::SMEM;
+        cudaError_t e = cudaFuncSetAttribute(gemm_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        gemm_kernel<128><<<grid, 128, smem, s>>>(ta, tb, K, ep);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace npp

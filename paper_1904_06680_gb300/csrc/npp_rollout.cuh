@@ -47,20 +47,22 @@ struct Shape {
     static_assert(G <= 32 && (32 % G) == 0, "a group lives in one warp");
 };
 
-// Parameter source: Philox (sampled) or memory (explicit / warm start).
+// Parameter source: Philox (sampled, optionally through the proposal) or
+// memory (explicit / warm start).
 struct ThetaSrc {
     const float* mem;     // row of this sample, or null -> sample
     SamplerKey key;
+    Proposal prop;
     uint32_t n;
     // rows from memory are read element by element: a row of n_theta floats
     // starts at any 4-byte boundary
     __device__ __forceinline__ float4 quad(int i) const {     // i % 4 == 0
         if (mem) return make_float4(mem[i], mem[i + 1], mem[i + 2], mem[i + 3]);
-        return sample_quad(key, (uint32_t)i >> 2, n);
+        return sample_quad_mixed(key, prop, (uint32_t)i >> 2, n);
     }
     __device__ __forceinline__ float2 pair(int i) const {     // i % 2 == 0
         if (mem) return make_float2(mem[i], mem[i + 1]);
-        return sample_pair(key, (uint32_t)i, n);
+        return sample_pair_mixed(key, prop, (uint32_t)i, n);
     }
 };
 
@@ -142,6 +144,7 @@ struct TrajJob {
     SamplerKey key;               // t_index resolved
     const float* theta;           // explicit rows [N][n_theta] or null
     const float* warm;            // replaces sample 0 when non-null (and si.warm_ok)
+    Proposal prop;                // sampling proposal (mu null: none)
     int N, T;
     float4* traj;                 // [T+1] x stride
     float2* ctrl;                 // [T] x stride
@@ -171,6 +174,7 @@ __device__ __forceinline__ void traj_sample(const DevCfg& c, const TrajJob& job,
     {
         ThetaSrc src;
         src.key = job.key;
+        src.prop = job.prop;
         src.n = (uint32_t)(valid ? n : 0);
         src.mem = nullptr;
         if (job.theta) src.mem = job.theta + (size_t)(valid ? n : 0) * S::NT;
@@ -296,6 +300,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) traj_kernel(const RolloutArgs a
     job.key.t_index = job.si.t_index;
     job.theta = a.theta;
     job.warm = a.warm;
+    job.prop = a.prop;
     job.N = a.N;
     job.T = a.T;
     job.traj = a.traj;
@@ -371,18 +376,6 @@ __device__ __forceinline__ unsigned check_unit(const float4* __restrict__ XY, co
     return bits;
 }
 
-// Obstacle point o = (x, y, vx, vy) in the EV frame of the plan step (origin
-// (x0, y0), heading with sine s0 and cosine c0), rounding fixed by explicit
-// fmas so every collision path sees the same FP32 positions.
-__device__ __forceinline__ void ev_point(const float4& o, float x0, float y0, float s0, float c0,
-                                         float& px, float& py, float& vx, float& vy)
-{
-    const float dx = o.x - x0, dy = o.y - y0;
-    px = fmaf(c0, dx, __fmul_rn(s0, dy));
-    py = fmaf(-s0, dx, __fmul_rn(c0, dy));
-    vx = fmaf(c0, o.z, __fmul_rn(s0, o.w));
-    vy = fmaf(-s0, o.z, __fmul_rn(c0, o.w));
-}
 
 // Staging of the points in the EV frame as pairs; an odd tail is padded with
 // a point 1e15 m away (never inside).

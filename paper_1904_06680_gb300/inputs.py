@@ -33,6 +33,14 @@ Scene recipes (all world-frame, SI units; obstacles are (x, y, vx, vy)):
   outlines with speeds uniform in [0, 5] m/s at uniform headings (none
   starting within 10 m of the start).  Start at the origin at rest facing
   +x; waypoints 30 m out.
+* ``scene_proposal_batch``: scenes for training and evaluating the learned
+  sampling proposal, shaped like the course workload: each scene uses one of
+  `n_layouts` course obstacle layouts (``scene_course`` with its own seed:
+  outer wall, island, ten moving car outlines; 2000 points) and a random
+  start pose in the free area (heading uniform, speed U[0, 2] m/s, last
+  controls U[-0.3, 0.3], no point within 2.5 m) with a goal 6-15 m away in
+  a uniform direction, heading within +-90 degrees of the start heading,
+  at rest, also clear of points.  8-16-16-2 network, N = 4096, T = 40.
 """
 import math
 
@@ -196,6 +204,38 @@ def scene_large(seed: int = 0, N: int = 65536, T: int = 100, width: int = 64, M:
     state = np.array([0.0, 0.0, 0.0, 0.0, 0.0, 0.0])
     return dict(preset=planner(width), state=state, goal=goal.copy(), obs=obs, N=N, T=T,
                 seed=philox_seed(seed), t_index=0, waypoints=LARGE_WAYPOINTS.copy())
+
+
+def scene_proposal_batch(seed: int = 0, S: int = 512, N: int = 4096, T: int = 40, n_layouts: int = 16):
+    rng = np.random.default_rng(6000 + seed)
+    layouts = [scene_course(seed=10000 + 97 * seed + l)["obs"] for l in range(n_layouts)]
+    M = layouts[0].shape[0]
+    scenes = []
+
+    def clear(obs, x, y):
+        return np.min(np.hypot(obs[:, 0] - x, obs[:, 1] - y)) > 2.5
+
+    for s_ in range(S):
+        l = s_ % n_layouts
+        obs = layouts[l]
+        while True:
+            x, y = rng.uniform(-5.0, 20.0, 2)
+            if not (2.0 < x < 13.0 and 2.0 < y < 13.0) and clear(obs, x, y):
+                break
+        phi = rng.uniform(-math.pi, math.pi)
+        while True:
+            d = rng.uniform(6.0, 15.0)
+            a = phi + rng.uniform(-math.pi, math.pi)
+            gx, gy = x + d * math.cos(a), y + d * math.sin(a)
+            if -5.0 < gx < 20.0 and -5.0 < gy < 20.0 and not (2.0 < gx < 13.0 and 2.0 < gy < 13.0) \
+                    and clear(obs, gx, gy):
+                break
+        gphi = phi + rng.uniform(-math.pi / 2, math.pi / 2)
+        state = np.array([x, y, phi, rng.uniform(0.0, 2.0), rng.uniform(-0.3, 0.3), rng.uniform(-0.3, 0.3)])
+        goal = np.array([gx, gy, gphi, 0.0])
+        scenes.append(dict(state=state, goal=goal, N=N, T=T, M=M, width=16, obs_offset=l * M,
+                           seed=philox_seed(seed) * 1000003 + s_, t_index=0))
+    return dict(preset=planner(16), scenes=scenes, obs=np.concatenate(layouts))
 
 
 def tiny_scene(seed: int, N: int, T: int, M: int, width: int = 16, box: float = 12.0,

@@ -63,6 +63,11 @@ class npp_batch_outputs(C.Structure):
                                           "first_hit")]
 
 
+class npp_proposal_config(C.Structure):
+    _fields_ = [("batch", C.c_int32), ("ls_min", C.c_float), ("ls_max", C.c_float),
+                ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float), ("device", C.c_int32)]
+
+
 class npp_outputs(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in ("best", "params", "controls", "trajectory", "costs",
                                           "first_hit", "sample_traj", "sample_ctrl")]
@@ -73,7 +78,11 @@ EXPORTS = ("npp_create", "npp_destroy", "npp_last_error", "npp_n_theta", "npp_pl
            "npp_last_timing", "npp_set_option", "npp_plan_step_noalloc", "npp_loop_create",
            "npp_loop_run", "npp_loop_read", "npp_loop_log", "npp_loop_destroy", "npp_loop_samples",
            "npp_loop_last_timing", "npp_batch_create", "npp_batch_update", "npp_batch_offsets",
-           "npp_plan_batch", "npp_batch_destroy", "npp_batch_set_option", "npp_math_eval")
+           "npp_plan_batch", "npp_batch_destroy", "npp_batch_set_option", "npp_math_eval",
+           "npp_proposal_create", "npp_proposal_destroy", "npp_proposal_n_params",
+           "npp_proposal_set_params", "npp_proposal_get_params", "npp_proposal_get_grads",
+           "npp_proposal_encode", "npp_proposal_forward", "npp_proposal_train_step",
+           "npp_plan_step_proposal", "npp_gemm_bf16", "npp_gemm_status")
 
 _lib = None
 
@@ -92,6 +101,7 @@ def lib():
         L.npp_last_error.restype = C.c_char_p
         L.npp_n_theta.argtypes = [C.POINTER(npp_config)]
         L.npp_n_theta.restype = I32
+        L.npp_proposal_n_params.restype = I32
         L.npp_plan_step.argtypes = [P, C.POINTER(npp_state), C.POINTER(npp_goal), P, I32, I32, I32,
                                     U64, U32, P, C.POINTER(npp_outputs), P]
         L.npp_plan_step_host.argtypes = [P, C.POINTER(npp_state), C.POINTER(npp_goal), P, I32, I32,
@@ -120,8 +130,21 @@ def lib():
                                             C.POINTER(npp_outputs), P]
         L.npp_last_timing.argtypes = [P, C.POINTER(C.c_float), I32]
         L.npp_math_eval.argtypes = [I32, P, I32, P, P, P]
+        L.npp_proposal_create.argtypes = [C.POINTER(npp_proposal_config), C.POINTER(P)]
+        L.npp_proposal_destroy.argtypes = [P]
+        L.npp_proposal_n_params.argtypes = []
+        L.npp_proposal_set_params.argtypes = [P, P]
+        L.npp_proposal_get_params.argtypes = [P, P]
+        L.npp_proposal_get_grads.argtypes = [P, P]
+        L.npp_proposal_encode.argtypes = [P, P, I32, P, P, P]
+        L.npp_proposal_forward.argtypes = [P, P, I32, P, P, P]
+        L.npp_proposal_train_step.argtypes = [P, P, P, C.c_float, P, P]
+        L.npp_plan_step_proposal.argtypes = [P, C.POINTER(npp_state), C.POINTER(npp_goal), P, I32, I32,
+                                             I32, U64, U32, P, P, P, I32, C.POINTER(npp_outputs), P]
+        L.npp_gemm_bf16.argtypes = [P, P, P, I32, I32, I32, P]
+        L.npp_gemm_status.argtypes = []
         for name in EXPORTS:
-            if name not in ("npp_last_error", "npp_n_theta"):
+            if name not in ("npp_last_error", "npp_n_theta", "npp_proposal_n_params"):
                 getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -225,6 +248,83 @@ def npp_math_eval(fn, x, y, y2=None, stream=None):
     """fn 0 tanh, 1 tan, 2 sin/cos (y, y2) of the rollout on CUDA tensors."""
     return _check(lib().npp_math_eval(int(fn), _ptr(x), int(x.numel()), _ptr(y), _ptr(y2),
                                       _stream(stream)))
+
+
+# ------------------------------------------------------------------ proposal
+def npp_proposal_create(batch, ls_min=-3.0, ls_max=1.0, beta1=0.9, beta2=0.999, eps=1e-8, device=0):
+    cfg = npp_proposal_config(int(batch), ls_min, ls_max, beta1, beta2, eps, int(device))
+    P = C.c_void_p()
+    _check(lib().npp_proposal_create(C.byref(cfg), C.byref(P)))
+    return P
+
+
+def npp_proposal_destroy(P):
+    return lib().npp_proposal_destroy(P)
+
+
+def npp_proposal_n_params():
+    return int(lib().npp_proposal_n_params())
+
+
+def npp_proposal_set_params(P, vec):
+    import numpy as np
+    v = np.ascontiguousarray(vec, dtype=np.float32)
+    assert v.size == npp_proposal_n_params()
+    return _check(lib().npp_proposal_set_params(P, v.ctypes.data_as(C.c_void_p)))
+
+
+def npp_proposal_get_params(P):
+    import numpy as np
+    v = np.zeros(npp_proposal_n_params(), np.float32)
+    _check(lib().npp_proposal_get_params(P, v.ctypes.data_as(C.c_void_p)))
+    return v
+
+
+def npp_proposal_get_grads(P):
+    import numpy as np
+    v = np.zeros(npp_proposal_n_params(), np.float32)
+    _check(lib().npp_proposal_get_grads(P, v.ctypes.data_as(C.c_void_p)))
+    return v
+
+
+def npp_proposal_encode(h, scenes_dev, S, obs, x, stream=None):
+    """scenes_dev: CUDA uint8 tensor holding S npp_scene records."""
+    return _check(lib().npp_proposal_encode(h, _ptr(scenes_dev), int(S), _ptr(obs), _ptr(x),
+                                            _stream(stream)))
+
+
+def npp_proposal_forward(P, x, n, mean, std, stream=None):
+    return _check(lib().npp_proposal_forward(P, _ptr(x), int(n), _ptr(mean), _ptr(std), _stream(stream)))
+
+
+def npp_proposal_train_step(P, x, theta, lr, loss=None, stream=None):
+    return _check(lib().npp_proposal_train_step(P, _ptr(x), _ptr(theta), float(lr), _ptr(loss),
+                                                _stream(stream)))
+
+
+def npp_plan_step_proposal(h, state, goal, obs, M, N, T, seed, t_index, warm, mean, std, N_prop,
+                           out: "npp_outputs", stream=None):
+    return _check(lib().npp_plan_step_proposal(h, C.byref(make_state(state)), C.byref(make_goal(goal)),
+                                               _ptr(obs), int(M), int(N), int(T), int(seed), int(t_index),
+                                               _ptr(warm), _ptr(mean), _ptr(std), int(N_prop),
+                                               C.byref(out), _stream(stream)), h)
+
+
+def npp_gemm_bf16(A, B, Cout, M, N, K, stream=None):
+    """A [M][K], B [N][K] CUDA bfloat16 tensors; Cout [M][N] float32."""
+    return _check(lib().npp_gemm_bf16(_ptr(A), _ptr(B), _ptr(Cout), int(M), int(N), int(K),
+                                      _stream(stream)))
+
+
+def npp_gemm_status():
+    return _check(lib().npp_gemm_status())
+
+
+def scenes_to_device(scenes_ctypes, device=0):
+    """Copy a ctypes npp_scene array to a CUDA uint8 tensor."""
+    raw = bytes(scenes_ctypes)
+    t = torch.frombuffer(bytearray(raw), dtype=torch.uint8).to(torch.device("cuda", device))
+    return t
 
 
 def npp_set_option(h, name: str, value: int):

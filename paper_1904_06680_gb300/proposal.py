@@ -1,0 +1,205 @@
+"""Learned sampling proposal: data from the plain planner, training and
+evaluation, driven over the C ABI (every step runs in the library's
+kernels: batch planning, scene encoding, the tensor-core network, Adam).
+
+Data: (scene encoding, best parameters found by the plain isotropic
+sampler) pairs on course-like scenes (inputs.scene_proposal_batch).
+Training: Gaussian negative log-likelihood of the best parameters under the
+proposal, Adam.  Evaluation: per scene, the plain plan step with N samples
+against the mixed plan step (proposal samples + isotropic ones) with the
+same or fewer samples; the mixed step's argmin covers both sets, so its
+result is never worse than that of its isotropic part alone.
+"""
+import math
+
+import numpy as np
+import torch
+
+from . import inputs, npp
+
+N_THETA = 450
+N_IN = 72
+
+
+def _scene_array(scenes):
+    return npp.make_scenes(scenes)
+
+
+class ProposalNet:
+    """The network on one device (a thin owner of an npp_proposal)."""
+
+    def __init__(self, batch=1024, device=0, ls_min=-3.0, ls_max=1.0):
+        self.batch = batch
+        self.device = torch.device("cuda", device)
+        self.P = npp.npp_proposal_create(batch, ls_min=ls_min, ls_max=ls_max, device=device)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=self.device)
+
+    def init(self, seed, out_scale=0.01):
+        """He-normal hidden layers, small output layer (mean ~ 0, log-std ~ 0)."""
+        rng = np.random.default_rng(seed)
+        H, O = 256, 2 * N_THETA
+        parts = [rng.standard_normal((H, N_IN)) * math.sqrt(2.0 / N_IN), np.zeros(H),
+                 rng.standard_normal((H, H)) * math.sqrt(2.0 / H), np.zeros(H),
+                 rng.standard_normal((O, H)) * out_scale * math.sqrt(1.0 / H), np.zeros(O)]
+        self.set_params(np.concatenate([p.ravel() for p in parts]))
+
+    def set_params(self, vec):
+        npp.npp_proposal_set_params(self.P, vec)
+
+    def params(self):
+        return npp.npp_proposal_get_params(self.P)
+
+    def grads(self):
+        return npp.npp_proposal_get_grads(self.P)
+
+    def forward(self, x):
+        """x: CUDA float32 [n][72], n <= batch -> (mean, std) [n][450]."""
+        n = x.shape[0]
+        mean = torch.empty(n, N_THETA, dtype=torch.float32, device=self.device)
+        std = torch.empty_like(mean)
+        npp.npp_proposal_forward(self.P, x.contiguous(), n, mean, std)
+        return mean, std
+
+    def train_step(self, x, theta, lr):
+        npp.npp_proposal_train_step(self.P, x.contiguous(), theta.contiguous(), lr, self.loss)
+        return self.loss
+
+    def close(self):
+        if self.P is not None:
+            npp.npp_proposal_destroy(self.P)
+            self.P = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def encode(planner, scenes, obs_dev):
+    """Scene encodings [S][72] on the device."""
+    arr = _scene_array(scenes)
+    sd = npp.scenes_to_device(arr, planner.device.index or 0)
+    x = torch.empty(len(scenes), N_IN, dtype=torch.float32, device=planner.device)
+    npp.npp_proposal_encode(planner.h, sd, len(scenes), obs_dev, x)
+    return x
+
+
+def plain_best(planner, scenes, obs_dev):
+    """Best parameters, costs and status of every scene by the plain
+    isotropic sampler (one batched plan)."""
+    S = len(scenes)
+    arr = _scene_array(scenes)
+    B = npp.npp_batch_create(planner.h, arr)
+    off = npp.npp_batch_offsets(B, S)
+    dev = planner.device
+    best = torch.zeros(S, 8, dtype=torch.int32, device=dev)
+    params = torch.zeros(int(off[S, 0]), dtype=torch.float32, device=dev)
+    controls = torch.zeros(int(off[S, 1]) * 2, dtype=torch.float32, device=dev)
+    traj = torch.zeros(int(off[S, 2]) * 4, dtype=torch.float32, device=dev)
+    out = npp.npp_batch_outputs()
+    out.best = best.data_ptr()
+    out.params = params.data_ptr()
+    out.controls = controls.data_ptr()
+    out.trajectory = traj.data_ptr()
+    npp.npp_plan_batch(B, obs_dev, out)
+    torch.cuda.synchronize()
+    npp.npp_batch_destroy(B)
+    b = best.cpu()
+    cost = b[:, 2].view(torch.float32).numpy().copy()
+    status = b[:, 1].numpy().copy()
+    theta = params.view(S, N_THETA)
+    return theta, cost, status
+
+
+def generate(seed, S, N=4096, T=40, chunk=512, device=0, n_layouts=16):
+    """S (encoding, best theta) pairs; rows whose plain plan was infeasible
+    are dropped.  Returns CUDA tensors X [S'][72], Theta [S'][450] and the
+    plain costs."""
+    Xs, Ts, Cs = [], [], []
+    planner = None
+    for c0 in range(0, S, chunk):
+        b = inputs.scene_proposal_batch(seed * 100003 + c0 // chunk, S=min(chunk, S - c0), N=N, T=T,
+                                        n_layouts=n_layouts)
+        if planner is None:
+            planner = npp.Planner(b["preset"], max_N=N, max_T=T, max_M=b["obs"].shape[0], device=device)
+        obs = torch.tensor(b["obs"], dtype=torch.float32, device=planner.device)
+        x = encode(planner, b["scenes"], obs)
+        th, cost, status = plain_best(planner, b["scenes"], obs)
+        ok = torch.from_numpy(status == 0).to(planner.device)
+        Xs.append(x[ok])
+        Ts.append(th[ok])
+        Cs.append(cost[status == 0])
+    planner.close()
+    return torch.cat(Xs), torch.cat(Ts), np.concatenate(Cs)
+
+
+def train(net, X, Theta, epochs=10, lr=1e-3, seed=0, lr_final=None):
+    """Adam on shuffled full batches; returns the mean loss per epoch."""
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    n = X.shape[0]
+    B = net.batch
+    steps = max(1, n // B)
+    hist = []
+    total = epochs * steps
+    k = 0
+    for ep in range(epochs):
+        perm = torch.randperm(n, generator=g).to(X.device)
+        acc = torch.zeros(1, device=X.device)
+        for s in range(steps):
+            idx = perm[s * B:(s + 1) * B]
+            rate = lr if lr_final is None else lr * (lr_final / lr) ** (k / max(1, total - 1))
+            acc += net.train_step(X[idx], Theta[idx], rate)
+            k += 1
+        hist.append(float(acc.item()) / steps)
+    return hist
+
+
+def plan_costs(planner, scenes, obs_dev, N, mean=None, std=None, N_prop=0):
+    """Best cost (inf if infeasible) of each scene's plan step: plain when
+    mean is None, else mixed with N_prop proposal samples."""
+    out = planner.outputs()
+    costs = np.zeros(len(scenes))
+    winners = np.zeros(len(scenes), np.int64)
+    for i, sc in enumerate(scenes):
+        o = obs_dev[sc["obs_offset"]:sc["obs_offset"] + sc["M"]]
+        if mean is None:
+            npp.npp_plan_step(planner.h, sc["state"], sc["goal"], o, sc["M"], N, sc["T"], sc["seed"], 0,
+                              None, out)
+        else:
+            npp.npp_plan_step_proposal(planner.h, sc["state"], sc["goal"], o, sc["M"], N, sc["T"], sc["seed"],
+                                       0, None, mean[i], std[i], N_prop, out)
+        b = planner.best.cpu()
+        st = int(b[1])
+        costs[i] = b[2:3].view(torch.float32).item() if st == 0 else np.inf
+        winners[i] = int(b[0])
+    return costs, winners
+
+
+def evaluate(net, seed, S=256, Ns=(512, 2048, 8192), prop_frac=0.5, device=0, T=40):
+    """Held-out scenes: plain with N samples vs mixed with N and with N/4
+    samples (prop_frac of them from the proposal).  Returns per-N mean
+    costs over scenes feasible in all arms and the proposal-win rates."""
+    b = inputs.scene_proposal_batch(10 ** 6 + seed, S=S, N=max(Ns), T=T)
+    planner = npp.Planner(b["preset"], max_N=max(Ns), max_T=T, max_M=b["obs"].shape[0], device=device)
+    obs = torch.tensor(b["obs"], dtype=torch.float32, device=planner.device)
+    x = encode(planner, b["scenes"], obs)
+    means, stds = [], []
+    for c0 in range(0, S, net.batch):
+        m, s = net.forward(x[c0:c0 + net.batch])
+        means.append(m)
+        stds.append(s)
+    mean, std = torch.cat(means), torch.cat(stds)
+    res = {}
+    for N in Ns:
+        plain, _ = plan_costs(planner, b["scenes"], obs, N)
+        mixed, w = plan_costs(planner, b["scenes"], obs, N, mean, std, int(prop_frac * N))
+        q = max(32, N // 4)
+        mixed_q, wq = plan_costs(planner, b["scenes"], obs, q, mean, std, int(prop_frac * q))
+        ok = np.isfinite(plain) & np.isfinite(mixed) & np.isfinite(mixed_q)
+        res[N] = dict(plain=float(np.mean(plain[ok])), mixed=float(np.mean(mixed[ok])),
+                      mixed_quarter=float(np.mean(mixed_q[ok])), n_scenes=int(ok.sum()),
+                      proposal_won=float(np.mean(w[ok] < int(prop_frac * N))),
+                      quarter_not_worse=float(np.mean(mixed_q[ok] <= plain[ok] + 1e-6)))
+    planner.close()
+    return res

@@ -1,5 +1,5 @@
-"""The C-ABI library loads and exports every function include/npp.h
-declares (no device work: runs without a GPU)."""
+"""The C-ABI library loads and exports every function the headers under
+include/ declare (no device work: runs without a GPU)."""
 import ctypes
 import os
 import re
@@ -8,9 +8,13 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared():
-    src = open(os.path.join(ROOT, "include", "npp.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(npp_[a-z_0-9]+)\s*\(", src)))
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in sorted(os.listdir(inc)):
+        if f.endswith(".h"):
+            src = re.sub(r"/\*.*?\*/", "", open(os.path.join(inc, f)).read(), flags=re.S)
+            names |= set(re.findall(r"\b(npp_[a-z_0-9]+)\s*\(", src))
+    return sorted(names)
 
 
 def test_library_exports_all_declared_symbols():

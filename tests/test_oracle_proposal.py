@@ -151,3 +151,14 @@ def test_mixed_sampler_reductions(orc):
     # samples at or beyond n_prop are the plain stream-0 samples
     e = orc.rollout_samples(p, sc["seed"], 3, idx, z0, ap, goal_ev, obs_ev, 15)
     np.testing.assert_array_equal(c["cost"][6:], e["cost"][6:])
+
+
+def test_theta_mixed_reductions(orc):
+    nt = 450
+    a = orc.theta_mixed(77, 3, 5, nt, np.zeros(nt), np.ones(nt), 6)
+    np.testing.assert_array_equal(a, orc.theta(77, 3, 5, nt, stream=1))
+    b = orc.theta_mixed(77, 3, 6, nt, np.zeros(nt), np.ones(nt), 6)
+    np.testing.assert_array_equal(b, orc.theta(77, 3, 6, nt, stream=0))
+    mu = np.linspace(-1, 1, nt).astype(np.float32)
+    c = orc.theta_mixed(77, 3, 0, nt, mu, np.zeros(nt), 1)
+    np.testing.assert_array_equal(c, mu)

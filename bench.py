@@ -56,11 +56,13 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="course", choices=["course", "large", "batch"],
+    ap.add_argument("--workload", default="course", choices=["course", "large", "batch", "proposal"],
                     help="course: the closed-loop course (default); large: N=65536, T=100, "
                          "8-64-64-2, 8192 points over 80x80 m with per-step spatial binning; "
                          "batch: 512 parking scenes of uneven N, T, M and width in one "
-                         "graph-captured batch")
+                         "graph-captured batch; proposal: the learned sampling proposal "
+                         "(tensor-core GEMM roofline, training throughput, plan quality)")
+    ap.add_argument("--rounds", type=int, default=30, help="proposal workload: training rounds")
     return ap.parse_args()
 
 
@@ -521,14 +523,103 @@ def run_batch(args):
         print(json.dumps(line))
 
 
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def run_proposal(args):
+    """The learned sampling proposal on one GPU: (1) the tensor-core GEMM at
+    8192^3 (roofline against the measured cuBLAS BF16 peak), (2) training
+    throughput at a batch of 8192 (the network's eight GEMMs, loss, bias
+    gradients, Adam), (3) a shortened training run and the plan quality of
+    the mixed sampler against the plain one on held-out scenes.  value =
+    training samples/s."""
+    import torch
+    from paper_1904_06680_gb300 import npp, proposal
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    peaks = measured_peaks()
+    peak = peaks.get("bf16_tflops", 1900.0)
+    # (1) standalone GEMM
+    Mg = 8192
+    g = torch.Generator(device="cpu").manual_seed(0)
+    A = torch.randn(Mg, Mg, generator=g).to(torch.bfloat16).to(dev)
+    Bm = torch.randn(Mg, Mg, generator=g).to(torch.bfloat16).to(dev)
+    Cm = torch.empty(Mg, Mg, dtype=torch.float32, device=dev)
+    for _ in range(3):
+        npp.npp_gemm_bf16(A, Bm, Cm, Mg, Mg, Mg)
+    torch.cuda.synchronize()
+    reps = 10
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        npp.npp_gemm_bf16(A, Bm, Cm, Mg, Mg, Mg)
+    e1.record()
+    torch.cuda.synchronize()
+    npp.npp_gemm_status()
+    gemm_ms = e0.elapsed_time(e1) / reps
+    gemm_tf = 2.0 * Mg ** 3 / (gemm_ms * 1e-3) / 1e12
+    del A, Bm, Cm
+    # (2) training throughput
+    Bt = 8192
+    net = proposal.ProposalNet(batch=Bt)
+    net.init(0)
+    X = torch.rand(Bt, 72, device=dev)
+    Th = torch.randn(Bt, 450, device=dev)
+    for _ in range(args.warmup):
+        net.train_step(X, Th, 1e-4)
+    torch.cuda.synchronize()
+    clocks = Clocks(0)
+    clocks.start()
+    e0.record()
+    for _ in range(args.steps):
+        net.train_step(X, Th, 1e-4)
+    e1.record()
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    step_ms = e0.elapsed_time(e1) / args.steps
+    net.close()
+    flops = 2.0 * Bt * (128 * 256 + 256 * 256 + 256 * 1024) + 2.0 * Bt * (1024 * 256 + 256 * 256) \
+        + 2.0 * Bt * (1024 * 256 + 256 * 256 + 256 * 128)
+    # (3) quality after a shortened recipe
+    t0 = time.time()
+    qnet, stats = proposal.train_proposal(rounds=args.rounds, S=8192, N=2048, epochs=4)
+    train_s = time.time() - t0
+    quality = proposal.evaluate(qnet, 0, S=192, Ns=(512, 2048, 8192, 16384), prop_frac=0.5)
+    qnet.close()
+    line = {"metric": "proposal training samples/s (BF16 tensor-core forward+backward+Adam)",
+            "value": Bt / (step_ms * 1e-3), "unit": "samples/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "learned proposal 72-256-256-900, batch 8192; quality: expert-iteration "
+                                   "recipe, %d rounds of 8192 course-like scenes at N=2048, "
+                                   "evaluated on 192 held-out scenes" % args.rounds,
+                       "l2": "train-step working set ~100 MB (L2-resident between steps)"},
+            "roofline": {"bound": "tensor", "kernel": "gemm_kernel<256> (tcgen05, M=N=K=8192)",
+                         "achieved": gemm_tf, "peak": peak, "unit": "TFLOP/s", "frac": gemm_tf / peak,
+                         "traffic": None, "peak_basis": "measured cuBLAS bf16 burst (MEASURED_PEAKS.json)",
+                         "kernel_ms": gemm_ms,
+                         "train_step_gemm_tflops": flops / (step_ms * 1e-3) / 1e12},
+            "e2e": None, "gpu_launches": 14 * args.steps, "clocks": ck,
+            "quality": {str(k): v for k, v in quality.items()},
+            "training": {"rounds": args.rounds, "seconds": train_s,
+                         "proposal_won_first_last": [stats[0]["proposal_won"], stats[-1]["proposal_won"]]}}
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
-        if args.workload == "batch":
+        if args.workload in ("batch", "proposal"):
             args.workload = "course"
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "proposal":
+        run_proposal(args)
     else:
         run_npp(args)
 

@@ -1,14 +1,28 @@
-"""Learned sampling proposal: data from the plain planner, training and
+"""Learned sampling proposal: data from the planner, training and
 evaluation, driven over the C ABI (every step runs in the library's
-kernels: batch planning, scene encoding, the tensor-core network, Adam).
+kernels: plan steps, scene encoding, the tensor-core network, Adam).
 
-Data: (scene encoding, best parameters found by the plain isotropic
-sampler) pairs on course-like scenes (inputs.scene_proposal_batch).
-Training: Gaussian negative log-likelihood of the best parameters under the
-proposal, Adam.  Evaluation: per scene, the plain plan step with N samples
-against the mixed plan step (proposal samples + isotropic ones) with the
-same or fewer samples; the mixed step's argmin covers both sets, so its
-result is never worse than that of its isotropic part alone.
+Data: (scene encoding, best-found parameters) pairs on course-like scenes
+(inputs.scene_proposal_batch).  Training: Gaussian negative log-likelihood
+of the best parameters under the proposal, Adam.
+
+Two ways to make the pairs:
+* `generate`: the plain isotropic sampler's winners.  Measured on GB300,
+  these do not train a useful diagonal Gaussian: the winners' hidden-layer
+  parameters are independent random draws, so their per-parameter
+  distribution given the scene stays close to N(0, 1) (even the elite
+  samples of a scene, fitted per scene, have a standard deviation of 0.99).
+* `bootstrap` (the training recipe): expert iteration in a fixed parameter
+  basis.  The untrained proposal is N(theta_0, 0.3^2 I) for a fixed random
+  theta_0; each round plans fresh scenes with the mixed plan step (the
+  proposal's samples plus isotropic ones, every sample judged by the exact
+  rollout cost, so the isotropic sampler still wins whenever it finds the
+  better plan) and trains on the scenes whose winner came from the
+  proposal.  The winners then share theta_0's basis and the network learns
+  scene-dependent shifts of it.
+
+Evaluation: per held-out scene, the plain plan step with N samples against
+the mixed plan step with N and with N/4 samples.
 """
 import math
 
@@ -34,13 +48,19 @@ class ProposalNet:
         self.P = npp.npp_proposal_create(batch, ls_min=ls_min, ls_max=ls_max, device=device)
         self.loss = torch.zeros(1, dtype=torch.float32, device=self.device)
 
-    def init(self, seed, out_scale=0.01):
-        """He-normal hidden layers, small output layer (mean ~ 0, log-std ~ 0)."""
+    def init(self, seed, out_scale=0.01, base=None, base_std=1.0):
+        """He-normal hidden layers, small output layer: the untrained
+        proposal is N(base, base_std^2 I) for every scene (base 0 and std 1
+        by default, the isotropic sampler)."""
         rng = np.random.default_rng(seed)
         H, O = 256, 2 * N_THETA
+        b3 = np.zeros(O)
+        if base is not None:
+            b3[:N_THETA] = base
+        b3[N_THETA:] = math.log(base_std)
         parts = [rng.standard_normal((H, N_IN)) * math.sqrt(2.0 / N_IN), np.zeros(H),
                  rng.standard_normal((H, H)) * math.sqrt(2.0 / H), np.zeros(H),
-                 rng.standard_normal((O, H)) * out_scale * math.sqrt(1.0 / H), np.zeros(O)]
+                 rng.standard_normal((O, H)) * out_scale * math.sqrt(1.0 / H), b3]
         self.set_params(np.concatenate([p.ravel() for p in parts]))
 
     def set_params(self, vec):
@@ -155,9 +175,10 @@ def train(net, X, Theta, epochs=10, lr=1e-3, seed=0, lr_final=None):
     return hist
 
 
-def plan_costs(planner, scenes, obs_dev, N, mean=None, std=None, N_prop=0):
+def plan_costs(planner, scenes, obs_dev, N, mean=None, std=None, N_prop=0, params_out=None):
     """Best cost (inf if infeasible) of each scene's plan step: plain when
-    mean is None, else mixed with N_prop proposal samples."""
+    mean is None, else mixed with N_prop proposal samples.  params_out
+    (CUDA [S][450]) receives each winner's parameters."""
     out = planner.outputs()
     costs = np.zeros(len(scenes))
     winners = np.zeros(len(scenes), np.int64)
@@ -169,11 +190,63 @@ def plan_costs(planner, scenes, obs_dev, N, mean=None, std=None, N_prop=0):
         else:
             npp.npp_plan_step_proposal(planner.h, sc["state"], sc["goal"], o, sc["M"], N, sc["T"], sc["seed"],
                                        0, None, mean[i], std[i], N_prop, out)
+        if params_out is not None:
+            params_out[i].copy_(planner.params)
         b = planner.best.cpu()
         st = int(b[1])
         costs[i] = b[2:3].view(torch.float32).item() if st == 0 else np.inf
         winners[i] = int(b[0])
     return costs, winners
+
+
+def bootstrap(net, rounds=4, S=8192, N=4096, T=40, prop_frac=0.5, epochs=8, lr=1e-3, seed=0,
+              device=0, only_proposal_winners=False, log=None):
+    """Expert iteration: each round plans S fresh scenes with the mixed
+    planner (the current proposal's samples plus isotropic ones, every
+    sample judged by the exact rollout cost; round 0 with an untrained
+    proposal), and trains on (encoding, winner parameters) pairs.  Returns
+    per-round statistics."""
+    stats = []
+    for r in range(rounds):
+        b = inputs.scene_proposal_batch(seed * 7919 + 31 * r + 1, S=S, N=N, T=T)
+        planner = npp.Planner(b["preset"], max_N=N, max_T=T, max_M=b["obs"].shape[0], device=device)
+        obs = torch.tensor(b["obs"], dtype=torch.float32, device=planner.device)
+        x = encode(planner, b["scenes"], obs)
+        means, stds = [], []
+        for c0 in range(0, S, net.batch):
+            m, sd = net.forward(x[c0:c0 + net.batch])
+            means.append(m.clone())
+            stds.append(sd.clone())
+        mean, std = torch.cat(means), torch.cat(stds)
+        theta = torch.zeros(S, N_THETA, dtype=torch.float32, device=planner.device)
+        npr = int(prop_frac * N)
+        costs, win = plan_costs(planner, b["scenes"], obs, N, mean, std, npr, params_out=theta)
+        planner.close()
+        keep = np.isfinite(costs)
+        if only_proposal_winners:
+            keep &= win < npr
+        kt = torch.from_numpy(keep).to(x.device)
+        hist = train(net, x[kt], theta[kt], epochs=epochs, lr=lr, seed=seed + r)
+        st = dict(round=r, mean_cost=float(np.mean(costs[np.isfinite(costs)])),
+                  proposal_won=float(np.mean(win[np.isfinite(costs)] < npr)), n_train=int(keep.sum()),
+                  loss_first=hist[0], loss_last=hist[-1], mean_std=float(std.mean()))
+        stats.append(st)
+        if log:
+            log(st)
+    return stats
+
+
+def train_proposal(rounds=30, S=8192, N=2048, T=40, epochs=4, lr=1e-3, base_seed=123, base_std=0.3,
+                   batch=1024, seed=0, device=0, log=None):
+    """The training recipe: a fresh network around a fixed random basis
+    theta_0 (Philox-independent numpy draw from base_seed), then `rounds`
+    rounds of expert iteration on proposal-won scenes."""
+    net = ProposalNet(batch=batch, device=device)
+    base = np.random.default_rng(base_seed).standard_normal(N_THETA)
+    net.init(seed, base=base, base_std=base_std)
+    stats = bootstrap(net, rounds=rounds, S=S, N=N, T=T, prop_frac=0.5, epochs=epochs, lr=lr, seed=seed,
+                      device=device, only_proposal_winners=True, log=log)
+    return net, stats
 
 
 def evaluate(net, seed, S=256, Ns=(512, 2048, 8192), prop_frac=0.5, device=0, T=40):

@@ -234,22 +234,28 @@ def test_mixed_plan_rejects_bad_arguments():
     pl.close()
 
 
-def test_learned_proposal_end_to_end_small():
-    """Data from the plain planner, a short training run, and the mixed
-    planner on held-out scenes: the training loss falls and the mixed plan
-    at the same sample count is never worse on average than plain
-    (its isotropic half alone is a plain plan of half the samples, so this
-    checks that the proposal half adds)."""
-    import torch
+def test_plain_pairs_and_training_run():
+    """Pairs from the plain batched planner feed the training loop."""
     from paper_1904_06680_gb300 import proposal
     X, Th, cost = proposal.generate(0, 1024, N=1024, T=40, chunk=512)
-    assert X.shape[0] > 512 and Th.shape == (X.shape[0], 450)
+    assert X.shape[0] > 512 and Th.shape == (X.shape[0], 450) and np.all(np.isfinite(cost))
     net = proposal.ProposalNet(batch=256)
     net.init(0)
-    hist = proposal.train(net, X, Th, epochs=20, lr=1e-3)
+    hist = proposal.train(net, X, Th, epochs=5, lr=1e-3)
     assert hist[-1] < hist[0], hist
-    res = proposal.evaluate(net, 0, S=48, Ns=(512,))
-    r = res[512]
-    assert r["n_scenes"] > 24
-    assert np.isfinite(r["mixed"]) and np.isfinite(r["plain"])
+    net.close()
+
+
+def test_learned_proposal_gains_over_plain():
+    """The training recipe, shortened (8 rounds of 4096 scenes at N = 2048),
+    then held-out scenes: the mixed plan step (half proposal samples) at
+    N = 512 has a clearly lower mean cost than the plain one at N = 512,
+    and the proposal's samples win most scenes."""
+    from paper_1904_06680_gb300 import proposal
+    net, stats = proposal.train_proposal(rounds=8, S=4096, N=2048, epochs=4)
+    assert stats[-1]["proposal_won"] > stats[0]["proposal_won"] + 0.08, stats
+    res = proposal.evaluate(net, 1, S=96, Ns=(512,), prop_frac=0.5)[512]
+    assert res["n_scenes"] > 60
+    assert res["mixed"] < res["plain"] - 0.1, res
+    assert res["proposal_won"] > 0.55, res
     net.close()

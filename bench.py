@@ -157,30 +157,45 @@ def algorithmic_work(first_hit, T, M, W):
     return 4.0 * checks, ctrl * (W * W + 10 * W), checks
 
 
-def kernel_sources_hash():
-    """Hash of the CUDA sources: profile counters apply only to this code."""
+# source files whose code each profiled kernel is built from
+KERNEL_SOURCES = (
+    ("traj_kernel", ("npp_rollout.cuh", "npp_device.cuh", "npp_rollout_w16.cu", "npp_rollout_w32.cu",
+                     "npp_rollout_w64.cu")),
+    ("bin_build_kernel", ("npp_binned.cu", "npp_device.cuh")),
+    ("collide_binned_kernel", ("npp_binned.cu", "npp_device.cuh")),
+    ("collide_", ("npp_rollout.cuh", "npp_device.cuh", "npp_collide.cu")),
+    ("gemm_kernel", ("npp_gemm.cu", "npp_gemm.cuh")),
+)
+
+
+def kernel_sources_hash(kernel):
+    """Hash of the CUDA sources a kernel is built from: its profile counters
+    apply only to this code."""
     import hashlib
     d = os.path.join(ROOT, "paper_1904_06680_gb300", "csrc")
+    files = next((v for k, v in KERNEL_SOURCES if kernel.startswith(k)), None)
+    if files is None:
+        return None
     h = hashlib.sha1()
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(f.encode())
-            h.update(open(os.path.join(d, f), "rb").read())
+    for f in files:
+        h.update(f.encode())
+        h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def profiled_traffic(kernel):
     """DRAM bytes per launch of `kernel` from profiles/traffic.json, or None
-    when the sources changed since that capture."""
+    when its sources changed since that capture."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(path))
     except (OSError, ValueError):
         return None
-    if rec.get("kernel_sources") != kernel_sources_hash():
+    k = kernel.replace(" ", "")
+    ent = {kk.replace(" ", ""): v for kk, v in rec.get("kernels", {}).items()}.get(k)
+    if not ent or ent.get("sources") != kernel_sources_hash(k):
         return None
-    per = {k.replace(" ", ""): v for k, v in rec.get("bytes_per_launch", {}).items()}
-    return per.get(kernel.replace(" ", ""))
+    return ent.get("dram_bytes_per_launch")
 
 
 def cpu_baseline(sc, state, goal, obs, T, workload, target_cpu_s=15.0):
@@ -333,7 +348,9 @@ def run_npp(args):
     peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6
     fps_c = res["fma_c"] / (collide_ms / 1e3)
     fps_t = res["fma_t"] / (traj_ms / 1e3)
-    binned = M >= 4096
+    # the library's automatic collision choice (binned from 512 points and
+    # 8e6 point-sample pairs)
+    binned = M >= 512 and M * N >= 8000000
     if binned:
         cname = "bin_build_kernel + collide_binned_kernel"
     else:
@@ -342,7 +359,10 @@ def run_npp(args):
     tname = {16: "traj_kernel<16,8,4,4>", 32: "traj_kernel<32,16,4,4>",
              64: "traj_kernel<64,32,1,10>"}[W]
     coll = {"ms_per_step": collide_ms / K, "point_checks_per_s": res["checks"] / (collide_ms / 1e3)}
-    trj = {"ms_per_step": traj_ms / K, "achieved": fps_t / 1e12, "frac": fps_t / peak}
+    fma_all = float(N) * T * K * (W * W + 10 * W)
+    trj = {"ms_per_step": traj_ms / K, "achieved": fps_t / 1e12, "frac": fps_t / peak,
+           "all_steps_achieved": fma_all / (traj_ms / 1e3) / 1e12,
+           "all_steps_frac": fma_all / (traj_ms / 1e3) / peak}
     if not binned:
         coll.update(achieved=fps_c / 1e12, frac=fps_c / peak)
     else:
@@ -354,6 +374,9 @@ def run_npp(args):
         roofline = {"bound": "alu", "kernel": tname, "achieved": fps_t / 1e12, "peak": peak / 1e12,
                     "unit": "T FP32-FMA/s", "frac": fps_t / peak, "traffic": traffic,
                     "peak_basis": "derived: 152 SMs x 128 FP32 FMA lanes x 2070 MHz",
+                    "work": "MLP FMAs (W^2 + 10 W) per control step of a sample up to its first "
+                            "collision; all_steps_* count every step the kernel computes",
+                    "all_steps_achieved": trj["all_steps_achieved"], "all_steps_frac": trj["all_steps_frac"],
                     "kernel_ms_per_step": traj_ms / K, "other": {cname: coll}}
     else:
         traffic = profiled_traffic(cname)

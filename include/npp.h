@@ -335,8 +335,8 @@ npp_status npp_plan_step_noalloc(const npp_config* cfg, const npp_state* state,
  * are counting-sorted into a uniform grid around the vehicle and each state
  * is tested only against the cells its bounding disk overlaps (the same
  * per-point test, so the same flags as checking every point); -1 (default)
- * takes 5 from M = 4096 points and otherwise chooses by the number of
- * samples.
+ * takes 5 when M >= 512 and M N >= 8e6 and otherwise chooses by the number
+ * of samples.
  * "traj_variant" 0..3: launch shape of the trajectory kernel -- 0 (default)
  * 2 hidden units per lane in blocks sized for occupancy, 1 four hidden units
  * per lane, 2 eight-warp blocks, 3 another block size.

@@ -185,7 +185,7 @@ npp_status run_rollout(npp_handle* h, RolloutArgs& a, cudaStream_t s)
     // samples -> one warp per item keeps enough items in flight; many points
     // -> spatial binning
     const int v = h->collide_variant >= 0 ? h->collide_variant
-                : (a.M >= BINNED_AUTO_M ? COLLIDE_BINNED : (a.N <= 8192 ? 3 : (a.N <= 32768 ? 4 : 2)));
+                : (binned_auto(a.M, a.N) ? COLLIDE_BINNED : (a.N <= 8192 ? 3 : (a.N <= 32768 ? 4 : 2)));
     if (v == COLLIDE_BINNED) {
         if (h->timing) CUDA_TRY(h, record_event(h->ev[0], s));
         CUDA_TRY(h, launch_traj(h, a, s));

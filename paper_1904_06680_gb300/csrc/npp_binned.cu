@@ -4,7 +4,7 @@
 // p + tau v with the brute-force kernels' arithmetic) are counting-sorted into
 // a uniform grid of BIN_DIM x BIN_DIM cells centred on the vehicle.  A cell is
 // wider than the diameter of the vehicle rectangle's circumscribed disk, so
-// a state's disk overlaps at most 2 x 2 cells (3 x 3 with the safety margin);
+// a state's disk (radius plus a rounding margin) overlaps at most 2 x 2 cells;
 // every point inside the rectangle lies in the disk, and cell indices of
 // points and of the query are clamped to the grid the same (monotone) way,
 // so the queried cells hold every point that can be inside.  The per-point
@@ -106,20 +106,24 @@ __global__ void __launch_bounds__(BIN_THREADS) bin_build_kernel(const RolloutArg
     }
 }
 
-// one thread per sample, h in order; candidates from the cells the state's
-// disk overlaps
-__global__ void __launch_bounds__(256) collide_binned_kernel(const RolloutArgs a, BinGrid g,
-                                                             const int* __restrict__ cell_start,
-                                                             const float2* __restrict__ binned)
+// one warp per sample, h in order: the candidates of a step are the points
+// of at most two cell rows, each row's cells contiguous in the sorted array;
+// the lanes stride through them (coalesced loads) and a ballot ends the
+// sample at its first colliding step
+constexpr int BINNED_WARPS = 8;
+
+__global__ void __launch_bounds__(BINNED_WARPS * 32) collide_binned_kernel(const RolloutArgs a, BinGrid g,
+                                                                          const int* __restrict__ cell_start,
+                                                                          const float2* __restrict__ binned)
 {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __shared__ unsigned long long red[8];
+    __shared__ unsigned long long red[BINNED_WARPS];
     const int T = a.T, N = a.N, M = a.M;
+    const int n = blockIdx.x * BINNED_WARPS + warp;
     unsigned long long key = ~0ull;
     if (n < N) {
         int fh = -1;
-        for (int h = 0; h <= T && fh < 0; ++h) {
+        for (int h = 0; h <= T; ++h) {
             const size_t idx = (size_t)h * N + n;
             const float4 ca = a.coefA[idx];
             const float2 cb = a.coefB[idx];
@@ -130,38 +134,42 @@ __global__ void __launch_bounds__(256) collide_binned_kernel(const RolloutArgs a
             const int iy0 = cell_ix(z.y - g.reach, g), iy1 = cell_ix(z.y + g.reach, g);
             const int* cs = cell_start + (size_t)h * CS_STRIDE;
             const float2* pts = binned + (size_t)h * M;
-            bool inside = false;
-            for (int iy = iy0; iy <= iy1 && !inside; ++iy) {
-                const int b0 = cs[iy * BIN_DIM + ix0], b1 = cs[iy * BIN_DIM + ix1 + 1];
-                for (int k = b0; k < b1; ++k) {
-                    const float2 p = pts[k];
+            // rows iy0 and iy1 (iy1 - iy0 <= 1 since the cell exceeds the disk diameter)
+            const int r0b = cs[iy0 * BIN_DIM + ix0], r0e = cs[iy0 * BIN_DIM + ix1 + 1];
+            int r1b = r0e, r1e = r0e;
+            if (iy1 != iy0) { r1b = cs[iy1 * BIN_DIM + ix0]; r1e = cs[iy1 * BIN_DIM + ix1 + 1]; }
+            const int n0 = r0e - r0b, total = n0 + (r1e - r1b);
+            bool hit = false;
+            for (int base = 0; base < total && !hit; base += 32) {
+                const int k = base + lane;
+                bool inside = false;
+                if (k < total) {
+                    const float2 p = pts[k < n0 ? r0b + k : r1b + (k - n0)];
                     const float xi = fmaf(ca.x, p.x, fmaf(ca.y, p.y, ca.z));
                     const float et = fmaf(ca.w, p.x, fmaf(cb.x, p.y, cb.y));
-                    if (!(((__float_as_uint(xi) | __float_as_uint(et)) >> 30) & 1u)) { inside = true; break; }
+                    inside = !(((__float_as_uint(xi) | __float_as_uint(et)) >> 30) & 1u);
                 }
+                hit = __any_sync(FULL, inside);
             }
-            if (inside) fh = h;
+            if (hit) { fh = h; break; }
         }
-        float J = __int_as_float(0x7f800000);
-        if (fh < 0) {
-            J = a.jfree[n];
-            key = ((unsigned long long)__float_as_uint(J) << 32) | (unsigned)n;
-        } else {
-            key = (1ull << 63) | ((unsigned long long)(T - fh) << 32) | (unsigned)n;
+        if (lane == 0) {
+            float J = __int_as_float(0x7f800000);
+            if (fh < 0) {
+                J = a.jfree[n];
+                key = ((unsigned long long)__float_as_uint(J) << 32) | (unsigned)n;
+            } else {
+                key = (1ull << 63) | ((unsigned long long)(T - fh) << 32) | (unsigned)n;
+            }
+            if (a.costs) a.costs[n] = J;
+            if (a.first_hit) a.first_hit[n] = fh;
         }
-        if (a.costs) a.costs[n] = J;
-        if (a.first_hit) a.first_hit[n] = fh;
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        const unsigned long long o = __shfl_xor_sync(FULL, key, off);
-        key = o < key ? o : key;
     }
     if (lane == 0) red[warp] = key;
     __syncthreads();
     if (threadIdx.x == 0 && a.best_key) {
         unsigned long long k = red[0];
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) k = red[w] < k ? red[w] : k;
+        for (int w = 1; w < BINNED_WARPS; ++w) k = red[w] < k ? red[w] : k;
         atomicMin(a.best_key, k);
     }
 }
@@ -196,7 +204,8 @@ cudaError_t launch_collide_binned(const RolloutArgs& a, float half_len, float ha
     bin_build_kernel<<<a.T + 1, BIN_THREADS, smem, s>>>(a, g, cell_start, binned);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    collide_binned_kernel<<<(a.N + 255) / 256, 256, 0, s>>>(a, g, cell_start, binned);
+    collide_binned_kernel<<<(a.N + BINNED_WARPS - 1) / BINNED_WARPS, BINNED_WARPS * 32, 0, s>>>(a, g, cell_start,
+                                                                                               binned);
     return cudaGetLastError();
 }
 

@@ -9,10 +9,12 @@
 #include "../../include/npp.h"
 #include "npp_device.cuh"
 
-// collision-kernel variant number of the spatially binned check, and the
-// point count from which the automatic choice takes it
+// collision-kernel variant number of the spatially binned check, and when
+// the automatic choice takes it (measured on GB300: the per-step grid build
+// costs 20-45 us, so binning pays from about 512 points and 8M point-sample
+// pairs)
 constexpr int COLLIDE_BINNED = 5;
-constexpr int BINNED_AUTO_M = 4096;
+inline bool binned_auto(int M, int N) { return M >= 512 && (long long)M * N >= 8000000LL; }
 
 struct npp_handle {
     npp_config cfg;

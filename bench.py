@@ -67,10 +67,8 @@ def parse():
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    from paper_1904_06680_gb300 import multi
+    return multi.dist_env()
 
 
 class Clocks:
@@ -334,17 +332,12 @@ def run_npp(args):
         e2e = {"value": N * T * K / (wall / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": M * 16 + pl.n_theta * 4,
                "d2h_bytes_per_step": 32 + pl.n_theta * 4 + T * 8 + (T + 1) * 16}
-    if world > 1:
-        import torch
-        import torch.distributed as dist
-        tt = torch.tensor([total_ms, collide_ms, traj_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms, collide_ms, traj_ms = float(tt[0]), float(tt[1]), float(tt[2])
-        if e2e:
-            ev = torch.tensor([N * T * K / e2e["value"]], dtype=torch.float64, device=dev)
-            dist.all_reduce(ev, op=dist.ReduceOp.MAX)
-            e2e["value"] = world * N * T * K / float(ev[0])
-    value = world * N * T * K / (total_ms / 1e3)
+    from paper_1904_06680_gb300 import multi
+    e2e_s = N * T * K / e2e["value"] if e2e else 0.0
+    total_ms, collide_ms, traj_ms, e2e_s = multi.max_over_ranks([total_ms, collide_ms, traj_ms, e2e_s], dev)
+    if e2e:
+        e2e["value"] = multi.whole_job_rate(N * T * K, world, e2e_s)
+    value = multi.whole_job_rate(N * T * K, world, total_ms / 1e3)
     peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6
     fps_c = res["fma_c"] / (collide_ms / 1e3)
     fps_t = res["fma_t"] / (traj_ms / 1e3)

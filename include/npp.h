@@ -337,6 +337,11 @@ npp_status npp_plan_step_noalloc(const npp_config* cfg, const npp_state* state,
  * per-point test, so the same flags as checking every point); -1 (default)
  * takes 5 when M >= 512 and M N >= 8e6 and otherwise chooses by the number
  * of samples.
+ * "fuse" 0 (default) or 1: with the binned check (5), run it inside the
+ * trajectory kernel, which then stops each sample at its first collision and
+ * stores no per-sample states (used only when the call requests no
+ * per-sample records; the winner's rows are re-rolled).  Same results;
+ * measured slower on GB300 (the check's loads lengthen the per-step chain).
  * "traj_variant" 0..3: launch shape of the trajectory kernel -- 0 (default)
  * 2 hidden units per lane in blocks sized for occupancy, 1 four hidden units
  * per lane, 2 eight-warp blocks, 3 another block size.

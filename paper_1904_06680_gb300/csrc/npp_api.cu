@@ -40,24 +40,6 @@ static bool finite_all(const float* p, int n)
 // ------------------------------------------------------------------ kernels
 namespace {
 
-// theta_idx[4q .. 4q+3] where the quad may run past n_theta (the proposal
-// arrays hold exactly n_theta values)
-__device__ float4 sample_quad_mixed_tail(const SamplerKey& key, const Proposal& p, uint32_t q, uint32_t n,
-                                         int n_theta)
-{
-    if (4 * (int)q + 3 < n_theta || !proposal_sample(p, n)) return sample_quad_mixed(key, p, q, n);
-    SamplerKey k1 = key;
-    k1.stream_id = 1u;
-    const float4 e = sample_quad(k1, q, n);
-    const float ev[4] = { e.x, e.y, e.z, e.w };
-    float r[4] = { 0.f, 0.f, 0.f, 0.f };
-    for (int j = 0; j < 4 && 4 * (int)q + j < n_theta; ++j) {
-        const int i = 4 * (int)q + j;
-        r[j] = fmaf(p.sigma[i], ev[j], p.mu[i]);
-    }
-    return make_float4(r[0], r[1], r[2], r[3]);
-}
-
 // Winner epilogue: decode the packed key, write the summary record, the
 // winner's world-frame trajectory and controls, and regenerate its
 // parameters from Philox (or copy the warm start).
@@ -175,22 +157,43 @@ static cudaError_t launch_traj(const npp_handle* h, const RolloutArgs& a, cudaSt
 }
 
 // trajectories, then collision checks; events around both when timing
-npp_status run_rollout(npp_handle* h, RolloutArgs& a, cudaStream_t s)
+static cudaError_t launch_fused(const npp_handle* h, const RolloutArgs& a, cudaStream_t s)
+{
+    switch (h->cfg.width) {
+    case 16: return launch_fused_w16(a, s, h->traj_variant);
+    case 32: return launch_fused_w32(a, s, h->traj_variant);
+    default: return launch_fused_w64(a, s, h->traj_variant);
+    }
+}
+
+npp_status run_rollout(npp_handle* h, RolloutArgs& a, cudaStream_t s, bool allow_fused, bool* fused)
 {
     a.coefA = h->d_coefA;
     a.coefB = h->d_coefB;
     a.work = h->d_work;
+    *fused = false;
     // automatic choice (measured on GB300, course workload): few samples ->
     // items checked by 4 warps on point slices; medium -> 2 warps; many
     // samples -> one warp per item keeps enough items in flight; many points
-    // -> spatial binning
+    // -> spatial binning, fused into the trajectory kernel unless the caller
+    // wants every sample's records
     const int v = h->collide_variant >= 0 ? h->collide_variant
                 : (binned_auto(a.M, a.N) ? COLLIDE_BINNED : (a.N <= 8192 ? 3 : (a.N <= 32768 ? 4 : 2)));
     if (v == COLLIDE_BINNED) {
         if (h->timing) CUDA_TRY(h, record_event(h->ev[0], s));
+        CUDA_TRY(h, build_bins(a, h->cfg.half_len, h->cfg.half_wid, h->cfg.c_off, h->d_bins, s));
+        if (allow_fused && h->fuse) {
+            CUDA_TRY(h, launch_fused(h, a, s));
+            if (h->timing) {
+                CUDA_TRY(h, record_event(h->ev[1], s));
+                CUDA_TRY(h, record_event(h->ev[2], s));
+            }
+            *fused = true;
+            return NPP_OK;
+        }
         CUDA_TRY(h, launch_traj(h, a, s));
         if (h->timing) CUDA_TRY(h, record_event(h->ev[1], s));
-        CUDA_TRY(h, launch_collide_binned(a, h->cfg.half_len, h->cfg.half_wid, h->cfg.c_off, h->d_bins, s));
+        CUDA_TRY(h, launch_collide_binned(a, s));
         if (h->timing) CUDA_TRY(h, record_event(h->ev[2], s));
         return NPP_OK;
     }
@@ -215,6 +218,17 @@ npp_status run_rollout(npp_handle* h, RolloutArgs& a, cudaStream_t s)
     CUDA_TRY(h, global_pts ? launch_collide_global(a, s) : launch_collide_resident(a, s, h->collide_active));
     if (h->timing) CUDA_TRY(h, record_event(h->ev[2], s));
     return NPP_OK;
+}
+
+cudaError_t launch_winner_epilogue(const npp_handle* h, const RolloutArgs& a, const EpilogueArgs& e, bool fused,
+                                   cudaStream_t s)
+{
+    if (!fused) return launch_epilogue(e, s);
+    switch (h->cfg.width) {
+    case 16: return launch_reroll_w16(a, e, s);
+    case 32: return launch_reroll_w32(a, e, s);
+    default: return launch_reroll_w64(a, e, s);
+    }
 }
 
 static SamplerKey make_key(uint64_t seed, uint32_t t_index, uint32_t stream_id)
@@ -307,6 +321,7 @@ npp_status npp_create(npp_handle** out, const npp_config* cfg, int32_t device)
     npp_handle* h = new npp_handle();
     h->cfg = *cfg;
     h->collide_variant = -1;
+    h->fuse = false;
     h->collide_active = -1;
     h->occ_M = -1;
     cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, device);
@@ -407,7 +422,9 @@ static npp_status plan_step_impl(npp_handle* h, const npp_state* state, const np
     a.jfree = h->d_jfree;
     a.best_key = h->d_key;
     CUDA_TRY(h, cudaMemsetAsync(h->d_key, 0xff, sizeof(unsigned long long), s));
-    if ((st = run_rollout(h, a, s)) != NPP_OK) return st;
+    bool fused = false;
+    const bool records = out->sample_traj != nullptr || out->sample_ctrl != nullptr;
+    if ((st = run_rollout(h, a, s, !records, &fused)) != NPP_OK) return st;
 
     EpilogueArgs e;
     memset(&e, 0, sizeof e);
@@ -423,8 +440,7 @@ static npp_status plan_step_impl(npp_handle* h, const npp_state* state, const np
     e.params = out->params;
     e.controls = out->controls;
     e.trajectory = out->trajectory;
-    epilogue_kernel<<<1, 256, 0, s>>>(e);
-    CUDA_TRY(h, cudaGetLastError());
+    CUDA_TRY(h, launch_winner_epilogue(h, a, e, fused, s));
     if (h->timing) CUDA_TRY(h, record_event(h->ev[3], s));
     return NPP_OK;
 }
@@ -517,7 +533,8 @@ npp_status npp_rollout_params(npp_handle* h, const npp_state* state, const npp_g
     a.ctrl = sample_ctrl_dev ? reinterpret_cast<float2*>(sample_ctrl_dev) : h->d_ctrl;
     a.jfree = h->d_jfree;
     a.best_key = nullptr;
-    if ((st = run_rollout(h, a, s)) != NPP_OK) return st;
+    bool fused = false;
+    if ((st = run_rollout(h, a, s, !sample_traj_dev && !sample_ctrl_dev, &fused)) != NPP_OK) return st;
     if (h->timing) CUDA_TRY(h, record_event(h->ev[3], s));
     return NPP_OK;
 }
@@ -530,6 +547,11 @@ npp_status npp_set_option(npp_handle* h, const char* name, int32_t value)
             return fail(h, NPP_INVALID_ARG, "collide_variant is -1..%d", COLLIDE_BINNED);
         h->collide_variant = value;
         h->occ_M = -1;
+        return NPP_OK;
+    }
+    if (std::strcmp(name, "fuse") == 0) {
+        if (value != 0 && value != 1) return fail(h, NPP_INVALID_ARG, "fuse is 0 or 1");
+        h->fuse = value != 0;
         return NPP_OK;
     }
     if (std::strcmp(name, "traj_variant") == 0) {

@@ -133,6 +133,7 @@ __global__ void __launch_bounds__(NW * 32) batch_traj_kernel(const BatchArgs b, 
         job.theta = nullptr;
         job.warm = nullptr;
         job.prop = Proposal{ nullptr, nullptr, 0 };
+        job.bins = nullptr;
         job.N = s.N;
         job.T = s.T;
         job.traj = nullptr;
@@ -260,6 +261,7 @@ __device__ void batch_reroll(const BatchArgs& b, const SceneDev& s, int idx, flo
     job.theta = nullptr;
     job.warm = nullptr;
     job.prop = Proposal{ nullptr, nullptr, 0 };
+    job.bins = nullptr;
     job.N = s.N;
     job.T = s.T;
     job.traj = b.trajectory ? reinterpret_cast<float4*>(b.trajectory) + s.traj_off : nullptr;

@@ -1,4 +1,6 @@
-// npp_binned.cu -- collision checks through per-timestep spatial binning.
+// npp_binned.cu -- collision checks through per-timestep spatial binning
+// (the grid build, and the check over stored trajectories; the check fused
+// into the trajectory kernel lives in npp_rollout.cuh).
 //
 // For every horizon step h the obstacle points at time h Ts (EV frame,
 // p + tau v with the brute-force kernels' arithmetic) are counting-sorted into
@@ -21,58 +23,38 @@ using namespace npp;
 
 namespace {
 
-constexpr int BIN_DIM = 128;
-constexpr int NCELL = BIN_DIM * BIN_DIM;
 constexpr int BIN_THREADS = 1024;
-// ints per step of the cell-start table: NCELL + 1 entries padded to a
-// multiple of 16 bytes, so that the float2 point arrays after the tables
-// stay 8-byte aligned for every T
-constexpr int CS_STRIDE = NCELL + 4;
-
-struct BinGrid {
-    float x0, y0;          // lower-left corner of the grid (EV frame)
-    float inv_cell, cell;
-    float reach;           // disk radius + margin used by the query
-};
-
-__device__ __forceinline__ int cell_ix(float x, const BinGrid& g)
-{
-    const float f = floorf((x - g.x0) * g.inv_cell);
-    return (int)fminf(fmaxf(f, 0.0f), (float)(BIN_DIM - 1));
-}
 
 // one block per horizon step: cell counts (shared), exclusive scan, scatter
-__global__ void __launch_bounds__(BIN_THREADS) bin_build_kernel(const RolloutArgs a, BinGrid g,
-                                                                int* __restrict__ cell_start,
+__global__ void __launch_bounds__(BIN_THREADS) bin_build_kernel(const RolloutArgs a, BinView g, int* __restrict__ cell_start,
                                                                 float2* __restrict__ binned)
 {
-    extern __shared__ int cnt[];             // [NCELL]
+    extern __shared__ int cnt[];             // [BIN_NCELL]
     const int h = blockIdx.x;
     const int M = a.M;
     const float tau = (float)h * a.c.Ts;
     const StepIn si = step_in(a);
     float s0, c0;
     sincosf(si.phi0, &s0, &c0);
-    for (int i = threadIdx.x; i < NCELL; i += blockDim.x) cnt[i] = 0;
+    for (int i = threadIdx.x; i < BIN_NCELL; i += blockDim.x) cnt[i] = 0;
     __syncthreads();
     for (int j = threadIdx.x; j < M; j += blockDim.x) {
         float ex, ey, evx, evy;
         ev_point(a.obs[j], si.x0, si.y0, s0, c0, ex, ey, evx, evy);
         const float px = fmaf(tau, evx, ex), py = fmaf(tau, evy, ey);
-        atomicAdd(&cnt[cell_ix(py, g) * BIN_DIM + cell_ix(px, g)], 1);
+        atomicAdd(&cnt[bin_cell(py, g) * BIN_DIM + bin_cell(px, g)], 1);
     }
     __syncthreads();
-    // exclusive scan of NCELL counts: each thread scans a contiguous run,
-    // then the run totals are scanned by warp 0
+    // exclusive scan of the counts: each thread scans a contiguous run,
+    // then warp 0 scans the run totals
     __shared__ int run_tot[BIN_THREADS];
-    constexpr int RUN = NCELL / BIN_THREADS;
+    constexpr int RUN = BIN_NCELL / BIN_THREADS;
     const int base = threadIdx.x * RUN;
     int acc = 0;
     for (int k = 0; k < RUN; ++k) { const int v = cnt[base + k]; cnt[base + k] = acc; acc += v; }
     run_tot[threadIdx.x] = acc;
     __syncthreads();
     if (threadIdx.x < 32) {
-        // warp 0 scans the BIN_THREADS run totals (32 per lane)
         constexpr int PER = BIN_THREADS / 32;
         int local = 0;
         for (int k = 0; k < PER; ++k) local += run_tot[threadIdx.x * PER + k];
@@ -91,9 +73,9 @@ __global__ void __launch_bounds__(BIN_THREADS) bin_build_kernel(const RolloutArg
     __syncthreads();
     for (int k = 0; k < RUN; ++k) cnt[base + k] += run_tot[threadIdx.x];
     __syncthreads();
-    int* cs = cell_start + (size_t)h * CS_STRIDE;
-    for (int i = threadIdx.x; i < NCELL; i += blockDim.x) cs[i] = cnt[i];
-    if (threadIdx.x == 0) cs[NCELL] = M;
+    int* cs = cell_start + (size_t)h * BIN_CS_STRIDE;
+    for (int i = threadIdx.x; i < BIN_NCELL; i += blockDim.x) cs[i] = cnt[i];
+    if (threadIdx.x == 0) cs[BIN_NCELL] = M;
     __syncthreads();
     // scatter (order within a cell is arbitrary; the test is an OR)
     float2* out = binned + (size_t)h * M;
@@ -101,23 +83,23 @@ __global__ void __launch_bounds__(BIN_THREADS) bin_build_kernel(const RolloutArg
         float ex, ey, evx, evy;
         ev_point(a.obs[j], si.x0, si.y0, s0, c0, ex, ey, evx, evy);
         const float px = fmaf(tau, evx, ex), py = fmaf(tau, evy, ey);
-        const int pos = atomicAdd(&cnt[cell_ix(py, g) * BIN_DIM + cell_ix(px, g)], 1);
+        const int pos = atomicAdd(&cnt[bin_cell(py, g) * BIN_DIM + bin_cell(px, g)], 1);
         out[pos] = make_float2(px, py);
     }
 }
 
-// one warp per sample, h in order: the candidates of a step are the points
-// of at most two cell rows, each row's cells contiguous in the sorted array;
-// the lanes stride through them (coalesced loads) and a ballot ends the
-// sample at its first colliding step
+// one warp per sample over the stored trajectories and inequality rows, h
+// in order: the candidates of a step are the points of at most two cell
+// rows, each row's cells contiguous in the sorted array; the lanes stride
+// through them (coalesced loads) and a ballot ends the sample at its first
+// colliding step
 constexpr int BINNED_WARPS = 8;
 
-__global__ void __launch_bounds__(BINNED_WARPS * 32) collide_binned_kernel(const RolloutArgs a, BinGrid g,
-                                                                          const int* __restrict__ cell_start,
-                                                                          const float2* __restrict__ binned)
+__global__ void __launch_bounds__(BINNED_WARPS * 32) collide_binned_kernel(const RolloutArgs a)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     __shared__ unsigned long long red[BINNED_WARPS];
+    const BinView& g = a.bins;
     const int T = a.T, N = a.N, M = a.M;
     const int n = blockIdx.x * BINNED_WARPS + warp;
     unsigned long long key = ~0ull;
@@ -130,11 +112,10 @@ __global__ void __launch_bounds__(BINNED_WARPS * 32) collide_binned_kernel(const
             // the rectangle lies in the disk of radius reach around the
             // reference point (reach covers the centre offset)
             const float4 z = a.traj[idx];
-            const int ix0 = cell_ix(z.x - g.reach, g), ix1 = cell_ix(z.x + g.reach, g);
-            const int iy0 = cell_ix(z.y - g.reach, g), iy1 = cell_ix(z.y + g.reach, g);
-            const int* cs = cell_start + (size_t)h * CS_STRIDE;
-            const float2* pts = binned + (size_t)h * M;
-            // rows iy0 and iy1 (iy1 - iy0 <= 1 since the cell exceeds the disk diameter)
+            const int ix0 = bin_cell(z.x - g.reach, g), ix1 = bin_cell(z.x + g.reach, g);
+            const int iy0 = bin_cell(z.y - g.reach, g), iy1 = bin_cell(z.y + g.reach, g);
+            const int* cs = g.cell_start + (size_t)h * BIN_CS_STRIDE;
+            const float2* pts = g.pts + (size_t)h * M;
             const int r0b = cs[iy0 * BIN_DIM + ix0], r0e = cs[iy0 * BIN_DIM + ix1 + 1];
             int r1b = r0e, r1e = r0e;
             if (iy1 != iy0) { r1b = cs[iy1 * BIN_DIM + ix0]; r1e = cs[iy1 * BIN_DIM + ix1 + 1]; }
@@ -181,31 +162,37 @@ namespace npp {
 // bytes of the per-step grids: (T+1) cell-start tables and (T+1) x M points
 size_t binned_workspace_bytes(int max_T, int max_M)
 {
-    return (size_t)(max_T + 1) * CS_STRIDE * sizeof(int) + (size_t)(max_T + 1) * max_M * sizeof(float2);
+    return (size_t)(max_T + 1) * BIN_CS_STRIDE * sizeof(int) + (size_t)(max_T + 1) * max_M * sizeof(float2);
 }
 
-cudaError_t launch_collide_binned(const RolloutArgs& a, float half_len, float half_wid, float c_off,
-                                  void* workspace, cudaStream_t s)
+// A cell wider than the diameter of the query disk (circumradius of the
+// rectangle plus |c_off|, plus a margin against rounding of positions of
+// O(100) m), a grid of BIN_DIM^2 cells centred on the vehicle.
+cudaError_t build_bins(RolloutArgs& a, float half_len, float half_wid, float c_off, void* workspace, cudaStream_t s)
 {
-    BinGrid g;
-    const double R = std::sqrt((double)half_len * half_len + (double)half_wid * half_wid)
-                   + std::fabs((double)c_off);
+    const double R = std::sqrt((double)half_len * half_len + (double)half_wid * half_wid) + std::fabs((double)c_off);
     const double cell = 2.0 * R + 0.25;
-    g.cell = (float)cell;
+    BinView g;
     g.inv_cell = (float)(1.0 / cell);
     g.x0 = (float)(-0.5 * BIN_DIM * cell);
-    g.y0 = g.x0;
-    g.reach = (float)(R + 0.05);           // margin against rounding (positions are O(100) m)
+    g.reach = (float)(R + 0.05);
     int* cell_start = static_cast<int*>(workspace);
-    float2* binned = reinterpret_cast<float2*>(cell_start + (size_t)(a.T + 1) * CS_STRIDE);
-    const int smem = NCELL * (int)sizeof(int);
+    float2* binned = reinterpret_cast<float2*>(cell_start + (size_t)(a.T + 1) * BIN_CS_STRIDE);
+    g.cell_start = cell_start;
+    g.pts = binned;
+    g.M = a.M;
+    const int smem = BIN_NCELL * (int)sizeof(int);
     cudaError_t e = ensure_smem(bin_build_kernel, smem);
     if (e != cudaSuccess) return e;
     bin_build_kernel<<<a.T + 1, BIN_THREADS, smem, s>>>(a, g, cell_start, binned);
     e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    collide_binned_kernel<<<(a.N + BINNED_WARPS - 1) / BINNED_WARPS, BINNED_WARPS * 32, 0, s>>>(a, g, cell_start,
-                                                                                               binned);
+    if (e == cudaSuccess) a.bins = g;
+    return e;
+}
+
+cudaError_t launch_collide_binned(const RolloutArgs& a, cudaStream_t s)
+{
+    collide_binned_kernel<<<(a.N + BINNED_WARPS - 1) / BINNED_WARPS, BINNED_WARPS * 32, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -172,6 +172,48 @@ __device__ __forceinline__ void ev_point(const float4& o, float x0, float y0, fl
     vy = fmaf(-s0, o.z, __fmul_rn(c0, o.w));
 }
 
+// theta[4q .. 4q+3] where the quad may run past n_theta (the proposal
+// arrays hold exactly n_theta values)
+__device__ __forceinline__ float4 sample_quad_mixed_tail(const SamplerKey& key, const Proposal& p, uint32_t q,
+                                                         uint32_t n, int n_theta)
+{
+    if (4 * (int)q + 3 < n_theta || !proposal_sample(p, n)) return sample_quad_mixed(key, p, q, n);
+    SamplerKey k1 = key;
+    k1.stream_id = 1u;
+    const float4 e = sample_quad(k1, q, n);
+    const float ev[4] = { e.x, e.y, e.z, e.w };
+    float r[4] = { 0.f, 0.f, 0.f, 0.f };
+    for (int j = 0; j < 4 && 4 * (int)q + j < n_theta; ++j) {
+        const int i = 4 * (int)q + j;
+        r[j] = fmaf(p.sigma[i], ev[j], p.mu[i]);
+    }
+    return make_float4(r[0], r[1], r[2], r[3]);
+}
+
+// ------------------------------------------------------------------ spatial bins
+// Per-step grids of the binned collision check: for step h, cell_start[h]
+// [BIN_DIM^2 + 1 entries, stride BIN_CS_STRIDE] indexes the points of
+// step h sorted by cell, pts + h M.  A query disk of radius `reach` around a
+// state spans at most two cells per axis.
+constexpr int BIN_DIM = 128;
+constexpr int BIN_NCELL = BIN_DIM * BIN_DIM;
+constexpr int BIN_CS_STRIDE = BIN_NCELL + 4;    // 16-byte multiple: the float2 points that follow stay aligned
+
+struct BinView {
+    float x0;              // lower-left corner of the grid (EV frame, both axes)
+    float inv_cell;
+    float reach;           // query radius
+    const int* cell_start; // null: no grids
+    const float2* pts;
+    int M;
+};
+
+__device__ __forceinline__ int bin_cell(float x, const BinView& g)
+{
+    const float f = floorf((x - g.x0) * g.inv_cell);
+    return (int)fminf(fmaxf(f, 0.0f), (float)(BIN_DIM - 1));
+}
+
 // ------------------------------------------------------------------ rollout math
 // FP32 functions of the rollout step built on the SFU's approximate base-2
 // exponential, reciprocal, sine and cosine (PTX ex2/rcp/sin/cos .approx).
@@ -281,6 +323,7 @@ struct RolloutArgs {
     const LoopDev* dyn;                // when set, per-step scalars come from here
     float4* pXY;                       // EV-frame point pairs in global memory (when the
     float4* pV;                        // points exceed shared memory), [ceil(M/2)]
+    BinView bins;                      // per-step grids (binned and fused collision checks)
 };
 
 __device__ __forceinline__ StepIn step_in(const RolloutArgs& a)
@@ -321,6 +364,15 @@ struct EpilogueArgs {
 cudaError_t launch_traj_w16(const RolloutArgs& a, cudaStream_t s, int variant);
 cudaError_t launch_traj_w32(const RolloutArgs& a, cudaStream_t s, int variant);
 cudaError_t launch_traj_w64(const RolloutArgs& a, cudaStream_t s, int variant);
+// trajectories with the binned collision check fused in (a.bins set): each
+// sample stops at its first collision; writes costs, first hits and the key
+cudaError_t launch_fused_w16(const RolloutArgs& a, cudaStream_t s, int variant);
+cudaError_t launch_fused_w32(const RolloutArgs& a, cudaStream_t s, int variant);
+cudaError_t launch_fused_w64(const RolloutArgs& a, cudaStream_t s, int variant);
+// winner epilogue that re-rolls the winner (no per-sample records needed)
+cudaError_t launch_reroll_w16(const RolloutArgs& a, const EpilogueArgs& e, cudaStream_t s);
+cudaError_t launch_reroll_w32(const RolloutArgs& a, const EpilogueArgs& e, cudaStream_t s);
+cudaError_t launch_reroll_w64(const RolloutArgs& a, const EpilogueArgs& e, cudaStream_t s);
 cudaError_t launch_collide_resident(const RolloutArgs& a, cudaStream_t s, int variant);
 cudaError_t launch_collide_global(const RolloutArgs& a, cudaStream_t s);
 int collide_global_blocks_per_sm();
@@ -330,8 +382,9 @@ int collide_max_points(int smem_limit);
 // the grids in `workspace` (binned_workspace_bytes) and checks every sample
 // against the points of the cells its bounding disk overlaps
 size_t binned_workspace_bytes(int max_T, int max_M);
-cudaError_t launch_collide_binned(const RolloutArgs& a, float half_len, float half_wid, float c_off,
-                                  void* workspace, cudaStream_t s);
+cudaError_t build_bins(RolloutArgs& a, float half_len, float half_wid, float c_off, void* workspace,
+                       cudaStream_t s);          // fills a.bins
+cudaError_t launch_collide_binned(const RolloutArgs& a, cudaStream_t s);
 cudaError_t launch_epilogue(const EpilogueArgs& e, cudaStream_t s);
 void set_global_error(const char* msg);
 

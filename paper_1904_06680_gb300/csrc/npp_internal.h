@@ -33,7 +33,8 @@ struct npp_handle {
     int collide_variant;                 // -1 automatic, else a fixed collision-kernel variant
                                          // (0..4 brute force, 5 spatially binned)
     int collide_active;                  // variant used for the current launch
-    int traj_variant;                    // 0: 2 hidden units per lane, 1: 4
+    int traj_variant;                    // trajectory launch shape (0..3)
+    bool fuse;                           // binned check fused into the trajectory kernel
     int occ_M, occ_blocks;               // cached occupancy for the last M
     float4* d_pXY;                       // EV-frame point pairs when M exceeds shared memory
     float4* d_pV;
@@ -69,8 +70,14 @@ inline cudaError_t record_event(cudaEvent_t ev, cudaStream_t s)
 npp_status fail(npp_handle* h, npp_status s, const char* fmt, ...);
 
 // trajectory + collision kernels of one plan step (fills workspace pointers,
-// the persistent grid and the work-counter reset)
-npp_status run_rollout(npp_handle* h, npp::RolloutArgs& a, cudaStream_t s);
+// the persistent grid and the work-counter reset); with the binned check and
+// allow_fused the two are one kernel that keeps no per-sample records
+// (*fused reports it: the winner epilogue must then re-roll the winner)
+npp_status run_rollout(npp_handle* h, npp::RolloutArgs& a, cudaStream_t s, bool allow_fused, bool* fused);
+
+// the winner epilogue matching run_rollout's path
+cudaError_t launch_winner_epilogue(const npp_handle* h, const npp::RolloutArgs& a, const npp::EpilogueArgs& e,
+                                   bool fused, cudaStream_t s);
 
 #define CUDA_TRY(h, call)                                                                  \
     do {                                                                                   \

@@ -150,7 +150,8 @@ npp_status enqueue_step(npp_loop* L, uint64_t seed)
     a.costs = L->d_costs;
     a.first_hit = L->d_fh;
     CUDA_TRY(h, cudaMemsetAsync(h->d_key, 0xff, sizeof(unsigned long long), s));
-    npp_status st = run_rollout(h, a, s);
+    bool fused = false;
+    npp_status st = run_rollout(h, a, s, true, &fused);
     if (st != NPP_OK) return st;
     EpilogueArgs e;
     memset(&e, 0, sizeof e);
@@ -165,7 +166,7 @@ npp_status enqueue_step(npp_loop* L, uint64_t seed)
     e.controls = L->d_controls;
     e.trajectory = L->d_trajectory;
     e.dyn = L->d_dyn;
-    CUDA_TRY(h, launch_epilogue(e, s));
+    CUDA_TRY(h, launch_winner_epilogue(h, a, e, fused, s));
     PlantCfg pc;
     pc.lf = h->cfg.lf; pc.lr = h->cfg.lr; pc.delta_max = h->cfg.delta_max;
     pc.u_min = h->cfg.u_min; pc.u_max = h->cfg.u_max; pc.Ts = h->cfg.Ts;

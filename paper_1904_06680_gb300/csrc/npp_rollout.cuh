@@ -29,6 +29,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "../../include/npp.h"
 #include "npp_device.cuh"
 
 namespace npp {
@@ -120,12 +121,74 @@ __device__ __forceinline__ float wrap_pi(float a)
 // (an exact scaling).  |v| < 2 holds exactly when bit 30 of v's IEEE pattern
 // is clear, so "both inside" is bit 30 of (xi | eta) clear: one 3-input logic
 // op per point-sample pair accumulates "some point inside".
+// (Rounding fixed by explicit fmas and round-to-nearest products, so that the
+// rows stored by the trajectory kernel and the rows the fused check computes
+// are the same bits.)
+__device__ __forceinline__ void coef_rows(const DevCfg& c, float x, float y, float sp, float cp, float4& A,
+                                          float2& B)
+{
+    const float sl = 2.0f * c.ihl, sw = 2.0f * c.ihw;
+    const float along = fmaf(cp, x, fmaf(sp, y, c.c_off));
+    const float across = fmaf(-sp, x, __fmul_rn(cp, y));
+    A = make_float4(__fmul_rn(cp, sl), __fmul_rn(sp, sl), -__fmul_rn(along, sl), -__fmul_rn(sp, sw));
+    B = make_float2(__fmul_rn(cp, sw), -__fmul_rn(across, sw));
+}
+
 __device__ __forceinline__ void write_coef(float4* coefA, float2* coefB, const DevCfg& c,
                                            long long idx, float x, float y, float sp, float cp)
 {
-    const float sl = 2.0f * c.ihl, sw = 2.0f * c.ihw;
-    coefA[idx] = make_float4(cp * sl, sp * sl, -((cp * x + sp * y + c.c_off) * sl), -sp * sw);
-    coefB[idx] = make_float2(cp * sw, -((-sp * x + cp * y) * sw));
+    float4 A;
+    float2 B;
+    coef_rows(c, x, y, sp, cp, A, B);
+    coefA[idx] = A;
+    coefB[idx] = B;
+}
+
+// Binned check of one state for the G lanes of each group of a warp (every
+// lane of the warp calls it; dead groups pass alive = false): the candidates
+// of the at most two cell rows the state's disk overlaps, strided over the
+// group's lanes, the per-point test of the brute-force kernels.  Returns,
+// uniformly over the group, whether some point is inside.
+template <int G>
+__device__ __forceinline__ bool group_collides(const BinView& bv, int h, float x, float y, const float4& A,
+                                               const float2& B, bool alive, int gl)
+{
+    int r0b = 0, r0e = 0, r1b = 0, r1e = 0;
+    if (alive) {
+        const int ix0 = bin_cell(x - bv.reach, bv), ix1 = bin_cell(x + bv.reach, bv);
+        const int iy0 = bin_cell(y - bv.reach, bv), iy1 = bin_cell(y + bv.reach, bv);
+        const int* cs = bv.cell_start + (size_t)h * BIN_CS_STRIDE;
+        r0b = cs[iy0 * BIN_DIM + ix0];
+        r0e = cs[iy0 * BIN_DIM + ix1 + 1];
+        r1b = r0e;
+        r1e = r0e;
+        if (iy1 != iy0) {
+            r1b = cs[iy1 * BIN_DIM + ix0];
+            r1e = cs[iy1 * BIN_DIM + ix1 + 1];
+        }
+    }
+    const int n0 = r0e - r0b, total = n0 + (r1e - r1b);
+    const int iters = (total + G - 1) / G;
+    const int maxit = __reduce_max_sync(FULL, iters);
+    const float2* pts = bv.pts + (size_t)h * bv.M;
+    const unsigned gmask = G == 32 ? FULL : (((1u << G) - 1u) << ((threadIdx.x & 31) / G * G));
+    bool hit = false;
+    for (int it = 0; it < maxit; ++it) {
+        const int k = it * G + gl;
+        bool inside = false;
+        if (k < total) {
+            const float2 p = pts[k < n0 ? r0b + k : r1b + (k - n0)];
+            const float xi = fmaf(A.x, p.x, fmaf(A.y, p.y, A.z));
+            const float et = fmaf(A.w, p.x, fmaf(B.x, p.y, B.y));
+            inside = !(((__float_as_uint(xi) | __float_as_uint(et)) >> 30) & 1u);
+        }
+        // every lane of the warp takes part in both votes (no short circuit)
+        const unsigned bal = __ballot_sync(FULL, inside);
+        hit = hit || (bal & gmask) != 0u;
+        const bool done = hit || (it + 1) * G >= total;
+        if (__all_sync(FULL, done)) break;
+    }
+    return hit;
 }
 
 // ------------------------------------------------------------------ traj
@@ -153,13 +216,24 @@ struct TrajJob {
     float2* coefB;
     long long coef_base;
     float* jfree;
+    const BinView* bins;          // fused check (traj_sample<.., true>)
+};
+
+// Result of a fused rollout, uniform over the sample's group: the first
+// colliding step (-1 if none) and the cost if collision-free.
+struct FusedOut {
+    int first_hit;
+    float cost;
 };
 
 // The trajectory of sample n (valid: n < N) computed by the G lanes of a
-// group (lane gl); hrow is the group's W-float shared exchange row.
-template <int W, int G>
-__device__ __forceinline__ void traj_sample(const DevCfg& c, const TrajJob& job, int n, bool valid,
-                                            int gl, float* hrow)
+// group (lane gl); hrow is the group's W-float shared exchange row.  FUSED:
+// every state h is checked against the binned points at the top of its step
+// (before the controls that leave it) and the loop ends once every group of
+// the warp has collided; nothing is stored.
+template <int W, int G, bool FUSED = false>
+__device__ __forceinline__ FusedOut traj_sample(const DevCfg& c, const TrajJob& job, int n, bool valid,
+                                                int gl, float* hrow)
 {
     using S = Shape<W, G>;
     constexpr int U = S::U;
@@ -188,10 +262,25 @@ __device__ __forceinline__ void traj_sample(const DevCfg& c, const TrajJob& job,
     const bool writer = valid && gl == 0;
     const long long rec = (long long)n - job.rec_shift;
 
+    bool alive = valid;
+    int fh = -1;
+    bool all_dead = false;
     for (int h = 0; h < T; ++h) {
         float sp, cp;
         sincos_r(ph, sp, cp);
-        if (writer) {
+        if constexpr (FUSED) {
+            float4 A;
+            float2 B;
+            coef_rows(c, x, y, sp, cp, A, B);
+            if (group_collides<G>(*job.bins, h, x, y, A, B, alive, gl) && alive) {
+                alive = false;
+                fh = h;
+            }
+            if (!__any_sync(FULL, alive)) {
+                all_dead = true;
+                break;
+            }
+        } else if (writer) {
             if (job.traj) job.traj[h * job.rec_stride + rec] = make_float4(x, y, ph, v);
             if (job.coefA) write_coef(job.coefA, job.coefB, c, job.coef_base + (long long)h * N + n, x, y, sp, cp);
         }
@@ -273,7 +362,28 @@ __device__ __forceinline__ void traj_sample(const DevCfg& c, const TrajJob& job,
         ap0 = a0;
         ap1 = a1;
     }
-    if (writer) {
+    FusedOut out;
+    out.first_hit = fh;
+    out.cost = __int_as_float(0x7f800000);
+    if constexpr (FUSED) {
+        if (!all_dead) {
+            float sp, cp;
+            sincos_r(ph, sp, cp);
+            float4 A;
+            float2 B;
+            coef_rows(c, x, y, sp, cp, A, B);
+            if (group_collides<G>(*job.bins, T, x, y, A, B, alive, gl) && alive) {
+                alive = false;
+                fh = T;
+            }
+        }
+        out.first_hit = fh;
+        if (alive) {
+            const float dx = x - gxi, dy = y - geta;
+            out.cost = c.w_pos * sqrtf(dx * dx + dy * dy) + c.w_phi * fabsf(wrap_pi(ph - gph))
+                     + c.w_v * fabsf(v - gv) + c.w_effort * E * invT;
+        }
+    } else if (writer) {
         float sp, cp;
         sincos_r(ph, sp, cp);
         if (job.traj) job.traj[T * job.rec_stride + rec] = make_float4(x, y, ph, v);
@@ -284,6 +394,7 @@ __device__ __forceinline__ void traj_sample(const DevCfg& c, const TrajJob& job,
                          + c.w_v * fabsf(v - gv) + c.w_effort * E * invT;
         }
     }
+    return out;
 }
 
 template <int W, int G, int NW, int MINB = 1>
@@ -311,7 +422,143 @@ __global__ void __launch_bounds__(NW * 32, MINB) traj_kernel(const RolloutArgs a
     job.coefB = a.coefB;
     job.coef_base = 0;
     job.jfree = a.jfree;
+    job.bins = nullptr;
     traj_sample<W, G>(a.c, job, n, n < a.N, gl, hx_all + b * W);
+}
+
+// Trajectories with the binned check fused in: per sample its first
+// collision and cost, folded into the (class, cost, index) minimum.
+template <int W, int G, int NW, int MINB = 1>
+__global__ void __launch_bounds__(NW * 32, MINB) fused_kernel(const RolloutArgs a)
+{
+    constexpr int B = TrajKernel<W, G, NW>::B;
+    __shared__ __align__(16) float hx_all[B * W];
+    __shared__ unsigned long long red[NW];
+    const int tid = threadIdx.x;
+    const int b = tid / G, gl = tid % G;
+    const int n = blockIdx.x * B + b;
+    TrajJob job;
+    job.si = step_in(a);
+    job.key = a.key;
+    job.key.t_index = job.si.t_index;
+    job.theta = a.theta;
+    job.warm = a.warm;
+    job.prop = a.prop;
+    job.N = a.N;
+    job.T = a.T;
+    job.traj = nullptr;
+    job.ctrl = nullptr;
+    job.rec_stride = 0;
+    job.rec_shift = 0;
+    job.coefA = nullptr;
+    job.coefB = nullptr;
+    job.coef_base = 0;
+    job.jfree = nullptr;
+    job.bins = &a.bins;
+    const bool valid = n < a.N;
+    const FusedOut r = traj_sample<W, G, true>(a.c, job, n, valid, gl, hx_all + b * W);
+    unsigned long long key = ~0ull;
+    if (valid && gl == 0) {
+        if (r.first_hit < 0)
+            key = ((unsigned long long)__float_as_uint(r.cost) << 32) | (unsigned)n;
+        else
+            key = (1ull << 63) | ((unsigned long long)(a.T - r.first_hit) << 32) | (unsigned)n;
+        if (a.costs) a.costs[n] = r.first_hit < 0 ? r.cost : __int_as_float(0x7f800000);
+        if (a.first_hit) a.first_hit[n] = r.first_hit;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(FULL, key, off);
+        key = o < key ? o : key;
+    }
+    if ((tid & 31) == 0) red[tid >> 5] = key;
+    __syncthreads();
+    if (tid == 0 && a.best_key) {
+        unsigned long long k = red[0];
+        for (int w = 1; w < NW; ++w) k = red[w] < k ? red[w] : k;
+        atomicMin(a.best_key, k);
+    }
+}
+
+// Winner epilogue for plan steps that keep no per-sample records: one warp
+// decodes the key, writes the summary, re-rolls the winner (every group of
+// the warp computes the same sample; identical writes) into the caller's
+// trajectory and control rows in the EV frame, then moves the rows to the
+// world frame (rows after an infeasible winner's first collision repeat the
+// colliding state, its controls there are zero) and regenerates its
+// parameters (warm start, proposal or isotropic sample).
+template <int W, int G>
+__global__ void __launch_bounds__(32) reroll_epilogue_kernel(const RolloutArgs a, const EpilogueArgs e)
+{
+    __shared__ __align__(16) float hrows[32 / G * W];
+    const int lane = threadIdx.x;
+    const StepIn si = step_in(a);
+    SamplerKey skey = a.key;
+    skey.t_index = si.t_index;
+    const unsigned long long key = *e.best_key;
+    const int idx = (int)(key & 0xffffffffull);
+    const bool dead = (key >> 63) != 0;
+    const unsigned hi = (unsigned)((key >> 32) & 0x7fffffffu);
+    const int fh = dead ? e.T - (int)hi : -1;
+    const int last = dead ? fh : e.T;
+    if (lane == 0) {
+        npp_best* o = reinterpret_cast<npp_best*>(e.best);
+        o->best_idx = idx;
+        o->status = dead ? NPP_INFEASIBLE : NPP_OK;
+        o->best_cost = dead ? __int_as_float(0x7f800000) : __uint_as_float(hi);
+        o->first_hit = fh;
+        o->reserved[0] = o->reserved[1] = o->reserved[2] = o->reserved[3] = 0;
+    }
+    TrajJob job;
+    job.si = si;
+    job.key = skey;
+    job.theta = a.theta;
+    job.warm = a.warm;
+    job.prop = a.prop;
+    job.N = a.N;
+    job.T = a.T;
+    job.traj = reinterpret_cast<float4*>(e.trajectory);
+    job.ctrl = reinterpret_cast<float2*>(e.controls);
+    job.rec_stride = 1;
+    job.rec_shift = idx;
+    job.coefA = nullptr;
+    job.coefB = nullptr;
+    job.coef_base = 0;
+    job.jfree = nullptr;
+    job.bins = nullptr;
+    if (e.trajectory || e.controls) traj_sample<W, G>(a.c, job, idx, true, lane % G, hrows + (lane / G) * W);
+    __syncwarp();
+    float s0, c0;
+    sincosf(si.phi0, &s0, &c0);
+    if (e.trajectory) {
+        float4* tr = reinterpret_cast<float4*>(e.trajectory);
+        const float4 zl = tr[last];
+        __syncwarp();                          // every lane has zl before rows change
+        for (int h = lane; h <= e.T; h += 32) {
+            const float4 z = h <= last ? tr[h] : zl;
+            float4 w;
+            w.x = si.x0 + c0 * z.x - s0 * z.y;
+            w.y = si.y0 + s0 * z.x + c0 * z.y;
+            w.z = si.phi0 + z.z;
+            w.w = z.w;
+            tr[h] = w;
+        }
+    }
+    if (e.controls)
+        for (int h = lane; h < e.T; h += 32)
+            if (h >= last) reinterpret_cast<float2*>(e.controls)[h] = make_float2(0.f, 0.f);
+    if (e.params) {
+        if (a.warm && idx == 0 && si.warm_ok) {
+            if (e.params != a.warm)
+                for (int i = lane; i < e.n_theta; i += 32) e.params[i] = a.warm[i];
+        } else {
+            for (int q = lane; 4 * q < e.n_theta; q += 32) {
+                const float4 v = sample_quad_mixed_tail(skey, a.prop, (uint32_t)q, (uint32_t)idx, e.n_theta);
+                const float vv[4] = { v.x, v.y, v.z, v.w };
+                for (int j = 0; j < 4 && 4 * q + j < e.n_theta; ++j) e.params[4 * q + j] = vv[j];
+            }
+        }
+    }
 }
 
 // ------------------------------------------------------------------ collide
@@ -845,6 +1092,22 @@ cudaError_t launch_traj(const RolloutArgs& a, cudaStream_t stream)
     using K = TrajKernel<W, G, NW>;
     const int grid = (a.N + K::B - 1) / K::B;
     traj_kernel<W, G, NW, MINB><<<grid, K::THREADS, 0, stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <int W, int G, int NW, int MINB = 1>
+cudaError_t launch_fused(const RolloutArgs& a, cudaStream_t stream)
+{
+    using K = TrajKernel<W, G, NW>;
+    const int grid = (a.N + K::B - 1) / K::B;
+    fused_kernel<W, G, NW, MINB><<<grid, K::THREADS, 0, stream>>>(a);
+    return cudaGetLastError();
+}
+
+template <int W, int G>
+cudaError_t launch_reroll(const RolloutArgs& a, const EpilogueArgs& e, cudaStream_t stream)
+{
+    reroll_epilogue_kernel<W, G><<<1, 32, 0, stream>>>(a, e);
     return cudaGetLastError();
 }
 

@@ -16,4 +16,19 @@ cudaError_t launch_traj_w32(const RolloutArgs& a, cudaStream_t s, int variant)
     }
 }
 
+cudaError_t launch_fused_w32(const RolloutArgs& a, cudaStream_t s, int variant)
+{
+    switch (variant) {
+    case 1: return launch_fused<32, 8, 8>(a, s);
+    case 2: return launch_fused<32, 16, 8>(a, s);
+    case 3: return launch_fused<32, 16, 8, 3>(a, s);
+    default: return launch_fused<32, 16, 4, 4>(a, s);
+    }
+}
+
+cudaError_t launch_reroll_w32(const RolloutArgs& a, const EpilogueArgs& e, cudaStream_t s)
+{
+    return launch_reroll<32, 16>(a, e, s);
+}
+
 }  // namespace npp

@@ -16,4 +16,19 @@ cudaError_t launch_traj_w64(const RolloutArgs& a, cudaStream_t s, int variant)
     }
 }
 
+cudaError_t launch_fused_w64(const RolloutArgs& a, cudaStream_t s, int variant)
+{
+    switch (variant) {
+    case 1: return launch_fused<64, 16, 8>(a, s);
+    case 2: return launch_fused<64, 32, 8>(a, s);
+    case 3: return launch_fused<64, 32, 2, 5>(a, s);
+    default: return launch_fused<64, 32, 1, 10>(a, s);
+    }
+}
+
+cudaError_t launch_reroll_w64(const RolloutArgs& a, const EpilogueArgs& e, cudaStream_t s)
+{
+    return launch_reroll<64, 32>(a, e, s);
+}
+
 }  // namespace npp

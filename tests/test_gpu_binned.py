@@ -26,7 +26,7 @@ def _cuda():
         pytest.skip("no CUDA device")
 
 
-def _plan(sc, variant, pl=None):
+def _plan(sc, variant, pl=None, fuse=0):
     import torch
     from paper_1904_06680_gb300 import npp
     N, T = sc["N"], sc["T"]
@@ -35,6 +35,7 @@ def _plan(sc, variant, pl=None):
     if own:
         pl = npp.Planner(sc["preset"], max_N=N, max_T=T, max_M=max(M, 1))
     npp.npp_set_option(pl.h, "collide_variant", variant)
+    npp.npp_set_option(pl.h, "fuse", fuse)
     obs = torch.tensor(sc["obs"], dtype=torch.float32, device="cuda") if M else None
     pl.plan(sc["state"], sc["goal"], obs, N, T, sc["seed"], sc["t_index"])
     torch.cuda.synchronize()
@@ -50,13 +51,49 @@ def _assert_same(a, b):
     assert (a["best_idx"], a["status"], a["first_hit_best"]) == (b["best_idx"], b["status"], b["first_hit_best"])
     assert np.float32(a["best_cost"]).view(np.int32) == np.float32(b["best_cost"]).view(np.int32)
     np.testing.assert_array_equal(a["params"], b["params"])
+    np.testing.assert_array_equal(a["trajectory"], b["trajectory"])
+    np.testing.assert_array_equal(a["controls"], b["controls"])
 
 
 @pytest.mark.parametrize("seed,N,T,M", [(1, 300, 20, 200), (2, 1000, 33, 1500), (3, 77, 5, 1),
                                         (4, 4096, 40, 5000)])
 def test_binned_equals_brute_force_random(seed, N, T, M):
+    """Stored-rows (default) and fused binned checks against
+    brute force: every sample's flag and cost, the winner and its re-rolled
+    rows."""
     sc = inputs.tiny_scene(seed, N, T, M, width=32, box=25.0, clear=2.0)
-    _assert_same(_plan(sc, BINNED), _plan(sc, 3))
+    brute = _plan(sc, 3)
+    _assert_same(_plan(sc, BINNED), brute)
+    _assert_same(_plan(sc, BINNED, fuse=1), brute)
+
+
+@pytest.mark.parametrize("width", [16, 64])
+def test_fused_binned_other_widths(width):
+    sc = inputs.tiny_scene(40 + width, 1500, 30, 900, width=width, box=25.0, clear=2.0)
+    brute = _plan(sc, 2)
+    _assert_same(_plan(sc, BINNED), brute)
+    _assert_same(_plan(sc, BINNED, fuse=1), brute)
+
+
+def test_fused_infeasible_and_warm_start():
+    """All samples collide (a converging ring of points): the fused path
+    reports the latest first collision and the winner's rows repeat the
+    colliding state with zero controls after it, as the stored path does."""
+    import torch
+    from paper_1904_06680_gb300 import npp
+    p = inputs.planner(32)
+    ang = np.linspace(0, 2 * np.pi, 400, endpoint=False)
+    obs = np.zeros((400, 4))
+    obs[:, 0], obs[:, 1] = 9 * np.cos(ang), 9 * np.sin(ang)
+    obs[:, 2], obs[:, 3] = -2 * np.cos(ang), -2 * np.sin(ang)
+    sc = dict(preset=p, state=np.array([0.0, 0.0, 0.3, 1.0, 0.1, 0.0]), goal=np.array([6.0, 2.0, 0.0, 0.0]),
+              obs=obs, N=2000, T=40, seed=inputs.philox_seed(5), t_index=3)
+    from paper_1904_06680_gb300 import npp as _npp
+    b = _plan(sc, 2)
+    for fuse in (0, 1):
+        a = _plan(sc, BINNED, fuse=fuse)
+        assert a["status"] == _npp.NPP_INFEASIBLE
+        _assert_same(a, b)
 
 
 def test_binned_without_points():
@@ -143,22 +180,25 @@ def test_binned_closed_loop_identical_to_brute_force():
     M = sc["obs"].shape[0]
     obs0 = torch.tensor(sc["obs"], dtype=torch.float32, device="cuda")
     runs = {}
-    for variant in (BINNED, 2):
+    for variant, fuse in ((BINNED, 0), (2, 0), (BINNED, 1)):
         pl = npp.Planner(p, max_N=N, max_T=T, max_M=M)
         npp.npp_set_option(pl.h, "collide_variant", variant)
+        npp.npp_set_option(pl.h, "fuse", fuse)
         L = npp.npp_loop_create(pl.h, sc["state"], sc["waypoints"], inputs.EPS, obs0, M, N, T, sc["seed"])
         npp.npp_loop_run(L, 1)
         s0 = npp.npp_loop_samples(L, N)
         npp.npp_loop_run(L, 19)
         s19 = npp.npp_loop_samples(L, N)
-        runs[variant] = (s0, s19, npp.npp_loop_log(L), npp.npp_loop_read(L))
+        runs[(variant, fuse)] = (s0, s19, npp.npp_loop_log(L), npp.npp_loop_read(L))
         npp.npp_loop_destroy(L)
         pl.close()
-    a, b = runs[BINNED], runs[2]
-    for k in range(2):
-        np.testing.assert_array_equal(a[k][1], b[k][1])
-        np.testing.assert_array_equal(a[k][0].view(np.int32), b[k][0].view(np.int32))
-    np.testing.assert_array_equal(a[2], b[2])
-    assert a[3] == b[3]
+    b = runs[(2, 0)]
+    for a in (runs[(BINNED, 0)], runs[(BINNED, 1)]):
+        for k in range(2):
+            np.testing.assert_array_equal(a[k][1], b[k][1])
+            np.testing.assert_array_equal(a[k][0].view(np.int32), b[k][0].view(np.int32))
+        np.testing.assert_array_equal(a[2], b[2])
+        assert a[3] == b[3]
+    a = runs[(BINNED, 0)]
     assert a[3]["t"] == 20
     assert np.any(a[1][1] < 0)                # feasible plans at step 19

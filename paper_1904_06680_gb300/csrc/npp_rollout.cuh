@@ -265,6 +265,7 @@ __device__ __forceinline__ FusedOut traj_sample(const DevCfg& c, const TrajJob& 
     bool alive = valid;
     int fh = -1;
     bool all_dead = false;
+    float rem = (float)T;                // T - h, exact in FP32
     for (int h = 0; h < T; ++h) {
         float sp, cp;
         sincos_r(ph, sp, cp);
@@ -280,9 +281,20 @@ __device__ __forceinline__ FusedOut traj_sample(const DevCfg& c, const TrajJob& 
                 all_dead = true;
                 break;
             }
-        } else if (writer) {
-            if (job.traj) job.traj[h * job.rec_stride + rec] = make_float4(x, y, ph, v);
-            if (job.coefA) write_coef(job.coefA, job.coefB, c, job.coef_base + (long long)h * N + n, x, y, sp, cp);
+        } else {
+            // pointer tests are uniform over the kernel; only the stores
+            // depend on the writer lane
+            if (job.traj && writer) job.traj[h * job.rec_stride + rec] = make_float4(x, y, ph, v);
+            if (job.coefA) {
+                float4 A;
+                float2 B;
+                coef_rows(c, x, y, sp, cp, A, B);
+                if (writer) {
+                    const long long ci = job.coef_base + (long long)h * N + n;
+                    job.coefA[ci] = A;
+                    job.coefB[ci] = B;
+                }
+            }
         }
         float s[NIN];
         s[0] = (gxi - x) * c.idxi;
@@ -292,7 +304,8 @@ __device__ __forceinline__ FusedOut traj_sample(const DevCfg& c, const TrajJob& 
         s[4] = ap0;
         s[5] = ap1;
         s[6] = v * c.idv;
-        s[7] = (float)(T - h) * invT;
+        s[7] = rem * invT;
+        rem -= 1.0f;
         float h1[U];
 #pragma unroll
         for (int j = 0; j < U; ++j) {

@@ -293,9 +293,13 @@ npp_status npp_batch_offsets(npp_batch* B, int64_t* offsets_host);
 npp_status npp_plan_batch(npp_batch* B, const float* obs_dev, const npp_batch_outputs* out,
                           void* stream);
 
-/* Launch shapes of the batch (no result changes): "slices" = warps that share
- * one 8-sample collision item, each on a slice of the points (2, 4 or 8;
- * default 4); "traj_warps" = warps per trajectory block (4 or 8; default 8).
+/* Launch shapes of the batch (no result changes): "collide" = collision
+ * check: 1 (default) per-scene, per-step spatial bins (one warp per sample,
+ * the points of the cells its rectangle's disk overlaps), 0 brute force over
+ * the scene's points, sorted by cell so that tiles out of reach of an
+ * item's live samples are skipped; "slices" = warps that share one 8-sample
+ * brute-force item, each on an interleaved share of the point tiles (2, 4 or
+ * 8; default 4); "traj_warps" = warps per trajectory block (4 or 8; default 8).
  * Synchronous (re-plans the work lists). */
 npp_status npp_batch_set_option(npp_batch* B, const char* name, int32_t value);
 

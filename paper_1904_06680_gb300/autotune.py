@@ -24,7 +24,9 @@ import torch
 from . import npp
 
 PLAN_VARIANTS = (0, 1, 2, 3, 4)
-BATCH_CANDIDATES = tuple((s, w) for s in (2, 4, 8) for w in (4, 8))
+# (collision check, point slices, trajectory warps): check 1 = per-step bins
+# (slices unused), 0 = brute force over cell-sorted point tiles
+BATCH_CANDIDATES = tuple([(1, 4, w) for w in (4, 8)] + [(0, s, w) for s in (2, 4, 8) for w in (4, 8)])
 
 _cache = {}
 
@@ -76,21 +78,27 @@ def tune_plan_step(planner, state, goal, obs, N, T, seed, reps=3, path=None):
     return best, _cache[key]["ms"]
 
 
+def _set_batch(batch, cand):
+    c, s, w = cand
+    npp.npp_batch_set_option(batch, "collide", c)
+    npp.npp_batch_set_option(batch, "slices", s)
+    npp.npp_batch_set_option(batch, "traj_warps", w)
+
+
 def tune_batch(batch, obs, out, key, reps=2, path=None, stream=None):
-    """Pick (slices, traj_warps) for a batch; returns ((slices, warps), ms
-    per candidate).  `key` names the batch layout for the cache."""
+    """Pick (collision check, slices, traj_warps) for a batch; returns the
+    choice and ms per candidate.  `key` names the batch layout for the
+    cache."""
     _load(path)
     k = "batch:" + key
-    if k in _cache:
-        s, w = _cache[k]["best"]
-        npp.npp_batch_set_option(batch, "slices", s)
-        npp.npp_batch_set_option(batch, "traj_warps", w)
-        return (s, w), _cache[k]["ms"]
+    if k in _cache and len(_cache[k]["best"]) == 3:
+        best = tuple(_cache[k]["best"])
+        _set_batch(batch, best)
+        return best, _cache[k]["ms"]
     stream = stream or torch.cuda.current_stream()
     times = {}
-    for s, w in BATCH_CANDIDATES:
-        npp.npp_batch_set_option(batch, "slices", s)
-        npp.npp_batch_set_option(batch, "traj_warps", w)
+    for cand in BATCH_CANDIDATES:
+        _set_batch(batch, cand)
         ts = []
         for r in range(reps + 1):
             e0 = torch.cuda.Event(enable_timing=True)
@@ -100,10 +108,9 @@ def tune_batch(batch, obs, out, key, reps=2, path=None, stream=None):
             e1.record(stream)
             e1.synchronize()
             ts.append(e0.elapsed_time(e1))
-        times[(s, w)] = float(np.median(ts[1:]))
+        times[cand] = float(np.median(ts[1:]))
     best = min(times, key=times.get)
-    npp.npp_batch_set_option(batch, "slices", best[0])
-    npp.npp_batch_set_option(batch, "traj_warps", best[1])
-    _cache[k] = {"best": list(best), "ms": {"%d,%d" % sw: t for sw, t in times.items()}}
+    _set_batch(batch, best)
+    _cache[k] = {"best": list(best), "ms": {"%d,%d,%d" % c: t for c, t in times.items()}}
     _store(path)
     return best, _cache[k]["ms"]

@@ -35,6 +35,9 @@ struct SceneDev {
     long long coef_off;      // first coefficient row
     long long samp_off;      // first sample (costs, first_hit, jfree)
     long long params_off, ctrl_off, traj_off;
+    long long tile_off;      // first point tile (32 pairs)
+    long long bin_off;       // first int of the scene's per-step cell tables
+    long long bpts_off;      // first float2 of the scene's per-step sorted points
     uint32_t k0, k1, t_index, pad;
 };
 
@@ -43,8 +46,16 @@ struct BatchArgs {
     const SceneDev* scenes;
     int S;
     const float4* obs;               // input points (world frame)
-    float4* pXY;                     // transformed pairs
+    float4* pXY;                     // transformed pairs, sorted by cell (static points first)
     float4* pV;
+    float4* tileP;                   // per tile of 32 pairs: (min x, max x, min y, max y) of its points
+    float4* tileV;                   // (min vx, max vx, min vy, max vy)
+    float reach;                     // radius around a rectangle's centre that holds it, plus a margin
+    // binned collision check (per scene and horizon step)
+    BinView grid;                    // geometry (cell_start, pts, M unused here)
+    int* bin_cs;                     // cell tables, scene s at bin_off
+    float2* bin_pts;                 // sorted points, scene s at bpts_off
+    const long long* bstep_prefix;   // prefix over scenes of T + 1 (grid-build blocks)
     float4* coefA;
     float2* coefB;
     float* jfree;
@@ -87,25 +98,219 @@ __device__ __forceinline__ StepIn scene_step_in(const SceneDev& s)
     return si;
 }
 
-// world -> EV frame, as pairs (odd tail padded with a far point)
-__global__ void batch_prologue_kernel(const BatchArgs b)
+// World -> EV frame, as pairs, ordered for tile culling: a counting sort by
+// a coarse cell of the EV-frame position (4 m cells, 64 x 64 around the
+// vehicle, clamped), static points before moving ones (the order of the
+// points does not change any result: a collision is "some point inside").
+// The odd tail is padded with a far point.  Then per tile of 32 pairs the
+// bounds of its real points' positions and velocities.
+constexpr int SORT_THREADS = 1024;
+constexpr int SORT_DIM = 64;
+constexpr int SORT_KEYS = 2 * SORT_DIM * SORT_DIM;   // static cells, then moving cells
+
+__device__ __forceinline__ int sort_key(float px, float py, float vx, float vy)
 {
-    const SceneDev& s = b.scenes[blockIdx.y];
-    const int npairs = (s.M + 1) / 2;
+    const int cx = (int)fminf(fmaxf(floorf((px + 128.0f) * 0.25f), 0.0f), (float)(SORT_DIM - 1));
+    const int cy = (int)fminf(fmaxf(floorf((py + 128.0f) * 0.25f), 0.0f), (float)(SORT_DIM - 1));
+    const bool moving = vx != 0.0f || vy != 0.0f;
+    return (moving ? SORT_DIM * SORT_DIM : 0) + cy * SORT_DIM + cx;
+}
+
+__global__ void __launch_bounds__(SORT_THREADS) batch_prologue_kernel(const BatchArgs b)
+{
+    extern __shared__ int cnt[];                       // [SORT_KEYS]
+    __shared__ int run_tot[SORT_THREADS];
+    const SceneDev& s = b.scenes[blockIdx.x];
+    const int M = s.M;
+    if (M == 0) return;
+    const int npairs = (M + 1) / 2;
     float sn, cs;
     sincosf(s.phi0, &sn, &cs);
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < npairs; q += gridDim.x * blockDim.x) {
-        float px[2], py[2], vx[2], vy[2];
+    for (int i = threadIdx.x; i < SORT_KEYS; i += blockDim.x) cnt[i] = 0;
+    __syncthreads();
+    for (int j = threadIdx.x; j < M; j += blockDim.x) {
+        float px, py, vx, vy;
+        ev_point(b.obs[s.obs_off + j], s.x0, s.y0, sn, cs, px, py, vx, vy);
+        atomicAdd(&cnt[sort_key(px, py, vx, vy)], 1);
+    }
+    __syncthreads();
+    constexpr int RUN = SORT_KEYS / SORT_THREADS;
+    const int base = threadIdx.x * RUN;
+    int acc = 0;
+    for (int k = 0; k < RUN; ++k) { const int v = cnt[base + k]; cnt[base + k] = acc; acc += v; }
+    run_tot[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        constexpr int PER = SORT_THREADS / 32;
+        int local = 0;
+        for (int k = 0; k < PER; ++k) local += run_tot[threadIdx.x * PER + k];
+        int incl = local;
+        for (int off = 1; off < 32; off <<= 1) {
+            const int v = __shfl_up_sync(FULL, incl, off);
+            if ((int)threadIdx.x >= off) incl += v;
+        }
+        int run = incl - local;
+        for (int k = 0; k < PER; ++k) {
+            const int v = run_tot[threadIdx.x * PER + k];
+            run_tot[threadIdx.x * PER + k] = run;
+            run += v;
+        }
+    }
+    __syncthreads();
+    for (int k = 0; k < RUN; ++k) cnt[base + k] += run_tot[threadIdx.x];
+    __syncthreads();
+    float* xy = reinterpret_cast<float*>(b.pXY + s.pair_off);
+    float* vv = reinterpret_cast<float*>(b.pV + s.pair_off);
+    for (int j = threadIdx.x; j < M; j += blockDim.x) {
+        float px, py, vx, vy;
+        ev_point(b.obs[s.obs_off + j], s.x0, s.y0, sn, cs, px, py, vx, vy);
+        const int pos = atomicAdd(&cnt[sort_key(px, py, vx, vy)], 1);
+        const int q = pos >> 1, o = pos & 1;
+        xy[4 * q + o] = px;
+        xy[4 * q + 2 + o] = py;
+        vv[4 * q + o] = vx;
+        vv[4 * q + 2 + o] = vy;
+    }
+    if (threadIdx.x == 0 && (M & 1)) {
+        const int q = M >> 1;
+        xy[4 * q + 1] = 1e15f;
+        xy[4 * q + 3] = 1e15f;
+        vv[4 * q + 1] = 0.0f;
+        vv[4 * q + 3] = 0.0f;
+    }
+    __syncthreads();
+    // tile bounds over the real points (the pad point is never inside)
+    const int ntiles = (npairs + 31) / 32;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int t = warp; t < ntiles; t += SORT_THREADS / 32) {
+        float mnx = INFINITY, mxx = -INFINITY, mny = INFINITY, mxy = -INFINITY;
+        float mnvx = INFINITY, mxvx = -INFINITY, mnvy = INFINITY, mxvy = -INFINITY;
+        const int q = t * 32 + lane;
         for (int o = 0; o < 2; ++o) {
             const int j = 2 * q + o;
-            px[o] = 1e15f; py[o] = 1e15f; vx[o] = 0.f; vy[o] = 0.f;
-            if (j < s.M) {
-                ev_point(b.obs[s.obs_off + j], s.x0, s.y0, sn, cs, px[o], py[o], vx[o], vy[o]);
+            if (q < npairs && j < M) {
+                const float px = xy[4 * q + o], py = xy[4 * q + 2 + o];
+                const float vx = vv[4 * q + o], vy = vv[4 * q + 2 + o];
+                mnx = fminf(mnx, px); mxx = fmaxf(mxx, px); mny = fminf(mny, py); mxy = fmaxf(mxy, py);
+                mnvx = fminf(mnvx, vx); mxvx = fmaxf(mxvx, vx); mnvy = fminf(mnvy, vy); mxvy = fmaxf(mxvy, vy);
             }
         }
-        b.pXY[s.pair_off + q] = make_float4(px[0], px[1], py[0], py[1]);
-        b.pV[s.pair_off + q] = make_float4(vx[0], vx[1], vy[0], vy[1]);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            mnx = fminf(mnx, __shfl_xor_sync(FULL, mnx, off));
+            mxx = fmaxf(mxx, __shfl_xor_sync(FULL, mxx, off));
+            mny = fminf(mny, __shfl_xor_sync(FULL, mny, off));
+            mxy = fmaxf(mxy, __shfl_xor_sync(FULL, mxy, off));
+            mnvx = fminf(mnvx, __shfl_xor_sync(FULL, mnvx, off));
+            mxvx = fmaxf(mxvx, __shfl_xor_sync(FULL, mxvx, off));
+            mnvy = fminf(mnvy, __shfl_xor_sync(FULL, mnvy, off));
+            mxvy = fmaxf(mxvy, __shfl_xor_sync(FULL, mxvy, off));
+        }
+        if (lane == 0) {
+            b.tileP[s.tile_off + t] = make_float4(mnx, mxx, mny, mxy);
+            b.tileV[s.tile_off + t] = make_float4(mnvx, mxvx, mnvy, mxvy);
+        }
     }
+}
+
+// The pair loop of one warp's tiles (t0, t0 + tstep, ...) for CC live
+// samples staged in the warp's slots, skipping tiles whose points, at time
+// tau, cannot reach the box around the live samples (box: xmin, xmax, ymin,
+// ymax).  fma rounding is monotone, so every point's extrapolated position
+// lies in the tile's extrapolated bounds; the per-point test is the
+// brute-force one.  Returns the hit bits in slot order.
+template <int CC>
+__device__ __forceinline__ unsigned check_slots_tiles(const float4* __restrict__ XY, const float4* __restrict__ V,
+                                                      int npairs, float tau, const float4* __restrict__ sA,
+                                                      const float2* __restrict__ sB, int L, int lane,
+                                                      const float4* __restrict__ tP, const float4* __restrict__ tV,
+                                                      int ntiles, int t0, int tstep, float4 box)
+{
+    unsigned long long A[CC], B[CC], NC[CC], D[CC], E[CC], NF[CC];
+#pragma unroll
+    for (int k = 0; k < CC; ++k) {
+        const int slot = k < L ? k : 0;
+        const float4 qa = sA[slot];
+        const float2 qb = sB[slot];
+        A[k] = pk(qa.x, qa.x); B[k] = pk(qa.y, qa.y); NC[k] = pk(qa.z, qa.z);
+        D[k] = pk(qa.w, qa.w); E[k] = pk(qb.x, qb.x); NF[k] = pk(qb.y, qb.y);
+    }
+    unsigned long long acc[CC];
+#pragma unroll
+    for (int k = 0; k < CC; ++k) acc[k] = 0ull;
+    const unsigned long long TT = pk(tau, tau);
+    for (int t = t0; t < ntiles; t += tstep) {
+        const float4 P = tP[t], Q = tV[t];
+        if (fmaf(tau, Q.x, P.x) > box.y || fmaf(tau, Q.y, P.y) < box.x ||
+            fmaf(tau, Q.z, P.z) > box.w || fmaf(tau, Q.w, P.w) < box.z)
+            continue;
+        const int q = t * 32 + lane;
+        if (q < npairs) {
+            const float4 xy = XY[q];
+            const float4 vv = V[q];
+            const unsigned long long PX = fma2(TT, pk(vv.x, vv.y), pk(xy.x, xy.y));
+            const unsigned long long PY = fma2(TT, pk(vv.z, vv.w), pk(xy.z, xy.w));
+#pragma unroll
+            for (int k = 0; k < CC; ++k) {
+                const unsigned long long xi = fma2(A[k], PX, fma2(B[k], PY, NC[k]));
+                const unsigned long long et = fma2(D[k], PX, fma2(E[k], PY, NF[k]));
+                acc[k] |= ~(xi | et);
+            }
+        }
+    }
+    unsigned bits = 0;
+#pragma unroll
+    for (int k = 0; k < CC; ++k) {
+        const bool inside = ((((unsigned)acc[k]) | (unsigned)(acc[k] >> 32)) >> 30) & 1u;
+        if (k < L && __any_sync(FULL, inside)) bits |= 1u << k;
+    }
+    return bits;
+}
+
+// one culled step of an 8-sample item for one warp (see warp_step)
+__device__ __forceinline__ unsigned warp_step_tiles(const float4* XY, const float4* V, int npairs, float tau,
+                                                    float4 ca, float2 cb, unsigned live, float4* sA, float2* sB,
+                                                    int lane, const float4* tP, const float4* tV, int ntiles,
+                                                    int t0, int tstep, float4 box)
+{
+    const bool owner = lane < 8 && ((live >> lane) & 1u);
+    const int rank = __popc(live & ((1u << lane) - 1u));
+    if (owner) { sA[rank] = ca; sB[rank] = cb; }
+    __syncwarp();
+    const int L = __popc(live);
+    unsigned bits;
+    if (L > 4)      bits = check_slots_tiles<8>(XY, V, npairs, tau, sA, sB, L, lane, tP, tV, ntiles, t0, tstep, box);
+    else if (L > 2) bits = check_slots_tiles<4>(XY, V, npairs, tau, sA, sB, L, lane, tP, tV, ntiles, t0, tstep, box);
+    else if (L > 1) bits = check_slots_tiles<2>(XY, V, npairs, tau, sA, sB, L, lane, tP, tV, ntiles, t0, tstep, box);
+    else            bits = check_slots_tiles<1>(XY, V, npairs, tau, sA, sB, L, lane, tP, tV, ntiles, t0, tstep, box);
+    __syncwarp();
+    return __ballot_sync(FULL, owner && ((bits >> rank) & 1u));
+}
+
+// Box (xmin, xmax, ymin, ymax) around the rectangles of the live samples of
+// an item (owner lanes 0..7), from their scaled inequality rows: the centre
+// is R^T (along, across) with cos, sin = A / sl, B / sl, along = -C' / sl,
+// across = -F' / sw; plus `reach` (the rectangle's circumradius and a margin
+// far above the rounding of this reconstruction).  Uniform over the warp.
+__device__ __forceinline__ float4 live_box(const DevCfg& c, float4 ca, float2 cb, bool owner, float reach)
+{
+    float xmn = INFINITY, xmx = -INFINITY, ymn = INFINITY, ymx = -INFINITY;
+    if (owner) {
+        const float isl = 1.0f / (2.0f * c.ihl), isw = 1.0f / (2.0f * c.ihw);
+        const float cp = ca.x * isl, sp = ca.y * isl;
+        const float along = -ca.z * isl, across = -cb.y * isw;
+        const float xc = cp * along - sp * across, yc = sp * along + cp * across;
+        xmn = xc - reach; xmx = xc + reach; ymn = yc - reach; ymx = yc + reach;
+    }
+#pragma unroll
+    for (int off = 4; off > 0; off >>= 1) {
+        xmn = fminf(xmn, __shfl_xor_sync(FULL, xmn, off));
+        xmx = fmaxf(xmx, __shfl_xor_sync(FULL, xmx, off));
+        ymn = fminf(ymn, __shfl_xor_sync(FULL, ymn, off));
+        ymx = fmaxf(ymx, __shfl_xor_sync(FULL, ymx, off));
+    }
+    return make_float4(__shfl_sync(FULL, xmn, 0), __shfl_sync(FULL, xmx, 0), __shfl_sync(FULL, ymn, 0),
+                       __shfl_sync(FULL, ymx, 0));
 }
 
 template <int W, int G, int NW>
@@ -194,8 +399,9 @@ __global__ void __launch_bounds__(S * 32) batch_collide_kernel(const BatchArgs b
         }
         const float4* XY = resident ? sXY : b.pXY + s.pair_off;
         const float4* V = resident ? sV : b.pV + s.pair_off;
-        const int per = (npairs + S - 1) / S;
-        const int q0 = min(npairs, warp * per), q1 = min(npairs, q0 + per);
+        const int ntiles = (npairs + 31) / 32;
+        const float4* tP = b.tileP + s.tile_off;
+        const float4* tV = b.tileV + s.tile_off;
         const int T = s.T, N = s.N;
         const int n0 = (int)(item - __ldg(b.citem_prefix + r)) * 8;
         const int cnt = min(8, N - n0);
@@ -215,9 +421,10 @@ __global__ void __launch_bounds__(S * 32) batch_collide_kernel(const BatchArgs b
             }
             const unsigned gone = __ballot_sync(FULL, lane < 8 && *(volatile int*)&dead_at[lane] <= h);
             live &= ~gone;
-            if (live == 0u || q1 <= q0) break;
-            const unsigned hits = warp_step(XY + q0, V + q0, q1 - q0, (float)h * b.c.Ts, cur_a, cur_b,
-                                            live, sA, sB, lane);
+            if (live == 0u || ntiles <= warp) break;
+            const float4 box = live_box(b.c, cur_a, cur_b, lane < 8 && ((live >> lane) & 1u), b.reach);
+            const unsigned hits = warp_step_tiles(XY, V, npairs, (float)h * b.c.Ts, cur_a, cur_b, live, sA, sB,
+                                                  lane, tP, tV, ntiles, warp, S, box);
             if ((hits >> lane) & 1u) atomicMin(&dead_at[lane], h);
             live &= ~hits;
         }
@@ -244,6 +451,91 @@ __global__ void __launch_bounds__(S * 32) batch_collide_kernel(const BatchArgs b
             }
             if (lane == 0) atomicMin(b.keys + si, key);
         }
+    }
+}
+
+// Grids of every scene and horizon step: block b -> (scene, h).
+__global__ void __launch_bounds__(1024) batch_bin_build_kernel(const BatchArgs b)
+{
+    extern __shared__ int cnt[];             // [BIN_NCELL]
+    __shared__ int run_tot[1024];
+    const long long blk = blockIdx.x;
+    const int si = find_slot(b.bstep_prefix, b.S, blk);
+    const SceneDev& s = b.scenes[si];
+    const int h = (int)(blk - __ldg(b.bstep_prefix + si));
+    float sn, cs;
+    sincosf(s.phi0, &sn, &cs);
+    build_step_bins<1024>(b.obs + s.obs_off, s.M, s.x0, s.y0, sn, cs, (float)h * b.c.Ts, b.grid,
+                          b.bin_cs + s.bin_off + (size_t)h * BIN_CS_STRIDE, b.bin_pts + s.bpts_off + (size_t)h * s.M,
+                          cnt, run_tot);
+}
+
+// Binned check of an 8-sample item per block, one warp per sample, over the
+// stored inequality rows (the rectangle's centre recovered from them, as in
+// live_box); the candidates of a step are the points of at most two cell
+// rows of the scene's grid; one key minimum per block.
+__global__ void __launch_bounds__(256) batch_binned_kernel(const BatchArgs b)
+{
+    __shared__ unsigned long long red[8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long item = blockIdx.x;
+    const int r = find_slot(b.citem_prefix, b.S, item);
+    const int si = b.order[r];
+    const SceneDev& s = b.scenes[si];
+    const int T = s.T, N = s.N, M = s.M;
+    const int n = (int)(item - __ldg(b.citem_prefix + r)) * 8 + warp;
+    const BinView& g = b.grid;
+    const float isl = 1.0f / (2.0f * b.c.ihl), isw = 1.0f / (2.0f * b.c.ihw);
+    unsigned long long key = ~0ull;
+    if (n < N) {
+        int fh = -1;
+        for (int h = 0; h <= T; ++h) {
+            const long long idx = s.coef_off + (long long)h * N + n;
+            const float4 ca = b.coefA[idx];
+            const float2 cb = b.coefB[idx];
+            const float cp = ca.x * isl, sp = ca.y * isl;
+            const float along = -ca.z * isl, across = -cb.y * isw;
+            const float xc = cp * along - sp * across, yc = sp * along + cp * across;
+            const int ix0 = bin_cell(xc - b.reach, g), ix1 = bin_cell(xc + b.reach, g);
+            const int iy0 = bin_cell(yc - b.reach, g), iy1 = bin_cell(yc + b.reach, g);
+            const int* cs = b.bin_cs + s.bin_off + (size_t)h * BIN_CS_STRIDE;
+            const float2* pts = b.bin_pts + s.bpts_off + (size_t)h * M;
+            const int r0b = cs[iy0 * BIN_DIM + ix0], r0e = cs[iy0 * BIN_DIM + ix1 + 1];
+            int r1b = r0e, r1e = r0e;
+            if (iy1 != iy0) { r1b = cs[iy1 * BIN_DIM + ix0]; r1e = cs[iy1 * BIN_DIM + ix1 + 1]; }
+            const int n0 = r0e - r0b, total = n0 + (r1e - r1b);
+            bool hit = false;
+            for (int base = 0; base < total && !hit; base += 32) {
+                const int k = base + lane;
+                bool inside = false;
+                if (k < total) {
+                    const float2 p = pts[k < n0 ? r0b + k : r1b + (k - n0)];
+                    const float xi = fmaf(ca.x, p.x, fmaf(ca.y, p.y, ca.z));
+                    const float et = fmaf(ca.w, p.x, fmaf(cb.x, p.y, cb.y));
+                    inside = !(((__float_as_uint(xi) | __float_as_uint(et)) >> 30) & 1u);
+                }
+                hit = __any_sync(FULL, inside);
+            }
+            if (hit) { fh = h; break; }
+        }
+        if (lane == 0) {
+            float J = __int_as_float(0x7f800000);
+            if (fh < 0) {
+                J = b.jfree[s.samp_off + n];
+                key = ((unsigned long long)__float_as_uint(J) << 32) | (unsigned)n;
+            } else {
+                key = (1ull << 63) | ((unsigned long long)(T - fh) << 32) | (unsigned)n;
+            }
+            if (b.costs) b.costs[s.samp_off + n] = J;
+            if (b.first_hit) b.first_hit[s.samp_off + n] = fh;
+        }
+    }
+    if (lane == 0) red[warp] = key;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long k = red[0];
+        for (int w = 1; w < 8; ++w) k = red[w] < k ? red[w] : k;
+        atomicMin(b.keys + si, k);
     }
 }
 
@@ -354,6 +646,14 @@ struct npp_batch {
     int n_torder[3];
     float4* d_pXY;
     float4* d_pV;
+    float4* d_tileP;
+    float4* d_tileV;
+    int* d_bin_cs;
+    float2* d_bin_pts;
+    long long* d_bstep_prefix;
+    long long bin_blocks;    // sum over scenes of T + 1
+    long long total_items;   // sum over scenes of ceil(N / 8)
+    int binned;              // collision check: 0 brute force (tile-culled), 1 per-step bins
     float4* d_coefA;
     float2* d_coefB;
     float* d_jfree;
@@ -377,7 +677,8 @@ void free_batch(npp_batch* B)
     if (!B) return;
     void* ptrs[] = { B->d_scenes, B->d_order, B->d_citem_prefix, B->d_torder[0], B->d_torder[1],
                      B->d_torder[2], B->d_titem_prefix[0], B->d_titem_prefix[1], B->d_titem_prefix[2],
-                     B->d_pXY, B->d_pV, B->d_coefA, B->d_coefB, B->d_jfree, B->d_keys, B->d_counters };
+                     B->d_pXY, B->d_pV, B->d_tileP, B->d_tileV, B->d_bin_cs, B->d_bin_pts, B->d_bstep_prefix,
+                     B->d_coefA, B->d_coefB, B->d_jfree, B->d_keys, B->d_counters };
     for (void* p : ptrs) if (p) cudaFree(p);
     delete B;
 }
@@ -386,7 +687,8 @@ npp_status upload_scenes(npp_batch* B)
 {
     npp_handle* h = B->h;
     std::vector<SceneDev> sd(B->S);
-    long long pair = 0, rows = 0, samp = 0, par = 0, ctl = 0, trj = 0;
+    long long pair = 0, rows = 0, samp = 0, par = 0, ctl = 0, trj = 0, tiles = 0, bcs = 0, bpts = 0;
+    std::vector<long long> bstep(B->S + 1, 0);
     for (int i = 0; i < B->S; ++i) {
         const npp_scene& s = B->scenes[i];
         SceneDev& d = sd[i];
@@ -396,6 +698,10 @@ npp_status upload_scenes(npp_batch* B)
         d.N = s.N; d.T = s.T; d.M = s.M; d.width = s.width;
         d.obs_off = s.obs_offset;
         d.pair_off = pair; pair += (s.M + 1) / 2;
+        d.tile_off = tiles; tiles += ((s.M + 1) / 2 + 31) / 32;
+        d.bin_off = bcs; bcs += (long long)(s.T + 1) * BIN_CS_STRIDE;
+        d.bpts_off = bpts; bpts += (long long)(s.T + 1) * s.M;
+        bstep[i + 1] = bstep[i] + s.T + 1;
         d.coef_off = rows; rows += (long long)s.N * (s.T + 1);
         d.samp_off = samp; samp += s.N;
         d.params_off = par; par += n_theta_w(s.width);
@@ -407,6 +713,8 @@ npp_status upload_scenes(npp_batch* B)
         d.pad = 0;
     }
     CUDA_TRY(h, cudaMemcpy(B->d_scenes, sd.data(), sizeof(SceneDev) * B->S, cudaMemcpyHostToDevice));
+    CUDA_TRY(h, cudaMemcpy(B->d_bstep_prefix, bstep.data(), sizeof(long long) * (B->S + 1), cudaMemcpyHostToDevice));
+    B->bin_blocks = bstep[B->S];
     return NPP_OK;
 }
 
@@ -498,7 +806,7 @@ npp_status npp_batch_create(npp_handle* h, const npp_scene* scenes, int32_t S, n
 {
     if (!h || !out || !scenes || S < 1) return fail(h, NPP_INVALID_ARG, "batch: bad arguments");
     *out = nullptr;
-    long long pairs = 0, rows = 0, samples = 0;
+    long long pairs = 0, rows = 0, samples = 0, tiles_total = 0, bin_ints = 0, bin_pts = 0, items = 0;
     int max_pairs = 0;
     for (int i = 0; i < S; ++i) {
         const npp_scene& s = scenes[i];
@@ -512,6 +820,10 @@ npp_status npp_batch_create(npp_handle* h, const npp_scene* scenes, int32_t S, n
         if (std::fabs(s.state.a_prev0) > 1.f || std::fabs(s.state.a_prev1) > 1.f)
             return fail(h, NPP_INVALID_ARG, "batch: scene %d previous controls outside [-1, 1]", i);
         pairs += (s.M + 1) / 2;
+        tiles_total += ((s.M + 1) / 2 + 31) / 32;
+        bin_ints += (long long)(s.T + 1) * BIN_CS_STRIDE;
+        bin_pts += (long long)(s.T + 1) * s.M;
+        items += (s.N + 7) / 8;
         rows += (long long)s.N * (s.T + 1);
         samples += s.N;
         max_pairs = std::max(max_pairs, (s.M + 1) / 2);
@@ -533,6 +845,8 @@ npp_status npp_batch_create(npp_handle* h, const npp_scene* scenes, int32_t S, n
     B->smem_optin = smem_optin;
     B->slices = 4;
     B->traj_warps = 8;
+    B->binned = 1;
+    B->total_items = items;
     cudaError_t e = cudaSuccess;
     auto A = [&](void** p, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(p, bytes > 0 ? bytes : 16); };
     A((void**)&B->d_scenes, sizeof(SceneDev) * S);
@@ -544,6 +858,11 @@ npp_status npp_batch_create(npp_handle* h, const npp_scene* scenes, int32_t S, n
     }
     A((void**)&B->d_pXY, sizeof(float4) * std::max(1LL, pairs));
     A((void**)&B->d_pV, sizeof(float4) * std::max(1LL, pairs));
+    A((void**)&B->d_tileP, sizeof(float4) * std::max(1LL, tiles_total));
+    A((void**)&B->d_tileV, sizeof(float4) * std::max(1LL, tiles_total));
+    A((void**)&B->d_bin_cs, sizeof(int) * std::max(1LL, bin_ints));
+    A((void**)&B->d_bin_pts, sizeof(float2) * std::max(1LL, bin_pts));
+    A((void**)&B->d_bstep_prefix, sizeof(long long) * (S + 1));
     A((void**)&B->d_coefA, sizeof(float4) * rows);
     A((void**)&B->d_coefB, sizeof(float2) * rows);
     A((void**)&B->d_jfree, sizeof(float) * samples);
@@ -612,6 +931,14 @@ npp_status npp_plan_batch(npp_batch* B, const float* obs_dev, const npp_batch_ou
     b.obs = reinterpret_cast<const float4*>(obs_dev);
     b.pXY = B->d_pXY;
     b.pV = B->d_pV;
+    b.tileP = B->d_tileP;
+    b.tileV = B->d_tileV;
+    b.reach = (float)(std::sqrt((double)h->cfg.half_len * h->cfg.half_len + (double)h->cfg.half_wid * h->cfg.half_wid)
+                      + std::fabs((double)h->cfg.c_off) + 0.1);
+    b.grid = make_bin_grid(h->cfg.half_len, h->cfg.half_wid, h->cfg.c_off);
+    b.bin_cs = B->d_bin_cs;
+    b.bin_pts = B->d_bin_pts;
+    b.bstep_prefix = B->d_bstep_prefix;
     b.coefA = B->d_coefA;
     b.coefB = B->d_coefB;
     b.jfree = B->d_jfree;
@@ -635,17 +962,28 @@ npp_status npp_plan_batch(npp_batch* B, const float* obs_dev, const npp_batch_ou
     CUDA_TRY(h, cudaMemsetAsync(B->d_keys, 0xff, sizeof(unsigned long long) * B->S, s));
     CUDA_TRY(h, cudaMemsetAsync(B->d_counters, 0, 64, s));
     if (B->max_pairs > 0) {
-        dim3 grid((unsigned)std::min(64, (B->max_pairs + 255) / 256), (unsigned)B->S);
-        batch_prologue_kernel<<<grid, 256, 0, s>>>(b);
+        const int smem = SORT_KEYS * (int)sizeof(int);
+        CUDA_TRY(h, ensure_smem(batch_prologue_kernel, smem));
+        batch_prologue_kernel<<<B->S, SORT_THREADS, smem, s>>>(b);
         CUDA_TRY(h, cudaGetLastError());
     }
     if (B->traj_warps == 4) launch_batch_traj<4>(B, b, s); else launch_batch_traj<8>(B, b, s);
     CUDA_TRY(h, cudaGetLastError());
     if (h->timing) CUDA_TRY(h, record_event(h->ev[1], s));
-    switch (B->slices) {
-    case 2: launch_batch_collide<2>(B, b, s); break;
-    case 8: launch_batch_collide<8>(B, b, s); break;
-    default: launch_batch_collide<4>(B, b, s); break;
+    if (B->binned) {
+        if (B->bin_blocks > 0) {
+            const int smem = BIN_NCELL * (int)sizeof(int);
+            CUDA_TRY(h, ensure_smem(batch_bin_build_kernel, smem));
+            batch_bin_build_kernel<<<(unsigned)B->bin_blocks, 1024, smem, s>>>(b);
+            CUDA_TRY(h, cudaGetLastError());
+        }
+        batch_binned_kernel<<<(unsigned)B->total_items, 256, 0, s>>>(b);
+    } else {
+        switch (B->slices) {
+        case 2: launch_batch_collide<2>(B, b, s); break;
+        case 8: launch_batch_collide<8>(B, b, s); break;
+        default: launch_batch_collide<4>(B, b, s); break;
+        }
     }
     CUDA_TRY(h, cudaGetLastError());
     if (h->timing) CUDA_TRY(h, record_event(h->ev[2], s));
@@ -664,6 +1002,9 @@ npp_status npp_batch_set_option(npp_batch* B, const char* name, int32_t value)
     } else if (std::strcmp(name, "traj_warps") == 0) {
         if (value != 4 && value != 8) return fail(B->h, NPP_INVALID_ARG, "traj_warps is 4 or 8");
         B->traj_warps = value;
+    } else if (std::strcmp(name, "collide") == 0) {
+        if (value != 0 && value != 1) return fail(B->h, NPP_INVALID_ARG, "collide is 0 or 1");
+        B->binned = value;
     } else {
         return fail(B->h, NPP_INVALID_ARG, "unknown batch option '%s'", name);
     }

@@ -25,67 +25,18 @@ namespace {
 
 constexpr int BIN_THREADS = 1024;
 
-// one block per horizon step: cell counts (shared), exclusive scan, scatter
+// one block per horizon step
 __global__ void __launch_bounds__(BIN_THREADS) bin_build_kernel(const RolloutArgs a, BinView g, int* __restrict__ cell_start,
                                                                 float2* __restrict__ binned)
 {
     extern __shared__ int cnt[];             // [BIN_NCELL]
+    __shared__ int run_tot[BIN_THREADS];
     const int h = blockIdx.x;
-    const int M = a.M;
-    const float tau = (float)h * a.c.Ts;
     const StepIn si = step_in(a);
     float s0, c0;
     sincosf(si.phi0, &s0, &c0);
-    for (int i = threadIdx.x; i < BIN_NCELL; i += blockDim.x) cnt[i] = 0;
-    __syncthreads();
-    for (int j = threadIdx.x; j < M; j += blockDim.x) {
-        float ex, ey, evx, evy;
-        ev_point(a.obs[j], si.x0, si.y0, s0, c0, ex, ey, evx, evy);
-        const float px = fmaf(tau, evx, ex), py = fmaf(tau, evy, ey);
-        atomicAdd(&cnt[bin_cell(py, g) * BIN_DIM + bin_cell(px, g)], 1);
-    }
-    __syncthreads();
-    // exclusive scan of the counts: each thread scans a contiguous run,
-    // then warp 0 scans the run totals
-    __shared__ int run_tot[BIN_THREADS];
-    constexpr int RUN = BIN_NCELL / BIN_THREADS;
-    const int base = threadIdx.x * RUN;
-    int acc = 0;
-    for (int k = 0; k < RUN; ++k) { const int v = cnt[base + k]; cnt[base + k] = acc; acc += v; }
-    run_tot[threadIdx.x] = acc;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        constexpr int PER = BIN_THREADS / 32;
-        int local = 0;
-        for (int k = 0; k < PER; ++k) local += run_tot[threadIdx.x * PER + k];
-        int incl = local;
-        for (int off = 1; off < 32; off <<= 1) {
-            const int v = __shfl_up_sync(FULL, incl, off);
-            if ((int)threadIdx.x >= off) incl += v;
-        }
-        int run = incl - local;
-        for (int k = 0; k < PER; ++k) {
-            const int v = run_tot[threadIdx.x * PER + k];
-            run_tot[threadIdx.x * PER + k] = run;
-            run += v;
-        }
-    }
-    __syncthreads();
-    for (int k = 0; k < RUN; ++k) cnt[base + k] += run_tot[threadIdx.x];
-    __syncthreads();
-    int* cs = cell_start + (size_t)h * BIN_CS_STRIDE;
-    for (int i = threadIdx.x; i < BIN_NCELL; i += blockDim.x) cs[i] = cnt[i];
-    if (threadIdx.x == 0) cs[BIN_NCELL] = M;
-    __syncthreads();
-    // scatter (order within a cell is arbitrary; the test is an OR)
-    float2* out = binned + (size_t)h * M;
-    for (int j = threadIdx.x; j < M; j += blockDim.x) {
-        float ex, ey, evx, evy;
-        ev_point(a.obs[j], si.x0, si.y0, s0, c0, ex, ey, evx, evy);
-        const float px = fmaf(tau, evx, ex), py = fmaf(tau, evy, ey);
-        const int pos = atomicAdd(&cnt[bin_cell(py, g) * BIN_DIM + bin_cell(px, g)], 1);
-        out[pos] = make_float2(px, py);
-    }
+    build_step_bins<BIN_THREADS>(a.obs, a.M, si.x0, si.y0, s0, c0, (float)h * a.c.Ts, g,
+                                 cell_start + (size_t)h * BIN_CS_STRIDE, binned + (size_t)h * a.M, cnt, run_tot);
 }
 
 // one warp per sample over the stored trajectories and inequality rows, h
@@ -170,12 +121,7 @@ size_t binned_workspace_bytes(int max_T, int max_M)
 // O(100) m), a grid of BIN_DIM^2 cells centred on the vehicle.
 cudaError_t build_bins(RolloutArgs& a, float half_len, float half_wid, float c_off, void* workspace, cudaStream_t s)
 {
-    const double R = std::sqrt((double)half_len * half_len + (double)half_wid * half_wid) + std::fabs((double)c_off);
-    const double cell = 2.0 * R + 0.25;
-    BinView g;
-    g.inv_cell = (float)(1.0 / cell);
-    g.x0 = (float)(-0.5 * BIN_DIM * cell);
-    g.reach = (float)(R + 0.05);
+    BinView g = make_bin_grid(half_len, half_wid, c_off);
     int* cell_start = static_cast<int*>(workspace);
     float2* binned = reinterpret_cast<float2*>(cell_start + (size_t)(a.T + 1) * BIN_CS_STRIDE);
     g.cell_start = cell_start;

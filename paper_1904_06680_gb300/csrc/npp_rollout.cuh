@@ -26,6 +26,7 @@
 #pragma once
 
 #include <cfloat>
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -189,6 +190,82 @@ __device__ __forceinline__ bool group_collides(const BinView& bv, int h, float x
         if (__all_sync(FULL, done)) break;
     }
     return hit;
+}
+
+// ------------------------------------------------------------------ bins
+// The grid of one horizon step (time tau) built by one block of THREADS
+// threads: counting sort of the extrapolated EV-frame points by cell (counts
+// in shared memory cnt[BIN_NCELL], exclusive scan, scatter).  Writes the
+// step's cell-start table cs[BIN_NCELL + 1] and the sorted points out[M].
+template <int THREADS>
+__device__ __forceinline__ void build_step_bins(const float4* __restrict__ obs, int M, float x0, float y0, float s0,
+                                                float c0, float tau, const BinView& g, int* __restrict__ cs,
+                                                float2* __restrict__ out, int* cnt, int* run_tot)
+{
+    for (int i = threadIdx.x; i < BIN_NCELL; i += THREADS) cnt[i] = 0;
+    __syncthreads();
+    for (int j = threadIdx.x; j < M; j += THREADS) {
+        float ex, ey, evx, evy;
+        ev_point(obs[j], x0, y0, s0, c0, ex, ey, evx, evy);
+        const float px = fmaf(tau, evx, ex), py = fmaf(tau, evy, ey);
+        atomicAdd(&cnt[bin_cell(py, g) * BIN_DIM + bin_cell(px, g)], 1);
+    }
+    __syncthreads();
+    // exclusive scan: each thread scans a contiguous run, then warp 0 scans
+    // the run totals
+    constexpr int RUN = BIN_NCELL / THREADS;
+    const int base = threadIdx.x * RUN;
+    int acc = 0;
+    for (int k = 0; k < RUN; ++k) { const int v = cnt[base + k]; cnt[base + k] = acc; acc += v; }
+    run_tot[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        constexpr int PER = THREADS / 32;
+        int local = 0;
+        for (int k = 0; k < PER; ++k) local += run_tot[threadIdx.x * PER + k];
+        int incl = local;
+        for (int off = 1; off < 32; off <<= 1) {
+            const int v = __shfl_up_sync(FULL, incl, off);
+            if ((int)threadIdx.x >= off) incl += v;
+        }
+        int run = incl - local;
+        for (int k = 0; k < PER; ++k) {
+            const int v = run_tot[threadIdx.x * PER + k];
+            run_tot[threadIdx.x * PER + k] = run;
+            run += v;
+        }
+    }
+    __syncthreads();
+    for (int k = 0; k < RUN; ++k) cnt[base + k] += run_tot[threadIdx.x];
+    __syncthreads();
+    for (int i = threadIdx.x; i < BIN_NCELL; i += THREADS) cs[i] = cnt[i];
+    if (threadIdx.x == 0) cs[BIN_NCELL] = M;
+    __syncthreads();
+    // scatter (order within a cell is arbitrary; the test is an OR)
+    for (int j = threadIdx.x; j < M; j += THREADS) {
+        float ex, ey, evx, evy;
+        ev_point(obs[j], x0, y0, s0, c0, ex, ey, evx, evy);
+        const float px = fmaf(tau, evx, ex), py = fmaf(tau, evy, ey);
+        const int pos = atomicAdd(&cnt[bin_cell(py, g) * BIN_DIM + bin_cell(px, g)], 1);
+        out[pos] = make_float2(px, py);
+    }
+}
+
+// A grid whose cell exceeds the diameter of the query disk: the rectangle's
+// circumradius plus |c_off|, plus a margin against rounding of positions of
+// O(100) m (host side).
+inline BinView make_bin_grid(float half_len, float half_wid, float c_off)
+{
+    const double R = std::sqrt((double)half_len * half_len + (double)half_wid * half_wid) + std::fabs((double)c_off);
+    const double cell = 2.0 * R + 0.25;
+    BinView g;
+    g.inv_cell = (float)(1.0 / cell);
+    g.x0 = (float)(-0.5 * BIN_DIM * cell);
+    g.reach = (float)(R + 0.05);
+    g.cell_start = nullptr;
+    g.pts = nullptr;
+    g.M = 0;
+    return g;
 }
 
 // ------------------------------------------------------------------ traj

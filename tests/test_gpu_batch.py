@@ -82,8 +82,9 @@ def test_batch_matches_single_plan_steps():
 
 
 def test_batch_options_and_graph_replay_identical():
-    """Every launch shape the autotuner may pick, and a CUDA-graph capture of
-    the batch replayed twice, give the same results."""
+    """Every collision check and launch shape the autotuner may pick (binned
+    and brute force), and a CUDA-graph capture of the batch replayed twice,
+    give the same results."""
     import torch
     from paper_1904_06680_gb300 import autotune, npp
     b = inputs.scene_batch(5, S=24, N_range=(64, 2048), M_range=(20, 3000), T_range=(5, 30))
@@ -107,15 +108,14 @@ def test_batch_options_and_graph_replay_identical():
     npp.npp_plan_batch(B, obs, out)
     ref = snap()
     assert 0 < int((ref[2] >= 0).sum()) < ref[2].numel()
-    for s, w in autotune.BATCH_CANDIDATES:
-        npp.npp_batch_set_option(B, "slices", s)
-        npp.npp_batch_set_option(B, "traj_warps", w)
+    for cand in autotune.BATCH_CANDIDATES:
+        autotune._set_batch(B, cand)
         for t in (best, costs, fh, params):
             t.zero_()
         npp.npp_plan_batch(B, obs, out)
         got = snap()
         for a, r in zip(got, ref):
-            assert torch.equal(a, r), (s, w)
+            assert torch.equal(a, r), cand
     choice, ms = autotune.tune_batch(B, obs, out, key="test24", reps=1)
     assert tuple(choice) in autotune.BATCH_CANDIDATES and len(ms) == len(autotune.BATCH_CANDIDATES)
     # capture in a CUDA graph on a side stream, replay twice
@@ -133,5 +133,7 @@ def test_batch_options_and_graph_replay_identical():
             assert torch.equal(a, r)
     with pytest.raises(npp.NppError):
         npp.npp_batch_set_option(B, "slices", 3)
+    with pytest.raises(npp.NppError):
+        npp.npp_batch_set_option(B, "collide", 2)
     npp.npp_batch_destroy(B)
     pl.close()

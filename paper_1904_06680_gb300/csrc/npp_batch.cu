@@ -319,6 +319,7 @@ __global__ void __launch_bounds__(NW * 32) batch_traj_kernel(const BatchArgs b, 
     constexpr int B = TrajKernel<W, G, NW>::B;
     __shared__ __align__(16) float hx_all[B * W];
     __shared__ long long qslot;
+    extern __shared__ float stage_all[];        // [LaneNet::SLOTS][NW * 32] when W == 32
     const int tid = threadIdx.x;
     const int bi = tid / G, gl = tid % G;
     const int n_sc = b.n_torder[wi];
@@ -339,6 +340,7 @@ __global__ void __launch_bounds__(NW * 32) batch_traj_kernel(const BatchArgs b, 
         job.warm = nullptr;
         job.prop = Proposal{ nullptr, nullptr, 0 };
         job.bins = nullptr;
+        job.stage = stage_all + tid;
         job.N = s.N;
         job.T = s.T;
         job.traj = nullptr;
@@ -349,7 +351,8 @@ __global__ void __launch_bounds__(NW * 32) batch_traj_kernel(const BatchArgs b, 
         job.coefB = b.coefB;
         job.coef_base = s.coef_off;
         job.jfree = b.jfree + s.samp_off;
-        traj_sample<W, G>(b.c, job, n, n < s.N, gl, hx_all + bi * W);
+        constexpr int STAGE_TH = W == 32 ? NW * 32 : 0;     // as traj_kernel
+        traj_sample<W, G, false, STAGE_TH>(b.c, job, n, n < s.N, gl, hx_all + bi * W);
     }
 }
 
@@ -554,6 +557,7 @@ __device__ void batch_reroll(const BatchArgs& b, const SceneDev& s, int idx, flo
     job.warm = nullptr;
     job.prop = Proposal{ nullptr, nullptr, 0 };
     job.bins = nullptr;
+    job.stage = nullptr;
     job.N = s.N;
     job.T = s.T;
     job.traj = b.trajectory ? reinterpret_cast<float4*>(b.trajectory) + s.traj_off : nullptr;
@@ -732,13 +736,19 @@ cudaError_t collide_grid(npp_batch* B, int* grid)
     return e;
 }
 
+template <int W, int G>
+constexpr int batch_stage_bytes(int nw) { return W == 32 ? LaneNet<W, G>::SLOTS * nw * 32 * (int)sizeof(float) : 0; }
+
 template <int NW>
 void traj_grids(npp_batch* B)
 {
     int nt = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nt, batch_traj_kernel<16, 8, NW>, NW * 32, 0);
+    const int s16 = batch_stage_bytes<16, 8>(NW), s32 = batch_stage_bytes<32, 16>(NW);
+    ensure_smem(batch_traj_kernel<16, 8, NW>, s16);
+    ensure_smem(batch_traj_kernel<32, 16, NW>, s32);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nt, batch_traj_kernel<16, 8, NW>, NW * 32, s16);
     B->grid_traj[0] = B->h->sm_count * std::max(1, nt);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nt, batch_traj_kernel<32, 16, NW>, NW * 32, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nt, batch_traj_kernel<32, 16, NW>, NW * 32, s32);
     B->grid_traj[1] = B->h->sm_count * std::max(1, nt);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nt, batch_traj_kernel<64, 32, NW>, NW * 32, 0);
     B->grid_traj[2] = B->h->sm_count * std::max(1, nt);
@@ -793,8 +803,14 @@ void launch_batch_collide(npp_batch* B, const BatchArgs& b, cudaStream_t s)
 template <int NW>
 void launch_batch_traj(npp_batch* B, const BatchArgs& b, cudaStream_t s)
 {
-    if (B->n_torder[0]) batch_traj_kernel<16, 8, NW><<<B->grid_traj[0], NW * 32, 0, s>>>(b, 0);
-    if (B->n_torder[1]) batch_traj_kernel<32, 16, NW><<<B->grid_traj[1], NW * 32, 0, s>>>(b, 1);
+    if (B->n_torder[0]) {
+        ensure_smem(batch_traj_kernel<16, 8, NW>, batch_stage_bytes<16, 8>(NW));
+        batch_traj_kernel<16, 8, NW><<<B->grid_traj[0], NW * 32, batch_stage_bytes<16, 8>(NW), s>>>(b, 0);
+    }
+    if (B->n_torder[1]) {
+        ensure_smem(batch_traj_kernel<32, 16, NW>, batch_stage_bytes<32, 16>(NW));
+        batch_traj_kernel<32, 16, NW><<<B->grid_traj[1], NW * 32, batch_stage_bytes<32, 16>(NW), s>>>(b, 1);
+    }
     if (B->n_torder[2]) batch_traj_kernel<64, 32, NW><<<B->grid_traj[2], NW * 32, 0, s>>>(b, 2);
 }
 

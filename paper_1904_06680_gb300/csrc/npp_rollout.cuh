@@ -107,6 +107,59 @@ struct LaneNet {
         const float2 pb3 = src.pair(S::OFF_B3);
         b3[0] = pb3.x; b3[1] = pb3.y;
     }
+
+    // Parameters generated by a rolled loop into this lane's slots of a
+    // shared staging area (slot k of the lane at st[k * TH]), then loaded
+    // into registers: the same values as load(), with one copy of the
+    // sampler's code instead of one per parameter quad.
+    static constexpr int QW1 = NIN / 4, QW2 = W / 4, QPU = QW1 + QW2;
+    static constexpr int NQUAD = U * QPU;                  // quads: W1 and W2 rows of the lane's units
+    static constexpr int NPAIR = 2 * U + 1;                // pairs: b1, b2, W3 rows (per unit pair), b3
+    static constexpr int SLOTS = 4 * NQUAD + 2 * NPAIR;
+
+    template <int TH>
+    __device__ __forceinline__ void load_staged(const ThetaSrc& src, int gl, float* st) {
+#pragma unroll 1
+        for (int it = 0; it < NQUAD; ++it) {
+            const int j = it / QPU, q = it - j * QPU;
+            const int u = gl * U + j;
+            const int pidx = q < QW1 ? u * NIN + 4 * q : S::OFF_W2 + u * W + 4 * (q - QW1);
+            const float4 v = src.quad(pidx);
+            st[(4 * it + 0) * TH] = v.x;
+            st[(4 * it + 1) * TH] = v.y;
+            st[(4 * it + 2) * TH] = v.z;
+            st[(4 * it + 3) * TH] = v.w;
+        }
+#pragma unroll 1
+        for (int pj = 0; pj < NPAIR; ++pj) {
+            int pidx = S::OFF_B3;
+            if (pj < 2 * U) {
+                const int jj = gl * U + (pj >> 2) * 2, kind = pj & 3;
+                pidx = kind == 0 ? S::OFF_B1 + jj : kind == 1 ? S::OFF_B2 + jj
+                     : kind == 2 ? S::OFF_W3 + jj : S::OFF_W3 + W + jj;
+            }
+            const float2 v = src.pair(pidx);
+            st[(4 * NQUAD + 2 * pj + 0) * TH] = v.x;
+            st[(4 * NQUAD + 2 * pj + 1) * TH] = v.y;
+        }
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+#pragma unroll
+            for (int i = 0; i < NIN; ++i) w1[j][i] = st[(4 * (j * QPU + i / 4) + i % 4) * TH];
+#pragma unroll
+            for (int i = 0; i < W; ++i) w2[j][i] = st[(4 * (j * QPU + QW1 + i / 4) + i % 4) * TH];
+        }
+#pragma unroll
+        for (int j = 0; j < U; j += 2) {
+            const int p0 = 4 * NQUAD + 2 * ((j >> 1) * 4);
+            b1[j] = st[(p0 + 0) * TH]; b1[j + 1] = st[(p0 + 1) * TH];
+            b2[j] = st[(p0 + 2) * TH]; b2[j + 1] = st[(p0 + 3) * TH];
+            w3[0][j] = st[(p0 + 4) * TH]; w3[0][j + 1] = st[(p0 + 5) * TH];
+            w3[1][j] = st[(p0 + 6) * TH]; w3[1][j + 1] = st[(p0 + 7) * TH];
+        }
+        b3[0] = st[(4 * NQUAD + 2 * (2 * U)) * TH];
+        b3[1] = st[(4 * NQUAD + 2 * (2 * U) + 1) * TH];
+    }
 };
 
 __device__ __forceinline__ float wrap_pi(float a)
@@ -294,6 +347,7 @@ struct TrajJob {
     long long coef_base;
     float* jfree;
     const BinView* bins;          // fused check (traj_sample<.., true>)
+    float* stage;                 // this thread's slot 0 of a staging area (stride stage_th), or null
 };
 
 // Result of a fused rollout, uniform over the sample's group: the first
@@ -308,7 +362,7 @@ struct FusedOut {
 // every state h is checked against the binned points at the top of its step
 // (before the controls that leave it) and the loop ends once every group of
 // the warp has collided; nothing is stored.
-template <int W, int G, bool FUSED = false>
+template <int W, int G, bool FUSED = false, int STAGE_TH = 0>
 __device__ __forceinline__ FusedOut traj_sample(const DevCfg& c, const TrajJob& job, int n, bool valid,
                                                 int gl, float* hrow)
 {
@@ -330,7 +384,8 @@ __device__ __forceinline__ FusedOut traj_sample(const DevCfg& c, const TrajJob& 
         src.mem = nullptr;
         if (job.theta) src.mem = job.theta + (size_t)(valid ? n : 0) * S::NT;
         else if (job.warm && n == 0 && si.warm_ok) src.mem = job.warm;
-        net.load(src, gl);
+        if constexpr (STAGE_TH > 0) net.template load_staged<STAGE_TH>(src, gl, job.stage);
+        else net.load(src, gl);
     }
 
     float x = 0.f, y = 0.f, ph = 0.f, v = si.v0, ap0 = si.ap0, ap1 = si.ap1, E = 0.f;
@@ -492,6 +547,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) traj_kernel(const RolloutArgs a
 {
     constexpr int B = TrajKernel<W, G, NW>::B;
     __shared__ __align__(16) float hx_all[B * W];
+    extern __shared__ float stage_all[];        // [LaneNet::SLOTS][NW * 32] when W == 32
     const int tid = threadIdx.x;
     const int b = tid / G, gl = tid % G;
     const int n = blockIdx.x * B + b;
@@ -513,7 +569,11 @@ __global__ void __launch_bounds__(NW * 32, MINB) traj_kernel(const RolloutArgs a
     job.coef_base = 0;
     job.jfree = a.jfree;
     job.bins = nullptr;
-    traj_sample<W, G>(a.c, job, n, n < a.N, gl, hx_all + b * W);
+    job.stage = stage_all + tid;
+    // staged parameter generation pays at W = 32 (measured on GB300: 11 %
+    // faster at T = 40); at W = 16 and 64 the direct load is faster
+    constexpr int STAGE_TH = W == 32 ? NW * 32 : 0;
+    traj_sample<W, G, false, STAGE_TH>(a.c, job, n, n < a.N, gl, hx_all + b * W);
 }
 
 // Trajectories with the binned check fused in: per sample its first
@@ -545,6 +605,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) fused_kernel(const RolloutArgs 
     job.coef_base = 0;
     job.jfree = nullptr;
     job.bins = &a.bins;
+    job.stage = nullptr;
     const bool valid = n < a.N;
     const FusedOut r = traj_sample<W, G, true>(a.c, job, n, valid, gl, hx_all + b * W);
     unsigned long long key = ~0ull;
@@ -616,6 +677,7 @@ __global__ void __launch_bounds__(32) reroll_epilogue_kernel(const RolloutArgs a
     job.coef_base = 0;
     job.jfree = nullptr;
     job.bins = nullptr;
+    job.stage = nullptr;
     if (e.trajectory || e.controls) traj_sample<W, G>(a.c, job, idx, true, lane % G, hrows + (lane / G) * W);
     __syncwarp();
     float s0, c0;
@@ -1181,7 +1243,10 @@ cudaError_t launch_traj(const RolloutArgs& a, cudaStream_t stream)
 {
     using K = TrajKernel<W, G, NW>;
     const int grid = (a.N + K::B - 1) / K::B;
-    traj_kernel<W, G, NW, MINB><<<grid, K::THREADS, 0, stream>>>(a);
+    const int smem = W == 32 ? LaneNet<W, G>::SLOTS * K::THREADS * (int)sizeof(float) : 0;
+    cudaError_t e = ensure_smem(traj_kernel<W, G, NW, MINB>, smem);
+    if (e != cudaSuccess) return e;
+    traj_kernel<W, G, NW, MINB><<<grid, K::THREADS, smem, stream>>>(a);
     return cudaGetLastError();
 }
 

@@ -157,6 +157,22 @@ npp_status npp_plan_step_host(npp_handle* h, const npp_state* state, const npp_g
                               uint64_t seed, uint32_t t_index, const float* warm_host,
                               const npp_outputs* out_host);
 
+/* The sampling loop of the paper's hill climb (TSHC, Sect. II-D "Fourth"-
+ * "Sixth": a restart perturbs the current best parameters by sigma_pert
+ * times normal noise) run on the device: round 0 is npp_plan_step; round
+ * r = 1 .. n_restarts-1 keeps the best so far as sample 0 and draws the other
+ * samples as theta_best + sigma_pert eps with eps the normals of Philox
+ * stream r (same counter layout), so the best cost never increases.  The
+ * paper leaves the update of sigma_pert to its cited work; here it is fixed
+ * per call.  out->params must be a device buffer of n_theta floats (it holds
+ * the running best); the outputs describe the final round (its winner is the
+ * best of all rounds).  NPP_INVALID_ARG for n_restarts < 1 or sigma_pert not
+ * finite and positive, otherwise as npp_plan_step. */
+npp_status npp_plan_tshc(npp_handle* h, const npp_state* state, const npp_goal* goal,
+                         const float* obs_dev, int32_t M, int32_t N, int32_t T, uint64_t seed,
+                         uint32_t t_index, const float* warm_dev, int32_t n_restarts, float sigma_pert,
+                         const npp_outputs* out, void* stream);
+
 /* Roll out K explicit parameter vectors theta_dev[K][n_theta] (no sampling,
  * no selection): writes costs[K], first_hit[K] and, when non-NULL, every
  * rollout's states sample_traj[T+1][K][4] and controls sample_ctrl[T][K][2]

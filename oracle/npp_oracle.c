@@ -426,19 +426,20 @@ static void sample_theta(const orc_config* c, uint64_t seed, uint32_t t_index,
 
 /* Sample n of a plan step with a sampling proposal (mean mu, standard
  * deviation sigma, both FP32): samples n < n_prop are mu + sigma * eps with
- * eps the normals of stream 1, rounded once to FP32 (a fused multiply-add,
+ * eps the normals of stream prop_stream (1 for the learned proposal, r for
+ * restart round r of the hill climb), rounded once to FP32 (a fused multiply-add,
  * C99 fmaf, correctly rounded); the others are the isotropic samples of the
  * given stream.  With n_prop = 0 this is sample_theta. */
 static void sample_theta_mixed(const orc_config* c, uint64_t seed, uint32_t t_index,
                                uint32_t stream, uint32_t n, const float* mu, const float* sigma,
-                               int n_prop, double* theta, float* tmp)
+                               int n_prop, uint32_t prop_stream, double* theta, float* tmp)
 {
     if ((int64_t)n >= (int64_t)n_prop || !mu || !sigma) {
         sample_theta(c, seed, t_index, stream, n, theta, tmp);
         return;
     }
     int nt = orc_n_theta(c);
-    orc_theta(seed, t_index, 1u, n, nt, tmp);
+    orc_theta(seed, t_index, prop_stream, n, nt, tmp);
     for (int i = 0; i < nt; ++i) theta[i] = (double)fmaf(sigma[i], tmp[i], mu[i]);
 }
 
@@ -467,19 +468,19 @@ void orc_rollout_theta(const orc_config* c, const double* theta, int K,
 /* theta_n of a plan step with a proposal (FP32 values, see
  * sample_theta_mixed) */
 void orc_theta_mixed(uint64_t seed, uint32_t t_index, uint32_t n, int n_theta, const float* mu,
-                     const float* sigma, int n_prop, float* out)
+                     const float* sigma, int n_prop, uint32_t prop_stream, float* out)
 {
     if ((int64_t)n >= (int64_t)n_prop || !mu || !sigma) {
         orc_theta(seed, t_index, 0u, n, n_theta, out);
         return;
     }
-    orc_theta(seed, t_index, 1u, n, n_theta, out);
+    orc_theta(seed, t_index, prop_stream, n, n_theta, out);
     for (int i = 0; i < n_theta; ++i) out[i] = fmaf(sigma[i], out[i], mu[i]);
 }
 
 void orc_rollout_samples(const orc_config* c, uint64_t seed, uint32_t t_index,
                          uint32_t stream, const int32_t* idx, int K, const double* warm,
-                         const float* mu, const float* sigma, int n_prop,
+                         const float* mu, const float* sigma, int n_prop, uint32_t prop_stream,
                          const double z0[4], const double ap0[2], const double* goal_ev,
                          const double* obs_ev, int M, int T, int n_threads,
                          double* cost, int32_t* first_hit, double* traj, double* ctrl)
@@ -498,7 +499,7 @@ void orc_rollout_samples(const orc_config* c, uint64_t seed, uint32_t t_index,
         for (int k = 0; k < K; ++k) {
             if (warm && idx[k] == 0) memcpy(theta, warm, sizeof(double) * nt);
             else sample_theta_mixed(c, seed, t_index, stream, (uint32_t)idx[k], mu, sigma, n_prop,
-                                    theta, tmp);
+                                    prop_stream, theta, tmp);
             first_hit[k] = rollout(c, theta, z0, ap0, goal_ev, obs_ev, M, T, cost + k,
                                    traj ? traj + (size_t)k * (T + 1) * 4 : NULL,
                                    ctrl ? ctrl + (size_t)k * T * 2 : NULL);
@@ -519,7 +520,7 @@ void orc_rollout_samples(const orc_config* c, uint64_t seed, uint32_t t_index,
 int orc_plan(const orc_config* c, const double* state_w, const double* goal_w,
              const double* obs_w, int M, int N, int T, uint64_t seed,
              uint32_t t_index, const double* warm, const float* mu, const float* sigma,
-             int n_prop, int n_threads,
+             int n_prop, uint32_t prop_stream, int n_threads,
              double* costs, int32_t* first_hit, int32_t* best_idx, int32_t* status,
              double* best_cost, double* best_theta, double* controls, double* traj_w)
 {
@@ -534,8 +535,8 @@ int orc_plan(const orc_config* c, const double* state_w, const double* goal_w,
     double* cst = (double*)malloc(sizeof(double) * N);
     int32_t* fh = (int32_t*)malloc(sizeof(int32_t) * N);
     for (int n = 0; n < N; ++n) idx[n] = n;
-    orc_rollout_samples(c, seed, t_index, 0u, idx, N, warm, mu, sigma, n_prop, z0, ap0, goal_ev,
-                        obs_ev, M, T, n_threads, cst, fh, NULL, NULL);
+    orc_rollout_samples(c, seed, t_index, 0u, idx, N, warm, mu, sigma, n_prop, prop_stream, z0, ap0,
+                        goal_ev, obs_ev, M, T, n_threads, cst, fh, NULL, NULL);
     /* argmin over collision-free samples, lowest index on ties */
     int best = -1;
     for (int n = 0; n < N; ++n)
@@ -555,7 +556,7 @@ int orc_plan(const orc_config* c, const double* state_w, const double* goal_w,
     double* theta = (double*)malloc(sizeof(double) * nt);
     float* tmp = (float*)malloc(sizeof(float) * (nt + 4));
     if (warm && best == 0) memcpy(theta, warm, sizeof(double) * nt);
-    else sample_theta_mixed(c, seed, t_index, 0u, (uint32_t)best, mu, sigma, n_prop, theta, tmp);
+    else sample_theta_mixed(c, seed, t_index, 0u, (uint32_t)best, mu, sigma, n_prop, prop_stream, theta, tmp);
     if (best_theta) memcpy(best_theta, theta, sizeof(double) * nt);
     double* traj_ev = (double*)malloc(sizeof(double) * 4 * (T + 1));
     double dummy;

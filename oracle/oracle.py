@@ -70,16 +70,16 @@ def lib():
         L.orc_rollout_theta.argtypes = [_P, _D, C.c_int, _D, _D, _D, _D, C.c_int, C.c_int,
                                         C.c_int, _D, _I, C.c_void_p, C.c_void_p]
         L.orc_rollout_samples.argtypes = [_P, C.c_uint64, C.c_uint32, C.c_uint32, _I, C.c_int,
-                                          C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                          C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_uint32,
                                           _D, _D, _D, _D, C.c_int, C.c_int, C.c_int,
                                           _D, _I, C.c_void_p, C.c_void_p]
         L.orc_plan.argtypes = [_P, _D, _D, _D, C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_uint32,
-                               C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, _D, _I,
+                               C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_uint32, C.c_int, _D, _I,
                                C.POINTER(C.c_int32),
                                C.POINTER(C.c_int32), C.POINTER(C.c_double), _D, _D, _D]
         L.orc_plan.restype = C.c_int
         L.orc_theta_mixed.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_int, C.c_void_p, C.c_void_p,
-                                      C.c_int, _F]
+                                      C.c_int, C.c_uint32, _F]
         _lib = L
     return _lib
 
@@ -133,12 +133,12 @@ def theta(seed, t_index, n, n_theta, stream=0):
     return out
 
 
-def theta_mixed(seed, t_index, n, n_theta, mu, sigma, n_prop):
+def theta_mixed(seed, t_index, n, n_theta, mu, sigma, n_prop, prop_stream=1):
     """FP32 parameters of sample n of a plan step with a proposal."""
     out = np.zeros(n_theta, np.float32)
     mu32, sg32 = _f32(mu), _f32(sigma)
     lib().orc_theta_mixed(int(seed), int(t_index), int(n), int(n_theta), _ptr(mu32), _ptr(sg32),
-                          int(n_prop), out)
+                          int(n_prop), int(prop_stream), out)
     return out
 
 
@@ -221,7 +221,7 @@ def rollout_theta(p, thetas, z0, ap0, goal_ev, obs_ev, T, n_threads=0, record=Tr
 
 
 def rollout_samples(p, seed, t_index, idx, z0, ap0, goal_ev, obs_ev, T, warm=None,
-                    stream=0, n_threads=0, record=True, mu=None, sigma=None, n_prop=0):
+                    stream=0, n_threads=0, record=True, mu=None, sigma=None, n_prop=0, prop_stream=1):
     """Rollouts of the sampled parameter vectors idx; with a proposal (mu,
     sigma FP32 arrays of n_theta) samples idx < n_prop are mu + sigma*eps."""
     c = make_config(p)
@@ -236,7 +236,7 @@ def rollout_samples(p, seed, t_index, idx, z0, ap0, goal_ev, obs_ev, T, warm=Non
     w = None if warm is None else _d(warm)
     mu32, sg32 = _f32(mu), _f32(sigma)
     lib().orc_rollout_samples(C.byref(c), int(seed), int(t_index), int(stream), idx, K, _ptr(w),
-                              _ptr(mu32), _ptr(sg32), int(n_prop),
+                              _ptr(mu32), _ptr(sg32), int(n_prop), int(prop_stream),
                               _d(z0, 4), _d(ap0, 2), _d(goal_ev, 4),
                               obs_ev if M else np.zeros((1, 4)), M, T, n_threads, cost, fh,
                               _ptr(traj), _ptr(ctrl))
@@ -244,7 +244,7 @@ def rollout_samples(p, seed, t_index, idx, z0, ap0, goal_ev, obs_ev, T, warm=Non
 
 
 def plan(p, state_w, goal_w, obs_w, N, T, seed, t_index, warm=None, n_threads=0, mu=None,
-         sigma=None, n_prop=0):
+         sigma=None, n_prop=0, prop_stream=1):
     c = make_config(p)
     nt = lib().orc_n_theta(C.byref(c))
     obs_w = _d(obs_w).reshape(-1, 4)
@@ -258,9 +258,28 @@ def plan(p, state_w, goal_w, obs_w, N, T, seed, t_index, warm=None, n_threads=0,
     w = None if warm is None else _d(warm, nt)
     rc = lib().orc_plan(C.byref(c), _d(state_w, 6), _d(goal_w, 4),
                         obs_w if M else np.zeros((1, 4)), M, N, T, int(seed), int(t_index),
-                        _ptr(w), _ptr(_f32(mu)), _ptr(_f32(sigma)), int(n_prop), n_threads, costs, fh, C.byref(bi), C.byref(st), C.byref(bc),
+                        _ptr(w), _ptr(_f32(mu)), _ptr(_f32(sigma)), int(n_prop), int(prop_stream), n_threads,
+                        costs, fh, C.byref(bi), C.byref(st), C.byref(bc),
                         bt, ctrl, traj)
     if rc == 1:
         raise ValueError("invalid plan arguments")
     return dict(costs=costs, first_hit=fh, best_idx=bi.value, status=st.value,
                 best_cost=bc.value, best_theta=bt, controls=ctrl, traj=traj)
+
+
+def plan_tshc(p, state_w, goal_w, obs_w, N, T, seed, t_index, n_restarts, sigma_pert, warm=None, n_threads=0):
+    """The hill climb's sampling loop (Sect. II-D): round 0 is `plan`; round
+    r >= 1 keeps the best so far as sample 0 and draws the others as
+    theta_best + sigma_pert eps (normals of Philox stream r).  Returns the
+    final round's result and the best cost after every round."""
+    nt = n_theta(p)
+    r = plan(p, state_w, goal_w, obs_w, N, T, seed, t_index, warm=warm, n_threads=n_threads)
+    history = [r["best_cost"]]
+    sig = np.full(nt, np.float32(sigma_pert), np.float32)
+    for k in range(1, n_restarts):
+        best = r["best_theta"].astype(np.float32)
+        r = plan(p, state_w, goal_w, obs_w, N, T, seed, t_index, warm=best.astype(np.float64),
+                 n_threads=n_threads, mu=best, sigma=sig, n_prop=N, prop_stream=k)
+        history.append(r["best_cost"])
+    r["history"] = history
+    return r

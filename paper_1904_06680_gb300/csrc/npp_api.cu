@@ -365,6 +365,7 @@ npp_status npp_create(npp_handle** out, const npp_config* cfg, int32_t device)
     }
     A((void**)&h->d_obs, (size_t)cfg->max_M * sizeof(float4));
     A((void**)&h->d_warm, (size_t)h->n_theta * sizeof(float));
+    A((void**)&h->d_sigma, (size_t)h->n_theta * sizeof(float));
     A((void**)&h->d_best, sizeof(npp_best));
     A((void**)&h->d_params, (size_t)h->n_theta * sizeof(float));
     A((void**)&h->d_controls, (size_t)cfg->max_T * 2 * sizeof(float));
@@ -389,7 +390,7 @@ npp_status npp_destroy(npp_handle* h)
     if (h->stream) cudaStreamSynchronize(h->stream);
     void* ptrs[] = { h->d_key, h->d_traj, h->d_ctrl, h->d_jfree, h->d_coefA, h->d_coefB, h->d_work,
                      h->d_pXY, h->d_pV, h->d_bins,
-                     h->d_obs, h->d_warm, h->d_best, h->d_params, h->d_controls, h->d_trajectory,
+                     h->d_obs, h->d_warm, h->d_sigma, h->d_best, h->d_params, h->d_controls, h->d_trajectory,
                      h->d_costs, h->d_fh };
     for (void* p : ptrs) if (p) cudaFree(p);
     if (h->stream) cudaStreamDestroy(h->stream);
@@ -452,7 +453,7 @@ npp_status npp_plan_step(npp_handle* h, const npp_state* state, const npp_goal* 
 {
     if (!h) return fail(nullptr, NPP_INVALID_ARG, "handle is NULL");
     return plan_step_impl(h, state, goal, obs_dev, M, N, T, seed, t_index, warm_dev,
-                          Proposal{ nullptr, nullptr, 0 }, out, stream);
+                          Proposal{ nullptr, nullptr, 0, 1u }, out, stream);
 }
 
 npp_status npp_plan_step_proposal(npp_handle* h, const npp_state* state, const npp_goal* goal,
@@ -466,7 +467,33 @@ npp_status npp_plan_step_proposal(npp_handle* h, const npp_state* state, const n
     if (N_prop > 0 && (!mean_dev || !std_dev))
         return fail(h, NPP_INVALID_ARG, "mean and std must not be NULL with N_prop > 0");
     return plan_step_impl(h, state, goal, obs_dev, M, N, T, seed, t_index, warm_dev,
-                          Proposal{ N_prop > 0 ? mean_dev : nullptr, std_dev, N_prop }, out, stream);
+                          Proposal{ N_prop > 0 ? mean_dev : nullptr, std_dev, N_prop, 1u }, out, stream);
+}
+
+__global__ void fill_kernel(float* p, int n, float v)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = v;
+}
+
+npp_status npp_plan_tshc(npp_handle* h, const npp_state* state, const npp_goal* goal, const float* obs_dev,
+                         int32_t M, int32_t N, int32_t T, uint64_t seed, uint32_t t_index, const float* warm_dev,
+                         int32_t n_restarts, float sigma_pert, const npp_outputs* out, void* stream)
+{
+    if (!h) return fail(nullptr, NPP_INVALID_ARG, "handle is NULL");
+    if (n_restarts < 1) return fail(h, NPP_INVALID_ARG, "n_restarts=%d must be >= 1", n_restarts);
+    if (!(sigma_pert > 0.0f) || !std::isfinite(sigma_pert))
+        return fail(h, NPP_INVALID_ARG, "sigma_pert must be finite and > 0");
+    if (!out || !out->params) return fail(h, NPP_INVALID_ARG, "outputs.params must not be NULL (the running best)");
+    npp_status st = plan_step_impl(h, state, goal, obs_dev, M, N, T, seed, t_index, warm_dev,
+                                   Proposal{ nullptr, nullptr, 0, 1u }, out, stream);
+    if (st != NPP_OK || n_restarts == 1) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    fill_kernel<<<(h->n_theta + 255) / 256, 256, 0, s>>>(h->d_sigma, h->n_theta, sigma_pert);
+    CUDA_TRY(h, cudaGetLastError());
+    for (int r = 1; r < n_restarts && st == NPP_OK; ++r)
+        st = plan_step_impl(h, state, goal, obs_dev, M, N, T, seed, t_index, out->params,
+                            Proposal{ out->params, h->d_sigma, N, (uint32_t)r }, out, stream);
+    return st;
 }
 
 npp_status npp_plan_step_host(npp_handle* h, const npp_state* state, const npp_goal* goal,

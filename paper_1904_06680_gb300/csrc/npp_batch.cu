@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(NW * 32) batch_traj_kernel(const BatchArgs b, 
         job.key.k0 = s.k0; job.key.k1 = s.k1; job.key.t_index = s.t_index; job.key.stream_id = 0u;
         job.theta = nullptr;
         job.warm = nullptr;
-        job.prop = Proposal{ nullptr, nullptr, 0 };
+        job.prop = Proposal{ nullptr, nullptr, 0, 1u };
         job.bins = nullptr;
         job.stage = stage_all + tid;
         job.N = s.N;
@@ -555,7 +555,7 @@ __device__ void batch_reroll(const BatchArgs& b, const SceneDev& s, int idx, flo
     job.key.k0 = s.k0; job.key.k1 = s.k1; job.key.t_index = s.t_index; job.key.stream_id = 0u;
     job.theta = nullptr;
     job.warm = nullptr;
-    job.prop = Proposal{ nullptr, nullptr, 0 };
+    job.prop = Proposal{ nullptr, nullptr, 0, 1u };
     job.bins = nullptr;
     job.stage = nullptr;
     job.N = s.N;

@@ -120,13 +120,15 @@ __device__ __forceinline__ float2 sample_pair(const SamplerKey& key, uint32_t i,
 }
 
 // Gaussian sampling proposal of a plan step: samples n < n_prop take
-// theta_i = fma(sigma_i, eps_i, mu_i) with eps the normals of stream 1 (one
-// rounding to FP32); the others are the isotropic samples.  mu and sigma
-// hold n_theta FP32 values.
+// theta_i = fma(sigma_i, eps_i, mu_i) with eps the normals of stream
+// `stream` (1 for the learned proposal; the restart rounds of the hill
+// climb use 1, 2, ...) rounded once to FP32; the others are the isotropic
+// samples.  mu and sigma hold n_theta FP32 values.
 struct Proposal {
     const float* mu;
     const float* sigma;
     int n_prop;
+    uint32_t stream;      // Philox stream of the proposal's normals (1 unless set)
 };
 
 __device__ __forceinline__ bool proposal_sample(const Proposal& p, uint32_t n)
@@ -141,7 +143,7 @@ __device__ __forceinline__ float4 sample_quad_mixed(const SamplerKey& key, const
 {
     if (!proposal_sample(p, n)) return sample_quad(key, q, n);
     SamplerKey k1 = key;
-    k1.stream_id = 1u;
+    k1.stream_id = p.stream;
     const float4 e = sample_quad(k1, q, n);
     const int i = 4 * (int)q;
     return make_float4(fmaf(p.sigma[i], e.x, p.mu[i]), fmaf(p.sigma[i + 1], e.y, p.mu[i + 1]),
@@ -154,7 +156,7 @@ __device__ __forceinline__ float2 sample_pair_mixed(const SamplerKey& key, const
 {
     if (!proposal_sample(p, n)) return sample_pair(key, i, n);
     SamplerKey k1 = key;
-    k1.stream_id = 1u;
+    k1.stream_id = p.stream;
     const float2 e = sample_pair(k1, i, n);
     return make_float2(fmaf(p.sigma[i], e.x, p.mu[i]), fmaf(p.sigma[i + 1], e.y, p.mu[i + 1]));
 }
@@ -179,7 +181,7 @@ __device__ __forceinline__ float4 sample_quad_mixed_tail(const SamplerKey& key, 
 {
     if (4 * (int)q + 3 < n_theta || !proposal_sample(p, n)) return sample_quad_mixed(key, p, q, n);
     SamplerKey k1 = key;
-    k1.stream_id = 1u;
+    k1.stream_id = p.stream;
     const float4 e = sample_quad(k1, q, n);
     const float ev[4] = { e.x, e.y, e.z, e.w };
     float r[4] = { 0.f, 0.f, 0.f, 0.f };

@@ -42,6 +42,7 @@ struct npp_handle {
     // host-mode staging
     float4* d_obs;
     float* d_warm;
+    float* d_sigma;                      // restart perturbation scale, [n_theta]
     npp_best* d_best;
     float* d_params;
     float* d_controls;

@@ -82,7 +82,7 @@ EXPORTS = ("npp_create", "npp_destroy", "npp_last_error", "npp_n_theta", "npp_pl
            "npp_proposal_create", "npp_proposal_destroy", "npp_proposal_n_params",
            "npp_proposal_set_params", "npp_proposal_get_params", "npp_proposal_get_grads",
            "npp_proposal_encode", "npp_proposal_forward", "npp_proposal_train_step",
-           "npp_plan_step_proposal", "npp_gemm_bf16", "npp_gemm_status")
+           "npp_plan_step_proposal", "npp_gemm_bf16", "npp_gemm_status", "npp_plan_tshc")
 
 _lib = None
 
@@ -142,6 +142,8 @@ def lib():
         L.npp_plan_step_proposal.argtypes = [P, C.POINTER(npp_state), C.POINTER(npp_goal), P, I32, I32,
                                              I32, U64, U32, P, P, P, I32, C.POINTER(npp_outputs), P]
         L.npp_gemm_bf16.argtypes = [P, P, P, I32, I32, I32, P]
+        L.npp_plan_tshc.argtypes = [P, C.POINTER(npp_state), C.POINTER(npp_goal), P, I32, I32, I32, U64, U32, P,
+                                    I32, C.c_float, C.POINTER(npp_outputs), P]
         L.npp_gemm_status.argtypes = []
         for name in EXPORTS:
             if name not in ("npp_last_error", "npp_n_theta", "npp_proposal_n_params"):
@@ -308,6 +310,13 @@ def npp_plan_step_proposal(h, state, goal, obs, M, N, T, seed, t_index, warm, me
                                                _ptr(obs), int(M), int(N), int(T), int(seed), int(t_index),
                                                _ptr(warm), _ptr(mean), _ptr(std), int(N_prop),
                                                C.byref(out), _stream(stream)), h)
+
+
+def npp_plan_tshc(h, state, goal, obs, M, N, T, seed, t_index, warm, n_restarts, sigma_pert,
+                  out: "npp_outputs", stream=None):
+    return _check(lib().npp_plan_tshc(h, C.byref(make_state(state)), C.byref(make_goal(goal)), _ptr(obs), int(M),
+                                      int(N), int(T), int(seed), int(t_index), _ptr(warm), int(n_restarts),
+                                      float(sigma_pert), C.byref(out), _stream(stream)), h)
 
 
 def npp_gemm_bf16(A, B, Cout, M, N, K, stream=None):

@@ -199,3 +199,18 @@ def test_no_obstacles_and_edge_sizes(orc):
     assert r["status"] == 0 and np.all(r["first_hit"] == -1)
     with pytest.raises(ValueError):
         orc.plan(sc["preset"], sc["state"], sc["goal"], sc["obs"], 0, 5, 1, 0)
+
+
+def test_tshc_rounds_never_worse(orc):
+    """The hill climb's restart rounds keep the best so far as sample 0, so
+    the best cost is non-increasing over rounds; with one round it is the
+    plain plan step."""
+    sc = inputs.tiny_scene(17, N=64, T=15, M=40, width=16, box=15.0)
+    st, gl, ob = (np.asarray(sc[k], np.float32).astype(np.float64) for k in ("state", "goal", "obs"))
+    r = orc.plan_tshc(sc["preset"], st, gl, ob, 64, 15, sc["seed"], sc["t_index"], 4, 0.3)
+    h = r["history"]
+    assert all(h[i + 1] <= h[i] for i in range(len(h) - 1)), h
+    assert h[-1] < h[0]
+    one = orc.plan_tshc(sc["preset"], st, gl, ob, 64, 15, sc["seed"], sc["t_index"], 1, 0.3)
+    plain = orc.plan(sc["preset"], st, gl, ob, 64, 15, sc["seed"], sc["t_index"])
+    assert one["best_cost"] == plain["best_cost"] and one["best_idx"] == plain["best_idx"]

@@ -97,3 +97,29 @@ def test_loop_reaches_waypoint_without_obstacles():
     d_end = math.hypot(goal[0] - log[-1, 0], goal[1] - log[-1, 1])
     assert reached_at is not None, (d0, d_end, log[-1])
     assert st["n_infeasible"] == 0
+
+
+def test_loop_completes_the_obstacle_free_course():
+    """The forward/reverse waypoint course of Experiment 4 (corners of a 15 m
+    square, 90-degree heading changes) without obstacles: the device loop
+    reaches all four waypoints within the completion tolerances (Table
+    hyperparameters) in at most 500 sampling times."""
+    import torch
+    from paper_1904_06680_gb300 import npp
+    sc = inputs.scene_course(0, n_wall=4, n_island=2, n_dyn=2)
+    sc["obs"][:, :2] += 1e4                       # the few points far away
+    p, N, T = sc["preset"], sc["N"], sc["T"]
+    M = sc["obs"].shape[0]
+    pl = npp.Planner(p, max_N=N, max_T=T, max_M=M)
+    obs0 = torch.tensor(sc["obs"], dtype=torch.float32, device="cuda")
+    L = npp.npp_loop_create(pl.h, sc["state"], sc["waypoints"], inputs.EPS, obs0, M, N, T, sc["seed"], max_log=600)
+    st = None
+    for _ in range(10):
+        npp.npp_loop_run(L, 50)
+        st = npp.npp_loop_read(L)
+        if st["done"]:
+            break
+    npp.npp_loop_destroy(L)
+    pl.close()
+    assert st["done"] == 1 and st["waypoint"] == 3, st
+    assert st["t"] <= 500 and st["n_infeasible"] == 0

@@ -202,3 +202,15 @@ def test_binned_closed_loop_identical_to_brute_force():
     a = runs[(BINNED, 0)]
     assert a[3]["t"] == 20
     assert np.any(a[1][1] < 0)                # feasible plans at step 19
+
+
+@pytest.mark.parametrize("N,T,M", [(1, 1, 0), (1, 1, 1), (1, 3, 600), (33, 1, 600), (5, 2, 2)])
+def test_all_variants_at_extreme_sizes(N, T, M):
+    """One sample, one step, no or one point: every collision variant (brute
+    force 0-4, binned stored and fused) gives the same result."""
+    sc = inputs.tiny_scene(60 + N + T + M, N, T, M, width=16, box=6.0, clear=1.0)
+    ref = _plan(sc, 2)
+    for v in (0, 1, 3, 4):
+        _assert_same(_plan(sc, v), ref)
+    for fuse in (0, 1):
+        _assert_same(_plan(sc, BINNED, fuse=fuse), ref)

@@ -181,6 +181,21 @@ npp_status run_rollout(npp_handle* h, RolloutArgs& a, cudaStream_t s, bool allow
                 : (binned_auto(a.M, a.N) ? COLLIDE_BINNED : (a.N <= 8192 ? 3 : (a.N <= 32768 ? 4 : 2)));
     if (v == COLLIDE_BINNED) {
         if (h->timing) CUDA_TRY(h, record_event(h->ev[0], s));
+        if (!(allow_fused && h->fuse)) {
+            // the grids depend only on the points: build them on the side
+            // stream while the trajectories run (fork/join events; under
+            // stream capture this makes two graph branches)
+            CUDA_TRY(h, cudaEventRecord(h->fork_ev, s));
+            CUDA_TRY(h, cudaStreamWaitEvent(h->side, h->fork_ev, 0));
+            CUDA_TRY(h, build_bins(a, h->cfg.half_len, h->cfg.half_wid, h->cfg.c_off, h->d_bins, h->side));
+            CUDA_TRY(h, cudaEventRecord(h->join_ev, h->side));
+            CUDA_TRY(h, launch_traj(h, a, s));
+            if (h->timing) CUDA_TRY(h, record_event(h->ev[1], s));
+            CUDA_TRY(h, cudaStreamWaitEvent(s, h->join_ev, 0));
+            CUDA_TRY(h, launch_collide_binned(a, s));
+            if (h->timing) CUDA_TRY(h, record_event(h->ev[2], s));
+            return NPP_OK;
+        }
         CUDA_TRY(h, build_bins(a, h->cfg.half_len, h->cfg.half_wid, h->cfg.c_off, h->d_bins, s));
         if (allow_fused && h->fuse) {
             CUDA_TRY(h, launch_fused(h, a, s));
@@ -191,10 +206,6 @@ npp_status run_rollout(npp_handle* h, RolloutArgs& a, cudaStream_t s, bool allow
             *fused = true;
             return NPP_OK;
         }
-        CUDA_TRY(h, launch_traj(h, a, s));
-        if (h->timing) CUDA_TRY(h, record_event(h->ev[1], s));
-        CUDA_TRY(h, launch_collide_binned(a, s));
-        if (h->timing) CUDA_TRY(h, record_event(h->ev[2], s));
         return NPP_OK;
     }
     // points beyond shared memory: point-sliced kernel on an L2-resident copy
@@ -373,6 +384,9 @@ npp_status npp_create(npp_handle** out, const npp_config* cfg, int32_t device)
     A((void**)&h->d_costs, (size_t)cfg->max_N * sizeof(float));
     A((void**)&h->d_fh, (size_t)cfg->max_N * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming);
     for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&h->ev[i]);
     if (e != cudaSuccess) {
         g_err = std::string("workspace allocation failed: ") + cudaGetErrorString(e);
@@ -394,6 +408,9 @@ npp_status npp_destroy(npp_handle* h)
                      h->d_costs, h->d_fh };
     for (void* p : ptrs) if (p) cudaFree(p);
     if (h->stream) cudaStreamDestroy(h->stream);
+    if (h->side) { cudaStreamSynchronize(h->side); cudaStreamDestroy(h->side); }
+    if (h->fork_ev) cudaEventDestroy(h->fork_ev);
+    if (h->join_ev) cudaEventDestroy(h->join_ev);
     for (int i = 0; i < 4; ++i) if (h->ev[i]) cudaEventDestroy(h->ev[i]);
     delete h;
     return NPP_OK;

@@ -50,6 +50,8 @@ struct npp_handle {
     float* d_costs;
     int32_t* d_fh;
     cudaStream_t stream;
+    cudaStream_t side;                   // concurrent branch of a plan step (grid build)
+    cudaEvent_t fork_ev, join_ev;
     bool timing;
     cudaEvent_t ev[4];                   // start, after trajectories, after collisions, end
     std::string err;

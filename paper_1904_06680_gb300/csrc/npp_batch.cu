@@ -492,10 +492,17 @@ __global__ void __launch_bounds__(256) batch_binned_kernel(const BatchArgs b)
     unsigned long long key = ~0ull;
     if (n < N) {
         int fh = -1;
+        // the next step's rows are loaded while the current step is checked
+        float4 nca = b.coefA[s.coef_off + n];
+        float2 ncb = b.coefB[s.coef_off + n];
         for (int h = 0; h <= T; ++h) {
-            const long long idx = s.coef_off + (long long)h * N + n;
-            const float4 ca = b.coefA[idx];
-            const float2 cb = b.coefB[idx];
+            const float4 ca = nca;
+            const float2 cb = ncb;
+            if (h < T) {
+                const long long nx = s.coef_off + (long long)(h + 1) * N + n;
+                nca = b.coefA[nx];
+                ncb = b.coefB[nx];
+            }
             const float cp = ca.x * isl, sp = ca.y * isl;
             const float along = -ca.z * isl, across = -cb.y * isw;
             const float xc = cp * along - sp * across, yc = sp * along + cp * across;

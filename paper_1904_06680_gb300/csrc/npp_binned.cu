@@ -56,13 +56,22 @@ __global__ void __launch_bounds__(BINNED_WARPS * 32) collide_binned_kernel(const
     unsigned long long key = ~0ull;
     if (n < N) {
         int fh = -1;
+        // the next step's rows are loaded while the current step is checked
+        float4 nca = a.coefA[n];
+        float2 ncb = a.coefB[n];
+        float4 nz = a.traj[n];
         for (int h = 0; h <= T; ++h) {
-            const size_t idx = (size_t)h * N + n;
-            const float4 ca = a.coefA[idx];
-            const float2 cb = a.coefB[idx];
+            const float4 ca = nca;
+            const float2 cb = ncb;
             // the rectangle lies in the disk of radius reach around the
             // reference point (reach covers the centre offset)
-            const float4 z = a.traj[idx];
+            const float4 z = nz;
+            if (h < T) {
+                const size_t nx = (size_t)(h + 1) * N + n;
+                nca = a.coefA[nx];
+                ncb = a.coefB[nx];
+                nz = a.traj[nx];
+            }
             const int ix0 = bin_cell(z.x - g.reach, g), ix1 = bin_cell(z.x + g.reach, g);
             const int iy0 = bin_cell(z.y - g.reach, g), iy1 = bin_cell(z.y + g.reach, g);
             const int* cs = g.cell_start + (size_t)h * BIN_CS_STRIDE;

@@ -448,6 +448,38 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def batch_cpu_baseline(bt, target_cpu_s=15.0):
+    """Oracle (as it stands) on the host cores: the first scenes of the batch,
+    a bounded number of samples each over their full horizon (brute-force
+    checks), rollout-steps per second of wall time."""
+    from oracle import oracle as orc
+    cores = os.cpu_count() or 1
+    done_steps, wall, used = 0.0, 0.0, 0
+    for s_ in bt["scenes"]:
+        if wall * cores > target_cpu_s:
+            break
+        o = bt["obs"][s_["obs_offset"]:s_["obs_offset"] + s_["M"]]
+        st = np.asarray(s_["state"], np.float32).astype(np.float64)
+        goal_ev, obs_ev = orc.frame_to_ev(st, np.asarray(s_["goal"], np.float32).astype(np.float64),
+                                          np.asarray(o, np.float32).astype(np.float64))
+        p = inputs_planner(s_["width"])
+        K = min(s_["N"], 512)
+        t0 = time.perf_counter()
+        orc.rollout_samples(p, s_["seed"], 0, np.arange(K, dtype=np.int32), [0, 0, 0, st[3]], st[4:6], goal_ev,
+                            obs_ev, s_["T"], n_threads=cores, record=False)
+        wall += time.perf_counter() - t0
+        done_steps += K * s_["T"]
+        used += 1
+    return {"value": done_steps / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "the first %d scenes of the batch, up to 512 samples each over the full horizon, brute-force "
+                      "checks, FP64 C with OpenMP (%.1f s wall)" % (used, wall)}
+
+
+def inputs_planner(width):
+    from paper_1904_06680_gb300 import inputs
+    return inputs.planner(width)
+
+
 def run_batch(args):
     """512 reverse-parking scenes (N log-uniform 1k-64k, T 20-80, M
     log-uniform 100-20000 with 30 % moving, widths 16/32/64) planned as one
@@ -552,6 +584,7 @@ def run_batch(args):
                        "l2": "flushed (256 MiB write) between replays"},
             "roofline": roof,
             "gpu_launches": (1 + n_widths + (2 if binned else 1) + 1) * K, "clocks": ck,
+            "cpu_baseline": None if (args.no_cpu_baseline or rank != 0) else batch_cpu_baseline(bt),
             "free_fraction": float(np.mean(fhs < 0)),
             "infeasible_scenes": int((best.cpu().view(S, 8)[:, 1] == 2).sum())}
     npp.npp_batch_destroy(B)
@@ -568,6 +601,26 @@ def measured_peaks():
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         return {}
+
+
+def proposal_cpu_baseline(B=256, reps=3):
+    """Oracle (numpy FP64, as it stands) forward + NLL + backward + Adam step
+    of the proposal network on a batch of B rows, samples per second."""
+    from oracle import proposal as OP
+    rng = np.random.default_rng(0)
+    params = OP.init_params(0)
+    X = rng.uniform(0, 1, (B, OP.N_IN))
+    th = rng.standard_normal((B, OP.N_THETA))
+    st = OP.adam_init()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        c = OP.forward(params, X)
+        g = OP.backward(params, c, th)
+        params, st = OP.adam_step(params, g, st, 1e-4)
+    wall = time.perf_counter() - t0
+    return {"value": B * reps / wall, "unit": "samples/s", "cores": os.cpu_count() or 1, "kind": "oracle",
+            "sample": "%d training steps of a %d-row batch (forward with BF16 rounding, NLL, backward, Adam) "
+                      "in numpy FP64 (%.1f s wall)" % (reps, B, wall)}
 
 
 def run_proposal(args):
@@ -644,6 +697,7 @@ def run_proposal(args):
                          "kernel_ms": gemm_ms,
                          "train_step_gemm_tflops": flops / (step_ms * 1e-3) / 1e12},
             "e2e": None, "gpu_launches": 14 * args.steps, "clocks": ck,
+            "cpu_baseline": None if args.no_cpu_baseline else proposal_cpu_baseline(),
             "quality": {str(k): v for k, v in quality.items()},
             "training": {"rounds": args.rounds, "seconds": train_s,
                          "proposal_won_first_last": [stats[0]["proposal_won"], stats[-1]["proposal_won"]]}}

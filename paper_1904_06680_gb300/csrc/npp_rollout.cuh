@@ -68,6 +68,28 @@ struct ThetaSrc {
     }
 };
 
+// Two FP32 values in one 64-bit register pair, for the packed FP32x2
+// instructions: fma.rn.f32x2 rounds each half exactly as fmaf does.
+__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi)
+{
+    unsigned long long d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+    return d;
+}
+__device__ __forceinline__ float2 f2_unpack(unsigned long long v)
+{
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c)
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
 template <int W, int G>
 struct LaneNet {
     using S = Shape<W, G>;
@@ -452,27 +474,29 @@ __device__ __forceinline__ FusedOut traj_sample(const DevCfg& c, const TrajJob& 
         // layer 2: each unit's dot product as four interleaved partial sums
         // (inputs i = 4q + r go to partial r), added pairwise with the bias
         // last: independent FMA chains keep the pipe busy
-        float part[U][4];
+        // (partials 0, 1 and 2, 3 as packed pairs: two FP32x2 FMAs per input
+        // quad, each half rounded as a separate fmaf)
+        unsigned long long p01[U], p23[U];
 #pragma unroll
-        for (int j = 0; j < U; ++j)
-#pragma unroll
-            for (int r = 0; r < 4; ++r) part[j][r] = 0.0f;
+        for (int j = 0; j < U; ++j) p01[j] = p23[j] = 0ull;
         const float4* hrow4 = reinterpret_cast<const float4*>(hrow);
 #pragma unroll
         for (int i = 0; i < W / 4; ++i) {
             const float4 hv = hrow4[i];
+            const unsigned long long h01 = f2_pack(hv.x, hv.y), h23 = f2_pack(hv.z, hv.w);
 #pragma unroll
             for (int j = 0; j < U; ++j) {
-                part[j][0] = fmaf(net.w2[j][4 * i + 0], hv.x, part[j][0]);
-                part[j][1] = fmaf(net.w2[j][4 * i + 1], hv.y, part[j][1]);
-                part[j][2] = fmaf(net.w2[j][4 * i + 2], hv.z, part[j][2]);
-                part[j][3] = fmaf(net.w2[j][4 * i + 3], hv.w, part[j][3]);
+                p01[j] = f2_fma(f2_pack(net.w2[j][4 * i + 0], net.w2[j][4 * i + 1]), h01, p01[j]);
+                p23[j] = f2_fma(f2_pack(net.w2[j][4 * i + 2], net.w2[j][4 * i + 3]), h23, p23[j]);
             }
         }
         __syncwarp();
         float acc2[U];
 #pragma unroll
-        for (int j = 0; j < U; ++j) acc2[j] = ((part[j][0] + part[j][1]) + (part[j][2] + part[j][3])) + net.b2[j];
+        for (int j = 0; j < U; ++j) {
+            const float2 q01 = f2_unpack(p01[j]), q23 = f2_unpack(p23[j]);
+            acc2[j] = ((q01.x + q01.y) + (q23.x + q23.y)) + net.b2[j];
+        }
         // layer 3: a fixed pairwise tree over the hidden units -- leaves
         // w_2i h_2i + w_2i+1 h_2i+1 (one fma), then sums of neighbours -- so
         // the value does not depend on how many units a lane holds

@@ -74,6 +74,12 @@ typedef struct {
     /* network: widths[0] = inputs, widths[n_layers] = 2 outputs */
     int32_t n_layers;
     int32_t widths[ORC_MAX_LAYERS + 1];
+    /* variants (Sect. V): goal offsets of the features in the body frame at
+     * t+h instead of the EV frame at t; velocity constraints imposed by
+     * discarding every sample whose speed leaves [v_min, v_max] */
+    int32_t feature_frame;    /* 0: EV frame at t, 1: body frame at t+h */
+    int32_t v_limits;         /* 1: speed limits on                     */
+    double v_min, v_max;      /* [m/s]                                  */
 } orc_config;
 
 enum { ORC_OK = 0, ORC_INFEASIBLE = 2, ORC_INVALID = 1 };
@@ -248,12 +254,21 @@ static double wrap_pi(double a)
 /* Eq. (eq_def_stph): deviations from the goal in the EV-aligned frame at t,
  * normalised by the Delta constants, and the last applied steering.  For
  * 8-input networks three more entries follow: last applied acceleration
- * command, normalised speed, and the remaining-horizon fraction. */
+ * command, normalised speed, and the remaining-horizon fraction.  With
+ * feature_frame = 1 the position deviation is expressed in the vehicle's
+ * own frame at t+h (rotated by -phi_{t+h}), the variant Sect. V names. */
 void orc_features(const orc_config* c, const double z[4], const double ap[2],
                   const double goal[4], int h, int T, double* s)
 {
-    s[0] = (goal[0] - z[0]) / c->dxi_n;
-    s[1] = (goal[1] - z[1]) / c->deta_n;
+    double dx = goal[0] - z[0], dy = goal[1] - z[1];
+    if (c->feature_frame == 1) {
+        double cp = cos(z[2]), sp = sin(z[2]);
+        double bx = cp * dx + sp * dy, by = -sp * dx + cp * dy;
+        dx = bx;
+        dy = by;
+    }
+    s[0] = dx / c->dxi_n;
+    s[1] = dy / c->deta_n;
     s[2] = wrap_pi(goal[2] - z[2]) / c->dphi_n;
     s[3] = (goal[3] - z[3]) / c->dv_n;
     s[4] = ap[0];
@@ -357,6 +372,15 @@ int orc_collide(const orc_config* c, double x, double y, double phi,
     return hit;
 }
 
+/* Velocity constraints by discarding samples (Sect. V): a state reached by
+ * the sample's own controls (h >= 1) whose speed is outside [v_min, v_max]
+ * ends the sample there as a collision does.  The initial speed is given,
+ * not chosen, so h = 0 is never discarded for it. */
+int orc_speed_violated(const orc_config* c, double v, int h)
+{
+    return c->v_limits == 1 && h > 0 && !(v >= c->v_min && v <= c->v_max);
+}
+
 /* ------------------------------------------------------------------ */
 /* one rollout                                                          */
 /* ------------------------------------------------------------------ */
@@ -375,7 +399,8 @@ static int rollout(const orc_config* c, const double* theta, const double z0[4],
     int fh = -1;
     for (int h = 0; h <= T; ++h) {
         if (traj) memcpy(traj + 4 * h, z, sizeof z);
-        if (orc_collide(c, z[0], z[1], z[2], obs, M, h * c->Ts, 0.0, NULL, NULL)) {
+        if (orc_speed_violated(c, z[3], h) ||
+            orc_collide(c, z[0], z[1], z[2], obs, M, h * c->Ts, 0.0, NULL, NULL)) {
             fh = h;
             break;
         }

@@ -22,17 +22,26 @@ class OrcConfig(C.Structure):
         "lf", "lr", "delta_max", "delta_rate_max", "u_min", "u_max", "Ts",
         "half_len", "half_wid", "c_off", "dxi_n", "deta_n", "dphi_n", "dv_n",
         "w_pos", "w_phi", "w_v", "w_effort")] + [
-        ("n_layers", C.c_int32), ("widths", C.c_int32 * (MAX_LAYERS + 1))]
+        ("n_layers", C.c_int32), ("widths", C.c_int32 * (MAX_LAYERS + 1)),
+        ("feature_frame", C.c_int32), ("v_limits", C.c_int32), ("v_min", C.c_double), ("v_max", C.c_double)]
+
+N_FLOAT = 18
 
 
 def make_config(p: dict) -> OrcConfig:
+    """Preset dict -> FP64 config; the variant keys (feature_frame, v_limits,
+    v_min, v_max) are optional and default to off."""
     c = OrcConfig()
-    for name, _ in OrcConfig._fields_[:-2]:
+    for name, _ in OrcConfig._fields_[:N_FLOAT]:
         setattr(c, name, float(p[name]))
     widths = list(p["widths"])
     c.n_layers = len(widths) - 1
     for i, w in enumerate(widths):
         c.widths[i] = int(w)
+    c.feature_frame = int(p.get("feature_frame", 0))
+    c.v_limits = int(p.get("v_limits", 0))
+    c.v_min = float(p.get("v_min", 0.0))
+    c.v_max = float(p.get("v_max", 0.0))
     return c
 
 
@@ -60,6 +69,8 @@ def lib():
         L.orc_theta.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_int, _F]
         L.orc_frame_to_ev.argtypes = [_D, _D, _D, C.c_int, _D, _D]
         L.orc_features.argtypes = [_P, _D, _D, _D, C.c_int, C.c_int, _D]
+        L.orc_speed_violated.argtypes = [_P, C.c_double, C.c_int]
+        L.orc_speed_violated.restype = C.c_int
         L.orc_mlp.argtypes = [_P, _D, _D, _D]
         L.orc_controls.argtypes = [_P, _D, _D, _D]
         L.orc_euler_step.argtypes = [_P, _D, _D, _D]
@@ -161,6 +172,11 @@ def features(p, z, ap, goal_ev, h, T):
     s = np.zeros(16)
     lib().orc_features(C.byref(make_config(p)), _d(z, 4), _d(ap, 2), _d(goal_ev, 4), h, T, s)
     return s[: p["widths"][0]]
+
+
+def speed_violated(p, v, h):
+    """Whether state h with speed v discards the sample (speed limits on, h >= 1)."""
+    return bool(lib().orc_speed_violated(C.byref(make_config(p)), float(v), int(h)))
 
 
 def mlp(p, th, s):

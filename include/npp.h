@@ -80,6 +80,16 @@ typedef struct {
     int32_t n_in;              /* network inputs: must be 8                      */
     int32_t width;             /* hidden width: 16, 32 or 64                     */
     int32_t max_N, max_T, max_M; /* workspace capacity of the handle             */
+    /* Variants of Sect. V (a zero-filled tail keeps the defaults): */
+    int32_t feature_frame;     /* goal offsets s0, s1 of the features (Eq. of s_{t+h}):
+                                  0 = in the EV frame at t (default), 1 = in the
+                                  vehicle's own frame at t+h                       */
+    int32_t v_limits;          /* 1 = velocity constraints by discarding samples: a
+                                  sample is discarded at the first state h >= 1 it
+                                  reaches whose speed is outside [v_min, v_max],
+                                  exactly as if it collided there (first_hit = h);
+                                  0 = off (default)                                */
+    float v_min, v_max;        /* speed limits [m/s] when v_limits = 1; v_min <= v_max */
 } npp_config;
 
 /* Vehicle state at the sampling time (world frame) with the controls applied
@@ -94,7 +104,8 @@ typedef struct {
     int32_t best_idx;   /* winning sample index                              */
     int32_t status;     /* NPP_OK or NPP_INFEASIBLE                          */
     float best_cost;    /* its cost (+inf when infeasible)                   */
-    int32_t first_hit;  /* its first colliding horizon index, -1 if none     */
+    int32_t first_hit;  /* its first colliding (or, with v_limits, speed-violating)
+                           horizon index, -1 if none                         */
     int32_t reserved[4];
 } npp_best;
 
@@ -108,7 +119,7 @@ typedef struct {
     float* controls;         /* [T][2]      applied normalised controls      */
     float* trajectory;       /* [T+1][4]    (x, y, phi, v)                   */
     float* costs;            /* [N]         per-sample cost, +inf if collided */
-    int32_t* first_hit;      /* [N]         first colliding h, -1 if none    */
+    int32_t* first_hit;      /* [N]         first colliding (or speed-violating) h, -1 if none */
     float* sample_traj;      /* [T+1][N][4] every sample's states, EV frame at t
                                 (origin at the vehicle, x along its heading);
                                 rows after a sample's first collision continue

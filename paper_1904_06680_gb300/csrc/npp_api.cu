@@ -284,6 +284,7 @@ static void fill_rollout_args(const npp_handle* h, RolloutArgs& a, const npp_sta
     a.gx = g->x; a.gy = g->y; a.gphi = g->phi; a.gv = g->v;
     a.obs = reinterpret_cast<const float4*>(obs);
     a.M = M; a.N = N; a.T = T;
+    a.vfirst = h->d_vfirst;
 }
 
 // ------------------------------------------------------------------ C ABI
@@ -318,6 +319,7 @@ npp_status npp_create(npp_handle** out, const npp_config* cfg, int32_t device)
         return fail(nullptr, NPP_INVALID_ARG, "config constant out of range");
     if (cfg->max_N < 1 || cfg->max_T < 1 || cfg->max_M < 0)
         return fail(nullptr, NPP_INVALID_ARG, "capacity max_N, max_T >= 1, max_M >= 0 required");
+    if (const char* ve = variant_error(*cfg)) return fail(nullptr, NPP_INVALID_ARG, "%s", ve);
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
         return fail(nullptr, NPP_CUDA_ERROR, "CUDA device %d not available", device);
@@ -340,23 +342,7 @@ npp_status npp_create(npp_handle** out, const npp_config* cfg, int32_t device)
     h->device = device;
     h->n_theta = n_theta_of(cfg->width);
     h->max_points = max_points;
-    DevCfg& d = h->dc;
-    const double L = (double)cfg->lf + cfg->lr;
-    d.delta_max = cfg->delta_max;
-    d.r_rate = (float)((double)cfg->delta_rate_max * cfg->Ts / cfg->delta_max);
-    d.lrL = (float)(cfg->lr / L);
-    d.iL = (float)(1.0 / L);
-    d.umid = (float)(0.5 * ((double)cfg->u_min + cfg->u_max));
-    d.uhalf = (float)(0.5 * ((double)cfg->u_max - cfg->u_min));
-    d.Ts = cfg->Ts;
-    d.ihl = (float)(1.0 / cfg->half_len);
-    d.ihw = (float)(1.0 / cfg->half_wid);
-    d.c_off = cfg->c_off;
-    d.idxi = (float)(1.0 / cfg->dxi_n);
-    d.ideta = (float)(1.0 / cfg->deta_n);
-    d.idphi = (float)(1.0 / cfg->dphi_n);
-    d.idv = (float)(1.0 / cfg->dv_n);
-    d.w_pos = cfg->w_pos; d.w_phi = cfg->w_phi; d.w_v = cfg->w_v; d.w_effort = cfg->w_effort;
+    h->dc = devcfg_from(*cfg);
 
     const size_t NT1 = (size_t)(cfg->max_T + 1) * cfg->max_N;
     const size_t NT = (size_t)cfg->max_T * cfg->max_N;
@@ -366,6 +352,7 @@ npp_status npp_create(npp_handle** out, const npp_config* cfg, int32_t device)
     A((void**)&h->d_traj, NT1 * sizeof(float4));
     A((void**)&h->d_ctrl, NT * sizeof(float2));
     A((void**)&h->d_jfree, (size_t)cfg->max_N * sizeof(float));
+    if (cfg->v_limits) A((void**)&h->d_vfirst, (size_t)cfg->max_N * sizeof(int));
     A((void**)&h->d_coefA, NT1 * sizeof(float4));
     A((void**)&h->d_coefB, NT1 * sizeof(float2));
     A((void**)&h->d_work, 64);
@@ -402,7 +389,7 @@ npp_status npp_destroy(npp_handle* h)
     if (!h) return NPP_OK;
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
-    void* ptrs[] = { h->d_key, h->d_traj, h->d_ctrl, h->d_jfree, h->d_coefA, h->d_coefB, h->d_work,
+    void* ptrs[] = { h->d_key, h->d_traj, h->d_ctrl, h->d_jfree, h->d_vfirst, h->d_coefA, h->d_coefB, h->d_work,
                      h->d_pXY, h->d_pV, h->d_bins,
                      h->d_obs, h->d_warm, h->d_sigma, h->d_best, h->d_params, h->d_controls, h->d_trajectory,
                      h->d_costs, h->d_fh };

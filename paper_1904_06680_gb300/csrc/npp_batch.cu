@@ -59,6 +59,7 @@ struct BatchArgs {
     float4* coefA;
     float2* coefB;
     float* jfree;
+    int* vfirst;                     // first speed-violating step per sample, or null (limits off)
     unsigned long long* keys;        // [S]
     unsigned* counters;              // [4] work queues: widths 16, 32, 64, collisions
     // item lists
@@ -351,6 +352,7 @@ __global__ void __launch_bounds__(NW * 32) batch_traj_kernel(const BatchArgs b, 
         job.coefB = b.coefB;
         job.coef_base = s.coef_off;
         job.jfree = b.jfree + s.samp_off;
+        job.vfirst = b.vfirst ? b.vfirst + s.samp_off : nullptr;
         constexpr int STAGE_TH = W == 32 ? NW * 32 : 0;     // as traj_kernel
         traj_sample<W, G, false, STAGE_TH>(b.c, job, n, n < s.N, gl, hx_all + bi * W);
     }
@@ -436,7 +438,7 @@ __global__ void __launch_bounds__(S * 32) batch_collide_kernel(const BatchArgs b
             unsigned long long key = ~0ull;
             if (mine) {
                 const int d = dead_at[lane];
-                const int fh = d <= T ? d : -1;
+                const int fh = discard_step(b.vfirst ? b.vfirst + s.samp_off : nullptr, n, d <= T ? d : -1);
                 float J = __int_as_float(0x7f800000);
                 if (fh < 0) {
                     J = b.jfree[s.samp_off + n];
@@ -529,6 +531,7 @@ __global__ void __launch_bounds__(256) batch_binned_kernel(const BatchArgs b)
             if (hit) { fh = h; break; }
         }
         if (lane == 0) {
+            fh = discard_step(b.vfirst ? b.vfirst + s.samp_off : nullptr, n, fh);
             float J = __int_as_float(0x7f800000);
             if (fh < 0) {
                 J = b.jfree[s.samp_off + n];
@@ -575,6 +578,7 @@ __device__ void batch_reroll(const BatchArgs& b, const SceneDev& s, int idx, flo
     job.coefB = nullptr;
     job.coef_base = 0;
     job.jfree = nullptr;
+    job.vfirst = nullptr;
     traj_sample<W, G>(b.c, job, idx, true, lane % G, hrows + (lane / G) * W);
 }
 
@@ -668,6 +672,7 @@ struct npp_batch {
     float4* d_coefA;
     float2* d_coefB;
     float* d_jfree;
+    int* d_vfirst;           // [samples] when the handle's speed limits are on
     unsigned long long* d_keys;
     unsigned* d_counters;
     int resident_pairs;
@@ -689,7 +694,7 @@ void free_batch(npp_batch* B)
     void* ptrs[] = { B->d_scenes, B->d_order, B->d_citem_prefix, B->d_torder[0], B->d_torder[1],
                      B->d_torder[2], B->d_titem_prefix[0], B->d_titem_prefix[1], B->d_titem_prefix[2],
                      B->d_pXY, B->d_pV, B->d_tileP, B->d_tileV, B->d_bin_cs, B->d_bin_pts, B->d_bstep_prefix,
-                     B->d_coefA, B->d_coefB, B->d_jfree, B->d_keys, B->d_counters };
+                     B->d_coefA, B->d_coefB, B->d_jfree, B->d_vfirst, B->d_keys, B->d_counters };
     for (void* p : ptrs) if (p) cudaFree(p);
     delete B;
 }
@@ -889,6 +894,7 @@ npp_status npp_batch_create(npp_handle* h, const npp_scene* scenes, int32_t S, n
     A((void**)&B->d_coefA, sizeof(float4) * rows);
     A((void**)&B->d_coefB, sizeof(float2) * rows);
     A((void**)&B->d_jfree, sizeof(float) * samples);
+    if (h->cfg.v_limits) A((void**)&B->d_vfirst, sizeof(int) * samples);
     A((void**)&B->d_keys, sizeof(unsigned long long) * S);
     A((void**)&B->d_counters, 64);
     if (e != cudaSuccess) {
@@ -965,6 +971,7 @@ npp_status npp_plan_batch(npp_batch* B, const float* obs_dev, const npp_batch_ou
     b.coefA = B->d_coefA;
     b.coefB = B->d_coefB;
     b.jfree = B->d_jfree;
+    b.vfirst = B->d_vfirst;
     b.keys = B->d_keys;
     b.counters = B->d_counters;
     b.order = B->d_order;

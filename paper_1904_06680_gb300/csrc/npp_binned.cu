@@ -95,6 +95,7 @@ __global__ void __launch_bounds__(BINNED_WARPS * 32) collide_binned_kernel(const
             if (hit) { fh = h; break; }
         }
         if (lane == 0) {
+            fh = discard_step(a.vfirst, n, fh);
             float J = __int_as_float(0x7f800000);
             if (fh < 0) {
                 J = a.jfree[n];

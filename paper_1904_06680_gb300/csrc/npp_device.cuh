@@ -3,8 +3,11 @@
 // kernel argument blocks shared by the kernels and their launchers.
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
+
+#include "../../include/npp.h"
 
 namespace npp {
 
@@ -20,7 +23,47 @@ struct DevCfg {
     float ihl, ihw, c_off;           // 1/half_len, 1/half_wid, centre offset
     float idxi, ideta, idphi, idv;   // 1 / feature normalisation constants
     float w_pos, w_phi, w_v, w_effort;
+    int body_frame;                  // goal offsets of the features in the frame at t+h
+    int vlim;                        // speed limits on: discard at the first h >= 1 outside
+    float v_lo, v_hi;                // [v_lo, v_hi]
 };
+
+// The device constants of a validated configuration (host side).
+inline DevCfg devcfg_from(const npp_config& cfg)
+{
+    DevCfg d;
+    const double L = (double)cfg.lf + cfg.lr;
+    d.delta_max = cfg.delta_max;
+    d.r_rate = (float)((double)cfg.delta_rate_max * cfg.Ts / cfg.delta_max);
+    d.lrL = (float)(cfg.lr / L);
+    d.iL = (float)(1.0 / L);
+    d.umid = (float)(0.5 * ((double)cfg.u_min + cfg.u_max));
+    d.uhalf = (float)(0.5 * ((double)cfg.u_max - cfg.u_min));
+    d.Ts = cfg.Ts;
+    d.ihl = (float)(1.0 / cfg.half_len);
+    d.ihw = (float)(1.0 / cfg.half_wid);
+    d.c_off = cfg.c_off;
+    d.idxi = (float)(1.0 / cfg.dxi_n);
+    d.ideta = (float)(1.0 / cfg.deta_n);
+    d.idphi = (float)(1.0 / cfg.dphi_n);
+    d.idv = (float)(1.0 / cfg.dv_n);
+    d.w_pos = cfg.w_pos; d.w_phi = cfg.w_phi; d.w_v = cfg.w_v; d.w_effort = cfg.w_effort;
+    d.body_frame = cfg.feature_frame;
+    d.vlim = cfg.v_limits;
+    d.v_lo = cfg.v_min;
+    d.v_hi = cfg.v_max;
+    return d;
+}
+
+// Range check of the variant fields of a configuration; null when valid.
+inline const char* variant_error(const npp_config& cfg)
+{
+    if (cfg.feature_frame != 0 && cfg.feature_frame != 1) return "feature_frame is 0 or 1";
+    if (cfg.v_limits != 0 && cfg.v_limits != 1) return "v_limits is 0 or 1";
+    if (cfg.v_limits == 1 && !(std::isfinite(cfg.v_min) && std::isfinite(cfg.v_max) && cfg.v_min <= cfg.v_max))
+        return "v_limits needs finite v_min <= v_max";
+    return nullptr;
+}
 
 // ------------------------------------------------------------------ sampler
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw: "Parallel random numbers: as
@@ -317,6 +360,8 @@ struct RolloutArgs {
     float4* traj;                      // [T+1][N] EV frame (always written)
     float2* ctrl;                      // [T][N]
     float* jfree;                      // [N] cost of each sample if collision-free
+    int* vfirst;                       // [N] first speed-violating step (-1 none), written by the
+                                       // trajectory kernel when c.vlim; null otherwise
     float4* coefA;                     // [T+1][N] (A, B, -C, D) scaled inequality rows
     float2* coefB;                     // [T+1][N] (E, -F)
     unsigned long long* best_key;      // packed (class, cost, index) minimum

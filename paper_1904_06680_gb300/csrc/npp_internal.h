@@ -26,6 +26,7 @@ struct npp_handle {
     float4* d_traj;                      // [(max_T+1) * max_N]
     float2* d_ctrl;                      // [max_T * max_N]
     float* d_jfree;                      // [max_N]
+    int* d_vfirst;                       // [max_N] first speed-violating step (speed limits on)
     float4* d_coefA;                     // [(max_T+1) * max_N]
     float2* d_coefB;                     // [(max_T+1) * max_N]
     unsigned* d_work;                    // persistent-kernel work counter

@@ -145,6 +145,7 @@ npp_status enqueue_step(npp_loop* L, uint64_t seed)
     a.traj = h->d_traj;
     a.ctrl = h->d_ctrl;
     a.jfree = h->d_jfree;
+    a.vfirst = h->d_vfirst;
     a.best_key = h->d_key;
     a.dyn = L->d_dyn;
     a.costs = L->d_costs;

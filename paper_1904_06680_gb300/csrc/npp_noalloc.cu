@@ -29,9 +29,11 @@ namespace {
 constexpr int NOALLOC_MAX_N = 16384;
 constexpr long long NOALLOC_MAX_STEPS = 16384LL * 42;     // 688,128 sample-steps
 // layout: [key, work counter | pad to 256] [cost if free, N floats]
+//         [first speed-violating step, N ints]
 //         [states float4] [controls float2] [coef A float4] [coef B float2]
 constexpr size_t OFF_JFREE = 256;
-constexpr size_t OFF_TRAJ = OFF_JFREE + (size_t)NOALLOC_MAX_N * 4;
+constexpr size_t OFF_VFIRST = OFF_JFREE + (size_t)NOALLOC_MAX_N * 4;
+constexpr size_t OFF_TRAJ = OFF_VFIRST + (size_t)NOALLOC_MAX_N * 4;
 constexpr size_t OFF_CTRL = OFF_TRAJ + (size_t)NOALLOC_MAX_STEPS * 16;
 constexpr size_t OFF_COEFA = OFF_CTRL + (size_t)NOALLOC_MAX_STEPS * 8;
 constexpr size_t OFF_COEFB = OFF_COEFA + (size_t)NOALLOC_MAX_STEPS * 16;
@@ -79,6 +81,7 @@ extern "C" npp_status npp_plan_step_noalloc(const npp_config* cfg, const npp_sta
         !(cfg->half_wid > 0.f) || !(cfg->dxi_n > 0.f) || !(cfg->deta_n > 0.f) ||
         !(cfg->dphi_n > 0.f) || !(cfg->dv_n > 0.f) || !(cfg->u_max >= cfg->u_min))
         return fail_noalloc(NPP_INVALID_ARG, "noalloc: config constant out of range");
+    if (const char* ve = variant_error(*cfg)) return fail_noalloc(NPP_INVALID_ARG, "noalloc: %s", ve);
     if (!finite_n(&state->x, 6) || !finite_n(&goal->x, 4) ||
         std::fabs(state->a_prev0) > 1.0f || std::fabs(state->a_prev1) > 1.0f)
         return fail_noalloc(NPP_INVALID_ARG, "noalloc: non-finite state/goal or |a_prev| > 1");
@@ -112,23 +115,7 @@ extern "C" npp_status npp_plan_step_noalloc(const npp_config* cfg, const npp_sta
     unsigned char* base = g_scratch_dev[dev];
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
 
-    DevCfg d;
-    const double L = (double)cfg->lf + cfg->lr;
-    d.delta_max = cfg->delta_max;
-    d.r_rate = (float)((double)cfg->delta_rate_max * cfg->Ts / cfg->delta_max);
-    d.lrL = (float)(cfg->lr / L);
-    d.iL = (float)(1.0 / L);
-    d.umid = (float)(0.5 * ((double)cfg->u_min + cfg->u_max));
-    d.uhalf = (float)(0.5 * ((double)cfg->u_max - cfg->u_min));
-    d.Ts = cfg->Ts;
-    d.ihl = (float)(1.0 / cfg->half_len);
-    d.ihw = (float)(1.0 / cfg->half_wid);
-    d.c_off = cfg->c_off;
-    d.idxi = (float)(1.0 / cfg->dxi_n);
-    d.ideta = (float)(1.0 / cfg->deta_n);
-    d.idphi = (float)(1.0 / cfg->dphi_n);
-    d.idv = (float)(1.0 / cfg->dv_n);
-    d.w_pos = cfg->w_pos; d.w_phi = cfg->w_phi; d.w_v = cfg->w_v; d.w_effort = cfg->w_effort;
+    const DevCfg d = devcfg_from(*cfg);
 
     RolloutArgs a;
     memset(&a, 0, sizeof a);
@@ -150,6 +137,7 @@ extern "C" npp_status npp_plan_step_noalloc(const npp_config* cfg, const npp_sta
     a.ctrl = out->sample_ctrl ? reinterpret_cast<float2*>(out->sample_ctrl)
                               : reinterpret_cast<float2*>(base + OFF_CTRL);
     a.jfree = reinterpret_cast<float*>(base + OFF_JFREE);
+    a.vfirst = cfg->v_limits ? reinterpret_cast<int*>(base + OFF_VFIRST) : nullptr;
     a.coefA = reinterpret_cast<float4*>(base + OFF_COEFA);
     a.coefB = reinterpret_cast<float2*>(base + OFF_COEFB);
     a.best_key = reinterpret_cast<unsigned long long*>(base);

@@ -220,6 +220,16 @@ __device__ __forceinline__ void write_coef(float4* coefA, float2* coefB, const D
     coefB[idx] = B;
 }
 
+// The step at which a sample is discarded: the earlier of its first colliding
+// step fh and its first speed-violating step vfirst[n] (either -1 for none;
+// vfirst null when speed limits are off).
+__device__ __forceinline__ int discard_step(const int* vfirst, long long n, int fh)
+{
+    if (!vfirst) return fh;
+    const int hv = vfirst[n];
+    return (hv >= 0 && (fh < 0 || hv < fh)) ? hv : fh;
+}
+
 // Binned check of one state for the G lanes of each group of a warp (every
 // lane of the warp calls it; dead groups pass alive = false): the candidates
 // of the at most two cell rows the state's disk overlaps, strided over the
@@ -368,6 +378,7 @@ struct TrajJob {
     float2* coefB;
     long long coef_base;
     float* jfree;
+    int* vfirst;                  // first speed-violating step per sample (speed limits on), or null
     const BinView* bins;          // fused check (traj_sample<.., true>)
     float* stage;                 // this thread's slot 0 of a staging area (stride stage_th), or null
 };
@@ -418,12 +429,18 @@ __device__ __forceinline__ FusedOut traj_sample(const DevCfg& c, const TrajJob& 
 
     bool alive = valid;
     int fh = -1;
+    int vbad = -1;                       // first state h >= 1 whose speed is outside the limits
     bool all_dead = false;
     float rem = (float)T;                // T - h, exact in FP32
     for (int h = 0; h < T; ++h) {
         float sp, cp;
         sincos_r(ph, sp, cp);
+        if (c.vlim && h > 0 && vbad < 0 && !(v >= c.v_lo && v <= c.v_hi)) vbad = h;
         if constexpr (FUSED) {
+            if (vbad == h && alive) {    // discarded here, as by a collision
+                alive = false;
+                fh = h;
+            }
             float4 A;
             float2 B;
             coef_rows(c, x, y, sp, cp, A, B);
@@ -451,8 +468,15 @@ __device__ __forceinline__ FusedOut traj_sample(const DevCfg& c, const TrajJob& 
             }
         }
         float s[NIN];
-        s[0] = (gxi - x) * c.idxi;
-        s[1] = (geta - y) * c.ideta;
+        if (c.body_frame) {
+            // goal offset in the vehicle's frame at t+h
+            const float dgx = gxi - x, dgy = geta - y;
+            s[0] = fmaf(cp, dgx, __fmul_rn(sp, dgy)) * c.idxi;
+            s[1] = fmaf(-sp, dgx, __fmul_rn(cp, dgy)) * c.ideta;
+        } else {
+            s[0] = (gxi - x) * c.idxi;
+            s[1] = (geta - y) * c.ideta;
+        }
         s[2] = wrap_pi(gph - ph) * c.idphi;
         s[3] = (gv - v) * c.idv;
         s[4] = ap0;
@@ -534,7 +558,12 @@ __device__ __forceinline__ FusedOut traj_sample(const DevCfg& c, const TrajJob& 
     FusedOut out;
     out.first_hit = fh;
     out.cost = __int_as_float(0x7f800000);
+    if (c.vlim && T > 0 && vbad < 0 && !(v >= c.v_lo && v <= c.v_hi)) vbad = T;
     if constexpr (FUSED) {
+        if (!all_dead && vbad == T && alive) {
+            alive = false;
+            fh = T;
+        }
         if (!all_dead) {
             float sp, cp;
             sincos_r(ph, sp, cp);
@@ -553,6 +582,7 @@ __device__ __forceinline__ FusedOut traj_sample(const DevCfg& c, const TrajJob& 
                      + c.w_v * fabsf(v - gv) + c.w_effort * E * invT;
         }
     } else if (writer) {
+        if (job.vfirst) job.vfirst[n] = vbad;
         float sp, cp;
         sincos_r(ph, sp, cp);
         if (job.traj) job.traj[T * job.rec_stride + rec] = make_float4(x, y, ph, v);
@@ -592,6 +622,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) traj_kernel(const RolloutArgs a
     job.coefB = a.coefB;
     job.coef_base = 0;
     job.jfree = a.jfree;
+    job.vfirst = a.c.vlim ? a.vfirst : nullptr;
     job.bins = nullptr;
     job.stage = stage_all + tid;
     // staged parameter generation pays at W = 32 (measured on GB300: 11 %
@@ -628,6 +659,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) fused_kernel(const RolloutArgs 
     job.coefB = nullptr;
     job.coef_base = 0;
     job.jfree = nullptr;
+    job.vfirst = nullptr;
     job.bins = &a.bins;
     job.stage = nullptr;
     const bool valid = n < a.N;
@@ -700,6 +732,7 @@ __global__ void __launch_bounds__(32) reroll_epilogue_kernel(const RolloutArgs a
     job.coefB = nullptr;
     job.coef_base = 0;
     job.jfree = nullptr;
+    job.vfirst = nullptr;
     job.bins = nullptr;
     job.stage = nullptr;
     if (e.trajectory || e.controls) traj_sample<W, G>(a.c, job, idx, true, lane % G, hrows + (lane / G) * W);
@@ -962,6 +995,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) collide_block_kernel(const Roll
             if (L == 0) break;
         }
         if (owner) {
+            fh = discard_step(a.vfirst, n, fh);
             float J = __int_as_float(0x7f800000);
             unsigned long long key;
             if (fh < 0) {
@@ -1119,6 +1153,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) collide_warp_kernel(const Rollo
             if (live == 0u) break;
         }
         if (mine) {
+            fh = discard_step(a.vfirst, n, fh);
             float J = __int_as_float(0x7f800000);
             unsigned long long key;
             if (fh < 0) {
@@ -1222,7 +1257,7 @@ __global__ void __launch_bounds__(S * 32, MINB) collide_slice_kernel(const Rollo
         __syncthreads();
         if (warp == 0 && mine) {
             const int d = dead_at[lane];
-            const int fh = d <= T ? d : -1;
+            const int fh = discard_step(a.vfirst, n, d <= T ? d : -1);
             float J = __int_as_float(0x7f800000);
             unsigned long long key;
             if (fh < 0) {

@@ -30,7 +30,8 @@ class npp_config(C.Structure):
         "half_len", "half_wid", "c_off", "dxi_n", "deta_n", "dphi_n", "dv_n",
         "w_pos", "w_phi", "w_v", "w_effort")] + [
         ("n_in", C.c_int32), ("width", C.c_int32), ("max_N", C.c_int32),
-        ("max_T", C.c_int32), ("max_M", C.c_int32)]
+        ("max_T", C.c_int32), ("max_M", C.c_int32),
+        ("feature_frame", C.c_int32), ("v_limits", C.c_int32), ("v_min", C.c_float), ("v_max", C.c_float)]
 
 
 class npp_state(C.Structure):
@@ -161,6 +162,10 @@ def make_config(p: dict, max_N: int, max_T: int, max_M: int) -> npp_config:
     c.n_in = widths[0]
     c.width = widths[1]
     c.max_N, c.max_T, c.max_M = int(max_N), int(max_T), int(max_M)
+    c.feature_frame = int(p.get("feature_frame", 0))
+    c.v_limits = int(p.get("v_limits", 0))
+    c.v_min = float(p.get("v_min", 0.0))
+    c.v_max = float(p.get("v_max", 0.0))
     return c
 
 

@@ -314,7 +314,7 @@ __device__ __forceinline__ float4 live_box(const DevCfg& c, float4 ca, float2 cb
                        __shfl_sync(FULL, ymx, 0));
 }
 
-template <int W, int G, int NW>
+template <int W, int G, int NW, bool VAR = false>
 __global__ void __launch_bounds__(NW * 32) batch_traj_kernel(const BatchArgs b, int wi)
 {
     constexpr int B = TrajKernel<W, G, NW>::B;
@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(NW * 32) batch_traj_kernel(const BatchArgs b, 
         job.jfree = b.jfree + s.samp_off;
         job.vfirst = b.vfirst ? b.vfirst + s.samp_off : nullptr;
         constexpr int STAGE_TH = W == 32 ? NW * 32 : 0;     // as traj_kernel
-        traj_sample<W, G, false, STAGE_TH>(b.c, job, n, n < s.N, gl, hx_all + bi * W);
+        traj_sample<W, G, false, STAGE_TH, VAR>(b.c, job, n, n < s.N, gl, hx_all + bi * W);
     }
 }
 
@@ -556,7 +556,7 @@ __global__ void __launch_bounds__(256) batch_binned_kernel(const BatchArgs b)
 // trajectory (EV frame, then converted to the world frame in place).  Every
 // group of G lanes of the warp computes the winner (the warp-wide shuffles
 // need all lanes); the groups write identical values.
-template <int W, int G>
+template <int W, int G, bool VAR>
 __device__ void batch_reroll(const BatchArgs& b, const SceneDev& s, int idx, float* hrows)
 {
     const int lane = threadIdx.x & 31;
@@ -579,7 +579,7 @@ __device__ void batch_reroll(const BatchArgs& b, const SceneDev& s, int idx, flo
     job.coef_base = 0;
     job.jfree = nullptr;
     job.vfirst = nullptr;
-    traj_sample<W, G>(b.c, job, idx, true, lane % G, hrows + (lane / G) * W);
+    traj_sample<W, G, false, 0, VAR>(b.c, job, idx, true, lane % G, hrows + (lane / G) * W);
 }
 
 __global__ void batch_epilogue_kernel(const BatchArgs b)
@@ -602,10 +602,11 @@ __global__ void batch_epilogue_kernel(const BatchArgs b)
         o->first_hit = fh;
         o->reserved[0] = o->reserved[1] = o->reserved[2] = o->reserved[3] = 0;
     }
+    const bool var = uses_variants(b.c);
     switch (s.width) {
-    case 16: batch_reroll<16, 8>(b, s, idx, hrow); break;
-    case 32: batch_reroll<32, 16>(b, s, idx, hrow); break;
-    default: batch_reroll<64, 32>(b, s, idx, hrow); break;
+    case 16: if (var) batch_reroll<16, 8, true>(b, s, idx, hrow); else batch_reroll<16, 8, false>(b, s, idx, hrow); break;
+    case 32: if (var) batch_reroll<32, 16, true>(b, s, idx, hrow); else batch_reroll<32, 16, false>(b, s, idx, hrow); break;
+    default: if (var) batch_reroll<64, 32, true>(b, s, idx, hrow); else batch_reroll<64, 32, false>(b, s, idx, hrow); break;
     }
     __syncwarp();
     // world frame; rows after an infeasible winner's first collision repeat
@@ -812,18 +813,26 @@ void launch_batch_collide(npp_batch* B, const BatchArgs& b, cudaStream_t s)
     batch_collide_kernel<S><<<B->grid_collide, BatchCollide<S>::THREADS, smem, s>>>(b);
 }
 
+template <int NW, bool VAR>
+void launch_batch_traj_v(npp_batch* B, const BatchArgs& b, cudaStream_t s)
+{
+    if (B->n_torder[0]) {
+        ensure_smem(batch_traj_kernel<16, 8, NW, VAR>, batch_stage_bytes<16, 8>(NW));
+        batch_traj_kernel<16, 8, NW, VAR><<<B->grid_traj[0], NW * 32, batch_stage_bytes<16, 8>(NW), s>>>(b, 0);
+    }
+    if (B->n_torder[1]) {
+        ensure_smem(batch_traj_kernel<32, 16, NW, VAR>, batch_stage_bytes<32, 16>(NW));
+        batch_traj_kernel<32, 16, NW, VAR><<<B->grid_traj[1], NW * 32, batch_stage_bytes<32, 16>(NW), s>>>(b, 1);
+    }
+    if (B->n_torder[2]) batch_traj_kernel<64, 32, NW, VAR><<<B->grid_traj[2], NW * 32, 0, s>>>(b, 2);
+}
+
+// rollout variants (body-frame features, speed limits) in their own kernels
 template <int NW>
 void launch_batch_traj(npp_batch* B, const BatchArgs& b, cudaStream_t s)
 {
-    if (B->n_torder[0]) {
-        ensure_smem(batch_traj_kernel<16, 8, NW>, batch_stage_bytes<16, 8>(NW));
-        batch_traj_kernel<16, 8, NW><<<B->grid_traj[0], NW * 32, batch_stage_bytes<16, 8>(NW), s>>>(b, 0);
-    }
-    if (B->n_torder[1]) {
-        ensure_smem(batch_traj_kernel<32, 16, NW>, batch_stage_bytes<32, 16>(NW));
-        batch_traj_kernel<32, 16, NW><<<B->grid_traj[1], NW * 32, batch_stage_bytes<32, 16>(NW), s>>>(b, 1);
-    }
-    if (B->n_torder[2]) batch_traj_kernel<64, 32, NW><<<B->grid_traj[2], NW * 32, 0, s>>>(b, 2);
+    if (uses_variants(b.c)) launch_batch_traj_v<NW, true>(B, b, s);
+    else launch_batch_traj_v<NW, false>(B, b, s);
 }
 
 }  // namespace

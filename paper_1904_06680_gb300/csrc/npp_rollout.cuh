@@ -394,8 +394,11 @@ struct FusedOut {
 // group (lane gl); hrow is the group's W-float shared exchange row.  FUSED:
 // every state h is checked against the binned points at the top of its step
 // (before the controls that leave it) and the loop ends once every group of
-// the warp has collided; nothing is stored.
-template <int W, int G, bool FUSED = false, int STAGE_TH = 0>
+// the warp has collided; nothing is stored.  VAR: the variants of c
+// (body-frame goal offsets, speed limits) are honoured; without it the
+// kernel is the plain rollout, and the launchers pick VAR whenever c turns
+// a variant on.
+template <int W, int G, bool FUSED = false, int STAGE_TH = 0, bool VAR = false>
 __device__ __forceinline__ FusedOut traj_sample(const DevCfg& c, const TrajJob& job, int n, bool valid,
                                                 int gl, float* hrow)
 {
@@ -435,7 +438,9 @@ __device__ __forceinline__ FusedOut traj_sample(const DevCfg& c, const TrajJob& 
     for (int h = 0; h < T; ++h) {
         float sp, cp;
         sincos_r(ph, sp, cp);
-        if (c.vlim && h > 0 && vbad < 0 && !(v >= c.v_lo && v <= c.v_hi)) vbad = h;
+        if constexpr (VAR) {
+            if (c.vlim && h > 0 && vbad < 0 && !(v >= c.v_lo && v <= c.v_hi)) vbad = h;
+        }
         if constexpr (FUSED) {
             if (vbad == h && alive) {    // discarded here, as by a collision
                 alive = false;
@@ -468,7 +473,7 @@ __device__ __forceinline__ FusedOut traj_sample(const DevCfg& c, const TrajJob& 
             }
         }
         float s[NIN];
-        if (c.body_frame) {
+        if (VAR && c.body_frame) {
             // goal offset in the vehicle's frame at t+h
             const float dgx = gxi - x, dgy = geta - y;
             s[0] = fmaf(cp, dgx, __fmul_rn(sp, dgy)) * c.idxi;
@@ -558,7 +563,9 @@ __device__ __forceinline__ FusedOut traj_sample(const DevCfg& c, const TrajJob& 
     FusedOut out;
     out.first_hit = fh;
     out.cost = __int_as_float(0x7f800000);
-    if (c.vlim && T > 0 && vbad < 0 && !(v >= c.v_lo && v <= c.v_hi)) vbad = T;
+    if constexpr (VAR) {
+        if (c.vlim && T > 0 && vbad < 0 && !(v >= c.v_lo && v <= c.v_hi)) vbad = T;
+    }
     if constexpr (FUSED) {
         if (!all_dead && vbad == T && alive) {
             alive = false;
@@ -582,7 +589,9 @@ __device__ __forceinline__ FusedOut traj_sample(const DevCfg& c, const TrajJob& 
                      + c.w_v * fabsf(v - gv) + c.w_effort * E * invT;
         }
     } else if (writer) {
-        if (job.vfirst) job.vfirst[n] = vbad;
+        if constexpr (VAR) {
+            if (job.vfirst) job.vfirst[n] = vbad;
+        }
         float sp, cp;
         sincos_r(ph, sp, cp);
         if (job.traj) job.traj[T * job.rec_stride + rec] = make_float4(x, y, ph, v);
@@ -596,7 +605,7 @@ __device__ __forceinline__ FusedOut traj_sample(const DevCfg& c, const TrajJob& 
     return out;
 }
 
-template <int W, int G, int NW, int MINB = 1>
+template <int W, int G, int NW, int MINB = 1, bool VAR = false>
 __global__ void __launch_bounds__(NW * 32, MINB) traj_kernel(const RolloutArgs a)
 {
     constexpr int B = TrajKernel<W, G, NW>::B;
@@ -628,12 +637,12 @@ __global__ void __launch_bounds__(NW * 32, MINB) traj_kernel(const RolloutArgs a
     // staged parameter generation pays at W = 32 (measured on GB300: 11 %
     // faster at T = 40); at W = 16 and 64 the direct load is faster
     constexpr int STAGE_TH = W == 32 ? NW * 32 : 0;
-    traj_sample<W, G, false, STAGE_TH>(a.c, job, n, n < a.N, gl, hx_all + b * W);
+    traj_sample<W, G, false, STAGE_TH, VAR>(a.c, job, n, n < a.N, gl, hx_all + b * W);
 }
 
 // Trajectories with the binned check fused in: per sample its first
 // collision and cost, folded into the (class, cost, index) minimum.
-template <int W, int G, int NW, int MINB = 1>
+template <int W, int G, int NW, int MINB = 1, bool VAR = false>
 __global__ void __launch_bounds__(NW * 32, MINB) fused_kernel(const RolloutArgs a)
 {
     constexpr int B = TrajKernel<W, G, NW>::B;
@@ -663,7 +672,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) fused_kernel(const RolloutArgs 
     job.bins = &a.bins;
     job.stage = nullptr;
     const bool valid = n < a.N;
-    const FusedOut r = traj_sample<W, G, true>(a.c, job, n, valid, gl, hx_all + b * W);
+    const FusedOut r = traj_sample<W, G, true, 0, VAR>(a.c, job, n, valid, gl, hx_all + b * W);
     unsigned long long key = ~0ull;
     if (valid && gl == 0) {
         if (r.first_hit < 0)
@@ -694,7 +703,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) fused_kernel(const RolloutArgs 
 // world frame (rows after an infeasible winner's first collision repeat the
 // colliding state, its controls there are zero) and regenerates its
 // parameters (warm start, proposal or isotropic sample).
-template <int W, int G>
+template <int W, int G, bool VAR = false>
 __global__ void __launch_bounds__(32) reroll_epilogue_kernel(const RolloutArgs a, const EpilogueArgs e)
 {
     __shared__ __align__(16) float hrows[32 / G * W];
@@ -735,7 +744,8 @@ __global__ void __launch_bounds__(32) reroll_epilogue_kernel(const RolloutArgs a
     job.vfirst = nullptr;
     job.bins = nullptr;
     job.stage = nullptr;
-    if (e.trajectory || e.controls) traj_sample<W, G>(a.c, job, idx, true, lane % G, hrows + (lane / G) * W);
+    if (e.trajectory || e.controls)
+        traj_sample<W, G, false, 0, VAR>(a.c, job, idx, true, lane % G, hrows + (lane / G) * W);
     __syncwarp();
     float s0, c0;
     sincosf(si.phi0, &s0, &c0);
@@ -1297,31 +1307,35 @@ inline cudaError_t ensure_smem(KernelFn fn, int smem)
     return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
-template <int W, int G, int NW, int MINB = 1>
+// Whether a configuration turns on a rollout variant (VAR kernels).
+__host__ __device__ inline bool uses_variants(const DevCfg& c) { return c.body_frame != 0 || c.vlim != 0; }
+
+template <int W, int G, int NW, int MINB = 1, bool VAR = false>
 cudaError_t launch_traj(const RolloutArgs& a, cudaStream_t stream)
 {
     using K = TrajKernel<W, G, NW>;
     const int grid = (a.N + K::B - 1) / K::B;
     const int smem = W == 32 ? LaneNet<W, G>::SLOTS * K::THREADS * (int)sizeof(float) : 0;
-    cudaError_t e = ensure_smem(traj_kernel<W, G, NW, MINB>, smem);
+    cudaError_t e = ensure_smem(traj_kernel<W, G, NW, MINB, VAR>, smem);
     if (e != cudaSuccess) return e;
-    traj_kernel<W, G, NW, MINB><<<grid, K::THREADS, smem, stream>>>(a);
+    traj_kernel<W, G, NW, MINB, VAR><<<grid, K::THREADS, smem, stream>>>(a);
     return cudaGetLastError();
 }
 
-template <int W, int G, int NW, int MINB = 1>
+template <int W, int G, int NW, int MINB = 1, bool VAR = false>
 cudaError_t launch_fused(const RolloutArgs& a, cudaStream_t stream)
 {
     using K = TrajKernel<W, G, NW>;
     const int grid = (a.N + K::B - 1) / K::B;
-    fused_kernel<W, G, NW, MINB><<<grid, K::THREADS, 0, stream>>>(a);
+    fused_kernel<W, G, NW, MINB, VAR><<<grid, K::THREADS, 0, stream>>>(a);
     return cudaGetLastError();
 }
 
 template <int W, int G>
 cudaError_t launch_reroll(const RolloutArgs& a, const EpilogueArgs& e, cudaStream_t stream)
 {
-    reroll_epilogue_kernel<W, G><<<1, 32, 0, stream>>>(a, e);
+    if (uses_variants(a.c)) reroll_epilogue_kernel<W, G, true><<<1, 32, 0, stream>>>(a, e);
+    else reroll_epilogue_kernel<W, G, false><<<1, 32, 0, stream>>>(a, e);
     return cudaGetLastError();
 }
 

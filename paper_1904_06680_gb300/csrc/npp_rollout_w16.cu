@@ -8,6 +8,8 @@ namespace npp {
 
 cudaError_t launch_traj_w16(const RolloutArgs& a, cudaStream_t s, int variant)
 {
+    // rollout variants run in the default shape
+    if (uses_variants(a.c)) return launch_traj<16, 8, 4, 4, true>(a, s);
     switch (variant) {
     case 1: return launch_traj<16, 4, 8>(a, s);
     case 2: return launch_traj<16, 8, 8>(a, s);
@@ -18,6 +20,7 @@ cudaError_t launch_traj_w16(const RolloutArgs& a, cudaStream_t s, int variant)
 
 cudaError_t launch_fused_w16(const RolloutArgs& a, cudaStream_t s, int variant)
 {
+    if (uses_variants(a.c)) return launch_fused<16, 8, 4, 4, true>(a, s);
     switch (variant) {
     case 1: return launch_fused<16, 4, 8>(a, s);
     case 2: return launch_fused<16, 8, 8>(a, s);

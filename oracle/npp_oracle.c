@@ -80,6 +80,14 @@ typedef struct {
     int32_t feature_frame;    /* 0: EV frame at t, 1: body frame at t+h */
     int32_t v_limits;         /* 1: speed limits on                     */
     double v_min, v_max;      /* [m/s]                                  */
+    /* general footprint (Sect. II-D: the EV as an arbitrarily refined
+     * polytope, convex or not): the union of fp_pieces convex polygons, each
+     * given by its vertices counter-clockwise in the vehicle's frame (x along
+     * the heading, origin at the reference point).  0 pieces: the rectangle
+     * above. */
+    int32_t fp_pieces;
+    const int32_t* fp_start;  /* [fp_pieces + 1] first vertex of each piece */
+    const double* fp_verts;   /* [fp_start[fp_pieces]][2]                */
 } orc_config;
 
 enum { ORC_OK = 0, ORC_INFEASIBLE = 2, ORC_INVALID = 1 };
@@ -342,10 +350,16 @@ void orc_euler_step(const orc_config* c, const double z[4], const double a[2], d
  * Returns 1 when some point satisfies all four strict inequalities.  When
  * n_clear / n_near are given, also counts points that are inside by more
  * than `margin` and points whose decision lies within `margin` of a face. */
+static int collide_footprint(const orc_config* c, double x, double y, double phi,
+                             const double* obs_ev, int M, double tau, double margin,
+                             int* n_clear, int* n_near);
+
 int orc_collide(const orc_config* c, double x, double y, double phi,
                 const double* obs_ev, int M, double tau, double margin,
                 int* n_clear, int* n_near)
 {
+    if (c->fp_pieces > 0)
+        return collide_footprint(c, x, y, phi, obs_ev, M, tau, margin, n_clear, n_near);
     double cp = cos(phi), sp = sin(phi);
     double A[4][2] = { { cp, sp }, { -cp, -sp }, { -sp, cp }, { sp, -cp } };
     double b[4] = { c->c_off + c->half_len, c->half_len - c->c_off,
@@ -365,6 +379,52 @@ int orc_collide(const orc_config* c, double x, double y, double phi,
         if (inside) hit = 1;
         if (worst < -margin) clear++;
         else if (worst <= margin) near++;
+        if (hit && !n_clear && !n_near) return 1;
+    }
+    if (n_clear) *n_clear = clear;
+    if (n_near) *n_near = near;
+    return hit;
+}
+
+/* The same check for a general footprint: point j at time t+h is moved into
+ * the vehicle's frame, q = R(-phi) (p_j(h) - [x, y]), and is inside a convex
+ * piece when it lies strictly to the left of every directed edge v_i ->
+ * v_{i+1} of that counter-clockwise polygon (cross product > 0); a
+ * collision is a point inside some piece.  For the margin counts a point's
+ * depth is the largest over pieces of its smallest distance to an edge line
+ * (positive inside). */
+static int collide_footprint(const orc_config* c, double x, double y, double phi,
+                             const double* obs_ev, int M, double tau, double margin,
+                             int* n_clear, int* n_near)
+{
+    double cp = cos(phi), sp = sin(phi);
+    int hit = 0, clear = 0, near = 0;
+    for (int j = 0; j < M; ++j) {
+        const double* p = obs_ev + 4 * j;
+        double dx = p[0] + tau * p[2] - x;
+        double dy = p[1] + tau * p[3] - y;
+        double qx = cp * dx + sp * dy, qy = -sp * dx + cp * dy;
+        double depth = -INFINITY;
+        int inside_any = 0;
+        for (int k = 0; k < c->fp_pieces; ++k) {
+            int b = c->fp_start[k], e = c->fp_start[k + 1], n = e - b;
+            int inside = 1;
+            double dmin = INFINITY;
+            for (int i = 0; i < n; ++i) {
+                const double* v0 = c->fp_verts + 2 * (b + i);
+                const double* v1 = c->fp_verts + 2 * (b + (i + 1) % n);
+                double ex = v1[0] - v0[0], ey = v1[1] - v0[1];
+                double cr = ex * (qy - v0[1]) - ey * (qx - v0[0]);
+                if (!(cr > 0.0)) inside = 0;
+                double d = cr / hypot(ex, ey);
+                if (d < dmin) dmin = d;
+            }
+            if (inside) inside_any = 1;
+            if (dmin > depth) depth = dmin;
+        }
+        if (inside_any) hit = 1;
+        if (depth > margin) clear++;
+        else if (depth >= -margin) near++;
         if (hit && !n_clear && !n_near) return 1;
     }
     if (n_clear) *n_clear = clear;

@@ -23,14 +23,17 @@ class OrcConfig(C.Structure):
         "half_len", "half_wid", "c_off", "dxi_n", "deta_n", "dphi_n", "dv_n",
         "w_pos", "w_phi", "w_v", "w_effort")] + [
         ("n_layers", C.c_int32), ("widths", C.c_int32 * (MAX_LAYERS + 1)),
-        ("feature_frame", C.c_int32), ("v_limits", C.c_int32), ("v_min", C.c_double), ("v_max", C.c_double)]
+        ("feature_frame", C.c_int32), ("v_limits", C.c_int32), ("v_min", C.c_double), ("v_max", C.c_double),
+        ("fp_pieces", C.c_int32), ("fp_start", C.POINTER(C.c_int32)), ("fp_verts", C.POINTER(C.c_double))]
 
 N_FLOAT = 18
 
 
 def make_config(p: dict) -> OrcConfig:
     """Preset dict -> FP64 config; the variant keys (feature_frame, v_limits,
-    v_min, v_max) are optional and default to off."""
+    v_min, v_max, footprint) are optional and default to off.  footprint: a
+    list of convex pieces, each an array of counter-clockwise vertices (x, y)
+    in the vehicle's frame."""
     c = OrcConfig()
     for name, _ in OrcConfig._fields_[:N_FLOAT]:
         setattr(c, name, float(p[name]))
@@ -42,6 +45,15 @@ def make_config(p: dict) -> OrcConfig:
     c.v_limits = int(p.get("v_limits", 0))
     c.v_min = float(p.get("v_min", 0.0))
     c.v_max = float(p.get("v_max", 0.0))
+    fp = p.get("footprint")
+    if fp:
+        pieces = [np.asarray(q, np.float64).reshape(-1, 2) for q in fp]
+        start = np.ascontiguousarray(np.cumsum([0] + [len(q) for q in pieces]), np.int32)
+        verts = np.ascontiguousarray(np.concatenate(pieces))
+        c._keep = (start, verts)                  # alive as long as the config
+        c.fp_pieces = len(pieces)
+        c.fp_start = start.ctypes.data_as(C.POINTER(C.c_int32))
+        c.fp_verts = verts.ctypes.data_as(C.POINTER(C.c_double))
     return c
 
 

@@ -143,6 +143,25 @@ npp_status npp_destroy(npp_handle* h);
  * failure of any call.  The pointer stays valid until the next failure. */
 const char* npp_last_error(const npp_handle* h);
 
+/* General vehicle footprint (Sect. II-D: the EV modelled as an arbitrarily
+ * refined polytope, convex or non-convex, checked by the linear inequalities
+ * A(phi)(p - [x, y]) < b(phi)): the union of n_pieces convex polygons.
+ * Piece k has the vertices verts_host[2*piece_start_host[k] ..
+ * 2*piece_start_host[k+1]) as (x, y) pairs in the vehicle's frame (x along
+ * the heading, origin at the reference point), counter-clockwise and
+ * strictly convex; piece_start_host[0] = 0.  A point collides when it is
+ * strictly inside some piece.  At most 16 pieces and 64 vertices in total.
+ * Host arrays, copied synchronously: call between plan steps, and before
+ * npp_loop_create.  n_pieces = 0 restores the rectangle of the config.  The
+ * plan-step, closed-loop, hill-climb and proposal entry points of h then use
+ * the polygon check (per-step spatial bins; collide_variant 0..4 selects a
+ * brute-force check over every point instead, with identical results);
+ * npp_batch_create on such a handle returns NPP_UNSUPPORTED.
+ * NPP_INVALID_ARG for a piece that is not strictly convex and
+ * counter-clockwise, winds more than once, or has fewer than 3 vertices. */
+npp_status npp_set_footprint(npp_handle* h, const float* verts_host, const int32_t* piece_start_host,
+                             int32_t n_pieces);
+
 /* Number of network parameters of cfg's network, or -1 if unsupported. */
 int32_t npp_n_theta(const npp_config* cfg);
 

@@ -172,6 +172,26 @@ npp_status run_rollout(npp_handle* h, RolloutArgs& a, cudaStream_t s, bool allow
     a.coefB = h->d_coefB;
     a.work = h->d_work;
     *fused = false;
+    if (h->fp_faces > 0) {
+        // general footprint: grids sized by its radius (side stream, as
+        // below), trajectories without the rectangle's rows, polygon check
+        a.coefA = nullptr;
+        a.coefB = nullptr;
+        a.poly.faces = h->d_fp;
+        a.poly.n_faces = h->fp_faces;
+        a.poly.brute = (h->collide_variant >= 0 && h->collide_variant < COLLIDE_BINNED) ? 1 : 0;
+        if (h->timing) CUDA_TRY(h, record_event(h->ev[0], s));
+        CUDA_TRY(h, cudaEventRecord(h->fork_ev, s));
+        CUDA_TRY(h, cudaStreamWaitEvent(h->side, h->fork_ev, 0));
+        CUDA_TRY(h, build_bins_radius(a, h->fp_radius, h->d_bins, h->side));
+        CUDA_TRY(h, cudaEventRecord(h->join_ev, h->side));
+        CUDA_TRY(h, launch_traj(h, a, s));
+        if (h->timing) CUDA_TRY(h, record_event(h->ev[1], s));
+        CUDA_TRY(h, cudaStreamWaitEvent(s, h->join_ev, 0));
+        CUDA_TRY(h, launch_collide_poly(a, s));
+        if (h->timing) CUDA_TRY(h, record_event(h->ev[2], s));
+        return NPP_OK;
+    }
     // automatic choice (measured on GB300, course workload): few samples ->
     // items checked by 4 warps on point slices; medium -> 2 warps; many
     // samples -> one warp per item keeps enough items in flight; many points
@@ -389,7 +409,7 @@ npp_status npp_destroy(npp_handle* h)
     if (!h) return NPP_OK;
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
-    void* ptrs[] = { h->d_key, h->d_traj, h->d_ctrl, h->d_jfree, h->d_vfirst, h->d_coefA, h->d_coefB, h->d_work,
+    void* ptrs[] = { h->d_key, h->d_traj, h->d_ctrl, h->d_jfree, h->d_vfirst, h->d_fp, h->d_coefA, h->d_coefB, h->d_work,
                      h->d_pXY, h->d_pV, h->d_bins,
                      h->d_obs, h->d_warm, h->d_sigma, h->d_best, h->d_params, h->d_controls, h->d_trajectory,
                      h->d_costs, h->d_fh };
@@ -567,6 +587,57 @@ npp_status npp_rollout_params(npp_handle* h, const npp_state* state, const npp_g
     bool fused = false;
     if ((st = run_rollout(h, a, s, !sample_traj_dev && !sample_ctrl_dev, &fused)) != NPP_OK) return st;
     if (h->timing) CUDA_TRY(h, record_event(h->ev[3], s));
+    return NPP_OK;
+}
+
+npp_status npp_set_footprint(npp_handle* h, const float* verts_host, const int32_t* piece_start_host,
+                             int32_t n_pieces)
+{
+    if (!h) return fail(nullptr, NPP_INVALID_ARG, "handle is NULL");
+    if (n_pieces < 0 || n_pieces > FP_MAX_PIECES)
+        return fail(h, NPP_INVALID_ARG, "n_pieces is 0..%d", FP_MAX_PIECES);
+    if (n_pieces == 0) {
+        h->fp_faces = 0;
+        return NPP_OK;
+    }
+    if (!verts_host || !piece_start_host) return fail(h, NPP_INVALID_ARG, "vertices and piece starts required");
+    if (piece_start_host[0] != 0) return fail(h, NPP_INVALID_ARG, "piece_start[0] must be 0");
+    const int nv = piece_start_host[n_pieces];
+    if (nv > FP_MAX_FACES) return fail(h, NPP_INVALID_ARG, "at most %d vertices in total", FP_MAX_FACES);
+    float4 faces[FP_MAX_FACES];
+    double radius = 0.0;
+    const double TWO_PI = 6.283185307179586;
+    for (int k = 0; k < n_pieces; ++k) {
+        const int b = piece_start_host[k], e = piece_start_host[k + 1], n = e - b;
+        if (n < 3 || b < 0 || e > nv) return fail(h, NPP_INVALID_ARG, "piece %d needs >= 3 vertices", k);
+        double turn = 0.0;
+        for (int i = 0; i < n; ++i) {
+            const float* v0 = verts_host + 2 * (b + i);
+            const float* v1 = verts_host + 2 * (b + (i + 1) % n);
+            const float* v2 = verts_host + 2 * (b + (i + 2) % n);
+            if (!std::isfinite(v0[0]) || !std::isfinite(v0[1]))
+                return fail(h, NPP_INVALID_ARG, "non-finite vertex in piece %d", k);
+            const double ax = (double)v1[0] - v0[0], ay = (double)v1[1] - v0[1];
+            const double bx = (double)v2[0] - v1[0], by = (double)v2[1] - v1[1];
+            const double cr = ax * by - ay * bx;
+            if (!(cr > 0.0))
+                return fail(h, NPP_INVALID_ARG, "piece %d is not strictly convex and counter-clockwise", k);
+            turn += std::atan2(cr, ax * bx + ay * by);
+            const double len = std::sqrt(ax * ax + ay * ay);
+            // outward unit normal of edge v0 -> v1 and its offset
+            const double nx = ay / len, ny = -ax / len;
+            faces[b + i] = make_float4((float)nx, (float)ny, (float)(nx * v0[0] + ny * v0[1]),
+                                       i == n - 1 ? 1.0f : 0.0f);
+            radius = std::fmax(radius, std::sqrt((double)v0[0] * v0[0] + (double)v0[1] * v0[1]));
+        }
+        if (std::fabs(turn - TWO_PI) > 1e-6)
+            return fail(h, NPP_INVALID_ARG, "piece %d winds more than once", k);
+    }
+    CUDA_TRY(h, cudaSetDevice(h->device));
+    if (!h->d_fp) CUDA_TRY(h, cudaMalloc((void**)&h->d_fp, sizeof(float4) * FP_MAX_FACES));
+    CUDA_TRY(h, cudaMemcpy(h->d_fp, faces, sizeof(float4) * nv, cudaMemcpyHostToDevice));
+    h->fp_faces = nv;
+    h->fp_radius = radius;
     return NPP_OK;
 }
 

@@ -843,6 +843,8 @@ npp_status npp_batch_create(npp_handle* h, const npp_scene* scenes, int32_t S, n
 {
     if (!h || !out || !scenes || S < 1) return fail(h, NPP_INVALID_ARG, "batch: bad arguments");
     *out = nullptr;
+    if (h->fp_faces > 0)
+        return fail(h, NPP_UNSUPPORTED, "batch: a general footprint is checked by the single-scene entry points only");
     long long pairs = 0, rows = 0, samples = 0, tiles_total = 0, bin_ints = 0, bin_pts = 0, items = 0;
     int max_pairs = 0;
     for (int i = 0; i < S; ++i) {

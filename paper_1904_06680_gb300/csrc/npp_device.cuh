@@ -253,6 +253,18 @@ struct BinView {
     int M;
 };
 
+// General footprint: the union of convex pieces, each the intersection of
+// half-planes n . q < b in the vehicle's frame (q relative to the reference
+// point, x along the heading), faces of one piece consecutive, w = 1 on the
+// last face of a piece.
+constexpr int FP_MAX_FACES = 64;
+constexpr int FP_MAX_PIECES = 16;
+struct PolyView {
+    const float4* faces;   // [n_faces] (nx, ny, b, last) with |n| = 1
+    int n_faces;           // 0: the rectangle
+    int brute;             // 1: every point each step (no grid cells)
+};
+
 __device__ __forceinline__ int bin_cell(float x, const BinView& g)
 {
     const float f = floorf((x - g.x0) * g.inv_cell);
@@ -371,6 +383,7 @@ struct RolloutArgs {
     float4* pXY;                       // EV-frame point pairs in global memory (when the
     float4* pV;                        // points exceed shared memory), [ceil(M/2)]
     BinView bins;                      // per-step grids (binned and fused collision checks)
+    PolyView poly;                     // general footprint (polygon checks)
 };
 
 __device__ __forceinline__ StepIn step_in(const RolloutArgs& a)
@@ -432,6 +445,8 @@ size_t binned_workspace_bytes(int max_T, int max_M);
 cudaError_t build_bins(RolloutArgs& a, float half_len, float half_wid, float c_off, void* workspace,
                        cudaStream_t s);          // fills a.bins
 cudaError_t launch_collide_binned(const RolloutArgs& a, cudaStream_t s);
+cudaError_t launch_collide_poly(const RolloutArgs& a, cudaStream_t s);
+cudaError_t build_bins_radius(RolloutArgs& a, double radius, void* workspace, cudaStream_t s);
 cudaError_t launch_epilogue(const EpilogueArgs& e, cudaStream_t s);
 void set_global_error(const char* msg);
 

@@ -27,6 +27,9 @@ struct npp_handle {
     float2* d_ctrl;                      // [max_T * max_N]
     float* d_jfree;                      // [max_N]
     int* d_vfirst;                       // [max_N] first speed-violating step (speed limits on)
+    float4* d_fp;                        // [FP_MAX_FACES] general footprint faces
+    int fp_faces;                        // 0: the rectangle of cfg
+    double fp_radius;                    // footprint's largest vertex distance
     float4* d_coefA;                     // [(max_T+1) * max_N]
     float2* d_coefB;                     // [(max_T+1) * max_N]
     unsigned* d_work;                    // persistent-kernel work counter

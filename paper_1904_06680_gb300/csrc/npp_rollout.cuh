@@ -339,9 +339,8 @@ __device__ __forceinline__ void build_step_bins(const float4* __restrict__ obs, 
 // A grid whose cell exceeds the diameter of the query disk: the rectangle's
 // circumradius plus |c_off|, plus a margin against rounding of positions of
 // O(100) m (host side).
-inline BinView make_bin_grid(float half_len, float half_wid, float c_off)
+inline BinView make_bin_grid_radius(double R)
 {
-    const double R = std::sqrt((double)half_len * half_len + (double)half_wid * half_wid) + std::fabs((double)c_off);
     const double cell = 2.0 * R + 0.25;
     BinView g;
     g.inv_cell = (float)(1.0 / cell);
@@ -351,6 +350,13 @@ inline BinView make_bin_grid(float half_len, float half_wid, float c_off)
     g.pts = nullptr;
     g.M = 0;
     return g;
+}
+
+// the rectangle lies in the disk of its circumradius plus |c_off|
+inline BinView make_bin_grid(float half_len, float half_wid, float c_off)
+{
+    return make_bin_grid_radius(std::sqrt((double)half_len * half_len + (double)half_wid * half_wid) +
+                                std::fabs((double)c_off));
 }
 
 // ------------------------------------------------------------------ traj

@@ -74,7 +74,7 @@ class npp_outputs(C.Structure):
                                           "first_hit", "sample_traj", "sample_ctrl")]
 
 
-EXPORTS = ("npp_create", "npp_destroy", "npp_last_error", "npp_n_theta", "npp_plan_step",
+EXPORTS = ("npp_create", "npp_destroy", "npp_last_error", "npp_n_theta", "npp_plan_step", "npp_set_footprint",
            "npp_plan_step_host", "npp_rollout_params", "npp_sample_params", "npp_set_timing",
            "npp_last_timing", "npp_set_option", "npp_plan_step_noalloc", "npp_loop_create",
            "npp_loop_run", "npp_loop_read", "npp_loop_log", "npp_loop_destroy", "npp_loop_samples",
@@ -112,6 +112,7 @@ def lib():
         L.npp_sample_params.argtypes = [U64, U32, U32, I32, I32, I32, P, P]
         L.npp_set_timing.argtypes = [P, I32]
         L.npp_set_option.argtypes = [P, C.c_char_p, I32]
+        L.npp_set_footprint.argtypes = [P, C.c_void_p, C.c_void_p, I32]
         L.npp_loop_create.argtypes = [P, C.POINTER(npp_state), P, I32, P, P, I32, I32, I32, U64, I32,
                                       C.POINTER(P)]
         L.npp_loop_run.argtypes = [P, I32, P]
@@ -207,6 +208,20 @@ def npp_destroy(h):
 def npp_last_error(h=None) -> str:
     r = lib().npp_last_error(h)
     return r.decode() if r else ""
+
+
+def npp_set_footprint(h, pieces):
+    """General footprint: a list of convex pieces, each an array of
+    counter-clockwise (x, y) vertices in the vehicle's frame; [] or None
+    restores the rectangle."""
+    import numpy as np
+    pieces = [np.asarray(q, np.float32).reshape(-1, 2) for q in (pieces or [])]
+    if not pieces:
+        return _check(lib().npp_set_footprint(h, None, None, 0), h)
+    start = np.ascontiguousarray(np.cumsum([0] + [len(q) for q in pieces]), np.int32)
+    verts = np.ascontiguousarray(np.concatenate(pieces), np.float32)
+    return _check(lib().npp_set_footprint(h, verts.ctypes.data_as(C.c_void_p), start.ctypes.data_as(C.c_void_p),
+                                          len(pieces)), h)
 
 
 def npp_n_theta(cfg: npp_config) -> int:
@@ -458,6 +473,8 @@ class Planner:
         self.cfg = make_config(preset, max_N, max_T, max_M)
         self.device = torch.device("cuda", device)
         self.h = npp_create(self.cfg, device)
+        if preset.get("footprint"):
+            npp_set_footprint(self.h, preset["footprint"])
         self.n_theta = npp_n_theta(self.cfg)
         d = self.device
         self.best = torch.zeros(8, dtype=torch.int32, device=d)

@@ -65,10 +65,10 @@ def _same(a, b):
 
 
 @pytest.mark.parametrize("fp", [RECT, CAR, L_SHAPE])
-@pytest.mark.parametrize("seed,N,T,M,width", [(101, 700, 25, 400, 16), (102, 2000, 30, 1500, 32),
-                                              (103, 33, 3, 1, 64), (104, 257, 12, 0, 16)])
-def test_binned_polygon_equals_brute_force(fp, seed, N, T, M, width):
-    sc = _with(inputs.tiny_scene(seed, N=N, T=T, M=M, width=width, box=25.0, clear=2.5), footprint=fp)
+@pytest.mark.parametrize("seed,N,T,M,width,box", [(101, 700, 25, 400, 16, 25.0), (102, 2000, 30, 1500, 32, 60.0),
+                                                  (103, 33, 3, 1, 64, 25.0), (104, 257, 12, 0, 16, 25.0)])
+def test_binned_polygon_equals_brute_force(fp, seed, N, T, M, width, box):
+    sc = _with(inputs.tiny_scene(seed, N=N, T=T, M=M, width=width, box=box, clear=3.0), footprint=fp)
     a, b = _plan(sc, -1), _plan(sc, 2)
     _same(a, b)
     if M > 100:
@@ -99,7 +99,7 @@ def test_rectangle_polygon_matches_rectangle_kernels():
     """The same rectangle two ways (scaled rows with the sign-bit test, and
     half-planes in the vehicle's frame): decisions differ only where a point
     sits within rounding of a face."""
-    sc = inputs.tiny_scene(121, N=4096, T=30, M=2000, width=32, box=30.0, clear=2.5)
+    sc = inputs.tiny_scene(121, N=4096, T=30, M=2000, width=32, box=60.0, clear=3.0)
     a = _plan(sc)
     b = _plan(_with(sc, footprint=RECT))
     agree = np.mean(a["first_hit"] == b["first_hit"])

@@ -244,13 +244,16 @@ typedef struct npp_loop npp_loop;
 typedef struct {
     float x, y, phi, v, a_prev0, a_prev1;  /* simulated vehicle after the last step */
     int32_t t;            /* sampling times completed                         */
-    int32_t waypoint;     /* index of the current waypoint                     */
+    int32_t waypoint;     /* index of the current waypoint (mission mode: of the
+                             goal setpoint on the reference path)              */
     int32_t done;         /* 1 once the last waypoint has been reached         */
     int32_t status;       /* status of the last plan step (OK / INFEASIBLE)    */
     int32_t best_idx;     /* winner of the last plan step                      */
     int32_t n_infeasible; /* plan steps that ended infeasible                  */
     float best_cost;      /* cost of the last winner                           */
-    int32_t reserved[3];
+    int32_t space_index;  /* mission mode: progress index on the reference path */
+    int32_t stop;         /* mission mode: next stop setpoint to reach          */
+    int32_t reserved;
 } npp_loop_state;
 
 /* Create a loop on handle h (which it uses; keep h alive): initial state s0,
@@ -261,6 +264,42 @@ typedef struct {
 npp_status npp_loop_create(npp_handle* h, const npp_state* s0, const float* waypoints_host,
                            int32_t n_wp, const float* eps_host, const float* obs_dev, int32_t M,
                            int32_t N, int32_t T, uint64_t seed, int32_t max_log, npp_loop** out);
+
+/* Mission layer of Alg. 1 (Steps 3, 4 and 7; Sect. II-B to II-D) on the
+ * device, for a loop created by npp_loop_create_mission. */
+typedef struct {
+    float range_front, range_back, range_side; /* range field visible at t, EV frame:
+                                                  xi in [-back, front], |eta| <= side [m] */
+    int32_t window;        /* setpoints searched ahead of the space index, >= 1        */
+    int32_t hide_outside;  /* 1: obstacle points outside the range field at t are not
+                              seen by that sampling time's plan step                 */
+} npp_mission;
+
+/* A loop that follows a reference path ref_host[n_ref][4] (x, y, phi, v,
+ * world frame; mission data of Sect. II-B) instead of a waypoint list.
+ * Setpoints with v = 0 and the last one are stop setpoints (a cusp, a parking
+ * position) that must be reached within eps before the path beyond them is
+ * used; reaching the last one completes the mission (npp_loop_state.done).
+ * At every sampling time, on the simulated vehicle's pose: the space index
+ * (Sect. II-C) is the setpoint closest to the vehicle among index ..
+ * min(index + window, next stop), ties to the lowest; the goal setpoint
+ * (Step 4; Sect. II-D (iv)) is the furthest setpoint from the space index on,
+ * up to the next stop, with it and every setpoint before it within or on the
+ * range field (the space index itself when even that one is outside).
+ * With hide_outside the points outside the range field at t are parked far
+ * away (at rest) for that plan step.  Log rows and npp_loop_state.waypoint
+ * carry the goal setpoint's index.  Other arguments and behaviour as
+ * npp_loop_create; NPP_INVALID_ARG for a negative or non-finite field
+ * extent, window < 1 or hide_outside not 0/1. */
+npp_status npp_loop_create_mission(npp_handle* h, const npp_state* s0, const float* ref_host, int32_t n_ref,
+                                   const npp_mission* mission, const float* eps_host, const float* obs_dev,
+                                   int32_t M, int32_t N, int32_t T, uint64_t seed, int32_t max_log,
+                                   npp_loop** out);
+
+/* Synchronise and copy the M obstacle points the next plan step of L sees
+ * (world frame at the current sampling time, (x, y, vx, vy); hidden points
+ * parked at (1e7, 1e7) at rest) into obs_host[M][4]. */
+npp_status npp_loop_points(npp_loop* L, float* obs_host);
 
 /* Run `steps` sampling times (graph replays), asynchronous on `stream`.
  * A loop's steps must not run concurrently with other work on its handle. */

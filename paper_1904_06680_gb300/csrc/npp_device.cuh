@@ -348,6 +348,11 @@ struct LoopDev {
     int status, best_idx, n_infeasible;
     float best_cost;
     float eps[4];                      // completion tolerances (xi, eta, phi, v)
+    // mission mode (reference path): space index, next stop setpoint, goal
+    // setpoint index, range field (front, back, side), index search window,
+    // points outside the range field hidden from the plan step
+    int mission, idx, stop, goal_k, window, hide;
+    float field[3];
 };
 
 // Per-step scalars of a plan step, from the arguments or from a LoopDev.

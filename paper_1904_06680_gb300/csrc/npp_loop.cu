@@ -50,26 +50,119 @@ struct npp_loop {
 
 namespace {
 
+// where points outside the range field are parked (world frame, at rest):
+// farther from any vehicle pose than a plan step can reach
+constexpr float HIDDEN_POINT = 1.0e7f;
+
 struct PlantCfg {
     double lf, lr, delta_max, u_min, u_max, Ts;
 };
 
-// Step 6 and 7 of Alg. 1: one sampling time of the simulated vehicle (the
-// kinematic bicycle of Sect. IV, FP64, explicit Euler on the old state) under
-// the winner's first applied control; obstacle points at the next time;
-// waypoint switch; log row (x, y, phi, v, a0, a1, best cost, waypoint).
-// obstacle points at the next sampling time: p0 + tau v, tau = (t+1) Ts
+// ---- mission layer (Alg. 1 Steps 3, 4, 7; Sect. II-B to II-D), FP64 on the
+// simulated vehicle's pose.  Readings: setpoints with v = 0 and the last
+// one are stop setpoints that must be reached within eps before the path
+// beyond them is used (the last one completes the mission); the space index
+// is the setpoint closest to the vehicle among idx .. min(idx + window,
+// stop), ties to the lowest; the goal is the furthest setpoint from the
+// space index on, up to the stop, with it and all before it within or on the
+// range field xi in [-back, front], |eta| <= side (EV frame at t).
+
+// (xi, eta) of a world point in the vehicle's frame
+__device__ __forceinline__ void ev_of(const LoopDev* d, double px, double py, double& xi, double& eta)
+{
+    const double c = cos(d->pphi), s = sin(d->pphi);
+    const double dx = px - d->px, dy = py - d->py;
+    xi = c * dx + s * dy;
+    eta = -s * dx + c * dy;
+}
+
+__device__ __forceinline__ bool in_field(const LoopDev* d, double px, double py)
+{
+    double xi, eta;
+    ev_of(d, px, py, xi, eta);
+    return -(double)d->field[1] <= xi && xi <= (double)d->field[0] && fabs(eta) <= (double)d->field[2];
+}
+
+__device__ __forceinline__ bool is_stop(const float4* ref, int n, int k) { return k == n - 1 || ref[k].w == 0.0f; }
+
+__device__ __forceinline__ int next_stop(const float4* ref, int n, int k)
+{
+    while (!is_stop(ref, n, k)) ++k;
+    return k;
+}
+
+// the tolerances of Table hyperparameters at the vehicle's pose and speed
+__device__ __forceinline__ bool reached(const LoopDev* d, const float4 g)
+{
+    double dxi, deta;
+    ev_of(d, g.x, g.y, dxi, deta);
+    const double dphi = remainder((double)g.z - d->pphi, 2.0 * M_PI);
+    return fabs(dxi) <= d->eps[0] && fabs(deta) <= d->eps[1] && fabs(dphi) <= d->eps[2] &&
+           fabs((double)g.w - d->pv) <= d->eps[3];
+}
+
+__device__ void select_goal(LoopDev* d, const float4* ref)
+{
+    int k = d->idx;
+    if (in_field(d, ref[k].x, ref[k].y))
+        while (k + 1 <= d->stop && in_field(d, ref[k + 1].x, ref[k + 1].y)) ++k;
+    d->goal_k = k;
+}
+
+// Step 7 (stop setpoints, completion) and Steps 3-4 (space index, goal) at
+// the vehicle's current pose
+__device__ void mission_update(LoopDev* d, const float4* ref)
+{
+    if (d->done) return;
+    const int n = d->n_wp;
+    int best = d->idx;
+    double bd = INFINITY;
+    const int last = min(d->idx + d->window, d->stop);
+    for (int k = d->idx; k <= last; ++k) {
+        const double dd = hypot((double)ref[k].x - d->px, (double)ref[k].y - d->py);
+        if (dd < bd) { best = k; bd = dd; }
+    }
+    d->idx = best;
+    if (reached(d, ref[d->stop])) {
+        if (d->stop == n - 1) {
+            d->done = 1;
+            return;
+        }
+        d->idx = d->stop;
+        d->stop = next_stop(ref, n, d->stop + 1);
+    }
+    select_goal(d, ref);
+}
+
+// mission start: first stop, goal at the initial pose
+__global__ void mission_init_kernel(LoopDev* d, const float4* __restrict__ ref)
+{
+    d->idx = 0;
+    d->stop = next_stop(ref, d->n_wp, 0);
+    select_goal(d, ref);
+    const float4 g = ref[d->goal_k];
+    d->gx = g.x; d->gy = g.y; d->gphi = g.z; d->gv = g.w;
+}
+
+// Obstacle points at the current sampling time t (the state kernel has
+// advanced t): p0 + tau v, tau = t Ts; with hide, points outside the range
+// field at t are moved far away (at rest), so no plan step sees them.
 __global__ void advance_obstacles_kernel(const LoopDev* d, const float4* __restrict__ obs0,
                                          float4* __restrict__ obs, int M, float Ts)
 {
-    const float tau = (float)(d->t + 1) * Ts;
+    const float tau = (float)d->t * Ts;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
         const float4 o = obs0[j];
-        obs[j] = make_float4(fmaf(tau, o.z, o.x), fmaf(tau, o.w, o.y), o.z, o.w);
+        const float px = fmaf(tau, o.z, o.x), py = fmaf(tau, o.w, o.y);
+        if (d->hide && !in_field(d, px, py)) obs[j] = make_float4(HIDDEN_POINT, HIDDEN_POINT, 0.0f, 0.0f);
+        else obs[j] = make_float4(px, py, o.z, o.w);
     }
 }
 
-// runs after advance_obstacles_kernel (which reads the old t); one thread
+// Steps 6 and 7 of Alg. 1: one sampling time of the simulated vehicle (the
+// kinematic bicycle of Sect. IV, FP64, explicit Euler on the old state) under
+// the winner's first applied control; waypoint switch or mission update;
+// log row (x, y, phi, v, a0, a1, best cost, goal index).  One thread.
 __global__ void advance_state_kernel(LoopDev* d, const float* __restrict__ controls,
                                      const npp_best* __restrict__ best, const float4* __restrict__ wps,
                                      float* __restrict__ log, int max_log, PlantCfg pc)
@@ -82,7 +175,8 @@ __global__ void advance_state_kernel(LoopDev* d, const float* __restrict__ contr
     if (d->t < max_log) {
         float* row = log + 8 * d->t;
         row[0] = (float)d->px; row[1] = (float)d->py; row[2] = (float)d->pphi; row[3] = (float)d->pv;
-        row[4] = (float)a0; row[5] = (float)a1; row[6] = best->best_cost; row[7] = (float)d->waypoint;
+        row[4] = (float)a0; row[5] = (float)a1; row[6] = best->best_cost;
+        row[7] = (float)(d->mission ? d->goal_k : d->waypoint);
     }
     const double L = pc.lf + pc.lr;
     const double delta = pc.delta_max * a0;
@@ -95,6 +189,15 @@ __global__ void advance_state_kernel(LoopDev* d, const float* __restrict__ contr
     d->pv = v + pc.Ts * u;
     d->t += 1;
     d->t_index += 1;
+    if (d->mission) {
+        mission_update(d, wps);
+        const float4 g = wps[d->goal_k];
+        d->gx = g.x; d->gy = g.y; d->gphi = g.z; d->gv = g.w;
+        d->x0 = (float)d->px; d->y0 = (float)d->py; d->phi0 = (float)d->pphi; d->v0 = (float)d->pv;
+        d->ap0 = (float)a0; d->ap1 = (float)a1;
+        d->warm_valid = 1;
+        return;
+    }
     // completion check against the current waypoint (Table hyperparameters)
     if (!d->done) {
         const float4 g = wps[d->waypoint];
@@ -171,25 +274,21 @@ npp_status enqueue_step(npp_loop* L, uint64_t seed)
     PlantCfg pc;
     pc.lf = h->cfg.lf; pc.lr = h->cfg.lr; pc.delta_max = h->cfg.delta_max;
     pc.u_min = h->cfg.u_min; pc.u_max = h->cfg.u_max; pc.Ts = h->cfg.Ts;
+    advance_state_kernel<<<1, 1, 0, s>>>(L->d_dyn, L->d_controls, L->d_best, L->d_wp, L->d_log,
+                                         L->max_log, pc);
+    CUDA_TRY(h, cudaGetLastError());
     if (L->M > 0) {
         advance_obstacles_kernel<<<(L->M + 255) / 256, 256, 0, s>>>(L->d_dyn, L->d_obs0, L->d_obs, L->M,
                                                                      (float)pc.Ts);
         CUDA_TRY(h, cudaGetLastError());
     }
-    advance_state_kernel<<<1, 1, 0, s>>>(L->d_dyn, L->d_controls, L->d_best, L->d_wp, L->d_log,
-                                         L->max_log, pc);
-    CUDA_TRY(h, cudaGetLastError());
     CUDA_TRY(h, record_event(L->ev[3], s));
     return NPP_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-npp_status npp_loop_create(npp_handle* h, const npp_state* s0, const float* waypoints_host,
-                           int32_t n_wp, const float* eps_host, const float* obs_dev, int32_t M,
-                           int32_t N, int32_t T, uint64_t seed, int32_t max_log, npp_loop** out)
+npp_status loop_create(npp_handle* h, const npp_state* s0, const float* waypoints_host, int32_t n_wp,
+                       const npp_mission* mission, const float* eps_host, const float* obs_dev, int32_t M,
+                       int32_t N, int32_t T, uint64_t seed, int32_t max_log, npp_loop** out)
 {
     if (!h || !out) return fail(h, NPP_INVALID_ARG, "handle and output pointer must not be NULL");
     *out = nullptr;
@@ -203,6 +302,14 @@ npp_status npp_loop_create(npp_handle* h, const npp_state* s0, const float* wayp
         return fail(h, NPP_INVALID_ARG, "loop: previous controls must lie in [-1, 1]");
     for (int i = 0; i < 4; ++i)
         if (!(eps_host[i] >= 0.f)) return fail(h, NPP_INVALID_ARG, "loop: tolerances must be >= 0");
+    if (mission) {
+        const float f[3] = { mission->range_front, mission->range_back, mission->range_side };
+        for (int i = 0; i < 3; ++i)
+            if (!(f[i] >= 0.f) || !std::isfinite(f[i]))
+                return fail(h, NPP_INVALID_ARG, "mission: range field extents must be finite and >= 0");
+        if (mission->window < 1 || (mission->hide_outside != 0 && mission->hide_outside != 1))
+            return fail(h, NPP_INVALID_ARG, "mission: window >= 1 and hide_outside 0 or 1 required");
+    }
     const npp_config& c = h->cfg;
     if (N < 1 || N > c.max_N || T < 1 || T > c.max_T || M < 0 || M > c.max_M)
         return fail(h, NPP_INVALID_ARG, "loop: N=%d T=%d M=%d outside the handle's capacity", N, T, M);
@@ -239,10 +346,29 @@ npp_status npp_loop_create(npp_handle* h, const npp_state* s0, const float* wayp
     d.n_wp = n_wp;
     for (int i = 0; i < 4; ++i) d.eps[i] = eps_host[i];
     d.status = NPP_OK;
+    if (mission) {
+        d.mission = 1;
+        d.window = mission->window;
+        d.hide = mission->hide_outside;
+        d.field[0] = mission->range_front;
+        d.field[1] = mission->range_back;
+        d.field[2] = mission->range_side;
+    }
     e = cudaMemcpy(L->d_dyn, &d, sizeof d, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(L->d_wp, waypoints_host, (size_t)n_wp * sizeof(float4), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && M > 0) e = cudaMemcpy(L->d_obs0, obs_dev, (size_t)M * sizeof(float4), cudaMemcpyDeviceToDevice);
     if (e == cudaSuccess && M > 0) e = cudaMemcpy(L->d_obs, obs_dev, (size_t)M * sizeof(float4), cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess && mission) {
+        // the first goal and the points seen at t = 0
+        mission_init_kernel<<<1, 1, 0, L->cap>>>(L->d_dyn, L->d_wp);
+        e = cudaGetLastError();
+        if (e == cudaSuccess && M > 0) {
+            advance_obstacles_kernel<<<(M + 255) / 256, 256, 0, L->cap>>>(L->d_dyn, L->d_obs0, L->d_obs, M,
+                                                                           (float)h->cfg.Ts);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(L->cap);
+    }
     if (e != cudaSuccess) {
         free_loop(L);
         return fail(h, NPP_CUDA_ERROR, "loop set-up copy failed: %s", cudaGetErrorString(e));
@@ -278,6 +404,36 @@ npp_status npp_loop_create(npp_handle* h, const npp_state* s0, const float* wayp
     return NPP_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+npp_status npp_loop_create(npp_handle* h, const npp_state* s0, const float* waypoints_host,
+                           int32_t n_wp, const float* eps_host, const float* obs_dev, int32_t M,
+                           int32_t N, int32_t T, uint64_t seed, int32_t max_log, npp_loop** out)
+{
+    return loop_create(h, s0, waypoints_host, n_wp, nullptr, eps_host, obs_dev, M, N, T, seed, max_log, out);
+}
+
+npp_status npp_loop_create_mission(npp_handle* h, const npp_state* s0, const float* ref_host, int32_t n_ref,
+                                   const npp_mission* mission, const float* eps_host, const float* obs_dev,
+                                   int32_t M, int32_t N, int32_t T, uint64_t seed, int32_t max_log,
+                                   npp_loop** out)
+{
+    if (!mission) return fail(h, NPP_INVALID_ARG, "mission is NULL");
+    return loop_create(h, s0, ref_host, n_ref, mission, eps_host, obs_dev, M, N, T, seed, max_log, out);
+}
+
+npp_status npp_loop_points(npp_loop* L, float* obs_host)
+{
+    if (!L || (!obs_host && L->M > 0)) return fail(L ? L->h : nullptr, NPP_INVALID_ARG, "loop: bad arguments");
+    npp_handle* h = L->h;
+    LOOP_TRY(h, cudaSetDevice(h->device));
+    LOOP_TRY(h, cudaDeviceSynchronize());
+    if (L->M > 0) LOOP_TRY(h, cudaMemcpy(obs_host, L->d_obs, (size_t)L->M * sizeof(float4), cudaMemcpyDeviceToHost));
+    return NPP_OK;
+}
+
 npp_status npp_loop_run(npp_loop* L, int32_t steps, void* stream)
 {
     if (!L || steps < 0) return fail(L ? L->h : nullptr, NPP_INVALID_ARG, "loop: bad arguments");
@@ -302,6 +458,11 @@ npp_status npp_loop_read(npp_loop* L, npp_loop_state* out_host)
     out_host->t = d.t; out_host->waypoint = d.waypoint; out_host->done = d.done;
     out_host->status = d.status; out_host->best_idx = d.best_idx;
     out_host->n_infeasible = d.n_infeasible; out_host->best_cost = d.best_cost;
+    if (d.mission) {
+        out_host->waypoint = d.goal_k;
+        out_host->space_index = d.idx;
+        out_host->stop = d.stop;
+    }
     return NPP_OK;
 }
 

@@ -41,6 +41,16 @@ Scene recipes (all world-frame, SI units; obstacles are (x, y, vx, vy)):
   controls U[-0.3, 0.3], no point within 2.5 m) with a goal 6-15 m away in
   a uniform direction, heading within +-90 degrees of the start heading,
   at rest, also clear of points.  8-16-16-2 network, N = 4096, T = 40.
+* ``scene_mission``: a transportation mission along a winding two-lane road
+  (centre line y = 4 sin(2 pi x / 60), x in [0, 150] m): the reference path
+  samples the centre line every 1 m at 4 m/s with the last setpoint at rest;
+  both road bounds are points every 0.5 m, 3.5 m either side; six parked-car
+  outlines (0.5 m spacing) sit in the lane at random stations at least 18 m
+  apart, alternately left and right of the centre line (their centre 2.2 m
+  off it, aligned with the road); one car outline drives towards the
+  vehicle in the far lane at 1 m/s.  Start at rest on the centre line.
+  8-32-32-2, N = 8192, T = 40; range field 25 m ahead, 8 m behind, 10 m to
+  either side.
 """
 import math
 
@@ -362,3 +372,53 @@ def scene_batch(seed: int = 0, S: int = 512, width_choices=(16, 32, 64), N_range
         obs_chunks.append(obs)
         off += len(loc)
     return dict(preset=planner(32), scenes=scenes, obs=np.concatenate(obs_chunks))
+
+
+# ------------------------------------------------------------------ missions
+MISSION_FIELD = (25.0, 8.0, 10.0)       # range field: front, back, side [m]
+
+
+def _road(x):
+    y = 4.0 * np.sin(2 * math.pi * x / 60.0)
+    dy = 4.0 * 2 * math.pi / 60.0 * np.cos(2 * math.pi * x / 60.0)
+    return y, np.arctan(dy)
+
+
+def scene_mission(seed: int = 0, N: int = 8192, T: int = 40, width: int = 32, length: float = 150.0,
+                  n_parked: int = 6, lane_speed: float = 4.0):
+    """See the module docstring."""
+    rng = np.random.default_rng(6000 + seed)
+    xs = np.arange(0.0, length + 0.5, 1.0)
+    ys, hs = _road(xs)
+    ref = np.stack([xs, ys, hs, np.full_like(xs, lane_speed)], 1)
+    ref[-1, 3] = 0.0
+    xb = np.arange(-10.0, length + 10.0, 0.5)
+    yb, hb = _road(xb)
+    nx, ny = -np.sin(hb), np.cos(hb)
+    bounds = np.concatenate([np.stack([xb + 3.5 * nx, yb + 3.5 * ny], 1),
+                             np.stack([xb - 3.5 * nx, yb - 3.5 * ny], 1)])
+    stations = []
+    while len(stations) < n_parked:
+        c = rng.uniform(20.0, length - 10.0)
+        if all(abs(c - o) >= 18.0 for o in stations):
+            stations.append(c)
+    stations.sort()
+    cars = []
+    side = 1.0 if rng.uniform() < 0.5 else -1.0
+    for c in stations:
+        yc, hc = _road(np.array([c]))
+        cars.append(_square_outline(c - side * 2.2 * math.sin(hc[0]), yc[0] + side * 2.2 * math.cos(hc[0]),
+                                    2.25, 0.9, hc[0], 25))
+        side = -side
+    xo = length - 20.0
+    yo, ho = _road(np.array([xo]))
+    oncoming = _square_outline(xo - 1.75 * math.sin(ho[0]), yo[0] + 1.75 * math.cos(ho[0]), 2.25, 0.9,
+                               ho[0], 25)
+    static = np.concatenate([bounds] + cars)
+    obs = np.zeros((len(static) + len(oncoming), 4))
+    obs[:len(static), :2] = static
+    obs[len(static):, :2] = oncoming
+    obs[len(static):, 2] = -1.0
+    state = np.array([0.0, ref[0, 1], ref[0, 2], 0.0, 0.0, 0.0])
+    return dict(preset=planner(width), state=state, goal=ref[-1].copy(), obs=obs, N=N, T=T,
+                seed=philox_seed(seed), t_index=0, ref=ref, field=MISSION_FIELD, window=20)

@@ -50,7 +50,7 @@ class npp_best(C.Structure):
 class npp_loop_state(C.Structure):
     _fields_ = [(n, C.c_float) for n in ("x", "y", "phi", "v", "a_prev0", "a_prev1")] + [
         (n, C.c_int32) for n in ("t", "waypoint", "done", "status", "best_idx", "n_infeasible")] + [
-        ("best_cost", C.c_float), ("reserved", C.c_int32 * 3)]
+        ("best_cost", C.c_float), ("space_index", C.c_int32), ("stop", C.c_int32), ("reserved", C.c_int32)]
 
 
 class npp_scene(C.Structure):
@@ -83,7 +83,8 @@ EXPORTS = ("npp_create", "npp_destroy", "npp_last_error", "npp_n_theta", "npp_pl
            "npp_proposal_create", "npp_proposal_destroy", "npp_proposal_n_params",
            "npp_proposal_set_params", "npp_proposal_get_params", "npp_proposal_get_grads",
            "npp_proposal_encode", "npp_proposal_forward", "npp_proposal_train_step",
-           "npp_plan_step_proposal", "npp_gemm_bf16", "npp_gemm_status", "npp_plan_tshc")
+           "npp_plan_step_proposal", "npp_gemm_bf16", "npp_gemm_status", "npp_plan_tshc",
+           "npp_loop_create_mission", "npp_loop_points")
 
 _lib = None
 
@@ -382,6 +383,33 @@ def npp_loop_create(h, state, waypoints, eps, obs, M, N, T, seed, max_log=1024):
                                  wp.shape[0], ep.ctypes.data_as(C.c_void_p), _ptr(obs), int(M),
                                  int(N), int(T), int(seed), int(max_log), C.byref(L)), h)
     return L
+
+
+class npp_mission(C.Structure):
+    _fields_ = [("range_front", C.c_float), ("range_back", C.c_float), ("range_side", C.c_float),
+                ("window", C.c_int32), ("hide_outside", C.c_int32)]
+
+
+def npp_loop_create_mission(h, state, ref, field, window, hide_outside, eps, obs, M, N, T, seed, max_log=1024):
+    """ref: array-like [n_ref][4] reference setpoints; field: (front, back,
+    side) of the range field; obs: CUDA tensor or None."""
+    import numpy as np
+    rp = np.ascontiguousarray(ref, dtype=np.float32).reshape(-1, 4)
+    ep = np.ascontiguousarray(eps, dtype=np.float32).reshape(4)
+    m = npp_mission(float(field[0]), float(field[1]), float(field[2]), int(window), int(hide_outside))
+    L = C.c_void_p()
+    _check(lib().npp_loop_create_mission(h, C.byref(make_state(state)), rp.ctypes.data_as(C.c_void_p),
+                                         rp.shape[0], C.byref(m), ep.ctypes.data_as(C.c_void_p), _ptr(obs),
+                                         int(M), int(N), int(T), int(seed), int(max_log), C.byref(L)), h)
+    return L
+
+
+def npp_loop_points(L, M):
+    """The M points (world frame, x, y, vx, vy) the next plan step sees."""
+    import numpy as np
+    out = np.zeros((max(M, 1), 4), np.float32)
+    _check(lib().npp_loop_points(L, out.ctypes.data_as(C.c_void_p)))
+    return out[:M]
 
 
 def npp_loop_run(L, steps, stream=None):

@@ -1,0 +1,133 @@
+"""The mission layer of the device loop (Alg. 1 Steps 3, 4, 7; Sect. II-B to
+II-D) against the oracle's mission logic (oracle/mission.py).
+
+* Every sampling time's goal setpoint on a forward/reverse path with a cusp,
+  replayed by the oracle from the logged poses; the mission completes.
+* The points the plan step sees with hide_outside: the oracle's range-field
+  visibility at the loop's pose and time.
+* The road mission (parked cars, road bounds, an oncoming car) completes
+  collision-free (executed poses checked by the oracle against every point).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mission as MS
+from paper_1904_06680_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _cusp_path():
+    fwd = [(float(k), 0.0, 0.0, 2.0) for k in range(0, 14)] + [(14.0, 0.0, 0.0, 0.0)]
+    rev = [(14.0 - k, 0.0, 0.0, -2.0) for k in range(1, 9)] + [(5.0, 0.0, 0.0, 0.0)]
+    return np.array(fwd + rev, np.float32)
+
+
+def _run_until_done(L, max_steps, chunk=20):
+    from paper_1904_06680_gb300 import npp
+    for _ in range(max_steps // chunk):
+        npp.npp_loop_run(L, chunk)
+        st = npp.npp_loop_read(L)
+        if st["done"]:
+            return st
+    return npp.npp_loop_read(L)
+
+
+def test_mission_goals_replayed_by_oracle():
+    import torch
+    from paper_1904_06680_gb300 import npp
+    p = inputs.planner(16)
+    N, T = 4096, 30
+    ref = _cusp_path()
+    field, window = (6.0, 4.0, 3.0), 5
+    pl = npp.Planner(p, max_N=N, max_T=T, max_M=1)
+    obs = torch.tensor([[1e4, 1e4, 0.0, 0.0]], dtype=torch.float32, device="cuda")
+    L = npp.npp_loop_create_mission(pl.h, [0.0, 0.0, 0.0, 0.0, 0.0, 0.0], ref, field, window, 0, inputs.EPS,
+                                    obs, 1, N, T, 31)
+    st = _run_until_done(L, 600)
+    log = npp.npp_loop_log(L)
+    npp.npp_loop_destroy(L)
+    pl.close()
+    assert st["done"], st
+    # replay: the goal of step t from the pose logged before it
+    m = MS.Mission(ref.astype(np.float64), np.float32(field).astype(np.float64), window, np.float32(inputs.EPS),
+                   tuple(log[0, :3].astype(np.float64)))
+    goals = [m.goal]
+    for t in range(1, len(log)):
+        goals.append(m.update(tuple(log[t, :3].astype(np.float64)), float(log[t, 3])))
+    np.testing.assert_array_equal(np.array(goals), log[:, 7].astype(int))
+    # the goal stepped through the forward part, the cusp and the reverse part
+    assert log[:, 7].min() < 8 and 14 in set(log[:, 7].astype(int)) and log[-1, 7] == len(ref) - 1
+    m.update((float(st["x"]), float(st["y"]), float(st["phi"])), float(st["v"]))
+    assert m.done and st["space_index"] == m.idx
+    assert np.any(log[:, 3] < -0.3)               # it reversed
+
+
+def test_mission_hides_points_outside_the_field():
+    import torch
+    from paper_1904_06680_gb300 import npp
+    sc = inputs.scene_mission(1, N=4096)
+    M = sc["obs"].shape[0]
+    pl = npp.Planner(sc["preset"], max_N=sc["N"], max_T=sc["T"], max_M=M)
+    obs = torch.tensor(sc["obs"], dtype=torch.float32, device="cuda")
+    L = npp.npp_loop_create_mission(pl.h, sc["state"], sc["ref"], sc["field"], sc["window"], 1, inputs.EPS,
+                                    obs, M, sc["N"], sc["T"], sc["seed"])
+    checked = 0
+    for steps in (0, 25, 60):
+        npp.npp_loop_run(L, steps)
+        st = npp.npp_loop_read(L)
+        seen = npp.npp_loop_points(L, M)
+        pose = (float(st["x"]), float(st["y"]), float(st["phi"]))
+        tau = st["t"] * sc["preset"]["Ts"]
+        want = MS.visible([tuple(o) for o in np.float32(sc["obs"]).astype(np.float64)], pose, tau,
+                          np.float32(sc["field"]).astype(np.float64))
+        hidden = seen[:, 0] >= 1e7
+        for j in range(M):
+            o = sc["obs"][j]
+            px, py = o[0] + tau * o[2], o[1] + tau * o[3]
+            xi, eta = MS.ev_coords(pose, px, py)
+            f = sc["field"]
+            margin = min(abs(xi - f[0]), abs(xi + f[1]), abs(abs(eta) - f[2]))
+            if margin < 1e-3:
+                continue
+            checked += 1
+            assert hidden[j] == (not want[j]), (steps, j, xi, eta)
+            if want[j]:
+                assert abs(seen[j, 0] - px) < 1e-4 and abs(seen[j, 1] - py) < 1e-4
+        assert 0 < np.count_nonzero(~hidden) < M
+    npp.npp_loop_destroy(L)
+    pl.close()
+    assert checked > 2 * M
+
+
+@pytest.mark.parametrize("seed", [0, 3])
+def test_road_mission_completes_collision_free(orc, seed):
+    import torch
+    from paper_1904_06680_gb300 import npp
+    sc = inputs.scene_mission(seed)
+    M = sc["obs"].shape[0]
+    pl = npp.Planner(sc["preset"], max_N=sc["N"], max_T=sc["T"], max_M=M)
+    obs = torch.tensor(sc["obs"], dtype=torch.float32, device="cuda")
+    L = npp.npp_loop_create_mission(pl.h, sc["state"], sc["ref"], sc["field"], sc["window"], 1, inputs.EPS,
+                                    obs, M, sc["N"], sc["T"], sc["seed"], max_log=1000)
+    st = _run_until_done(L, 1000)
+    log = npp.npp_loop_log(L, 1000)
+    npp.npp_loop_destroy(L)
+    pl.close()
+    assert st["done"], (st, log[-1])
+    # the executed poses against every point (hidden or not) at their time
+    p = sc["preset"]
+    for t in range(len(log)):
+        hit = orc.collide(p, float(log[t, 0]), float(log[t, 1]), float(log[t, 2]), sc["obs"], tau=t * p["Ts"])[0]
+        assert not hit, t
+    # it got past every parked car: the space index reached the end
+    assert st["space_index"] >= len(sc["ref"]) - 3

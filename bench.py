@@ -56,13 +56,14 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="course", choices=["course", "large", "batch", "proposal"],
+    ap.add_argument("--workload", default="course", choices=["course", "large", "batch", "proposal", "mission"],
                     help="course: the closed-loop course (default); large: N=65536, T=100, "
                          "8-64-64-2, 8192 points over 80x80 m with per-step spatial binning; "
                          "batch: 512 parking scenes of uneven N, T, M and width in one "
                          "graph-captured batch; proposal: the learned sampling proposal "
                          "(tensor-core GEMM roofline, training throughput, plan quality)")
     ap.add_argument("--rounds", type=int, default=30, help="proposal workload: training rounds")
+    ap.add_argument("--missions", type=int, default=10, help="mission workload: scene seeds")
     return ap.parse_args()
 
 
@@ -704,12 +705,103 @@ def run_proposal(args):
     print(json.dumps(line))
 
 
+def executed_collisions(log, obs, p):
+    """Sampling times whose executed pose (log rows: x, y, phi before the
+    step) has some obstacle point (at its position at that time) strictly
+    inside the vehicle rectangle: an evaluation of the run, numpy."""
+    bad = []
+    hl, hw, co = p["half_len"], p["half_wid"], p["c_off"]
+    for t in range(len(log)):
+        x, y, ph = (float(v) for v in log[t, :3])
+        tau = t * p["Ts"]
+        dx = obs[:, 0] + tau * obs[:, 2] - x
+        dy = obs[:, 1] + tau * obs[:, 3] - y
+        c, s_ = np.cos(ph), np.sin(ph)
+        xi, eta = c * dx + s_ * dy - co, -s_ * dx + c * dy
+        if np.any((np.abs(xi) < hl) & (np.abs(eta) < hw)):
+            bad.append(t)
+    return bad
+
+
+def run_mission(args):
+    """Road missions (mission layer on the device loop: reference path,
+    goal in the range field, points outside it hidden) for several scene
+    seeds: outcome (completed, collision-free, sampling times needed) and the
+    plan-step throughput over all sampling times (device events captured in
+    each step's graph; L2 flushed between steps)."""
+    import torch
+    from paper_1904_06680_gb300 import inputs, npp
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n_missions = args.missions
+    max_steps = 800
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    results, step_ms = [], []
+    sc0 = inputs.scene_mission(0)
+    N, T, W = sc0["N"], sc0["T"], sc0["preset"]["widths"][1]
+    launches = 0
+    clocks = Clocks(local)
+    t_wall = time.perf_counter()
+    clocks.start()
+    for k in range(n_missions):
+        sc = inputs.scene_mission(args.seed + k + rank * 1000)
+        M = sc["obs"].shape[0]
+        pl = npp.Planner(sc["preset"], max_N=N, max_T=T, max_M=M, device=local)
+        obs = torch.tensor(sc["obs"], dtype=torch.float32, device=dev)
+        L = npp.npp_loop_create_mission(pl.h, sc["state"], sc["ref"], sc["field"], sc["window"], 1, inputs.EPS,
+                                        obs, M, N, T, sc["seed"], max_log=max_steps)
+        done_at = None
+        for t in range(max_steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            npp.npp_loop_run(L, 1)
+            tm = npp.npp_loop_last_timing(L)
+            if t >= args.warmup or k > 0:
+                step_ms.append(tm["total"])
+            # trajectories, collision check (+ grid build when binned), epilogue, vehicle, points
+            launches += 6 if (M >= 512 and M * N >= 8e6) else 5
+            if t % 10 == 9 and npp.npp_loop_read(L)["done"]:
+                done_at = npp.npp_loop_read(L)["t"]
+                break
+        st = npp.npp_loop_read(L)
+        log = npp.npp_loop_log(L, max_steps)
+        npp.npp_loop_destroy(L)
+        pl.close()
+        hits = executed_collisions(log, sc["obs"], sc["preset"])
+        results.append(dict(seed=args.seed + k, completed=bool(st["done"]), steps=int(st["t"]),
+                            done_at=done_at, collisions=len(hits), n_infeasible=int(st["n_infeasible"])))
+    ck = clocks.stop()
+    wall = time.perf_counter() - t_wall
+    tot_ms = float(np.sum(step_ms))
+    ok = [r for r in results if r["completed"] and r["collisions"] == 0]
+    line = {"metric": "rollout_steps_per_s", "value": N * T * len(step_ms) / (tot_ms * 1e-3),
+            "unit": "rollout-steps/s", "n_gpus": world, "steps": len(step_ms), "warmup": args.warmup,
+            "ms_per_step": tot_ms / len(step_ms), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "mission", "description":
+                       "road missions (reference path along a winding two-lane road, 150 m; six parked cars "
+                       "in the lane, an oncoming car; range field 25/8/10 m with points outside it hidden): "
+                       "N=%d samples, T=%d, MLP 8-%d-%d-2, one plan step per sampling time" % (N, T, W, W),
+                       "missions": n_missions, "l2": "flushed (256 MiB write) between sampling times"},
+            "mission": {"completed": sum(r["completed"] for r in results), "collision_free_and_completed": len(ok),
+                        "of": len(results),
+                        "sampling_times_mean": float(np.mean([r["steps"] for r in ok])) if ok else None,
+                        "sampling_times_max": max((r["steps"] for r in ok), default=None),
+                        "runs": results, "wall_s": wall},
+            "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": launches, "clocks": ck}
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
-        if args.workload in ("batch", "proposal"):
+        if args.workload in ("batch", "proposal", "mission"):
             args.workload = "course"
         run_reference(args)
+    elif args.workload == "mission":
+        run_mission(args)
     elif args.workload == "batch":
         run_batch(args)
     elif args.workload == "proposal":

@@ -64,6 +64,8 @@ def parse():
                          "(tensor-core GEMM roofline, training throughput, plan quality)")
     ap.add_argument("--rounds", type=int, default=30, help="proposal workload: training rounds")
     ap.add_argument("--missions", type=int, default=10, help="mission workload: scene seeds")
+    ap.add_argument("--footprint", default="rect", choices=["rect", "car"],
+                    help="course/large: the rectangle, or a two-piece car outline (general polygon check)")
     return ap.parse_args()
 
 
@@ -162,6 +164,7 @@ KERNEL_SOURCES = (
                      "npp_rollout_w64.cu")),
     ("bin_build_kernel", ("npp_binned.cu", "npp_device.cuh")),
     ("collide_binned_kernel", ("npp_binned.cu", "npp_device.cuh")),
+    ("collide_poly_kernel", ("npp_binned.cu", "npp_device.cuh")),
     ("collide_", ("npp_rollout.cuh", "npp_device.cuh", "npp_collide.cu")),
     ("gemm_kernel", ("npp_gemm.cu", "npp_gemm.cuh")),
 )
@@ -235,6 +238,10 @@ def run_npp(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     sc, desc = workload_setup(args.workload, args.seed + rank)
+    poly = args.footprint == "car"
+    if poly:
+        sc["preset"] = dict(sc["preset"], footprint=inputs.CAR_FOOTPRINT)
+        desc += "; footprint: car outline with a pointed nose and a tow bar (two convex pieces, 10 faces)"
     p = sc["preset"]
     N, T = sc["N"], sc["T"]
     W = p["widths"][1]
@@ -344,8 +351,10 @@ def run_npp(args):
     fps_t = res["fma_t"] / (traj_ms / 1e3)
     # the library's automatic collision choice (binned from 512 points and
     # 8e6 point-sample pairs)
-    binned = M >= 512 and M * N >= 8000000
-    if binned:
+    binned = poly or (M >= 512 and M * N >= 8000000)
+    if poly:
+        cname = "bin_build_kernel + collide_poly_kernel"
+    elif binned:
         cname = "bin_build_kernel + collide_binned_kernel"
     else:
         cname = ("collide_slice_kernel<4,4>" if N <= 8192 else

@@ -374,6 +374,13 @@ def scene_batch(seed: int = 0, S: int = 512, width_choices=(16, 32, 64), N_range
     return dict(preset=planner(32), scenes=scenes, obs=np.concatenate(obs_chunks))
 
 
+# a general footprint (vehicle frame, counter-clockwise pieces): a car body
+# with a pointed nose and a tow bar behind it; the union is not convex
+CAR_FOOTPRINT = [
+    [[-2.25, -0.9], [1.8, -0.9], [2.6, -0.3], [2.6, 0.3], [1.8, 0.9], [-2.25, 0.9]],
+    [[-3.3, -0.1], [-2.2, -0.1], [-2.2, 0.1], [-3.3, 0.1]],
+]
+
 # ------------------------------------------------------------------ missions
 MISSION_FIELD = (25.0, 8.0, 10.0)       # range field: front, back, side [m]
 

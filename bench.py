@@ -164,7 +164,7 @@ KERNEL_SOURCES = (
                      "npp_rollout_w64.cu")),
     ("bin_build_kernel", ("npp_binned.cu", "npp_device.cuh")),
     ("collide_binned_kernel", ("npp_binned.cu", "npp_device.cuh")),
-    ("collide_poly_kernel", ("npp_binned.cu", "npp_device.cuh")),
+    ("collide_poly_kernel", ("npp_poly.cu", "npp_device.cuh")),
     ("collide_", ("npp_rollout.cuh", "npp_device.cuh", "npp_collide.cu")),
     ("gemm_kernel", ("npp_gemm.cu", "npp_gemm.cuh")),
 )

@@ -180,6 +180,9 @@ npp_status run_rollout(npp_handle* h, RolloutArgs& a, cudaStream_t s, bool allow
         a.poly.faces = h->d_fp;
         a.poly.n_faces = h->fp_faces;
         a.poly.brute = (h->collide_variant >= 0 && h->collide_variant < COLLIDE_BINNED) ? 1 : 0;
+        // enlarged by 1e-3 relative and 1e-6 m^2: larger than any rounding of
+        // a point's squared distance, so no inside point is skipped
+        a.poly.r2 = (float)(h->fp_radius * h->fp_radius * 1.001 + 1e-6);
         if (h->timing) CUDA_TRY(h, record_event(h->ev[0], s));
         CUDA_TRY(h, cudaEventRecord(h->fork_ev, s));
         CUDA_TRY(h, cudaStreamWaitEvent(h->side, h->fork_ev, 0));

@@ -116,101 +116,6 @@ __global__ void __launch_bounds__(BINNED_WARPS * 32) collide_binned_kernel(const
     }
 }
 
-// Whether point p (EV frame at the step's time) is inside the general
-// footprint at pose (x, y) with heading cosine and sine (cp, sp): p moved
-// into the vehicle's frame, q = R(-phi) (p - [x, y]), is inside a convex
-// piece when n . q < b holds strictly for all of its faces (Eq. of the
-// polytope check, Sect. II-D); the footprint is the union of its pieces.
-__device__ __forceinline__ bool poly_inside(const float4* faces, int n_faces, float2 p, float x, float y,
-                                            float cp, float sp)
-{
-    const float dx = p.x - x, dy = p.y - y;
-    const float qx = fmaf(cp, dx, __fmul_rn(sp, dy));
-    const float qy = fmaf(-sp, dx, __fmul_rn(cp, dy));
-    bool any = false, in = true;
-    for (int f = 0; f < n_faces; ++f) {
-        const float4 F = faces[f];
-        in = in & (fmaf(F.x, qx, __fmul_rn(F.y, qy)) < F.z);
-        if (F.w != 0.0f) {
-            any = any | in;
-            in = true;
-        }
-    }
-    return any;
-}
-
-// Polygon footprint check, one warp per sample over the stored states, h in
-// order: the candidates are the points of the (at most two) cell rows the
-// footprint's bounding disk overlaps (binned), or every point of the step
-// (brute force, the same per-point test); the lanes stride through them and
-// a ballot ends the sample at its first colliding step.  Faces are staged in
-// shared memory (uniform reads).
-__global__ void __launch_bounds__(BINNED_WARPS * 32) collide_poly_kernel(const RolloutArgs a)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __shared__ unsigned long long red[BINNED_WARPS];
-    __shared__ float4 faces[FP_MAX_FACES];
-    const int nf = a.poly.n_faces;
-    for (int i = threadIdx.x; i < nf; i += blockDim.x) faces[i] = a.poly.faces[i];
-    __syncthreads();
-    const BinView& g = a.bins;
-    const int T = a.T, N = a.N, M = a.M;
-    const bool brute = a.poly.brute != 0;
-    const int n = blockIdx.x * BINNED_WARPS + warp;
-    unsigned long long key = ~0ull;
-    if (n < N) {
-        int fh = -1;
-        float4 nz = a.traj[n];
-        for (int h = 0; h <= T; ++h) {
-            const float4 z = nz;
-            if (h < T) nz = a.traj[(size_t)(h + 1) * N + n];
-            float sp, cp;
-            sincos_r(z.z, sp, cp);
-            const float2* pts = g.pts + (size_t)h * M;
-            int r0b = 0, n0 = M, r1b = 0, total = M;
-            if (!brute) {
-                const int ix0 = bin_cell(z.x - g.reach, g), ix1 = bin_cell(z.x + g.reach, g);
-                const int iy0 = bin_cell(z.y - g.reach, g), iy1 = bin_cell(z.y + g.reach, g);
-                const int* cs = g.cell_start + (size_t)h * BIN_CS_STRIDE;
-                r0b = cs[iy0 * BIN_DIM + ix0];
-                const int r0e = cs[iy0 * BIN_DIM + ix1 + 1];
-                int r1e = r0e;
-                r1b = r0e;
-                if (iy1 != iy0) { r1b = cs[iy1 * BIN_DIM + ix0]; r1e = cs[iy1 * BIN_DIM + ix1 + 1]; }
-                n0 = r0e - r0b;
-                total = n0 + (r1e - r1b);
-            }
-            bool hit = false;
-            for (int base = 0; base < total && !hit; base += 32) {
-                const int k = base + lane;
-                bool inside = false;
-                if (k < total) inside = poly_inside(faces, nf, pts[k < n0 ? r0b + k : r1b + (k - n0)], z.x, z.y, cp, sp);
-                hit = __any_sync(FULL, inside);
-            }
-            if (hit) { fh = h; break; }
-        }
-        if (lane == 0) {
-            fh = discard_step(a.vfirst, n, fh);
-            float J = __int_as_float(0x7f800000);
-            if (fh < 0) {
-                J = a.jfree[n];
-                key = ((unsigned long long)__float_as_uint(J) << 32) | (unsigned)n;
-            } else {
-                key = (1ull << 63) | ((unsigned long long)(T - fh) << 32) | (unsigned)n;
-            }
-            if (a.costs) a.costs[n] = J;
-            if (a.first_hit) a.first_hit[n] = fh;
-        }
-    }
-    if (lane == 0) red[warp] = key;
-    __syncthreads();
-    if (threadIdx.x == 0 && a.best_key) {
-        unsigned long long k = red[0];
-        for (int w = 1; w < BINNED_WARPS; ++w) k = red[w] < k ? red[w] : k;
-        atomicMin(a.best_key, k);
-    }
-}
-
 }  // namespace
 
 namespace npp {
@@ -252,12 +157,6 @@ cudaError_t build_bins_radius(RolloutArgs& a, double radius, void* workspace, cu
 cudaError_t launch_collide_binned(const RolloutArgs& a, cudaStream_t s)
 {
     collide_binned_kernel<<<(a.N + BINNED_WARPS - 1) / BINNED_WARPS, BINNED_WARPS * 32, 0, s>>>(a);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_collide_poly(const RolloutArgs& a, cudaStream_t s)
-{
-    collide_poly_kernel<<<(a.N + BINNED_WARPS - 1) / BINNED_WARPS, BINNED_WARPS * 32, 0, s>>>(a);
     return cudaGetLastError();
 }
 

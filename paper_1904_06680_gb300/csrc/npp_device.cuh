@@ -263,6 +263,7 @@ struct PolyView {
     const float4* faces;   // [n_faces] (nx, ny, b, last) with |n| = 1
     int n_faces;           // 0: the rectangle
     int brute;             // 1: every point each step (no grid cells)
+    float r2;              // squared radius of a disk around the reference point holding the footprint
 };
 
 __device__ __forceinline__ int bin_cell(float x, const BinView& g)

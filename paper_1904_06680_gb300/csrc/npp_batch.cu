@@ -477,7 +477,7 @@ __global__ void __launch_bounds__(1024) batch_bin_build_kernel(const BatchArgs b
 
 // Binned check of an 8-sample item per block, one warp per sample, over the
 // stored inequality rows (the rectangle's centre recovered from them, as in
-// live_box); the candidates of a step are the points of at most two cell
+// live_box); the candidates of a step are the points of at most three cell
 // rows of the scene's grid; one key minimum per block.
 __global__ void __launch_bounds__(256) batch_binned_kernel(const BatchArgs b)
 {
@@ -508,20 +508,15 @@ __global__ void __launch_bounds__(256) batch_binned_kernel(const BatchArgs b)
             const float cp = ca.x * isl, sp = ca.y * isl;
             const float along = -ca.z * isl, across = -cb.y * isw;
             const float xc = cp * along - sp * across, yc = sp * along + cp * across;
-            const int ix0 = bin_cell(xc - b.reach, g), ix1 = bin_cell(xc + b.reach, g);
-            const int iy0 = bin_cell(yc - b.reach, g), iy1 = bin_cell(yc + b.reach, g);
-            const int* cs = b.bin_cs + s.bin_off + (size_t)h * BIN_CS_STRIDE;
+            const CandRows cr = cand_rows(b.bin_cs + s.bin_off + (size_t)h * BIN_CS_STRIDE, g, xc, yc, b.reach);
             const float2* pts = b.bin_pts + s.bpts_off + (size_t)h * M;
-            const int r0b = cs[iy0 * BIN_DIM + ix0], r0e = cs[iy0 * BIN_DIM + ix1 + 1];
-            int r1b = r0e, r1e = r0e;
-            if (iy1 != iy0) { r1b = cs[iy1 * BIN_DIM + ix0]; r1e = cs[iy1 * BIN_DIM + ix1 + 1]; }
-            const int n0 = r0e - r0b, total = n0 + (r1e - r1b);
+            const int total = cr.total;
             bool hit = false;
             for (int base = 0; base < total && !hit; base += 32) {
                 const int k = base + lane;
                 bool inside = false;
                 if (k < total) {
-                    const float2 p = pts[k < n0 ? r0b + k : r1b + (k - n0)];
+                    const float2 p = pts[cr.index(k)];
                     const float xi = fmaf(ca.x, p.x, fmaf(ca.y, p.y, ca.z));
                     const float et = fmaf(ca.w, p.x, fmaf(cb.x, p.y, cb.y));
                     inside = !(((__float_as_uint(xi) | __float_as_uint(et)) >> 30) & 1u);

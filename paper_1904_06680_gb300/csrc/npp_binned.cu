@@ -5,9 +5,10 @@
 // For every horizon step h the obstacle points at time h Ts (EV frame,
 // p + tau v with the brute-force kernels' arithmetic) are counting-sorted into
 // a uniform grid of BIN_DIM x BIN_DIM cells centred on the vehicle.  A cell is
-// wider than the diameter of the vehicle rectangle's circumscribed disk, so
-// a state's disk (radius plus a rounding margin) overlaps at most 2 x 2 cells;
-// every point inside the rectangle lies in the disk, and cell indices of
+// wider than the radius of the vehicle rectangle's circumscribed disk (plus a
+// rounding margin), so a state's disk overlaps at most 3 x 3 cells (rows of
+// cells are contiguous runs: at most three per query, `cand_rows`); every
+// point inside the rectangle lies in the disk, and cell indices of
 // points and of the query are clamped to the grid the same (monotone) way,
 // so the queried cells hold every point that can be inside.  The per-point
 // test is the brute-force one (same coefficients, same fma sequence), hence
@@ -40,7 +41,7 @@ __global__ void __launch_bounds__(BIN_THREADS) bin_build_kernel(const RolloutArg
 }
 
 // one warp per sample over the stored trajectories and inequality rows, h
-// in order: the candidates of a step are the points of at most two cell
+// in order: the candidates of a step are the points of at most three cell
 // rows, each row's cells contiguous in the sorted array; the lanes stride
 // through them (coalesced loads) and a ballot ends the sample at its first
 // colliding step
@@ -49,7 +50,6 @@ constexpr int BINNED_WARPS = 8;
 __global__ void __launch_bounds__(BINNED_WARPS * 32) collide_binned_kernel(const RolloutArgs a)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __shared__ unsigned long long red[BINNED_WARPS];
     const BinView& g = a.bins;
     const int T = a.T, N = a.N, M = a.M;
     const int n = blockIdx.x * BINNED_WARPS + warp;
@@ -72,20 +72,15 @@ __global__ void __launch_bounds__(BINNED_WARPS * 32) collide_binned_kernel(const
                 ncb = a.coefB[nx];
                 nz = a.traj[nx];
             }
-            const int ix0 = bin_cell(z.x - g.reach, g), ix1 = bin_cell(z.x + g.reach, g);
-            const int iy0 = bin_cell(z.y - g.reach, g), iy1 = bin_cell(z.y + g.reach, g);
-            const int* cs = g.cell_start + (size_t)h * BIN_CS_STRIDE;
+            const CandRows cr = cand_rows(g.cell_start + (size_t)h * BIN_CS_STRIDE, g, z.x, z.y, g.reach);
             const float2* pts = g.pts + (size_t)h * M;
-            const int r0b = cs[iy0 * BIN_DIM + ix0], r0e = cs[iy0 * BIN_DIM + ix1 + 1];
-            int r1b = r0e, r1e = r0e;
-            if (iy1 != iy0) { r1b = cs[iy1 * BIN_DIM + ix0]; r1e = cs[iy1 * BIN_DIM + ix1 + 1]; }
-            const int n0 = r0e - r0b, total = n0 + (r1e - r1b);
+            const int total = cr.total;
             bool hit = false;
             for (int base = 0; base < total && !hit; base += 32) {
                 const int k = base + lane;
                 bool inside = false;
                 if (k < total) {
-                    const float2 p = pts[k < n0 ? r0b + k : r1b + (k - n0)];
+                    const float2 p = pts[cr.index(k)];
                     const float xi = fmaf(ca.x, p.x, fmaf(ca.y, p.y, ca.z));
                     const float et = fmaf(ca.w, p.x, fmaf(cb.x, p.y, cb.y));
                     inside = !(((__float_as_uint(xi) | __float_as_uint(et)) >> 30) & 1u);
@@ -107,13 +102,10 @@ __global__ void __launch_bounds__(BINNED_WARPS * 32) collide_binned_kernel(const
             if (a.first_hit) a.first_hit[n] = fh;
         }
     }
-    if (lane == 0) red[warp] = key;
-    __syncthreads();
-    if (threadIdx.x == 0 && a.best_key) {
-        unsigned long long k = red[0];
-        for (int w = 1; w < BINNED_WARPS; ++w) k = red[w] < k ? red[w] : k;
-        atomicMin(a.best_key, k);
-    }
+    // each warp folds its key into the minimum on its own (no block barrier:
+    // samples end at different steps); the read skips atomics that cannot win
+    if (lane == 0 && n < N && a.best_key && key < *reinterpret_cast<volatile unsigned long long*>(a.best_key))
+        atomicMin(a.best_key, key);
 }
 
 }  // namespace
@@ -126,7 +118,7 @@ size_t binned_workspace_bytes(int max_T, int max_M)
     return (size_t)(max_T + 1) * BIN_CS_STRIDE * sizeof(int) + (size_t)(max_T + 1) * max_M * sizeof(float2);
 }
 
-// A cell wider than the diameter of the query disk (circumradius of the
+// Cells wider than the radius of the query disk (circumradius of the
 // rectangle plus |c_off|, plus a margin against rounding of positions of
 // O(100) m), a grid of BIN_DIM^2 cells centred on the vehicle.
 cudaError_t build_bins(RolloutArgs& a, float half_len, float half_wid, float c_off, void* workspace, cudaStream_t s)

@@ -43,7 +43,7 @@ __device__ __forceinline__ bool poly_inside(const float4* faces, int n_faces, fl
 }
 
 // Polygon footprint check, one warp per sample over the stored states, h in
-// order: the candidates are the points of the (at most two) cell rows the
+// order: the candidates are the points of the (at most three) cell rows the
 // footprint's bounding disk overlaps (binned), or every point of the step
 // (brute force, the same per-point test); the lanes stride through them and
 // a ballot ends the sample at its first colliding step.  Faces are staged in
@@ -51,7 +51,6 @@ __device__ __forceinline__ bool poly_inside(const float4* faces, int n_faces, fl
 __global__ void __launch_bounds__(POLY_WARPS * 32) collide_poly_kernel(const RolloutArgs a)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __shared__ unsigned long long red[POLY_WARPS];
     __shared__ float4 faces[FP_MAX_FACES];
     const int nf = a.poly.n_faces;
     for (int i = threadIdx.x; i < nf; i += blockDim.x) faces[i] = a.poly.faces[i];
@@ -70,25 +69,16 @@ __global__ void __launch_bounds__(POLY_WARPS * 32) collide_poly_kernel(const Rol
             float sp, cp;
             sincos_r(z.z, sp, cp);
             const float2* pts = g.pts + (size_t)h * M;
-            int r0b = 0, n0 = M, r1b = 0, total = M;
-            if (!brute) {
-                const int ix0 = bin_cell(z.x - g.reach, g), ix1 = bin_cell(z.x + g.reach, g);
-                const int iy0 = bin_cell(z.y - g.reach, g), iy1 = bin_cell(z.y + g.reach, g);
-                const int* cs = g.cell_start + (size_t)h * BIN_CS_STRIDE;
-                r0b = cs[iy0 * BIN_DIM + ix0];
-                const int r0e = cs[iy0 * BIN_DIM + ix1 + 1];
-                int r1e = r0e;
-                r1b = r0e;
-                if (iy1 != iy0) { r1b = cs[iy1 * BIN_DIM + ix0]; r1e = cs[iy1 * BIN_DIM + ix1 + 1]; }
-                n0 = r0e - r0b;
-                total = n0 + (r1e - r1b);
-            }
+            // brute force: every point, as one run
+            CandRows cr{0, M, 0, 0, 0, M};
+            if (!brute) cr = cand_rows(g.cell_start + (size_t)h * BIN_CS_STRIDE, g, z.x, z.y, g.reach);
+            const int total = cr.total;
             bool hit = false;
             for (int base = 0; base < total && !hit; base += 32) {
                 const int k = base + lane;
                 bool inside = false;
                 if (k < total)
-                    inside = poly_inside(faces, nf, a.poly.r2, pts[k < n0 ? r0b + k : r1b + (k - n0)], z.x, z.y, cp, sp);
+                    inside = poly_inside(faces, nf, a.poly.r2, pts[cr.index(k)], z.x, z.y, cp, sp);
                 hit = __any_sync(FULL, inside);
             }
             if (hit) { fh = h; break; }
@@ -106,13 +96,10 @@ __global__ void __launch_bounds__(POLY_WARPS * 32) collide_poly_kernel(const Rol
             if (a.first_hit) a.first_hit[n] = fh;
         }
     }
-    if (lane == 0) red[warp] = key;
-    __syncthreads();
-    if (threadIdx.x == 0 && a.best_key) {
-        unsigned long long k = red[0];
-        for (int w = 1; w < POLY_WARPS; ++w) k = red[w] < k ? red[w] : k;
-        atomicMin(a.best_key, k);
-    }
+    // each warp folds its key into the minimum on its own (no block barrier:
+    // samples end at different steps); the read skips atomics that cannot win
+    if (lane == 0 && n < N && a.best_key && key < *reinterpret_cast<volatile unsigned long long*>(a.best_key))
+        atomicMin(a.best_key, key);
 }
 
 }  // namespace

@@ -232,28 +232,16 @@ __device__ __forceinline__ int discard_step(const int* vfirst, long long n, int 
 
 // Binned check of one state for the G lanes of each group of a warp (every
 // lane of the warp calls it; dead groups pass alive = false): the candidates
-// of the at most two cell rows the state's disk overlaps, strided over the
+// of the at most three cell rows the state's disk overlaps, strided over the
 // group's lanes, the per-point test of the brute-force kernels.  Returns,
 // uniformly over the group, whether some point is inside.
 template <int G>
 __device__ __forceinline__ bool group_collides(const BinView& bv, int h, float x, float y, const float4& A,
                                                const float2& B, bool alive, int gl)
 {
-    int r0b = 0, r0e = 0, r1b = 0, r1e = 0;
-    if (alive) {
-        const int ix0 = bin_cell(x - bv.reach, bv), ix1 = bin_cell(x + bv.reach, bv);
-        const int iy0 = bin_cell(y - bv.reach, bv), iy1 = bin_cell(y + bv.reach, bv);
-        const int* cs = bv.cell_start + (size_t)h * BIN_CS_STRIDE;
-        r0b = cs[iy0 * BIN_DIM + ix0];
-        r0e = cs[iy0 * BIN_DIM + ix1 + 1];
-        r1b = r0e;
-        r1e = r0e;
-        if (iy1 != iy0) {
-            r1b = cs[iy1 * BIN_DIM + ix0];
-            r1e = cs[iy1 * BIN_DIM + ix1 + 1];
-        }
-    }
-    const int n0 = r0e - r0b, total = n0 + (r1e - r1b);
+    CandRows cr{0, 0, 0, 0, 0, 0};
+    if (alive) cr = cand_rows(bv.cell_start + (size_t)h * BIN_CS_STRIDE, bv, x, y, bv.reach);
+    const int total = cr.total;
     const int iters = (total + G - 1) / G;
     const int maxit = __reduce_max_sync(FULL, iters);
     const float2* pts = bv.pts + (size_t)h * bv.M;
@@ -263,7 +251,7 @@ __device__ __forceinline__ bool group_collides(const BinView& bv, int h, float x
         const int k = it * G + gl;
         bool inside = false;
         if (k < total) {
-            const float2 p = pts[k < n0 ? r0b + k : r1b + (k - n0)];
+            const float2 p = pts[cr.index(k)];
             const float xi = fmaf(A.x, p.x, fmaf(A.y, p.y, A.z));
             const float et = fmaf(A.w, p.x, fmaf(B.x, p.y, B.y));
             inside = !(((__float_as_uint(xi) | __float_as_uint(et)) >> 30) & 1u);
@@ -341,7 +329,11 @@ __device__ __forceinline__ void build_step_bins(const float4* __restrict__ obs, 
 // O(100) m (host side).
 inline BinView make_bin_grid_radius(double R)
 {
-    const double cell = 2.0 * R + 0.25;
+    // query radius R + 0.05 (rounding of positions of O(100) m); cells a
+    // little wider than it, so a query spans at most three cells per axis
+    // (a query square of side 2r over cells of width c covers (2r + c)^2 of
+    // candidates on average: 9 r^2 here against 16 r^2 for c = 2r)
+    const double cell = R + 0.15;
     BinView g;
     g.inv_cell = (float)(1.0 / cell);
     g.x0 = (float)(-0.5 * BIN_DIM * cell);

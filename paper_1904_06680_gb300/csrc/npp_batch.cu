@@ -477,7 +477,7 @@ __global__ void __launch_bounds__(1024) batch_bin_build_kernel(const BatchArgs b
 
 // Binned check of an 8-sample item per block, one warp per sample, over the
 // stored inequality rows (the rectangle's centre recovered from them, as in
-// live_box); the candidates of a step are the points of at most three cell
+// live_box); the candidates of a step are the points of at most five cell
 // rows of the scene's grid; one key minimum per block.
 __global__ void __launch_bounds__(256) batch_binned_kernel(const BatchArgs b)
 {

@@ -5,9 +5,9 @@
 // For every horizon step h the obstacle points at time h Ts (EV frame,
 // p + tau v with the brute-force kernels' arithmetic) are counting-sorted into
 // a uniform grid of BIN_DIM x BIN_DIM cells centred on the vehicle.  A cell is
-// wider than the radius of the vehicle rectangle's circumscribed disk (plus a
-// rounding margin), so a state's disk overlaps at most 3 x 3 cells (rows of
-// cells are contiguous runs: at most three per query, `cand_rows`); every
+// wider than half the radius of the vehicle rectangle's circumscribed disk
+// (plus a rounding margin), so a state's disk overlaps at most 5 x 5 cells
+// (rows of cells are contiguous runs: at most five per query, `cand_rows`); every
 // point inside the rectangle lies in the disk, and cell indices of
 // points and of the query are clamped to the grid the same (monotone) way,
 // so the queried cells hold every point that can be inside.  The per-point
@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(BIN_THREADS) bin_build_kernel(const RolloutArg
 }
 
 // one warp per sample over the stored trajectories and inequality rows, h
-// in order: the candidates of a step are the points of at most three cell
+// in order: the candidates of a step are the points of at most five cell
 // rows, each row's cells contiguous in the sorted array; the lanes stride
 // through them (coalesced loads) and a ballot ends the sample at its first
 // colliding step
@@ -118,7 +118,7 @@ size_t binned_workspace_bytes(int max_T, int max_M)
     return (size_t)(max_T + 1) * BIN_CS_STRIDE * sizeof(int) + (size_t)(max_T + 1) * max_M * sizeof(float2);
 }
 
-// Cells wider than the radius of the query disk (circumradius of the
+// Cells wider than half the radius of the query disk (circumradius of the
 // rectangle plus |c_off|, plus a margin against rounding of positions of
 // O(100) m), a grid of BIN_DIM^2 cells centred on the vehicle.
 cudaError_t build_bins(RolloutArgs& a, float half_len, float half_wid, float c_off, void* workspace, cudaStream_t s)

@@ -239,7 +239,7 @@ __device__ __forceinline__ float4 sample_quad_mixed_tail(const SamplerKey& key, 
 // Per-step grids of the binned collision check: for step h, cell_start[h]
 // [BIN_DIM^2 + 1 entries, stride BIN_CS_STRIDE] indexes the points of
 // step h sorted by cell, pts + h M.  A query disk of radius `reach` around a
-// state spans at most three cells per axis.
+// state spans at most five cells per axis.
 constexpr int BIN_DIM = 128;
 constexpr int BIN_NCELL = BIN_DIM * BIN_DIM;
 constexpr int BIN_CS_STRIDE = BIN_NCELL + 4;    // 16-byte multiple: the float2 points that follow stay aligned
@@ -273,17 +273,24 @@ __device__ __forceinline__ int bin_cell(float x, const BinView& g)
 }
 
 // The candidate points of a query disk in one step's grid: the cells of the
-// (at most three) cell rows its bounding square overlaps, each row's cells
-// one contiguous run of the cell-sorted points.  Cells are at least as wide
-// as the query radius, so the square spans at most three cells per axis;
+// (at most five) cell rows its bounding square overlaps, each row's cells
+// one contiguous run of the cell-sorted points.  Cells are at least half as
+// wide as the query radius, so the square spans at most five cells per axis;
 // indices are clamped monotonically at the grid border, so every point that
 // can lie in the disk is a candidate.
+constexpr int BIN_MAX_ROWS = 5;      // cell rows a query can span (cells >= half the query radius)
 struct CandRows {
-    int b0, n0, b1, n1, b2, total;
+    int b[BIN_MAX_ROWS];             // first sorted point of each row's run
+    int e[BIN_MAX_ROWS];             // candidates before the end of each run (inclusive prefix)
+    int total;
     // index (into the step's sorted points) of candidate k < total
     __device__ __forceinline__ int index(int k) const
     {
-        return k < n0 ? b0 + k : (k < n0 + n1 ? b1 + (k - n0) : b2 + (k - n0 - n1));
+        int i = b[0] + k;
+#pragma unroll
+        for (int r = 1; r < BIN_MAX_ROWS; ++r)
+            if (k >= e[r - 1]) i = b[r] + (k - e[r - 1]);
+        return i;
     }
 };
 
@@ -293,20 +300,19 @@ __device__ __forceinline__ CandRows cand_rows(const int* __restrict__ cs, const 
     const int ix0 = bin_cell(x - r, g), ix1 = bin_cell(x + r, g);
     const int iy0 = bin_cell(y - r, g), iy1 = bin_cell(y + r, g);
     CandRows c;
-    c.b0 = cs[iy0 * BIN_DIM + ix0];
-    c.n0 = cs[iy0 * BIN_DIM + ix1 + 1] - c.b0;
-    c.b1 = c.b2 = c.b0;
-    c.n1 = 0;
-    int n2 = 0;
-    if (iy1 > iy0) {
-        c.b1 = cs[(iy0 + 1) * BIN_DIM + ix0];
-        c.n1 = cs[(iy0 + 1) * BIN_DIM + ix1 + 1] - c.b1;
+    int acc = 0;
+#pragma unroll
+    for (int k = 0; k < BIN_MAX_ROWS; ++k) {
+        int beg = 0, len = 0;
+        if (iy0 + k <= iy1) {
+            beg = cs[(iy0 + k) * BIN_DIM + ix0];
+            len = cs[(iy0 + k) * BIN_DIM + ix1 + 1] - beg;
+        }
+        c.b[k] = beg;
+        acc += len;
+        c.e[k] = acc;
     }
-    if (iy1 > iy0 + 1) {
-        c.b2 = cs[(iy0 + 2) * BIN_DIM + ix0];
-        n2 = cs[(iy0 + 2) * BIN_DIM + ix1 + 1] - c.b2;
-    }
-    c.total = c.n0 + c.n1 + n2;
+    c.total = acc;
     return c;
 }
 

@@ -43,7 +43,7 @@ __device__ __forceinline__ bool poly_inside(const float4* faces, int n_faces, fl
 }
 
 // Polygon footprint check, one warp per sample over the stored states, h in
-// order: the candidates are the points of the (at most three) cell rows the
+// order: the candidates are the points of the (at most five) cell rows the
 // footprint's bounding disk overlaps (binned), or every point of the step
 // (brute force, the same per-point test); the lanes stride through them and
 // a ballot ends the sample at its first colliding step.  Faces are staged in
@@ -70,8 +70,14 @@ __global__ void __launch_bounds__(POLY_WARPS * 32) collide_poly_kernel(const Rol
             sincos_r(z.z, sp, cp);
             const float2* pts = g.pts + (size_t)h * M;
             // brute force: every point, as one run
-            CandRows cr{0, M, 0, 0, 0, M};
-            if (!brute) cr = cand_rows(g.cell_start + (size_t)h * BIN_CS_STRIDE, g, z.x, z.y, g.reach);
+            CandRows cr = {};
+            if (brute) {
+                cr.total = M;
+#pragma unroll
+                for (int k = 0; k < BIN_MAX_ROWS; ++k) cr.e[k] = M;
+            } else {
+                cr = cand_rows(g.cell_start + (size_t)h * BIN_CS_STRIDE, g, z.x, z.y, g.reach);
+            }
             const int total = cr.total;
             bool hit = false;
             for (int base = 0; base < total && !hit; base += 32) {

@@ -359,8 +359,11 @@ def run_npp(args):
     else:
         cname = ("collide_slice_kernel<4,4>" if N <= 8192 else
                  "collide_slice_kernel<2,8>" if N <= 32768 else "collide_warp_kernel<8,2>")
-    tname = {16: "traj_kernel<16,8,4,4>", 32: "traj_kernel<32,16,4,4>",
-             64: "traj_kernel<64,32,1,10>"}[W]
+    # default launch shapes; the last template argument is the variant flag
+    # (off: no speed limits, features in the EV frame at t)
+    var = int(bool(p.get("v_limits", 0) or p.get("feature_frame", 0)))
+    tname = {16: "traj_kernel<16,8,4,4,%d>", 32: "traj_kernel<32,16,4,4,%d>",
+             64: "traj_kernel<64,32,1,10,%d>"}[W] % var
     coll = {"ms_per_step": collide_ms / K, "point_checks_per_s": res["checks"] / (collide_ms / 1e3)}
     fma_all = float(N) * T * K * (W * W + 10 * W)
     trj = {"ms_per_step": traj_ms / K, "achieved": fps_t / 1e12, "frac": fps_t / peak,

@@ -45,8 +45,9 @@ Scene recipes (all world-frame, SI units; obstacles are (x, y, vx, vy)):
   (centre line y = 4 sin(2 pi x / 60), x in [0, 150] m): the reference path
   samples the centre line every 1 m at 4 m/s with the last setpoint at rest;
   both road bounds are points every 0.5 m, 3.5 m either side; six parked-car
-  outlines (0.5 m spacing) sit in the lane at random stations at least 18 m
-  apart, alternately left and right of the centre line (their centre 2.2 m
+  outlines (0.5 m spacing) sit in the lane, one at a random station in each of
+  six 20 m slots from x = 20 m (neighbours at least 18 m apart),
+  alternately left and right of the centre line (their centre 2.2 m
   off it, aligned with the road); one car outline drives towards the
   vehicle in the far lane at 1 m/s.  Start at rest on the centre line.
   8-32-32-2, N = 8192, T = 40; range field 25 m ahead, 8 m behind, 10 m to
@@ -404,12 +405,10 @@ def scene_mission(seed: int = 0, N: int = 8192, T: int = 40, width: int = 32, le
     nx, ny = -np.sin(hb), np.cos(hb)
     bounds = np.concatenate([np.stack([xb + 3.5 * nx, yb + 3.5 * ny], 1),
                              np.stack([xb - 3.5 * nx, yb - 3.5 * ny], 1)])
-    stations = []
-    while len(stations) < n_parked:
-        c = rng.uniform(20.0, length - 10.0)
-        if all(abs(c - o) >= 18.0 for o in stations):
-            stations.append(c)
-    stations.sort()
+    # one station per slot of equal length, placed so that neighbours are at
+    # least 18 m apart
+    slot = (length - 30.0) / n_parked
+    stations = [20.0 + k * slot + rng.uniform(0.0, max(slot - 18.0, 0.0)) for k in range(n_parked)]
     cars = []
     side = 1.0 if rng.uniform() < 0.5 else -1.0
     for c in stations:

@@ -57,3 +57,18 @@ def test_scene_batch_recipe():
         g, st = s["goal"], s["state"]
         assert math.hypot(g[0] - st[0], g[1] - st[1]) < 15.0
     assert off == b["obs"].shape[0]
+
+
+def test_mission_scenes_generate_with_spaced_cars():
+    """Every seed builds (no rejection loop) with the parked cars at least
+    18 m apart along the road and the reference path ending at rest."""
+    import time
+    t0 = time.perf_counter()
+    for seed in range(50):
+        sc = inputs.scene_mission(seed)
+        assert sc["ref"][-1, 3] == 0.0 and np.all(sc["ref"][:-1, 3] > 0)
+        cars = sc["obs"][1 + 2 * len(np.arange(-10.0, 160.0, 0.5)) - 1:-25, :2]
+        xs = np.sort(cars.reshape(6, 25, 2)[:, :, 0].mean(axis=1))
+        # centres sit 2.2 m off the centre line: along x they move by <= 2.2 sin(0.41) each
+        assert np.all(np.diff(xs) >= 18.0 - 2 * 2.2 * 0.4), (seed, xs)
+    assert time.perf_counter() - t0 < 5.0

@@ -137,6 +137,8 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v)
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+constexpr int GEMM_GROUP_M = 16;
+
 template <int BN>
 __global__ void __launch_bounds__(128, 1)
 gemm_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int K,
@@ -152,7 +154,20 @@ gemm_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUte
     int* flags = reinterpret_cast<int*>(tmem_slot + 1);      // [0] abort, [1] issued, [2] consumed
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    // grouped tile order: consecutive CTAs walk GEMM_GROUP_M row tiles
+    // before the next column tile, so the CTAs resident at once share a few
+    // tiles of A and of B in L2 (launch order: x fastest, then y)
+    int m0, n0;
+    {
+        const int n_tiles = gridDim.x, m_tiles = gridDim.y;
+        const int pid = blockIdx.y * n_tiles + blockIdx.x;
+        const int per_group = GEMM_GROUP_M * n_tiles;
+        const int first_m = (pid / per_group) * GEMM_GROUP_M;
+        const int gsize = min(m_tiles - first_m, GEMM_GROUP_M);
+        const int in_group = pid % per_group;
+        m0 = (first_m + in_group % gsize) * BM;
+        n0 = (in_group / gsize) * BN;
+    }
     const int nk = K / BK;
 
     if (threadIdx.x == 0) {

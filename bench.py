@@ -347,6 +347,9 @@ def run_npp(args):
         e2e["value"] = multi.whole_job_rate(N * T * K, world, e2e_s)
     value = multi.whole_job_rate(N * T * K, world, total_ms / 1e3)
     peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6
+    # the library's own FMA-stream microbenchmark, beside the derived peak
+    fma_measured = {"ffma": npp.npp_measure_fma_peak(local, False) / 1e12,
+                    "ffma2": npp.npp_measure_fma_peak(local, True) / 1e12, "unit": "T FP32-FMA/s"}
     fps_c = res["fma_c"] / (collide_ms / 1e3)
     fps_t = res["fma_t"] / (traj_ms / 1e3)
     # the library's automatic collision choice (binned from 512 points and
@@ -383,6 +386,7 @@ def run_npp(args):
         roofline = {"bound": "alu", "kernel": tname, "achieved": fps_t / 1e12, "peak": peak / 1e12,
                     "unit": "T FP32-FMA/s", "frac": fps_t / peak, "traffic": traffic,
                     "peak_basis": "derived: 152 SMs x 128 FP32 FMA lanes x 2070 MHz",
+                    "peak_measured": fma_measured,
                     "work": "MLP FMAs (W^2 + 10 W) per control step of a sample up to its first "
                             "collision; all_steps_* count every step the kernel computes",
                     "all_steps_achieved": trj["all_steps_achieved"], "all_steps_frac": trj["all_steps_frac"],
@@ -395,6 +399,7 @@ def run_npp(args):
                     "frac": fps_c / peak,
                     "traffic": None if traffic is None else traffic,
                     "peak_basis": "derived: 152 SMs x 128 FP32 FMA lanes x 2070 MHz",
+                    "peak_measured": fma_measured,
                     "kernel_ms_per_step": collide_ms / K,
                     "point_checks_per_s": res["checks"] / (collide_ms / 1e3),
                     "other": {tname: trj}}

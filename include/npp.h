@@ -228,6 +228,16 @@ npp_status npp_sample_params(uint64_t seed, uint32_t t_index, uint32_t stream_id
 npp_status npp_math_eval(int32_t fn, const float* x_dev, int32_t n, float* y_dev, float* y2_dev,
                          void* stream);
 
+/* Measurement (no counterpart in the paper): FP32 fused multiply-adds per
+ * second that device `device` sustains on streams of independent FMA chains
+ * (packed = 0: scalar FFMA; 1: packed FP32x2 FMA, two per instruction), every
+ * SM filled, best of three timed runs after a warm-up; the denominator of
+ * the rollout kernels' roofline next to the figure derived from SM count,
+ * FP32 lanes and clock.  Synchronous, on the default stream; takes a few
+ * milliseconds.  NPP_INVALID_ARG for a NULL output or packed not 0/1,
+ * NPP_CUDA_ERROR if the device is unavailable. */
+npp_status npp_measure_fma_peak(int32_t device, int32_t packed, double* fma_per_s);
+
 /* ---------------------------------------------------------------------
  * Device-resident closed loop (Alg. 1): each sampling time is one CUDA graph
  * replay holding the plan step and an advance kernel that applies the

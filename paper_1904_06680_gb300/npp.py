@@ -84,7 +84,7 @@ EXPORTS = ("npp_create", "npp_destroy", "npp_last_error", "npp_n_theta", "npp_pl
            "npp_proposal_set_params", "npp_proposal_get_params", "npp_proposal_get_grads",
            "npp_proposal_encode", "npp_proposal_forward", "npp_proposal_train_step",
            "npp_plan_step_proposal", "npp_gemm_bf16", "npp_gemm_status", "npp_plan_tshc",
-           "npp_loop_create_mission", "npp_loop_points")
+           "npp_loop_create_mission", "npp_loop_points", "npp_measure_fma_peak")
 
 _lib = None
 
@@ -114,6 +114,7 @@ def lib():
         L.npp_set_timing.argtypes = [P, I32]
         L.npp_set_option.argtypes = [P, C.c_char_p, I32]
         L.npp_set_footprint.argtypes = [P, C.c_void_p, C.c_void_p, I32]
+        L.npp_measure_fma_peak.argtypes = [I32, I32, C.POINTER(C.c_double)]
         L.npp_loop_create.argtypes = [P, C.POINTER(npp_state), P, I32, P, P, I32, I32, I32, U64, I32,
                                       C.POINTER(P)]
         L.npp_loop_run.argtypes = [P, I32, P]
@@ -209,6 +210,13 @@ def npp_destroy(h):
 def npp_last_error(h=None) -> str:
     r = lib().npp_last_error(h)
     return r.decode() if r else ""
+
+
+def npp_measure_fma_peak(device=0, packed=False):
+    """FP32 FMAs per second on independent FMA streams (scalar or packed)."""
+    v = C.c_double()
+    _check(lib().npp_measure_fma_peak(int(device), int(bool(packed)), C.byref(v)))
+    return v.value
 
 
 def npp_set_footprint(h, pieces):

@@ -52,3 +52,24 @@ def test_heading_sincos_bound():
     ec = np.abs(c - np.cos(p64))
     assert es.max() < 1e-6, (es.max(), phi[np.argmax(es)])
     assert ec.max() < 1e-6, (ec.max(), phi[np.argmax(ec)])
+
+
+def test_fma_peak_microbenchmark():
+    """The FMA-stream microbenchmark (roofline denominator) against the
+    device's FP32 lanes at its maximum clock: between half and all of it
+    (a few per cent above only from clock-reading noise)."""
+    import subprocess
+    import torch
+    from paper_1904_06680_gb300 import npp
+    props = torch.cuda.get_device_properties(0)
+    try:
+        mhz = float(subprocess.run(["nvidia-smi", "-i", "0", "--query-gpu=clocks.max.sm",
+                                    "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                   timeout=10).stdout.split()[0])
+    except (OSError, ValueError, IndexError, subprocess.TimeoutExpired):
+        pytest.skip("no SM clock reading")
+    derived = props.multi_processor_count * 128 * mhz * 1e6
+    for packed in (False, True):
+        r = npp.npp_measure_fma_peak(0, packed) / derived
+        assert 0.5 < r < 1.05, (packed, r)
+    assert npp.lib().npp_measure_fma_peak(0, 2, None) == npp.NPP_INVALID_ARG

@@ -166,26 +166,6 @@ static cudaError_t launch_fused(const npp_handle* h, const RolloutArgs& a, cudaS
     }
 }
 
-// First sample of the tail of a binned plan step's trajectory launch: the
-// samples of all full waves of the trajectory kernel, or 0 (no split) when
-// the samples fill at most one wave or a whole number of waves.
-static int split_point(npp_handle* h, const RolloutArgs& a)
-{
-    if (!h->split) return 0;
-    const int key = h->cfg.width * 16 + h->traj_variant * 2 + (uses_variants(a.c) ? 1 : 0);
-    if (h->wave_key != key) {
-        switch (h->cfg.width) {
-        case 16: h->wave_samples = traj_wave_w16(a, h->traj_variant, h->sm_count); break;
-        case 32: h->wave_samples = traj_wave_w32(a, h->traj_variant, h->sm_count); break;
-        default: h->wave_samples = traj_wave_w64(a, h->traj_variant, h->sm_count); break;
-        }
-        h->wave_key = key;
-    }
-    const int w = h->wave_samples;
-    if (w <= 0 || a.N <= w || a.N % w == 0) return 0;
-    return (a.N / w) * w;
-}
-
 npp_status run_rollout(npp_handle* h, RolloutArgs& a, cudaStream_t s, bool allow_fused, bool* fused)
 {
     a.coefA = h->d_coefA;
@@ -232,34 +212,6 @@ npp_status run_rollout(npp_handle* h, RolloutArgs& a, cudaStream_t s, bool allow
             CUDA_TRY(h, cudaStreamWaitEvent(h->side, h->fork_ev, 0));
             CUDA_TRY(h, build_bins(a, h->cfg.half_len, h->cfg.half_wid, h->cfg.c_off, h->d_bins, h->side));
             CUDA_TRY(h, cudaEventRecord(h->join_ev, h->side));
-            const int n1 = split_point(h, a);
-            if (n1 > 0) {
-                // trajectories of the full waves; then, concurrently, the
-                // tail's trajectories (high priority: its check is last) and
-                // the first part's check (low priority, filling the SMs the
-                // tail leaves idle); then the tail's check
-                RolloutArgs a1 = a, a2 = a;
-                a1.n_lo = 0;
-                a1.n_hi = n1;
-                a2.n_lo = n1;
-                a2.n_hi = a.N;
-                CUDA_TRY(h, launch_traj(h, a1, s));
-                CUDA_TRY(h, cudaEventRecord(h->ev_tA, s));
-                CUDA_TRY(h, cudaStreamWaitEvent(h->hp, h->ev_tA, 0));
-                CUDA_TRY(h, launch_traj(h, a2, h->hp));
-                CUDA_TRY(h, cudaEventRecord(h->ev_tB, h->hp));
-                CUDA_TRY(h, cudaStreamWaitEvent(h->side2, h->ev_tA, 0));
-                CUDA_TRY(h, cudaStreamWaitEvent(h->side2, h->join_ev, 0));
-                CUDA_TRY(h, launch_collide_binned(a1, h->side2));
-                CUDA_TRY(h, cudaEventRecord(h->ev_cA, h->side2));
-                CUDA_TRY(h, cudaStreamWaitEvent(s, h->ev_tB, 0));
-                if (h->timing) CUDA_TRY(h, record_event(h->ev[1], s));
-                CUDA_TRY(h, cudaStreamWaitEvent(s, h->join_ev, 0));
-                CUDA_TRY(h, launch_collide_binned(a2, s));
-                CUDA_TRY(h, cudaStreamWaitEvent(s, h->ev_cA, 0));
-                if (h->timing) CUDA_TRY(h, record_event(h->ev[2], s));
-                return NPP_OK;
-            }
             CUDA_TRY(h, launch_traj(h, a, s));
             if (h->timing) CUDA_TRY(h, record_event(h->ev[1], s));
             CUDA_TRY(h, cudaStreamWaitEvent(s, h->join_ev, 0));
@@ -443,15 +395,6 @@ npp_status npp_create(npp_handle** out, const npp_config* cfg, int32_t device)
     A((void**)&h->d_fh, (size_t)cfg->max_N * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
-    int prio_least = 0, prio_greatest = 0;
-    cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
-    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->side2, cudaStreamNonBlocking, prio_least);
-    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->hp, cudaStreamNonBlocking, prio_greatest);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_tA, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_tB, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_cA, cudaEventDisableTiming);
-    h->split = true;
-    h->wave_key = -1;
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming);
     for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&h->ev[i]);
@@ -469,7 +412,6 @@ npp_status npp_destroy(npp_handle* h)
     if (!h) return NPP_OK;
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
-    for (cudaStream_t st : { h->side, h->side2, h->hp }) if (st) cudaStreamSynchronize(st);
     void* ptrs[] = { h->d_key, h->d_traj, h->d_ctrl, h->d_jfree, h->d_vfirst, h->d_fp, h->d_coefA, h->d_coefB, h->d_work,
                      h->d_pXY, h->d_pV, h->d_bins,
                      h->d_obs, h->d_warm, h->d_sigma, h->d_best, h->d_params, h->d_controls, h->d_trajectory,
@@ -479,9 +421,6 @@ npp_status npp_destroy(npp_handle* h)
     if (h->side) { cudaStreamSynchronize(h->side); cudaStreamDestroy(h->side); }
     if (h->fork_ev) cudaEventDestroy(h->fork_ev);
     if (h->join_ev) cudaEventDestroy(h->join_ev);
-    if (h->side2) cudaStreamDestroy(h->side2);
-    if (h->hp) cudaStreamDestroy(h->hp);
-    for (cudaEvent_t ev : { h->ev_tA, h->ev_tB, h->ev_cA }) if (ev) cudaEventDestroy(ev);
     for (int i = 0; i < 4; ++i) if (h->ev[i]) cudaEventDestroy(h->ev[i]);
     delete h;
     return NPP_OK;
@@ -713,11 +652,6 @@ npp_status npp_set_option(npp_handle* h, const char* name, int32_t value)
             return fail(h, NPP_INVALID_ARG, "collide_variant is -1..%d", COLLIDE_BINNED);
         h->collide_variant = value;
         h->occ_M = -1;
-        return NPP_OK;
-    }
-    if (std::strcmp(name, "split") == 0) {
-        if (value != 0 && value != 1) return fail(h, NPP_INVALID_ARG, "split is 0 or 1");
-        h->split = value != 0;
         return NPP_OK;
     }
     if (std::strcmp(name, "fuse") == 0) {

@@ -52,10 +52,9 @@ __global__ void __launch_bounds__(BINNED_WARPS * 32) collide_binned_kernel(const
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const BinView& g = a.bins;
     const int T = a.T, N = a.N, M = a.M;
-    const int n = a.n_lo + blockIdx.x * BINNED_WARPS + warp;
-    const int n_hi = a.n_hi > 0 ? a.n_hi : N;
+    const int n = blockIdx.x * BINNED_WARPS + warp;
     unsigned long long key = ~0ull;
-    if (n < n_hi) {
+    if (n < N) {
         int fh = -1;
         // the next step's rows are loaded while the current step is checked
         float4 nca = a.coefA[n];
@@ -105,7 +104,7 @@ __global__ void __launch_bounds__(BINNED_WARPS * 32) collide_binned_kernel(const
     }
     // each warp folds its key into the minimum on its own (no block barrier:
     // samples end at different steps); the read skips atomics that cannot win
-    if (lane == 0 && n < n_hi && a.best_key && key < *reinterpret_cast<volatile unsigned long long*>(a.best_key))
+    if (lane == 0 && n < N && a.best_key && key < *reinterpret_cast<volatile unsigned long long*>(a.best_key))
         atomicMin(a.best_key, key);
 }
 
@@ -149,8 +148,7 @@ cudaError_t build_bins_radius(RolloutArgs& a, double radius, void* workspace, cu
 
 cudaError_t launch_collide_binned(const RolloutArgs& a, cudaStream_t s)
 {
-    const int n = (a.n_hi > 0 ? a.n_hi : a.N) - a.n_lo;
-    collide_binned_kernel<<<(n + BINNED_WARPS - 1) / BINNED_WARPS, BINNED_WARPS * 32, 0, s>>>(a);
+    collide_binned_kernel<<<(a.N + BINNED_WARPS - 1) / BINNED_WARPS, BINNED_WARPS * 32, 0, s>>>(a);
     return cudaGetLastError();
 }
 

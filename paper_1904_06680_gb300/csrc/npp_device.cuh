@@ -28,9 +28,6 @@ struct DevCfg {
     float v_lo, v_hi;                // [v_lo, v_hi]
 };
 
-// Whether a configuration turns on a rollout variant (VAR kernels).
-__host__ __device__ inline bool uses_variants(const DevCfg& c) { return c.body_frame != 0 || c.vlim != 0; }
-
 // The device constants of a validated configuration (host side).
 inline DevCfg devcfg_from(const npp_config& cfg)
 {
@@ -437,8 +434,6 @@ struct RolloutArgs {
     float4* pV;                        // points exceed shared memory), [ceil(M/2)]
     BinView bins;                      // per-step grids (binned and fused collision checks)
     PolyView poly;                     // general footprint (polygon checks)
-    int n_lo, n_hi;                    // samples of this launch of the trajectory and binned
-                                       // kernels: [n_lo, n_hi), n_hi = 0 meaning N
 };
 
 __device__ __forceinline__ StepIn step_in(const RolloutArgs& a)
@@ -501,9 +496,6 @@ cudaError_t build_bins(RolloutArgs& a, float half_len, float half_wid, float c_o
                        cudaStream_t s);          // fills a.bins
 cudaError_t launch_collide_binned(const RolloutArgs& a, cudaStream_t s);
 cudaError_t launch_collide_poly(const RolloutArgs& a, cudaStream_t s);
-int traj_wave_w16(const RolloutArgs& a, int variant, int sm_count);
-int traj_wave_w32(const RolloutArgs& a, int variant, int sm_count);
-int traj_wave_w64(const RolloutArgs& a, int variant, int sm_count);
 cudaError_t build_bins_radius(RolloutArgs& a, double radius, void* workspace, cudaStream_t s);
 cudaError_t launch_epilogue(const EpilogueArgs& e, cudaStream_t s);
 void set_global_error(const char* msg);

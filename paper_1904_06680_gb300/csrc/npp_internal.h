@@ -56,13 +56,6 @@ struct npp_handle {
     cudaStream_t stream;
     cudaStream_t side;                   // concurrent branch of a plan step (grid build)
     cudaEvent_t fork_ev, join_ev;
-    // split binned plan step: the trajectories of all full waves, then the
-    // tail (high-priority stream) while the first part is checked (low
-    // priority), then the tail's check
-    bool split;                          // option "split" (default on)
-    cudaStream_t side2, hp;
-    cudaEvent_t ev_tA, ev_tB, ev_cA;
-    int wave_key, wave_samples;          // cached samples per full trajectory wave
     bool timing;
     cudaEvent_t ev[4];                   // start, after trajectories, after collisions, end
     std::string err;

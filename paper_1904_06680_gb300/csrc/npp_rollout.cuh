@@ -612,8 +612,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) traj_kernel(const RolloutArgs a
     extern __shared__ float stage_all[];        // [LaneNet::SLOTS][NW * 32] when W == 32
     const int tid = threadIdx.x;
     const int b = tid / G, gl = tid % G;
-    const int n = a.n_lo + blockIdx.x * B + b;
-    const int n_hi = a.n_hi > 0 ? a.n_hi : a.N;
+    const int n = blockIdx.x * B + b;
     TrajJob job;
     job.si = step_in(a);
     job.key = a.key;
@@ -637,7 +636,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) traj_kernel(const RolloutArgs a
     // staged parameter generation pays at W = 32 (measured on GB300: 11 %
     // faster at T = 40); at W = 16 and 64 the direct load is faster
     constexpr int STAGE_TH = W == 32 ? NW * 32 : 0;
-    traj_sample<W, G, false, STAGE_TH, VAR>(a.c, job, n, n < n_hi, gl, hx_all + b * W);
+    traj_sample<W, G, false, STAGE_TH, VAR>(a.c, job, n, n < a.N, gl, hx_all + b * W);
 }
 
 // Trajectories with the binned check fused in: per sample its first
@@ -1307,32 +1306,19 @@ inline cudaError_t ensure_smem(KernelFn fn, int smem)
     return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
+// Whether a configuration turns on a rollout variant (VAR kernels).
+__host__ __device__ inline bool uses_variants(const DevCfg& c) { return c.body_frame != 0 || c.vlim != 0; }
+
 template <int W, int G, int NW, int MINB = 1, bool VAR = false>
 cudaError_t launch_traj(const RolloutArgs& a, cudaStream_t stream)
 {
     using K = TrajKernel<W, G, NW>;
-    const int n_hi = a.n_hi > 0 ? a.n_hi : a.N;
-    const int grid = (n_hi - a.n_lo + K::B - 1) / K::B;
+    const int grid = (a.N + K::B - 1) / K::B;
     const int smem = W == 32 ? LaneNet<W, G>::SLOTS * K::THREADS * (int)sizeof(float) : 0;
     cudaError_t e = ensure_smem(traj_kernel<W, G, NW, MINB, VAR>, smem);
     if (e != cudaSuccess) return e;
     traj_kernel<W, G, NW, MINB, VAR><<<grid, K::THREADS, smem, stream>>>(a);
     return cudaGetLastError();
-}
-
-// samples of one full wave of the trajectory kernel (every SM holding as
-// many blocks as fit), 0 if unknown
-template <int W, int G, int NW, int MINB = 1, bool VAR = false>
-int traj_wave(int sm_count)
-{
-    using K = TrajKernel<W, G, NW>;
-    const int smem = W == 32 ? LaneNet<W, G>::SLOTS * K::THREADS * (int)sizeof(float) : 0;
-    if (ensure_smem(traj_kernel<W, G, NW, MINB, VAR>, smem) != cudaSuccess) return 0;
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, traj_kernel<W, G, NW, MINB, VAR>, K::THREADS, smem) !=
-        cudaSuccess)
-        return 0;
-    return nb * sm_count * K::B;
 }
 
 template <int W, int G, int NW, int MINB = 1, bool VAR = false>

@@ -29,17 +29,6 @@ cudaError_t launch_fused_w16(const RolloutArgs& a, cudaStream_t s, int variant)
     }
 }
 
-int traj_wave_w16(const RolloutArgs& a, int variant, int sm_count)
-{
-    if (uses_variants(a.c)) return traj_wave<16, 8, 4, 4, true>(sm_count);
-    switch (variant) {
-    case 1: return traj_wave<16, 4, 8>(sm_count);
-    case 2: return traj_wave<16, 8, 8>(sm_count);
-    case 3: return traj_wave<16, 8, 8, 3>(sm_count);
-    default: return traj_wave<16, 8, 4, 4>(sm_count);
-    }
-}
-
 cudaError_t launch_reroll_w16(const RolloutArgs& a, const EpilogueArgs& e, cudaStream_t s)
 {
     return launch_reroll<16, 8>(a, e, s);

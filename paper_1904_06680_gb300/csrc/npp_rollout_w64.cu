@@ -29,17 +29,6 @@ cudaError_t launch_fused_w64(const RolloutArgs& a, cudaStream_t s, int variant)
     }
 }
 
-int traj_wave_w64(const RolloutArgs& a, int variant, int sm_count)
-{
-    if (uses_variants(a.c)) return traj_wave<64, 32, 1, 10, true>(sm_count);
-    switch (variant) {
-    case 1: return traj_wave<64, 16, 8>(sm_count);
-    case 2: return traj_wave<64, 32, 8>(sm_count);
-    case 3: return traj_wave<64, 32, 2, 5>(sm_count);
-    default: return traj_wave<64, 32, 1, 10>(sm_count);
-    }
-}
-
 cudaError_t launch_reroll_w64(const RolloutArgs& a, const EpilogueArgs& e, cudaStream_t s)
 {
     return launch_reroll<64, 32>(a, e, s);

@@ -214,25 +214,3 @@ def test_all_variants_at_extreme_sizes(N, T, M):
         _assert_same(_plan(sc, v), ref)
     for fuse in (0, 1):
         _assert_same(_plan(sc, BINNED, fuse=fuse), ref)
-
-
-@pytest.mark.parametrize("N", [5000, 16384, 4096])
-def test_split_plan_step_identical(N):
-    """Trajectories split at the last full wave, the first part's check
-    overlapping the tail: the same flags, costs, winner and rows as one
-    trajectory launch followed by one check (N = 4096 fits one wave: no
-    split)."""
-    import torch
-    from paper_1904_06680_gb300 import npp
-    sc = inputs.scene_course(1, N=N)
-    M = sc["obs"].shape[0]
-    res = []
-    for split in (0, 1):
-        pl = npp.Planner(sc["preset"], max_N=N, max_T=sc["T"], max_M=M)
-        npp.npp_set_option(pl.h, "split", split)
-        obs = torch.tensor(sc["obs"], dtype=torch.float32, device="cuda")
-        pl.plan(sc["state"], sc["goal"], obs, N, sc["T"], sc["seed"], 3)
-        torch.cuda.synchronize()
-        res.append(pl.result(N, sc["T"]))
-        pl.close()
-    _assert_same(res[0], res[1])

@@ -753,6 +753,9 @@ def run_mission(args):
     import torch
     from paper_1904_06680_gb300 import inputs, npp
     rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     n_missions = args.missions
@@ -796,12 +799,24 @@ def run_mission(args):
     ck = clocks.stop()
     wall = time.perf_counter() - t_wall
     tot_ms = float(np.sum(step_ms))
+    units = float(N * T * len(step_ms))
+    if world > 1:
+        # every rank flies its own missions (seeds offset by rank): units of
+        # all ranks over the slowest rank's device time
+        import torch.distributed as dist
+        from paper_1904_06680_gb300 import multi
+        u = torch.tensor([units], dtype=torch.float64, device=dev)
+        dist.all_reduce(u)
+        units = float(u.item())
+        tot_ms = multi.max_over_ranks([tot_ms], dev)[0]
+        dist.barrier()
+        dist.destroy_process_group()
     ok = [r for r in results if r["completed"] and r["collisions"] == 0]
-    line = {"metric": "rollout_steps_per_s", "value": N * T * len(step_ms) / (tot_ms * 1e-3),
+    line = {"metric": "rollout_steps_per_s", "value": units / (tot_ms * 1e-3),
             "unit": "rollout-steps/s", "n_gpus": world, "steps": len(step_ms), "warmup": args.warmup,
             "ms_per_step": tot_ms / len(step_ms), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "mission", "description":
+            "config": {"workload": "mission", "parallelism": "replicas (rank = mission seeds)", "description":
                        "road missions (reference path along a winding two-lane road, 150 m; six parked cars "
                        "in the lane, an oncoming car; range field 25/8/10 m with points outside it hidden): "
                        "N=%d samples, T=%d, MLP 8-%d-%d-2, one plan step per sampling time" % (N, T, W, W),

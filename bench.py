@@ -222,9 +222,11 @@ def cpu_baseline(sc, state, goal, obs, T, workload, target_cpu_s=15.0):
                         record=False)
     wall = time.perf_counter() - t0
     return {"value": K * T / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "single_thread": len(probe) * T / (per_sample * len(probe)),
             "sample": "first plan step of the %s scene: %d samples (the step draws %d) over "
                       "the full horizon T=%d, M=%d points (brute force), FP64 C with OpenMP "
-                      "(%.1f s wall)" % (workload, K, sc["N"], T, obs.shape[0], wall)}
+                      "(%.1f s wall); single_thread: 64 samples on one core" % (
+                          workload, K, sc["N"], T, obs.shape[0], wall)}
 
 
 def run_npp(args):

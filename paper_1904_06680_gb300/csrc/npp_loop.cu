@@ -126,10 +126,10 @@ __device__ void mission_update(LoopDev* d, const float4* ref)
     if (reached(d, ref[d->stop])) {
         if (d->stop == n - 1) {
             d->done = 1;
-            return;
+        } else {
+            d->idx = d->stop;
+            d->stop = next_stop(ref, n, d->stop + 1);
         }
-        d->idx = d->stop;
-        d->stop = next_stop(ref, n, d->stop + 1);
     }
     select_goal(d, ref);
 }

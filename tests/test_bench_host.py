@@ -1,0 +1,34 @@
+"""Host-side pieces of the benchmark that decide reported outcomes, checked
+on the CPU: the collision check of executed poses (mission success) against
+the oracle's point-in-rectangle test, and the algorithmic-work counts."""
+import numpy as np
+
+import bench
+from paper_1904_06680_gb300 import inputs
+
+
+def test_executed_collisions_match_oracle(orc):
+    p = inputs.planner(32)
+    rng = np.random.default_rng(3)
+    obs = np.zeros((40, 4))
+    obs[:, :2] = rng.uniform(-10, 10, (40, 2))
+    obs[:15, 2:] = rng.uniform(-1, 1, (15, 2))
+    log = np.zeros((60, 8), np.float32)
+    log[:, 0] = rng.uniform(-6, 6, 60)
+    log[:, 1] = rng.uniform(-6, 6, 60)
+    log[:, 2] = rng.uniform(-3, 3, 60)
+    got = bench.executed_collisions(log, obs, p)
+    want = [t for t in range(60)
+            if orc.collide(p, float(log[t, 0]), float(log[t, 1]), float(log[t, 2]), obs, tau=t * p["Ts"])[0]]
+    assert got == want
+    assert 0 < len(want) < 60
+
+
+def test_algorithmic_work_counts():
+    fh = np.array([-1, 0, 5, 39])
+    T, M, W = 40, 100, 32
+    fma_c, fma_t, checks = bench.algorithmic_work(fh, T, M, W)
+    live_states = (T + 1) + 1 + 6 + 40          # states 0..first_hit (all T+1 if free)
+    assert checks == live_states * M
+    assert fma_c == 4.0 * checks
+    assert fma_t == (T + 0 + 5 + 39) * (W * W + 10 * W)

@@ -247,3 +247,21 @@ def test_collide_variants_identical():
         npp.npp_set_option(pl.h, "collide_variant", 6)
     npp.npp_set_option(pl.h, "collide_variant", -1)
     pl.close()
+
+
+def test_steering_rate_limit_on_every_rollout():
+    """Fig. 8: the applied normalised steering moves by at most
+    delta_rate_max Ts / delta_max per step (and stays in [-1, 1]) in every
+    step of every sample of a full-size plan step."""
+    sc = inputs.scene_course(0)
+    g = P.gpu_plan(sc, record=True)
+    p = sc["preset"]
+    r = np.float32(p["delta_rate_max"] * p["Ts"] / p["delta_max"])
+    a0 = g["sample_ctrl"][:, :, 0]                        # [T][N]
+    prev = np.vstack([np.full((1, a0.shape[1]), np.float32(sc["state"][4])), a0[:-1]])
+    fh = g["first_hit"]
+    live = np.arange(sc["T"])[:, None] < np.where(fh < 0, sc["T"], fh)[None, :]
+    step = np.abs(a0 - prev)[live]
+    assert step.max() <= r * (1 + 2 ** -22) + 2 ** -23, step.max()
+    assert np.abs(a0[live]).max() <= 1.0
+    assert np.mean(step >= r * (1 - 1e-6)) > 0.1           # the limit binds often

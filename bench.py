@@ -798,6 +798,25 @@ def run_mission(args):
         hits = executed_collisions(log, sc["obs"], sc["preset"])
         results.append(dict(seed=args.seed + k, completed=bool(st["done"]), steps=int(st["t"]),
                             done_at=done_at, collisions=len(hits), n_infeasible=int(st["n_infeasible"])))
+    # the reverse parking mission (Experiment 5) over the same seeds: outcome only
+    parking = []
+    for k in range(n_missions):
+        sp = inputs.scene_parking(args.seed + k + rank * 1000)
+        Mp = sp["obs"].shape[0]
+        pl = npp.Planner(sp["preset"], max_N=sp["N"], max_T=sp["T"], max_M=Mp, device=local)
+        obs = torch.tensor(sp["obs"], dtype=torch.float32, device=dev)
+        L = npp.npp_loop_create(pl.h, sp["state"], sp["waypoints"], inputs.EPS, obs, Mp, sp["N"], sp["T"],
+                                sp["seed"], max_log=max_steps)
+        for t in range(max_steps):
+            npp.npp_loop_run(L, 1)
+            st = npp.npp_loop_read(L)
+            if st["done"]:
+                break
+        log = npp.npp_loop_log(L, max_steps)
+        npp.npp_loop_destroy(L)
+        pl.close()
+        parking.append(dict(seed=args.seed + k, completed=bool(st["done"]), steps=int(st["t"]),
+                            collisions=len(executed_collisions(log, sp["obs"], sp["preset"]))))
     ck = clocks.stop()
     wall = time.perf_counter() - t_wall
     tot_ms = float(np.sum(step_ms))
@@ -828,6 +847,10 @@ def run_mission(args):
                         "sampling_times_mean": float(np.mean([r["steps"] for r in ok])) if ok else None,
                         "sampling_times_max": max((r["steps"] for r in ok), default=None),
                         "runs": results, "wall_s": wall},
+            "parking": {"completed": sum(r["completed"] for r in parking),
+                        "collision_free_and_completed": sum(r["completed"] and r["collisions"] == 0 for r in parking),
+                        "of": len(parking), "description": "reverse parking (Experiment 5: auxiliary waypoint, "
+                        "then the slot), N=16384, T=60, MLP 8-16-16-2", "runs": parking},
             "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": launches, "clocks": ck}
     if rank == 0:
         print(json.dumps(line))

@@ -52,6 +52,11 @@ Scene recipes (all world-frame, SI units; obstacles are (x, y, vx, vy)):
   vehicle in the far lane at 1 m/s.  Start at rest on the centre line.
   8-32-32-2, N = 8192, T = 40; range field 25 m ahead, 8 m behind, 10 m to
   either side.
+* ``scene_parking``: the reverse parking mission of the paper's Experiment 5
+  (Fig. 8, bottom row) in the scaled slot layout of ``scene_batch``: start at
+  rest at (0, 2.5) facing +x, an auxiliary waypoint at the origin facing +y,
+  then the parking position inside the slot (0, -6.25) facing +y, both at
+  rest; the walls as points every 0.25 m; 8-16-16-2, N = 16384, T = 60.
 """
 import math
 
@@ -428,3 +433,15 @@ def scene_mission(seed: int = 0, N: int = 8192, T: int = 40, width: int = 32, le
     state = np.array([0.0, ref[0, 1], ref[0, 2], 0.0, 0.0, 0.0])
     return dict(preset=planner(width), state=state, goal=ref[-1].copy(), obs=obs, N=N, T=T,
                 seed=philox_seed(seed), t_index=0, ref=ref, field=MISSION_FIELD, window=20)
+
+
+def scene_parking(seed: int = 0, N: int = 16384, T: int = 60, width: int = 16):
+    """See the module docstring (the scene is fixed; `seed` picks the
+    sampler's Philox seed, as the paper's ten random seeds)."""
+    walls = parking_walls()
+    obs = np.zeros((len(walls), 4))
+    obs[:, :2] = walls
+    waypoints = np.array([[0.0, 0.0, math.pi / 2, 0.0], [0.0, -6.25, math.pi / 2, 0.0]])
+    state = np.array([0.0, 2.5, 0.0, 0.0, 0.0, 0.0])
+    return dict(preset=planner(width), state=state, goal=waypoints[0].copy(), obs=obs, N=N, T=T,
+                seed=philox_seed(seed), t_index=0, waypoints=waypoints)

@@ -131,3 +131,26 @@ def test_road_mission_completes_collision_free(orc, seed):
         assert not hit, t
     # it got past every parked car: the space index reached the end
     assert st["space_index"] >= len(sc["ref"]) - 3
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_parking_mission_completes_collision_free(orc, seed):
+    """Experiment 5 (reverse parking, auxiliary waypoint then the slot): both
+    waypoints reached within the tolerances, no executed pose in collision."""
+    import torch
+    from paper_1904_06680_gb300 import npp
+    sc = inputs.scene_parking(seed)
+    M = sc["obs"].shape[0]
+    pl = npp.Planner(sc["preset"], max_N=sc["N"], max_T=sc["T"], max_M=M)
+    obs = torch.tensor(sc["obs"], dtype=torch.float32, device="cuda")
+    L = npp.npp_loop_create(pl.h, sc["state"], sc["waypoints"], inputs.EPS, obs, M, sc["N"], sc["T"], sc["seed"],
+                            max_log=800)
+    st = _run_until_done(L, 800)
+    log = npp.npp_loop_log(L, 800)
+    npp.npp_loop_destroy(L)
+    pl.close()
+    assert st["done"] and st["waypoint"] == 1, st
+    p = sc["preset"]
+    for t in range(len(log)):
+        assert not orc.collide(p, float(log[t, 0]), float(log[t, 1]), float(log[t, 2]), sc["obs"])[0], t
+    assert np.any(log[:, 3] < -0.2)               # it reversed into the slot

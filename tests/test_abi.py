@@ -4,6 +4,10 @@ import ctypes
 import os
 import re
 
+import pytest
+
+from paper_1904_06680_gb300 import inputs
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -39,3 +43,14 @@ def test_n_theta_and_config_validation_without_device():
         assert npp.npp_n_theta(npp.make_config(inputs.planner(w), 1, 1, 1)) == n
     assert npp.npp_n_theta(npp.make_config(dict(inputs.planner(16), widths=(8, 24, 24, 2)), 1, 1, 1)) == -1
     assert npp.npp_n_theta(npp.make_config(inputs.PAPER, 1, 1, 1)) == -1
+
+
+def test_binding_fails_loudly_without_library(monkeypatch):
+    """No CPU fallback: without the built library every entry point raises."""
+    from paper_1904_06680_gb300 import npp
+    monkeypatch.setattr(npp, "_lib", None)
+    monkeypatch.setattr(npp, "LIB_PATH", os.path.join(os.path.dirname(npp.LIB_PATH), "missing", "libnpp.so"))
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        npp.lib()
+    with pytest.raises(RuntimeError):
+        npp.npp_n_theta(npp.make_config(inputs.planner(16), 1, 1, 1))

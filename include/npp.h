@@ -407,7 +407,17 @@ npp_status npp_batch_destroy(npp_batch* B);
  * it runs, because cudaMalloc may synchronise the device and take unbounded
  * time.  There is no counterpart in the paper; it is a deployment variant.
  *
- * No handle: the constants come from cfg (its max_* fields are ignored), the
+ * It runs npp_plan_step's trajectory kernel and winner epilogue with one
+ * collision check whatever M and N are: the brute-force check with all
+ * points in shared memory (collide_variant 3 for N <= 8192, else 4), never
+ * the spatial binning a handle picks for many points.  So M is limited to
+ * the points shared memory holds (about 14,000 on GB300; more returns
+ * NPP_UNSUPPORTED) and a large M * N runs slower than npp_plan_step.  All
+ * collision checks give the same flags, so the outputs equal
+ * npp_plan_step's.
+ *
+ * No handle: the constants come from cfg (its max_* fields are ignored and
+ * it is checked as npp_create checks it), the
  * workspace is one fixed file-scope device array of about 33 MB that every
  * GPU loading this part of the library holds until the process exits.
  * Limits: 1 <= N <= 16384 and N * (T + 1) <= 688128 sample-steps (for

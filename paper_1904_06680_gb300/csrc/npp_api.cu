@@ -333,16 +333,9 @@ npp_status npp_create(npp_handle** out, const npp_config* cfg, int32_t device)
     if (npp_n_theta(cfg) < 0)
         return fail(nullptr, NPP_UNSUPPORTED, "network [%d, %d, %d, 2] is not built (n_in 8; width 16, 32, 64)",
                     cfg->n_in, cfg->width, cfg->width);
-    const float* f = &cfg->lf;
-    if (!finite_all(f, 18)) return fail(nullptr, NPP_INVALID_ARG, "config has a non-finite constant");
-    if (!(cfg->lf + cfg->lr > 0.f) || !(cfg->lr >= 0.f) || !(cfg->delta_max > 0.f) ||
-        !(cfg->delta_rate_max > 0.f) || !(cfg->u_max >= cfg->u_min) || !(cfg->Ts > 0.f) ||
-        !(cfg->half_len > 0.f) || !(cfg->half_wid > 0.f) || !(cfg->dxi_n > 0.f) ||
-        !(cfg->deta_n > 0.f) || !(cfg->dphi_n > 0.f) || !(cfg->dv_n > 0.f))
-        return fail(nullptr, NPP_INVALID_ARG, "config constant out of range");
+    if (const char* ce = config_error(*cfg)) return fail(nullptr, NPP_INVALID_ARG, "%s", ce);
     if (cfg->max_N < 1 || cfg->max_T < 1 || cfg->max_M < 0)
         return fail(nullptr, NPP_INVALID_ARG, "capacity max_N, max_T >= 1, max_M >= 0 required");
-    if (const char* ve = variant_error(*cfg)) return fail(nullptr, NPP_INVALID_ARG, "%s", ve);
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
         return fail(nullptr, NPP_CUDA_ERROR, "CUDA device %d not available", device);

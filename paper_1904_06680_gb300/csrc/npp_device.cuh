@@ -65,6 +65,22 @@ inline const char* variant_error(const npp_config& cfg)
     return nullptr;
 }
 
+// Range check of the vehicle, feature and cost constants and the variant
+// fields of a configuration (not the network shape, not the capacities);
+// null when valid.  Every entry point that takes a configuration uses it.
+inline const char* config_error(const npp_config& cfg)
+{
+    const float* f = &cfg.lf;                // the 18 float constants lf .. w_effort
+    for (int i = 0; i < 18; ++i)
+        if (!std::isfinite(f[i])) return "config has a non-finite constant";
+    if (!(cfg.lf + cfg.lr > 0.f) || !(cfg.lr >= 0.f) || !(cfg.delta_max > 0.f) ||
+        !(cfg.delta_rate_max > 0.f) || !(cfg.u_max >= cfg.u_min) || !(cfg.Ts > 0.f) ||
+        !(cfg.half_len > 0.f) || !(cfg.half_wid > 0.f) || !(cfg.dxi_n > 0.f) ||
+        !(cfg.deta_n > 0.f) || !(cfg.dphi_n > 0.f) || !(cfg.dv_n > 0.f))
+        return "config constant out of range";
+    return variant_error(cfg);
+}
+
 // ------------------------------------------------------------------ sampler
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw: "Parallel random numbers: as
 // easy as 1, 2, 3", SC'11): ten rounds of two 32x32->64 multiplies with the

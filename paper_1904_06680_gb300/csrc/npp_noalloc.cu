@@ -3,9 +3,16 @@
 // Some callers cannot call cudaMalloc: a plugin whose host application owns
 // every device allocation, or a real-time control loop that must not
 // allocate once it runs, because cudaMalloc may synchronise the device and
-// take unbounded time.  npp_plan_step_noalloc serves them: it runs the same
-// kernels as npp_plan_step, but its workspace is one file-scope __device__
-// array of fixed size instead of handle-owned cudaMalloc buffers.
+// take unbounded time.  npp_plan_step_noalloc serves them: it runs the
+// trajectory kernel and the winner epilogue of npp_plan_step, with one
+// collision check -- the brute-force check with the points held in shared
+// memory (items of 8 samples on 4 or 2 point slices) -- whatever M and N
+// are.  It never uses the spatial binning that npp_plan_step picks for many
+// points, so M is limited to the points shared memory holds (about 14,000
+// with the 227 KB of a GB300 block) and a large M * N runs slower than
+// through a handle.  Every collision check gives the same flags, so the
+// results equal npp_plan_step's.  Its workspace is one file-scope
+// __device__ array of fixed size instead of handle-owned cudaMalloc buffers.
 //
 // The array (NOALLOC_BYTES, about 33 MB) exists on every GPU on which this
 // library's module is loaded, until the process exits.  All calls share it,
@@ -76,12 +83,8 @@ extern "C" npp_status npp_plan_step_noalloc(const npp_config* cfg, const npp_sta
     if (cfg->n_in != 8 || (cfg->width != 16 && cfg->width != 32 && cfg->width != 64))
         return fail_noalloc(NPP_UNSUPPORTED, "noalloc: network [%d, %d, %d, 2] is not built",
                             cfg->n_in, cfg->width, cfg->width);
-    if (!finite_n(&cfg->lf, 18) || !(cfg->lf + cfg->lr > 0.f) || !(cfg->delta_max > 0.f) ||
-        !(cfg->delta_rate_max > 0.f) || !(cfg->Ts > 0.f) || !(cfg->half_len > 0.f) ||
-        !(cfg->half_wid > 0.f) || !(cfg->dxi_n > 0.f) || !(cfg->deta_n > 0.f) ||
-        !(cfg->dphi_n > 0.f) || !(cfg->dv_n > 0.f) || !(cfg->u_max >= cfg->u_min))
-        return fail_noalloc(NPP_INVALID_ARG, "noalloc: config constant out of range");
-    if (const char* ve = variant_error(*cfg)) return fail_noalloc(NPP_INVALID_ARG, "noalloc: %s", ve);
+    // the same checks as npp_create
+    if (const char* ce = config_error(*cfg)) return fail_noalloc(NPP_INVALID_ARG, "noalloc: %s", ce);
     if (!finite_n(&state->x, 6) || !finite_n(&goal->x, 4) ||
         std::fabs(state->a_prev0) > 1.0f || std::fabs(state->a_prev1) > 1.0f)
         return fail_noalloc(NPP_INVALID_ARG, "noalloc: non-finite state/goal or |a_prev| > 1");

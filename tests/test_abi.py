@@ -3,6 +3,7 @@ include/ declare (no device work: runs without a GPU)."""
 import ctypes
 import os
 import re
+import types
 
 import pytest
 
@@ -54,3 +55,21 @@ def test_binding_fails_loudly_without_library(monkeypatch):
         npp.lib()
     with pytest.raises(RuntimeError):
         npp.npp_n_theta(npp.make_config(inputs.planner(16), 1, 1, 1))
+
+
+def test_config_checks_shared_by_create_and_noalloc():
+    """npp_create and the allocation-free plan step reject the same
+    configurations (the checks run before any device call)."""
+    from paper_1904_06680_gb300 import npp
+    bad = [dict(lr=-0.5), dict(Ts=0.0), dict(half_wid=float("nan")), dict(u_min=3.0, u_max=-3.0),
+           dict(feature_frame=2)]
+    out = npp.npp_outputs()
+    out.best = 16                      # never dereferenced: the configuration is rejected first
+    for b in bad:
+        cfg = npp.make_config(dict(inputs.planner(16), **b), 8, 4, 4)
+        with pytest.raises(npp.NppError) as e1:
+            npp.npp_create(cfg, 0)
+        with pytest.raises(npp.NppError) as e2:
+            npp.npp_plan_step_noalloc(cfg, [0, 0, 0, 0, 0, 0], [5, 0, 0, 0], None, 0, 8, 4, 1, 0, None, out,
+                                      stream=types.SimpleNamespace(cuda_stream=0))
+        assert e1.value.status == e2.value.status == npp.NPP_INVALID_ARG, b

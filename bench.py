@@ -42,9 +42,9 @@ if ROOT not in sys.path:
 
 METRIC = "rollout-steps/s (N×T incl. M-point checks)"
 UNIT = "rollout-steps/s"
-SM_COUNT = 152
-FP32_LANES_PER_SM = 128
-SM_MAX_MHZ = 2070.0
+DEFAULT_FUSE = 0                 # the library's default of the "fuse" option
+FP32_LANES_PER_SM = 128          # FP32 FMA lanes per SM (4 schedulers x 32) on sm_100-class parts
+SM_MAX_MHZ_NOMINAL = 2070.0      # GB300 maximum SM clock, used only when the device does not report it
 
 
 def parse():
@@ -56,14 +56,18 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="course", choices=["course", "large", "batch", "proposal", "mission"],
-                    help="course: the closed-loop course (default); large: N=65536, T=100, "
+    ap.add_argument("--workload", default="large", choices=["course", "large", "batch", "proposal", "mission"],
+                    help="large (default, the largest single-GPU configuration): N=65536, T=100, "
                          "8-64-64-2, 8192 points over 80x80 m with per-step spatial binning; "
+                         "course: the closed-loop forward/reverse course (N=16384, T=40, 8-32-32-2, M=2000); "
                          "batch: 512 parking scenes of uneven N, T, M and width in one "
                          "graph-captured batch; proposal: the learned sampling proposal "
                          "(tensor-core GEMM roofline, training throughput, plan quality)")
     ap.add_argument("--rounds", type=int, default=30, help="proposal workload: training rounds")
     ap.add_argument("--missions", type=int, default=10, help="mission workload: scene seeds")
+    ap.add_argument("--set", action="append", default=[], metavar="NAME=VALUE",
+                    help="course/large: a launch option of the planner handle (npp_set_option), e.g. "
+                         "collide_variant=3 or fuse=0; repeatable")
     ap.add_argument("--footprint", default="rect", choices=["rect", "car"],
                     help="course/large: the rectangle, or a two-piece car outline (general polygon check)")
     return ap.parse_args()
@@ -74,9 +78,75 @@ def dist_env():
     return multi.dist_env()
 
 
+class Nvml:
+    """Read-only NVML queries through ctypes (clocks, clock-event reasons,
+    power) for the device torch calls `cuda_index`; None-valued when the
+    library or the device cannot be found."""
+
+    # clock-event reason bits of NVML
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, cuda_index):
+        import ctypes
+        self.h = None
+        try:
+            self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if self.lib.nvmlInit_v2() != 0:
+                return
+            import torch
+            pr = torch.cuda.get_device_properties(cuda_index)
+            dom, bus, devn = (getattr(pr, k, None) for k in ("pci_domain_id", "pci_bus_id", "pci_device_id"))
+            h = ctypes.c_void_p()
+            if bus is not None:
+                bid = ("%08X:%02X:%02X.0" % (dom or 0, bus, devn or 0)).encode()
+                if self.lib.nvmlDeviceGetHandleByPciBusId_v2(bid, ctypes.byref(h)) != 0:
+                    h = ctypes.c_void_p()
+            if not h.value and self.lib.nvmlDeviceGetHandleByIndex_v2(int(cuda_index), ctypes.byref(h)) != 0:
+                return
+            self.h = h
+            self.reasons_fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                getattr(self.lib, "nvmlDeviceGetCurrentClocksThrottleReasons")
+        except (OSError, AttributeError):
+            self.h = None
+
+    def _u(self, fn, *args):
+        import ctypes
+        v = ctypes.c_uint()
+        return v.value if fn(self.h, *args, ctypes.byref(v)) == 0 else None
+
+    def max_sm_mhz(self):
+        return None if self.h is None else self._u(self.lib.nvmlDeviceGetMaxClockInfo, 1)
+
+    def sample(self):
+        """(sm MHz, reason bits, power W) now."""
+        import ctypes
+        mhz = self._u(self.lib.nvmlDeviceGetClockInfo, 1)
+        r = ctypes.c_ulonglong()
+        bits = r.value if self.reasons_fn(self.h, ctypes.byref(r)) == 0 else 0
+        mw = self._u(self.lib.nvmlDeviceGetPowerUsage)
+        return mhz, bits, (mw or 0) / 1000.0
+
+
+def fp32_peak(cuda_index):
+    """Derived FP32 FMA peak (FMA/s) of the device: SM count from the device
+    properties x 128 FMA lanes x the maximum SM clock (NVML, else the
+    device attribute, else the GB300 nominal), with its basis."""
+    import torch
+    pr = torch.cuda.get_device_properties(cuda_index)
+    sms = pr.multi_processor_count
+    mhz, src = Nvml(cuda_index).max_sm_mhz(), "NVML max SM clock"
+    if not mhz:
+        khz = getattr(pr, "clock_rate", 0) or 0
+        mhz, src = (khz / 1000.0, "device clock-rate attribute") if khz else (SM_MAX_MHZ_NOMINAL, "GB300 nominal")
+    return sms * FP32_LANES_PER_SM * mhz * 1e6, "derived: %d SMs x %d FP32 FMA lanes x %.0f MHz (%s)" % (
+        sms, FP32_LANES_PER_SM, mhz, src)
+
+
 class Clocks:
-    """SM clock and throttle reasons, sampled by a background thread that
-    queries nvidia-smi back to back while the timed steps run."""
+    """SM clock and throttle reasons during the timed region: an in-process
+    NVML sampler (every 2 ms) plus nvidia-smi queried back to back, both on
+    background threads."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -85,8 +155,16 @@ class Clocks:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.rows = []
+        self.nv = []
         self.stop_flag = False
         self.thread = None
+        self.nv_thread = None
+        self.nvml = Nvml(gpu_index)
+
+    def _poll_nvml(self):
+        while not self.stop_flag:
+            self.nv.append(self.nvml.sample())
+            time.sleep(0.002)
 
     def _poll(self):
         while not self.stop_flag:
@@ -106,12 +184,34 @@ class Clocks:
         self.stop_flag = False
         self.thread = threading.Thread(target=self._poll, daemon=True)
         self.thread.start()
+        if self.nvml.h is not None:
+            self.nv_thread = threading.Thread(target=self._poll_nvml, daemon=True)
+            self.nv_thread.start()
 
     def stop(self):
         self.stop_flag = True
-        if self.thread is not None:
-            self.thread.join(timeout=10)
+        for t in (self.thread, self.nv_thread):
+            if t is not None:
+                t.join(timeout=10)
         rows = self.rows
+        nv = [x for x in self.nv if x[0]]
+        if nv:
+            reasons = set()
+            for _, bits, _ in nv:
+                for b, name in Nvml.REASONS.items():
+                    if bits & b:
+                        reasons.add(name)
+            for r in rows:
+                for name, val in zip(["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                                      "sw_power_cap"], r[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(name)
+            return {"sm_mhz": float(np.median([x[0] for x in nv])),
+                    "sm_max_mhz": float(self.nvml.max_sm_mhz() or np.nan),
+                    "sm_mhz_min": float(np.min([x[0] for x in nv])),
+                    "power_w_max": float(np.max([x[2] for x in nv])),
+                    "samples": len(nv), "samples_nvidia_smi": len(rows), "source": "NVML every 2 ms + nvidia-smi",
+                    "reasons": sorted(reasons)}
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
 
@@ -202,31 +302,33 @@ def profiled_traffic(kernel):
 
 def cpu_baseline(sc, state, goal, obs, T, workload, target_cpu_s=15.0):
     """Oracle (as it stands) on the host cores: a bounded sample of the first
-    plan step's workload (sample indices 0..K-1; beyond N they are further
-    Philox draws of the same distribution), every one over the full
-    horizon, about `target_cpu_s` seconds of single-core work."""
+    plan step's workload -- blocks of 1024 samples (indices 0..1024 r - 1;
+    beyond N they are further Philox draws of the same distribution), each
+    over the full horizon, r chosen for about `target_cpu_s` seconds of
+    single-core work -- and the first 1024 samples on one core."""
     from oracle import oracle as orc
     p = sc["preset"]
     cores = os.cpu_count() or 1
     goal_ev, obs_ev = orc.frame_to_ev(state, goal, obs)
     z0 = [0.0, 0.0, 0.0, state[3]]
-    probe = np.arange(64, dtype=np.int32)
+    probe = np.arange(1024, dtype=np.int32)
     t0 = time.perf_counter()
     orc.rollout_samples(p, sc["seed"], 0, probe, z0, state[4:6], goal_ev, obs_ev, T, n_threads=1,
                         record=False)
-    per_sample = max(time.perf_counter() - t0, 1e-6) / len(probe)
-    K = int(min(8 * sc["N"], max(256, target_cpu_s / per_sample)))
+    single_s = max(time.perf_counter() - t0, 1e-6)
+    r = int(min(64, max(1, round(target_cpu_s / single_s))))
+    K = 1024 * r
     idx = np.arange(K, dtype=np.int32)
     t0 = time.perf_counter()
     orc.rollout_samples(p, sc["seed"], 0, idx, z0, state[4:6], goal_ev, obs_ev, T, n_threads=cores,
                         record=False)
     wall = time.perf_counter() - t0
     return {"value": K * T / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "single_thread": len(probe) * T / (per_sample * len(probe)),
-            "sample": "first plan step of the %s scene: %d samples (the step draws %d) over "
-                      "the full horizon T=%d, M=%d points (brute force), FP64 C with OpenMP "
-                      "(%.1f s wall); single_thread: 64 samples on one core" % (
-                          workload, K, sc["N"], T, obs.shape[0], wall)}
+            "single_thread": 1024 * T / single_s,
+            "sample": "first plan step of the %s scene: %d x 1024 samples (the step draws %d) over "
+                      "the full horizon T=%d, M=%d points (brute force), FP64 C with OpenMP on %d "
+                      "threads (%.1f s wall); single_thread: the first 1024 samples on one core (%.1f s)" % (
+                          workload, r, sc["N"], T, obs.shape[0], cores, wall, single_s)}
 
 
 def run_npp(args):
@@ -251,6 +353,9 @@ def run_npp(args):
     K, Wu = args.steps, args.warmup
     pl = npp.Planner(p, max_N=N, max_T=T, max_M=M, device=local)
     npp.npp_set_timing(pl.h, True)
+    options = dict(kv.split("=", 1) for kv in args.set)
+    for name, val in options.items():
+        npp.npp_set_option(pl.h, name, int(val))
     obs0_dev = torch.tensor(sc["obs"], dtype=torch.float32, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
 
@@ -348,65 +453,73 @@ def run_npp(args):
     if e2e:
         e2e["value"] = multi.whole_job_rate(N * T * K, world, e2e_s)
     value = multi.whole_job_rate(N * T * K, world, total_ms / 1e3)
-    peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6
+    peak, peak_basis = fp32_peak(local)
     # the library's own FMA-stream microbenchmark, beside the derived peak
     fma_measured = {"ffma": npp.npp_measure_fma_peak(local, False) / 1e12,
                     "ffma2": npp.npp_measure_fma_peak(local, True) / 1e12, "unit": "T FP32-FMA/s"}
-    fps_c = res["fma_c"] / (collide_ms / 1e3)
-    fps_t = res["fma_t"] / (traj_ms / 1e3)
     # the library's automatic collision choice (binned from 512 points and
-    # 8e6 point-sample pairs)
-    binned = poly or (M >= 512 and M * N >= 8000000)
-    if poly:
-        cname = "bin_build_kernel + collide_poly_kernel"
-    elif binned:
-        cname = "bin_build_kernel + collide_binned_kernel"
-    else:
-        cname = ("collide_slice_kernel<4,4>" if N <= 8192 else
-                 "collide_slice_kernel<2,8>" if N <= 32768 else "collide_warp_kernel<8,2>")
+    # 8e6 point-sample pairs); "fuse" runs the binned check inside the
+    # trajectory kernel
+    cv = int(options.get("collide_variant", -1))
+    binned = poly or cv == 5 or (cv < 0 and M >= 512 and M * N >= 8000000)
+    fused = binned and not poly and int(options.get("fuse", DEFAULT_FUSE)) == 1
     # default launch shapes; the last template argument is the variant flag
     # (off: no speed limits, features in the EV frame at t)
     var = int(bool(p.get("v_limits", 0) or p.get("feature_frame", 0)))
-    tname = {16: "traj_kernel<16,8,4,4,%d>", 32: "traj_kernel<32,16,4,4,%d>",
-             64: "traj_kernel<64,32,1,10,%d>"}[W] % var
-    coll = {"ms_per_step": collide_ms / K, "point_checks_per_s": res["checks"] / (collide_ms / 1e3)}
+    shape = {16: "<16,8,4,4,%d>", 32: "<32,16,4,4,%d>", 64: "<64,32,1,10,%d>"}[W] % var
     fma_all = float(N) * T * K * (W * W + 10 * W)
-    trj = {"ms_per_step": traj_ms / K, "achieved": fps_t / 1e12, "frac": fps_t / peak,
-           "all_steps_achieved": fma_all / (traj_ms / 1e3) / 1e12,
-           "all_steps_frac": fma_all / (traj_ms / 1e3) / peak}
-    if not binned:
-        coll.update(achieved=fps_c / 1e12, frac=fps_c / peak)
-    else:
-        coll["note"] = ("binned: checks only the points of the cells a state's bounding disk "
-                        "overlaps; point_checks_per_s counts the brute-force equivalent")
-    if binned:
+    if fused:
+        # [0] grid build, [1] the fused trajectory-and-check kernel
+        fname = "fused_kernel" + shape
+        fps = res["fma_t"] / (collide_ms / 1e3)
+        roofline = {"bound": "alu", "kernel": fname, "achieved": fps / 1e12, "peak": peak / 1e12,
+                    "unit": "T FP32-FMA/s", "frac": fps / peak, "traffic": profiled_traffic(fname),
+                    "peak_basis": peak_basis, "peak_measured": fma_measured,
+                    "work": "MLP FMAs (W^2 + 10 W) per control step of a sample up to its first collision "
+                            "(the kernel stops each sample at most two steps later); the binned check's "
+                            "candidate tests in the same kernel are not counted",
+                    "kernel_ms_per_step": collide_ms / K,
+                    "other": {"bin_build_kernel": {"ms_per_step": traj_ms / K}},
+                    "dominant": fname}
+    elif binned:
         # the binned (or polygon) check does only the candidate work of the
         # cells a state overlaps, which has no fixed algorithmic count; the
-        # MLP rollout is the work every plan step must do (and the dominant
-        # kernel on the default workloads)
-        traffic = profiled_traffic(tname)
+        # MLP rollout is the work every plan step must do
+        tname = "traj_kernel" + shape
+        cname = "bin_build_kernel + " + ("collide_poly_kernel" if poly else "collide_binned_kernel")
+        fps_t = res["fma_t"] / (traj_ms / 1e3)
         roofline = {"bound": "alu", "kernel": tname, "achieved": fps_t / 1e12, "peak": peak / 1e12,
-                    "unit": "T FP32-FMA/s", "frac": fps_t / peak, "traffic": traffic,
-                    "peak_basis": "derived: 152 SMs x 128 FP32 FMA lanes x 2070 MHz",
-                    "peak_measured": fma_measured,
+                    "unit": "T FP32-FMA/s", "frac": fps_t / peak, "traffic": profiled_traffic(tname),
+                    "peak_basis": peak_basis, "peak_measured": fma_measured,
                     "work": "MLP FMAs (W^2 + 10 W) per control step of a sample up to its first "
                             "collision; all_steps_* count every step the kernel computes",
-                    "all_steps_achieved": trj["all_steps_achieved"], "all_steps_frac": trj["all_steps_frac"],
-                    "kernel_ms_per_step": traj_ms / K, "other": {cname: coll},
+                    "all_steps_achieved": fma_all / (traj_ms / 1e3) / 1e12,
+                    "all_steps_frac": fma_all / (traj_ms / 1e3) / peak,
+                    "kernel_ms_per_step": traj_ms / K,
+                    "other": {cname: {"ms_per_step": collide_ms / K}},
                     "dominant": tname if traj_ms >= collide_ms else cname}
     else:
-        traffic = profiled_traffic(cname)
+        tname = "traj_kernel" + shape
+        cname = {0: "collide_block_kernel<16,128,1>", 1: "collide_block_kernel<8,64,2>",
+                 2: "collide_warp_kernel<8,2>", 3: "collide_slice_kernel<4,4>",
+                 4: "collide_slice_kernel<2,8>"}.get(
+            cv, "collide_slice_kernel<4,4>" if N <= 8192 else
+            "collide_slice_kernel<2,8>" if N <= 32768 else "collide_warp_kernel<8,2>")
+        fps_c = res["fma_c"] / (collide_ms / 1e3)
+        fps_t = res["fma_t"] / (traj_ms / 1e3)
         roofline = {"bound": "alu", "kernel": cname,
                     "achieved": fps_c / 1e12, "peak": peak / 1e12, "unit": "T FP32-FMA/s",
-                    "frac": fps_c / peak,
-                    "traffic": None if traffic is None else traffic,
-                    "peak_basis": "derived: 152 SMs x 128 FP32 FMA lanes x 2070 MHz",
-                    "peak_measured": fma_measured,
+                    "frac": fps_c / peak, "traffic": profiled_traffic(cname),
+                    "peak_basis": peak_basis, "peak_measured": fma_measured,
+                    "work": "4 FMAs per point-check (two rows of the rotated inequality test) of a sample "
+                            "up to its first collision",
                     "kernel_ms_per_step": collide_ms / K,
                     "point_checks_per_s": res["checks"] / (collide_ms / 1e3),
-                    "other": {tname: trj}}
-        if binned:
-            roofline["note"] = coll["note"]
+                    "other": {tname: {"ms_per_step": traj_ms / K, "achieved": fps_t / 1e12,
+                                      "frac": fps_t / peak}},
+                    "dominant": cname if collide_ms >= traj_ms else tname}
+    # the same achieved rate against the library's measured FMA-stream peaks
+    roofline["frac_of_measured"] = {k: roofline["achieved"] / fma_measured[k] for k in ("ffma", "ffma2")}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": Wu, "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -415,7 +528,8 @@ def run_npp(args):
                        "l2": "flushed (256 MiB write) between timed steps",
                        "timing": "sum of per-step CUDA-event durations (events captured in the "
                                  "step graph, replayed on the launching stream)"},
-            "roofline": roofline, "e2e": e2e, "gpu_launches": (6 if binned else 5) * K, "clocks": ck,
+            "roofline": roofline, "e2e": e2e, "gpu_launches": (6 if binned and not fused else 5) * K,
+            "clocks": ck, "options": options,
             "free_fraction": float(np.mean(res["free"])),
             "waypoints_reached": res["waypoints_reached"], "infeasible_steps": res["n_infeasible"]}
     if rank == 0 and not args.no_cpu_baseline:
@@ -568,7 +682,7 @@ def run_batch(args):
         tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         total_ms = float(tt[0])
-    peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6
+    peak, peak_basis = fp32_peak(local)
     col_ms, trj_ms = float(np.mean(col)), float(np.mean(trj))
     binned = choice[0] == 1
     # MLP FMAs of live control steps, per scene width
@@ -581,7 +695,7 @@ def run_batch(args):
     if binned and trj_ms >= col_ms:
         roof = {"bound": "alu", "kernel": "batch_traj_kernel (widths 16/32/64)", "achieved": fps_t / 1e12,
                 "peak": peak / 1e12, "unit": "T FP32-FMA/s", "frac": fps_t / peak, "traffic": None,
-                "peak_basis": "derived: 152 SMs x 128 FP32 FMA lanes x 2070 MHz",
+                "peak_basis": peak_basis,
                 "work": "MLP FMAs (W^2 + 10 W) per control step up to first collision",
                 "kernel_ms_per_step": trj_ms,
                 "other": {"batch_bin_build_kernel + batch_binned_kernel": {
@@ -593,7 +707,7 @@ def run_batch(args):
         roof = {"bound": "alu", "kernel": ("batch_binned_kernel" if binned else "batch_collide_kernel<%d>" % choice[1]),
                 "achieved": fps / 1e12, "peak": peak / 1e12, "unit": "T FP32-FMA/s",
                 "frac": fps / peak, "traffic": None,
-                "peak_basis": "derived: 152 SMs x 128 FP32 FMA lanes x 2070 MHz",
+                "peak_basis": peak_basis,
                 "kernel_ms_per_step": col_ms, "traj_ms_per_step": trj_ms,
                 "point_checks_per_s": checks / (col_ms / 1e3)}
     n_widths = len(set(s["width"] for s in sc))

@@ -329,7 +329,9 @@ npp_status npp_loop_samples(npp_loop* L, float* costs_host, int32_t* first_hit_h
 
 /* Stage times of the last replayed step in ms (events captured in the
  * graph): [0] trajectory kernel, [1] collision kernel, [2] selection
- * epilogue + advance, [3] whole step; writes up to n values. */
+ * epilogue + advance, [3] whole step; writes up to n values.  When the
+ * binned check runs fused into the trajectory kernel ("fuse"), [0] is the
+ * grid build and [1] the fused kernel. */
 npp_status npp_loop_last_timing(npp_loop* L, float* stage_ms, int32_t n);
 
 /* Free the loop (after synchronising the device). */
@@ -462,8 +464,9 @@ npp_status npp_set_option(npp_handle* h, const char* name, int32_t value);
  * npp_last_timing synchronises on the last recorded event and writes up to n
  * durations in milliseconds: [0] trajectory kernel, [1] collision kernel,
  * [2] selection epilogue, [3] the whole call (npp_rollout_params has no
- * epilogue: [2] is 0).  Disabled by default; enabling it adds four event
- * records per call. */
+ * epilogue: [2] is 0); with the fused binned check, [0] is the grid build
+ * and [1] the fused trajectory-and-check kernel.  Disabled by default;
+ * enabling it adds four event records per call. */
 npp_status npp_set_timing(npp_handle* h, int32_t enable);
 npp_status npp_last_timing(npp_handle* h, float* stage_ms, int32_t n);
 

@@ -444,6 +444,27 @@ int orc_speed_violated(const orc_config* c, double v, int h)
 /* ------------------------------------------------------------------ */
 /* one rollout                                                          */
 /* ------------------------------------------------------------------ */
+/* Cost of a collision-free rollout (the reading of the cost: the paper
+ * gives none): pose distance of the final EV-frame state z to the goal plus
+ * the mean squared normalised control, E = sum over the T applied controls
+ * of a0^2 + a1^2. */
+static double terminal_cost(const orc_config* c, const double z[4], double E, int T, const double goal[4])
+{
+    double dpos = hypot(z[0] - goal[0], z[1] - goal[1]);
+    return c->w_pos * dpos + c->w_phi * fabs(wrap_pi(z[2] - goal[2]))
+         + c->w_v * fabs(z[3] - goal[3]) + c->w_effort * E / (double)T;
+}
+
+/* The cost of a collision-free rollout from its final state zT and its
+ * applied controls ctrl[T][2] (for instance a GPU rollout's own FP32 rows,
+ * so that the cost is checked at the GPU's states). */
+double orc_cost(const orc_config* c, const double zT[4], const double* ctrl, int T, const double goal[4])
+{
+    double E = 0.0;
+    for (int h = 0; h < T; ++h) E += ctrl[2 * h] * ctrl[2 * h] + ctrl[2 * h + 1] * ctrl[2 * h + 1];
+    return terminal_cost(c, zT, E, T, goal);
+}
+
 /* z0 = EV-frame state (x, y, phi, v) (normally (0,0,0,v0)), ap0 = last
  * applied controls, goal/obs in the EV frame.  traj[(T+1)][4] and
  * ctrl[T][2] in the EV frame; for a collided sample rows after the first
@@ -481,9 +502,7 @@ static int rollout(const orc_config* c, const double* theta, const double z0[4],
         if (ctrl) for (int h = fh; h < T; ++h) { ctrl[2 * h] = 0.0; ctrl[2 * h + 1] = 0.0; }
         *cost = INFINITY;
     } else {
-        double dpos = hypot(z[0] - goal[0], z[1] - goal[1]);
-        *cost = c->w_pos * dpos + c->w_phi * fabs(wrap_pi(z[2] - goal[2]))
-              + c->w_v * fabs(z[3] - goal[3]) + c->w_effort * E / (double)T;
+        *cost = terminal_cost(c, z, E, T, goal);
     }
     return fh;
 }

@@ -90,6 +90,8 @@ def lib():
                                   C.c_double, C.c_double, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.orc_collide.restype = C.c_int
         L.orc_step.argtypes = [_P, _D, _D, _D, _D, C.c_int, C.c_int, _D, _D]
+        L.orc_cost.argtypes = [_P, _D, _D, C.c_int, _D]
+        L.orc_cost.restype = C.c_double
         L.orc_rollout_theta.argtypes = [_P, _D, C.c_int, _D, _D, _D, _D, C.c_int, C.c_int,
                                         C.c_int, _D, _I, C.c_void_p, C.c_void_p]
         L.orc_rollout_samples.argtypes = [_P, C.c_uint64, C.c_uint32, C.c_uint32, _I, C.c_int,
@@ -228,6 +230,13 @@ def step(p, th, z, ap, goal_ev, h, T):
     lib().orc_step(C.byref(make_config(p)), _d(th), _d(z, 4), _d(ap, 2), _d(goal_ev, 4),
                    int(h), int(T), a, zn)
     return a, zn
+
+
+def cost(p, zT, ctrl, goal_ev):
+    """Cost of a collision-free rollout from its final EV-frame state zT and
+    its applied controls ctrl [T][2] (the rollout's cost formula)."""
+    ctrl = _d(ctrl).reshape(-1, 2)
+    return lib().orc_cost(C.byref(make_config(p)), _d(zT, 4), ctrl, ctrl.shape[0], _d(goal_ev, 4))
 
 
 # ----------------------------------------------------------------- rollouts

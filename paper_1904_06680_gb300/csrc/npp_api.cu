@@ -219,16 +219,13 @@ npp_status run_rollout(npp_handle* h, RolloutArgs& a, cudaStream_t s, bool allow
             if (h->timing) CUDA_TRY(h, record_event(h->ev[2], s));
             return NPP_OK;
         }
+        // fused: the grids first, then the trajectories with the check
+        // inside (timing: [0] the grid build, [1] the fused kernel)
         CUDA_TRY(h, build_bins(a, h->cfg.half_len, h->cfg.half_wid, h->cfg.c_off, h->d_bins, s));
-        if (allow_fused && h->fuse) {
-            CUDA_TRY(h, launch_fused(h, a, s));
-            if (h->timing) {
-                CUDA_TRY(h, record_event(h->ev[1], s));
-                CUDA_TRY(h, record_event(h->ev[2], s));
-            }
-            *fused = true;
-            return NPP_OK;
-        }
+        if (h->timing) CUDA_TRY(h, record_event(h->ev[1], s));
+        CUDA_TRY(h, launch_fused(h, a, s));
+        if (h->timing) CUDA_TRY(h, record_event(h->ev[2], s));
+        *fused = true;
         return NPP_OK;
     }
     // points beyond shared memory: point-sliced kernel on an L2-resident copy

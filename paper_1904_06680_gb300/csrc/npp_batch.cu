@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(NW * 32) batch_traj_kernel(const BatchArgs b, 
         job.jfree = b.jfree + s.samp_off;
         job.vfirst = b.vfirst ? b.vfirst + s.samp_off : nullptr;
         constexpr int STAGE_TH = W == 32 ? NW * 32 : 0;     // as traj_kernel
-        traj_sample<W, G, false, STAGE_TH, VAR>(b.c, job, n, n < s.N, gl, hx_all + bi * W);
+        traj_sample<W, G, STAGE_TH, VAR>(b.c, job, n, n < s.N, gl, hx_all + bi * W);
     }
 }
 
@@ -574,7 +574,7 @@ __device__ void batch_reroll(const BatchArgs& b, const SceneDev& s, int idx, flo
     job.coef_base = 0;
     job.jfree = nullptr;
     job.vfirst = nullptr;
-    traj_sample<W, G, false, 0, VAR>(b.c, job, idx, true, lane % G, hrows + (lane / G) * W);
+    traj_sample<W, G, 0, VAR>(b.c, job, idx, true, lane % G, hrows + (lane / G) * W);
 }
 
 __global__ void batch_epilogue_kernel(const BatchArgs b)

@@ -90,12 +90,16 @@ __device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsig
     return d;
 }
 
+// The weights of one lane: rows of W1 and W2 as packed pairs of adjacent
+// inputs (2k, 2k + 1), the operands of the FP32x2 FMAs of the step.
 template <int W, int G>
 struct LaneNet {
     using S = Shape<W, G>;
     static constexpr int U = S::U;
-    float w1[U][NIN], b1[U];
-    float w2[U][W], b2[U];
+    unsigned long long w1p[U][NIN / 2];
+    float b1[U];
+    unsigned long long w2p[U][W / 2];
+    float b2[U];
     float w3[2][U], b3[2];
 
     // lane gl of the group holds hidden units gl*U .. gl*U + U - 1
@@ -106,12 +110,14 @@ struct LaneNet {
 #pragma unroll
             for (int i = 0; i < NIN; i += 4) {
                 const float4 q = src.quad(u * NIN + i);
-                w1[j][i] = q.x; w1[j][i + 1] = q.y; w1[j][i + 2] = q.z; w1[j][i + 3] = q.w;
+                w1p[j][i / 2] = f2_pack(q.x, q.y);
+                w1p[j][i / 2 + 1] = f2_pack(q.z, q.w);
             }
 #pragma unroll
             for (int i = 0; i < W; i += 4) {
                 const float4 q = src.quad(S::OFF_W2 + u * W + i);
-                w2[j][i] = q.x; w2[j][i + 1] = q.y; w2[j][i + 2] = q.z; w2[j][i + 3] = q.w;
+                w2p[j][i / 2] = f2_pack(q.x, q.y);
+                w2p[j][i / 2 + 1] = f2_pack(q.z, q.w);
             }
         }
 #pragma unroll
@@ -167,9 +173,13 @@ struct LaneNet {
 #pragma unroll
         for (int j = 0; j < U; ++j) {
 #pragma unroll
-            for (int i = 0; i < NIN; ++i) w1[j][i] = st[(4 * (j * QPU + i / 4) + i % 4) * TH];
+            for (int i = 0; i < NIN; i += 2)
+                w1p[j][i / 2] = f2_pack(st[(4 * (j * QPU + i / 4) + i % 4) * TH],
+                                        st[(4 * (j * QPU + i / 4) + i % 4 + 1) * TH]);
 #pragma unroll
-            for (int i = 0; i < W; ++i) w2[j][i] = st[(4 * (j * QPU + QW1 + i / 4) + i % 4) * TH];
+            for (int i = 0; i < W; i += 2)
+                w2p[j][i / 2] = f2_pack(st[(4 * (j * QPU + QW1 + i / 4) + i % 4) * TH],
+                                        st[(4 * (j * QPU + QW1 + i / 4) + i % 4 + 1) * TH]);
         }
 #pragma unroll
         for (int j = 0; j < U; j += 2) {
@@ -184,11 +194,15 @@ struct LaneNet {
     }
 };
 
+// Every rounding of the rollout step below is written out (fmaf, __fmul_rn,
+// __fadd_rn, __fsub_rn): the compiler may not contract a product and a sum
+// differently in different kernels, so every kernel that rolls a sample out
+// (trajectories, fused check, batch, winner re-roll) produces the same bits.
 __device__ __forceinline__ float wrap_pi(float a)
 {
     const float TWO_PI = 6.28318530717958647692f;
     const float INV_TWO_PI = 0.15915494309189533577f;
-    return a - TWO_PI * floorf((a + 3.14159265358979323846f) * INV_TWO_PI);
+    return fmaf(-TWO_PI, floorf(__fmul_rn(__fadd_rn(a, 3.14159265358979323846f), INV_TWO_PI)), a);
 }
 
 // The rectangle's four inequalities at state (x, y, phi), scaled so that a
@@ -378,7 +392,7 @@ struct TrajJob {
     long long coef_base;
     float* jfree;
     int* vfirst;                  // first speed-violating step per sample (speed limits on), or null
-    const BinView* bins;          // fused check (traj_sample<.., true>)
+    const BinView* bins;          // fused check (traj_sample_fused)
     float* stage;                 // this thread's slot 0 of a staging area (stride stage_th), or null
 };
 
@@ -389,50 +403,179 @@ struct FusedOut {
     float cost;
 };
 
-// The trajectory of sample n (valid: n < N) computed by the G lanes of a
-// group (lane gl); hrow is the group's W-float shared exchange row.  FUSED:
-// every state h is checked against the binned points at the top of its step
-// (before the controls that leave it) and the loop ends once every group of
-// the warp has collided; nothing is stored.  VAR: the variants of c
-// (body-frame goal offsets, speed limits) are honoured; without it the
-// kernel is the plain rollout, and the launchers pick VAR whenever c turns
-// a variant on.
-template <int W, int G, bool FUSED = false, int STAGE_TH = 0, bool VAR = false>
-__device__ __forceinline__ FusedOut traj_sample(const DevCfg& c, const TrajJob& job, int n, bool valid,
-                                                int gl, float* hrow)
+// The goal in the EV frame at t and the constants of one rollout.
+struct GoalEV {
+    float xi, eta, phi, v;
+};
+
+__device__ __forceinline__ GoalEV goal_ev(const StepIn& si)
 {
-    using S = Shape<W, G>;
-    constexpr int U = S::U;
-    const StepIn& si = job.si;
     float s0, c0;
     sincosf(si.phi0, &s0, &c0);
-    const float gdx = si.gx - si.x0, gdy = si.gy - si.y0;
-    const float gxi = c0 * gdx + s0 * gdy, geta = -s0 * gdx + c0 * gdy;
-    const float gph = si.gphi - si.phi0, gv = si.gv;
+    const float gdx = __fsub_rn(si.gx, si.x0), gdy = __fsub_rn(si.gy, si.y0);
+    GoalEV g;
+    g.xi = fmaf(c0, gdx, __fmul_rn(s0, gdy));
+    g.eta = fmaf(-s0, gdx, __fmul_rn(c0, gdy));
+    g.phi = __fsub_rn(si.gphi, si.phi0);
+    g.v = si.gv;
+    return g;
+}
 
-    LaneNet<W, G> net;
-    {
-        ThetaSrc src;
-        src.key = job.key;
-        src.prop = job.prop;
-        src.n = (uint32_t)(valid ? n : 0);
-        src.mem = nullptr;
-        if (job.theta) src.mem = job.theta + (size_t)(valid ? n : 0) * S::NT;
-        else if (job.warm && n == 0 && si.warm_ok) src.mem = job.warm;
-        if constexpr (STAGE_TH > 0) net.template load_staged<STAGE_TH>(src, gl, job.stage);
-        else net.load(src, gl);
+// The network of sample n (valid: n < N) loaded into the lanes of its group.
+template <int W, int G, int STAGE_TH>
+__device__ __forceinline__ void load_net(LaneNet<W, G>& net, const TrajJob& job, int n, bool valid, int gl)
+{
+    ThetaSrc src;
+    src.key = job.key;
+    src.prop = job.prop;
+    src.n = (uint32_t)(valid ? n : 0);
+    src.mem = nullptr;
+    if (job.theta) src.mem = job.theta + (size_t)(valid ? n : 0) * Shape<W, G>::NT;
+    else if (job.warm && n == 0 && job.si.warm_ok) src.mem = job.warm;
+    if constexpr (STAGE_TH > 0) net.template load_staged<STAGE_TH>(src, gl, job.stage);
+    else net.load(src, gl);
+}
+
+// One control step h from state (x, y, ph, v) whose heading has sine sp and
+// cosine cp: features (Eq. eq_def_stph), network a = X(s, theta) (Eq.
+// eq_def_at) by the G lanes of the group (hrow: the group's W-float shared
+// exchange row), rate-limited controls, effort, Euler step of the kinematic
+// bicycle on the old state (Sect. IV).  Updates the state, the last
+// controls, the effort E and rem = T - h; returns the applied controls.
+template <int W, int G, bool VAR>
+__device__ __forceinline__ float2 control_step(const DevCfg& c, const LaneNet<W, G>& net, const GoalEV& g,
+                                               float invT, int gl, float* hrow, float sp, float cp, float& x,
+                                               float& y, float& ph, float& v, float& ap0, float& ap1, float& E,
+                                               float& rem)
+{
+    constexpr int U = Shape<W, G>::U;
+    float s[NIN];
+    if (VAR && c.body_frame) {
+        // goal offset in the vehicle's frame at t+h
+        const float dgx = __fsub_rn(g.xi, x), dgy = __fsub_rn(g.eta, y);
+        s[0] = __fmul_rn(fmaf(cp, dgx, __fmul_rn(sp, dgy)), c.idxi);
+        s[1] = __fmul_rn(fmaf(-sp, dgx, __fmul_rn(cp, dgy)), c.ideta);
+    } else {
+        s[0] = __fmul_rn(__fsub_rn(g.xi, x), c.idxi);
+        s[1] = __fmul_rn(__fsub_rn(g.eta, y), c.ideta);
     }
+    s[2] = __fmul_rn(wrap_pi(__fsub_rn(g.phi, ph)), c.idphi);
+    s[3] = __fmul_rn(__fsub_rn(g.v, v), c.idv);
+    s[4] = ap0;
+    s[5] = ap1;
+    s[6] = __fmul_rn(v, c.idv);
+    s[7] = __fmul_rn(rem, invT);
+    rem = __fsub_rn(rem, 1.0f);
+    // layer 1: the even and odd inputs as the two halves of FP32x2 FMAs,
+    // then their sum and the bias
+    unsigned long long sp2[NIN / 2];
+#pragma unroll
+    for (int i = 0; i < NIN / 2; ++i) sp2[i] = f2_pack(s[2 * i], s[2 * i + 1]);
+    float h1[U];
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+        unsigned long long q = f2_fma(net.w1p[j][0], sp2[0], 0ull);
+#pragma unroll
+        for (int i = 1; i < NIN / 2; ++i) q = f2_fma(net.w1p[j][i], sp2[i], q);
+        const float2 qq = f2_unpack(q);
+        h1[j] = tanh_r(__fadd_rn(__fadd_rn(qq.x, qq.y), net.b1[j]));
+    }
+#pragma unroll
+    for (int j = 0; j < U; ++j) hrow[gl * U + j] = h1[j];
+    __syncwarp();
+    // layer 2: each unit's dot product as four interleaved partial sums
+    // (inputs i = 4q + r go to partial r), added pairwise with the bias
+    // last: independent FMA chains keep the pipe busy
+    // (partials 0, 1 and 2, 3 as packed pairs: two FP32x2 FMAs per input
+    // quad, each half rounded as a separate fmaf)
+    unsigned long long p01[U], p23[U];
+#pragma unroll
+    for (int j = 0; j < U; ++j) p01[j] = p23[j] = 0ull;
+    const float4* hrow4 = reinterpret_cast<const float4*>(hrow);
+#pragma unroll
+    for (int i = 0; i < W / 4; ++i) {
+        const float4 hv = hrow4[i];
+        const unsigned long long h01 = f2_pack(hv.x, hv.y), h23 = f2_pack(hv.z, hv.w);
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            p01[j] = f2_fma(net.w2p[j][2 * i], h01, p01[j]);
+            p23[j] = f2_fma(net.w2p[j][2 * i + 1], h23, p23[j]);
+        }
+    }
+    __syncwarp();
+    float acc2[U];
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+        const float2 q01 = f2_unpack(p01[j]), q23 = f2_unpack(p23[j]);
+        acc2[j] = __fadd_rn(__fadd_rn(__fadd_rn(q01.x, q01.y), __fadd_rn(q23.x, q23.y)), net.b2[j]);
+    }
+    // layer 3: a fixed pairwise tree over the hidden units -- leaves
+    // w_2i h_2i + w_2i+1 h_2i+1 (one fma), then sums of neighbours -- so
+    // the value does not depend on how many units a lane holds
+    float h2[U];
+#pragma unroll
+    for (int j = 0; j < U; ++j) h2[j] = tanh_r(acc2[j]);
+    float p0 = fmaf(net.w3[0][1], h2[1], __fmul_rn(net.w3[0][0], h2[0]));
+    float p1 = fmaf(net.w3[1][1], h2[1], __fmul_rn(net.w3[1][0], h2[0]));
+    if constexpr (U == 4) {
+        p0 = __fadd_rn(p0, fmaf(net.w3[0][3], h2[3], __fmul_rn(net.w3[0][2], h2[2])));
+        p1 = __fadd_rn(p1, fmaf(net.w3[1][3], h2[3], __fmul_rn(net.w3[1][2], h2[2])));
+    }
+#pragma unroll
+    for (int off = 1; off < G; off <<= 1) {
+        p0 = __fadd_rn(p0, __shfl_xor_sync(FULL, p0, off));
+        p1 = __fadd_rn(p1, __shfl_xor_sync(FULL, p1, off));
+    }
+    const float ar0 = tanh_r(__fadd_rn(net.b3[0], p0));
+    const float ar1 = tanh_r(__fadd_rn(net.b3[1], p1));
+    float a0 = fminf(fmaxf(ar0, __fsub_rn(ap0, c.r_rate)), __fadd_rn(ap0, c.r_rate));
+    a0 = fminf(fmaxf(a0, -1.0f), 1.0f);
+    const float a1 = ar1;
+    E = __fadd_rn(E, fmaf(a0, a0, __fmul_rn(a1, a1)));
+    const float td = tan_r(__fmul_rn(c.delta_max, a0));
+    const float tb = __fmul_rn(c.lrL, td);
+    const float dv = __fmul_rn(c.Ts, v);
+    x = fmaf(dv, fmaf(-sp, tb, cp), x);
+    y = fmaf(dv, fmaf(cp, tb, sp), y);
+    ph = fmaf(__fmul_rn(dv, td), c.iL, ph);
+    v = fmaf(c.Ts, fmaf(c.uhalf, a1, c.umid), v);
+    ap0 = a0;
+    ap1 = a1;
+    return make_float2(a0, a1);
+}
 
-    float x = 0.f, y = 0.f, ph = 0.f, v = si.v0, ap0 = si.ap0, ap1 = si.ap1, E = 0.f;
+// cost of a collision-free rollout from its final state and effort
+__device__ __forceinline__ float final_cost(const DevCfg& c, const GoalEV& g, float x, float y, float ph, float v,
+                                            float E, float invT)
+{
+    const float dx = __fsub_rn(x, g.xi), dy = __fsub_rn(y, g.eta);
+    const float d = __fsqrt_rn(fmaf(dx, dx, __fmul_rn(dy, dy)));
+    const float e = __fmul_rn(__fmul_rn(c.w_effort, E), invT);
+    return fmaf(c.w_pos, d, fmaf(c.w_phi, fabsf(wrap_pi(__fsub_rn(ph, g.phi))),
+                                 fmaf(c.w_v, fabsf(__fsub_rn(v, g.v)), e)));
+}
+
+// The trajectory of sample n (valid: n < N) computed by the G lanes of a
+// group (lane gl); hrow is the group's W-float shared exchange row.  Writes
+// the records the job asks for (states, controls, scaled inequality rows,
+// cost if collision-free, first speed-violating step).  VAR: the variants
+// of c (body-frame goal offsets, speed limits) are honoured; without it the
+// kernel is the plain rollout, and the launchers pick VAR whenever c turns
+// a variant on.
+template <int W, int G, int STAGE_TH = 0, bool VAR = false>
+__device__ __forceinline__ void traj_sample(const DevCfg& c, const TrajJob& job, int n, bool valid, int gl,
+                                            float* hrow)
+{
+    const GoalEV g = goal_ev(job.si);
+    LaneNet<W, G> net;
+    load_net<W, G, STAGE_TH>(net, job, n, valid, gl);
+
+    float x = 0.f, y = 0.f, ph = 0.f, v = job.si.v0, ap0 = job.si.ap0, ap1 = job.si.ap1, E = 0.f;
     const int T = job.T, N = job.N;
     const float invT = 1.0f / (float)T;
     const bool writer = valid && gl == 0;
     const long long rec = (long long)n - job.rec_shift;
-
-    bool alive = valid;
-    int fh = -1;
     int vbad = -1;                       // first state h >= 1 whose speed is outside the limits
-    bool all_dead = false;
     float rem = (float)T;                // T - h, exact in FP32
     for (int h = 0; h < T; ++h) {
         float sp, cp;
@@ -440,154 +583,27 @@ __device__ __forceinline__ FusedOut traj_sample(const DevCfg& c, const TrajJob& 
         if constexpr (VAR) {
             if (c.vlim && h > 0 && vbad < 0 && !(v >= c.v_lo && v <= c.v_hi)) vbad = h;
         }
-        if constexpr (FUSED) {
-            if (vbad == h && alive) {    // discarded here, as by a collision
-                alive = false;
-                fh = h;
-            }
+        // pointer tests are uniform over the kernel; only the stores
+        // depend on the writer lane
+        if (job.traj && writer) job.traj[h * job.rec_stride + rec] = make_float4(x, y, ph, v);
+        if (job.coefA) {
             float4 A;
             float2 B;
             coef_rows(c, x, y, sp, cp, A, B);
-            if (group_collides<G>(*job.bins, h, x, y, A, B, alive, gl) && alive) {
-                alive = false;
-                fh = h;
-            }
-            if (!__any_sync(FULL, alive)) {
-                all_dead = true;
-                break;
-            }
-        } else {
-            // pointer tests are uniform over the kernel; only the stores
-            // depend on the writer lane
-            if (job.traj && writer) job.traj[h * job.rec_stride + rec] = make_float4(x, y, ph, v);
-            if (job.coefA) {
-                float4 A;
-                float2 B;
-                coef_rows(c, x, y, sp, cp, A, B);
-                if (writer) {
-                    const long long ci = job.coef_base + (long long)h * N + n;
-                    job.coefA[ci] = A;
-                    job.coefB[ci] = B;
-                }
+            if (writer) {
+                const long long ci = job.coef_base + (long long)h * N + n;
+                job.coefA[ci] = A;
+                job.coefB[ci] = B;
             }
         }
-        float s[NIN];
-        if (VAR && c.body_frame) {
-            // goal offset in the vehicle's frame at t+h
-            const float dgx = gxi - x, dgy = geta - y;
-            s[0] = fmaf(cp, dgx, __fmul_rn(sp, dgy)) * c.idxi;
-            s[1] = fmaf(-sp, dgx, __fmul_rn(cp, dgy)) * c.ideta;
-        } else {
-            s[0] = (gxi - x) * c.idxi;
-            s[1] = (geta - y) * c.ideta;
-        }
-        s[2] = wrap_pi(gph - ph) * c.idphi;
-        s[3] = (gv - v) * c.idv;
-        s[4] = ap0;
-        s[5] = ap1;
-        s[6] = v * c.idv;
-        s[7] = rem * invT;
-        rem -= 1.0f;
-        float h1[U];
-#pragma unroll
-        for (int j = 0; j < U; ++j) {
-            float acc = net.b1[j];
-#pragma unroll
-            for (int i = 0; i < NIN; ++i) acc = fmaf(net.w1[j][i], s[i], acc);
-            h1[j] = tanh_r(acc);
-        }
-#pragma unroll
-        for (int j = 0; j < U; ++j) hrow[gl * U + j] = h1[j];
-        __syncwarp();
-        // layer 2: each unit's dot product as four interleaved partial sums
-        // (inputs i = 4q + r go to partial r), added pairwise with the bias
-        // last: independent FMA chains keep the pipe busy
-        // (partials 0, 1 and 2, 3 as packed pairs: two FP32x2 FMAs per input
-        // quad, each half rounded as a separate fmaf)
-        unsigned long long p01[U], p23[U];
-#pragma unroll
-        for (int j = 0; j < U; ++j) p01[j] = p23[j] = 0ull;
-        const float4* hrow4 = reinterpret_cast<const float4*>(hrow);
-#pragma unroll
-        for (int i = 0; i < W / 4; ++i) {
-            const float4 hv = hrow4[i];
-            const unsigned long long h01 = f2_pack(hv.x, hv.y), h23 = f2_pack(hv.z, hv.w);
-#pragma unroll
-            for (int j = 0; j < U; ++j) {
-                p01[j] = f2_fma(f2_pack(net.w2[j][4 * i + 0], net.w2[j][4 * i + 1]), h01, p01[j]);
-                p23[j] = f2_fma(f2_pack(net.w2[j][4 * i + 2], net.w2[j][4 * i + 3]), h23, p23[j]);
-            }
-        }
-        __syncwarp();
-        float acc2[U];
-#pragma unroll
-        for (int j = 0; j < U; ++j) {
-            const float2 q01 = f2_unpack(p01[j]), q23 = f2_unpack(p23[j]);
-            acc2[j] = ((q01.x + q01.y) + (q23.x + q23.y)) + net.b2[j];
-        }
-        // layer 3: a fixed pairwise tree over the hidden units -- leaves
-        // w_2i h_2i + w_2i+1 h_2i+1 (one fma), then sums of neighbours -- so
-        // the value does not depend on how many units a lane holds
-        float h2[U];
-#pragma unroll
-        for (int j = 0; j < U; ++j) h2[j] = tanh_r(acc2[j]);
-        float p0 = fmaf(net.w3[0][1], h2[1], net.w3[0][0] * h2[0]);
-        float p1 = fmaf(net.w3[1][1], h2[1], net.w3[1][0] * h2[0]);
-        if constexpr (U == 4) {
-            p0 += fmaf(net.w3[0][3], h2[3], net.w3[0][2] * h2[2]);
-            p1 += fmaf(net.w3[1][3], h2[3], net.w3[1][2] * h2[2]);
-        }
-#pragma unroll
-        for (int off = 1; off < G; off <<= 1) {
-            p0 += __shfl_xor_sync(FULL, p0, off);
-            p1 += __shfl_xor_sync(FULL, p1, off);
-        }
-        const float ar0 = tanh_r(net.b3[0] + p0);
-        const float ar1 = tanh_r(net.b3[1] + p1);
-        float a0 = fminf(fmaxf(ar0, ap0 - c.r_rate), ap0 + c.r_rate);
-        a0 = fminf(fmaxf(a0, -1.0f), 1.0f);
-        const float a1 = ar1;
-        E += a0 * a0 + a1 * a1;
-        if (writer && job.ctrl) job.ctrl[h * job.rec_stride + rec] = make_float2(a0, a1);
-        const float td = tan_r(c.delta_max * a0);
-        const float tb = c.lrL * td;
-        const float dv = c.Ts * v;
-        x += dv * (cp - sp * tb);
-        y += dv * (sp + cp * tb);
-        ph += dv * td * c.iL;
-        v += c.Ts * (c.umid + c.uhalf * a1);
-        ap0 = a0;
-        ap1 = a1;
+        const float2 a = control_step<W, G, VAR>(c, net, g, invT, gl, hrow, sp, cp, x, y, ph, v, ap0, ap1, E,
+                                                 rem);
+        if (writer && job.ctrl) job.ctrl[h * job.rec_stride + rec] = a;
     }
-    FusedOut out;
-    out.first_hit = fh;
-    out.cost = __int_as_float(0x7f800000);
     if constexpr (VAR) {
         if (c.vlim && T > 0 && vbad < 0 && !(v >= c.v_lo && v <= c.v_hi)) vbad = T;
     }
-    if constexpr (FUSED) {
-        if (!all_dead && vbad == T && alive) {
-            alive = false;
-            fh = T;
-        }
-        if (!all_dead) {
-            float sp, cp;
-            sincos_r(ph, sp, cp);
-            float4 A;
-            float2 B;
-            coef_rows(c, x, y, sp, cp, A, B);
-            if (group_collides<G>(*job.bins, T, x, y, A, B, alive, gl) && alive) {
-                alive = false;
-                fh = T;
-            }
-        }
-        out.first_hit = fh;
-        if (alive) {
-            const float dx = x - gxi, dy = y - geta;
-            out.cost = c.w_pos * sqrtf(dx * dx + dy * dy) + c.w_phi * fabsf(wrap_pi(ph - gph))
-                     + c.w_v * fabsf(v - gv) + c.w_effort * E * invT;
-        }
-    } else if (writer) {
+    if (writer) {
         if constexpr (VAR) {
             if (job.vfirst) job.vfirst[n] = vbad;
         }
@@ -595,12 +611,225 @@ __device__ __forceinline__ FusedOut traj_sample(const DevCfg& c, const TrajJob& 
         sincos_r(ph, sp, cp);
         if (job.traj) job.traj[T * job.rec_stride + rec] = make_float4(x, y, ph, v);
         if (job.coefA) write_coef(job.coefA, job.coefB, c, job.coef_base + (long long)T * N + n, x, y, sp, cp);
-        if (job.jfree) {
-            const float dx = x - gxi, dy = y - geta;
-            job.jfree[n] = c.w_pos * sqrtf(dx * dx + dy * dy) + c.w_phi * fabsf(wrap_pi(ph - gph))
-                         + c.w_v * fabsf(v - gv) + c.w_effort * E * invT;
+        if (job.jfree) job.jfree[n] = final_cost(c, g, x, y, ph, v, E, invT);
+    }
+}
+
+// ------------------------------------------------------------------ fused, pipelined check
+// cp.async copies of 4 or 8 bytes from global to shared memory; with pred
+// false nothing is read and zeros are written.
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem, bool pred)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(gmem), "r"(pred ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool pred)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(gmem), "r"(pred ? 8 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory");
+}
+
+// candidates of a state copied ahead of its test (per group; beyond them the
+// test reads the rest directly)
+constexpr int FUSED_PREFETCH = 64;
+
+// Shared memory of one group's pipelined check: the cell-run bounds of the
+// two states in flight (entries 0..4 the first sorted point of each of the
+// at most five cell rows of the query, 5..9 the end of each row; zeros for
+// rows beyond the query), their inequality rows (kept here rather than in
+// registers, which the network's weights fill) and the candidate points of
+// the state being checked (the first KMAX * G candidates, KMAX per lane).
+template <int G, int KMAX>
+struct PipeSlot {
+    int4 cs[2][3];
+    float4 rA[2];             // scaled inequality rows of the two states in flight
+    float2 rB[2];
+    float2 pt[KMAX * G];
+};
+
+// Stage 1, state h at (x, y): copies of its cell-run bounds into cs.
+template <int G>
+__device__ __forceinline__ void pipe_runs(const BinView& bv, int h, float x, float y, bool live, int gl,
+                                          int* cs)
+{
+    const int* tab = bv.cell_start + (size_t)h * BIN_CS_STRIDE;
+    const int ix0 = bin_cell(x - bv.reach, bv), ix1 = bin_cell(x + bv.reach, bv);
+    const int iy0 = bin_cell(y - bv.reach, bv), iy1 = bin_cell(y + bv.reach, bv);
+#pragma unroll
+    for (int t = 0; t < (2 * BIN_MAX_ROWS + G - 1) / G; ++t) {
+        const int j = gl + t * G;
+        if (j < 2 * BIN_MAX_ROWS) {
+            const int r = j < BIN_MAX_ROWS ? j : j - BIN_MAX_ROWS;
+            const bool ok = live && iy0 + r <= iy1;
+            const int col = j < BIN_MAX_ROWS ? ix0 : ix1 + 1;
+            cp_async4(cs + j, ok ? tab + (iy0 + r) * BIN_DIM + col : tab, ok);
         }
     }
+}
+
+__device__ __forceinline__ CandRows runs_from(const int* cs)
+{
+    const int4 a = reinterpret_cast<const int4*>(cs)[0];
+    const int4 b = reinterpret_cast<const int4*>(cs)[1];
+    const int2 c2 = reinterpret_cast<const int2*>(cs)[4];
+    const int beg[BIN_MAX_ROWS] = { a.x, a.y, a.z, a.w, b.x };
+    const int end[BIN_MAX_ROWS] = { b.y, b.z, b.w, c2.x, c2.y };
+    CandRows cr;
+    int acc = 0;
+#pragma unroll
+    for (int r = 0; r < BIN_MAX_ROWS; ++r) {
+        cr.b[r] = beg[r];
+        acc += end[r] - beg[r];
+        cr.e[r] = acc;
+    }
+    cr.total = acc;
+    return cr;
+}
+
+// Stage 2, state h: from its cell-run bounds (complete and visible to the
+// group), copies of its first KMAX * G candidates into pt (each lane its
+// own KMAX); returns the candidate count.
+template <int G, int KMAX>
+__device__ __forceinline__ int pipe_points(const BinView& bv, int h, const int* cs, float2* pt, int gl)
+{
+    const CandRows cr = runs_from(cs);
+    const float2* pts = bv.pts + (size_t)h * bv.M;
+#pragma unroll
+    for (int i = 0; i < KMAX; ++i) {
+        const int k = gl + i * G;
+        const bool ok = k < cr.total;
+        cp_async8(pt + i * G + gl, ok ? pts + cr.index(k) : pts, ok);
+    }
+    return cr.total;
+}
+
+// Stage 3, state h (rows A, B): the per-point test of the brute-force
+// kernels on the copied candidates, then (rarely) on the candidates beyond
+// KMAX * G read directly.  Every lane of the warp calls it; returns,
+// uniformly over the group, whether some candidate is inside.
+template <int G, int KMAX>
+__device__ __forceinline__ bool pipe_test(const BinView& bv, int h, const int* cs, const float2* pt, int total,
+                                          const float4& A, const float2& B, int gl)
+{
+    const unsigned gmask = G == 32 ? FULL : (((1u << G) - 1u) << ((threadIdx.x & 31) / G * G));
+    bool inside = false;
+#pragma unroll
+    for (int i = 0; i < KMAX; ++i) {
+        if (gl + i * G < total) {
+            const float2 p = pt[i * G + gl];
+            const float xi = fmaf(A.x, p.x, fmaf(A.y, p.y, A.z));
+            const float et = fmaf(A.w, p.x, fmaf(B.x, p.y, B.y));
+            inside |= !(((__float_as_uint(xi) | __float_as_uint(et)) >> 30) & 1u);
+        }
+    }
+    bool hit = (__ballot_sync(FULL, inside) & gmask) != 0u;
+    constexpr int PRE = KMAX * G;
+    if (__any_sync(FULL, total > PRE && !hit)) {
+        const CandRows cr = runs_from(cs);
+        const float2* pts = bv.pts + (size_t)h * bv.M;
+        const int iters = (!hit && total > PRE) ? (total - PRE + G - 1) / G : 0;
+        const int maxit = __reduce_max_sync(FULL, iters);
+        for (int it = 0; it < maxit; ++it) {
+            const int k = PRE + it * G + gl;
+            bool in2 = false;
+            if (it < iters && k < total) {
+                const float2 p = pts[cr.index(k)];
+                const float xi = fmaf(A.x, p.x, fmaf(A.y, p.y, A.z));
+                const float et = fmaf(A.w, p.x, fmaf(B.x, p.y, B.y));
+                in2 = !(((__float_as_uint(xi) | __float_as_uint(et)) >> 30) & 1u);
+            }
+            // every lane of the warp takes part in the vote (no short
+            // circuit: groups that already hit still vote)
+            const unsigned bal = __ballot_sync(FULL, in2);
+            hit = hit || (bal & gmask) != 0u;
+        }
+    }
+    return hit;
+}
+
+// The rollout of sample n with the binned collision check fused in and
+// pipelined one step behind the network: at the top of step h the copies
+// of state h's cell-run bounds are issued and, from the bounds of state
+// h - 1 (issued a step earlier), the copies of its candidate points; the
+// network of step h then runs while they are in flight, and state h - 1 is
+// tested after it.  A sample therefore computes at most two control steps
+// past its first collision, and the loop ends once every group of the warp
+// is discarded; nothing per step is stored.  The decisions are those of
+// the binned check over stored states (same grids, rows and per-point
+// test), so the first collision and cost equal the two-kernel path's.
+// slot: the group's PipeSlot; VAR as in traj_sample (speed limits discard
+// at the first state h >= 1 out of range, unless an earlier state collides).
+template <int W, int G, int KMAX, bool VAR>
+__device__ __forceinline__ FusedOut traj_sample_fused(const DevCfg& c, const TrajJob& job, int n, bool valid,
+                                                      int gl, float* hrow, PipeSlot<G, KMAX>* slot)
+{
+    const GoalEV g = goal_ev(job.si);
+    LaneNet<W, G> net;
+    load_net<W, G, 0>(net, job, n, valid, gl);
+    const BinView& bv = *job.bins;
+
+    float x = 0.f, y = 0.f, ph = 0.f, v = job.si.v0, ap0 = job.si.ap0, ap1 = job.si.ap1, E = 0.f;
+    const int T = job.T;
+    const float invT = 1.0f / (float)T;
+    float rem = (float)T;
+    bool alive = valid;
+    int fh = -1, vdisc = -1;
+    int total_p = 0;
+    for (int h = 0; h <= T + 1; ++h) {
+        float sp = 0.f, cp = 1.f;
+        __syncwarp();                    // the slots rewritten below were read by the whole group
+        if (h <= T) {
+            sincos_r(ph, sp, cp);
+            if constexpr (VAR) {
+                if (c.vlim && alive && h > 0 && vdisc < 0 && !(v >= c.v_lo && v <= c.v_hi)) vdisc = h;
+            }
+            float4 A;
+            float2 B;
+            coef_rows(c, x, y, sp, cp, A, B);
+            if (gl == 0) {
+                slot->rA[h & 1] = A;
+                slot->rB[h & 1] = B;
+            }
+            pipe_runs<G>(bv, h, x, y, alive, gl, reinterpret_cast<int*>(slot->cs[h & 1]));
+        }
+        cp_async_commit();
+        if (h >= 1) {
+            cp_async_wait<1>();          // bounds of state h - 1 (all but the newest group)
+            __syncwarp();
+            total_p = pipe_points<G, KMAX>(bv, h - 1, reinterpret_cast<const int*>(slot->cs[(h - 1) & 1]),
+                                           slot->pt, gl);
+        }
+        cp_async_commit();
+        if (h < T)
+            control_step<W, G, VAR>(c, net, g, invT, gl, hrow, sp, cp, x, y, ph, v, ap0, ap1, E, rem);
+        if (h >= 1) {
+            cp_async_wait<0>();          // own candidate copies of state h - 1
+            const bool hit = pipe_test<G, KMAX>(bv, h - 1, reinterpret_cast<const int*>(slot->cs[(h - 1) & 1]),
+                                                slot->pt, total_p, slot->rA[(h - 1) & 1],
+                                                slot->rB[(h - 1) & 1], gl);
+            if (alive && hit) {
+                alive = false;
+                fh = h - 1;
+            } else if (alive && vdisc == h) {
+                alive = false;
+                fh = h;
+            }
+            if (!__any_sync(FULL, alive)) break;
+        }
+    }
+    cp_async_wait<0>();
+    FusedOut out;
+    out.first_hit = fh;
+    out.cost = __int_as_float(0x7f800000);
+    if (alive) out.cost = final_cost(c, g, x, y, ph, v, E, invT);
     return out;
 }
 
@@ -636,7 +865,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) traj_kernel(const RolloutArgs a
     // staged parameter generation pays at W = 32 (measured on GB300: 11 %
     // faster at T = 40); at W = 16 and 64 the direct load is faster
     constexpr int STAGE_TH = W == 32 ? NW * 32 : 0;
-    traj_sample<W, G, false, STAGE_TH, VAR>(a.c, job, n, n < a.N, gl, hx_all + b * W);
+    traj_sample<W, G, STAGE_TH, VAR>(a.c, job, n, n < a.N, gl, hx_all + b * W);
 }
 
 // Trajectories with the binned check fused in: per sample its first
@@ -645,7 +874,9 @@ template <int W, int G, int NW, int MINB = 1, bool VAR = false>
 __global__ void __launch_bounds__(NW * 32, MINB) fused_kernel(const RolloutArgs a)
 {
     constexpr int B = TrajKernel<W, G, NW>::B;
+    constexpr int KMAX = FUSED_PREFETCH / G;
     __shared__ __align__(16) float hx_all[B * W];
+    __shared__ PipeSlot<G, KMAX> slots[B];
     __shared__ unsigned long long red[NW];
     const int tid = threadIdx.x;
     const int b = tid / G, gl = tid % G;
@@ -671,7 +902,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) fused_kernel(const RolloutArgs 
     job.bins = &a.bins;
     job.stage = nullptr;
     const bool valid = n < a.N;
-    const FusedOut r = traj_sample<W, G, true, 0, VAR>(a.c, job, n, valid, gl, hx_all + b * W);
+    const FusedOut r = traj_sample_fused<W, G, KMAX, VAR>(a.c, job, n, valid, gl, hx_all + b * W, slots + b);
     unsigned long long key = ~0ull;
     if (valid && gl == 0) {
         if (r.first_hit < 0)
@@ -744,7 +975,7 @@ __global__ void __launch_bounds__(32) reroll_epilogue_kernel(const RolloutArgs a
     job.bins = nullptr;
     job.stage = nullptr;
     if (e.trajectory || e.controls)
-        traj_sample<W, G, false, 0, VAR>(a.c, job, idx, true, lane % G, hrows + (lane / G) * W);
+        traj_sample<W, G, 0, VAR>(a.c, job, idx, true, lane % G, hrows + (lane / G) * W);
     __syncwarp();
     float s0, c0;
     sincosf(si.phi0, &s0, &c0);

@@ -87,11 +87,14 @@ def test_polygon_parity_small(orc, fp, width, N, T, M, seed):
     rs = P.replay_stats(sc, g, idx)
     assert not rs["bad"], rs["bad"][:5]
     o = P.oracle_samples(sc, idx)
-    ok = P.traj_stats(sc, g, o, idx)
-    assert ok.mean() >= 0.93, ok.mean()
+    frac, ok, err, kap, _ = P.traj_check(sc, g, idx, o)
+    assert frac >= P.CONSISTENT_FRAC, (frac, err[~ok][:5], kap[~ok][:5])
+    assert ok[g["best_idx"]]
+    ca = P.cost_at_gpu_states(sc, g, idx)
+    assert np.nanmax(ca, initial=0.0) <= P.COST_RTOL, np.nanmax(ca)
     wc = P.winner_check(g, o["cost"], o["first_hit"])
     if not wc.get("infeasible"):
-        assert wc["gpu_pick_oracle_cost"] <= wc["best_unambiguous"] * (1 + P.COST_RTOL) + P.COST_RTOL, wc
+        assert wc["ok"], wc
     assert 0 < np.count_nonzero(g["first_hit"] >= 0) < N
 
 

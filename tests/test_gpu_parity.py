@@ -82,13 +82,17 @@ def test_plan_parity_small(orc, width, N, T, M, seed):
     # collision decisions at the GPU's states
     fs = P.flag_stats(sc, g, idx)
     assert not fs["bad"], fs["bad"][:5]
-    # free-running trajectories
-    ok = P.traj_stats(sc, g, o, idx)
-    assert ok.mean() >= 0.93, ok.mean()
-    # chosen sample
+    # free-running trajectories against the oracle's own sensitivity, the
+    # winner's included
+    frac, ok, err, kap, _ = P.traj_check(sc, g, idx, o)
+    assert frac >= P.CONSISTENT_FRAC, (frac, err[~ok][:5], kap[~ok][:5])
+    assert ok[g["best_idx"]], (err[g["best_idx"]], kap[g["best_idx"]])
+    # costs at the GPU's own states; the chosen sample
+    ca = P.cost_at_gpu_states(sc, g, idx)
+    assert np.nanmax(ca, initial=0.0) <= P.COST_RTOL, np.nanmax(ca)
     wc = P.winner_check(g, o["cost"], o["first_hit"])
     if not wc.get("infeasible"):
-        assert wc["gpu_pick_oracle_cost"] <= wc["best_unambiguous"] * (1 + P.COST_RTOL) + P.COST_RTOL, wc
+        assert wc["ok"], wc
     # winner trajectory and controls in the world frame
     b = g["best_idx"]
     fh = int(g["first_hit"][b])
@@ -177,33 +181,58 @@ def test_single_scene_full(orc):
     assert not rs["bad"], rs["bad"][:5]
     fs = P.flag_stats(sc, g, idx)
     assert not fs["bad"], fs["bad"][:5]
-    ok = P.traj_stats(sc, g, o, idx)
-    assert ok.mean() >= 0.93
+    frac, ok, err, kap, _ = P.traj_check(sc, g, idx, o)
+    assert frac >= P.CONSISTENT_FRAC, (frac, err[~ok][:5], kap[~ok][:5])
+    assert ok[g["best_idx"]]
+    ca = P.cost_at_gpu_states(sc, g, idx)
+    assert np.nanmax(ca, initial=0.0) <= P.COST_RTOL, np.nanmax(ca)
     wc = P.winner_check(g, o["cost"], o["first_hit"])
-    assert wc["gpu_pick_oracle_cost"] <= wc["best_unambiguous"] * (1 + P.COST_RTOL) + P.COST_RTOL, wc
+    assert wc["ok"], wc
 
 
-def test_course_full_size(orc):
-    """The closed-loop course workload at full size (N=16384, T=40,
-    8-32-32-2, M=2000), as the benchmark launches it: collision status and
-    cost of every sample from the oracle, replay and flags on a sample of
-    1024 indices, the winner against the oracle's best."""
-    sc = inputs.scene_course(0)
+def _full_size(sc, fh_agree_min):
+    """Every sample's collision status and cost from the oracle; per-step
+    replay, flags at the GPU's states, the trajectory rule and the cost at
+    the GPU's states on 1024 sampled indices plus the winner."""
     g = P.gpu_plan(sc)
     N = sc["N"]
     o = P.oracle_samples(sc, np.arange(N), record=False)
     wc = P.winner_check(g, o["cost"], o["first_hit"])
-    assert wc["agree_frac"] >= 0.99, wc
-    assert wc["gpu_pick_oracle_cost"] <= wc["best_unambiguous"] * (1 + P.COST_RTOL) + P.COST_RTOL, wc
+    assert wc["agree_frac"] >= fh_agree_min, wc
+    assert wc["ok"], wc
     idx = np.random.default_rng(0).choice(N, 1024, replace=False)
     idx = np.union1d(idx, [g["best_idx"]])
+    kb = int(np.searchsorted(idx, g["best_idx"]))
     rs = P.replay_stats(sc, g, idx)
     assert not rs["bad"], rs["bad"][:5]
     fs = P.flag_stats(sc, g, idx)
     assert not fs["bad"], fs["bad"][:5]
-    o2 = P.oracle_samples(sc, idx)
-    ok = P.traj_stats(sc, g, o2, idx)
-    assert ok.mean() >= 0.93, ok.mean()
+    frac, ok, err, kap, o2 = P.traj_check(sc, g, idx)
+    assert frac >= P.CONSISTENT_FRAC, (frac, err[~ok][:5], kap[~ok][:5])
+    assert ok[kb], (err[kb], kap[kb])
+    # where GPU and oracle disagree on the first collision, the oracle's own
+    # first collision moves under the 1e-6 probes as well
+    assert np.all(kap[o2["first_hit"] != g["first_hit"][idx]] >= P.COND_FH)
+    ca = P.cost_at_gpu_states(sc, g, idx)
+    assert np.nanmax(ca, initial=0.0) <= P.COST_RTOL, np.nanmax(ca)
+    return g
+
+
+def test_course_full_size(orc):
+    """The closed-loop course workload at full size (N=16384, T=40,
+    8-32-32-2, M=2000), as the benchmark launches it (binned collision
+    check)."""
+    _full_size(inputs.scene_course(0), 0.99)
+
+
+def test_large_full_size(orc):
+    """The largest workload at full size (N=65536, T=100, 8-64-64-2, M=8192
+    over 80 x 80 m, 20 % moving), as the benchmark launches it (binned
+    collision check).  Over T=100 steps more samples are sensitive: the
+    first collision step agrees on >= 98 % of all samples, and on the
+    sampled indices every disagreement is on a sample whose own oracle
+    trajectory changes its first collision under the 1e-6 probes."""
+    _full_size(inputs.scene_large(0), 0.98)
 
 
 def test_large_point_set_from_global_memory(orc):

@@ -69,11 +69,14 @@ def test_body_frame_parity_small(orc, width, N, T, M, seed):
     fs = P.flag_stats(sc, g, idx)
     assert not fs["bad"], fs["bad"][:5]
     o = P.oracle_samples(sc, idx)
-    ok = P.traj_stats(sc, g, o, idx)
-    assert ok.mean() >= 0.93, ok.mean()
+    frac, ok, err, kap, _ = P.traj_check(sc, g, idx, o)
+    assert frac >= P.CONSISTENT_FRAC, (frac, err[~ok][:5], kap[~ok][:5])
+    assert ok[g["best_idx"]]
+    ca = P.cost_at_gpu_states(sc, g, idx)
+    assert np.nanmax(ca, initial=0.0) <= P.COST_RTOL, np.nanmax(ca)
     wc = P.winner_check(g, o["cost"], o["first_hit"])
     if not wc.get("infeasible"):
-        assert wc["gpu_pick_oracle_cost"] <= wc["best_unambiguous"] * (1 + P.COST_RTOL) + P.COST_RTOL, wc
+        assert wc["ok"], wc
     # the frame matters: the plain path picks other controls
     g0 = P.gpu_plan(_with(sc, feature_frame=0))
     assert not np.array_equal(g0["sample_ctrl"], g["sample_ctrl"])

@@ -214,3 +214,28 @@ def test_tshc_rounds_never_worse(orc):
     one = orc.plan_tshc(sc["preset"], st, gl, ob, 64, 15, sc["seed"], sc["t_index"], 1, 0.3)
     plain = orc.plan(sc["preset"], st, gl, ob, 64, 15, sc["seed"], sc["t_index"])
     assert one["best_cost"] == plain["best_cost"] and one["best_idx"] == plain["best_idx"]
+
+
+def test_cost_from_final_state_and_controls(orc):
+    """orc.cost (the cost of a rollout from its final state and its applied
+    controls) equals the rollout's own cost for every collision-free sample,
+    and in hand-worked cases: at the goal only the effort term remains; a
+    3-4-5 offset, a heading error across the +-pi wrap and a speed error add
+    their weighted magnitudes."""
+    p = inputs.planner(16)
+    sc = inputs.tiny_scene(5, N=64, T=15, M=40, width=16)
+    st = np.asarray(sc["state"], np.float64)
+    goal_ev, obs_ev = orc.frame_to_ev(st, np.asarray(sc["goal"], np.float64), np.asarray(sc["obs"], np.float64))
+    o = orc.rollout_samples(p, sc["seed"], 0, np.arange(64, dtype=np.int32), [0, 0, 0, st[3]], st[4:6],
+                            goal_ev, obs_ev, 15)
+    free = np.flatnonzero(o["first_hit"] < 0)
+    assert len(free) > 0
+    for k in free:
+        assert orc.cost(p, o["traj"][k][-1], o["ctrl"][k], goal_ev) == o["cost"][k]
+    ctrl = np.array([[0.5, -0.5], [1.0, 0.0], [0.0, 0.0], [-0.25, 0.75]])      # E = 0.5 + 1 + 0 + 0.625
+    g = np.array([3.0, 4.0, 3.0, 2.0])
+    assert math.isclose(orc.cost(p, g, ctrl, g), p["w_effort"] * 2.125 / 4, rel_tol=1e-15)
+    z = np.array([0.0, 0.0, -3.0, 5.0])                  # heading error 6 rad wraps to 6 - 2 pi
+    want = (p["w_pos"] * 5.0 + p["w_phi"] * (2 * math.pi - 6.0) + p["w_v"] * 3.0
+            + p["w_effort"] * 2.125 / 4)
+    assert math.isclose(orc.cost(p, z, ctrl, g), want, rel_tol=1e-14)

@@ -266,6 +266,19 @@ typedef struct {
     int32_t reserved;
 } npp_loop_state;
 
+/* The hill climb of Sect. II-D (TSHC, N_restarts rounds; Table
+ * hyperparameters) in every sampling time of the loops created on h after
+ * this call: round 0 is the plan step (warm start = the last winner); each
+ * of the n_restarts - 1 further rounds draws N samples theta = theta_best +
+ * sigma_pert eps (eps the normals of Philox stream r, r = round) with
+ * theta_best -- the winner so far -- as sample 0, so the best cost never
+ * increases; the last round's winner is applied.  The same rounds as
+ * npp_plan_tshc.  The paper takes sigma_pert from its cited work; here it is
+ * one fixed scale.  n_restarts in [1, 64] (1, the default: the plan step
+ * alone); sigma_pert > 0 and finite when n_restarts > 1.  Loops created
+ * earlier keep their setting. */
+npp_status npp_set_loop_restarts(npp_handle* h, int32_t n_restarts, float sigma_pert);
+
 /* Create a loop on handle h (which it uses; keep h alive): initial state s0,
  * waypoints_host[n_wp][4] (x, y, phi, v), eps_host[4], obstacle points
  * obs_dev[M][4] at t = 0 (copied; the caller's array is not modified), N
@@ -420,7 +433,7 @@ npp_status npp_batch_destroy(npp_batch* B);
  *
  * No handle: the constants come from cfg (its max_* fields are ignored and
  * it is checked as npp_create checks it), the
- * workspace is one fixed file-scope device array of about 33 MB that every
+ * workspace is one fixed file-scope device array of about 17 MB that every
  * GPU loading this part of the library holds until the process exits.
  * Limits: 1 <= N <= 16384 and N * (T + 1) <= 688128 sample-steps (for
  * example N = 16384 with T <= 41); larger requests return NPP_INVALID_ARG

@@ -51,7 +51,7 @@ __global__ void epilogue_kernel(const EpilogueArgs e)
     if (e.dyn) {
         x0 = e.dyn->x0; y0 = e.dyn->y0; phi0 = e.dyn->phi0;
         skey.t_index = e.dyn->t_index;
-        warm_ok = e.dyn->warm_valid != 0;
+        warm_ok = e.dyn->warm_valid != 0 || e.warm_force != 0;
     }
     const unsigned long long key = *e.best_key;
     const int idx = (int)(key & 0xffffffffull);
@@ -147,6 +147,19 @@ cudaError_t launch_epilogue(const EpilogueArgs& e, cudaStream_t s)
 }  // namespace npp
 
 // ------------------------------------------------------------------ helpers
+namespace {
+__global__ void fill_value_kernel(float* p, int n, float v)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = v;
+}
+}  // namespace
+
+cudaError_t fill_floats(float* p, int n, float v, cudaStream_t s)
+{
+    fill_value_kernel<<<(n + 255) / 256, 256, 0, s>>>(p, n, v);
+    return cudaGetLastError();
+}
+
 static cudaError_t launch_traj(const npp_handle* h, const RolloutArgs& a, cudaStream_t s)
 {
     switch (h->cfg.width) {
@@ -168,8 +181,10 @@ static cudaError_t launch_fused(const npp_handle* h, const RolloutArgs& a, cudaS
 
 npp_status run_rollout(npp_handle* h, RolloutArgs& a, cudaStream_t s, bool allow_fused, bool* fused)
 {
-    a.coefA = h->d_coefA;
-    a.coefB = h->d_coefB;
+    // no rows are stored: every collision kernel recomputes them from the
+    // stored states
+    a.coefA = nullptr;
+    a.coefB = nullptr;
     a.work = h->d_work;
     *fused = false;
     if (h->fp_faces > 0) {
@@ -348,6 +363,8 @@ npp_status npp_create(npp_handle** out, const npp_config* cfg, int32_t device)
     h->cfg = *cfg;
     h->collide_variant = -1;
     h->fuse = false;
+    h->loop_restarts = 1;
+    h->loop_sigma = 0.0f;
     h->collide_active = -1;
     h->occ_M = -1;
     cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, device);
@@ -366,8 +383,6 @@ npp_status npp_create(npp_handle** out, const npp_config* cfg, int32_t device)
     A((void**)&h->d_ctrl, NT * sizeof(float2));
     A((void**)&h->d_jfree, (size_t)cfg->max_N * sizeof(float));
     if (cfg->v_limits) A((void**)&h->d_vfirst, (size_t)cfg->max_N * sizeof(int));
-    A((void**)&h->d_coefA, NT1 * sizeof(float4));
-    A((void**)&h->d_coefB, NT1 * sizeof(float2));
     A((void**)&h->d_work, 64);
     A(&h->d_bins, binned_workspace_bytes(cfg->max_T, cfg->max_M));
     if (cfg->max_M > max_points) {
@@ -402,7 +417,7 @@ npp_status npp_destroy(npp_handle* h)
     if (!h) return NPP_OK;
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
-    void* ptrs[] = { h->d_key, h->d_traj, h->d_ctrl, h->d_jfree, h->d_vfirst, h->d_fp, h->d_coefA, h->d_coefB, h->d_work,
+    void* ptrs[] = { h->d_key, h->d_traj, h->d_ctrl, h->d_jfree, h->d_vfirst, h->d_fp, h->d_work,
                      h->d_pXY, h->d_pV, h->d_bins,
                      h->d_obs, h->d_warm, h->d_sigma, h->d_best, h->d_params, h->d_controls, h->d_trajectory,
                      h->d_costs, h->d_fh };
@@ -490,6 +505,17 @@ npp_status npp_plan_step_proposal(npp_handle* h, const npp_state* state, const n
 __global__ void fill_kernel(float* p, int n, float v)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = v;
+}
+
+npp_status npp_set_loop_restarts(npp_handle* h, int32_t n_restarts, float sigma_pert)
+{
+    if (!h) return fail(nullptr, NPP_INVALID_ARG, "handle is NULL");
+    if (n_restarts < 1 || n_restarts > 64) return fail(h, NPP_INVALID_ARG, "n_restarts=%d outside [1, 64]", n_restarts);
+    if (n_restarts > 1 && (!(sigma_pert > 0.0f) || !std::isfinite(sigma_pert)))
+        return fail(h, NPP_INVALID_ARG, "sigma_pert must be finite and > 0");
+    h->loop_restarts = n_restarts;
+    h->loop_sigma = n_restarts > 1 ? sigma_pert : 0.0f;
+    return NPP_OK;
 }
 
 npp_status npp_plan_tshc(npp_handle* h, const npp_state* state, const npp_goal* goal, const float* obs_dev,

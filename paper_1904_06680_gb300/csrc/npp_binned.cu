@@ -40,8 +40,9 @@ __global__ void __launch_bounds__(BIN_THREADS) bin_build_kernel(const RolloutArg
                                  cell_start + (size_t)h * BIN_CS_STRIDE, binned + (size_t)h * a.M, cnt, run_tot);
 }
 
-// one warp per sample over the stored trajectories and inequality rows, h
-// in order: the candidates of a step are the points of at most five cell
+// one warp per sample over the stored states (each step's inequality rows
+// recomputed from the state), h in order: the candidates of a step are the
+// points of at most five cell
 // rows, each row's cells contiguous in the sorted array; the lanes stride
 // through them (coalesced loads) and a ballot ends the sample at its first
 // colliding step
@@ -56,22 +57,16 @@ __global__ void __launch_bounds__(BINNED_WARPS * 32) collide_binned_kernel(const
     unsigned long long key = ~0ull;
     if (n < N) {
         int fh = -1;
-        // the next step's rows are loaded while the current step is checked
-        float4 nca = a.coefA[n];
-        float2 ncb = a.coefB[n];
+        // the next step's state is loaded while the current step is checked
         float4 nz = a.traj[n];
         for (int h = 0; h <= T; ++h) {
-            const float4 ca = nca;
-            const float2 cb = ncb;
             // the rectangle lies in the disk of radius reach around the
             // reference point (reach covers the centre offset)
             const float4 z = nz;
-            if (h < T) {
-                const size_t nx = (size_t)(h + 1) * N + n;
-                nca = a.coefA[nx];
-                ncb = a.coefB[nx];
-                nz = a.traj[nx];
-            }
+            if (h < T) nz = a.traj[(size_t)(h + 1) * N + n];
+            float4 ca;
+            float2 cb;
+            rows_of_state(a.c, z, ca, cb);
             const CandRows cr = cand_rows(g.cell_start + (size_t)h * BIN_CS_STRIDE, g, z.x, z.y, g.reach);
             const float2* pts = g.pts + (size_t)h * M;
             const int total = cr.total;

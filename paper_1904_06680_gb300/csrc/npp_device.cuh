@@ -446,6 +446,8 @@ struct RolloutArgs {
     unsigned* work;                    // work-queue counter of the persistent collision kernel
     int grid_collide;                  // persistent grid size
     const LoopDev* dyn;                // when set, per-step scalars come from here
+    int warm_force;                    // the warm start replaces sample 0 even before the loop's
+                                       // first step (restart rounds: it is the incumbent)
     float4* pXY;                       // EV-frame point pairs in global memory (when the
     float4* pV;                        // points exceed shared memory), [ceil(M/2)]
     BinView bins;                      // per-step grids (binned and fused collision checks)
@@ -460,7 +462,7 @@ __device__ __forceinline__ StepIn step_in(const RolloutArgs& a)
         s.x0 = d.x0; s.y0 = d.y0; s.phi0 = d.phi0; s.v0 = d.v0; s.ap0 = d.ap0; s.ap1 = d.ap1;
         s.gx = d.gx; s.gy = d.gy; s.gphi = d.gphi; s.gv = d.gv;
         s.t_index = d.t_index;
-        s.warm_ok = d.warm_valid != 0;
+        s.warm_ok = d.warm_valid != 0 || a.warm_force != 0;
     } else {
         s.x0 = a.x0; s.y0 = a.y0; s.phi0 = a.phi0; s.v0 = a.v0; s.ap0 = a.ap0; s.ap1 = a.ap1;
         s.gx = a.gx; s.gy = a.gy; s.gphi = a.gphi; s.gv = a.gv;
@@ -484,6 +486,7 @@ struct EpilogueArgs {
     float* controls;
     float* trajectory;
     const LoopDev* dyn;                // when set, x0, y0, phi0, t_index, warm validity from here
+    int warm_force;                    // as RolloutArgs::warm_force
 };
 
 // launchers: trajectory kernel per network width, one collision kernel

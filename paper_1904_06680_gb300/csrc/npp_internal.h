@@ -30,8 +30,6 @@ struct npp_handle {
     float4* d_fp;                        // [FP_MAX_FACES] general footprint faces
     int fp_faces;                        // 0: the rectangle of cfg
     double fp_radius;                    // footprint's largest vertex distance
-    float4* d_coefA;                     // [(max_T+1) * max_N]
-    float2* d_coefB;                     // [(max_T+1) * max_N]
     unsigned* d_work;                    // persistent-kernel work counter
     int sm_count;
     int collide_variant;                 // -1 automatic, else a fixed collision-kernel variant
@@ -39,6 +37,8 @@ struct npp_handle {
     int collide_active;                  // variant used for the current launch
     int traj_variant;                    // trajectory launch shape (0..3)
     bool fuse;                           // binned check fused into the trajectory kernel
+    int loop_restarts;                   // hill-climb rounds per sampling time of new loops (1: none)
+    float loop_sigma;                    // their perturbation scale
     int occ_M, occ_blocks;               // cached occupancy for the last M
     float4* d_pXY;                       // EV-frame point pairs when M exceeds shared memory
     float4* d_pV;
@@ -72,6 +72,9 @@ inline cudaError_t record_event(cudaEvent_t ev, cudaStream_t s)
     return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal)
                                                : cudaEventRecord(ev, s);
 }
+
+// p[0 .. n) = v on stream s
+cudaError_t fill_floats(float* p, int n, float v, cudaStream_t s);
 
 // records a message for npp_last_error and returns s
 npp_status fail(npp_handle* h, npp_status s, const char* fmt, ...);

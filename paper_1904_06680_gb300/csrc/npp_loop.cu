@@ -4,7 +4,11 @@
 // the simulated vehicle (Step 6), moves the obstacle points, switches to the
 // next waypoint once the current one is reached within the tolerances of
 // Table hyperparameters (Steps 4 and 7) and keeps the winner's parameters as
-// the next warm start (Sect. II-D "Fifth").  The host only replays the graph.
+// the next warm start (Sect. II-D "Fifth").  With restarts set on the handle
+// (npp_set_loop_restarts) the plan step of every sampling time is the hill
+// climb of Sect. II-D: after the first round, each further round samples
+// theta = theta_best + sigma_pert eps around the best so far (kept as sample
+// 0), as npp_plan_tshc does.  The host only replays the graph.
 #include <cmath>
 #include <cstring>
 
@@ -42,6 +46,8 @@ struct npp_loop {
     float* d_log;            // [max_log][8]
     float* d_costs;          // [N] per-sample costs of the last step
     int32_t* d_fh;           // [N] per-sample first collisions of the last step
+    int restarts;            // hill-climb rounds per sampling time (1: the plan step alone)
+    float* d_sigma;          // [n_theta] their perturbation scale
     cudaEvent_t ev[4];       // captured: start, after trajectories, after collisions, end
     cudaStream_t cap;
     cudaGraph_t graph;
@@ -225,7 +231,7 @@ void free_loop(npp_loop* L)
     if (L->graph) cudaGraphDestroy(L->graph);
     if (L->cap) cudaStreamDestroy(L->cap);
     void* ptrs[] = { L->d_dyn, L->d_wp, L->d_obs0, L->d_obs, L->d_warm, L->d_best, L->d_controls,
-                     L->d_trajectory, L->d_log, L->d_costs, L->d_fh };
+                     L->d_trajectory, L->d_log, L->d_costs, L->d_fh, L->d_sigma };
     for (void* p : ptrs) if (p) cudaFree(p);
     for (int i = 0; i < 4; ++i) if (L->ev[i]) cudaEventDestroy(L->ev[i]);
     delete L;
@@ -271,6 +277,35 @@ npp_status enqueue_step(npp_loop* L, uint64_t seed)
     e.trajectory = L->d_trajectory;
     e.dyn = L->d_dyn;
     CUDA_TRY(h, launch_winner_epilogue(h, a, e, fused, s));
+    // restart rounds: the winner so far is sample 0 (warm start, valid even
+    // at the loop's first step), every other sample a perturbation of it on
+    // the round's own Philox stream; the winner's parameters, controls and
+    // trajectory are overwritten by each round's (never worse) winner.  The
+    // stage events time the first round; the end event the whole step.
+    const bool timing = h->timing;
+    h->timing = false;
+    for (int r = 1; r < L->restarts; ++r) {
+        RolloutArgs ar = a;
+        ar.prop = Proposal{ L->d_warm, L->d_sigma, L->N, (uint32_t)r };
+        ar.warm = L->d_warm;
+        ar.warm_force = 1;
+        CUDA_TRY(h, cudaMemsetAsync(h->d_key, 0xff, sizeof(unsigned long long), s));
+        bool fr = false;
+        st = run_rollout(h, ar, s, true, &fr);
+        if (st != NPP_OK) {
+            h->timing = timing;
+            return st;
+        }
+        EpilogueArgs er = e;
+        er.prop = ar.prop;
+        er.warm_force = 1;
+        cudaError_t ce = launch_winner_epilogue(h, ar, er, fr, s);
+        if (ce != cudaSuccess) {
+            h->timing = timing;
+            return fail(h, NPP_CUDA_ERROR, "restart epilogue: %s", cudaGetErrorString(ce));
+        }
+    }
+    h->timing = timing;
     PlantCfg pc;
     pc.lf = h->cfg.lf; pc.lr = h->cfg.lr; pc.delta_max = h->cfg.delta_max;
     pc.u_min = h->cfg.u_min; pc.u_max = h->cfg.u_max; pc.Ts = h->cfg.Ts;
@@ -332,6 +367,8 @@ npp_status loop_create(npp_handle* h, const npp_state* s0, const float* waypoint
     A((void**)&L->d_log, (size_t)(max_log > 0 ? max_log : 1) * 8 * sizeof(float));
     A((void**)&L->d_costs, (size_t)N * sizeof(float));
     A((void**)&L->d_fh, (size_t)N * sizeof(int32_t));
+    L->restarts = h->loop_restarts;
+    if (L->restarts > 1) A((void**)&L->d_sigma, (size_t)h->n_theta * sizeof(float));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&L->cap, cudaStreamNonBlocking);
     for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&L->ev[i]);
     if (e != cudaSuccess) {
@@ -358,6 +395,10 @@ npp_status loop_create(npp_handle* h, const npp_state* s0, const float* waypoint
     if (e == cudaSuccess) e = cudaMemcpy(L->d_wp, waypoints_host, (size_t)n_wp * sizeof(float4), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && M > 0) e = cudaMemcpy(L->d_obs0, obs_dev, (size_t)M * sizeof(float4), cudaMemcpyDeviceToDevice);
     if (e == cudaSuccess && M > 0) e = cudaMemcpy(L->d_obs, obs_dev, (size_t)M * sizeof(float4), cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess && L->restarts > 1) {
+        e = fill_floats(L->d_sigma, h->n_theta, h->loop_sigma, L->cap);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(L->cap);
+    }
     if (e == cudaSuccess && mission) {
         // the first goal and the points seen at t = 0
         mission_init_kernel<<<1, 1, 0, L->cap>>>(L->d_dyn, L->d_wp);

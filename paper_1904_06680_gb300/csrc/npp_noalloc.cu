@@ -14,7 +14,7 @@
 // results equal npp_plan_step's.  Its workspace is one file-scope
 // __device__ array of fixed size instead of handle-owned cudaMalloc buffers.
 //
-// The array (NOALLOC_BYTES, about 33 MB) exists on every GPU on which this
+// The array (NOALLOC_BYTES, about 17 MB) exists on every GPU on which this
 // library's module is loaded, until the process exits.  All calls share it,
 // so calls that overlap on the GPU (on different streams, or from different
 // threads) race; each call clears the parts that must start at zero.
@@ -36,15 +36,12 @@ namespace {
 constexpr int NOALLOC_MAX_N = 16384;
 constexpr long long NOALLOC_MAX_STEPS = 16384LL * 42;     // 688,128 sample-steps
 // layout: [key, work counter | pad to 256] [cost if free, N floats]
-//         [first speed-violating step, N ints]
-//         [states float4] [controls float2] [coef A float4] [coef B float2]
+//         [first speed-violating step, N ints] [states float4] [controls float2]
 constexpr size_t OFF_JFREE = 256;
 constexpr size_t OFF_VFIRST = OFF_JFREE + (size_t)NOALLOC_MAX_N * 4;
 constexpr size_t OFF_TRAJ = OFF_VFIRST + (size_t)NOALLOC_MAX_N * 4;
 constexpr size_t OFF_CTRL = OFF_TRAJ + (size_t)NOALLOC_MAX_STEPS * 16;
-constexpr size_t OFF_COEFA = OFF_CTRL + (size_t)NOALLOC_MAX_STEPS * 8;
-constexpr size_t OFF_COEFB = OFF_COEFA + (size_t)NOALLOC_MAX_STEPS * 16;
-constexpr size_t NOALLOC_BYTES = OFF_COEFB + (size_t)NOALLOC_MAX_STEPS * 8;
+constexpr size_t NOALLOC_BYTES = OFF_CTRL + (size_t)NOALLOC_MAX_STEPS * 8;
 
 static __device__ __align__(256) unsigned char g_scratch[NOALLOC_BYTES];
 
@@ -141,8 +138,8 @@ extern "C" npp_status npp_plan_step_noalloc(const npp_config* cfg, const npp_sta
                               : reinterpret_cast<float2*>(base + OFF_CTRL);
     a.jfree = reinterpret_cast<float*>(base + OFF_JFREE);
     a.vfirst = cfg->v_limits ? reinterpret_cast<int*>(base + OFF_VFIRST) : nullptr;
-    a.coefA = reinterpret_cast<float4*>(base + OFF_COEFA);
-    a.coefB = reinterpret_cast<float2*>(base + OFF_COEFB);
+    a.coefA = nullptr;                   // the collision kernels recompute the rows from the states
+    a.coefB = nullptr;
     a.best_key = reinterpret_cast<unsigned long long*>(base);
     a.work = reinterpret_cast<unsigned*>(base + 8);
     int sm_count = 1;

@@ -224,6 +224,17 @@ __device__ __forceinline__ void coef_rows(const DevCfg& c, float x, float y, flo
     B = make_float2(__fmul_rn(cp, sw), -__fmul_rn(across, sw));
 }
 
+// The rows of a stored state z = (x, y, phi, v): the trajectory kernel's own
+// arithmetic on the same FP32 values, so a collision kernel that recomputes
+// them from the stored state gets the same bits the rollout had (and no
+// rows need to be stored).
+__device__ __forceinline__ void rows_of_state(const DevCfg& c, const float4& z, float4& A, float2& B)
+{
+    float sp, cp;
+    sincos_r(z.z, sp, cp);
+    coef_rows(c, z.x, z.y, sp, cp, A, B);
+}
+
 __device__ __forceinline__ void write_coef(float4* coefA, float2* coefB, const DevCfg& c,
                                            long long idx, float x, float y, float sp, float cp)
 {
@@ -1172,21 +1183,19 @@ __global__ void __launch_bounds__(NW * 32, MINB) collide_block_kernel(const Roll
         int fh = -1;
         int rank = tid;
         int L = cnt;
-        float4 ca = make_float4(0.f, 0.f, 0.f, 0.f);
-        float2 cb = make_float2(0.f, 0.f);
-        if (owner) { ca = a.coefA[n]; cb = a.coefB[n]; }
+        float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (owner) z = a.traj[n];
         __syncthreads();                      // points staged / previous item done
         for (int h = 0; h <= T; ++h) {
             const int buf = h & 1;
             if (alive) {
+                float4 ca;
+                float2 cb;
+                rows_of_state(c, z, ca, cb);
                 cfA[buf * SBMAX + rank] = ca;
                 cfB[buf * SBMAX + rank] = cb;
                 hitf[buf * SBMAX + rank] = 0;
-                if (h < T) {
-                    const size_t idx = (size_t)(h + 1) * N + n;
-                    ca = a.coefA[idx];
-                    cb = a.coefB[idx];
-                }
+                if (h < T) z = a.traj[(size_t)(h + 1) * N + n];
             }
             __syncthreads();
             const int nch = (L + 7) / 8;
@@ -1375,17 +1384,13 @@ __global__ void __launch_bounds__(NW * 32, MINB) collide_warp_kernel(const Rollo
         const bool mine = lane < cnt;
         unsigned live = (1u << cnt) - 1u;
         int fh = -1;
-        float4 ca = make_float4(0.f, 0.f, 0.f, 0.f);
-        float2 cb = make_float2(0.f, 0.f);
-        if (mine) { ca = a.coefA[n]; cb = a.coefB[n]; }
+        float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (mine) z = a.traj[n];
         for (int h = 0; h <= T; ++h) {
-            const float4 cur_a = ca;
-            const float2 cur_b = cb;
-            if (mine && h < T) {
-                const size_t idx = (size_t)(h + 1) * N + n;
-                ca = a.coefA[idx];
-                cb = a.coefB[idx];
-            }
+            float4 cur_a;
+            float2 cur_b;
+            rows_of_state(c, z, cur_a, cur_b);
+            if (mine && h < T) z = a.traj[(size_t)(h + 1) * N + n];
             const unsigned hits = warp_step(XY, V, npairs, (float)h * c.Ts, cur_a, cur_b, live,
                                             sA, sB, lane);
             if ((hits >> lane) & 1u) fh = h;
@@ -1474,17 +1479,13 @@ __global__ void __launch_bounds__(S * 32, MINB) collide_slice_kernel(const Rollo
         const int n = n0 + lane;
         const bool mine = lane < cnt;
         unsigned live = (1u << cnt) - 1u;
-        float4 ca = make_float4(0.f, 0.f, 0.f, 0.f);
-        float2 cb = make_float2(0.f, 0.f);
-        if (mine) { ca = a.coefA[n]; cb = a.coefB[n]; }
+        float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (mine) z = a.traj[n];
         for (int h = 0; h <= T; ++h) {
-            const float4 cur_a = ca;
-            const float2 cur_b = cb;
-            if (mine && h < T) {
-                const size_t idx = (size_t)(h + 1) * N + n;
-                ca = a.coefA[idx];
-                cb = a.coefB[idx];
-            }
+            float4 cur_a;
+            float2 cur_b;
+            rows_of_state(c, z, cur_a, cur_b);
+            if (mine && h < T) z = a.traj[(size_t)(h + 1) * N + n];
             // drop samples another slice already found colliding at or before h
             const unsigned gone = __ballot_sync(FULL, lane < 8 && *(volatile int*)&dead_at[lane] <= h);
             live &= ~gone;

@@ -52,6 +52,15 @@ Scene recipes (all world-frame, SI units; obstacles are (x, y, vx, vy)):
   vehicle in the far lane at 1 m/s.  Start at rest on the centre line.
   8-32-32-2, N = 8192, T = 40; range field 25 m ahead, 8 m behind, 10 m to
   either side.
+* ``scene_turnaround``: the paper's Experiment 1 (Sect. V): start at rest at
+  the origin facing +x, one waypoint at the origin facing -x at rest, no
+  obstacle points (one point parked 10 km away, so the kernels see M = 1);
+  the paper's vehicle (Table veh) with an 8-16-16-2 network, N = 16384,
+  T = 80; `seed` picks the sampler's Philox seed.
+* ``scene_waypoints``: the paper's Experiment 4 (Sect. V): start at rest at
+  the origin, the four waypoints of ``scene_course`` (forward and reverse
+  driving with 90-degree heading changes), no obstacle points (one parked
+  10 km away); 8-32-32-2, N = 16384, T = 40.
 * ``scene_parking``: the reverse parking mission of the paper's Experiment 5
   (Fig. 8, bottom row) in the scaled slot layout of ``scene_batch``: start at
   rest at (0, 2.5) facing +x, an auxiliary waypoint at the origin facing +y,
@@ -445,3 +454,18 @@ def scene_parking(seed: int = 0, N: int = 16384, T: int = 60, width: int = 16):
     state = np.array([0.0, 2.5, 0.0, 0.0, 0.0, 0.0])
     return dict(preset=planner(width), state=state, goal=waypoints[0].copy(), obs=obs, N=N, T=T,
                 seed=philox_seed(seed), t_index=0, waypoints=waypoints)
+
+
+def scene_turnaround(seed: int = 0, N: int = 16384, T: int = 80):
+    """See the module docstring (Experiment 1)."""
+    obs = np.array([[1e4, 1e4, 0.0, 0.0]])
+    waypoints = np.array([[0.0, 0.0, math.pi, 0.0]])
+    return dict(preset=dict(PAPER, widths=(8, 16, 16, 2)), state=np.zeros(6), goal=waypoints[0].copy(), obs=obs,
+                N=N, T=T, seed=philox_seed(seed), t_index=0, waypoints=waypoints)
+
+
+def scene_waypoints(seed: int = 0, N: int = 16384, T: int = 40):
+    """See the module docstring (Experiment 4)."""
+    obs = np.array([[1e4, 1e4, 0.0, 0.0]])
+    return dict(preset=planner(32), state=np.zeros(6), goal=COURSE_WAYPOINTS[0].copy(), obs=obs, N=N, T=T,
+                seed=philox_seed(seed), t_index=0, waypoints=COURSE_WAYPOINTS.copy())

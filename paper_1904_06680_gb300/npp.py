@@ -84,7 +84,7 @@ EXPORTS = ("npp_create", "npp_destroy", "npp_last_error", "npp_n_theta", "npp_pl
            "npp_proposal_set_params", "npp_proposal_get_params", "npp_proposal_get_grads",
            "npp_proposal_encode", "npp_proposal_forward", "npp_proposal_train_step",
            "npp_plan_step_proposal", "npp_gemm_bf16", "npp_gemm_status", "npp_plan_tshc",
-           "npp_loop_create_mission", "npp_loop_points", "npp_measure_fma_peak")
+           "npp_loop_create_mission", "npp_loop_points", "npp_measure_fma_peak", "npp_set_loop_restarts")
 
 _lib = None
 
@@ -118,6 +118,7 @@ def lib():
         L.npp_loop_create.argtypes = [P, C.POINTER(npp_state), P, I32, P, P, I32, I32, I32, U64, I32,
                                       C.POINTER(P)]
         L.npp_loop_run.argtypes = [P, I32, P]
+        L.npp_set_loop_restarts.argtypes = [P, I32, C.c_float]
         L.npp_loop_read.argtypes = [P, C.POINTER(npp_loop_state)]
         L.npp_loop_log.argtypes = [P, P, I32, C.POINTER(I32)]
         L.npp_loop_destroy.argtypes = [P]
@@ -410,6 +411,12 @@ def npp_loop_create_mission(h, state, ref, field, window, hide_outside, eps, obs
                                          rp.shape[0], C.byref(m), ep.ctypes.data_as(C.c_void_p), _ptr(obs),
                                          int(M), int(N), int(T), int(seed), int(max_log), C.byref(L)), h)
     return L
+
+
+def npp_set_loop_restarts(h, n_restarts: int, sigma_pert: float = 0.0):
+    """Hill-climb rounds per sampling time of loops created afterwards on h
+    (1: the plan step alone)."""
+    return _check(lib().npp_set_loop_restarts(h, int(n_restarts), float(sigma_pert)), h)
 
 
 def npp_loop_points(L, M):

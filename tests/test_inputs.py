@@ -72,3 +72,19 @@ def test_mission_scenes_generate_with_spaced_cars():
         # centres sit 2.2 m off the centre line: along x they move by <= 2.2 sin(0.41) each
         assert np.all(np.diff(xs) >= 18.0 - 2 * 2.2 * 0.4), (seed, xs)
     assert time.perf_counter() - t0 < 5.0
+
+
+def test_paper_experiment_scenes():
+    """Experiment 1 (turn-around) and 4 (four waypoints) as the paper sets
+    them up (Sect. V): start at rest at the origin, no obstacle points (one
+    point parked 10 km away), goals at rest."""
+    import math
+    e1 = inputs.scene_turnaround(3)
+    assert np.array_equal(e1["state"], np.zeros(6))
+    assert np.allclose(e1["waypoints"], [[0.0, 0.0, math.pi, 0.0]])
+    assert e1["obs"].shape == (1, 4) and np.min(np.hypot(e1["obs"][:, 0], e1["obs"][:, 1])) > 1e3
+    assert e1["preset"]["widths"] == (8, 16, 16, 2) and e1["preset"]["lf"] == inputs.PAPER["lf"]
+    e4 = inputs.scene_waypoints(3)
+    assert np.array_equal(e4["state"], np.zeros(6)) and e4["waypoints"].shape == (4, 4)
+    assert np.all(e4["waypoints"][:, 3] == 0.0)
+    assert e1["seed"] != inputs.scene_turnaround(4)["seed"]

@@ -466,7 +466,7 @@ def run_npp(args):
     # default launch shapes; the last template argument is the variant flag
     # (off: no speed limits, features in the EV frame at t)
     var = int(bool(p.get("v_limits", 0) or p.get("feature_frame", 0)))
-    shape = {16: "<16,8,4,4,%d>", 32: "<32,16,4,4,%d>", 64: "<64,32,1,10,%d>"}[W] % var
+    shape = {16: "<16,8,4,4,%d>", 32: "<32,16,4,4,%d>", 64: "<64,32,1,16,%d,8>"}[W] % var
     fma_all = float(N) * T * K * (W * W + 10 * W)
     if fused:
         # [0] grid build, [1] the fused trajectory-and-check kernel

@@ -676,7 +676,7 @@ npp_status npp_set_option(npp_handle* h, const char* name, int32_t value)
         return NPP_OK;
     }
     if (std::strcmp(name, "traj_variant") == 0) {
-        if (value < 0 || value > 3) return fail(h, NPP_INVALID_ARG, "traj_variant is 0..3");
+        if (value < 0 || value > 4) return fail(h, NPP_INVALID_ARG, "traj_variant is 0..4");
         h->traj_variant = value;
         return NPP_OK;
     }

@@ -342,6 +342,7 @@ __global__ void __launch_bounds__(NW * 32) batch_traj_kernel(const BatchArgs b, 
         job.prop = Proposal{ nullptr, nullptr, 0, 1u };
         job.bins = nullptr;
         job.stage = stage_all + tid;
+        job.w2s = nullptr;
         job.N = s.N;
         job.T = s.T;
         job.traj = nullptr;
@@ -563,6 +564,7 @@ __device__ void batch_reroll(const BatchArgs& b, const SceneDev& s, int idx, flo
     job.prop = Proposal{ nullptr, nullptr, 0, 1u };
     job.bins = nullptr;
     job.stage = nullptr;
+    job.w2s = nullptr;
     job.N = s.N;
     job.T = s.T;
     job.traj = b.trajectory ? reinterpret_cast<float4*>(b.trajectory) + s.traj_off : nullptr;

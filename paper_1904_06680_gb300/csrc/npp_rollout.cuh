@@ -91,16 +91,37 @@ __device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsig
 }
 
 // The weights of one lane: rows of W1 and W2 as packed pairs of adjacent
-// inputs (2k, 2k + 1), the operands of the FP32x2 FMAs of the step.
-template <int W, int G>
+// inputs (2k, 2k + 1), the operands of the FP32x2 FMAs of the step.  With
+// KSQ > 0 the last KSQ input quads of each W2 row live in shared memory
+// instead of registers (fewer registers per thread, more warps per SM):
+// unit j's quad QR + q of this lane at w2s[(j KSQ + q) G] as two packed
+// pairs, lanes of a group adjacent (conflict-free 16-byte loads).
+template <int W, int G, int KSQ = 0>
 struct LaneNet {
     using S = Shape<W, G>;
     static constexpr int U = S::U;
+    static constexpr int QR = W / 4 - KSQ;        // W2 input quads per unit in registers
+    static_assert(KSQ >= 0 && KSQ < W / 4, "some quads in registers");
     unsigned long long w1p[U][NIN / 2];
     float b1[U];
-    unsigned long long w2p[U][W / 2];
+    unsigned long long w2p[U][2 * QR];
     float b2[U];
     float w3[2][U], b3[2];
+    ulonglong2* w2s;                              // this lane's slot of the shared part (KSQ > 0)
+
+    __device__ __forceinline__ void put_w2(int j, int qi, float4 q) {
+        if (qi < QR) {
+            w2p[j][2 * qi] = f2_pack(q.x, q.y);
+            w2p[j][2 * qi + 1] = f2_pack(q.z, q.w);
+        } else {
+            w2s[(j * KSQ + (qi - QR)) * G] = make_ulonglong2(f2_pack(q.x, q.y), f2_pack(q.z, q.w));
+        }
+    }
+    // the packed pairs (4 qi, 4 qi + 1) and (4 qi + 2, 4 qi + 3) of unit j
+    __device__ __forceinline__ ulonglong2 get_w2(int j, int qi) const {
+        if (qi < QR) return make_ulonglong2(w2p[j][2 * qi], w2p[j][2 * qi + 1]);
+        return w2s[(j * KSQ + (qi - QR)) * G];
+    }
 
     // lane gl of the group holds hidden units gl*U .. gl*U + U - 1
     __device__ __forceinline__ void load(const ThetaSrc& src, int gl) {
@@ -114,11 +135,7 @@ struct LaneNet {
                 w1p[j][i / 2 + 1] = f2_pack(q.z, q.w);
             }
 #pragma unroll
-            for (int i = 0; i < W; i += 4) {
-                const float4 q = src.quad(S::OFF_W2 + u * W + i);
-                w2p[j][i / 2] = f2_pack(q.x, q.y);
-                w2p[j][i / 2 + 1] = f2_pack(q.z, q.w);
-            }
+            for (int i = 0; i < W; i += 4) put_w2(j, i / 4, src.quad(S::OFF_W2 + u * W + i));
         }
 #pragma unroll
         for (int j = 0; j < U; j += 2) {
@@ -147,6 +164,7 @@ struct LaneNet {
 
     template <int TH>
     __device__ __forceinline__ void load_staged(const ThetaSrc& src, int gl, float* st) {
+        static_assert(KSQ == 0, "staged loading keeps every weight in registers");
 #pragma unroll 1
         for (int it = 0; it < NQUAD; ++it) {
             const int j = it / QPU, q = it - j * QPU;
@@ -404,6 +422,7 @@ struct TrajJob {
     float* jfree;
     int* vfirst;                  // first speed-violating step per sample (speed limits on), or null
     const BinView* bins;          // fused check (traj_sample_fused)
+    ulonglong2* w2s;              // this lane's slot of the shared W2 quads (LaneNet KSQ > 0), or null
     float* stage;                 // this thread's slot 0 of a staging area (stride stage_th), or null
 };
 
@@ -433,9 +452,10 @@ __device__ __forceinline__ GoalEV goal_ev(const StepIn& si)
 }
 
 // The network of sample n (valid: n < N) loaded into the lanes of its group.
-template <int W, int G, int STAGE_TH>
-__device__ __forceinline__ void load_net(LaneNet<W, G>& net, const TrajJob& job, int n, bool valid, int gl)
+template <int W, int G, int STAGE_TH, int KSQ = 0>
+__device__ __forceinline__ void load_net(LaneNet<W, G, KSQ>& net, const TrajJob& job, int n, bool valid, int gl)
 {
+    net.w2s = job.w2s;
     ThetaSrc src;
     src.key = job.key;
     src.prop = job.prop;
@@ -453,8 +473,8 @@ __device__ __forceinline__ void load_net(LaneNet<W, G>& net, const TrajJob& job,
 // exchange row), rate-limited controls, effort, Euler step of the kinematic
 // bicycle on the old state (Sect. IV).  Updates the state, the last
 // controls, the effort E and rem = T - h; returns the applied controls.
-template <int W, int G, bool VAR>
-__device__ __forceinline__ float2 control_step(const DevCfg& c, const LaneNet<W, G>& net, const GoalEV& g,
+template <int W, int G, bool VAR, int KSQ = 0>
+__device__ __forceinline__ float2 control_step(const DevCfg& c, const LaneNet<W, G, KSQ>& net, const GoalEV& g,
                                                float invT, int gl, float* hrow, float sp, float cp, float& x,
                                                float& y, float& ph, float& v, float& ap0, float& ap1, float& E,
                                                float& rem)
@@ -509,8 +529,9 @@ __device__ __forceinline__ float2 control_step(const DevCfg& c, const LaneNet<W,
         const unsigned long long h01 = f2_pack(hv.x, hv.y), h23 = f2_pack(hv.z, hv.w);
 #pragma unroll
         for (int j = 0; j < U; ++j) {
-            p01[j] = f2_fma(net.w2p[j][2 * i], h01, p01[j]);
-            p23[j] = f2_fma(net.w2p[j][2 * i + 1], h23, p23[j]);
+            const ulonglong2 w = net.get_w2(j, i);
+            p01[j] = f2_fma(w.x, h01, p01[j]);
+            p23[j] = f2_fma(w.y, h23, p23[j]);
         }
     }
     __syncwarp();
@@ -573,13 +594,13 @@ __device__ __forceinline__ float final_cost(const DevCfg& c, const GoalEV& g, fl
 // of c (body-frame goal offsets, speed limits) are honoured; without it the
 // kernel is the plain rollout, and the launchers pick VAR whenever c turns
 // a variant on.
-template <int W, int G, int STAGE_TH = 0, bool VAR = false>
+template <int W, int G, int STAGE_TH = 0, bool VAR = false, int KSQ = 0>
 __device__ __forceinline__ void traj_sample(const DevCfg& c, const TrajJob& job, int n, bool valid, int gl,
                                             float* hrow)
 {
     const GoalEV g = goal_ev(job.si);
-    LaneNet<W, G> net;
-    load_net<W, G, STAGE_TH>(net, job, n, valid, gl);
+    LaneNet<W, G, KSQ> net;
+    load_net<W, G, STAGE_TH, KSQ>(net, job, n, valid, gl);
 
     float x = 0.f, y = 0.f, ph = 0.f, v = job.si.v0, ap0 = job.si.ap0, ap1 = job.si.ap1, E = 0.f;
     const int T = job.T, N = job.N;
@@ -607,8 +628,8 @@ __device__ __forceinline__ void traj_sample(const DevCfg& c, const TrajJob& job,
                 job.coefB[ci] = B;
             }
         }
-        const float2 a = control_step<W, G, VAR>(c, net, g, invT, gl, hrow, sp, cp, x, y, ph, v, ap0, ap1, E,
-                                                 rem);
+        const float2 a = control_step<W, G, VAR, KSQ>(c, net, g, invT, gl, hrow, sp, cp, x, y, ph, v, ap0, ap1,
+                                                      E, rem);
         if (writer && job.ctrl) job.ctrl[h * job.rec_stride + rec] = a;
     }
     if constexpr (VAR) {
@@ -844,12 +865,14 @@ __device__ __forceinline__ FusedOut traj_sample_fused(const DevCfg& c, const Tra
     return out;
 }
 
-template <int W, int G, int NW, int MINB = 1, bool VAR = false>
+template <int W, int G, int NW, int MINB = 1, bool VAR = false, int KSQ = 0>
 __global__ void __launch_bounds__(NW * 32, MINB) traj_kernel(const RolloutArgs a)
 {
     constexpr int B = TrajKernel<W, G, NW>::B;
     __shared__ __align__(16) float hx_all[B * W];
-    extern __shared__ float stage_all[];        // [LaneNet::SLOTS][NW * 32] when W == 32
+    // [LaneNet::SLOTS][NW * 32] floats of parameter staging when W == 32;
+    // with KSQ > 0 the shared W2 quads, [group][U][KSQ][G] of 16 bytes
+    extern __shared__ __align__(16) float stage_all[];
     const int tid = threadIdx.x;
     const int b = tid / G, gl = tid % G;
     const int n = blockIdx.x * B + b;
@@ -873,10 +896,13 @@ __global__ void __launch_bounds__(NW * 32, MINB) traj_kernel(const RolloutArgs a
     job.vfirst = a.c.vlim ? a.vfirst : nullptr;
     job.bins = nullptr;
     job.stage = stage_all + tid;
+    job.w2s = nullptr;
+    if constexpr (KSQ > 0)
+        job.w2s = reinterpret_cast<ulonglong2*>(stage_all) + (size_t)b * (Shape<W, G>::U * KSQ * G) + gl;
     // staged parameter generation pays at W = 32 (measured on GB300: 11 %
     // faster at T = 40); at W = 16 and 64 the direct load is faster
-    constexpr int STAGE_TH = W == 32 ? NW * 32 : 0;
-    traj_sample<W, G, STAGE_TH, VAR>(a.c, job, n, n < a.N, gl, hx_all + b * W);
+    constexpr int STAGE_TH = (W == 32 && KSQ == 0) ? NW * 32 : 0;
+    traj_sample<W, G, STAGE_TH, VAR, KSQ>(a.c, job, n, n < a.N, gl, hx_all + b * W);
 }
 
 // Trajectories with the binned check fused in: per sample its first
@@ -912,6 +938,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) fused_kernel(const RolloutArgs 
     job.vfirst = nullptr;
     job.bins = &a.bins;
     job.stage = nullptr;
+    job.w2s = nullptr;
     const bool valid = n < a.N;
     const FusedOut r = traj_sample_fused<W, G, KMAX, VAR>(a.c, job, n, valid, gl, hx_all + b * W, slots + b);
     unsigned long long key = ~0ull;
@@ -985,6 +1012,7 @@ __global__ void __launch_bounds__(32) reroll_epilogue_kernel(const RolloutArgs a
     job.vfirst = nullptr;
     job.bins = nullptr;
     job.stage = nullptr;
+    job.w2s = nullptr;
     if (e.trajectory || e.controls)
         traj_sample<W, G, 0, VAR>(a.c, job, idx, true, lane % G, hrows + (lane / G) * W);
     __syncwarp();
@@ -1541,15 +1569,16 @@ inline cudaError_t ensure_smem(KernelFn fn, int smem)
 // Whether a configuration turns on a rollout variant (VAR kernels).
 __host__ __device__ inline bool uses_variants(const DevCfg& c) { return c.body_frame != 0 || c.vlim != 0; }
 
-template <int W, int G, int NW, int MINB = 1, bool VAR = false>
+template <int W, int G, int NW, int MINB = 1, bool VAR = false, int KSQ = 0>
 cudaError_t launch_traj(const RolloutArgs& a, cudaStream_t stream)
 {
     using K = TrajKernel<W, G, NW>;
     const int grid = (a.N + K::B - 1) / K::B;
-    const int smem = W == 32 ? LaneNet<W, G>::SLOTS * K::THREADS * (int)sizeof(float) : 0;
-    cudaError_t e = ensure_smem(traj_kernel<W, G, NW, MINB, VAR>, smem);
+    const int smem = KSQ > 0 ? K::THREADS * Shape<W, G>::U * KSQ * 16
+                   : W == 32 ? LaneNet<W, G>::SLOTS * K::THREADS * (int)sizeof(float) : 0;
+    cudaError_t e = ensure_smem(traj_kernel<W, G, NW, MINB, VAR, KSQ>, smem);
     if (e != cudaSuccess) return e;
-    traj_kernel<W, G, NW, MINB, VAR><<<grid, K::THREADS, smem, stream>>>(a);
+    traj_kernel<W, G, NW, MINB, VAR, KSQ><<<grid, K::THREADS, smem, stream>>>(a);
     return cudaGetLastError();
 }
 

@@ -278,6 +278,33 @@ def test_collide_variants_identical():
     pl.close()
 
 
+def test_trajectory_launch_shapes_identical_at_width_64():
+    """Every launch shape of the 8-64-64-2 trajectory kernel -- the default
+    one keeps half of each lane's layer-2 weights in shared memory, shape 4
+    keeps them all in registers -- gives the same bits: per-sample states,
+    controls, costs, first collisions and the winner."""
+    import torch
+    from paper_1904_06680_gb300 import npp
+    sc = inputs.tiny_scene(33, N=700, T=30, M=250, width=64, box=30.0)
+    N, T = sc["N"], sc["T"]
+    obs = torch.tensor(sc["obs"], dtype=torch.float32, device="cuda")
+    pl = npp.Planner(sc["preset"], max_N=N, max_T=T, max_M=obs.shape[0], record_samples=True)
+    res = []
+    for tv in range(5):
+        npp.npp_set_option(pl.h, "traj_variant", tv)
+        pl.plan(sc["state"], sc["goal"], obs, N, T, sc["seed"], sc["t_index"])
+        torch.cuda.synchronize()
+        res.append(pl.result(N, T))
+    for r in res[1:]:
+        for k in ("sample_traj", "sample_ctrl", "costs", "first_hit", "params", "trajectory"):
+            assert np.array_equal(r[k], res[0][k]), k
+        assert r["best_idx"] == res[0]["best_idx"]
+    assert 0 < np.sum(res[0]["first_hit"] >= 0) < N
+    with pytest.raises(npp.NppError):
+        npp.npp_set_option(pl.h, "traj_variant", 5)
+    pl.close()
+
+
 def test_steering_rate_limit_on_every_rollout():
     """Fig. 8: the applied normalised steering moves by at most
     delta_rate_max Ts / delta_max per step (and stays in [-1, 1]) in every

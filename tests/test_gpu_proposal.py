@@ -259,3 +259,21 @@ def test_learned_proposal_gains_over_plain():
     assert res["mixed"] < res["plain"] - 0.1, res
     assert res["proposal_won"] > 0.55, res
     net.close()
+
+
+def test_proposal_reaches_plain_cost_at_a_quarter_of_the_samples():
+    """The learned proposal's target: after the training recipe (30 rounds of
+    8192 course-like scenes at N = 2048, expert iteration), on 256 held-out
+    scenes the mixed plan step (half of its samples from the proposal, half
+    isotropic, every sample judged by the exact rollout cost, so the plain
+    sampler's samples win whenever the proposal's are worse) with N/4 = 512
+    samples has a lower mean cost than the plain plan step with N = 2048
+    samples, and so does N/4 = 2048 against N = 8192."""
+    from paper_1904_06680_gb300 import proposal
+    net, stats = proposal.train_proposal(rounds=30, S=8192, N=2048, epochs=4)
+    res = proposal.evaluate(net, 2, S=256, Ns=(2048, 8192), prop_frac=0.5)
+    net.close()
+    for N in (2048, 8192):
+        r = res[N]
+        assert r["n_scenes"] > 200, r
+        assert r["mixed_quarter"] <= r["plain"] - 0.02, (N, r)

@@ -366,13 +366,16 @@ def run_npp(args):
         L = npp.npp_loop_create(pl.h, sc["state"], sc["waypoints"], inputs.EPS, obs0_dev, M, N, T,
                                 sc["seed"], max_log=max(nsteps, 1))
         out = dict(step_ms=[], collide_ms=[], traj_ms=[], fma_c=0.0, fma_t=0.0, checks=0.0,
-                   free=[], best_cost=[])
+                   free=[], best_cost=[], cand_tests=0.0, states=0.0)
         for t in range(nsteps):
             flush.zero_()
             torch.cuda.synchronize()
             npp.npp_loop_run(L, 1)
             tm = npp.npp_loop_last_timing(L)
             if record:
+                ct, cs = npp.npp_last_counts(pl.h)
+                out["cand_tests"] += ct
+                out["states"] += cs
                 _, fh = npp.npp_loop_samples(L, N)
                 out["step_ms"].append(tm["total"])
                 out["collide_ms"].append(tm["collide"])
@@ -488,6 +491,21 @@ def run_npp(args):
         tname = "traj_kernel" + shape
         cname = "bin_build_kernel + " + ("collide_poly_kernel" if poly else "collide_binned_kernel")
         fps_t = res["fma_t"] / (traj_ms / 1e3)
+        coll = {"ms_per_step": collide_ms / K}
+        if not poly and res["states"] > 0:
+            # the check's algorithmic bytes: per state checked its stored
+            # state (16 B) and the ten cell-run bounds of its query (40 B),
+            # per candidate test one point (8 B), per sample its free cost
+            # read and cost / first-hit written (12 B)
+            nbytes = res["states"] * 56.0 + res["cand_tests"] * 8.0 + 12.0 * N * K
+            coll.update(candidate_tests_per_s=res["cand_tests"] / (collide_ms / 1e3),
+                        candidate_tests_per_state=res["cand_tests"] / res["states"],
+                        states_per_s=res["states"] / (collide_ms / 1e3),
+                        bytes_per_step=nbytes / K, achieved_gbs=nbytes / (collide_ms / 1e3) / 1e9,
+                        traffic=profiled_traffic("collide_binned_kernel"),
+                        bytes_note="algorithmic: 56 B per state checked (state + ten cell-run bounds), "
+                                   "8 B per candidate test, 12 B per sample; traffic = DRAM bytes per "
+                                   "launch from profiles/traffic.json")
         roofline = {"bound": "alu", "kernel": tname, "achieved": fps_t / 1e12, "peak": peak / 1e12,
                     "unit": "T FP32-FMA/s", "frac": fps_t / peak, "traffic": profiled_traffic(tname),
                     "peak_basis": peak_basis, "peak_measured": fma_measured,
@@ -496,15 +514,15 @@ def run_npp(args):
                     "all_steps_achieved": fma_all / (traj_ms / 1e3) / 1e12,
                     "all_steps_frac": fma_all / (traj_ms / 1e3) / peak,
                     "kernel_ms_per_step": traj_ms / K,
-                    "other": {cname: {"ms_per_step": collide_ms / K}},
+                    "other": {cname: coll},
                     "dominant": tname if traj_ms >= collide_ms else cname}
     else:
         tname = "traj_kernel" + shape
         cname = {0: "collide_block_kernel<16,128,1>", 1: "collide_block_kernel<8,64,2>",
-                 2: "collide_warp_kernel<8,2>", 3: "collide_slice_kernel<4,4>",
-                 4: "collide_slice_kernel<2,8>"}.get(
-            cv, "collide_slice_kernel<4,4>" if N <= 8192 else
-            "collide_slice_kernel<2,8>" if N <= 32768 else "collide_warp_kernel<8,2>")
+                 2: "collide_warp_kernel<8,2>", 3: "collide_slice_kernel<4,2,0,2>",
+                 4: "collide_slice_kernel<2,2,0,4>"}.get(
+            cv, "collide_slice_kernel<4,2,0,2>" if N <= 8192 else
+            "collide_slice_kernel<2,2,0,4>" if N <= 32768 else "collide_warp_kernel<8,2>")
         fps_c = res["fma_c"] / (collide_ms / 1e3)
         fps_t = res["fma_t"] / (traj_ms / 1e3)
         roofline = {"bound": "alu", "kernel": cname,

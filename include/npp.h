@@ -486,6 +486,13 @@ npp_status npp_set_option(npp_handle* h, const char* name, int32_t value);
 npp_status npp_set_timing(npp_handle* h, int32_t enable);
 npp_status npp_last_timing(npp_handle* h, float* stage_ms, int32_t n);
 
+/* Work counters of the last timed plan step's binned collision check (also
+ * of the first round of a closed loop's sampling time created with timing
+ * on): [0] candidate point tests (each one evaluation of the rectangle's
+ * inequalities), [1] states checked.  Zero when that step used another
+ * collision check.  Synchronises the device; needs timing enabled. */
+npp_status npp_last_counts(npp_handle* h, uint64_t* counts, int32_t n);
+
 #ifdef __cplusplus
 }
 #endif

@@ -230,7 +230,13 @@ npp_status run_rollout(npp_handle* h, RolloutArgs& a, cudaStream_t s, bool allow
             CUDA_TRY(h, launch_traj(h, a, s));
             if (h->timing) CUDA_TRY(h, record_event(h->ev[1], s));
             CUDA_TRY(h, cudaStreamWaitEvent(s, h->join_ev, 0));
+            if (h->timing) {
+                // measurement counters of the check (candidate tests, states)
+                CUDA_TRY(h, cudaMemsetAsync(h->d_counts, 0, 2 * sizeof(unsigned long long), s));
+                a.counts = h->d_counts;
+            }
             CUDA_TRY(h, launch_collide_binned(a, s));
+            a.counts = nullptr;
             if (h->timing) CUDA_TRY(h, record_event(h->ev[2], s));
             return NPP_OK;
         }
@@ -384,6 +390,7 @@ npp_status npp_create(npp_handle** out, const npp_config* cfg, int32_t device)
     A((void**)&h->d_jfree, (size_t)cfg->max_N * sizeof(float));
     if (cfg->v_limits) A((void**)&h->d_vfirst, (size_t)cfg->max_N * sizeof(int));
     A((void**)&h->d_work, 64);
+    A((void**)&h->d_counts, 64);
     A(&h->d_bins, binned_workspace_bytes(cfg->max_T, cfg->max_M));
     if (cfg->max_M > max_points) {
         A((void**)&h->d_pXY, (size_t)(cfg->max_M / 2 + 1) * sizeof(float4));
@@ -417,7 +424,7 @@ npp_status npp_destroy(npp_handle* h)
     if (!h) return NPP_OK;
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
-    void* ptrs[] = { h->d_key, h->d_traj, h->d_ctrl, h->d_jfree, h->d_vfirst, h->d_fp, h->d_work,
+    void* ptrs[] = { h->d_key, h->d_traj, h->d_ctrl, h->d_jfree, h->d_vfirst, h->d_fp, h->d_work, h->d_counts,
                      h->d_pXY, h->d_pV, h->d_bins,
                      h->d_obs, h->d_warm, h->d_sigma, h->d_best, h->d_params, h->d_controls, h->d_trajectory,
                      h->d_costs, h->d_fh };
@@ -687,6 +694,19 @@ npp_status npp_set_timing(npp_handle* h, int32_t enable)
 {
     if (!h) return fail(nullptr, NPP_INVALID_ARG, "handle is NULL");
     h->timing = enable != 0;
+    return NPP_OK;
+}
+
+npp_status npp_last_counts(npp_handle* h, uint64_t* counts, int32_t n)
+{
+    if (!h) return fail(nullptr, NPP_INVALID_ARG, "handle is NULL");
+    if (!h->timing) return fail(h, NPP_INVALID_ARG, "timing is not enabled on this handle");
+    if (!counts || n < 1) return fail(h, NPP_INVALID_ARG, "counts must hold n >= 1 values");
+    CUDA_TRY(h, cudaSetDevice(h->device));
+    CUDA_TRY(h, cudaDeviceSynchronize());
+    unsigned long long c[2] = { 0ull, 0ull };
+    CUDA_TRY(h, cudaMemcpy(c, h->d_counts, sizeof c, cudaMemcpyDeviceToHost));
+    for (int i = 0; i < n && i < 2; ++i) counts[i] = c[i];
     return NPP_OK;
 }
 

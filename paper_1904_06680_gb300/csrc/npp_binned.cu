@@ -40,49 +40,85 @@ __global__ void __launch_bounds__(BIN_THREADS) bin_build_kernel(const RolloutArg
                                  cell_start + (size_t)h * BIN_CS_STRIDE, binned + (size_t)h * a.M, cnt, run_tot);
 }
 
-// one warp per sample over the stored states (each step's inequality rows
-// recomputed from the state), h in order: the candidates of a step are the
-// points of at most five cell
-// rows, each row's cells contiguous in the sorted array; the lanes stride
-// through them (coalesced loads) and a ballot ends the sample at its first
-// colliding step
+// One warp per sample over its stored states (each step's inequality rows
+// recomputed from the state).  The warp checks BIN_SB consecutive steps at
+// once, an 8-lane group per step: a step's candidates are the points of at
+// most five cell rows, each row's cells contiguous in the sorted array; the
+// group's lanes stride through them, each lane first issuing the loads of up
+// to BIN_R candidates and then testing them (the rest, rarely any, one by
+// one).  The chunk's first colliding step, if any, ends the sample.  Steps
+// are independent given the stored states, so checking a few past the first
+// collision changes nothing; it replaces one chain of two dependent loads
+// per step (cell bounds, then candidates) by one per chunk.
 constexpr int BINNED_WARPS = 8;
+constexpr int BIN_SB = 4;                  // steps per chunk
+constexpr int BIN_GS = 32 / BIN_SB;        // lanes per step
+constexpr int BIN_R = 8;                   // candidates loaded ahead per lane (64 per step)
+
+__device__ __forceinline__ bool inside_rows(const float4& A, const float2& B, float2 p)
+{
+    const float xi = fmaf(A.x, p.x, fmaf(A.y, p.y, A.z));
+    const float et = fmaf(A.w, p.x, fmaf(B.x, p.y, B.y));
+    return !(((__float_as_uint(xi) | __float_as_uint(et)) >> 30) & 1u);
+}
 
 __global__ void __launch_bounds__(BINNED_WARPS * 32) collide_binned_kernel(const RolloutArgs a)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gid = lane / BIN_GS, gl = lane % BIN_GS;
     const BinView& g = a.bins;
     const int T = a.T, N = a.N, M = a.M;
     const int n = blockIdx.x * BINNED_WARPS + warp;
     unsigned long long key = ~0ull;
+    unsigned ntest = 0, nstate = 0;          // this lane's candidate tests and states (measurement)
     if (n < N) {
         int fh = -1;
-        // the next step's state is loaded while the current step is checked
-        float4 nz = a.traj[n];
-        for (int h = 0; h <= T; ++h) {
+        for (int h0 = 0; h0 <= T; h0 += BIN_SB) {
+            const int h = h0 + gid;
+            const bool ok = h <= T;
             // the rectangle lies in the disk of radius reach around the
             // reference point (reach covers the centre offset)
-            const float4 z = nz;
-            if (h < T) nz = a.traj[(size_t)(h + 1) * N + n];
+            const float4 z = ok ? a.traj[(size_t)h * N + n] : make_float4(0.f, 0.f, 0.f, 0.f);
             float4 ca;
             float2 cb;
             rows_of_state(a.c, z, ca, cb);
-            const CandRows cr = cand_rows(g.cell_start + (size_t)h * BIN_CS_STRIDE, g, z.x, z.y, g.reach);
-            const float2* pts = g.pts + (size_t)h * M;
+            CandRows cr = {};
+            if (ok) cr = cand_rows(g.cell_start + (size_t)h * BIN_CS_STRIDE, g, z.x, z.y, g.reach);
+            const float2* pts = g.pts + (size_t)(ok ? h : 0) * M;
             const int total = cr.total;
-            bool hit = false;
-            for (int base = 0; base < total && !hit; base += 32) {
-                const int k = base + lane;
-                bool inside = false;
-                if (k < total) {
-                    const float2 p = pts[cr.index(k)];
-                    const float xi = fmaf(ca.x, p.x, fmaf(ca.y, p.y, ca.z));
-                    const float et = fmaf(ca.w, p.x, fmaf(cb.x, p.y, cb.y));
-                    inside = !(((__float_as_uint(xi) | __float_as_uint(et)) >> 30) & 1u);
-                }
-                hit = __any_sync(FULL, inside);
+            float2 pr[BIN_R];
+#pragma unroll
+            for (int r = 0; r < BIN_R; ++r) {
+                const int k = gl + r * BIN_GS;
+                pr[r] = k < total ? pts[cr.index(k)] : make_float2(0.f, 0.f);
             }
-            if (hit) { fh = h; break; }
+            bool inside = false;
+            nstate += (ok && gl == 0) ? 1u : 0u;
+#pragma unroll
+            for (int r = 0; r < BIN_R; ++r)
+                if (gl + r * BIN_GS < total) {
+                    inside |= inside_rows(ca, cb, pr[r]);
+                    ++ntest;
+                }
+            constexpr int PRE = BIN_R * BIN_GS;
+            const int rest = total > PRE ? (total - PRE + BIN_GS - 1) / BIN_GS : 0;
+            const int maxr = __reduce_max_sync(FULL, rest);
+            for (int it = 0; it < maxr; ++it) {
+                const int k = PRE + it * BIN_GS + gl;
+                if (it < rest && k < total) {
+                    inside |= inside_rows(ca, cb, pts[cr.index(k)]);
+                    ++ntest;
+                }
+            }
+            const unsigned bal = __ballot_sync(FULL, inside);
+            unsigned steps_hit = 0;
+#pragma unroll
+            for (int s = 0; s < BIN_SB; ++s)
+                if ((bal >> (s * BIN_GS)) & ((1u << BIN_GS) - 1u)) steps_hit |= 1u << s;
+            if (steps_hit) {
+                fh = h0 + __ffs(steps_hit) - 1;
+                break;
+            }
         }
         if (lane == 0) {
             fh = discard_step(a.vfirst, n, fh);
@@ -95,6 +131,18 @@ __global__ void __launch_bounds__(BINNED_WARPS * 32) collide_binned_kernel(const
             }
             if (a.costs) a.costs[n] = J;
             if (a.first_hit) a.first_hit[n] = fh;
+        }
+    }
+    if (a.counts) {
+        unsigned long long t = ntest, s = nstate;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            t += __shfl_xor_sync(FULL, t, off);
+            s += __shfl_xor_sync(FULL, s, off);
+        }
+        if (lane == 0 && n < N) {
+            atomicAdd(a.counts, t);
+            atomicAdd(a.counts + 1, s);
         }
     }
     // each warp folds its key into the minimum on its own (no block barrier:

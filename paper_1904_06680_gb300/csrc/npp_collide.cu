@@ -1,7 +1,9 @@
 // Collision kernels with all obstacle points resident in shared memory.
 // Variants compute the same values: 0 block-balanced (16 warps, one block per
 // SM, items of up to 128 samples); 1 block-balanced with 8 warps and two
-// blocks per SM; 2 warp-owned items of 8 samples pulled from a queue.
+// blocks per SM; 2 warp-owned items of 8 samples pulled from a queue; 3 / 4
+// items of 8 samples on 4 / 2 point slices, two / four items per 8-warp
+// block sharing one staged copy of the points (two blocks per SM).
 #include "npp_rollout.cuh"
 
 namespace npp {
@@ -14,8 +16,8 @@ cudaError_t launch_collide_resident(const RolloutArgs& a, cudaStream_t s, int va
     case 0: return launch_collide_block<16, 128, 1>(a, s);
     case 1: return launch_collide_block<8, 64, 2>(a, s);
     case 2: return launch_collide_warp<8, 2>(a, s);
-    case 3: return launch_collide_slice<4, 4>(a, s);
-    default: return launch_collide_slice<2, 8>(a, s);
+    case 3: return launch_collide_slice<4, 2, 2>(a, s);
+    default: return launch_collide_slice<2, 2, 4>(a, s);
     }
 }
 
@@ -25,8 +27,8 @@ int collide_resident_blocks_per_sm(int M, int variant)
     case 0: return collide_block_blocks_per_sm<16, 128, 1>(M);
     case 1: return collide_block_blocks_per_sm<8, 64, 2>(M);
     case 2: return collide_warp_blocks_per_sm<8, 2>(M);
-    case 3: return collide_slice_blocks_per_sm<4, 4>(M);
-    default: return collide_slice_blocks_per_sm<2, 8>(M);
+    case 3: return collide_slice_blocks_per_sm<4, 2, 2>(M);
+    default: return collide_slice_blocks_per_sm<2, 2, 4>(M);
     }
 }
 

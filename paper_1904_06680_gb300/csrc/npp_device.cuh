@@ -451,6 +451,8 @@ struct RolloutArgs {
     float4* pXY;                       // EV-frame point pairs in global memory (when the
     float4* pV;                        // points exceed shared memory), [ceil(M/2)]
     BinView bins;                      // per-step grids (binned and fused collision checks)
+    unsigned long long* counts;        // measurement counters of the binned check, or null:
+                                       // [0] candidate point tests, [1] states checked
     PolyView poly;                     // general footprint (polygon checks)
 };
 

@@ -58,6 +58,7 @@ struct npp_handle {
     cudaEvent_t fork_ev, join_ev;
     bool timing;
     cudaEvent_t ev[4];                   // start, after trajectories, after collisions, end
+    unsigned long long* d_counts;        // [2] binned-check counters of the last timed plan step
     std::string err;
 };
 

@@ -1460,36 +1460,53 @@ __global__ void __launch_bounds__(NW * 32, MINB) collide_warp_kernel(const Rollo
 // share, per sample, the earliest step at which any slice found a collision
 // (dead_at, shared-memory atomicMin) and stop checking a sample at steps at
 // or after it.  The item's first collision per sample is the minimum over
-// the slices, identical to checking all points at once.
-template <int S>
+// the slices, identical to checking all points at once.  A block holds P
+// such item groups of S warps: they share one staged copy of the points (so
+// the staging does not cap the warps per SM) and each group synchronises on
+// its own named barrier.
+template <int S, int P = 1>
 struct CollideSliceKernel {
-    static constexpr int THREADS = S * 32;
-    static constexpr int fixed_bytes() { return S * 8 * 24 + 8 * 4 + 16 + S * 8 + 64; }
+    static constexpr int THREADS = P * S * 32;
+    static constexpr int fixed_bytes() { return P * S * 8 * 24 + P * (8 * 4 + 16) + P * S * 8 + 64; }
     static int smem_bytes(int M) { return ((M + 1) / 2) * 32 + fixed_bytes(); }
 };
 
-template <int S, int MINB, bool GLOBAL_PTS = false>
-__global__ void __launch_bounds__(S * 32, MINB) collide_slice_kernel(const RolloutArgs a)
+// barrier of one item group (named barrier 1 + group, its S warps; the
+// whole block when the block is one group)
+template <int S, int P>
+__device__ __forceinline__ void group_sync(int grp)
 {
-    using K = CollideSliceKernel<S>;
+    if constexpr (P == 1) __syncthreads();
+    else asm volatile("bar.sync %0, %1;" ::"r"(1 + grp), "n"(S * 32) : "memory");
+}
+
+template <int S, int MINB, bool GLOBAL_PTS = false, int P = 1>
+__global__ void __launch_bounds__(P * S * 32, MINB) collide_slice_kernel(const RolloutArgs a)
+{
+    static_assert(P >= 1 && P <= 15, "one named barrier per item group");
+    using K = CollideSliceKernel<S, P>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int npairs = (a.M + 1) / 2;
     const int sp = GLOBAL_PTS ? 0 : npairs;                      // pairs held in shared memory
     const float4* XY = GLOBAL_PTS ? a.pXY : reinterpret_cast<float4*>(smem_raw);
     const float4* V = GLOBAL_PTS ? a.pV : reinterpret_cast<float4*>(smem_raw) + npairs;
-    float4* slotA = reinterpret_cast<float4*>(smem_raw) + 2 * sp;  // [S][8]
-    float2* slotB = reinterpret_cast<float2*>(slotA + S * 8);    // [S][8]
-    int* dead_at = reinterpret_cast<int*>(slotB + S * 8);        // [8]
-    int* qslot = dead_at + 8;
-    unsigned long long* red = reinterpret_cast<unsigned long long*>(qslot + 4);
+    float4* slotA = reinterpret_cast<float4*>(smem_raw) + 2 * sp;  // [P S][8]
+    float2* slotB = reinterpret_cast<float2*>(slotA + P * S * 8);  // [P S][8]
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
+    const int grp = warp / S, ws = warp % S, gtid = tid - grp * S * 32;
+    int* dead_at = reinterpret_cast<int*>(slotB + P * S * 8) + grp * 12;   // [P][8] (+ qslot, pad)
+    int* qslot = dead_at + 8;
+    unsigned long long* red = reinterpret_cast<unsigned long long*>(
+        reinterpret_cast<int*>(slotB + P * S * 8) + P * 12);             // [P S]
     const DevCfg& c = a.c;
     const int T = a.T, N = a.N;
-    if (!GLOBAL_PTS)
+    if (!GLOBAL_PTS) {
         stage_points<K::THREADS>(a, reinterpret_cast<float4*>(smem_raw), reinterpret_cast<float4*>(smem_raw) + npairs);
+        if constexpr (P > 1) __syncthreads();
+    }
     const int per = (npairs + S - 1) / S;
-    const int q0 = min(npairs, warp * per), q1 = min(npairs, q0 + per);
+    const int q0 = min(npairs, ws * per), q1 = min(npairs, q0 + per);
     const int nslice = q1 - q0;
     float4* sA = slotA + warp * 8;
     float2* sB = slotB + warp * 8;
@@ -1497,9 +1514,9 @@ __global__ void __launch_bounds__(S * 32, MINB) collide_slice_kernel(const Rollo
     unsigned long long best = ~0ull;
     const int nitems = (N + 7) / 8;
     for (;;) {
-        if (tid < 8) dead_at[tid] = T + 1;
-        if (tid == 0) *qslot = (int)atomicAdd(a.work, 1u);
-        __syncthreads();
+        if (gtid < 8) dead_at[gtid] = T + 1;
+        if (gtid == 0) *qslot = (int)atomicAdd(a.work, 1u);
+        group_sync<S, P>(grp);
         const int item = *qslot;
         if (item >= nitems) break;
         const int n0 = item * 8;
@@ -1523,8 +1540,8 @@ __global__ void __launch_bounds__(S * 32, MINB) collide_slice_kernel(const Rollo
             if ((hits >> lane) & 1u) atomicMin(&dead_at[lane], h);
             live &= ~hits;
         }
-        __syncthreads();
-        if (warp == 0 && mine) {
+        group_sync<S, P>(grp);
+        if (ws == 0 && mine) {
             const int d = dead_at[lane];
             const int fh = discard_step(a.vfirst, n, d <= T ? d : -1);
             float J = __int_as_float(0x7f800000);
@@ -1539,7 +1556,7 @@ __global__ void __launch_bounds__(S * 32, MINB) collide_slice_kernel(const Rollo
             if (a.first_hit) a.first_hit[n] = fh;
             best = key < best ? key : best;
         }
-        __syncthreads();
+        group_sync<S, P>(grp);
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -1550,7 +1567,7 @@ __global__ void __launch_bounds__(S * 32, MINB) collide_slice_kernel(const Rollo
     __syncthreads();
     if (tid == 0 && a.best_key) {
         unsigned long long k = red[0];
-        for (int w = 1; w < S; ++w) k = red[w] < k ? red[w] : k;
+        for (int w = 1; w < P * S; ++w) k = red[w] < k ? red[w] : k;
         atomicMin(a.best_key, k);
     }
 }
@@ -1683,26 +1700,26 @@ cudaError_t launch_collide_slice_global(const RolloutArgs& a, cudaStream_t strea
     return cudaGetLastError();
 }
 
-template <int S, int MINB>
+template <int S, int MINB, int P = 1>
 cudaError_t launch_collide_slice(const RolloutArgs& a, cudaStream_t stream)
 {
-    using K = CollideSliceKernel<S>;
+    using K = CollideSliceKernel<S, P>;
     const int smem = K::smem_bytes(a.M);
-    cudaError_t e = ensure_smem(collide_slice_kernel<S, MINB>, smem);
+    cudaError_t e = ensure_smem(collide_slice_kernel<S, MINB, false, P>, smem);
     if (e != cudaSuccess) return e;
-    const int grid = max(1, min((a.N + 7) / 8, a.grid_collide));
-    collide_slice_kernel<S, MINB><<<grid, K::THREADS, smem, stream>>>(a);
+    const int grid = max(1, min(((a.N + 7) / 8 + P - 1) / P, a.grid_collide));
+    collide_slice_kernel<S, MINB, false, P><<<grid, K::THREADS, smem, stream>>>(a);
     return cudaGetLastError();
 }
 
-template <int S, int MINB>
+template <int S, int MINB, int P = 1>
 int collide_slice_blocks_per_sm(int M)
 {
-    using K = CollideSliceKernel<S>;
+    using K = CollideSliceKernel<S, P>;
     int nb = 0;
     const int smem = K::smem_bytes(M);
-    if (ensure_smem(collide_slice_kernel<S, MINB>, smem) != cudaSuccess) return 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, collide_slice_kernel<S, MINB>, K::THREADS, smem);
+    if (ensure_smem(collide_slice_kernel<S, MINB, false, P>, smem) != cudaSuccess) return 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, collide_slice_kernel<S, MINB, false, P>, K::THREADS, smem);
     return nb > 0 ? nb : 1;
 }
 

@@ -84,7 +84,7 @@ EXPORTS = ("npp_create", "npp_destroy", "npp_last_error", "npp_n_theta", "npp_pl
            "npp_proposal_set_params", "npp_proposal_get_params", "npp_proposal_get_grads",
            "npp_proposal_encode", "npp_proposal_forward", "npp_proposal_train_step",
            "npp_plan_step_proposal", "npp_gemm_bf16", "npp_gemm_status", "npp_plan_tshc",
-           "npp_loop_create_mission", "npp_loop_points", "npp_measure_fma_peak", "npp_set_loop_restarts")
+           "npp_loop_create_mission", "npp_loop_points", "npp_measure_fma_peak", "npp_set_loop_restarts", "npp_last_counts")
 
 _lib = None
 
@@ -119,6 +119,7 @@ def lib():
                                       C.POINTER(P)]
         L.npp_loop_run.argtypes = [P, I32, P]
         L.npp_set_loop_restarts.argtypes = [P, I32, C.c_float]
+        L.npp_last_counts.argtypes = [P, C.POINTER(C.c_uint64), I32]
         L.npp_loop_read.argtypes = [P, C.POINTER(npp_loop_state)]
         L.npp_loop_log.argtypes = [P, P, I32, C.POINTER(I32)]
         L.npp_loop_destroy.argtypes = [P]
@@ -411,6 +412,14 @@ def npp_loop_create_mission(h, state, ref, field, window, hide_outside, eps, obs
                                          rp.shape[0], C.byref(m), ep.ctypes.data_as(C.c_void_p), _ptr(obs),
                                          int(M), int(N), int(T), int(seed), int(max_log), C.byref(L)), h)
     return L
+
+
+def npp_last_counts(h):
+    """(candidate point tests, states checked) of the last timed plan step's
+    binned collision check (synchronises)."""
+    c = (C.c_uint64 * 2)()
+    _check(lib().npp_last_counts(h, c, 2), h)
+    return int(c[0]), int(c[1])
 
 
 def npp_set_loop_restarts(h, n_restarts: int, sigma_pert: float = 0.0):

@@ -123,6 +123,75 @@ struct LaneNet {
         return w2s[(j * KSQ + (qi - QR)) * G];
     }
 
+    // With KSQ > 0: the same values as load(), generated by rolled loops
+    // (one copy of the sampler's code per loop instead of one per quad, so
+    // the kernel's code stays small) and staged through this lane's own
+    // shared W2 slots, which no other lane reads: first the W2 quads held in
+    // registers, then the W1 quads and the bias / W3 pairs, last the shared
+    // W2 quads straight into their slots.
+    __device__ __forceinline__ void load_rolled(const ThetaSrc& src, int gl) {
+        static_assert(KSQ > 0 && QR <= KSQ && U * (NIN / 4) + 2 * U + 1 <= U * KSQ, "staging fits the slots");
+        constexpr int QW1 = NIN / 4;
+#pragma unroll 1
+        for (int it = 0; it < U * QR; ++it) {
+            const int j = it / QR, qi = it - j * QR;
+            const float4 q = src.quad(S::OFF_W2 + (gl * U + j) * W + 4 * qi);
+            w2s[it * G] = make_ulonglong2(f2_pack(q.x, q.y), f2_pack(q.z, q.w));
+        }
+#pragma unroll
+        for (int j = 0; j < U; ++j)
+#pragma unroll
+            for (int qi = 0; qi < QR; ++qi) {
+                const ulonglong2 t = w2s[(j * QR + qi) * G];
+                w2p[j][2 * qi] = t.x;
+                w2p[j][2 * qi + 1] = t.y;
+            }
+#pragma unroll 1
+        for (int it = 0; it < U * QW1 + 2 * U + 1; ++it) {
+            if (it < U * QW1) {
+                const int j = it / QW1, qi = it - j * QW1;
+                const float4 q = src.quad((gl * U + j) * NIN + 4 * qi);
+                w2s[it * G] = make_ulonglong2(f2_pack(q.x, q.y), f2_pack(q.z, q.w));
+            } else {
+                const int pj = it - U * QW1;
+                int pidx = S::OFF_B3;
+                if (pj < 2 * U) {
+                    const int jj = gl * U + (pj >> 2) * 2, kind = pj & 3;
+                    pidx = kind == 0 ? S::OFF_B1 + jj : kind == 1 ? S::OFF_B2 + jj
+                         : kind == 2 ? S::OFF_W3 + jj : S::OFF_W3 + W + jj;
+                }
+                const float2 p = src.pair(pidx);
+                w2s[it * G] = make_ulonglong2(f2_pack(p.x, p.y), 0ull);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < U; ++j)
+#pragma unroll
+            for (int qi = 0; qi < QW1; ++qi) {
+                const ulonglong2 t = w2s[(j * QW1 + qi) * G];
+                w1p[j][2 * qi] = t.x;
+                w1p[j][2 * qi + 1] = t.y;
+            }
+#pragma unroll
+        for (int j = 0; j < U; j += 2) {
+            const int p0 = U * QW1 + (j >> 1) * 4;
+            const float2 pb1 = f2_unpack(w2s[(p0 + 0) * G].x), pb2 = f2_unpack(w2s[(p0 + 1) * G].x);
+            const float2 pw0 = f2_unpack(w2s[(p0 + 2) * G].x), pw1 = f2_unpack(w2s[(p0 + 3) * G].x);
+            b1[j] = pb1.x; b1[j + 1] = pb1.y;
+            b2[j] = pb2.x; b2[j + 1] = pb2.y;
+            w3[0][j] = pw0.x; w3[0][j + 1] = pw0.y;
+            w3[1][j] = pw1.x; w3[1][j + 1] = pw1.y;
+        }
+        const float2 pb3 = f2_unpack(w2s[(U * QW1 + 2 * U) * G].x);
+        b3[0] = pb3.x; b3[1] = pb3.y;
+#pragma unroll 1
+        for (int it = 0; it < U * KSQ; ++it) {
+            const int j = it / KSQ, qs = it - j * KSQ;
+            const float4 q = src.quad(S::OFF_W2 + (gl * U + j) * W + 4 * (QR + qs));
+            w2s[it * G] = make_ulonglong2(f2_pack(q.x, q.y), f2_pack(q.z, q.w));
+        }
+    }
+
     // lane gl of the group holds hidden units gl*U .. gl*U + U - 1
     __device__ __forceinline__ void load(const ThetaSrc& src, int gl) {
 #pragma unroll
@@ -464,6 +533,7 @@ __device__ __forceinline__ void load_net(LaneNet<W, G, KSQ>& net, const TrajJob&
     if (job.theta) src.mem = job.theta + (size_t)(valid ? n : 0) * Shape<W, G>::NT;
     else if (job.warm && n == 0 && job.si.warm_ok) src.mem = job.warm;
     if constexpr (STAGE_TH > 0) net.template load_staged<STAGE_TH>(src, gl, job.stage);
+    else if constexpr (KSQ > 0) net.load_rolled(src, gl);
     else net.load(src, gl);
 }
 

@@ -1,8 +1,8 @@
 // Trajectory kernel for the 8-64-64-2 network.  Launch shapes (all compute
-// identical values): 0 (default, fastest measured on GB300: 3.61 against
+// identical values): 0 (default, fastest measured on GB300: 3.29 against
 // 4.02 ms at N = 65536, T = 100) the last 8 of each lane's 16 W2 input quads
 // in shared memory (8 KB per warp), so that 127 registers without spills
-// and 16 one-warp blocks fit per SM; 1 four hidden units per lane, 2
+// and 16 one-warp blocks fit per SM, parameters generated by rolled loops; 1 four hidden units per lane, 2
 // eight-warp blocks, 3 <64, 32, 2, 5>, 4 every weight in registers
 // <64, 32, 1, 10> (168 registers with spills, 12 warps per SM);
 // template arguments <width, lanes per sample, warps per block, blocks per SM hint>.

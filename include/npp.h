@@ -468,10 +468,11 @@ npp_status npp_plan_step_noalloc(const npp_config* cfg, const npp_state* state,
  * measured slower on GB300 (the check's loads lengthen the per-step chain).
  * "traj_variant" 0..4: launch shape of the trajectory kernel -- 0 (default)
  * 2 hidden units per lane in blocks sized for occupancy, 1 four hidden units
- * per lane, 2 eight-warp blocks, 3 another block size, 4 (width 64; the
- * default shape otherwise) every weight in registers (12 warps per SM; the
- * width-64 default keeps half of each lane's layer-2 weights in shared
- * memory so that 16 fit).
+ * per lane, 2 eight-warp blocks, 3 another block size, 4 at width 64 every
+ * weight in registers (12 warps per SM; the width-64 default keeps half of
+ * each lane's layer-2 weights in shared memory so that 16 fit), at width 32
+ * 5 of each lane's 8 layer-2 input quads in shared memory (20 warps per
+ * SM), at width 16 the default shape.
  * Returns NPP_INVALID_ARG for an unknown name or value. */
 npp_status npp_set_option(npp_handle* h, const char* name, int32_t value);
 

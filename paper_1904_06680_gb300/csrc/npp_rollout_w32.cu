@@ -1,6 +1,10 @@
 // Trajectory kernel for the 8-32-32-2 network.  Launch shapes (all compute
 // identical values): 0 (default, fastest measured on GB300) <32, 16, 4, 4>,
-// 1 four hidden units per lane, 2 eight-warp blocks, 3 <32, 16, 8, 3>;
+// 1 four hidden units per lane, 2 eight-warp blocks, 3 <32, 16, 8, 3>, 4 the
+// last 5 of each lane's 8 W2 input quads in shared memory (5 KB per warp;
+// parameters generated by rolled loops through those slots) so that 20
+// warps fit per SM (measured 0.161 against 0.164 ms on the course: this
+// width is not bound by occupancy, so it is not the default);
 // template arguments <width, lanes per sample, warps per block, blocks per SM hint>.
 #include "npp_rollout.cuh"
 
@@ -14,6 +18,7 @@ cudaError_t launch_traj_w32(const RolloutArgs& a, cudaStream_t s, int variant)
     case 1: return launch_traj<32, 8, 8>(a, s);
     case 2: return launch_traj<32, 16, 8>(a, s);
     case 3: return launch_traj<32, 16, 8, 3>(a, s);
+    case 4: return launch_traj<32, 16, 4, 5, false, 5>(a, s);
     default: return launch_traj<32, 16, 4, 4>(a, s);
     }
 }

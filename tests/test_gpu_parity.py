@@ -261,7 +261,8 @@ def test_collide_variants_identical():
     obs = torch.tensor(sc["obs"], dtype=torch.float32, device="cuda")
     pl = npp.Planner(sc["preset"], max_N=N, max_T=T, max_M=obs.shape[0])
     res = []
-    for v, tv in [(0, 0), (1, 1), (2, 0), (0, 1), (1, 0), (3, 0), (4, 0), (5, 0), (5, 1), (2, 2), (3, 3)]:
+    for v, tv in [(0, 0), (1, 1), (2, 0), (0, 1), (1, 0), (3, 0), (4, 0), (5, 0), (5, 1), (2, 2), (3, 3), (4, 4),
+                  (5, 4)]:
         npp.npp_set_option(pl.h, "collide_variant", v)
         npp.npp_set_option(pl.h, "traj_variant", tv)
         pl.plan(sc["state"], sc["goal"], obs, N, T, sc["seed"], sc["t_index"])

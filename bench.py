@@ -285,8 +285,9 @@ def kernel_sources_hash(kernel):
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from profiles/traffic.json, or None
+def profiled_traffic(kernel, workload=None):
+    """DRAM bytes per launch of `kernel` from profiles/traffic.json (the entry
+    "kernel@workload" where the traffic depends on the workload), or None
     when its sources changed since that capture."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
@@ -294,7 +295,8 @@ def profiled_traffic(kernel):
     except (OSError, ValueError):
         return None
     k = kernel.replace(" ", "")
-    ent = {kk.replace(" ", ""): v for kk, v in rec.get("kernels", {}).items()}.get(k)
+    ents = {kk.replace(" ", ""): v for kk, v in rec.get("kernels", {}).items()}
+    ent = ents.get("%s@%s" % (k, workload)) or ents.get(k)
     if not ent or ent.get("sources") != kernel_sources_hash(k):
         return None
     return ent.get("dram_bytes_per_launch")
@@ -469,14 +471,14 @@ def run_npp(args):
     # default launch shapes; the last template argument is the variant flag
     # (off: no speed limits, features in the EV frame at t)
     var = int(bool(p.get("v_limits", 0) or p.get("feature_frame", 0)))
-    shape = {16: "<16,8,4,4,%d>", 32: "<32,16,4,4,%d>", 64: "<64,32,1,16,%d,8>"}[W] % var
+    shape = {16: "<16,8,4,4,%d,0>", 32: "<32,16,4,4,%d,0>", 64: "<64,32,1,16,%d,8>"}[W] % var
     fma_all = float(N) * T * K * (W * W + 10 * W)
     if fused:
         # [0] grid build, [1] the fused trajectory-and-check kernel
         fname = "fused_kernel" + shape
         fps = res["fma_t"] / (collide_ms / 1e3)
         roofline = {"bound": "alu", "kernel": fname, "achieved": fps / 1e12, "peak": peak / 1e12,
-                    "unit": "T FP32-FMA/s", "frac": fps / peak, "traffic": profiled_traffic(fname),
+                    "unit": "T FP32-FMA/s", "frac": fps / peak, "traffic": profiled_traffic(fname, args.workload),
                     "peak_basis": peak_basis, "peak_measured": fma_measured,
                     "work": "MLP FMAs (W^2 + 10 W) per control step of a sample up to its first collision "
                             "(the kernel stops each sample at most two steps later); the binned check's "
@@ -502,12 +504,12 @@ def run_npp(args):
                         candidate_tests_per_state=res["cand_tests"] / res["states"],
                         states_per_s=res["states"] / (collide_ms / 1e3),
                         bytes_per_step=nbytes / K, achieved_gbs=nbytes / (collide_ms / 1e3) / 1e9,
-                        traffic=profiled_traffic("collide_binned_kernel"),
+                        traffic=profiled_traffic("collide_binned_kernel", args.workload),
                         bytes_note="algorithmic: 56 B per state checked (state + ten cell-run bounds), "
                                    "8 B per candidate test, 12 B per sample; traffic = DRAM bytes per "
                                    "launch from profiles/traffic.json")
         roofline = {"bound": "alu", "kernel": tname, "achieved": fps_t / 1e12, "peak": peak / 1e12,
-                    "unit": "T FP32-FMA/s", "frac": fps_t / peak, "traffic": profiled_traffic(tname),
+                    "unit": "T FP32-FMA/s", "frac": fps_t / peak, "traffic": profiled_traffic(tname, args.workload),
                     "peak_basis": peak_basis, "peak_measured": fma_measured,
                     "work": "MLP FMAs (W^2 + 10 W) per control step of a sample up to its first "
                             "collision; all_steps_* count every step the kernel computes",
@@ -527,7 +529,7 @@ def run_npp(args):
         fps_t = res["fma_t"] / (traj_ms / 1e3)
         roofline = {"bound": "alu", "kernel": cname,
                     "achieved": fps_c / 1e12, "peak": peak / 1e12, "unit": "T FP32-FMA/s",
-                    "frac": fps_c / peak, "traffic": profiled_traffic(cname),
+                    "frac": fps_c / peak, "traffic": profiled_traffic(cname, args.workload),
                     "peak_basis": peak_basis, "peak_measured": fma_measured,
                     "work": "4 FMAs per point-check (two rows of the rotated inequality test) of a sample "
                             "up to its first collision",
@@ -936,6 +938,8 @@ def run_mission(args):
         sp = inputs.scene_parking(args.seed + k + rank * 1000)
         Mp = sp["obs"].shape[0]
         pl = npp.Planner(sp["preset"], max_N=sp["N"], max_T=sp["T"], max_M=Mp, device=local)
+        # the hill climb of Sect. II-D in every sampling time (4 rounds)
+        npp.npp_set_loop_restarts(pl.h, 4, 0.1)
         obs = torch.tensor(sp["obs"], dtype=torch.float32, device=dev)
         L = npp.npp_loop_create(pl.h, sp["state"], sp["waypoints"], inputs.EPS, obs, Mp, sp["N"], sp["T"],
                                 sp["seed"], max_log=max_steps)
@@ -982,7 +986,8 @@ def run_mission(args):
             "parking": {"completed": sum(r["completed"] for r in parking),
                         "collision_free_and_completed": sum(r["completed"] and r["collisions"] == 0 for r in parking),
                         "of": len(parking), "description": "reverse parking (Experiment 5: auxiliary waypoint, "
-                        "then the slot), N=16384, T=60, MLP 8-16-16-2", "runs": parking},
+                        "then the slot), N=16384, T=60, MLP 8-16-16-2, 4 hill-climb rounds per sampling time "
+                        "(sigma_pert 0.1)", "runs": parking},
             "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": launches, "clocks": ck}
     if rank == 0:
         print(json.dumps(line))

@@ -368,16 +368,17 @@ def run_npp(args):
         L = npp.npp_loop_create(pl.h, sc["state"], sc["waypoints"], inputs.EPS, obs0_dev, M, N, T,
                                 sc["seed"], max_log=max(nsteps, 1))
         out = dict(step_ms=[], collide_ms=[], traj_ms=[], fma_c=0.0, fma_t=0.0, checks=0.0,
-                   free=[], best_cost=[], cand_tests=0.0, states=0.0)
+                   free=[], best_cost=[], cand_tests=0.0, states=0.0, rolled=0.0)
         for t in range(nsteps):
             flush.zero_()
             torch.cuda.synchronize()
             npp.npp_loop_run(L, 1)
             tm = npp.npp_loop_last_timing(L)
             if record:
-                ct, cs = npp.npp_last_counts(pl.h)
+                ct, cs, cr = npp.npp_last_counts(pl.h)
                 out["cand_tests"] += ct
                 out["states"] += cs
+                out["rolled"] += cr
                 _, fh = npp.npp_loop_samples(L, N)
                 out["step_ms"].append(tm["total"])
                 out["collide_ms"].append(tm["collide"])
@@ -472,7 +473,6 @@ def run_npp(args):
     # (off: no speed limits, features in the EV frame at t)
     var = int(bool(p.get("v_limits", 0) or p.get("feature_frame", 0)))
     shape = {16: "<16,8,4,4,%d,0>", 32: "<32,16,4,4,%d,0>", 64: "<64,32,1,16,%d,8>"}[W] % var
-    fma_all = float(N) * T * K * (W * W + 10 * W)
     if fused:
         # [0] grid build, [1] the fused trajectory-and-check kernel
         fname = "fused_kernel" + shape
@@ -508,13 +508,19 @@ def run_npp(args):
                         bytes_note="algorithmic: 56 B per state checked (state + ten cell-run bounds), "
                                    "8 B per candidate test, 12 B per sample; traffic = DRAM bytes per "
                                    "launch from profiles/traffic.json")
+        # sample-steps the trajectory launches rolled out (N T per plan step
+        # in one launch; fewer in step chunks, which drop collided samples)
+        rolled = res["rolled"] if res["rolled"] > 0 else float(N) * T * K
+        fma_rolled = rolled * (W * W + 10 * W)
         roofline = {"bound": "alu", "kernel": tname, "achieved": fps_t / 1e12, "peak": peak / 1e12,
                     "unit": "T FP32-FMA/s", "frac": fps_t / peak, "traffic": profiled_traffic(tname, args.workload),
                     "peak_basis": peak_basis, "peak_measured": fma_measured,
                     "work": "MLP FMAs (W^2 + 10 W) per control step of a sample up to its first "
-                            "collision; all_steps_* count every step the kernel computes",
-                    "all_steps_achieved": fma_all / (traj_ms / 1e3) / 1e12,
-                    "all_steps_frac": fma_all / (traj_ms / 1e3) / peak,
+                            "collision; rolled_steps_* count every step the kernel computed",
+                    "rolled_steps_per_plan_step": rolled / K,
+                    "rolled_steps_of_all": rolled / (float(N) * T * K),
+                    "rolled_steps_achieved": fma_rolled / (traj_ms / 1e3) / 1e12,
+                    "rolled_steps_frac": fma_rolled / (traj_ms / 1e3) / peak,
                     "kernel_ms_per_step": traj_ms / K,
                     "other": {cname: coll},
                     "dominant": tname if traj_ms >= collide_ms else cname}

@@ -344,7 +344,8 @@ npp_status npp_loop_samples(npp_loop* L, float* costs_host, int32_t* first_hit_h
  * graph): [0] trajectory kernel, [1] collision kernel, [2] selection
  * epilogue + advance, [3] whole step; writes up to n values.  When the
  * binned check runs fused into the trajectory kernel ("fuse"), [0] is the
- * grid build and [1] the fused kernel. */
+ * grid build and [1] the fused kernel; in step chunks ("chunks"), [0] and
+ * [1] are summed over the chunks. */
 npp_status npp_loop_last_timing(npp_loop* L, float* stage_ms, int32_t n);
 
 /* Free the loop (after synchronising the device). */
@@ -466,6 +467,16 @@ npp_status npp_plan_step_noalloc(const npp_config* cfg, const npp_state* state,
  * stores no per-sample states (used only when the call requests no
  * per-sample records; the winner's rows are re-rolled).  Same results;
  * measured slower on GB300 (the check's loads lengthen the per-step chain).
+ * "chunks" 0..8: with the binned check (5) and no per-sample records
+ * requested (sample_traj and sample_ctrl NULL, and the closed loop), roll
+ * the horizon out in that many chunks of steps, each followed by the check
+ * of the states it produced; only the samples still collision-free go on to
+ * the next chunk, so no sample is rolled out more than one chunk past its
+ * first collision.  Each chunk regenerates its samples' parameters and
+ * continues from the stored state and the carried FP32 values, so every
+ * output (costs, first_hit, the winner and its rows) is the one of a single
+ * launch.  0 (default): automatic (2 at width 64, else 1), 1: one launch
+ * each; at most T chunks.
  * "traj_variant" 0..4: launch shape of the trajectory kernel -- 0 (default)
  * 2 hidden units per lane in blocks sized for occupancy, 1 four hidden units
  * per lane, 2 eight-warp blocks, 3 another block size, 4 at width 64 every
@@ -482,16 +493,20 @@ npp_status npp_set_option(npp_handle* h, const char* name, int32_t value);
  * durations in milliseconds: [0] trajectory kernel, [1] collision kernel,
  * [2] selection epilogue, [3] the whole call (npp_rollout_params has no
  * epilogue: [2] is 0); with the fused binned check, [0] is the grid build
- * and [1] the fused trajectory-and-check kernel.  Disabled by default;
- * enabling it adds four event records per call. */
+ * and [1] the fused trajectory-and-check kernel; with the step chunks
+ * ("chunks"), [0] and [1] are the sums over the chunks' trajectory and check
+ * launches.  Disabled by default; enabling it adds four event records per
+ * call (and two per chunk). */
 npp_status npp_set_timing(npp_handle* h, int32_t enable);
 npp_status npp_last_timing(npp_handle* h, float* stage_ms, int32_t n);
 
 /* Work counters of the last timed plan step's binned collision check (also
  * of the first round of a closed loop's sampling time created with timing
  * on): [0] candidate point tests (each one evaluation of the rectangle's
- * inequalities), [1] states checked.  Zero when that step used another
- * collision check.  Synchronises the device; needs timing enabled. */
+ * inequalities), [1] states checked, [2] sample-steps the trajectory kernel
+ * rolled out (N T in one launch, fewer with the step chunks).  Zero when
+ * that step used another collision check.  Synchronises the device; needs
+ * timing enabled; writes up to n (at most 3) values. */
 npp_status npp_last_counts(npp_handle* h, uint64_t* counts, int32_t n);
 
 #ifdef __cplusplus

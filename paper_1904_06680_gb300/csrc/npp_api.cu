@@ -154,6 +154,27 @@ __global__ void fill_value_kernel(float* p, int n, float v)
 }
 }  // namespace
 
+cudaError_t stage_times(const cudaEvent_t* ev, const cudaEvent_t* cev, int nch, float t[4])
+{
+    cudaError_t e = cudaSuccess;
+    if (nch > 1) {
+        t[0] = t[1] = 0.f;
+        for (int k = 0; k < nch && e == cudaSuccess; ++k) {
+            float a = 0.f, b = 0.f;
+            e = cudaEventElapsedTime(&a, cev[2 * k], cev[2 * k + 1]);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&b, cev[2 * k + 1], cev[2 * k + 2]);
+            t[0] += a;
+            t[1] += b;
+        }
+    } else {
+        e = cudaEventElapsedTime(&t[0], ev[0], ev[1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t[1], ev[1], ev[2]);
+    }
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t[2], ev[2], ev[3]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t[3], ev[0], ev[3]);
+    return e;
+}
+
 cudaError_t fill_floats(float* p, int n, float v, cudaStream_t s)
 {
     fill_value_kernel<<<(n + 255) / 256, 256, 0, s>>>(p, n, v);
@@ -179,6 +200,61 @@ static cudaError_t launch_fused(const npp_handle* h, const RolloutArgs& a, cudaS
     }
 }
 
+// Step chunks of a binned plan step: 1 (one trajectory launch and one check)
+// when the caller wants every sample's records or chooses so, else the
+// handle's setting or the automatic choice, at most one per step.  Each
+// chunk regenerates its samples' parameters (measured on GB300 at N = 65536,
+// T = 100, width 64: 0.59 ms per full generation, 0.12 ms of launch and tail
+// per chunk, 0.027 ms per step of all samples), so two chunks pay at width
+// 64 (3.83 -> 3.31 ms per plan step; 3, 4, 6 chunks: 3.50, 3.87, 4.69 ms)
+// and none at width 32 and T = 40 (0.258 ms in one launch, 0.293 in two).
+static int chunk_count(const npp_handle* h, const RolloutArgs& a, bool no_records)
+{
+    if (!no_records || h->chunks == 1 || a.T < 2) return 1;
+    const int k = h->chunks > 1 ? h->chunks : (h->cfg.width == 64 ? 2 : 1);
+    return std::min(k, a.T);
+}
+
+// The binned plan step in K chunks of the horizon: chunk k rolls the
+// samples still collision-free from the states chunk k - 1 stored over
+// steps [T k / K, T (k + 1) / K) and checks the states it produced; a
+// sample ends with its chunk's first collision, so no sample is rolled out
+// more than one chunk past its first collision.  Per sample the arithmetic
+// and the results are those of the single launch (the carried values are
+// the FP32 values the single loop holds); only the records past a sample's
+// last chunk are not written.  The grids are being built on the side
+// stream (join_ev) while chunk 0's trajectories run.
+static npp_status run_chunked(npp_handle* h, RolloutArgs& a, cudaStream_t s, int K)
+{
+    CUDA_TRY(h, cudaMemsetAsync(h->d_live_n, 0, NPP_MAX_CHUNKS * sizeof(int), s));
+    a.carry = h->d_carry;
+    const size_t half = (size_t)h->cfg.max_N;
+    for (int k = 0; k < K; ++k) {
+        a.chunk_lo = (int)((long long)a.T * k / K);
+        a.chunk_hi = (int)((long long)a.T * (k + 1) / K);
+        a.live_in = k > 0 ? h->d_live + ((k - 1) % 2) * half : nullptr;
+        a.live_n_in = k > 0 ? h->d_live_n + (k - 1) : nullptr;
+        a.live_out = k + 1 < K ? h->d_live + (k % 2) * half : nullptr;
+        a.live_n_out = k + 1 < K ? h->d_live_n + k : nullptr;
+        if (h->timing) CUDA_TRY(h, record_event(h->cev[2 * k], s));
+        CUDA_TRY(h, launch_traj(h, a, s));
+        if (h->timing) CUDA_TRY(h, record_event(h->cev[2 * k + 1], s));
+        if (k == 0) CUDA_TRY(h, cudaStreamWaitEvent(s, h->join_ev, 0));
+        CUDA_TRY(h, launch_collide_binned(a, s));
+    }
+    if (h->timing) {
+        CUDA_TRY(h, record_event(h->cev[2 * K], s));
+        CUDA_TRY(h, record_event(h->ev[2], s));
+        h->last_chunks = K;
+    }
+    a.chunk_lo = a.chunk_hi = 0;
+    a.live_in = a.live_n_in = nullptr;
+    a.live_out = a.live_n_out = nullptr;
+    a.carry = nullptr;
+    a.counts = nullptr;
+    return NPP_OK;
+}
+
 npp_status run_rollout(npp_handle* h, RolloutArgs& a, cudaStream_t s, bool allow_fused, bool* fused)
 {
     // no rows are stored: every collision kernel recomputes them from the
@@ -187,6 +263,7 @@ npp_status run_rollout(npp_handle* h, RolloutArgs& a, cudaStream_t s, bool allow
     a.coefB = nullptr;
     a.work = h->d_work;
     *fused = false;
+    if (h->timing) h->last_chunks = 1;
     if (h->fp_faces > 0) {
         // general footprint: grids sized by its radius (side stream, as
         // below), trajectories without the rectangle's rows, polygon check
@@ -220,6 +297,12 @@ npp_status run_rollout(npp_handle* h, RolloutArgs& a, cudaStream_t s, bool allow
     if (v == COLLIDE_BINNED) {
         if (h->timing) CUDA_TRY(h, record_event(h->ev[0], s));
         if (!(allow_fused && h->fuse)) {
+            if (h->timing) {
+                // measurement counters (candidate tests, states checked,
+                // sample-steps rolled out)
+                CUDA_TRY(h, cudaMemsetAsync(h->d_counts, 0, 4 * sizeof(unsigned long long), s));
+                a.counts = h->d_counts;
+            }
             // the grids depend only on the points: build them on the side
             // stream while the trajectories run (fork/join events; under
             // stream capture this makes two graph branches)
@@ -227,14 +310,11 @@ npp_status run_rollout(npp_handle* h, RolloutArgs& a, cudaStream_t s, bool allow
             CUDA_TRY(h, cudaStreamWaitEvent(h->side, h->fork_ev, 0));
             CUDA_TRY(h, build_bins(a, h->cfg.half_len, h->cfg.half_wid, h->cfg.c_off, h->d_bins, h->side));
             CUDA_TRY(h, cudaEventRecord(h->join_ev, h->side));
+            const int K = chunk_count(h, a, allow_fused);
+            if (K > 1) return run_chunked(h, a, s, K);
             CUDA_TRY(h, launch_traj(h, a, s));
             if (h->timing) CUDA_TRY(h, record_event(h->ev[1], s));
             CUDA_TRY(h, cudaStreamWaitEvent(s, h->join_ev, 0));
-            if (h->timing) {
-                // measurement counters of the check (candidate tests, states)
-                CUDA_TRY(h, cudaMemsetAsync(h->d_counts, 0, 2 * sizeof(unsigned long long), s));
-                a.counts = h->d_counts;
-            }
             CUDA_TRY(h, launch_collide_binned(a, s));
             a.counts = nullptr;
             if (h->timing) CUDA_TRY(h, record_event(h->ev[2], s));
@@ -369,6 +449,8 @@ npp_status npp_create(npp_handle** out, const npp_config* cfg, int32_t device)
     h->cfg = *cfg;
     h->collide_variant = -1;
     h->fuse = false;
+    h->chunks = 0;
+    h->last_chunks = 1;
     h->loop_restarts = 1;
     h->loop_sigma = 0.0f;
     h->collide_active = -1;
@@ -391,6 +473,9 @@ npp_status npp_create(npp_handle** out, const npp_config* cfg, int32_t device)
     if (cfg->v_limits) A((void**)&h->d_vfirst, (size_t)cfg->max_N * sizeof(int));
     A((void**)&h->d_work, 64);
     A((void**)&h->d_counts, 64);
+    A((void**)&h->d_live, (size_t)2 * cfg->max_N * sizeof(int));
+    A((void**)&h->d_live_n, NPP_MAX_CHUNKS * sizeof(int));
+    A((void**)&h->d_carry, (size_t)cfg->max_N * sizeof(float4));
     A(&h->d_bins, binned_workspace_bytes(cfg->max_T, cfg->max_M));
     if (cfg->max_M > max_points) {
         A((void**)&h->d_pXY, (size_t)(cfg->max_M / 2 + 1) * sizeof(float4));
@@ -410,6 +495,7 @@ npp_status npp_create(npp_handle** out, const npp_config* cfg, int32_t device)
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming);
     for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&h->ev[i]);
+    for (int i = 0; i < NPP_CHUNK_EVENTS && e == cudaSuccess; ++i) e = cudaEventCreate(&h->cev[i]);
     if (e != cudaSuccess) {
         g_err = std::string("workspace allocation failed: ") + cudaGetErrorString(e);
         npp_destroy(h);
@@ -425,6 +511,7 @@ npp_status npp_destroy(npp_handle* h)
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
     void* ptrs[] = { h->d_key, h->d_traj, h->d_ctrl, h->d_jfree, h->d_vfirst, h->d_fp, h->d_work, h->d_counts,
+                     h->d_live, h->d_live_n, h->d_carry,
                      h->d_pXY, h->d_pV, h->d_bins,
                      h->d_obs, h->d_warm, h->d_sigma, h->d_best, h->d_params, h->d_controls, h->d_trajectory,
                      h->d_costs, h->d_fh };
@@ -434,6 +521,7 @@ npp_status npp_destroy(npp_handle* h)
     if (h->fork_ev) cudaEventDestroy(h->fork_ev);
     if (h->join_ev) cudaEventDestroy(h->join_ev);
     for (int i = 0; i < 4; ++i) if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+    for (int i = 0; i < NPP_CHUNK_EVENTS; ++i) if (h->cev[i]) cudaEventDestroy(h->cev[i]);
     delete h;
     return NPP_OK;
 }
@@ -682,6 +770,11 @@ npp_status npp_set_option(npp_handle* h, const char* name, int32_t value)
         h->fuse = value != 0;
         return NPP_OK;
     }
+    if (std::strcmp(name, "chunks") == 0) {
+        if (value < 0 || value > NPP_MAX_CHUNKS) return fail(h, NPP_INVALID_ARG, "chunks is 0..%d", NPP_MAX_CHUNKS);
+        h->chunks = value;
+        return NPP_OK;
+    }
     if (std::strcmp(name, "traj_variant") == 0) {
         if (value < 0 || value > 4) return fail(h, NPP_INVALID_ARG, "traj_variant is 0..4");
         h->traj_variant = value;
@@ -704,9 +797,9 @@ npp_status npp_last_counts(npp_handle* h, uint64_t* counts, int32_t n)
     if (!counts || n < 1) return fail(h, NPP_INVALID_ARG, "counts must hold n >= 1 values");
     CUDA_TRY(h, cudaSetDevice(h->device));
     CUDA_TRY(h, cudaDeviceSynchronize());
-    unsigned long long c[2] = { 0ull, 0ull };
+    unsigned long long c[3] = { 0ull, 0ull, 0ull };
     CUDA_TRY(h, cudaMemcpy(c, h->d_counts, sizeof c, cudaMemcpyDeviceToHost));
-    for (int i = 0; i < n && i < 2; ++i) counts[i] = c[i];
+    for (int i = 0; i < n && i < 3; ++i) counts[i] = c[i];
     return NPP_OK;
 }
 
@@ -718,13 +811,11 @@ npp_status npp_last_timing(npp_handle* h, float* stage_ms, int32_t n)
     CUDA_TRY(h, cudaSetDevice(h->device));
     CUDA_TRY(h, cudaEventSynchronize(h->ev[3]));
     float t[4] = { 0.f, 0.f, 0.f, 0.f };
-    CUDA_TRY(h, cudaEventElapsedTime(&t[0], h->ev[0], h->ev[1]));
-    CUDA_TRY(h, cudaEventElapsedTime(&t[1], h->ev[1], h->ev[2]));
-    CUDA_TRY(h, cudaEventElapsedTime(&t[2], h->ev[2], h->ev[3]));
-    CUDA_TRY(h, cudaEventElapsedTime(&t[3], h->ev[0], h->ev[3]));
+    CUDA_TRY(h, stage_times(h->ev, h->cev, h->last_chunks, t));
     for (int i = 0; i < n && i < 4; ++i) stage_ms[i] = t[i];
     return NPP_OK;
 }
+
 
 npp_status npp_sample_params(uint64_t seed, uint32_t t_index, uint32_t stream_id, int32_t n0,
                              int32_t K, int32_t n_theta, float* out_dev, void* stream)

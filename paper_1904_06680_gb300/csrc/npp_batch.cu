@@ -996,7 +996,10 @@ npp_status npp_plan_batch(npp_batch* B, const float* obs_dev, const npp_batch_ou
     b.trajectory = out->trajectory;
     b.costs = out->costs;
     b.first_hit = out->first_hit;
-    if (h->timing) CUDA_TRY(h, record_event(h->ev[0], s));
+    if (h->timing) {
+        CUDA_TRY(h, record_event(h->ev[0], s));
+        h->last_chunks = 1;
+    }
     CUDA_TRY(h, cudaMemsetAsync(B->d_keys, 0xff, sizeof(unsigned long long) * B->S, s));
     CUDA_TRY(h, cudaMemsetAsync(B->d_counters, 0, 64, s));
     if (B->max_pairs > 0) {

@@ -62,20 +62,32 @@ __device__ __forceinline__ bool inside_rows(const float4& A, const float2& B, fl
     return !(((__float_as_uint(xi) | __float_as_uint(et)) >> 30) & 1u);
 }
 
-__global__ void __launch_bounds__(BINNED_WARPS * 32) collide_binned_kernel(const RolloutArgs a)
+__global__ void __launch_bounds__(BINNED_WARPS * 32, 5) collide_binned_kernel(const RolloutArgs a)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gid = lane / BIN_GS, gl = lane % BIN_GS;
     const BinView& g = a.bins;
     const int T = a.T, N = a.N, M = a.M;
-    const int n = blockIdx.x * BINNED_WARPS + warp;
+    int n = blockIdx.x * BINNED_WARPS + warp;
+    bool valid = n < N;
+    if (a.live_in) {
+        const int cnt = *a.live_n_in;
+        valid = n < cnt;
+        n = valid ? a.live_in[n] : 0;
+    }
+    // the states of this launch: all (0 .. T), or those of one chunk
+    // (0 .. chunk_hi for the first, chunk_lo + 1 .. chunk_hi after it)
+    const bool chunked = a.chunk_hi > 0;
+    const int hs = chunked && a.chunk_lo > 0 ? a.chunk_lo + 1 : 0;
+    const int he = chunked ? a.chunk_hi : T;
     unsigned long long key = ~0ull;
+    bool fold = false;                       // lane 0: this warp's sample ended here (key to fold)
     unsigned ntest = 0, nstate = 0;          // this lane's candidate tests and states (measurement)
-    if (n < N) {
+    if (valid) {
         int fh = -1;
-        for (int h0 = 0; h0 <= T; h0 += BIN_SB) {
+        for (int h0 = hs; h0 <= he; h0 += BIN_SB) {
             const int h = h0 + gid;
-            const bool ok = h <= T;
+            const bool ok = h <= he;
             // the rectangle lies in the disk of radius reach around the
             // reference point (reach covers the centre offset)
             const float4 z = ok ? a.traj[(size_t)h * N + n] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -122,15 +134,21 @@ __global__ void __launch_bounds__(BINNED_WARPS * 32) collide_binned_kernel(const
         }
         if (lane == 0) {
             fh = discard_step(a.vfirst, n, fh);
-            float J = __int_as_float(0x7f800000);
-            if (fh < 0) {
-                J = a.jfree[n];
-                key = ((unsigned long long)__float_as_uint(J) << 32) | (unsigned)n;
+            if (fh < 0 && he < T) {
+                // collision-free so far: on to the next chunk
+                a.live_out[atomicAdd(a.live_n_out, 1)] = n;
             } else {
-                key = (1ull << 63) | ((unsigned long long)(T - fh) << 32) | (unsigned)n;
+                float J = __int_as_float(0x7f800000);
+                if (fh < 0) {
+                    J = a.jfree[n];
+                    key = ((unsigned long long)__float_as_uint(J) << 32) | (unsigned)n;
+                } else {
+                    key = (1ull << 63) | ((unsigned long long)(T - fh) << 32) | (unsigned)n;
+                }
+                if (a.costs) a.costs[n] = J;
+                if (a.first_hit) a.first_hit[n] = fh;
+                fold = true;
             }
-            if (a.costs) a.costs[n] = J;
-            if (a.first_hit) a.first_hit[n] = fh;
         }
     }
     if (a.counts) {
@@ -140,14 +158,14 @@ __global__ void __launch_bounds__(BINNED_WARPS * 32) collide_binned_kernel(const
             t += __shfl_xor_sync(FULL, t, off);
             s += __shfl_xor_sync(FULL, s, off);
         }
-        if (lane == 0 && n < N) {
+        if (lane == 0 && valid) {
             atomicAdd(a.counts, t);
             atomicAdd(a.counts + 1, s);
         }
     }
     // each warp folds its key into the minimum on its own (no block barrier:
     // samples end at different steps); the read skips atomics that cannot win
-    if (lane == 0 && n < N && a.best_key && key < *reinterpret_cast<volatile unsigned long long*>(a.best_key))
+    if (fold && a.best_key && key < *reinterpret_cast<volatile unsigned long long*>(a.best_key))
         atomicMin(a.best_key, key);
 }
 

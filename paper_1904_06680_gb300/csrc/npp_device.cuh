@@ -451,8 +451,22 @@ struct RolloutArgs {
     float4* pXY;                       // EV-frame point pairs in global memory (when the
     float4* pV;                        // points exceed shared memory), [ceil(M/2)]
     BinView bins;                      // per-step grids (binned and fused collision checks)
-    unsigned long long* counts;        // measurement counters of the binned check, or null:
-                                       // [0] candidate point tests, [1] states checked
+    unsigned long long* counts;        // measurement counters, or null: [0] candidate point tests
+                                       // and [1] states checked by the binned check, [2] sample-steps
+                                       // computed by the trajectory kernel
+    // Step chunks (binned check, no per-sample records wanted): a
+    // trajectory launch computes steps chunk_lo .. chunk_hi - 1 (states up to
+    // chunk_hi), the check covers the states the chunk produced; chunk_hi 0:
+    // the whole horizon in one launch each.  live_in (length *live_n_in)
+    // lists the samples still collision-free before the chunk (null: all N);
+    // the check appends the chunk's survivors to live_out, counting in
+    // *live_n_out.  carry: [N] values carried between chunks.
+    int chunk_lo, chunk_hi;
+    const int* live_in;
+    const int* live_n_in;
+    int* live_out;
+    int* live_n_out;
+    float4* carry;
     PolyView poly;                     // general footprint (polygon checks)
 };
 

@@ -16,6 +16,10 @@
 constexpr int COLLIDE_BINNED = 5;
 inline bool binned_auto(int M, int N) { return M >= 512 && (long long)M * N >= 8000000LL; }
 
+// most step chunks of one plan step, and the stage events they need
+constexpr int NPP_MAX_CHUNKS = 8;
+constexpr int NPP_CHUNK_EVENTS = 2 * NPP_MAX_CHUNKS + 1;
+
 struct npp_handle {
     npp_config cfg;
     int device;
@@ -37,6 +41,12 @@ struct npp_handle {
     int collide_active;                  // variant used for the current launch
     int traj_variant;                    // trajectory launch shape (0..3)
     bool fuse;                           // binned check fused into the trajectory kernel
+    int chunks;                          // step chunks of the binned path when no per-sample records
+                                         // are wanted (0: automatic, 1: one launch each)
+    int last_chunks;                     // chunks of the last timed plan step (its stage events)
+    int* d_live;                         // [2][max_N] samples still collision-free between chunks
+    int* d_live_n;                       // [NPP_MAX_CHUNKS] their counts
+    float4* d_carry;                     // [max_N] values carried from chunk to chunk
     int loop_restarts;                   // hill-climb rounds per sampling time of new loops (1: none)
     float loop_sigma;                    // their perturbation scale
     int occ_M, occ_blocks;               // cached occupancy for the last M
@@ -58,7 +68,9 @@ struct npp_handle {
     cudaEvent_t fork_ev, join_ev;
     bool timing;
     cudaEvent_t ev[4];                   // start, after trajectories, after collisions, end
-    unsigned long long* d_counts;        // [2] binned-check counters of the last timed plan step
+    cudaEvent_t cev[NPP_CHUNK_EVENTS];   // chunked step: before trajectories k (2k), before check k
+                                         // (2k + 1), after the last check (2K)
+    unsigned long long* d_counts;        // measurement counters of the last timed plan step
     std::string err;
 };
 
@@ -79,6 +91,11 @@ cudaError_t fill_floats(float* p, int n, float v, cudaStream_t s);
 
 // records a message for npp_last_error and returns s
 npp_status fail(npp_handle* h, npp_status s, const char* fmt, ...);
+
+// stage times of a plan step from its events: [0] trajectories, [1] the
+// collision check (each summed over the chunks when nch > 1), [2] the
+// epilogue and what follows, [3] the whole step
+cudaError_t stage_times(const cudaEvent_t* ev, const cudaEvent_t* cev, int nch, float t[4]);
 
 // trajectory + collision kernels of one plan step (fills workspace pointers,
 // the persistent grid and the work-counter reset); with the binned check and

@@ -49,6 +49,8 @@ struct npp_loop {
     int restarts;            // hill-climb rounds per sampling time (1: the plan step alone)
     float* d_sigma;          // [n_theta] their perturbation scale
     cudaEvent_t ev[4];       // captured: start, after trajectories, after collisions, end
+    cudaEvent_t cev[NPP_CHUNK_EVENTS];  // captured chunk stage events (plan step in chunks)
+    int nch;                 // chunks of the captured plan step
     cudaStream_t cap;
     cudaGraph_t graph;
     cudaGraphExec_t exec;
@@ -234,6 +236,7 @@ void free_loop(npp_loop* L)
                      L->d_trajectory, L->d_log, L->d_costs, L->d_fh, L->d_sigma };
     for (void* p : ptrs) if (p) cudaFree(p);
     for (int i = 0; i < 4; ++i) if (L->ev[i]) cudaEventDestroy(L->ev[i]);
+    for (int i = 0; i < NPP_CHUNK_EVENTS; ++i) if (L->cev[i]) cudaEventDestroy(L->cev[i]);
     delete L;
 }
 
@@ -371,6 +374,7 @@ npp_status loop_create(npp_handle* h, const npp_state* s0, const float* waypoint
     if (L->restarts > 1) A((void**)&L->d_sigma, (size_t)h->n_theta * sizeof(float));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&L->cap, cudaStreamNonBlocking);
     for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&L->ev[i]);
+    for (int i = 0; i < NPP_CHUNK_EVENTS && e == cudaSuccess; ++i) e = cudaEventCreate(&L->cev[i]);
     if (e != cudaSuccess) {
         free_loop(L);
         return fail(h, NPP_CUDA_ERROR, "loop allocation failed: %s", cudaGetErrorString(e));
@@ -418,8 +422,10 @@ npp_status loop_create(npp_handle* h, const npp_state* s0, const float* waypoint
     // N, T, M, which the loop fixes
     // the plan step records its stage events (the loop's own) into the graph
     const bool timing = h->timing;
-    cudaEvent_t hev[4];
+    cudaEvent_t hev[4], hcev[NPP_CHUNK_EVENTS];
     for (int i = 0; i < 4; ++i) { hev[i] = h->ev[i]; h->ev[i] = L->ev[i]; }
+    for (int i = 0; i < NPP_CHUNK_EVENTS; ++i) { hcev[i] = h->cev[i]; h->cev[i] = L->cev[i]; }
+    const int h_last_chunks = h->last_chunks;
     h->timing = true;
     e = cudaStreamBeginCapture(L->cap, cudaStreamCaptureModeThreadLocal);
     npp_status st = NPP_OK;
@@ -427,7 +433,10 @@ npp_status loop_create(npp_handle* h, const npp_state* s0, const float* waypoint
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(L->cap, &g);
     h->timing = timing;
+    L->nch = h->last_chunks;
+    h->last_chunks = h_last_chunks;
     for (int i = 0; i < 4; ++i) h->ev[i] = hev[i];
+    for (int i = 0; i < NPP_CHUNK_EVENTS; ++i) h->cev[i] = hcev[i];
     if (e != cudaSuccess || st != NPP_OK || e2 != cudaSuccess || !g) {
         if (g) cudaGraphDestroy(g);
         free_loop(L);
@@ -542,10 +551,7 @@ npp_status npp_loop_last_timing(npp_loop* L, float* stage_ms, int32_t n)
     LOOP_TRY(h, cudaSetDevice(h->device));
     LOOP_TRY(h, cudaEventSynchronize(L->ev[3]));
     float t[4] = { 0.f, 0.f, 0.f, 0.f };
-    LOOP_TRY(h, cudaEventElapsedTime(&t[0], L->ev[0], L->ev[1]));
-    LOOP_TRY(h, cudaEventElapsedTime(&t[1], L->ev[1], L->ev[2]));
-    LOOP_TRY(h, cudaEventElapsedTime(&t[2], L->ev[2], L->ev[3]));
-    LOOP_TRY(h, cudaEventElapsedTime(&t[3], L->ev[0], L->ev[3]));
+    LOOP_TRY(h, stage_times(L->ev, L->cev, L->nch, t));
     for (int i = 0; i < n && i < 4; ++i) stage_ms[i] = t[i];
     return NPP_OK;
 }

@@ -493,6 +493,11 @@ struct TrajJob {
     const BinView* bins;          // fused check (traj_sample_fused)
     ulonglong2* w2s;              // this lane's slot of the shared W2 quads (LaneNet KSQ > 0), or null
     float* stage;                 // this thread's slot 0 of a staging area (stride stage_th), or null
+    // One chunk of the horizon: steps h_lo .. h_hi - 1 from the stored state
+    // h_lo and the carried (last controls, effort, first speed violation);
+    // h_hi < 0: the whole horizon from the initial state
+    int h_lo = 0, h_hi = -1;
+    float4* carry = nullptr;      // [N] carried values between chunks
 };
 
 // Result of a fused rollout, uniform over the sample's group: the first
@@ -678,8 +683,18 @@ __device__ __forceinline__ void traj_sample(const DevCfg& c, const TrajJob& job,
     const bool writer = valid && gl == 0;
     const long long rec = (long long)n - job.rec_shift;
     int vbad = -1;                       // first state h >= 1 whose speed is outside the limits
-    float rem = (float)T;                // T - h, exact in FP32
-    for (int h = 0; h < T; ++h) {
+    const int h_lo = job.h_lo, h_hi = job.h_hi < 0 ? T : job.h_hi;
+    if (h_lo > 0) {
+        // a later chunk: the state the previous chunk stored, and what it
+        // carried (the same FP32 values the whole-horizon loop would hold)
+        const float4 z = job.traj[h_lo * job.rec_stride + (valid ? rec : 0)];
+        const float4 cv = job.carry[valid ? n : 0];
+        x = z.x; y = z.y; ph = z.z; v = z.w;
+        ap0 = cv.x; ap1 = cv.y; E = cv.z;
+        vbad = __float_as_int(cv.w);
+    }
+    float rem = (float)(T - h_lo);       // T - h, exact in FP32
+    for (int h = h_lo; h < h_hi; ++h) {
         float sp, cp;
         sincos_r(ph, sp, cp);
         if constexpr (VAR) {
@@ -701,6 +716,18 @@ __device__ __forceinline__ void traj_sample(const DevCfg& c, const TrajJob& job,
         const float2 a = control_step<W, G, VAR, KSQ>(c, net, g, invT, gl, hrow, sp, cp, x, y, ph, v, ap0, ap1,
                                                       E, rem);
         if (writer && job.ctrl) job.ctrl[h * job.rec_stride + rec] = a;
+    }
+    if (h_hi < T) {
+        // end of a chunk: state h_hi (checked with this chunk, the next
+        // chunk's start) and the carried values
+        if (writer) {
+            job.traj[h_hi * job.rec_stride + rec] = make_float4(x, y, ph, v);
+            job.carry[n] = make_float4(ap0, ap1, E, __int_as_float(vbad));
+            if constexpr (VAR) {
+                if (job.vfirst) job.vfirst[n] = vbad;
+            }
+        }
+        return;
     }
     if constexpr (VAR) {
         if (c.vlim && T > 0 && vbad < 0 && !(v >= c.v_lo && v <= c.v_hi)) vbad = T;
@@ -945,7 +972,15 @@ __global__ void __launch_bounds__(NW * 32, MINB) traj_kernel(const RolloutArgs a
     extern __shared__ __align__(16) float stage_all[];
     const int tid = threadIdx.x;
     const int b = tid / G, gl = tid % G;
-    const int n = blockIdx.x * B + b;
+    int n = blockIdx.x * B + b;
+    bool valid = n < a.N;
+    if (a.live_in) {
+        // a later chunk: the samples still collision-free, listed
+        const int cnt = *a.live_n_in;
+        if ((int)blockIdx.x * B >= cnt) return;            // the whole block idle (no block barrier below)
+        valid = n < cnt;
+        n = valid ? a.live_in[n] : 0;
+    }
     TrajJob job;
     job.si = step_in(a);
     job.key = a.key;
@@ -972,7 +1007,15 @@ __global__ void __launch_bounds__(NW * 32, MINB) traj_kernel(const RolloutArgs a
     // staged parameter generation pays at W = 32 (measured on GB300: 11 %
     // faster at T = 40); at W = 16 and 64 the direct load is faster
     constexpr int STAGE_TH = (W == 32 && KSQ == 0) ? NW * 32 : 0;
-    traj_sample<W, G, STAGE_TH, VAR, KSQ>(a.c, job, n, n < a.N, gl, hx_all + b * W);
+    if (a.chunk_hi > 0) {
+        job.h_lo = a.chunk_lo;
+        job.h_hi = a.chunk_hi;
+        job.carry = a.carry;
+    }
+    traj_sample<W, G, STAGE_TH, VAR, KSQ>(a.c, job, n, valid, gl, hx_all + b * W);
+    // measurement: sample-steps computed (timing on)
+    if (a.counts && valid && gl == 0)
+        atomicAdd(a.counts + 2, (unsigned long long)((a.chunk_hi > 0 ? a.chunk_hi : a.T) - a.chunk_lo));
 }
 
 // Trajectories with the binned check fused in: per sample its first

@@ -415,11 +415,11 @@ def npp_loop_create_mission(h, state, ref, field, window, hide_outside, eps, obs
 
 
 def npp_last_counts(h):
-    """(candidate point tests, states checked) of the last timed plan step's
-    binned collision check (synchronises)."""
-    c = (C.c_uint64 * 2)()
-    _check(lib().npp_last_counts(h, c, 2), h)
-    return int(c[0]), int(c[1])
+    """(candidate point tests, states checked, sample-steps rolled out) of
+    the last timed plan step with the binned collision check (synchronises)."""
+    c = (C.c_uint64 * 3)()
+    _check(lib().npp_last_counts(h, c, 3), h)
+    return int(c[0]), int(c[1]), int(c[2])
 
 
 def npp_set_loop_restarts(h, n_restarts: int, sigma_pert: float = 0.0):

@@ -42,7 +42,7 @@ if ROOT not in sys.path:
 
 METRIC = "rollout-steps/s (N×T incl. M-point checks)"
 UNIT = "rollout-steps/s"
-DEFAULT_FUSE = 0                 # the library's default of the "fuse" option
+DEFAULT_FUSE = -1                # the library's default of the "fuse" option (-1: at width 64)
 FP32_LANES_PER_SM = 128          # FP32 FMA lanes per SM (4 schedulers x 32) on sm_100-class parts
 SM_MAX_MHZ_NOMINAL = 2070.0      # GB300 maximum SM clock, used only when the device does not report it
 
@@ -262,6 +262,8 @@ def algorithmic_work(first_hit, T, M, W):
 KERNEL_SOURCES = (
     ("traj_kernel", ("npp_rollout.cuh", "npp_device.cuh", "npp_rollout_w16.cu", "npp_rollout_w32.cu",
                      "npp_rollout_w64.cu")),
+    ("fused_kernel", ("npp_rollout.cuh", "npp_device.cuh", "npp_rollout_w16.cu", "npp_rollout_w32.cu",
+                      "npp_rollout_w64.cu")),
     ("bin_build_kernel", ("npp_binned.cu", "npp_device.cuh")),
     ("collide_binned_kernel", ("npp_binned.cu", "npp_device.cuh")),
     ("collide_poly_kernel", ("npp_poly.cu", "npp_device.cuh")),
@@ -468,22 +470,44 @@ def run_npp(args):
     # trajectory kernel
     cv = int(options.get("collide_variant", -1))
     binned = poly or cv == 5 or (cv < 0 and M >= 512 and M * N >= 8000000)
-    fused = binned and not poly and int(options.get("fuse", DEFAULT_FUSE)) == 1
+    fz = int(options.get("fuse", DEFAULT_FUSE))
+    fused = binned and not poly and (fz == 1 or (fz < 0 and W == 64))
+    # the library's step chunks of the split binned path (option "chunks";
+    # 0: two at width 64), each one trajectory and one check launch
+    nch = 1
+    if binned and not poly and not fused:
+        nch = min(int(options.get("chunks", 0)) or (2 if W == 64 else 1), T)
+    # per sampling time: plan step kernels, epilogue, vehicle and obstacle advance
+    launches_per_step = (2 if fused else 1 + 2 * nch if binned and not poly else 3 if poly else 2) + 3
     # default launch shapes; the last template argument is the variant flag
     # (off: no speed limits, features in the EV frame at t)
     var = int(bool(p.get("v_limits", 0) or p.get("feature_frame", 0)))
     shape = {16: "<16,8,4,4,%d,0>", 32: "<32,16,4,4,%d,0>", 64: "<64,32,1,16,%d,8>"}[W] % var
     if fused:
-        # [0] grid build, [1] the fused trajectory-and-check kernel
-        fname = "fused_kernel" + shape
+        # [0] grid build, [1] the trajectory kernel with the windowed check
+        fshape = {16: "<16,8,4,4,%d,0,16,4>", 32: "<32,16,4,5,%d,5,8,4>", 64: "<64,32,1,16,%d,12,8,4>"}[W] % var
+        fname = "fused_kernel" + fshape
         fps = res["fma_t"] / (collide_ms / 1e3)
+        rolled = res["rolled"] if res["rolled"] > 0 else float(N) * T * K
+        fma_rolled = rolled * (W * W + 10 * W)
+        check = {}
+        if res["states"] > 0:
+            check = {"candidate_tests_per_state": res["cand_tests"] / res["states"],
+                     "states_checked_per_plan_step": res["states"] / K,
+                     "candidate_tests_per_s": res["cand_tests"] / (collide_ms / 1e3)}
         roofline = {"bound": "alu", "kernel": fname, "achieved": fps / 1e12, "peak": peak / 1e12,
                     "unit": "T FP32-FMA/s", "frac": fps / peak, "traffic": profiled_traffic(fname, args.workload),
                     "peak_basis": peak_basis, "peak_measured": fma_measured,
-                    "work": "MLP FMAs (W^2 + 10 W) per control step of a sample up to its first collision "
-                            "(the kernel stops each sample at most two steps later); the binned check's "
-                            "candidate tests in the same kernel are not counted",
+                    "work": "MLP FMAs (W^2 + 10 W) per control step of a sample up to its first collision; "
+                            "the kernel rolls a sample out to the end of the window (8 states at width 64) holding its first "
+                            "collision (rolled_steps_*) and checks the window's states itself (its candidate "
+                            "tests are not counted as work)",
+                    "rolled_steps_per_plan_step": rolled / K,
+                    "rolled_steps_of_all": rolled / (float(N) * T * K),
+                    "rolled_steps_achieved": fma_rolled / (collide_ms / 1e3) / 1e12,
+                    "rolled_steps_frac": fma_rolled / (collide_ms / 1e3) / peak,
                     "kernel_ms_per_step": collide_ms / K,
+                    "windowed_check": check,
                     "other": {"bin_build_kernel": {"ms_per_step": traj_ms / K}},
                     "dominant": fname}
     elif binned:
@@ -554,7 +578,7 @@ def run_npp(args):
                        "l2": "flushed (256 MiB write) between timed steps",
                        "timing": "sum of per-step CUDA-event durations (events captured in the "
                                  "step graph, replayed on the launching stream)"},
-            "roofline": roofline, "e2e": e2e, "gpu_launches": (6 if binned and not fused else 5) * K,
+            "roofline": roofline, "e2e": e2e, "gpu_launches": launches_per_step * K,
             "clocks": ck, "options": options,
             "free_fraction": float(np.mean(res["free"])),
             "waypoints_reached": res["waypoints_reached"], "infeasible_steps": res["n_infeasible"]}

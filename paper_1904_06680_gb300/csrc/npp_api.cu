@@ -255,14 +255,13 @@ static npp_status run_chunked(npp_handle* h, RolloutArgs& a, cudaStream_t s, int
     return NPP_OK;
 }
 
-npp_status run_rollout(npp_handle* h, RolloutArgs& a, cudaStream_t s, bool allow_fused, bool* fused)
+npp_status run_rollout(npp_handle* h, RolloutArgs& a, cudaStream_t s, bool no_records)
 {
     // no rows are stored: every collision kernel recomputes them from the
     // stored states
     a.coefA = nullptr;
     a.coefB = nullptr;
     a.work = h->d_work;
-    *fused = false;
     if (h->timing) h->last_chunks = 1;
     if (h->fp_faces > 0) {
         // general footprint: grids sized by its radius (side stream, as
@@ -290,13 +289,17 @@ npp_status run_rollout(npp_handle* h, RolloutArgs& a, cudaStream_t s, bool allow
     // automatic choice (measured on GB300, course workload): few samples ->
     // items checked by 4 warps on point slices; medium -> 2 warps; many
     // samples -> one warp per item keeps enough items in flight; many points
-    // -> spatial binning, fused into the trajectory kernel unless the caller
-    // wants every sample's records
+    // -> spatial binning; at width 64 checked window by window inside the
+    // trajectory kernel unless the caller wants every sample's records
+    // (measured at N = 65536, T = 100, M = 8192: 2.72 ms per plan step
+    // against 3.83 in two kernels and 3.31 in two step chunks; at width 32,
+    // T = 40 the two kernels stay faster, 0.258 against 0.311 ms)
     const int v = h->collide_variant >= 0 ? h->collide_variant
                 : (binned_auto(a.M, a.N) ? COLLIDE_BINNED : (a.N <= 8192 ? 3 : (a.N <= 32768 ? 4 : 2)));
     if (v == COLLIDE_BINNED) {
         if (h->timing) CUDA_TRY(h, record_event(h->ev[0], s));
-        if (!(allow_fused && h->fuse)) {
+        const bool fuse = no_records && (h->fuse == 1 || (h->fuse < 0 && h->cfg.width == 64));
+        if (!fuse) {
             if (h->timing) {
                 // measurement counters (candidate tests, states checked,
                 // sample-steps rolled out)
@@ -310,7 +313,7 @@ npp_status run_rollout(npp_handle* h, RolloutArgs& a, cudaStream_t s, bool allow
             CUDA_TRY(h, cudaStreamWaitEvent(h->side, h->fork_ev, 0));
             CUDA_TRY(h, build_bins(a, h->cfg.half_len, h->cfg.half_wid, h->cfg.c_off, h->d_bins, h->side));
             CUDA_TRY(h, cudaEventRecord(h->join_ev, h->side));
-            const int K = chunk_count(h, a, allow_fused);
+            const int K = chunk_count(h, a, no_records);
             if (K > 1) return run_chunked(h, a, s, K);
             CUDA_TRY(h, launch_traj(h, a, s));
             if (h->timing) CUDA_TRY(h, record_event(h->ev[1], s));
@@ -320,13 +323,17 @@ npp_status run_rollout(npp_handle* h, RolloutArgs& a, cudaStream_t s, bool allow
             if (h->timing) CUDA_TRY(h, record_event(h->ev[2], s));
             return NPP_OK;
         }
-        // fused: the grids first, then the trajectories with the check
-        // inside (timing: [0] the grid build, [1] the fused kernel)
+        // fused: the grids first, then the trajectories with the windowed
+        // check inside (timing: [0] the grid build, [1] the fused kernel)
+        if (h->timing) {
+            CUDA_TRY(h, cudaMemsetAsync(h->d_counts, 0, 4 * sizeof(unsigned long long), s));
+            a.counts = h->d_counts;
+        }
         CUDA_TRY(h, build_bins(a, h->cfg.half_len, h->cfg.half_wid, h->cfg.c_off, h->d_bins, s));
         if (h->timing) CUDA_TRY(h, record_event(h->ev[1], s));
         CUDA_TRY(h, launch_fused(h, a, s));
+        a.counts = nullptr;
         if (h->timing) CUDA_TRY(h, record_event(h->ev[2], s));
-        *fused = true;
         return NPP_OK;
     }
     // points beyond shared memory: point-sliced kernel on an L2-resident copy
@@ -352,16 +359,6 @@ npp_status run_rollout(npp_handle* h, RolloutArgs& a, cudaStream_t s, bool allow
     return NPP_OK;
 }
 
-cudaError_t launch_winner_epilogue(const npp_handle* h, const RolloutArgs& a, const EpilogueArgs& e, bool fused,
-                                   cudaStream_t s)
-{
-    if (!fused) return launch_epilogue(e, s);
-    switch (h->cfg.width) {
-    case 16: return launch_reroll_w16(a, e, s);
-    case 32: return launch_reroll_w32(a, e, s);
-    default: return launch_reroll_w64(a, e, s);
-    }
-}
 
 static SamplerKey make_key(uint64_t seed, uint32_t t_index, uint32_t stream_id)
 {
@@ -448,7 +445,7 @@ npp_status npp_create(npp_handle** out, const npp_config* cfg, int32_t device)
     npp_handle* h = new npp_handle();
     h->cfg = *cfg;
     h->collide_variant = -1;
-    h->fuse = false;
+    h->fuse = -1;
     h->chunks = 0;
     h->last_chunks = 1;
     h->loop_restarts = 1;
@@ -550,9 +547,8 @@ static npp_status plan_step_impl(npp_handle* h, const npp_state* state, const np
     a.jfree = h->d_jfree;
     a.best_key = h->d_key;
     CUDA_TRY(h, cudaMemsetAsync(h->d_key, 0xff, sizeof(unsigned long long), s));
-    bool fused = false;
     const bool records = out->sample_traj != nullptr || out->sample_ctrl != nullptr;
-    if ((st = run_rollout(h, a, s, !records, &fused)) != NPP_OK) return st;
+    if ((st = run_rollout(h, a, s, !records)) != NPP_OK) return st;
 
     EpilogueArgs e;
     memset(&e, 0, sizeof e);
@@ -568,7 +564,7 @@ static npp_status plan_step_impl(npp_handle* h, const npp_state* state, const np
     e.params = out->params;
     e.controls = out->controls;
     e.trajectory = out->trajectory;
-    CUDA_TRY(h, launch_winner_epilogue(h, a, e, fused, s));
+    CUDA_TRY(h, launch_epilogue(e, s));
     if (h->timing) CUDA_TRY(h, record_event(h->ev[3], s));
     return NPP_OK;
 }
@@ -698,8 +694,7 @@ npp_status npp_rollout_params(npp_handle* h, const npp_state* state, const npp_g
     a.ctrl = sample_ctrl_dev ? reinterpret_cast<float2*>(sample_ctrl_dev) : h->d_ctrl;
     a.jfree = h->d_jfree;
     a.best_key = nullptr;
-    bool fused = false;
-    if ((st = run_rollout(h, a, s, !sample_traj_dev && !sample_ctrl_dev, &fused)) != NPP_OK) return st;
+    if ((st = run_rollout(h, a, s, !sample_traj_dev && !sample_ctrl_dev)) != NPP_OK) return st;
     if (h->timing) CUDA_TRY(h, record_event(h->ev[3], s));
     return NPP_OK;
 }
@@ -766,8 +761,8 @@ npp_status npp_set_option(npp_handle* h, const char* name, int32_t value)
         return NPP_OK;
     }
     if (std::strcmp(name, "fuse") == 0) {
-        if (value != 0 && value != 1) return fail(h, NPP_INVALID_ARG, "fuse is 0 or 1");
-        h->fuse = value != 0;
+        if (value < -1 || value > 1) return fail(h, NPP_INVALID_ARG, "fuse is -1, 0 or 1");
+        h->fuse = value;
         return NPP_OK;
     }
     if (std::strcmp(name, "chunks") == 0) {

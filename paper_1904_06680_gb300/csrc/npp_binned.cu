@@ -51,16 +51,9 @@ __global__ void __launch_bounds__(BIN_THREADS) bin_build_kernel(const RolloutArg
 // collision changes nothing; it replaces one chain of two dependent loads
 // per step (cell bounds, then candidates) by one per chunk.
 constexpr int BINNED_WARPS = 8;
-constexpr int BIN_SB = 4;                  // steps per chunk
-constexpr int BIN_GS = 32 / BIN_SB;        // lanes per step
-constexpr int BIN_R = 8;                   // candidates loaded ahead per lane (64 per step)
-
-__device__ __forceinline__ bool inside_rows(const float4& A, const float2& B, float2 p)
-{
-    const float xi = fmaf(A.x, p.x, fmaf(A.y, p.y, A.z));
-    const float et = fmaf(A.w, p.x, fmaf(B.x, p.y, B.y));
-    return !(((__float_as_uint(xi) | __float_as_uint(et)) >> 30) & 1u);
-}
+constexpr int BIN_SB = 32 / BIN_ITEM_LANES; // steps per chunk
+constexpr int BIN_GS = BIN_ITEM_LANES;      // lanes per step
+constexpr int BIN_R = 8;                    // candidates loaded ahead per lane (64 per step)
 
 __global__ void __launch_bounds__(BINNED_WARPS * 32, 5) collide_binned_kernel(const RolloutArgs a)
 {
@@ -91,37 +84,8 @@ __global__ void __launch_bounds__(BINNED_WARPS * 32, 5) collide_binned_kernel(co
             // the rectangle lies in the disk of radius reach around the
             // reference point (reach covers the centre offset)
             const float4 z = ok ? a.traj[(size_t)h * N + n] : make_float4(0.f, 0.f, 0.f, 0.f);
-            float4 ca;
-            float2 cb;
-            rows_of_state(a.c, z, ca, cb);
-            CandRows cr = {};
-            if (ok) cr = cand_rows(g.cell_start + (size_t)h * BIN_CS_STRIDE, g, z.x, z.y, g.reach);
-            const float2* pts = g.pts + (size_t)(ok ? h : 0) * M;
-            const int total = cr.total;
-            float2 pr[BIN_R];
-#pragma unroll
-            for (int r = 0; r < BIN_R; ++r) {
-                const int k = gl + r * BIN_GS;
-                pr[r] = k < total ? pts[cr.index(k)] : make_float2(0.f, 0.f);
-            }
-            bool inside = false;
             nstate += (ok && gl == 0) ? 1u : 0u;
-#pragma unroll
-            for (int r = 0; r < BIN_R; ++r)
-                if (gl + r * BIN_GS < total) {
-                    inside |= inside_rows(ca, cb, pr[r]);
-                    ++ntest;
-                }
-            constexpr int PRE = BIN_R * BIN_GS;
-            const int rest = total > PRE ? (total - PRE + BIN_GS - 1) / BIN_GS : 0;
-            const int maxr = __reduce_max_sync(FULL, rest);
-            for (int it = 0; it < maxr; ++it) {
-                const int k = PRE + it * BIN_GS + gl;
-                if (it < rest && k < total) {
-                    inside |= inside_rows(ca, cb, pts[cr.index(k)]);
-                    ++ntest;
-                }
-            }
+            const bool inside = binned_item_inside<BIN_R>(a.c, g, z, h, ok, gl, ntest);
             const unsigned bal = __ballot_sync(FULL, inside);
             unsigned steps_hit = 0;
 #pragma unroll

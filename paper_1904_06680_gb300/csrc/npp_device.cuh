@@ -509,15 +509,13 @@ struct EpilogueArgs {
 cudaError_t launch_traj_w16(const RolloutArgs& a, cudaStream_t s, int variant);
 cudaError_t launch_traj_w32(const RolloutArgs& a, cudaStream_t s, int variant);
 cudaError_t launch_traj_w64(const RolloutArgs& a, cudaStream_t s, int variant);
-// trajectories with the binned collision check fused in (a.bins set): each
-// sample stops at its first collision; writes costs, first hits and the key
+// trajectories with the binned collision check done window by window by
+// the trajectory warps (a.bins set): each sample stops within one window
+// of its first collision; writes costs, first hits, the key and the states
+// and controls up to that window
 cudaError_t launch_fused_w16(const RolloutArgs& a, cudaStream_t s, int variant);
 cudaError_t launch_fused_w32(const RolloutArgs& a, cudaStream_t s, int variant);
 cudaError_t launch_fused_w64(const RolloutArgs& a, cudaStream_t s, int variant);
-// winner epilogue that re-rolls the winner (no per-sample records needed)
-cudaError_t launch_reroll_w16(const RolloutArgs& a, const EpilogueArgs& e, cudaStream_t s);
-cudaError_t launch_reroll_w32(const RolloutArgs& a, const EpilogueArgs& e, cudaStream_t s);
-cudaError_t launch_reroll_w64(const RolloutArgs& a, const EpilogueArgs& e, cudaStream_t s);
 cudaError_t launch_collide_resident(const RolloutArgs& a, cudaStream_t s, int variant);
 cudaError_t launch_collide_global(const RolloutArgs& a, cudaStream_t s);
 int collide_global_blocks_per_sm();

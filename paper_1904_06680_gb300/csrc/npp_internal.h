@@ -40,7 +40,8 @@ struct npp_handle {
                                          // (0..4 brute force, 5 spatially binned)
     int collide_active;                  // variant used for the current launch
     int traj_variant;                    // trajectory launch shape (0..3)
-    bool fuse;                           // binned check fused into the trajectory kernel
+    int fuse;                            // binned check inside the trajectory kernel: -1 automatic
+                                         // (at width 64), 0 off, 1 on
     int chunks;                          // step chunks of the binned path when no per-sample records
                                          // are wanted (0: automatic, 1: one launch each)
     int last_chunks;                     // chunks of the last timed plan step (its stage events)
@@ -98,14 +99,12 @@ npp_status fail(npp_handle* h, npp_status s, const char* fmt, ...);
 cudaError_t stage_times(const cudaEvent_t* ev, const cudaEvent_t* cev, int nch, float t[4]);
 
 // trajectory + collision kernels of one plan step (fills workspace pointers,
-// the persistent grid and the work-counter reset); with the binned check and
-// allow_fused the two are one kernel that keeps no per-sample records
-// (*fused reports it: the winner epilogue must then re-roll the winner)
-npp_status run_rollout(npp_handle* h, npp::RolloutArgs& a, cudaStream_t s, bool allow_fused, bool* fused);
-
-// the winner epilogue matching run_rollout's path
-cudaError_t launch_winner_epilogue(const npp_handle* h, const npp::RolloutArgs& a, const npp::EpilogueArgs& e,
-                                   bool fused, cudaStream_t s);
+// the persistent grid and the work-counter reset).  no_records: the caller
+// needs no sample's records beyond the winner's, so the binned check may
+// run in step chunks or inside the trajectory kernel ("fuse"), which stop
+// rolling a sample out after its first collision (the winner's rows, up to
+// its first collision, are always complete)
+npp_status run_rollout(npp_handle* h, npp::RolloutArgs& a, cudaStream_t s, bool no_records);
 
 #define CUDA_TRY(h, call)                                                                  \
     do {                                                                                   \

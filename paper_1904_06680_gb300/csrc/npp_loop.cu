@@ -263,8 +263,7 @@ npp_status enqueue_step(npp_loop* L, uint64_t seed)
     a.costs = L->d_costs;
     a.first_hit = L->d_fh;
     CUDA_TRY(h, cudaMemsetAsync(h->d_key, 0xff, sizeof(unsigned long long), s));
-    bool fused = false;
-    npp_status st = run_rollout(h, a, s, true, &fused);
+    npp_status st = run_rollout(h, a, s, true);
     if (st != NPP_OK) return st;
     EpilogueArgs e;
     memset(&e, 0, sizeof e);
@@ -279,7 +278,7 @@ npp_status enqueue_step(npp_loop* L, uint64_t seed)
     e.controls = L->d_controls;
     e.trajectory = L->d_trajectory;
     e.dyn = L->d_dyn;
-    CUDA_TRY(h, launch_winner_epilogue(h, a, e, fused, s));
+    CUDA_TRY(h, launch_epilogue(e, s));
     // restart rounds: the winner so far is sample 0 (warm start, valid even
     // at the loop's first step), every other sample a perturbation of it on
     // the round's own Philox stream; the winner's parameters, controls and
@@ -293,8 +292,7 @@ npp_status enqueue_step(npp_loop* L, uint64_t seed)
         ar.warm = L->d_warm;
         ar.warm_force = 1;
         CUDA_TRY(h, cudaMemsetAsync(h->d_key, 0xff, sizeof(unsigned long long), s));
-        bool fr = false;
-        st = run_rollout(h, ar, s, true, &fr);
+        st = run_rollout(h, ar, s, true);
         if (st != NPP_OK) {
             h->timing = timing;
             return st;
@@ -302,7 +300,7 @@ npp_status enqueue_step(npp_loop* L, uint64_t seed)
         EpilogueArgs er = e;
         er.prop = ar.prop;
         er.warm_force = 1;
-        cudaError_t ce = launch_winner_epilogue(h, ar, er, fr, s);
+        cudaError_t ce = launch_epilogue(er, s);
         if (ce != cudaSuccess) {
             h->timing = timing;
             return fail(h, NPP_CUDA_ERROR, "restart epilogue: %s", cudaGetErrorString(ce));

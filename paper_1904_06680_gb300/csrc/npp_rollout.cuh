@@ -342,39 +342,60 @@ __device__ __forceinline__ int discard_step(const int* vfirst, long long n, int 
     return (hv >= 0 && (fh < 0 || hv < fh)) ? hv : fh;
 }
 
-// Binned check of one state for the G lanes of each group of a warp (every
-// lane of the warp calls it; dead groups pass alive = false): the candidates
-// of the at most five cell rows the state's disk overlaps, strided over the
-// group's lanes, the per-point test of the brute-force kernels.  Returns,
-// uniformly over the group, whether some point is inside.
-template <int G>
-__device__ __forceinline__ bool group_collides(const BinView& bv, int h, float x, float y, const float4& A,
-                                               const float2& B, bool alive, int gl)
+// One state of one sample against one step's grid, checked by an 8-lane
+// group of a warp (four such items per warp at a time): the candidates of
+// the at most five cell rows the state's disk overlaps, strided over the
+// group's lanes, each lane first issuing the loads of up to R candidates and
+// then testing them with the brute-force kernels' per-point test (the rest,
+// rarely any, one by one).  Every lane of the warp calls it (warp-wide
+// reduction inside); the lanes of an item that is not ok test nothing.
+// Returns the lane's verdict (the item's is the OR over its 8 lanes) and
+// counts the lane's candidate tests in ntest.
+constexpr int BIN_ITEM_LANES = 8;
+
+__device__ __forceinline__ bool inside_rows(const float4& A, const float2& B, float2 p)
 {
+    const float xi = fmaf(A.x, p.x, fmaf(A.y, p.y, A.z));
+    const float et = fmaf(A.w, p.x, fmaf(B.x, p.y, B.y));
+    return !(((__float_as_uint(xi) | __float_as_uint(et)) >> 30) & 1u);
+}
+
+template <int R>
+__device__ __forceinline__ bool binned_item_inside(const DevCfg& c, const BinView& g, const float4& z, int h,
+                                                   bool ok, int gl, unsigned& ntest)
+{
+    constexpr int L = BIN_ITEM_LANES;
+    float4 ca;
+    float2 cb;
+    rows_of_state(c, z, ca, cb);
     CandRows cr = {};
-    if (alive) cr = cand_rows(bv.cell_start + (size_t)h * BIN_CS_STRIDE, bv, x, y, bv.reach);
+    if (ok) cr = cand_rows(g.cell_start + (size_t)h * BIN_CS_STRIDE, g, z.x, z.y, g.reach);
+    const float2* pts = g.pts + (size_t)(ok ? h : 0) * g.M;
     const int total = cr.total;
-    const int iters = (total + G - 1) / G;
-    const int maxit = __reduce_max_sync(FULL, iters);
-    const float2* pts = bv.pts + (size_t)h * bv.M;
-    const unsigned gmask = G == 32 ? FULL : (((1u << G) - 1u) << ((threadIdx.x & 31) / G * G));
-    bool hit = false;
-    for (int it = 0; it < maxit; ++it) {
-        const int k = it * G + gl;
-        bool inside = false;
-        if (k < total) {
-            const float2 p = pts[cr.index(k)];
-            const float xi = fmaf(A.x, p.x, fmaf(A.y, p.y, A.z));
-            const float et = fmaf(A.w, p.x, fmaf(B.x, p.y, B.y));
-            inside = !(((__float_as_uint(xi) | __float_as_uint(et)) >> 30) & 1u);
-        }
-        // every lane of the warp takes part in both votes (no short circuit)
-        const unsigned bal = __ballot_sync(FULL, inside);
-        hit = hit || (bal & gmask) != 0u;
-        const bool done = hit || (it + 1) * G >= total;
-        if (__all_sync(FULL, done)) break;
+    float2 pr[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int k = gl + r * L;
+        pr[r] = k < total ? pts[cr.index(k)] : make_float2(0.f, 0.f);
     }
-    return hit;
+    bool inside = false;
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+        if (gl + r * L < total) {
+            inside |= inside_rows(ca, cb, pr[r]);
+            ++ntest;
+        }
+    constexpr int PRE = R * L;
+    const int rest = total > PRE ? (total - PRE + L - 1) / L : 0;
+    const int maxr = __reduce_max_sync(FULL, rest);
+    for (int it = 0; it < maxr; ++it) {
+        const int k = PRE + it * L + gl;
+        if (it < rest && k < total) {
+            inside |= inside_rows(ca, cb, pts[cr.index(k)]);
+            ++ntest;
+        }
+    }
+    return inside;
 }
 
 // ------------------------------------------------------------------ bins
@@ -490,7 +511,7 @@ struct TrajJob {
     long long coef_base;
     float* jfree;
     int* vfirst;                  // first speed-violating step per sample (speed limits on), or null
-    const BinView* bins;          // fused check (traj_sample_fused)
+    const BinView* bins;          // grids of the windowed check (traj_sample_windowed)
     ulonglong2* w2s;              // this lane's slot of the shared W2 quads (LaneNet KSQ > 0), or null
     float* stage;                 // this thread's slot 0 of a staging area (stride stage_th), or null
     // One chunk of the horizon: steps h_lo .. h_hi - 1 from the stored state
@@ -744,221 +765,99 @@ __device__ __forceinline__ void traj_sample(const DevCfg& c, const TrajJob& job,
     }
 }
 
-// ------------------------------------------------------------------ fused, pipelined check
-// cp.async copies of 4 or 8 bytes from global to shared memory; with pred
-// false nothing is read and zeros are written.
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem, bool pred)
+// ------------------------------------------------------------------ fused: windowed check
+// The rollout of sample n with the binned check done by the trajectory
+// warp itself, one window of CW states at a time: the group rolls its
+// sample through steps h0 .. h0 + CW - 1 (storing the states and controls
+// the caller asked for, and the states in the warp's shared window), then
+// the warp checks the window's states of every group still alive, four
+// (group, state) items at a time with the binned check's item code
+// (binned_item_inside: the same grids, rows and per-point test, so the same
+// flags), the earliest colliding state of a group ending its sample.  A
+// sample is therefore rolled out at most CW - 1 steps past its first
+// collision, its parameters generated once, and the loop ends once no group
+// of the warp is alive.  VAR as in traj_sample (a sample is discarded at its
+// first state h >= 1 whose speed is out of range, unless an earlier state
+// collides).  wnd: the warp's [32/G][CW] states; steps counts the control
+// steps the warp computed (lane 0 of each valid group), ntest / nstate the
+// check's candidate tests and states.
+template <int W, int G, int STAGE_TH, bool VAR, int KSQ, int CW, int R>
+__device__ __forceinline__ FusedOut traj_sample_windowed(const DevCfg& c, const TrajJob& job, int n, bool valid,
+                                                         int gl, float* hrow, float4* wnd, unsigned& steps,
+                                                         unsigned& ntest, unsigned& nstate)
 {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(gmem), "r"(pred ? 4 : 0)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool pred)
-{
-    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(gmem), "r"(pred ? 8 : 0)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int PENDING>
-__device__ __forceinline__ void cp_async_wait()
-{
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory");
-}
-
-// candidates of a state copied ahead of its test (per group; beyond them the
-// test reads the rest directly)
-constexpr int FUSED_PREFETCH = 64;
-
-// Shared memory of one group's pipelined check: the cell-run bounds of the
-// two states in flight (entries 0..4 the first sorted point of each of the
-// at most five cell rows of the query, 5..9 the end of each row; zeros for
-// rows beyond the query), their inequality rows (kept here rather than in
-// registers, which the network's weights fill) and the candidate points of
-// the state being checked (the first KMAX * G candidates, KMAX per lane).
-template <int G, int KMAX>
-struct PipeSlot {
-    int4 cs[2][3];
-    float4 rA[2];             // scaled inequality rows of the two states in flight
-    float2 rB[2];
-    float2 pt[KMAX * G];
-};
-
-// Stage 1, state h at (x, y): copies of its cell-run bounds into cs.
-template <int G>
-__device__ __forceinline__ void pipe_runs(const BinView& bv, int h, float x, float y, bool live, int gl,
-                                          int* cs)
-{
-    const int* tab = bv.cell_start + (size_t)h * BIN_CS_STRIDE;
-    const int ix0 = bin_cell(x - bv.reach, bv), ix1 = bin_cell(x + bv.reach, bv);
-    const int iy0 = bin_cell(y - bv.reach, bv), iy1 = bin_cell(y + bv.reach, bv);
-#pragma unroll
-    for (int t = 0; t < (2 * BIN_MAX_ROWS + G - 1) / G; ++t) {
-        const int j = gl + t * G;
-        if (j < 2 * BIN_MAX_ROWS) {
-            const int r = j < BIN_MAX_ROWS ? j : j - BIN_MAX_ROWS;
-            const bool ok = live && iy0 + r <= iy1;
-            const int col = j < BIN_MAX_ROWS ? ix0 : ix1 + 1;
-            cp_async4(cs + j, ok ? tab + (iy0 + r) * BIN_DIM + col : tab, ok);
-        }
-    }
-}
-
-__device__ __forceinline__ CandRows runs_from(const int* cs)
-{
-    const int4 a = reinterpret_cast<const int4*>(cs)[0];
-    const int4 b = reinterpret_cast<const int4*>(cs)[1];
-    const int2 c2 = reinterpret_cast<const int2*>(cs)[4];
-    const int beg[BIN_MAX_ROWS] = { a.x, a.y, a.z, a.w, b.x };
-    const int end[BIN_MAX_ROWS] = { b.y, b.z, b.w, c2.x, c2.y };
-    CandRows cr;
-    int acc = 0;
-#pragma unroll
-    for (int r = 0; r < BIN_MAX_ROWS; ++r) {
-        cr.b[r] = beg[r];
-        acc += end[r] - beg[r];
-        cr.e[r] = acc;
-    }
-    cr.total = acc;
-    return cr;
-}
-
-// Stage 2, state h: from its cell-run bounds (complete and visible to the
-// group), copies of its first KMAX * G candidates into pt (each lane its
-// own KMAX); returns the candidate count.
-template <int G, int KMAX>
-__device__ __forceinline__ int pipe_points(const BinView& bv, int h, const int* cs, float2* pt, int gl)
-{
-    const CandRows cr = runs_from(cs);
-    const float2* pts = bv.pts + (size_t)h * bv.M;
-#pragma unroll
-    for (int i = 0; i < KMAX; ++i) {
-        const int k = gl + i * G;
-        const bool ok = k < cr.total;
-        cp_async8(pt + i * G + gl, ok ? pts + cr.index(k) : pts, ok);
-    }
-    return cr.total;
-}
-
-// Stage 3, state h (rows A, B): the per-point test of the brute-force
-// kernels on the copied candidates, then (rarely) on the candidates beyond
-// KMAX * G read directly.  Every lane of the warp calls it; returns,
-// uniformly over the group, whether some candidate is inside.
-template <int G, int KMAX>
-__device__ __forceinline__ bool pipe_test(const BinView& bv, int h, const int* cs, const float2* pt, int total,
-                                          const float4& A, const float2& B, int gl)
-{
-    const unsigned gmask = G == 32 ? FULL : (((1u << G) - 1u) << ((threadIdx.x & 31) / G * G));
-    bool inside = false;
-#pragma unroll
-    for (int i = 0; i < KMAX; ++i) {
-        if (gl + i * G < total) {
-            const float2 p = pt[i * G + gl];
-            const float xi = fmaf(A.x, p.x, fmaf(A.y, p.y, A.z));
-            const float et = fmaf(A.w, p.x, fmaf(B.x, p.y, B.y));
-            inside |= !(((__float_as_uint(xi) | __float_as_uint(et)) >> 30) & 1u);
-        }
-    }
-    bool hit = (__ballot_sync(FULL, inside) & gmask) != 0u;
-    constexpr int PRE = KMAX * G;
-    if (__any_sync(FULL, total > PRE && !hit)) {
-        const CandRows cr = runs_from(cs);
-        const float2* pts = bv.pts + (size_t)h * bv.M;
-        const int iters = (!hit && total > PRE) ? (total - PRE + G - 1) / G : 0;
-        const int maxit = __reduce_max_sync(FULL, iters);
-        for (int it = 0; it < maxit; ++it) {
-            const int k = PRE + it * G + gl;
-            bool in2 = false;
-            if (it < iters && k < total) {
-                const float2 p = pts[cr.index(k)];
-                const float xi = fmaf(A.x, p.x, fmaf(A.y, p.y, A.z));
-                const float et = fmaf(A.w, p.x, fmaf(B.x, p.y, B.y));
-                in2 = !(((__float_as_uint(xi) | __float_as_uint(et)) >> 30) & 1u);
-            }
-            // every lane of the warp takes part in the vote (no short
-            // circuit: groups that already hit still vote)
-            const unsigned bal = __ballot_sync(FULL, in2);
-            hit = hit || (bal & gmask) != 0u;
-        }
-    }
-    return hit;
-}
-
-// The rollout of sample n with the binned collision check fused in and
-// pipelined one step behind the network: at the top of step h the copies
-// of state h's cell-run bounds are issued and, from the bounds of state
-// h - 1 (issued a step earlier), the copies of its candidate points; the
-// network of step h then runs while they are in flight, and state h - 1 is
-// tested after it.  A sample therefore computes at most two control steps
-// past its first collision, and the loop ends once every group of the warp
-// is discarded; nothing per step is stored.  The decisions are those of
-// the binned check over stored states (same grids, rows and per-point
-// test), so the first collision and cost equal the two-kernel path's.
-// slot: the group's PipeSlot; VAR as in traj_sample (speed limits discard
-// at the first state h >= 1 out of range, unless an earlier state collides).
-template <int W, int G, int KMAX, bool VAR>
-__device__ __forceinline__ FusedOut traj_sample_fused(const DevCfg& c, const TrajJob& job, int n, bool valid,
-                                                      int gl, float* hrow, PipeSlot<G, KMAX>* slot)
-{
+    constexpr int NG = 32 / G;                 // groups (samples) per warp
+    constexpr int SPI = 4 / NG;                // states of a group per check round
+    static_assert(NG <= 4 && 32 % G == 0, "at most four groups per warp");
+    const int lane = threadIdx.x & 31, grp = lane / G;
     const GoalEV g = goal_ev(job.si);
-    LaneNet<W, G> net;
-    load_net<W, G, 0>(net, job, n, valid, gl);
+    LaneNet<W, G, KSQ> net;
+    load_net<W, G, STAGE_TH, KSQ>(net, job, n, valid, gl);
     const BinView& bv = *job.bins;
 
     float x = 0.f, y = 0.f, ph = 0.f, v = job.si.v0, ap0 = job.si.ap0, ap1 = job.si.ap1, E = 0.f;
     const int T = job.T;
     const float invT = 1.0f / (float)T;
+    const bool writer = valid && gl == 0;
+    const long long rec = n;
+    int vbad = -1;
     float rem = (float)T;
     bool alive = valid;
-    int fh = -1, vdisc = -1;
-    int total_p = 0;
-    for (int h = 0; h <= T + 1; ++h) {
-        float sp = 0.f, cp = 1.f;
-        __syncwarp();                    // the slots rewritten below were read by the whole group
-        if (h <= T) {
+    int fh = -1;
+    for (int h0 = 0; h0 <= T && __any_sync(FULL, alive); h0 += CW) {
+        const int ns = min(CW, T + 1 - h0);    // states h0 .. h0 + ns - 1
+        for (int j = 0; j < ns; ++j) {
+            const int h = h0 + j;
+            float sp, cp;
             sincos_r(ph, sp, cp);
             if constexpr (VAR) {
-                if (c.vlim && alive && h > 0 && vdisc < 0 && !(v >= c.v_lo && v <= c.v_hi)) vdisc = h;
+                if (c.vlim && h > 0 && vbad < 0 && !(v >= c.v_lo && v <= c.v_hi)) vbad = h;
             }
-            float4 A;
-            float2 B;
-            coef_rows(c, x, y, sp, cp, A, B);
-            if (gl == 0) {
-                slot->rA[h & 1] = A;
-                slot->rB[h & 1] = B;
+            const float4 z = make_float4(x, y, ph, v);
+            if (gl == 0) wnd[grp * CW + j] = z;
+            if (writer && alive && job.traj) job.traj[h * job.rec_stride + rec] = z;
+            if (h < T) {
+                const float2 a = control_step<W, G, VAR, KSQ>(c, net, g, invT, gl, hrow, sp, cp, x, y, ph, v,
+                                                              ap0, ap1, E, rem);
+                if (writer && alive && job.ctrl) job.ctrl[h * job.rec_stride + rec] = a;
+                ++steps;
             }
-            pipe_runs<G>(bv, h, x, y, alive, gl, reinterpret_cast<int*>(slot->cs[h & 1]));
         }
-        cp_async_commit();
-        if (h >= 1) {
-            cp_async_wait<1>();          // bounds of state h - 1 (all but the newest group)
-            __syncwarp();
-            total_p = pipe_points<G, KMAX>(bv, h - 1, reinterpret_cast<const int*>(slot->cs[(h - 1) & 1]),
-                                           slot->pt, gl);
-        }
-        cp_async_commit();
-        if (h < T)
-            control_step<W, G, VAR>(c, net, g, invT, gl, hrow, sp, cp, x, y, ph, v, ap0, ap1, E, rem);
-        if (h >= 1) {
-            cp_async_wait<0>();          // own candidate copies of state h - 1
-            const bool hit = pipe_test<G, KMAX>(bv, h - 1, reinterpret_cast<const int*>(slot->cs[(h - 1) & 1]),
-                                                slot->pt, total_p, slot->rA[(h - 1) & 1],
-                                                slot->rB[(h - 1) & 1], gl);
-            if (alive && hit) {
-                alive = false;
-                fh = h - 1;
-            } else if (alive && vdisc == h) {
-                alive = false;
-                fh = h;
+        __syncwarp();
+        // the window's check: round si0 takes items q = lane / 8 (group
+        // q % NG, state si0 + q / NG), so a group's items come in order
+        const unsigned amask = __ballot_sync(FULL, alive);
+        int first = -1;                        // earliest colliding state of this lane's group (slot)
+        for (int si0 = 0; si0 < ns; si0 += SPI) {
+            const int q = lane / BIN_ITEM_LANES, il = lane % BIN_ITEM_LANES;
+            const int bi = q % NG, si = si0 + q / NG;
+            const bool ok = si < ns && ((amask >> (bi * G)) & 1u) != 0u;
+            const float4 z = ok ? wnd[bi * CW + si] : make_float4(0.f, 0.f, 0.f, 0.f);
+            nstate += (ok && il == 0) ? 1u : 0u;
+            const bool in = binned_item_inside<R>(c, bv, z, h0 + si, ok, il, ntest);
+            const unsigned bal = __ballot_sync(FULL, in);
+            if (first < 0) {
+#pragma unroll
+                for (int qq = 0; qq < 4; ++qq)
+                    if (first < 0 && qq % NG == grp && ((bal >> (qq * BIN_ITEM_LANES)) & 0xFFu) != 0u)
+                        first = si0 + qq / NG;
             }
-            if (!__any_sync(FULL, alive)) break;
+            if (__all_sync(FULL, !alive || first >= 0)) break;
+        }
+        __syncwarp();                          // the window is rewritten next
+        int d = first >= 0 ? h0 + first : -1;
+        if constexpr (VAR) {
+            if (vbad >= 0 && (d < 0 || vbad < d)) d = vbad;
+        }
+        if (alive && d >= 0) {
+            alive = false;
+            fh = d;
         }
     }
-    cp_async_wait<0>();
     FusedOut out;
-    out.first_hit = fh;
+    out.first_hit = valid ? fh : -1;
     out.cost = __int_as_float(0x7f800000);
-    if (alive) out.cost = final_cost(c, g, x, y, ph, v, E, invT);
+    if (valid && alive) out.cost = final_cost(c, g, x, y, ph, v, E, invT);
     return out;
 }
 
@@ -1018,19 +917,33 @@ __global__ void __launch_bounds__(NW * 32, MINB) traj_kernel(const RolloutArgs a
         atomicAdd(a.counts + 2, (unsigned long long)((a.chunk_hi > 0 ? a.chunk_hi : a.T) - a.chunk_lo));
 }
 
-// Trajectories with the binned check fused in: per sample its first
-// collision and cost, folded into the (class, cost, index) minimum.
-template <int W, int G, int NW, int MINB = 1, bool VAR = false>
+// Shared memory a trajectory block needs beyond its hidden rows: the
+// parameter staging (width 32, every weight in registers) or the shared
+// layer-2 quads (KSQ > 0), in bytes.
+template <int W, int G, int NW, int KSQ>
+__host__ __device__ constexpr int traj_stage_bytes()
+{
+    return KSQ > 0 ? NW * 32 * Shape<W, G>::U * KSQ * 16
+         : W == 32 ? LaneNet<W, G>::SLOTS * NW * 32 * (int)sizeof(float) : 0;
+}
+
+// Trajectories with the binned check done window by window by the
+// trajectory warps themselves (traj_sample_windowed; the grids are built
+// before the launch): per sample its first collision and cost, written and
+// folded into the (class, cost, index) minimum; states and controls stored
+// up to the window of a sample's first collision, which holds every row the
+// winner epilogue reads.
+template <int W, int G, int NW, int MINB = 1, bool VAR = false, int KSQ = 0, int CW = 16, int R = 4>
 __global__ void __launch_bounds__(NW * 32, MINB) fused_kernel(const RolloutArgs a)
 {
     constexpr int B = TrajKernel<W, G, NW>::B;
-    constexpr int KMAX = FUSED_PREFETCH / G;
     __shared__ __align__(16) float hx_all[B * W];
-    __shared__ PipeSlot<G, KMAX> slots[B];
-    __shared__ unsigned long long red[NW];
+    // the staging or shared W2 quads of traj_kernel, then each warp's window
+    extern __shared__ __align__(16) float stage_all[];
     const int tid = threadIdx.x;
     const int b = tid / G, gl = tid % G;
     const int n = blockIdx.x * B + b;
+    const bool valid = n < a.N;
     TrajJob job;
     job.si = step_in(a);
     job.key = a.key;
@@ -1040,9 +953,9 @@ __global__ void __launch_bounds__(NW * 32, MINB) fused_kernel(const RolloutArgs 
     job.prop = a.prop;
     job.N = a.N;
     job.T = a.T;
-    job.traj = nullptr;
-    job.ctrl = nullptr;
-    job.rec_stride = 0;
+    job.traj = a.traj;
+    job.ctrl = a.ctrl;
+    job.rec_stride = a.N;
     job.rec_shift = 0;
     job.coefA = nullptr;
     job.coefB = nullptr;
@@ -1050,115 +963,41 @@ __global__ void __launch_bounds__(NW * 32, MINB) fused_kernel(const RolloutArgs 
     job.jfree = nullptr;
     job.vfirst = nullptr;
     job.bins = &a.bins;
-    job.stage = nullptr;
+    job.stage = stage_all + tid;
     job.w2s = nullptr;
-    const bool valid = n < a.N;
-    const FusedOut r = traj_sample_fused<W, G, KMAX, VAR>(a.c, job, n, valid, gl, hx_all + b * W, slots + b);
-    unsigned long long key = ~0ull;
+    if constexpr (KSQ > 0)
+        job.w2s = reinterpret_cast<ulonglong2*>(stage_all) + (size_t)b * (Shape<W, G>::U * KSQ * G) + gl;
+    constexpr int STAGE_TH = (W == 32 && KSQ == 0) ? NW * 32 : 0;
+    float4* wnd = reinterpret_cast<float4*>(reinterpret_cast<char*>(stage_all) + traj_stage_bytes<W, G, NW, KSQ>()) +
+                  (size_t)(tid / 32) * (32 / G) * CW;
+    unsigned steps = 0, ntest = 0, nstate = 0;
+    const FusedOut r = traj_sample_windowed<W, G, STAGE_TH, VAR, KSQ, CW, R>(a.c, job, n, valid, gl,
+                                                                              hx_all + b * W, wnd, steps, ntest,
+                                                                              nstate);
     if (valid && gl == 0) {
+        unsigned long long key;
         if (r.first_hit < 0)
             key = ((unsigned long long)__float_as_uint(r.cost) << 32) | (unsigned)n;
         else
             key = (1ull << 63) | ((unsigned long long)(a.T - r.first_hit) << 32) | (unsigned)n;
-        if (a.costs) a.costs[n] = r.first_hit < 0 ? r.cost : __int_as_float(0x7f800000);
+        if (a.costs) a.costs[n] = r.cost;
         if (a.first_hit) a.first_hit[n] = r.first_hit;
+        // the read skips atomics that cannot win
+        if (a.best_key && key < *reinterpret_cast<volatile unsigned long long*>(a.best_key))
+            atomicMin(a.best_key, key);
     }
+    if (a.counts) {
+        unsigned long long t = ntest, s = nstate;
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        const unsigned long long o = __shfl_xor_sync(FULL, key, off);
-        key = o < key ? o : key;
-    }
-    if ((tid & 31) == 0) red[tid >> 5] = key;
-    __syncthreads();
-    if (tid == 0 && a.best_key) {
-        unsigned long long k = red[0];
-        for (int w = 1; w < NW; ++w) k = red[w] < k ? red[w] : k;
-        atomicMin(a.best_key, k);
-    }
-}
-
-// Winner epilogue for plan steps that keep no per-sample records: one warp
-// decodes the key, writes the summary, re-rolls the winner (every group of
-// the warp computes the same sample; identical writes) into the caller's
-// trajectory and control rows in the EV frame, then moves the rows to the
-// world frame (rows after an infeasible winner's first collision repeat the
-// colliding state, its controls there are zero) and regenerates its
-// parameters (warm start, proposal or isotropic sample).
-template <int W, int G, bool VAR = false>
-__global__ void __launch_bounds__(32) reroll_epilogue_kernel(const RolloutArgs a, const EpilogueArgs e)
-{
-    __shared__ __align__(16) float hrows[32 / G * W];
-    const int lane = threadIdx.x;
-    const StepIn si = step_in(a);
-    SamplerKey skey = a.key;
-    skey.t_index = si.t_index;
-    const unsigned long long key = *e.best_key;
-    const int idx = (int)(key & 0xffffffffull);
-    const bool dead = (key >> 63) != 0;
-    const unsigned hi = (unsigned)((key >> 32) & 0x7fffffffu);
-    const int fh = dead ? e.T - (int)hi : -1;
-    const int last = dead ? fh : e.T;
-    if (lane == 0) {
-        npp_best* o = reinterpret_cast<npp_best*>(e.best);
-        o->best_idx = idx;
-        o->status = dead ? NPP_INFEASIBLE : NPP_OK;
-        o->best_cost = dead ? __int_as_float(0x7f800000) : __uint_as_float(hi);
-        o->first_hit = fh;
-        o->reserved[0] = o->reserved[1] = o->reserved[2] = o->reserved[3] = 0;
-    }
-    TrajJob job;
-    job.si = si;
-    job.key = skey;
-    job.theta = a.theta;
-    job.warm = a.warm;
-    job.prop = a.prop;
-    job.N = a.N;
-    job.T = a.T;
-    job.traj = reinterpret_cast<float4*>(e.trajectory);
-    job.ctrl = reinterpret_cast<float2*>(e.controls);
-    job.rec_stride = 1;
-    job.rec_shift = idx;
-    job.coefA = nullptr;
-    job.coefB = nullptr;
-    job.coef_base = 0;
-    job.jfree = nullptr;
-    job.vfirst = nullptr;
-    job.bins = nullptr;
-    job.stage = nullptr;
-    job.w2s = nullptr;
-    if (e.trajectory || e.controls)
-        traj_sample<W, G, 0, VAR>(a.c, job, idx, true, lane % G, hrows + (lane / G) * W);
-    __syncwarp();
-    float s0, c0;
-    sincosf(si.phi0, &s0, &c0);
-    if (e.trajectory) {
-        float4* tr = reinterpret_cast<float4*>(e.trajectory);
-        const float4 zl = tr[last];
-        __syncwarp();                          // every lane has zl before rows change
-        for (int h = lane; h <= e.T; h += 32) {
-            const float4 z = h <= last ? tr[h] : zl;
-            float4 w;
-            w.x = si.x0 + c0 * z.x - s0 * z.y;
-            w.y = si.y0 + s0 * z.x + c0 * z.y;
-            w.z = si.phi0 + z.z;
-            w.w = z.w;
-            tr[h] = w;
+        for (int off = 16; off > 0; off >>= 1) {
+            t += __shfl_xor_sync(FULL, t, off);
+            s += __shfl_xor_sync(FULL, s, off);
         }
-    }
-    if (e.controls)
-        for (int h = lane; h < e.T; h += 32)
-            if (h >= last) reinterpret_cast<float2*>(e.controls)[h] = make_float2(0.f, 0.f);
-    if (e.params) {
-        if (a.warm && idx == 0 && si.warm_ok) {
-            if (e.params != a.warm)
-                for (int i = lane; i < e.n_theta; i += 32) e.params[i] = a.warm[i];
-        } else {
-            for (int q = lane; 4 * q < e.n_theta; q += 32) {
-                const float4 v = sample_quad_mixed_tail(skey, a.prop, (uint32_t)q, (uint32_t)idx, e.n_theta);
-                const float vv[4] = { v.x, v.y, v.z, v.w };
-                for (int j = 0; j < 4 && 4 * q + j < e.n_theta; ++j) e.params[4 * q + j] = vv[j];
-            }
+        if ((tid & 31) == 0) {
+            atomicAdd(a.counts, t);
+            atomicAdd(a.counts + 1, s);
         }
+        if (valid && gl == 0) atomicAdd(a.counts + 2, (unsigned long long)steps);
     }
 }
 
@@ -1704,28 +1543,22 @@ cudaError_t launch_traj(const RolloutArgs& a, cudaStream_t stream)
 {
     using K = TrajKernel<W, G, NW>;
     const int grid = (a.N + K::B - 1) / K::B;
-    const int smem = KSQ > 0 ? K::THREADS * Shape<W, G>::U * KSQ * 16
-                   : W == 32 ? LaneNet<W, G>::SLOTS * K::THREADS * (int)sizeof(float) : 0;
+    const int smem = traj_stage_bytes<W, G, NW, KSQ>();
     cudaError_t e = ensure_smem(traj_kernel<W, G, NW, MINB, VAR, KSQ>, smem);
     if (e != cudaSuccess) return e;
     traj_kernel<W, G, NW, MINB, VAR, KSQ><<<grid, K::THREADS, smem, stream>>>(a);
     return cudaGetLastError();
 }
 
-template <int W, int G, int NW, int MINB = 1, bool VAR = false>
+template <int W, int G, int NW, int MINB = 1, bool VAR = false, int KSQ = 0, int CW = 16, int R = 4>
 cudaError_t launch_fused(const RolloutArgs& a, cudaStream_t stream)
 {
     using K = TrajKernel<W, G, NW>;
     const int grid = (a.N + K::B - 1) / K::B;
-    fused_kernel<W, G, NW, MINB, VAR><<<grid, K::THREADS, 0, stream>>>(a);
-    return cudaGetLastError();
-}
-
-template <int W, int G>
-cudaError_t launch_reroll(const RolloutArgs& a, const EpilogueArgs& e, cudaStream_t stream)
-{
-    if (uses_variants(a.c)) reroll_epilogue_kernel<W, G, true><<<1, 32, 0, stream>>>(a, e);
-    else reroll_epilogue_kernel<W, G, false><<<1, 32, 0, stream>>>(a, e);
+    const int smem = traj_stage_bytes<W, G, NW, KSQ>() + NW * (32 / G) * CW * (int)sizeof(float4);
+    cudaError_t e = ensure_smem(fused_kernel<W, G, NW, MINB, VAR, KSQ, CW, R>, smem);
+    if (e != cudaSuccess) return e;
+    fused_kernel<W, G, NW, MINB, VAR, KSQ, CW, R><<<grid, K::THREADS, smem, stream>>>(a);
     return cudaGetLastError();
 }
 

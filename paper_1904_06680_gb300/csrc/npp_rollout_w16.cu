@@ -18,20 +18,17 @@ cudaError_t launch_traj_w16(const RolloutArgs& a, cudaStream_t s, int variant)
     }
 }
 
+// Trajectories with the windowed binned check (fused_kernel; template
+// arguments after the trajectory kernel's: window of states, candidates
+// loaded ahead per lane)
 cudaError_t launch_fused_w16(const RolloutArgs& a, cudaStream_t s, int variant)
 {
-    if (uses_variants(a.c)) return launch_fused<16, 8, 4, 4, true>(a, s);
+    if (uses_variants(a.c)) return launch_fused<16, 8, 4, 4, true, 0, 16, 4>(a, s);
     switch (variant) {
-    case 1: return launch_fused<16, 4, 8>(a, s);
-    case 2: return launch_fused<16, 8, 8>(a, s);
-    case 3: return launch_fused<16, 8, 8, 3>(a, s);
-    default: return launch_fused<16, 8, 4, 4>(a, s);
+    case 2: return launch_fused<16, 8, 4, 4, false, 0, 8, 4>(a, s);
+    case 3: return launch_fused<16, 8, 4, 4, false, 0, 16, 2>(a, s);
+    default: return launch_fused<16, 8, 4, 4, false, 0, 16, 4>(a, s);
     }
-}
-
-cudaError_t launch_reroll_w16(const RolloutArgs& a, const EpilogueArgs& e, cudaStream_t s)
-{
-    return launch_reroll<16, 8>(a, e, s);
 }
 
 }  // namespace npp

@@ -23,20 +23,22 @@ cudaError_t launch_traj_w32(const RolloutArgs& a, cudaStream_t s, int variant)
     }
 }
 
+// Trajectories with the windowed binned check (fused_kernel; template
+// arguments after the trajectory kernel's: window of states, candidates
+// loaded ahead per lane).  Not the library's choice at this width: on the
+// course (N = 16384, T = 40, M = 2000) the default shape, 5 of 8 W2 quads in
+// shared memory and windows of 8, took 0.311 ms per plan step against 0.258
+// in two kernels (1: 0.348, 3: 0.330).
 cudaError_t launch_fused_w32(const RolloutArgs& a, cudaStream_t s, int variant)
 {
-    if (uses_variants(a.c)) return launch_fused<32, 16, 4, 4, true>(a, s);
+    if (uses_variants(a.c)) return launch_fused<32, 16, 4, 5, true, 5, 8, 4>(a, s);
     switch (variant) {
-    case 1: return launch_fused<32, 8, 8>(a, s);
-    case 2: return launch_fused<32, 16, 8>(a, s);
-    case 3: return launch_fused<32, 16, 8, 3>(a, s);
-    default: return launch_fused<32, 16, 4, 4>(a, s);
+    case 1: return launch_fused<32, 16, 4, 4, false, 0, 16, 4>(a, s);
+    case 2: return launch_fused<32, 16, 4, 4, false, 0, 8, 4>(a, s);
+    case 3: return launch_fused<32, 16, 4, 3, false, 0, 16, 4>(a, s);
+    case 4: return launch_fused<32, 16, 4, 5, false, 5, 16, 4>(a, s);
+    default: return launch_fused<32, 16, 4, 5, false, 5, 8, 4>(a, s);
     }
-}
-
-cudaError_t launch_reroll_w32(const RolloutArgs& a, const EpilogueArgs& e, cudaStream_t s)
-{
-    return launch_reroll<32, 16>(a, e, s);
 }
 
 }  // namespace npp

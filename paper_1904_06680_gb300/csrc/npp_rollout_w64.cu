@@ -23,20 +23,23 @@ cudaError_t launch_traj_w64(const RolloutArgs& a, cudaStream_t s, int variant)
     }
 }
 
+// Trajectories with the windowed binned check (fused_kernel; template
+// arguments after the trajectory kernel's: window of states, candidates
+// loaded ahead per lane).  Measured on GB300 at N = 65536, T = 100,
+// M = 8192 (ms per plan step): 0 (default) 12 W2 quads of 16 in shared
+// memory, windows of 8 states: 2.68; 1 10 quads, windows of 16: 2.76;
+// 2 12 quads, windows of 16: 2.73; 3 and 4 with 8 candidates ahead: 2.94 -
+// 2.98 (no register left for them without spills).
 cudaError_t launch_fused_w64(const RolloutArgs& a, cudaStream_t s, int variant)
 {
-    if (uses_variants(a.c)) return launch_fused<64, 32, 1, 10, true>(a, s);
+    if (uses_variants(a.c)) return launch_fused<64, 32, 1, 16, true, 12, 8, 4>(a, s);
     switch (variant) {
-    case 1: return launch_fused<64, 16, 8>(a, s);
-    case 2: return launch_fused<64, 32, 8>(a, s);
-    case 3: return launch_fused<64, 32, 2, 5>(a, s);
-    default: return launch_fused<64, 32, 1, 10>(a, s);
+    case 1: return launch_fused<64, 32, 1, 16, false, 10, 16, 4>(a, s);
+    case 2: return launch_fused<64, 32, 1, 16, false, 12, 16, 4>(a, s);
+    case 3: return launch_fused<64, 32, 1, 16, false, 12, 16, 8>(a, s);
+    case 4: return launch_fused<64, 32, 1, 16, false, 8, 8, 4>(a, s);
+    default: return launch_fused<64, 32, 1, 16, false, 12, 8, 4>(a, s);
     }
-}
-
-cudaError_t launch_reroll_w64(const RolloutArgs& a, const EpilogueArgs& e, cudaStream_t s)
-{
-    return launch_reroll<64, 32>(a, e, s);
 }
 
 }  // namespace npp

@@ -35,6 +35,7 @@ def _planner(sc, chunks, timing=False):
     M = sc["obs"].shape[0]
     pl = npp.Planner(sc["preset"], max_N=N, max_T=T, max_M=max(M, 1))
     npp.npp_set_option(pl.h, "collide_variant", BINNED)
+    npp.npp_set_option(pl.h, "fuse", 0)
     npp.npp_set_option(pl.h, "chunks", chunks)
     if timing:
         npp.npp_set_timing(pl.h, True)
@@ -206,3 +207,57 @@ def test_chunks_in_the_closed_loop(restarts):
             np.testing.assert_array_equal(c.view(np.int32), c0.view(np.int32))
         np.testing.assert_array_equal(r[1], runs[0][1])
         assert r[2] == runs[0][2]
+
+
+def _plan_fused(sc, variant=0, timing=False):
+    """The plan step with the windowed check inside the trajectory kernel
+    (option fuse) in launch shape `variant`."""
+    import torch
+    from paper_1904_06680_gb300 import npp
+    N, T = sc["N"], sc["T"]
+    M = sc["obs"].shape[0]
+    pl = _planner(sc, 1, timing)
+    npp.npp_set_option(pl.h, "fuse", 1)
+    npp.npp_set_option(pl.h, "traj_variant", variant)
+    obs = torch.tensor(sc["obs"], dtype=torch.float32, device="cuda") if M else None
+    pl.plan(sc["state"], sc["goal"], obs, N, T, sc["seed"], sc["t_index"])
+    torch.cuda.synchronize()
+    r = pl.result(N, T)
+    if timing:
+        r["counts"] = npp.npp_last_counts(pl.h)
+    pl.close()
+    return r
+
+
+def window_steps(first_hit, T, CW, per_warp):
+    """Control steps the windowed kernel computes: a sample's warp rolls
+    windows of CW states until every sample of the warp (per_warp
+    consecutive ones) has collided, the window of its first collision
+    included; min(CW (k + 1), T) steps through window k."""
+    fh = np.asarray(first_hit)
+    own = np.where(fh < 0, T, np.minimum((fh // CW + 1) * CW, T))
+    pad = (-len(own)) % per_warp
+    warp = np.concatenate([own, np.zeros(pad, own.dtype)]).reshape(-1, per_warp).max(axis=1)
+    return int(np.repeat(warp, per_warp)[:len(own)].sum())
+
+
+@pytest.mark.parametrize("width,variants", [(16, (0, 2, 3)), (32, (0, 1, 2, 3, 4)), (64, (0, 1, 2, 3, 4))])
+def test_fused_window_shapes_equal_single_launch(width, variants):
+    sc = inputs.tiny_scene(140 + width, 2100, 37, 900, width=width, box=14.0, clear=1.5)
+    one = _plan(sc, 1)
+    for v in variants:
+        _assert_same(_plan_fused(sc, v), one)
+
+
+@pytest.mark.parametrize("width,cw,per_warp", [(64, 8, 1), (32, 8, 2), (16, 16, 4)])
+def test_fused_work_counter_follows_the_window_rule(width, cw, per_warp):
+    sc = inputs.tiny_scene(150 + width, 3000, 45, 1500, width=width, box=14.0, clear=1.5)
+    one = _plan(sc, 1)
+    r = _plan_fused(sc, 0, timing=True)
+    _assert_same(r, one)
+    assert r["counts"][2] == window_steps(one["first_hit"], sc["T"], cw, per_warp)
+
+
+def test_fused_at_the_large_workload():
+    sc = inputs.scene_large(0)
+    _assert_same(_plan_fused(sc, 0), _plan(sc, 1))

@@ -279,14 +279,16 @@ def test_collide_variants_identical():
     pl.close()
 
 
-def test_trajectory_launch_shapes_identical_at_width_64():
-    """Every launch shape of the 8-64-64-2 trajectory kernel -- the default
-    one keeps half of each lane's layer-2 weights in shared memory, shape 4
-    keeps them all in registers -- gives the same bits: per-sample states,
-    controls, costs, first collisions and the winner."""
+@pytest.mark.parametrize("width", [64, 32])
+def test_trajectory_launch_shapes_identical(width):
+    """Every launch shape of the trajectory kernel gives the same bits:
+    per-sample states, controls, costs, first collisions and the winner.
+    At width 64 the default keeps half of each lane's layer-2 weights in
+    shared memory and shape 4 all in registers; at width 32 shape 4 keeps 5
+    of each lane's 8 layer-2 input quads in shared memory."""
     import torch
     from paper_1904_06680_gb300 import npp
-    sc = inputs.tiny_scene(33, N=700, T=30, M=250, width=64, box=30.0)
+    sc = inputs.tiny_scene(33, N=700, T=30, M=250, width=width, box=30.0)
     N, T = sc["N"], sc["T"]
     obs = torch.tensor(sc["obs"], dtype=torch.float32, device="cuda")
     pl = npp.Planner(sc["preset"], max_N=N, max_T=T, max_M=obs.shape[0], record_samples=True)

@@ -102,7 +102,11 @@ typedef struct { float x, y, phi, v; } npp_goal;
 /* Device-side summary of one plan step. */
 typedef struct {
     int32_t best_idx;   /* winning sample index                              */
-    int32_t status;     /* NPP_OK or NPP_INFEASIBLE                          */
+    int32_t status;     /* NPP_OK or NPP_INFEASIBLE; NPP_DEVICE_TIMEOUT when a
+                           bounded device-side wait of this step (the bulk
+                           copy staging the obstacle points of a brute-force
+                           check, about a second) gave up: the step's results
+                           are then not valid                                */
     float best_cost;    /* its cost (+inf when infeasible)                   */
     int32_t first_hit;  /* its first colliding (or, with v_limits, speed-violating)
                            horizon index, -1 if none                         */

@@ -63,6 +63,11 @@ __global__ void epilogue_kernel(const EpilogueArgs e)
         npp_best* b = reinterpret_cast<npp_best*>(e.best);
         b->best_idx = idx;
         b->status = dead ? NPP_INFEASIBLE : NPP_OK;
+        if (e.fault && *e.fault) {
+            // a bounded wait of this step's kernels gave up: no valid result
+            b->status = NPP_DEVICE_TIMEOUT;
+            *e.fault = 0u;
+        }
         b->best_cost = dead ? __int_as_float(0x7f800000) : __uint_as_float(hi);
         b->first_hit = fh;
         b->reserved[0] = b->reserved[1] = b->reserved[2] = b->reserved[3] = 0;
@@ -340,7 +345,6 @@ npp_status run_rollout(npp_handle* h, RolloutArgs& a, cudaStream_t s, bool no_re
     const bool global_pts = a.M > h->max_points;
     if (global_pts) {
         a.pXY = h->d_pXY;
-        a.pV = h->d_pV;
         a.grid_collide = h->sm_count * collide_global_blocks_per_sm();
     } else {
         if (h->occ_M != a.M || h->collide_active != v) {
@@ -403,6 +407,7 @@ static void fill_rollout_args(const npp_handle* h, RolloutArgs& a, const npp_sta
     a.obs = reinterpret_cast<const float4*>(obs);
     a.M = M; a.N = N; a.T = T;
     a.vfirst = h->d_vfirst;
+    a.fault = h->d_fault;
 }
 
 // ------------------------------------------------------------------ C ABI
@@ -470,13 +475,13 @@ npp_status npp_create(npp_handle** out, const npp_config* cfg, int32_t device)
     if (cfg->v_limits) A((void**)&h->d_vfirst, (size_t)cfg->max_N * sizeof(int));
     A((void**)&h->d_work, 64);
     A((void**)&h->d_counts, 64);
+    A((void**)&h->d_fault, sizeof(unsigned));
     A((void**)&h->d_live, (size_t)2 * cfg->max_N * sizeof(int));
     A((void**)&h->d_live_n, NPP_MAX_CHUNKS * sizeof(int));
     A((void**)&h->d_carry, (size_t)cfg->max_N * sizeof(float4));
     A(&h->d_bins, binned_workspace_bytes(cfg->max_T, cfg->max_M));
     if (cfg->max_M > max_points) {
-        A((void**)&h->d_pXY, (size_t)(cfg->max_M / 2 + 1) * sizeof(float4));
-        A((void**)&h->d_pV, (size_t)(cfg->max_M / 2 + 1) * sizeof(float4));
+        A((void**)&h->d_pXY, (size_t)64 * pair_blocks(cfg->max_M) * sizeof(float4));
     }
     A((void**)&h->d_obs, (size_t)cfg->max_M * sizeof(float4));
     A((void**)&h->d_warm, (size_t)h->n_theta * sizeof(float));
@@ -487,6 +492,7 @@ npp_status npp_create(npp_handle** out, const npp_config* cfg, int32_t device)
     A((void**)&h->d_trajectory, (size_t)(cfg->max_T + 1) * 4 * sizeof(float));
     A((void**)&h->d_costs, (size_t)cfg->max_N * sizeof(float));
     A((void**)&h->d_fh, (size_t)cfg->max_N * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemset(h->d_fault, 0, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming);
@@ -509,7 +515,7 @@ npp_status npp_destroy(npp_handle* h)
     if (h->stream) cudaStreamSynchronize(h->stream);
     void* ptrs[] = { h->d_key, h->d_traj, h->d_ctrl, h->d_jfree, h->d_vfirst, h->d_fp, h->d_work, h->d_counts,
                      h->d_live, h->d_live_n, h->d_carry,
-                     h->d_pXY, h->d_pV, h->d_bins,
+                     h->d_pXY, h->d_fault, h->d_bins,
                      h->d_obs, h->d_warm, h->d_sigma, h->d_best, h->d_params, h->d_controls, h->d_trajectory,
                      h->d_costs, h->d_fh };
     for (void* p : ptrs) if (p) cudaFree(p);
@@ -560,6 +566,7 @@ static npp_status plan_step_impl(npp_handle* h, const npp_state* state, const np
     e.traj = a.traj;
     e.ctrl = a.ctrl;
     e.best_key = h->d_key;
+    e.fault = h->d_fault;
     e.best = out->best;
     e.params = out->params;
     e.controls = out->controls;
@@ -670,7 +677,8 @@ npp_status npp_plan_step_host(npp_handle* h, const npp_state* state, const npp_g
     if (out_host->first_hit)
         CUDA_TRY(h, cudaMemcpyAsync(out_host->first_hit, h->d_fh, (size_t)N * 4, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(h, cudaStreamSynchronize(s));
-    return out_host->best->status == NPP_INFEASIBLE ? NPP_INFEASIBLE : NPP_OK;
+    const int32_t st_best = out_host->best->status;
+    return st_best == NPP_INFEASIBLE || st_best == NPP_DEVICE_TIMEOUT ? (npp_status)st_best : NPP_OK;
 }
 
 npp_status npp_rollout_params(npp_handle* h, const npp_state* state, const npp_goal* goal,

@@ -45,9 +45,11 @@ int collide_global_blocks_per_sm()
     return nb > 0 ? nb : 1;
 }
 
+// points whose pair blocks fit beside the largest fixed part (and the
+// staging barrier, static shared memory)
 int collide_max_points(int smem_limit)
 {
-    return 2 * ((smem_limit - CollideResident::fixed_bytes()) / 32);
+    return 64 * ((smem_limit - CollideResident::fixed_bytes() - 16) / 1024);
 }
 
 }  // namespace npp

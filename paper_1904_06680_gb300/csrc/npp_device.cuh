@@ -423,6 +423,10 @@ struct StepIn {
     bool warm_ok;
 };
 
+// blocks of 32 point pairs (64 points) holding M obstacle points in the
+// brute-force checks' layout (XY entries of a block, then its V entries)
+__host__ __device__ constexpr int pair_blocks(int M) { return (M + 63) / 64; }
+
 struct RolloutArgs {
     DevCfg c;
     float x0, y0, phi0, v0, ap0, ap1;  // world-frame state and last controls
@@ -448,8 +452,11 @@ struct RolloutArgs {
     const LoopDev* dyn;                // when set, per-step scalars come from here
     int warm_force;                    // the warm start replaces sample 0 even before the loop's
                                        // first step (restart rounds: it is the incumbent)
-    float4* pXY;                       // EV-frame point pairs in global memory (when the
-    float4* pV;                        // points exceed shared memory), [ceil(M/2)]
+    float4* pXY;                       // EV-frame point pairs in global memory when the points
+                                       // exceed shared memory: 64 pair_blocks(M) entries, the
+                                       // shared-memory staging's blocked layout
+    unsigned* fault;                   // set when a bounded device wait gave up (read and
+                                       // cleared by the winner epilogue), or null
     BinView bins;                      // per-step grids (binned and fused collision checks)
     unsigned long long* counts;        // measurement counters, or null: [0] candidate point tests
                                        // and [1] states checked by the binned check, [2] sample-steps
@@ -503,6 +510,8 @@ struct EpilogueArgs {
     float* trajectory;
     const LoopDev* dyn;                // when set, x0, y0, phi0, t_index, warm validity from here
     int warm_force;                    // as RolloutArgs::warm_force
+    unsigned* fault;                   // as RolloutArgs::fault: nonzero turns the result's status
+                                       // into NPP_DEVICE_TIMEOUT (and is cleared), or null
 };
 
 // launchers: trajectory kernel per network width, one collision kernel

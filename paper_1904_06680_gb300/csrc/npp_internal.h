@@ -52,7 +52,7 @@ struct npp_handle {
     float loop_sigma;                    // their perturbation scale
     int occ_M, occ_blocks;               // cached occupancy for the last M
     float4* d_pXY;                       // EV-frame point pairs when M exceeds shared memory
-    float4* d_pV;
+    unsigned* d_fault;                   // device-wait fault flag of the plan steps (RolloutArgs::fault)
     void* d_bins;                        // per-step spatial grids of the binned collision check
     // host-mode staging
     float4* d_obs;

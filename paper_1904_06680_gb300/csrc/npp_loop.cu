@@ -259,6 +259,7 @@ npp_status enqueue_step(npp_loop* L, uint64_t seed)
     a.jfree = h->d_jfree;
     a.vfirst = h->d_vfirst;
     a.best_key = h->d_key;
+    a.fault = h->d_fault;
     a.dyn = L->d_dyn;
     a.costs = L->d_costs;
     a.first_hit = L->d_fh;
@@ -273,6 +274,7 @@ npp_status enqueue_step(npp_loop* L, uint64_t seed)
     e.traj = a.traj;
     e.ctrl = a.ctrl;
     e.best_key = h->d_key;
+    e.fault = h->d_fault;
     e.best = L->d_best;
     e.params = L->d_warm;
     e.controls = L->d_controls;

@@ -142,14 +142,15 @@ extern "C" npp_status npp_plan_step_noalloc(const npp_config* cfg, const npp_sta
     a.coefB = nullptr;
     a.best_key = reinterpret_cast<unsigned long long*>(base);
     a.work = reinterpret_cast<unsigned*>(base + 8);
+    a.fault = reinterpret_cast<unsigned*>(base + 12);
     int sm_count = 1;
     cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev);
     const int variant = N <= 8192 ? 3 : 4;
     a.grid_collide = (sm_count > 0 ? sm_count : 1) * collide_resident_blocks_per_sm(M, variant);
 
-    // the best key starts at all ones, the work counter at zero
+    // the best key starts at all ones, the work counter and fault flag at zero
     e = cudaMemsetAsync(base, 0xff, 8, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(base + 8, 0, 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + 8, 0, 8, s);
     if (e == cudaSuccess) {
         switch (cfg->width) {
         case 16: e = launch_traj_w16(a, s, 0); break;
@@ -168,6 +169,7 @@ extern "C" npp_status npp_plan_step_noalloc(const npp_config* cfg, const npp_sta
         ep.traj = a.traj;
         ep.ctrl = a.ctrl;
         ep.best_key = a.best_key;
+        ep.fault = a.fault;
         ep.best = out->best;
         ep.params = out->params;
         ep.controls = out->controls;

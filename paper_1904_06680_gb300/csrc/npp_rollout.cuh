@@ -32,6 +32,7 @@
 
 #include "../../include/npp.h"
 #include "npp_device.cuh"
+#include "npp_async.cuh"
 
 namespace npp {
 
@@ -1002,9 +1003,14 @@ __global__ void __launch_bounds__(NW * 32, MINB) fused_kernel(const RolloutArgs 
 }
 
 // ------------------------------------------------------------------ collide
-// Points live in shared memory as pairs: XY[q] = (x_2q, x_2q+1, y_2q, y_2q+1),
-// V[q] = (vx_2q, vx_2q+1, vy_2q, vy_2q+1), so that one packed FP32x2 FMA
-// handles the same sample against two points.
+// Points live in shared memory as pairs: XY_q = (x_2q, x_2q+1, y_2q, y_2q+1),
+// V_q = (vx_2q, vx_2q+1, vy_2q, vy_2q+1), so that one packed FP32x2 FMA
+// handles the same sample against two points.  The pairs come in blocks of
+// 32: block b holds its 32 XY entries, then its 32 V entries (XY_q at
+// pair_index(q), V_q 32 entries later) -- the same 1024 bytes as the
+// block's 64 raw points, so the staging moves them into the EV frame in
+// place, and a warp reads 32 consecutive XY (or V) entries at once.
+__device__ __forceinline__ int pair_index(int q) { return q + (q & ~31); }
 __device__ __forceinline__ unsigned long long pk(float lo, float hi)
 {
     return ((unsigned long long)__float_as_uint(hi) << 32) | __float_as_uint(lo);
@@ -1023,8 +1029,7 @@ __device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigne
 // |eta''|); a sample collides iff some lane has m < 1.  Returns the hit bits
 // of the CC slots.
 template <int CC>
-__device__ __forceinline__ unsigned check_unit(const float4* __restrict__ XY, const float4* __restrict__ V,
-                                               int q0, int q1, float tau,
+__device__ __forceinline__ unsigned check_unit(const float4* __restrict__ P, int q0, int q1, float tau,
                                                const float4* __restrict__ cfA, const float2* __restrict__ cfB,
                                                int cs, int nvalid, int lane)
 {
@@ -1042,9 +1047,9 @@ __device__ __forceinline__ unsigned check_unit(const float4* __restrict__ XY, co
     for (int k = 0; k < CC; ++k) acc[k] = 0ull;
     const unsigned long long TT = pk(tau, tau);
 #pragma unroll 2
-    for (int q = q0 + lane; q < q1; q += 32) {
-        const float4 xy = XY[q];
-        const float4 vv = V[q];
+    for (int q = q0 + lane, i = pair_index(q0 + lane); q < q1; q += 32, i += 64) {
+        const float4 xy = P[i];
+        const float4 vv = P[i + 32];
         const unsigned long long PX = fma2(TT, pk(vv.x, vv.y), pk(xy.x, xy.y));
         const unsigned long long PY = fma2(TT, pk(vv.z, vv.w), pk(xy.z, xy.w));
 #pragma unroll
@@ -1064,29 +1069,63 @@ __device__ __forceinline__ unsigned check_unit(const float4* __restrict__ XY, co
 }
 
 
-// Staging of the points in the EV frame as pairs; an odd tail is padded with
-// a point 1e15 m away (never inside).
+// Staging of the M obstacle points in shared memory P (pair_blocks(M)
+// blocks of 64 points): one bulk copy by the copy engine (TMA) of the
+// world-frame points, 16 bytes each, to the start of P, then each warp
+// moves whole blocks into the EV frame in place (ev_point on the point's
+// owner lane, the pairs assembled by shuffles).  Points past M (an odd tail
+// and the rest of the last block) are placed 1e15 m away (never inside).
+// Returns the number of pairs, or -1 when the copy's bounded wait ran out:
+// *a.fault is then set and the whole block must return.
 template <int THREADS>
-__device__ __forceinline__ int stage_points(const RolloutArgs& a, float4* XY, float4* V)
+__device__ __forceinline__ int stage_points(const RolloutArgs& a, float4* P)
 {
-    const int npairs = (a.M + 1) / 2;
+    __shared__ uint64_t bar;
+    const int M = a.M, nb = pair_blocks(M);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    if (tid == 0 && M > 0) {
+        mbar_expect_tx(&bar, (uint32_t)M * 16u);
+        bulk_load(P, a.obs, (uint32_t)M * 16u, &bar);
+    }
+    const bool ok = M == 0 || mbar_wait(&bar, 0);
+    if (__syncthreads_or(!ok)) {
+        if (tid == 0 && a.fault) atomicOr(a.fault, 1u);
+        return -1;
+    }
     const StepIn si = step_in(a);
     float s0, c0;
     sincosf(si.phi0, &s0, &c0);
-    float* xy = reinterpret_cast<float*>(XY);
-    float* vv = reinterpret_cast<float*>(V);
-    for (int j = threadIdx.x; j < 2 * npairs; j += THREADS) {
-        float px = 1e15f, py = 1e15f, vx = 0.f, vy = 0.f;
-        if (j < a.M) {
-            ev_point(a.obs[j], si.x0, si.y0, s0, c0, px, py, vx, vy);
-        }
-        const int q = j >> 1, o2 = j & 1;
-        xy[4 * q + o2] = px;
-        xy[4 * q + 2 + o2] = py;
-        vv[4 * q + o2] = vx;
-        vv[4 * q + 2 + o2] = vy;
+    for (int b = warp; b < nb; b += THREADS / 32) {
+        // lane l moves points j0 = 64 b + l and j1 = j0 + 32
+        const int j0 = 64 * b + lane, j1 = j0 + 32;
+        float x0 = 1e15f, y0 = 1e15f, u0 = 0.f, w0 = 0.f;
+        float x1 = 1e15f, y1 = 1e15f, u1 = 0.f, w1 = 0.f;
+        if (j0 < M) ev_point(P[j0], si.x0, si.y0, s0, c0, x0, y0, u0, w0);
+        if (j1 < M) ev_point(P[j1], si.x0, si.y0, s0, c0, x1, y1, u1, w1);
+        // pair r = lane of the block: its points 2r, 2r + 1 sit on lanes
+        // 2r mod 32 and 2r + 1 mod 32, in the second half for r >= 16
+        // (a shuffle reads the source lane's variable, so both halves travel
+        // and the receiving lane picks)
+        const int l0 = (2 * lane) & 31, l1 = l0 + 1;
+        const bool hi = lane >= 16;
+        const auto pick = [&](float lo_v, float hi_v, int src) {
+            const float a_ = __shfl_sync(FULL, lo_v, src), b_ = __shfl_sync(FULL, hi_v, src);
+            return hi ? b_ : a_;
+        };
+        const float ax0 = pick(x0, x1, l0), ax1 = pick(x0, x1, l1);
+        const float ay0 = pick(y0, y1, l0), ay1 = pick(y0, y1, l1);
+        const float au0 = pick(u0, u1, l0), au1 = pick(u0, u1, l1);
+        const float aw0 = pick(w0, w1, l0), aw1 = pick(w0, w1, l1);
+        __syncwarp();                         // every raw point of the block read
+        P[64 * b + lane] = make_float4(ax0, ax1, ay0, ay1);
+        P[64 * b + 32 + lane] = make_float4(au0, au1, aw0, aw1);
     }
-    return npairs;
+    return (M + 1) / 2;
 }
 
 // Point slices per chunk for this step: the count whose units spread best
@@ -1117,7 +1156,7 @@ struct CollideBlockKernel {
     static constexpr int fixed_bytes() {
         return 2 * SBMAX * 16 + 2 * SBMAX * 8 + 2 * SBMAX * 4 + NW * 8 + 64;
     }
-    static int smem_bytes(int M) { return ((M + 1) / 2) * 32 + fixed_bytes(); }
+    static int smem_bytes(int M) { return pair_blocks(M) * 1024 + fixed_bytes(); }
 };
 
 // Block-balanced collision kernel.  Block b owns an equal contiguous share of
@@ -1132,10 +1171,8 @@ __global__ void __launch_bounds__(NW * 32, MINB) collide_block_kernel(const Roll
 {
     using K = CollideBlockKernel<NW, SBMAX>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int npairs_all = (a.M + 1) / 2;
-    float4* XY = reinterpret_cast<float4*>(smem_raw);
-    float4* V = XY + npairs_all;
-    float4* cfA = V + npairs_all;                              // [2][SBMAX]
+    float4* P = reinterpret_cast<float4*>(smem_raw);           // the point pairs
+    float4* cfA = P + 64 * pair_blocks(a.M);                   // [2][SBMAX]
     float2* cfB = reinterpret_cast<float2*>(cfA + 2 * SBMAX);  // [2][SBMAX]
     int* hitf = reinterpret_cast<int*>(cfB + 2 * SBMAX);       // [2][SBMAX]
     unsigned long long* red = reinterpret_cast<unsigned long long*>(hitf + 2 * SBMAX);
@@ -1144,7 +1181,8 @@ __global__ void __launch_bounds__(NW * 32, MINB) collide_block_kernel(const Roll
     const int warp = tid >> 5, lane = tid & 31;
     const DevCfg& c = a.c;
     const int T = a.T, N = a.N;
-    const int npairs = stage_points<K::THREADS>(a, XY, V);
+    const int npairs = stage_points<K::THREADS>(a, P);
+    if (npairs < 0) return;                                    // the staging copy gave up (a.fault set)
 
     // this block's share of the samples
     const int per_block = (N + gridDim.x - 1) / gridDim.x;
@@ -1191,10 +1229,10 @@ __global__ void __launch_bounds__(NW * 32, MINB) collide_block_kernel(const Roll
                 const int cs = ch * 8;
                 const int nv = min(8, L - cs);
                 unsigned bits;
-                if (nv > 4)      bits = check_unit<8>(XY, V, q0, q1, tau, A_, B_, cs, nv, lane);
-                else if (nv > 2) bits = check_unit<4>(XY, V, q0, q1, tau, A_, B_, cs, nv, lane);
-                else if (nv > 1) bits = check_unit<2>(XY, V, q0, q1, tau, A_, B_, cs, nv, lane);
-                else             bits = check_unit<1>(XY, V, q0, q1, tau, A_, B_, cs, nv, lane);
+                if (nv > 4)      bits = check_unit<8>(P, q0, q1, tau, A_, B_, cs, nv, lane);
+                else if (nv > 2) bits = check_unit<4>(P, q0, q1, tau, A_, B_, cs, nv, lane);
+                else if (nv > 1) bits = check_unit<2>(P, q0, q1, tau, A_, B_, cs, nv, lane);
+                else             bits = check_unit<1>(P, q0, q1, tau, A_, B_, cs, nv, lane);
                 if (lane < 8 && ((bits >> lane) & 1u)) hitf[buf * SBMAX + cs + lane] = 1;
             }
             __syncthreads();
@@ -1264,8 +1302,8 @@ __global__ void __launch_bounds__(NW * 32, MINB) collide_block_kernel(const Roll
 // reads the CC slots with broadcast loads.  Returns the hit bits in slot
 // order.
 template <int CC>
-__device__ __forceinline__ unsigned check_slots(const float4* __restrict__ XY, const float4* __restrict__ V,
-                                                int npairs, float tau, const float4* __restrict__ sA,
+__device__ __forceinline__ unsigned check_slots(const float4* __restrict__ P, int q0, int q1, float tau,
+                                                const float4* __restrict__ sA,
                                                 const float2* __restrict__ sB, int L, int lane)
 {
     unsigned long long A[CC], B[CC], NC[CC], D[CC], E[CC], NF[CC];
@@ -1282,9 +1320,9 @@ __device__ __forceinline__ unsigned check_slots(const float4* __restrict__ XY, c
     for (int k = 0; k < CC; ++k) acc[k] = 0ull;
     const unsigned long long TT = pk(tau, tau);
 #pragma unroll 2
-    for (int q = lane; q < npairs; q += 32) {
-        const float4 xy = XY[q];
-        const float4 vv = V[q];
+    for (int q = q0 + lane, i = pair_index(q0 + lane); q < q1; q += 32, i += 64) {
+        const float4 xy = P[i];
+        const float4 vv = P[i + 32];
         const unsigned long long PX = fma2(TT, pk(vv.x, vv.y), pk(xy.x, xy.y));
         const unsigned long long PY = fma2(TT, pk(vv.z, vv.w), pk(xy.z, xy.w));
 #pragma unroll
@@ -1305,8 +1343,8 @@ __device__ __forceinline__ unsigned check_slots(const float4* __restrict__ XY, c
 
 // One step of an 8-sample item for one warp: the owner lanes (lane < 8 with
 // their bit in `live`) stage their coefficient rows, the warp checks the
-// points [XY, XY + npairs), and the hits come back as a lane mask.
-__device__ __forceinline__ unsigned warp_step(const float4* XY, const float4* V, int npairs, float tau,
+// point pairs [q0, q1), and the hits come back as a lane mask.
+__device__ __forceinline__ unsigned warp_step(const float4* P, int q0, int q1, float tau,
                                               float4 ca, float2 cb, unsigned live, float4* sA,
                                               float2* sB, int lane)
 {
@@ -1316,10 +1354,10 @@ __device__ __forceinline__ unsigned warp_step(const float4* XY, const float4* V,
     __syncwarp();
     const int L = __popc(live);
     unsigned bits;
-    if (L > 4)      bits = check_slots<8>(XY, V, npairs, tau, sA, sB, L, lane);
-    else if (L > 2) bits = check_slots<4>(XY, V, npairs, tau, sA, sB, L, lane);
-    else if (L > 1) bits = check_slots<2>(XY, V, npairs, tau, sA, sB, L, lane);
-    else            bits = check_slots<1>(XY, V, npairs, tau, sA, sB, L, lane);
+    if (L > 4)      bits = check_slots<8>(P, q0, q1, tau, sA, sB, L, lane);
+    else if (L > 2) bits = check_slots<4>(P, q0, q1, tau, sA, sB, L, lane);
+    else if (L > 1) bits = check_slots<2>(P, q0, q1, tau, sA, sB, L, lane);
+    else            bits = check_slots<1>(P, q0, q1, tau, sA, sB, L, lane);
     __syncwarp();
     return __ballot_sync(FULL, owner && ((bits >> rank) & 1u));
 }
@@ -1328,24 +1366,23 @@ template <int NW>
 struct CollideWarpKernel {
     static constexpr int THREADS = NW * 32;
     static constexpr int fixed_bytes() { return NW * 8 * 24 + NW * 8 + 64; }
-    static int smem_bytes(int M) { return ((M + 1) / 2) * 32 + fixed_bytes(); }
+    static int smem_bytes(int M) { return pair_blocks(M) * 1024 + fixed_bytes(); }
 };
 
 template <int NW, int MINB>
 __global__ void __launch_bounds__(NW * 32, MINB) collide_warp_kernel(const RolloutArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int npairs = (a.M + 1) / 2;
-    float4* XY = reinterpret_cast<float4*>(smem_raw);
-    float4* V = XY + npairs;
-    float4* slotA = V + npairs;                                  // [NW][8]
+    float4* P = reinterpret_cast<float4*>(smem_raw);             // the point pairs
+    float4* slotA = P + 64 * pair_blocks(a.M);                   // [NW][8]
     float2* slotB = reinterpret_cast<float2*>(slotA + NW * 8);   // [NW][8]
     unsigned long long* red = reinterpret_cast<unsigned long long*>(slotB + NW * 8);
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     const DevCfg& c = a.c;
     const int T = a.T, N = a.N;
-    stage_points<NW * 32>(a, XY, V);
+    const int npairs = stage_points<NW * 32>(a, P);
+    if (npairs < 0) return;                                      // the staging copy gave up (a.fault set)
     __syncthreads();
     float4* sA = slotA + warp * 8;
     float2* sB = slotB + warp * 8;
@@ -1371,7 +1408,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) collide_warp_kernel(const Rollo
             float2 cur_b;
             rows_of_state(c, z, cur_a, cur_b);
             if (mine && h < T) z = a.traj[(size_t)(h + 1) * N + n];
-            const unsigned hits = warp_step(XY, V, npairs, (float)h * c.Ts, cur_a, cur_b, live,
+            const unsigned hits = warp_step(P, 0, npairs, (float)h * c.Ts, cur_a, cur_b, live,
                                             sA, sB, lane);
             if ((hits >> lane) & 1u) fh = h;
             live &= ~hits;
@@ -1420,7 +1457,7 @@ template <int S, int P = 1>
 struct CollideSliceKernel {
     static constexpr int THREADS = P * S * 32;
     static constexpr int fixed_bytes() { return P * S * 8 * 24 + P * (8 * 4 + 16) + P * S * 8 + 64; }
-    static int smem_bytes(int M) { return ((M + 1) / 2) * 32 + fixed_bytes(); }
+    static int smem_bytes(int M) { return pair_blocks(M) * 1024 + fixed_bytes(); }
 };
 
 // barrier of one item group (named barrier 1 + group, its S warps; the
@@ -1439,10 +1476,9 @@ __global__ void __launch_bounds__(P * S * 32, MINB) collide_slice_kernel(const R
     using K = CollideSliceKernel<S, P>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int npairs = (a.M + 1) / 2;
-    const int sp = GLOBAL_PTS ? 0 : npairs;                      // pairs held in shared memory
-    const float4* XY = GLOBAL_PTS ? a.pXY : reinterpret_cast<float4*>(smem_raw);
-    const float4* V = GLOBAL_PTS ? a.pV : reinterpret_cast<float4*>(smem_raw) + npairs;
-    float4* slotA = reinterpret_cast<float4*>(smem_raw) + 2 * sp;  // [P S][8]
+    const int sb = GLOBAL_PTS ? 0 : pair_blocks(a.M);            // pair blocks held in shared memory
+    const float4* Pts = GLOBAL_PTS ? a.pXY : reinterpret_cast<float4*>(smem_raw);
+    float4* slotA = reinterpret_cast<float4*>(smem_raw) + 64 * sb;  // [P S][8]
     float2* slotB = reinterpret_cast<float2*>(slotA + P * S * 8);  // [P S][8]
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -1454,7 +1490,7 @@ __global__ void __launch_bounds__(P * S * 32, MINB) collide_slice_kernel(const R
     const DevCfg& c = a.c;
     const int T = a.T, N = a.N;
     if (!GLOBAL_PTS) {
-        stage_points<K::THREADS>(a, reinterpret_cast<float4*>(smem_raw), reinterpret_cast<float4*>(smem_raw) + npairs);
+        if (stage_points<K::THREADS>(a, reinterpret_cast<float4*>(smem_raw)) < 0) return;   // a.fault set
         if constexpr (P > 1) __syncthreads();
     }
     const int per = (npairs + S - 1) / S;
@@ -1487,7 +1523,7 @@ __global__ void __launch_bounds__(P * S * 32, MINB) collide_slice_kernel(const R
             const unsigned gone = __ballot_sync(FULL, lane < 8 && *(volatile int*)&dead_at[lane] <= h);
             live &= ~gone;
             if (live == 0u || nslice <= 0) break;
-            const unsigned hits = warp_step(XY + q0, V + q0, nslice, (float)h * c.Ts, cur_a, cur_b,
+            const unsigned hits = warp_step(Pts, q0, q1, (float)h * c.Ts, cur_a, cur_b,
                                             live, sA, sB, lane);
             if ((hits >> lane) & 1u) atomicMin(&dead_at[lane], h);
             live &= ~hits;
@@ -1610,11 +1646,12 @@ int collide_warp_blocks_per_sm(int M)
     return nb > 0 ? nb : 1;
 }
 
-// EV-frame point pairs written to global memory (for point sets larger than
-// shared memory); same arithmetic as stage_points.
+// EV-frame point pairs written to global memory in the staging's blocked
+// layout (for point sets larger than shared memory); same arithmetic as
+// stage_points.
 static __global__ void transform_pairs_kernel(const RolloutArgs a)
 {
-    const int npairs = (a.M + 1) / 2;
+    const int npairs = 32 * pair_blocks(a.M);
     const StepIn si = step_in(a);
     float s0, c0;
     sincosf(si.phi0, &s0, &c0);
@@ -1627,8 +1664,8 @@ static __global__ void transform_pairs_kernel(const RolloutArgs a)
                 ev_point(a.obs[j], si.x0, si.y0, s0, c0, px[o], py[o], vx[o], vy[o]);
             }
         }
-        a.pXY[q] = make_float4(px[0], px[1], py[0], py[1]);
-        a.pV[q] = make_float4(vx[0], vx[1], vy[0], vy[1]);
+        a.pXY[pair_index(q)] = make_float4(px[0], px[1], py[0], py[1]);
+        a.pXY[pair_index(q) + 32] = make_float4(vx[0], vx[1], vy[0], vy[1]);
     }
 }
 
@@ -1636,7 +1673,7 @@ template <int S, int MINB>
 cudaError_t launch_collide_slice_global(const RolloutArgs& a, cudaStream_t stream)
 {
     using K = CollideSliceKernel<S>;
-    const int npairs = (a.M + 1) / 2;
+    const int npairs = 32 * pair_blocks(a.M);
     transform_pairs_kernel<<<max(1, min(1024, (npairs + 255) / 256)), 256, 0, stream>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -96,6 +96,16 @@ def test_fused_infeasible_and_warm_start():
         _assert_same(a, b)
 
 
+def test_points_beyond_shared_memory():
+    """More points than shared memory holds: the brute-force check reads the
+    EV-frame pairs from global memory (written in the staging's blocked
+    layout); the same flags and winner as the binned check."""
+    sc = inputs.tiny_scene(77, N=600, T=10, M=20000, width=16, box=40.0, clear=1.0)
+    brute = _plan(sc, 3)
+    assert np.any(brute["first_hit"] >= 0)
+    _assert_same(_plan(sc, BINNED), brute)
+
+
 def test_binned_without_points():
     sc = inputs.tiny_scene(5, 500, 20, 0, width=16)
     r = _plan(sc, BINNED)

@@ -44,16 +44,15 @@ __global__ void __launch_bounds__(BIN_THREADS) bin_build_kernel(const RolloutArg
 // recomputed from the state).  The warp checks BIN_SB consecutive steps at
 // once, an 8-lane group per step: a step's candidates are the points of at
 // most five cell rows, each row's cells contiguous in the sorted array; the
-// group's lanes stride through them, each lane first issuing the loads of up
-// to BIN_R candidates and then testing them (the rest, rarely any, one by
-// one).  The chunk's first colliding step, if any, ends the sample.  Steps
+// group's lanes stride through each row's run, one candidate per row and
+// lane loaded ahead (binned_item_inside_rows; longer rows one pass at a time
+// after them).  The chunk's first colliding step, if any, ends the sample.  Steps
 // are independent given the stored states, so checking a few past the first
 // collision changes nothing; it replaces one chain of two dependent loads
 // per step (cell bounds, then candidates) by one per chunk.
 constexpr int BINNED_WARPS = 8;
 constexpr int BIN_SB = 32 / BIN_ITEM_LANES; // steps per chunk
 constexpr int BIN_GS = BIN_ITEM_LANES;      // lanes per step
-constexpr int BIN_R = 8;                    // candidates loaded ahead per lane (64 per step)
 
 __global__ void __launch_bounds__(BINNED_WARPS * 32, 5) collide_binned_kernel(const RolloutArgs a)
 {
@@ -85,7 +84,7 @@ __global__ void __launch_bounds__(BINNED_WARPS * 32, 5) collide_binned_kernel(co
             // reference point (reach covers the centre offset)
             const float4 z = ok ? a.traj[(size_t)h * N + n] : make_float4(0.f, 0.f, 0.f, 0.f);
             nstate += (ok && gl == 0) ? 1u : 0u;
-            const bool inside = binned_item_inside<BIN_R>(a.c, g, z, h, ok, gl, ntest);
+            const bool inside = binned_item_inside_rows<1>(a.c, g, z, h, ok, gl, ntest);
             const unsigned bal = __ballot_sync(FULL, inside);
             unsigned steps_hit = 0;
 #pragma unroll

@@ -260,15 +260,15 @@ def algorithmic_work(first_hit, T, M, W):
 
 # source files whose code each profiled kernel is built from
 KERNEL_SOURCES = (
-    ("traj_kernel", ("npp_rollout.cuh", "npp_device.cuh", "npp_rollout_w16.cu", "npp_rollout_w32.cu",
-                     "npp_rollout_w64.cu")),
-    ("fused_kernel", ("npp_rollout.cuh", "npp_device.cuh", "npp_rollout_w16.cu", "npp_rollout_w32.cu",
-                      "npp_rollout_w64.cu")),
-    ("bin_build_kernel", ("npp_binned.cu", "npp_device.cuh")),
-    ("collide_binned_kernel", ("npp_binned.cu", "npp_device.cuh")),
-    ("collide_poly_kernel", ("npp_poly.cu", "npp_device.cuh")),
-    ("collide_", ("npp_rollout.cuh", "npp_device.cuh", "npp_collide.cu")),
-    ("gemm_kernel", ("npp_gemm.cu", "npp_gemm.cuh")),
+    ("traj_kernel", ("npp_rollout.cuh", "npp_device.cuh", "npp_async.cuh", "npp_rollout_w16.cu",
+                     "npp_rollout_w32.cu", "npp_rollout_w64.cu")),
+    ("fused_kernel", ("npp_rollout.cuh", "npp_device.cuh", "npp_async.cuh", "npp_rollout_w16.cu",
+                      "npp_rollout_w32.cu", "npp_rollout_w64.cu")),
+    ("bin_build_kernel", ("npp_binned.cu", "npp_rollout.cuh", "npp_device.cuh", "npp_async.cuh")),
+    ("collide_binned_kernel", ("npp_binned.cu", "npp_rollout.cuh", "npp_device.cuh", "npp_async.cuh")),
+    ("collide_poly_kernel", ("npp_poly.cu", "npp_rollout.cuh", "npp_device.cuh", "npp_async.cuh")),
+    ("collide_", ("npp_rollout.cuh", "npp_device.cuh", "npp_collide.cu", "npp_async.cuh")),
+    ("gemm_kernel", ("npp_gemm.cu", "npp_gemm.cuh", "npp_async.cuh")),
 )
 
 

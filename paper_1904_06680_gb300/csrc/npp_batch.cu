@@ -477,13 +477,17 @@ __global__ void __launch_bounds__(1024) batch_bin_build_kernel(const BatchArgs b
 }
 
 // Binned check of an 8-sample item per block, one warp per sample, over the
-// stored inequality rows (the rectangle's centre recovered from them, as in
-// live_box); the candidates of a step are the points of at most five cell
-// rows of the scene's grid; one key minimum per block.
+// stored inequality rows: four steps at once, eight lanes per step, each
+// cell row's run of candidates taken directly (binned_rows_inside, as the
+// single-scene check); the query disk around the rectangle's centre
+// recovered from its rows (as in live_box).  The chunk's first colliding
+// step ends the sample; one key minimum per block.
 __global__ void __launch_bounds__(256) batch_binned_kernel(const BatchArgs b)
 {
     __shared__ unsigned long long red[8];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gid = lane / BIN_ITEM_LANES, gl = lane % BIN_ITEM_LANES;
+    constexpr int SB = 32 / BIN_ITEM_LANES;            // steps per chunk
     const long long item = blockIdx.x;
     const int r = find_slot(b.citem_prefix, b.S, item);
     const int si = b.order[r];
@@ -495,36 +499,33 @@ __global__ void __launch_bounds__(256) batch_binned_kernel(const BatchArgs b)
     unsigned long long key = ~0ull;
     if (n < N) {
         int fh = -1;
-        // the next step's rows are loaded while the current step is checked
-        float4 nca = b.coefA[s.coef_off + n];
-        float2 ncb = b.coefB[s.coef_off + n];
-        for (int h = 0; h <= T; ++h) {
-            const float4 ca = nca;
-            const float2 cb = ncb;
-            if (h < T) {
-                const long long nx = s.coef_off + (long long)(h + 1) * N + n;
-                nca = b.coefA[nx];
-                ncb = b.coefB[nx];
+        for (int h0 = 0; h0 <= T; h0 += SB) {
+            const int h = h0 + gid;
+            const bool ok = h <= T;
+            float4 ca = make_float4(0.f, 0.f, 0.f, 0.f);
+            float2 cb = make_float2(0.f, 0.f);
+            if (ok) {
+                const long long idx = s.coef_off + (long long)h * N + n;
+                ca = b.coefA[idx];
+                cb = b.coefB[idx];
             }
             const float cp = ca.x * isl, sp = ca.y * isl;
             const float along = -ca.z * isl, across = -cb.y * isw;
             const float xc = cp * along - sp * across, yc = sp * along + cp * across;
-            const CandRows cr = cand_rows(b.bin_cs + s.bin_off + (size_t)h * BIN_CS_STRIDE, g, xc, yc, b.reach);
-            const float2* pts = b.bin_pts + s.bpts_off + (size_t)h * M;
-            const int total = cr.total;
-            bool hit = false;
-            for (int base = 0; base < total && !hit; base += 32) {
-                const int k = base + lane;
-                bool inside = false;
-                if (k < total) {
-                    const float2 p = pts[cr.index(k)];
-                    const float xi = fmaf(ca.x, p.x, fmaf(ca.y, p.y, ca.z));
-                    const float et = fmaf(ca.w, p.x, fmaf(cb.x, p.y, cb.y));
-                    inside = !(((__float_as_uint(xi) | __float_as_uint(et)) >> 30) & 1u);
-                }
-                hit = __any_sync(FULL, inside);
+            const int hq = ok ? h : 0;
+            unsigned ntest = 0;
+            const bool inside = binned_rows_inside<1>(g, b.bin_cs + s.bin_off + (size_t)hq * BIN_CS_STRIDE,
+                                                      b.bin_pts + s.bpts_off + (size_t)hq * M, ca, cb, xc, yc,
+                                                      b.reach, ok, gl, ntest);
+            const unsigned bal = __ballot_sync(FULL, inside);
+            unsigned steps_hit = 0;
+#pragma unroll
+            for (int k = 0; k < SB; ++k)
+                if ((bal >> (k * BIN_ITEM_LANES)) & ((1u << BIN_ITEM_LANES) - 1u)) steps_hit |= 1u << k;
+            if (steps_hit) {
+                fh = h0 + __ffs(steps_hit) - 1;
+                break;
             }
-            if (hit) { fh = h; break; }
         }
         if (lane == 0) {
             fh = discard_step(b.vfirst ? b.vfirst + s.samp_off : nullptr, n, fh);

@@ -410,16 +410,14 @@ __device__ __forceinline__ bool binned_item_inside(const DevCfg& c, const BinVie
 // against 0.078 ms on the course (25); inside the trajectory kernel's
 // window check it costs registers (spills) and is not used there.
 template <int RR>
-__device__ __forceinline__ bool binned_item_inside_rows(const DevCfg& c, const BinView& g, const float4& z, int h,
-                                                        bool ok, int gl, unsigned& ntest)
+__device__ __forceinline__ bool binned_rows_inside(const BinView& g, const int* __restrict__ cs,
+                                                   const float2* __restrict__ pts, const float4& ca,
+                                                   const float2& cb, float qx, float qy, float reach, bool ok,
+                                                   int gl, unsigned& ntest)
 {
     constexpr int L = BIN_ITEM_LANES;
-    float4 ca;
-    float2 cb;
-    rows_of_state(c, z, ca, cb);
     CandRows cr = {};
-    if (ok) cr = cand_rows(g.cell_start + (size_t)h * BIN_CS_STRIDE, g, z.x, z.y, g.reach);
-    const float2* pts = g.pts + (size_t)(ok ? h : 0) * g.M;
+    if (ok) cr = cand_rows(cs, g, qx, qy, reach);
     int len[BIN_MAX_ROWS];
 #pragma unroll
     for (int r = 0; r < BIN_MAX_ROWS; ++r) len[r] = cr.e[r] - (r > 0 ? cr.e[r - 1] : 0);
@@ -455,6 +453,19 @@ __device__ __forceinline__ bool binned_item_inside_rows(const DevCfg& c, const B
         }
     }
     return inside;
+}
+
+// the row-wise item check of state z at step h of grid g (its rows
+// recomputed, the query disk around its reference point)
+template <int RR>
+__device__ __forceinline__ bool binned_item_inside_rows(const DevCfg& c, const BinView& g, const float4& z, int h,
+                                                        bool ok, int gl, unsigned& ntest)
+{
+    float4 ca;
+    float2 cb;
+    rows_of_state(c, z, ca, cb);
+    return binned_rows_inside<RR>(g, g.cell_start + (size_t)(ok ? h : 0) * BIN_CS_STRIDE,
+                                  g.pts + (size_t)(ok ? h : 0) * g.M, ca, cb, z.x, z.y, g.reach, ok, gl, ntest);
 }
 
 // ------------------------------------------------------------------ bins

@@ -314,13 +314,18 @@ __device__ __forceinline__ float4 live_box(const DevCfg& c, float4 ca, float2 cb
                        __shfl_sync(FULL, ymx, 0));
 }
 
-template <int W, int G, int NW, bool VAR = false>
-__global__ void __launch_bounds__(NW * 32) batch_traj_kernel(const BatchArgs b, int wi)
+// KSQ > 0: the last KSQ layer-2 input quads of each lane in shared memory
+// (as the single-scene width-64 kernel: 128 registers and MINB blocks per
+// SM instead of every weight in registers at 250)
+template <int W, int G, int NW, bool VAR = false, int KSQ = 0, int MINB = 1>
+__global__ void __launch_bounds__(NW * 32, MINB) batch_traj_kernel(const BatchArgs b, int wi)
 {
     constexpr int B = TrajKernel<W, G, NW>::B;
     __shared__ __align__(16) float hx_all[B * W];
     __shared__ long long qslot;
-    extern __shared__ float stage_all[];        // [LaneNet::SLOTS][NW * 32] when W == 32
+    // [LaneNet::SLOTS][NW * 32] floats when W == 32 (KSQ = 0); the shared W2
+    // quads [group][U][KSQ][G] of 16 bytes when KSQ > 0
+    extern __shared__ __align__(16) float stage_all[];
     const int tid = threadIdx.x;
     const int bi = tid / G, gl = tid % G;
     const int n_sc = b.n_torder[wi];
@@ -343,6 +348,8 @@ __global__ void __launch_bounds__(NW * 32) batch_traj_kernel(const BatchArgs b, 
         job.bins = nullptr;
         job.stage = stage_all + tid;
         job.w2s = nullptr;
+        if constexpr (KSQ > 0)
+            job.w2s = reinterpret_cast<ulonglong2*>(stage_all) + (size_t)bi * (Shape<W, G>::U * KSQ * G) + gl;
         job.N = s.N;
         job.T = s.T;
         job.traj = nullptr;
@@ -354,8 +361,8 @@ __global__ void __launch_bounds__(NW * 32) batch_traj_kernel(const BatchArgs b, 
         job.coef_base = s.coef_off;
         job.jfree = b.jfree + s.samp_off;
         job.vfirst = b.vfirst ? b.vfirst + s.samp_off : nullptr;
-        constexpr int STAGE_TH = W == 32 ? NW * 32 : 0;     // as traj_kernel
-        traj_sample<W, G, STAGE_TH, VAR>(b.c, job, n, n < s.N, gl, hx_all + bi * W);
+        constexpr int STAGE_TH = (W == 32 && KSQ == 0) ? NW * 32 : 0;     // as traj_kernel
+        traj_sample<W, G, STAGE_TH, VAR, KSQ>(b.c, job, n, n < s.N, gl, hx_all + bi * W);
     }
 }
 
@@ -750,18 +757,26 @@ cudaError_t collide_grid(npp_batch* B, int* grid)
 template <int W, int G>
 constexpr int batch_stage_bytes(int nw) { return W == 32 ? LaneNet<W, G>::SLOTS * nw * 32 * (int)sizeof(float) : 0; }
 
+// width 64: 8 of 16 layer-2 input quads per lane in shared memory, 16 warps
+// per SM (the single-scene default; 250 registers and 8 warps per SM with
+// every weight in registers)
+constexpr int BATCH_KSQ64 = 8;
+constexpr int batch_w2s_bytes64(int nw) { return nw * 32 * 2 * BATCH_KSQ64 * 16; }
+
 template <int NW>
 void traj_grids(npp_batch* B)
 {
     int nt = 0;
     const int s16 = batch_stage_bytes<16, 8>(NW), s32 = batch_stage_bytes<32, 16>(NW);
     ensure_smem(batch_traj_kernel<16, 8, NW>, s16);
-    ensure_smem(batch_traj_kernel<32, 16, NW>, s32);
+    ensure_smem(batch_traj_kernel<32, 16, NW, false, 0, 16 / NW>, s32);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nt, batch_traj_kernel<16, 8, NW>, NW * 32, s16);
     B->grid_traj[0] = B->h->sm_count * std::max(1, nt);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nt, batch_traj_kernel<32, 16, NW>, NW * 32, s32);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nt, batch_traj_kernel<32, 16, NW, false, 0, 16 / NW>, NW * 32, s32);
     B->grid_traj[1] = B->h->sm_count * std::max(1, nt);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nt, batch_traj_kernel<64, 32, NW>, NW * 32, 0);
+    auto k64 = batch_traj_kernel<64, 32, NW, false, BATCH_KSQ64, 16 / NW>;
+    ensure_smem(k64, batch_w2s_bytes64(NW));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nt, k64, NW * 32, batch_w2s_bytes64(NW));
     B->grid_traj[2] = B->h->sm_count * std::max(1, nt);
 }
 
@@ -819,10 +834,14 @@ void launch_batch_traj_v(npp_batch* B, const BatchArgs& b, cudaStream_t s)
         batch_traj_kernel<16, 8, NW, VAR><<<B->grid_traj[0], NW * 32, batch_stage_bytes<16, 8>(NW), s>>>(b, 0);
     }
     if (B->n_torder[1]) {
-        ensure_smem(batch_traj_kernel<32, 16, NW, VAR>, batch_stage_bytes<32, 16>(NW));
-        batch_traj_kernel<32, 16, NW, VAR><<<B->grid_traj[1], NW * 32, batch_stage_bytes<32, 16>(NW), s>>>(b, 1);
+        ensure_smem(batch_traj_kernel<32, 16, NW, VAR, 0, 16 / NW>, batch_stage_bytes<32, 16>(NW));
+        batch_traj_kernel<32, 16, NW, VAR, 0, 16 / NW><<<B->grid_traj[1], NW * 32, batch_stage_bytes<32, 16>(NW), s>>>(b, 1);
     }
-    if (B->n_torder[2]) batch_traj_kernel<64, 32, NW, VAR><<<B->grid_traj[2], NW * 32, 0, s>>>(b, 2);
+    if (B->n_torder[2]) {
+        auto k64 = batch_traj_kernel<64, 32, NW, VAR, BATCH_KSQ64, 16 / NW>;
+        ensure_smem(k64, batch_w2s_bytes64(NW));
+        k64<<<B->grid_traj[2], NW * 32, batch_w2s_bytes64(NW), s>>>(b, 2);
+    }
 }
 
 // rollout variants (body-frame features, speed limits) in their own kernels

@@ -51,6 +51,7 @@ struct BatchArgs {
     float4* tileP;                   // per tile of 32 pairs: (min x, max x, min y, max y) of its points
     float4* tileV;                   // (min vx, max vx, min vy, max vy)
     float reach;                     // radius around a rectangle's centre that holds it, plus a margin
+    int windowed64;                  // width-64 scenes checked inside their trajectory kernel
     // binned collision check (per scene and horizon step)
     BinView grid;                    // geometry (cell_start, pts, M unused here)
     int* bin_cs;                     // cell tables, scene s at bin_off
@@ -317,7 +318,12 @@ __device__ __forceinline__ float4 live_box(const DevCfg& c, float4 ca, float2 cb
 // KSQ > 0: the last KSQ layer-2 input quads of each lane in shared memory
 // (as the single-scene width-64 kernel: 128 registers and MINB blocks per
 // SM instead of every weight in registers at 250)
-template <int W, int G, int NW, bool VAR = false, int KSQ = 0, int MINB = 1>
+// WIN: the scene's binned check done window by window inside the kernel
+// (traj_sample_windowed, windows of BATCH_CW states, the scene's grids built
+// before the launch): each sample's cost, first collision and the scene's
+// key are written here, nothing per step is stored
+constexpr int BATCH_CW = 8;
+template <int W, int G, int NW, bool VAR = false, int KSQ = 0, int MINB = 1, bool WIN = false>
 __global__ void __launch_bounds__(NW * 32, MINB) batch_traj_kernel(const BatchArgs b, int wi)
 {
     constexpr int B = TrajKernel<W, G, NW>::B;
@@ -362,7 +368,37 @@ __global__ void __launch_bounds__(NW * 32, MINB) batch_traj_kernel(const BatchAr
         job.jfree = b.jfree + s.samp_off;
         job.vfirst = b.vfirst ? b.vfirst + s.samp_off : nullptr;
         constexpr int STAGE_TH = (W == 32 && KSQ == 0) ? NW * 32 : 0;     // as traj_kernel
-        traj_sample<W, G, STAGE_TH, VAR, KSQ>(b.c, job, n, n < s.N, gl, hx_all + bi * W);
+        if constexpr (WIN) {
+            const int si = b.torder[wi][r];
+            BinView bv = b.grid;
+            bv.cell_start = b.bin_cs + s.bin_off;
+            bv.pts = b.bin_pts + s.bpts_off;
+            bv.M = s.M;
+            job.bins = &bv;
+            job.coefA = nullptr;
+            job.coefB = nullptr;
+            job.jfree = nullptr;
+            job.vfirst = nullptr;
+            float4* wnd = reinterpret_cast<float4*>(reinterpret_cast<char*>(stage_all) +
+                                                    NW * 32 * Shape<W, G>::U * KSQ * 16) +
+                          (size_t)(tid / 32) * (32 / G) * BATCH_CW;
+            unsigned steps = 0, ntest = 0, nstate = 0;
+            const bool valid = n < s.N;
+            const FusedOut o = traj_sample_windowed<W, G, STAGE_TH, VAR, KSQ, BATCH_CW, 4>(
+                b.c, job, n, valid, gl, hx_all + bi * W, wnd, steps, ntest, nstate);
+            if (valid && gl == 0) {
+                unsigned long long key;
+                if (o.first_hit < 0)
+                    key = ((unsigned long long)__float_as_uint(o.cost) << 32) | (unsigned)n;
+                else
+                    key = (1ull << 63) | ((unsigned long long)(s.T - o.first_hit) << 32) | (unsigned)n;
+                if (b.costs) b.costs[s.samp_off + n] = o.cost;
+                if (b.first_hit) b.first_hit[s.samp_off + n] = o.first_hit;
+                if (key < *reinterpret_cast<volatile unsigned long long*>(b.keys + si)) atomicMin(b.keys + si, key);
+            }
+        } else {
+            traj_sample<W, G, STAGE_TH, VAR, KSQ>(b.c, job, n, n < s.N, gl, hx_all + bi * W);
+        }
     }
 }
 
@@ -499,6 +535,7 @@ __global__ void __launch_bounds__(256) batch_binned_kernel(const BatchArgs b)
     const int r = find_slot(b.citem_prefix, b.S, item);
     const int si = b.order[r];
     const SceneDev& s = b.scenes[si];
+    if (b.windowed64 && s.width == 64) return;       // checked inside the trajectory kernel (block-uniform)
     const int T = s.T, N = s.N, M = s.M;
     const int n = (int)(item - __ldg(b.citem_prefix + r)) * 8 + warp;
     const BinView& g = b.grid;
@@ -762,6 +799,11 @@ constexpr int batch_stage_bytes(int nw) { return W == 32 ? LaneNet<W, G>::SLOTS 
 // every weight in registers)
 constexpr int BATCH_KSQ64 = 8;
 constexpr int batch_w2s_bytes64(int nw) { return nw * 32 * 2 * BATCH_KSQ64 * 16; }
+// with the windowed check: the W2 quads of 12 inputs per lane in shared
+// memory (registers for the check, as the single-scene kernel) and the
+// warps' windows of states
+constexpr int BATCH_KSQ64W = 12;
+constexpr int batch_w64w_bytes(int nw) { return nw * 32 * 2 * BATCH_KSQ64W * 16 + nw * BATCH_CW * 16; }
 
 template <int NW>
 void traj_grids(npp_batch* B)
@@ -837,7 +879,11 @@ void launch_batch_traj_v(npp_batch* B, const BatchArgs& b, cudaStream_t s)
         ensure_smem(batch_traj_kernel<32, 16, NW, VAR, 0, 16 / NW>, batch_stage_bytes<32, 16>(NW));
         batch_traj_kernel<32, 16, NW, VAR, 0, 16 / NW><<<B->grid_traj[1], NW * 32, batch_stage_bytes<32, 16>(NW), s>>>(b, 1);
     }
-    if (B->n_torder[2]) {
+    if (B->n_torder[2] && b.windowed64) {
+        auto k64 = batch_traj_kernel<64, 32, NW, VAR, BATCH_KSQ64W, 16 / NW, true>;
+        ensure_smem(k64, batch_w64w_bytes(NW));
+        k64<<<B->grid_traj[2], NW * 32, batch_w64w_bytes(NW), s>>>(b, 2);
+    } else if (B->n_torder[2]) {
         auto k64 = batch_traj_kernel<64, 32, NW, VAR, BATCH_KSQ64, 16 / NW>;
         ensure_smem(k64, batch_w2s_bytes64(NW));
         k64<<<B->grid_traj[2], NW * 32, batch_w2s_bytes64(NW), s>>>(b, 2);
@@ -993,6 +1039,7 @@ npp_status npp_plan_batch(npp_batch* B, const float* obs_dev, const npp_batch_ou
     b.reach = (float)(std::sqrt((double)h->cfg.half_len * h->cfg.half_len + (double)h->cfg.half_wid * h->cfg.half_wid)
                       + std::fabs((double)h->cfg.c_off) + 0.1);
     b.grid = make_bin_grid(h->cfg.half_len, h->cfg.half_wid, h->cfg.c_off);
+    b.windowed64 = B->binned ? 1 : 0;
     b.bin_cs = B->d_bin_cs;
     b.bin_pts = B->d_bin_pts;
     b.bstep_prefix = B->d_bstep_prefix;
@@ -1028,16 +1075,18 @@ npp_status npp_plan_batch(npp_batch* B, const float* obs_dev, const npp_batch_ou
         batch_prologue_kernel<<<B->S, SORT_THREADS, smem, s>>>(b);
         CUDA_TRY(h, cudaGetLastError());
     }
+    // with the binned check the grids come first: the width-64 scenes are
+    // checked inside their trajectory kernel (windowed), the others after
+    if (B->binned && B->bin_blocks > 0) {
+        const int smem = BIN_NCELL * (int)sizeof(int);
+        CUDA_TRY(h, ensure_smem(batch_bin_build_kernel, smem));
+        batch_bin_build_kernel<<<(unsigned)B->bin_blocks, 1024, smem, s>>>(b);
+        CUDA_TRY(h, cudaGetLastError());
+    }
     if (B->traj_warps == 4) launch_batch_traj<4>(B, b, s); else launch_batch_traj<8>(B, b, s);
     CUDA_TRY(h, cudaGetLastError());
     if (h->timing) CUDA_TRY(h, record_event(h->ev[1], s));
     if (B->binned) {
-        if (B->bin_blocks > 0) {
-            const int smem = BIN_NCELL * (int)sizeof(int);
-            CUDA_TRY(h, ensure_smem(batch_bin_build_kernel, smem));
-            batch_bin_build_kernel<<<(unsigned)B->bin_blocks, 1024, smem, s>>>(b);
-            CUDA_TRY(h, cudaGetLastError());
-        }
         batch_binned_kernel<<<(unsigned)B->total_items, 256, 0, s>>>(b);
     } else {
         switch (B->slices) {

@@ -242,6 +242,20 @@ npp_status npp_math_eval(int32_t fn, const float* x_dev, int32_t n, float* y_dev
  * NPP_CUDA_ERROR if the device is unavailable. */
 npp_status npp_measure_fma_peak(int32_t device, int32_t packed, double* fma_per_s);
 
+/* Failure detection (no counterpart in the paper).  npp_wait_probe runs the
+ * library's bounded mbarrier wait (the one of the obstacle-point staging and
+ * the GEMM pipeline) in one block on the current device, on a barrier whose
+ * single expected arrival happens (arrive = 1) or never happens (arrive =
+ * 0), with a limit of limit_cycles clock cycles (1 .. 4e9); writes 1 to
+ * *completed_host if the wait saw the phase complete, 0 if it gave up.  The
+ * context stays usable either way.  Synchronous.
+ * npp_inject_fault sets the handle's device fault flag exactly as a timed-out
+ * wait of a plan step's kernels does: the next plan step reports
+ * NPP_DEVICE_TIMEOUT in its npp_best.status (npp_plan_step_host returns it)
+ * and clears the flag. */
+npp_status npp_wait_probe(int64_t limit_cycles, int32_t arrive, int32_t* completed_host);
+npp_status npp_inject_fault(npp_handle* h);
+
 /* ---------------------------------------------------------------------
  * Device-resident closed loop (Alg. 1): each sampling time is one CUDA graph
  * replay holding the plan step and an advance kernel that applies the

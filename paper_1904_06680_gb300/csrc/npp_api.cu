@@ -786,6 +786,15 @@ npp_status npp_set_option(npp_handle* h, const char* name, int32_t value)
     return fail(h, NPP_INVALID_ARG, "unknown option '%s'", name);
 }
 
+npp_status npp_inject_fault(npp_handle* h)
+{
+    if (!h) return fail(nullptr, NPP_INVALID_ARG, "handle is NULL");
+    CUDA_TRY(h, cudaSetDevice(h->device));
+    const unsigned one = 1u;
+    CUDA_TRY(h, cudaMemcpy(h->d_fault, &one, sizeof one, cudaMemcpyHostToDevice));
+    return NPP_OK;
+}
+
 npp_status npp_set_timing(npp_handle* h, int32_t enable)
 {
     if (!h) return fail(nullptr, NPP_INVALID_ARG, "handle is NULL");

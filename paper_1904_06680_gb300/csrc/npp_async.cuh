@@ -50,12 +50,19 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity)
     return ok != 0;
 }
 
-// bounded wait for the phase with the given parity to complete
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+// one arrival on bar (no transaction bytes)
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// bounded wait for the phase with the given parity to complete: false once
+// `limit` clock cycles have passed without it
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit = WAIT_CYCLES)
 {
     const long long t0 = clock64();
     while (!mbar_try(bar, parity))
-        if (clock64() - t0 > WAIT_CYCLES) return false;
+        if (clock64() - t0 > limit) return false;
     return true;
 }
 

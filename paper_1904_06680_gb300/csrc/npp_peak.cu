@@ -8,8 +8,26 @@
 
 #include "../../include/npp.h"
 #include "npp_internal.h"
+#include "npp_async.cuh"
 
 namespace {
+
+// The bounded mbarrier wait of the staging copies and the GEMM pipeline on
+// a barrier of one expected arrival: with `arrive` the block's first thread
+// arrives and the phase completes; without it nothing ever arrives and the
+// wait must give up after `limit` cycles and report it.
+__global__ void wait_probe_kernel(long long limit, int arrive, int* out)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        npp::mbar_init(&bar, 1);
+        npp::mbar_init_fence();
+    }
+    __syncthreads();
+    if (arrive && threadIdx.x == 0) npp::mbar_arrive(&bar);
+    const bool done = npp::mbar_wait(&bar, 0, limit);
+    if (threadIdx.x == 0) *out = done ? 1 : 0;
+}
 
 constexpr int PEAK_THREADS = 256;
 constexpr int PEAK_BLOCKS_PER_SM = 8;
@@ -89,5 +107,29 @@ extern "C" npp_status npp_measure_fma_peak(int32_t device, int32_t packed, doubl
         return NPP_CUDA_ERROR;
     }
     *fma_per_s = (double)blocks * PEAK_THREADS * (double)iters * 8.0 / (best_ms * 1e-3);
+    return NPP_OK;
+}
+
+extern "C" npp_status npp_wait_probe(int64_t limit_cycles, int32_t arrive, int32_t* completed_host)
+{
+    if (!completed_host || limit_cycles < 1 || limit_cycles > 4000000000LL || (arrive != 0 && arrive != 1)) {
+        npp::set_global_error("npp_wait_probe: limit outside [1, 4e9] cycles, arrive not 0/1 or NULL output");
+        return NPP_INVALID_ARG;
+    }
+    int* d = nullptr;
+    cudaError_t e = cudaMalloc((void**)&d, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(d, 0xff, sizeof(int));
+    if (e == cudaSuccess) {
+        wait_probe_kernel<<<1, 32>>>((long long)limit_cycles, arrive, d);
+        e = cudaGetLastError();
+    }
+    int v = -1;
+    if (e == cudaSuccess) e = cudaMemcpy(&v, d, sizeof(int), cudaMemcpyDeviceToHost);
+    if (d) cudaFree(d);
+    if (e != cudaSuccess) {
+        npp::set_global_error("npp_wait_probe: launch or copy failed");
+        return NPP_CUDA_ERROR;
+    }
+    *completed_host = v;
     return NPP_OK;
 }

@@ -84,7 +84,8 @@ EXPORTS = ("npp_create", "npp_destroy", "npp_last_error", "npp_n_theta", "npp_pl
            "npp_proposal_set_params", "npp_proposal_get_params", "npp_proposal_get_grads",
            "npp_proposal_encode", "npp_proposal_forward", "npp_proposal_train_step",
            "npp_plan_step_proposal", "npp_gemm_bf16", "npp_gemm_status", "npp_plan_tshc",
-           "npp_loop_create_mission", "npp_loop_points", "npp_measure_fma_peak", "npp_set_loop_restarts", "npp_last_counts")
+           "npp_loop_create_mission", "npp_loop_points", "npp_measure_fma_peak", "npp_set_loop_restarts", "npp_last_counts",
+           "npp_wait_probe", "npp_inject_fault")
 
 _lib = None
 
@@ -115,6 +116,8 @@ def lib():
         L.npp_set_option.argtypes = [P, C.c_char_p, I32]
         L.npp_set_footprint.argtypes = [P, C.c_void_p, C.c_void_p, I32]
         L.npp_measure_fma_peak.argtypes = [I32, I32, C.POINTER(C.c_double)]
+        L.npp_wait_probe.argtypes = [C.c_int64, I32, C.POINTER(I32)]
+        L.npp_inject_fault.argtypes = [P]
         L.npp_loop_create.argtypes = [P, C.POINTER(npp_state), P, I32, P, P, I32, I32, I32, U64, I32,
                                       C.POINTER(P)]
         L.npp_loop_run.argtypes = [P, I32, P]
@@ -420,6 +423,19 @@ def npp_last_counts(h):
     c = (C.c_uint64 * 3)()
     _check(lib().npp_last_counts(h, c, 3), h)
     return int(c[0]), int(c[1]), int(c[2])
+
+
+def npp_wait_probe(limit_cycles: int, arrive: bool):
+    """Run the library's bounded mbarrier wait on a barrier whose one arrival
+    happens (arrive) or never does; True if the wait saw it complete."""
+    v = C.c_int32(-1)
+    _check(lib().npp_wait_probe(int(limit_cycles), int(bool(arrive)), C.byref(v)))
+    return v.value == 1
+
+
+def npp_inject_fault(h):
+    """Set the handle's device fault flag as a timed-out wait would."""
+    _check(lib().npp_inject_fault(h), h)
 
 
 def npp_set_loop_restarts(h, n_restarts: int, sigma_pert: float = 0.0):

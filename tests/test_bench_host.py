@@ -1,6 +1,8 @@
 """Host-side pieces of the benchmark that decide reported outcomes, checked
 on the CPU: the collision check of executed poses (mission success) against
 the oracle's point-in-rectangle test, and the algorithmic-work counts."""
+import os
+
 import numpy as np
 
 import bench
@@ -32,3 +34,24 @@ def test_algorithmic_work_counts():
     assert checks == live_states * M
     assert fma_c == 4.0 * checks
     assert fma_t == (T + 0 + 5 + 39) * (W * W + 10 * W)
+
+
+def test_profiled_traffic_entries_are_current():
+    """Every DRAM-traffic entry in profiles/traffic.json names a kernel whose
+    CUDA sources are known and unchanged since the capture (an entry whose
+    kernel changed would report counters of other code); the per-workload
+    entries of kernels used by several workloads are found by workload."""
+    import json
+    import bench
+    rec = json.load(open(os.path.join(os.path.dirname(bench.__file__), "profiles", "traffic.json")))
+    assert rec["kernels"]
+    for key, ent in rec["kernels"].items():
+        name = key.split("@")[0]
+        assert bench.kernel_sources_hash(name) is not None, key
+        assert ent["sources"] == bench.kernel_sources_hash(name), key
+        assert ent["dram_bytes_per_launch"] == ent["read"] + ent["write"], key
+        assert "--clock-control none" in ent["command"], key
+    for key in rec["kernels"]:
+        if "@" in key:
+            name, wl = key.split("@")
+            assert bench.profiled_traffic(name, wl) == rec["kernels"][key]["dram_bytes_per_launch"]

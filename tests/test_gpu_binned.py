@@ -58,9 +58,9 @@ def _assert_same(a, b):
 @pytest.mark.parametrize("seed,N,T,M", [(1, 300, 20, 200), (2, 1000, 33, 1500), (3, 77, 5, 1),
                                         (4, 4096, 40, 5000)])
 def test_binned_equals_brute_force_random(seed, N, T, M):
-    """Stored-rows (default) and fused binned checks against
-    brute force: every sample's flag and cost, the winner and its re-rolled
-    rows."""
+    """The two-kernel binned check and the windowed check inside the
+    trajectory kernel (fuse=1) against brute force: every sample's flag and
+    cost, the winner and its rows."""
     sc = inputs.tiny_scene(seed, N, T, M, width=32, box=25.0, clear=2.0)
     brute = _plan(sc, 3)
     _assert_same(_plan(sc, BINNED), brute)
@@ -76,9 +76,10 @@ def test_fused_binned_other_widths(width):
 
 
 def test_fused_infeasible_and_warm_start():
-    """All samples collide (a converging ring of points): the fused path
-    reports the latest first collision and the winner's rows repeat the
-    colliding state with zero controls after it, as the stored path does."""
+    """All samples collide (a converging ring of points): the windowed
+    check reports the latest first collision and the winner's rows repeat
+    the colliding state with zero controls after it, as the two-kernel path
+    does.""""
     import torch
     from paper_1904_06680_gb300 import npp
     p = inputs.planner(32)
@@ -217,7 +218,7 @@ def test_binned_closed_loop_identical_to_brute_force():
 @pytest.mark.parametrize("N,T,M", [(1, 1, 0), (1, 1, 1), (1, 3, 600), (33, 1, 600), (5, 2, 2)])
 def test_all_variants_at_extreme_sizes(N, T, M):
     """One sample, one step, no or one point: every collision variant (brute
-    force 0-4, binned stored and fused) gives the same result."""
+    force 0-4, binned in two kernels and windowed) gives the same result."""
     sc = inputs.tiny_scene(60 + N + T + M, N, T, M, width=16, box=6.0, clear=1.0)
     ref = _plan(sc, 2)
     for v in (0, 1, 3, 4):

@@ -79,7 +79,7 @@ def test_fused_infeasible_and_warm_start():
     """All samples collide (a converging ring of points): the windowed
     check reports the latest first collision and the winner's rows repeat
     the colliding state with zero controls after it, as the two-kernel path
-    does.""""
+    does."""
     import torch
     from paper_1904_06680_gb300 import npp
     p = inputs.planner(32)

@@ -1,12 +1,17 @@
 #!/usr/bin/env python
 """Planner benchmark: rollout-steps/s of the closed-loop plan step.
 
-Workload (one GPU): the forward/reverse waypoint course, N = 16384 sampled
-8-32-32-2 networks per plan step, horizon T = 40, 2000 obstacle points (500
-on moving car outlines).  A "step" is one sampling time of the closed loop
-run on the device as one CUDA-graph replay: sampling, rollout, collision
-checks, selection, winner epilogue, then the simulated vehicle, obstacle and
-waypoint advance; the winner's parameters warm-start the next step.
+Default workload (one GPU, the largest single-GPU configuration): the large
+closed loop, N = 65536 sampled 8-64-64-2 networks per plan step, horizon
+T = 100, M = 8192 obstacle points (20 % on moving car outlines) in an
+80 x 80 m area, per-step spatial binning of the points.  A "step" is one
+sampling time of the closed loop run on the device as one CUDA-graph
+replay: sampling, rollout, collision checks (at width 64 window by window
+inside the trajectory kernel), selection, winner epilogue, then the
+simulated vehicle, obstacle and waypoint advance; the winner's parameters
+warm-start the next step.  `--workload course` runs the forward/reverse
+waypoint course (N = 16384, T = 40, 8-32-32-2, M = 2000); batch, proposal
+and mission are the other workloads.
 
 value   = N * T * K / (sum of the K steps' device time), inputs resident in
           HBM, L2 flushed (256 MiB write) between steps, CUDA events captured
@@ -14,16 +19,19 @@ value   = N * T * K / (sum of the K steps' device time), inputs resident in
 e2e     = the same closed loop through the host-buffer entry point (obstacle
           copy in, plan, result copy out, synchronise, host vehicle model),
           wall clock per plan call;
-roofline = the collision kernel (the dominant one): algorithmic FP32 FMAs
-          (4 per point-check of a live sample: two rows of the rotated
-          inequality test) over its event-timed duration, against the FMA
-          peak 152 SMs x 128 lanes x 2.07 GHz; `traffic` comes from the
-          committed ncu summary while the kernel sources are unchanged.
+roofline = the dominant kernel (the trajectory kernel, with the windowed
+          check at width 64): algorithmic FP32 FMAs (W^2 + 10 W per control
+          step of a sample up to its first collision) over its event-timed
+          duration, against the FMA peak SMs x 128 lanes x the maximum SM
+          clock (read from the device); with a brute-force check chosen
+          (--set collide_variant=0..4) the collision kernel, 4 FMAs per
+          point check of a live sample; `traffic` comes from the committed
+          ncu summary while the kernel sources are unchanged.
 
 `--impl reference` times the CPU oracle on the host cores on the same
 workload with a bounded number of samples per step.
-Multi-GPU (torchrun): every rank plans its own course scene (weak scaling,
-no collective on the data path); max over ranks.
+Multi-GPU (torchrun): every rank plans its own scene (weak scaling, no
+collective on the data path); max over ranks.
 """
 import argparse
 import json

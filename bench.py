@@ -53,6 +53,7 @@ UNIT = "rollout-steps/s"
 DEFAULT_FUSE = -1                # the library's default of the "fuse" option (-1: at width 64)
 FP32_LANES_PER_SM = 128          # FP32 FMA lanes per SM (4 schedulers x 32) on sm_100-class parts
 SM_MAX_MHZ_NOMINAL = 2070.0      # GB300 maximum SM clock, used only when the device does not report it
+BIN_DIM = 128                    # cells per side of the library's per-step grids (the grid build's table size)
 
 
 def parse():
@@ -500,9 +501,28 @@ def run_npp(args):
         fma_rolled = rolled * (W * W + 10 * W)
         check = {}
         if res["states"] > 0:
+            # the window check's algorithmic reads (L2-resident grids): per
+            # state checked the ten cell-run bounds of its query (40 B; the
+            # state itself is in the warp's shared window), per candidate
+            # test one point (8 B)
+            wbytes = res["states"] * 40.0 + res["cand_tests"] * 8.0
             check = {"candidate_tests_per_state": res["cand_tests"] / res["states"],
                      "states_checked_per_plan_step": res["states"] / K,
-                     "candidate_tests_per_s": res["cand_tests"] / (collide_ms / 1e3)}
+                     "candidate_tests_per_s": res["cand_tests"] / (collide_ms / 1e3),
+                     "bytes_per_step": wbytes / K, "achieved_gbs": wbytes / (collide_ms / 1e3) / 1e9,
+                     "bytes_note": "algorithmic grid reads: 40 B per state checked (ten cell-run "
+                                   "bounds), 8 B per candidate test, over the kernel's duration"}
+        # the grid build's algorithmic bytes per plan step: for each of the
+        # T + 1 grids the M world points read twice (count, scatter; 16 B
+        # each), the cell-start table and the sorted points written
+        bin_bytes = (T + 1) * (32.0 * M + 4.0 * (BIN_DIM * BIN_DIM + 1) + 8.0 * M)
+        bin_s = traj_ms / K / 1e3
+        bins = {"ms_per_step": traj_ms / K, "bytes_per_step": bin_bytes,
+                "achieved_gbs": bin_bytes / bin_s / 1e9 if bin_s > 0 else None,
+                "traffic": profiled_traffic("bin_build_kernel", args.workload),
+                "bytes_note": "algorithmic: per grid the M points read twice (16 B), the cell-start "
+                              "table and M sorted points (8 B) written; traffic = DRAM bytes per launch "
+                              "from profiles/traffic.json (the grids stay in L2)"}
         roofline = {"bound": "alu", "kernel": fname, "achieved": fps / 1e12, "peak": peak / 1e12,
                     "unit": "T FP32-FMA/s", "frac": fps / peak, "traffic": profiled_traffic(fname, args.workload),
                     "peak_basis": peak_basis, "peak_measured": fma_measured,
@@ -516,7 +536,7 @@ def run_npp(args):
                     "rolled_steps_frac": fma_rolled / (collide_ms / 1e3) / peak,
                     "kernel_ms_per_step": collide_ms / K,
                     "windowed_check": check,
-                    "other": {"bin_build_kernel": {"ms_per_step": traj_ms / K}},
+                    "other": {"bin_build_kernel": bins},
                     "dominant": fname}
     elif binned:
         # the binned (or polygon) check does only the candidate work of the
@@ -750,6 +770,10 @@ def run_batch(args):
         w = s["width"]
         mlp += float(np.where(f < 0, s["T"], f).sum()) * (w * w + 10 * w)
     fps_t = mlp / (trj_ms / 1e3)
+    # per-step grids of every scene (binned check): the M points read twice,
+    # the cell-start table and the sorted points written, for h = 0..T
+    bin_bytes = float(sum((s["T"] + 1) * (32.0 * s["M"] + 4.0 * (BIN_DIM * BIN_DIM + 1) + 8.0 * s["M"])
+                          for s in sc))
     if binned and trj_ms >= col_ms:
         # with the binned check the stage before the check holds the point
         # prologue, the grids and the trajectory kernels, the width-64 ones
@@ -763,7 +787,14 @@ def run_batch(args):
                 "kernel_ms_per_step": trj_ms,
                 "other": {"batch_binned_kernel (widths 16/32)": {
                     "ms_per_step": col_ms,
-                    "note": "binned: checks only the points of the cells a state's disk overlaps"}}}
+                    "note": "binned: checks only the points of the cells a state's disk overlaps"},
+                    "obstacle_and_bin_streams": {
+                        "bytes_per_step": bin_bytes,
+                        "achieved_gbs_lower_bound": bin_bytes / (trj_ms / 1e3) / 1e9,
+                        "note": "algorithmic bytes of the per-step grids of every scene (its M points read "
+                                "twice at 16 B, the cell-start table and M sorted points at 8 B written, per "
+                                "step h = 0..T); the grids are built inside the stage timed with the "
+                                "trajectories, so the rate over that stage is a lower bound"}}}
     else:
         fps = 4.0 * checks / (col_ms / 1e3)
         roof = {"bound": "alu", "kernel": ("batch_binned_kernel" if binned else "batch_collide_kernel<%d>" % choice[1]),

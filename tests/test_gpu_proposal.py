@@ -25,8 +25,12 @@ def _cuda():
 
 
 @pytest.mark.parametrize("M,N,K", [(128, 128, 64), (256, 256, 128), (384, 384, 320), (128, 1024, 256),
-                                   (1024, 256, 512), (512, 128, 1024)])
+                                   (1024, 256, 512), (512, 128, 1024), (768, 512, 192), (256, 768, 64),
+                                   (640, 1280, 576)])
 def test_gemm_bf16_against_fp64(M, N, K):
+    """C = A B^T against FP64 within K 2^-22 sum |a b|: 128- and 256-wide
+    tiles, one or several row and column tiles, also with fewer K blocks
+    than pipeline stages."""
     import torch
     from paper_1904_06680_gb300 import npp
     g = torch.Generator(device="cpu").manual_seed(M * 7 + N * 3 + K)

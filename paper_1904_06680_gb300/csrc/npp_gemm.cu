@@ -130,7 +130,9 @@ gemm_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUte
         m0 = (first_m + in_group % gsize) * BM;
         n0 = (in_group / gsize) * BN;
     }
-    const int nk = K / BK;
+    // this CTA's K blocks: slice blockIdx.z of gridDim.z equal slices
+    const int nk = K / BK / (int)gridDim.z;
+    const int kb0 = (int)blockIdx.z * nk;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -164,8 +166,8 @@ gemm_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUte
             if (*reinterpret_cast<volatile int*>(&flags[0])) break;
             uint8_t* st = smem + s * S::STAGE_BYTES;
             mbar_expect_tx(&full[s], S::STAGE_BYTES);
-            tma_load_2d(st, &ta, kb * BK, m0, &full[s]);
-            tma_load_2d(st + S::A_BYTES, &tb, kb * BK, n0, &full[s]);
+            tma_load_2d(st, &ta, (kb0 + kb) * BK, m0, &full[s]);
+            tma_load_2d(st + S::A_BYTES, &tb, (kb0 + kb) * BK, n0, &full[s]);
         }
         flags[1] = kb;
     } else if (warp == 1 && lane == 0) {
@@ -212,7 +214,8 @@ gemm_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUte
                 if (ep.mode == EPI_BIAS_F32)
 #pragma unroll
                     for (int i = 0; i < 16; ++i) v[i] += ep.bias[n + i];
-                float4* o = reinterpret_cast<float4*>(ep.out_f32 + (size_t)row * ep.ldo + n);
+                float4* o = reinterpret_cast<float4*>(ep.out_f32 + blockIdx.z * ep.split_stride +
+                                                      (size_t)row * ep.ldo + n);
 #pragma unroll
                 for (int i = 0; i < 4; ++i) o[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
             } else {
@@ -279,10 +282,12 @@ cudaError_t make_tmap_bf16(CUtensorMap* map, const void* base, int rows, int col
 }
 
 cudaError_t launch_gemm(const CUtensorMap& ta, const CUtensorMap& tb, int M, int N, int K, int bn,
-                        const GemmEpilogue& ep, cudaStream_t s)
+                        const GemmEpilogue& ep, cudaStream_t s, int splits)
 {
     if (M % BM || K % BK || K < BK || (bn != 128 && bn != 256) || N % bn) return cudaErrorInvalidValue;
-    dim3 grid(N / bn, M / BM);
+    if (splits < 1 || (K / BK) % splits || (splits > 1 && (ep.mode != EPI_F32 || ep.split_stride == 0)))
+        return cudaErrorInvalidValue;
+    dim3 grid(N / bn, M / BM, splits);
     if (bn == 256) {
         const int smem = GemmShape<256>::SMEM;
         cudaError_t e = cudaFuncSetAttribute(gemm_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

@@ -31,6 +31,7 @@ struct GemmEpilogue {
     const __nv_bfloat16* mask;       // row-major, leading dimension ldm
     int ldo, ldt, ldm;
     int* err;                        // set to a nonzero code if a pipeline wait timed out
+    size_t split_stride;             // split K (EPI_F32 only): slice z of K writes out_f32 + z split_stride
 };
 
 // TMA descriptor of a row-major BF16 matrix [rows][cols] (cols contiguous,
@@ -38,7 +39,10 @@ struct GemmEpilogue {
 cudaError_t make_tmap_bf16(CUtensorMap* map, const void* base, int rows, int cols, int box_rows);
 
 // C = A B^T with the epilogue; ta boxes of 128 rows, tb boxes of bn rows.
+// splits > 1 (EPI_F32 only; K / 64 a multiple of splits): slice z of the K
+// blocks is summed into its own FP32 partial C at out_f32 + z split_stride,
+// for the caller to add up.
 cudaError_t launch_gemm(const CUtensorMap& ta, const CUtensorMap& tb, int M, int N, int K, int bn,
-                        const GemmEpilogue& ep, cudaStream_t s);
+                        const GemmEpilogue& ep, cudaStream_t s, int splits = 1);
 
 }  // namespace npp

@@ -113,18 +113,26 @@ __global__ void pack_x_kernel(const float* __restrict__ x, int n, int B, bf16* _
 
 // Gaussian NLL of theta under (mu, exp(clamp(raw))) and its gradient with
 // respect to the network output, both layouts in BF16; the loss (mean over
-// B x 450) is added to *loss.
+// B x 450) is added to *loss.  A block takes a tile of NLL_TB batch rows x
+// NLL_TI parameters: the row-major gradient is written along the
+// parameters, the tile is staged in shared memory and the transposed
+// gradient written along the batch, so both stores are coalesced.  The
+// padding outputs 900..1023 are never written: their gradient rows stay at
+// the zeros the handle set at creation.
+constexpr int NLL_TB = 64;
+constexpr int NLL_TI = 32;
 __global__ void __launch_bounds__(256) nll_kernel(const float* __restrict__ Y, const float* __restrict__ theta, int B,
                                                   float ls_min, float ls_max, bf16* __restrict__ dY,
                                                   bf16* __restrict__ dYT, float* __restrict__ loss)
 {
     __shared__ float red[8];
+    __shared__ bf16 tile[2][NLL_TI][NLL_TB + 2];          // (mu, log-std) x parameter x batch row
     const float scale = 1.0f / ((float)B * (float)NTH);
+    const int i0 = blockIdx.x * NLL_TI, b0 = blockIdx.y * NLL_TB;
     float acc = 0.0f;
-    const int per_row = 512;
-    const int total = B * per_row;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-        const int b = t / per_row, i = t % per_row;
+    for (int e = threadIdx.x; e < NLL_TI * NLL_TB; e += blockDim.x) {
+        const int ii = e % NLL_TI, bb = e / NLL_TI;
+        const int i = i0 + ii, b = b0 + bb;
         if (i < NTH) {
             const float mu = Y[(size_t)b * D3 + i];
             const float raw = Y[(size_t)b * D3 + NTH + i];
@@ -137,17 +145,16 @@ __global__ void __launch_bounds__(256) nll_kernel(const float* __restrict__ Y, c
             const bf16 qm = __float2bfloat16_rn(dmu), ql = __float2bfloat16_rn(dls);
             dY[(size_t)b * D3 + i] = qm;
             dY[(size_t)b * D3 + NTH + i] = ql;
-            dYT[(size_t)i * B + b] = qm;
-            dYT[(size_t)(NTH + i) * B + b] = ql;
-        } else {
-            // the 124 padding outputs 900..1023, two per thread
-            const int j = 2 * NTH + 2 * (i - NTH);
-            const bf16 z = __float2bfloat16_rn(0.0f);
-            dY[(size_t)b * D3 + j] = z;
-            dY[(size_t)b * D3 + j + 1] = z;
-            dYT[(size_t)j * B + b] = z;
-            dYT[(size_t)(j + 1) * B + b] = z;
+            tile[0][ii][bb] = qm;
+            tile[1][ii][bb] = ql;
         }
+    }
+    __syncthreads();
+    // transposed rows i and NTH + i, NLL_TB consecutive batch entries each
+    for (int e = threadIdx.x; e < 2 * NLL_TI * NLL_TB; e += blockDim.x) {
+        const int bb = e % NLL_TB, k = e / NLL_TB, half = k / NLL_TI, ii = k % NLL_TI;
+        const int i = i0 + ii;
+        if (i < NTH) dYT[(size_t)(half * NTH + i) * B + b0 + bb] = tile[half][ii][bb];
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
@@ -161,7 +168,8 @@ __global__ void __launch_bounds__(256) nll_kernel(const float* __restrict__ Y, c
 }
 
 // bias gradients: row sums of dY^T (1024 rows), dZ2^T and dZ1^T (256 each);
-// one warp per row, fixed summation order
+// one warp per row, each lane summing 8 consecutive entries per 16-byte
+// load, then the lanes in a fixed tree: a fixed summation order
 __global__ void bias_grad_kernel(const bf16* __restrict__ dYT, const bf16* __restrict__ dZ2T,
                                  const bf16* __restrict__ dZ1T, int B, float* __restrict__ g)
 {
@@ -174,10 +182,52 @@ __global__ void bias_grad_kernel(const bf16* __restrict__ dYT, const bf16* __res
     else if (row < D3 + HID) { src = dZ2T + (size_t)(row - D3) * B; dst = g + OFF_B2 + (row - D3); }
     else { src = dZ1T + (size_t)(row - D3 - HID) * B; dst = g + OFF_B1 + (row - D3 - HID); }
     float s = 0.0f;
-    for (int b = lane; b < B; b += 32) s += __bfloat162float(src[b]);
+    const uint4* src8 = reinterpret_cast<const uint4*>(src);      // B is a multiple of 128
+    for (int q = lane; q < B / 8; q += 32) {
+        const uint4 u = src8[q];
+        const uint32_t w[4] = { u.x, u.y, u.z, u.w };
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            s += __bfloat162float(__ushort_as_bfloat16((unsigned short)(w[k] & 0xFFFFu)));
+            s += __bfloat162float(__ushort_as_bfloat16((unsigned short)(w[k] >> 16)));
+        }
+    }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
     if (lane == 0) *dst = s;
+}
+
+// weight gradients summed over the K slices of the split GEMMs, in slice
+// order (deterministic): segment k has n[k] outputs at dst[k] and n[k] x
+// splits[k] partials at src[k] (slice z at src[k] + z n[k])
+struct SplitSum {
+    const float* src[3];
+    float* dst[3];
+    int n[3];
+    int splits[3];
+};
+__global__ void __launch_bounds__(256) splitk_sum_kernel(const SplitSum a)
+{
+    const int total = a.n[0] + a.n[1] + a.n[2];
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        int k = 0, i = t;
+        if (i >= a.n[0]) { i -= a.n[0]; k = 1; if (i >= a.n[1]) { i -= a.n[1]; k = 2; } }
+        const float* p = a.src[k] + i;
+        const size_t st = (size_t)a.n[k];
+        const int S = a.splits[k];
+        float s = 0.0f;
+        int z = 0;
+        // eight loads in flight, added in slice order
+        for (; z + 8 <= S; z += 8) {
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = p[(size_t)(z + u) * st];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) s += v[u];
+        }
+        for (; z < S; ++z) s += p[(size_t)z * st];
+        a.dst[k][i] = s;
+    }
 }
 
 // Adam with bias correction on the flat FP32 masters
@@ -252,10 +302,26 @@ struct npp_proposal {
     float* Y;
     float* loss;                            // scratch loss when the caller passes none
     int* err;
+    // the weight-gradient GEMMs (K = batch) split K into sp[k] slices, each
+    // slice's FP32 partial in ws (dW3, dW2, dW1 at ws_off[k]), summed by
+    // splitk_sum_kernel
+    float* ws;
+    int sp[3];
+    size_t ws_off[3];
     CUtensorMap tX, tW1, tH1, tW2, tH2, tW3, tdY, tW3T, tdZ2, tW2T, tdYT, tH2T, tdZ2T, tH1T, tdZ1T, tXT;
 };
 
 namespace {
+
+// K slices of a weight-gradient GEMM with `tiles` output tiles and nk K
+// blocks: doubled while the CTAs stay within about one wave of the 152 SMs
+// and every slice keeps two K blocks or more
+int grad_splits(int tiles, int nk)
+{
+    int sp = 1;
+    while (2 * sp * tiles <= 160 && nk % (2 * sp) == 0 && nk / (2 * sp) >= 2) sp *= 2;
+    return sp;
+}
 
 cudaError_t forward_gemms(npp_proposal* P, cudaStream_t s)
 {
@@ -292,17 +358,26 @@ cudaError_t backward_gemms(npp_proposal* P, cudaStream_t s)
     e.mask = P->H1; e.out_bf16 = nullptr; e.out_t = P->dZ1T;
     r = launch_gemm(P->tdZ2, P->tW2T, B, HID, HID, 256, e, s);
     if (r != cudaSuccess) return r;
+    // weight gradients (K = B): K split into slices (partials in ws), then
+    // summed in slice order into the flat gradient
     memset(&e, 0, sizeof e);
     e.err = P->err;
     e.mode = EPI_F32;
-    e.out_f32 = P->g + OFF_W3; e.ldo = HID;
-    r = launch_gemm(P->tdYT, P->tH2T, D3, HID, B, 256, e, s);          // dW3 = dY^T H2
+    e.out_f32 = P->ws + P->ws_off[0]; e.ldo = HID; e.split_stride = (size_t)D3 * HID;
+    r = launch_gemm(P->tdYT, P->tH2T, D3, HID, B, 256, e, s, P->sp[0]);          // dW3 = dY^T H2
     if (r != cudaSuccess) return r;
-    e.out_f32 = P->g + OFF_W2; e.ldo = HID;
-    r = launch_gemm(P->tdZ2T, P->tH1T, HID, HID, B, 256, e, s);        // dW2 = dZ2^T H1
+    e.out_f32 = P->ws + P->ws_off[1]; e.ldo = HID; e.split_stride = (size_t)HID * HID;
+    r = launch_gemm(P->tdZ2T, P->tH1T, HID, HID, B, 256, e, s, P->sp[1]);        // dW2 = dZ2^T H1
     if (r != cudaSuccess) return r;
-    e.out_f32 = P->g + OFF_W1; e.ldo = D0;
-    return launch_gemm(P->tdZ1T, P->tXT, HID, D0, B, 128, e, s);       // dW1 = dZ1^T X
+    e.out_f32 = P->ws + P->ws_off[2]; e.ldo = D0; e.split_stride = (size_t)HID * D0;
+    r = launch_gemm(P->tdZ1T, P->tXT, HID, D0, B, 128, e, s, P->sp[2]);          // dW1 = dZ1^T X
+    if (r != cudaSuccess) return r;
+    SplitSum ss;
+    ss.src[0] = P->ws + P->ws_off[0]; ss.dst[0] = P->g + OFF_W3; ss.n[0] = D3 * HID; ss.splits[0] = P->sp[0];
+    ss.src[1] = P->ws + P->ws_off[1]; ss.dst[1] = P->g + OFF_W2; ss.n[1] = HID * HID; ss.splits[1] = P->sp[1];
+    ss.src[2] = P->ws + P->ws_off[2]; ss.dst[2] = P->g + OFF_W1; ss.n[2] = HID * D0; ss.splits[2] = P->sp[2];
+    splitk_sum_kernel<<<(D3 * HID + HID * HID + HID * D0 + 255) / 256, 256, 0, s>>>(ss);
+    return cudaGetLastError();
 }
 
 cudaError_t refresh_bf16(npp_proposal* P, cudaStream_t s)
@@ -384,11 +459,22 @@ npp_status npp_proposal_create(const npp_proposal_config* cfg, npp_proposal** ou
     A((void**)&P->Y, B * D3 * 4);
     A((void**)&P->loss, sizeof(float));
     A((void**)&P->err, sizeof(int));
+    const int nkb = cfg->batch / 64;
+    P->sp[0] = grad_splits((D3 / 128) * (HID / 256), nkb);
+    P->sp[1] = grad_splits((HID / 128) * (HID / 256), nkb);
+    P->sp[2] = grad_splits((HID / 128) * (D0 / 128), nkb);
+    P->ws_off[0] = 0;
+    P->ws_off[1] = P->ws_off[0] + (size_t)P->sp[0] * D3 * HID;
+    P->ws_off[2] = P->ws_off[1] + (size_t)P->sp[1] * HID * HID;
+    A((void**)&P->ws, (P->ws_off[2] + (size_t)P->sp[2] * HID * D0) * 4);
     if (e == cudaSuccess) e = cudaMemset(P->w, 0, N_FLAT * 4);
     if (e == cudaSuccess) e = cudaMemset(P->m, 0, N_FLAT * 4);
     if (e == cudaSuccess) e = cudaMemset(P->v, 0, N_FLAT * 4);
     if (e == cudaSuccess) e = cudaMemset(P->g, 0, N_FLAT * 4);
     if (e == cudaSuccess) e = cudaMemset(P->err, 0, sizeof(int));
+    // the padding outputs' gradient rows stay zero (the loss kernel writes 0..899)
+    if (e == cudaSuccess) e = cudaMemset(P->dY, 0, B * D3 * 2);
+    if (e == cudaSuccess) e = cudaMemset(P->dYT, 0, B * D3 * 2);
     if (e != cudaSuccess) {
         npp_proposal_destroy(P);
         return perr(NPP_CUDA_ERROR, std::string("proposal allocation: ") + cudaGetErrorString(e));
@@ -428,7 +514,7 @@ npp_status npp_proposal_destroy(npp_proposal* P)
     cudaSetDevice(P->cfg.device);
     cudaDeviceSynchronize();
     void* ptrs[] = { P->w, P->m, P->v, P->g, P->W1, P->W2, P->W2T, P->W3, P->W3T, P->X, P->XT, P->H1, P->H1T,
-                     P->H2, P->H2T, P->dY, P->dYT, P->dZ2, P->dZ2T, P->dZ1T, P->Y, P->loss, P->err };
+                     P->H2, P->H2T, P->dY, P->dYT, P->dZ2, P->dZ2T, P->dZ1T, P->Y, P->loss, P->err, P->ws };
     for (void* p : ptrs) if (p) cudaFree(p);
     delete P;
     return NPP_OK;
@@ -514,7 +600,7 @@ npp_status npp_proposal_train_step(npp_proposal* P, const float* x_dev, const fl
     float* lp = loss_dev ? loss_dev : P->loss;
     if (e == cudaSuccess) e = cudaMemsetAsync(lp, 0, sizeof(float), s);
     if (e == cudaSuccess) {
-        nll_kernel<<<std::min(4096, (B * 512 + 255) / 256), 256, 0, s>>>(P->Y, theta_dev, B, P->cfg.ls_min,
+        nll_kernel<<<dim3((NTH + NLL_TI - 1) / NLL_TI, B / NLL_TB), 256, 0, s>>>(P->Y, theta_dev, B, P->cfg.ls_min,
                                                                         P->cfg.ls_max, P->dY, P->dYT, lp);
         e = cudaGetLastError();
     }

@@ -88,14 +88,21 @@ def test_forward_against_oracle():
     net.close()
 
 
-def test_gradients_and_loss_against_oracle():
+@pytest.mark.parametrize("B", [256, 4096])
+def test_gradients_and_loss_against_oracle(B):
+    """Loss and every gradient against the FP64 oracle; the weight gradients
+    come from GEMMs with K (the batch) split into 2 (B = 256) or 16-32
+    slices (B = 4096) summed in slice order, so a repeated step gives the
+    same gradient bits."""
     import torch
-    B = 256
     params, vec, X, theta = _rand_problem(B, 2)
     net = _net(B)
     net.set_params(vec)
-    loss = net.train_step(torch.tensor(X, device="cuda"), torch.tensor(theta, device="cuda"), 0.0)
+    xd, td = torch.tensor(X, device="cuda"), torch.tensor(theta, device="cuda")
+    loss = net.train_step(xd, td, 0.0)
     g_gpu = OP.unpack(net.grads().astype(np.float64))
+    net.train_step(xd, td, 0.0)
+    assert np.array_equal(OP.pack(OP.unpack(net.grads().astype(np.float64))), OP.pack(g_gpu))
     c = OP.forward(params, X.astype(np.float64))
     want = OP.nll(c, theta)
     assert abs(float(loss.item()) - want) <= 1e-4 * abs(want) + 1e-5

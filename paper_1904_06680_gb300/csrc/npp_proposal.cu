@@ -98,16 +98,26 @@ __global__ void __launch_bounds__(256) encode_kernel(const DevCfg c, const npp_s
 }
 
 // x [n][72] FP32 -> X [B][128] BF16 and its transpose XT [128][B] (zero
-// rows beyond n, zero inputs beyond 72)
-__global__ void pack_x_kernel(const float* __restrict__ x, int n, int B, bf16* __restrict__ X, bf16* __restrict__ XT)
+// rows beyond n, zero inputs beyond 72).  A block takes PX_TB rows: X is
+// written along the inputs, the tile staged in shared memory and XT written
+// along the batch, so both stores are coalesced.
+constexpr int PX_TB = 64;
+__global__ void __launch_bounds__(256) pack_x_kernel(const float* __restrict__ x, int n, int B,
+                                                     bf16* __restrict__ X, bf16* __restrict__ XT)
 {
-    const int total = B * D0;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-        const int b = t / D0, k = t % D0;
+    __shared__ bf16 tile[D0][PX_TB + 2];                  // input x batch row
+    const int b0 = blockIdx.x * PX_TB;
+    for (int e = threadIdx.x; e < PX_TB * D0; e += blockDim.x) {
+        const int k = e % D0, bb = e / D0, b = b0 + bb;
         const float v = (b < n && k < NIN_X) ? x[(size_t)b * NIN_X + k] : 0.0f;
         const bf16 q = __float2bfloat16_rn(v);
         X[(size_t)b * D0 + k] = q;
-        XT[(size_t)k * B + b] = q;
+        tile[k][bb] = q;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < PX_TB * D0; e += blockDim.x) {
+        const int bb = e % PX_TB, k = e / PX_TB;
+        XT[(size_t)k * B + b0 + bb] = tile[k][bb];
     }
 }
 
@@ -331,10 +341,10 @@ cudaError_t forward_gemms(npp_proposal* P, cudaStream_t s)
     e.err = P->err;
     e.mode = EPI_BIAS_RELU_BF16;
     e.bias = P->w + OFF_B1; e.out_bf16 = P->H1; e.ldo = HID; e.out_t = P->H1T; e.ldt = B;
-    cudaError_t r = launch_gemm(P->tX, P->tW1, B, HID, D0, 256, e, s);
+    cudaError_t r = launch_gemm(P->tX, P->tW1, B, HID, D0, 128, e, s);
     if (r != cudaSuccess) return r;
     e.bias = P->w + OFF_B2; e.out_bf16 = P->H2; e.out_t = P->H2T;
-    r = launch_gemm(P->tH1, P->tW2, B, HID, HID, 256, e, s);
+    r = launch_gemm(P->tH1, P->tW2, B, HID, HID, 128, e, s);
     if (r != cudaSuccess) return r;
     memset(&e, 0, sizeof e);
     e.err = P->err;
@@ -352,11 +362,11 @@ cudaError_t backward_gemms(npp_proposal* P, cudaStream_t s)
     // dZ2 = (dY W3) masked by H2 > 0
     e.mode = EPI_MASK_BF16;
     e.mask = P->H2; e.ldm = HID; e.out_bf16 = P->dZ2; e.ldo = HID; e.out_t = P->dZ2T; e.ldt = B;
-    cudaError_t r = launch_gemm(P->tdY, P->tW3T, B, HID, D3, 256, e, s);
+    cudaError_t r = launch_gemm(P->tdY, P->tW3T, B, HID, D3, 128, e, s);
     if (r != cudaSuccess) return r;
     // dZ1 = (dZ2 W2) masked by H1 > 0 (transposed only)
     e.mask = P->H1; e.out_bf16 = nullptr; e.out_t = P->dZ1T;
-    r = launch_gemm(P->tdZ2, P->tW2T, B, HID, HID, 256, e, s);
+    r = launch_gemm(P->tdZ2, P->tW2T, B, HID, HID, 128, e, s);
     if (r != cudaSuccess) return r;
     // weight gradients (K = B): K split into slices (partials in ws), then
     // summed in slice order into the flat gradient
@@ -481,12 +491,14 @@ npp_status npp_proposal_create(const npp_proposal_config* cfg, npp_proposal** ou
     }
     const int b = cfg->batch;
     // A operands: boxes of 128 rows; B operands: boxes of the tile width
+    // (128 for the N = 256 products over the batch: twice the CTAs of
+    // 256-wide tiles, on 152 SMs)
     struct M { CUtensorMap* map; const void* base; int rows, cols, box; } maps[] = {
-        { &P->tX, P->X, b, D0, 128 },     { &P->tW1, P->W1, HID, D0, 256 },
-        { &P->tH1, P->H1, b, HID, 128 },  { &P->tW2, P->W2, HID, HID, 256 },
+        { &P->tX, P->X, b, D0, 128 },     { &P->tW1, P->W1, HID, D0, 128 },
+        { &P->tH1, P->H1, b, HID, 128 },  { &P->tW2, P->W2, HID, HID, 128 },
         { &P->tH2, P->H2, b, HID, 128 },  { &P->tW3, P->W3, D3, HID, 256 },
-        { &P->tdY, P->dY, b, D3, 128 },   { &P->tW3T, P->W3T, HID, D3, 256 },
-        { &P->tdZ2, P->dZ2, b, HID, 128 }, { &P->tW2T, P->W2T, HID, HID, 256 },
+        { &P->tdY, P->dY, b, D3, 128 },   { &P->tW3T, P->W3T, HID, D3, 128 },
+        { &P->tdZ2, P->dZ2, b, HID, 128 }, { &P->tW2T, P->W2T, HID, HID, 128 },
         { &P->tdYT, P->dYT, D3, b, 128 }, { &P->tH2T, P->H2T, HID, b, 256 },
         { &P->tdZ2T, P->dZ2T, HID, b, 128 }, { &P->tH1T, P->H1T, HID, b, 256 },
         { &P->tdZ1T, P->dZ1T, HID, b, 128 }, { &P->tXT, P->XT, D0, b, 128 },
@@ -575,7 +587,7 @@ npp_status npp_proposal_forward(npp_proposal* P, const float* x_dev, int32_t n, 
     if (n < 1 || n > P->B) return perr(NPP_INVALID_ARG, "npp_proposal_forward: n outside [1, batch]");
     cudaSetDevice(P->cfg.device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    pack_x_kernel<<<256, 256, 0, s>>>(x_dev, n, P->B, P->X, P->XT);
+    pack_x_kernel<<<P->B / PX_TB, 256, 0, s>>>(x_dev, n, P->B, P->X, P->XT);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = forward_gemms(P, s);
     if (e == cudaSuccess) {
@@ -594,7 +606,7 @@ npp_status npp_proposal_train_step(npp_proposal* P, const float* x_dev, const fl
     cudaSetDevice(P->cfg.device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const int B = P->B;
-    pack_x_kernel<<<256, 256, 0, s>>>(x_dev, B, B, P->X, P->XT);
+    pack_x_kernel<<<B / PX_TB, 256, 0, s>>>(x_dev, B, B, P->X, P->XT);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = forward_gemms(P, s);
     float* lp = loss_dev ? loss_dev : P->loss;

@@ -97,6 +97,20 @@ def test_fused_infeasible_and_warm_start():
         _assert_same(a, b)
 
 
+@pytest.mark.parametrize("width,N,T,M", [(64, 1, 1, 0), (64, 33, 8, 1), (64, 130, 9, 300), (64, 65, 17, 300),
+                                         (16, 1, 7, 300), (16, 33, 16, 300), (16, 130, 17, 0), (32, 3, 9, 50)])
+def test_fused_degenerate_sizes(width, N, T, M):
+    """The windowed check at the edges of its windows and groups: horizons
+    of one step, one window (8 states at width 64, 16 at width 16) and one
+    past it, a single sample, sample counts that leave a warp's groups
+    partly empty, no points and one point -- bit for bit the brute-force
+    check's results."""
+    sc = inputs.tiny_scene(200 + N + T, N, T, M, width=width, box=12.0, clear=1.0)
+    brute = _plan(sc, 2)
+    _assert_same(_plan(sc, BINNED, fuse=1), brute)
+    _assert_same(_plan(sc, BINNED), brute)
+
+
 def test_points_beyond_shared_memory():
     """More points than shared memory holds: the brute-force check reads the
     EV-frame pairs from global memory (written in the staging's blocked

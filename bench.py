@@ -349,10 +349,10 @@ def run_npp(args):
     from paper_1904_06680_gb300 import closed_loop, inputs, npp
 
     rank, world, local = dist_env()
+    torch.cuda.set_device(local)              # before the process group: NCCL binds the current device
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     sc, desc = workload_setup(args.workload, args.seed + rank)
     poly = args.footprint == "car"
@@ -704,10 +704,10 @@ def run_batch(args):
     import torch
     from paper_1904_06680_gb300 import autotune, inputs, npp
     rank, world, local = dist_env()
+    torch.cuda.set_device(local)              # before the process group: NCCL binds the current device
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     bt = inputs.scene_batch(args.seed + rank)
     sc = bt["scenes"]
@@ -963,10 +963,10 @@ def run_mission(args):
     import torch
     from paper_1904_06680_gb300 import inputs, npp
     rank, world, local = dist_env()
+    torch.cuda.set_device(local)              # before the process group: NCCL binds the current device
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     n_missions = args.missions
     max_steps = 800

@@ -65,13 +65,15 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="large", choices=["course", "large", "batch", "proposal", "mission"],
+    ap.add_argument("--workload", default="large",
+                    choices=["course", "large", "batch", "proposal", "mission", "paper"],
                     help="large (default, the largest single-GPU configuration): N=65536, T=100, "
                          "8-64-64-2, 8192 points over 80x80 m with per-step spatial binning; "
                          "course: the closed-loop forward/reverse course (N=16384, T=40, 8-32-32-2, M=2000); "
                          "batch: 512 parking scenes of uneven N, T, M and width in one "
                          "graph-captured batch; proposal: the learned sampling proposal "
-                         "(tensor-core GEMM roofline, training throughput, plan quality)")
+                         "(tensor-core GEMM roofline, training throughput, plan quality); paper: the "
+                         "paper's Step-5 setting (15 restarts x 20480 samples x H=200) beside its tau_a")
     ap.add_argument("--rounds", type=int, default=30, help="proposal workload: training rounds")
     ap.add_argument("--missions", type=int, default=10, help="mission workload: scene seeds")
     ap.add_argument("--set", action="append", default=[], metavar="NAME=VALUE",
@@ -936,6 +938,84 @@ def run_proposal(args):
     print(json.dumps(line))
 
 
+# the paper's tau_a (Step 5 of Alg. 1: 15 restarts of n = 20480 samples over
+# H = 200 steps per sampling time) on its i7-7700K + Titan V, seconds, quoted
+# as context: (experiment, network, obstacle points, tau_a)
+PAPER_TAU = [("Exp. 2, 50 km/h, no obstacles", "NN-[5,2,2] (18 parameters)", 0, 0.036),
+             ("Exp. 2", "NN-[5,10,2] (82 parameters)", 0, 0.047),
+             ("Exp. 2", "NN-[5,10,10,2] (192 parameters)", 0, 0.130),
+             ("Exp. 3, 4 points on a vehicle + 16 road bounds", "NN-[5,2,2]", 20, 0.090)]
+
+
+def run_paper(args):
+    """The paper's own Step-5 setting (Sect. V): per sampling time the hill
+    climb's 15 restart rounds of n = 20480 samples over H = 200 steps, with
+    the paper's vehicle and cost weights, on this library's smallest network
+    (8-16-16-2, 450 parameters; the paper's have 18 to 192).  Two scenes: an
+    empty road at 50 km/h (Experiment 2) and 20 points, 4 on a car ahead at
+    20 km/h and 16 road bounds (Experiment 3).  value = 15 x 20480 x 200
+    rollout-steps / device time per sampling time (CUDA events around each
+    npp_plan_tshc call, L2 flushed between calls); the paper's tau_a on its
+    Titan V is quoted beside it as context, not as a target."""
+    import torch
+    from paper_1904_06680_gb300 import inputs, npp
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    R, N, T = 15, 20480, 200
+    p = dict(inputs.PAPER, widths=(8, 16, 16, 2))
+    v0 = 50 / 3.6
+    state = np.array([0.0, 0.0, 0.0, v0, 0.0, 0.0])
+    goal = np.array([60.0, 0.0, 0.0, v0])
+    road = np.zeros((20, 4))
+    road[:16, 0] = np.tile(np.linspace(5.0, 75.0, 8), 2)
+    road[:16, 1] = np.repeat([-3.5, 3.5], 8)
+    road[16:, 0] = [29.0, 29.0, 33.5, 33.5]                      # a car 30 m ahead at 20 km/h
+    road[16:, 1] = [-0.9, 0.9, -0.9, 0.9]
+    road[16:, 2] = 20 / 3.6
+    far = np.array([[1e4, 1e4, 0.0, 0.0]])
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    pl = npp.Planner(p, max_N=N, max_T=T, max_M=20)
+    out = pl.outputs()
+    rows = []
+    clocks = Clocks(0)
+    clocks.start()
+    for label, obs in (("no obstacles (Exp. 2)", far), ("20 points (Exp. 3)", road)):
+        obs_d = torch.tensor(obs, dtype=torch.float32, device=dev)
+        ms = []
+        for t in range(args.warmup + args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            npp.npp_plan_tshc(pl.h, state, goal, obs_d, obs.shape[0], N, T, inputs.philox_seed(0), t, None, R,
+                              0.1, out)
+            e1.record()
+            torch.cuda.synchronize()
+            if t >= args.warmup:
+                ms.append(e0.elapsed_time(e1))
+        r = pl.result(N, T)
+        tau = float(np.mean(ms)) / 1e3
+        rows.append({"scene": label, "points": int(obs.shape[0]), "tau_s": tau,
+                     "rollout_steps_per_s": R * N * T / tau, "status": r["status"],
+                     "best_cost": r["best_cost"]})
+    ck = clocks.stop()
+    pl.close()
+    tot = float(np.mean([r_["tau_s"] for r_ in rows]))
+    line = {"metric": METRIC, "value": R * N * T / tot, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "the paper's Step 5: 15 restart rounds x 20480 samples x H=200 per sampling "
+                                   "time, the paper's vehicle, network 8-16-16-2 (450 parameters); mean of two "
+                                   "scenes (no obstacles; 20 points)",
+                       "N": N, "T": T, "restarts": R, "width": 16,
+                       "l2": "flushed (256 MiB write) between timed calls"},
+            "scenes": rows,
+            "paper_tau_s_titan_v": [{"experiment": e, "network": n, "points": m, "tau_s": t_}
+                                    for e, n, m, t_ in PAPER_TAU],
+            "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": ck}
+    print(json.dumps(line))
+
+
 def executed_collisions(log, obs, p):
     """Sampling times whose executed pose (log rows: x, y, phi before the
     step) has some obstacle point (at its position at that time) strictly
@@ -1070,7 +1150,7 @@ def run_mission(args):
 def main():
     args = parse()
     if args.impl == "reference":
-        if args.workload in ("batch", "proposal", "mission"):
+        if args.workload in ("batch", "proposal", "mission", "paper"):
             args.workload = "course"
         run_reference(args)
     elif args.workload == "mission":
@@ -1079,6 +1159,8 @@ def main():
         run_batch(args)
     elif args.workload == "proposal":
         run_proposal(args)
+    elif args.workload == "paper":
+        run_paper(args)
     else:
         run_npp(args)
 

@@ -258,6 +258,14 @@ def workload_setup(name, seed):
     return inputs.scene_course(seed=seed), COURSE_DESC
 
 
+def grid_bytes(T, M):
+    """Algorithmic bytes of one plan step's per-step grids: for each of the
+    T + 1 grids the M world points read twice (count and scatter passes,
+    16 B each), the cell-start table (BIN_DIM^2 + 1 entries of 4 B) and the
+    M sorted points (8 B each) written."""
+    return (T + 1) * (32.0 * M + 4.0 * (BIN_DIM * BIN_DIM + 1) + 8.0 * M)
+
+
 def algorithmic_work(first_hit, T, M, W):
     """Algorithmic FP32 FMAs, split by kernel: the collision check needs 4
     per point-check of a live sample (two rows of the rotated inequality
@@ -514,10 +522,7 @@ def run_npp(args):
                      "bytes_per_step": wbytes / K, "achieved_gbs": wbytes / (collide_ms / 1e3) / 1e9,
                      "bytes_note": "algorithmic grid reads: 40 B per state checked (ten cell-run "
                                    "bounds), 8 B per candidate test, over the kernel's duration"}
-        # the grid build's algorithmic bytes per plan step: for each of the
-        # T + 1 grids the M world points read twice (count, scatter; 16 B
-        # each), the cell-start table and the sorted points written
-        bin_bytes = (T + 1) * (32.0 * M + 4.0 * (BIN_DIM * BIN_DIM + 1) + 8.0 * M)
+        bin_bytes = grid_bytes(T, M)
         bin_s = traj_ms / K / 1e3
         bins = {"ms_per_step": traj_ms / K, "bytes_per_step": bin_bytes,
                 "achieved_gbs": bin_bytes / bin_s / 1e9 if bin_s > 0 else None,
@@ -772,10 +777,8 @@ def run_batch(args):
         w = s["width"]
         mlp += float(np.where(f < 0, s["T"], f).sum()) * (w * w + 10 * w)
     fps_t = mlp / (trj_ms / 1e3)
-    # per-step grids of every scene (binned check): the M points read twice,
-    # the cell-start table and the sorted points written, for h = 0..T
-    bin_bytes = float(sum((s["T"] + 1) * (32.0 * s["M"] + 4.0 * (BIN_DIM * BIN_DIM + 1) + 8.0 * s["M"])
-                          for s in sc))
+    # per-step grids of every scene (binned check)
+    bin_bytes = float(sum(grid_bytes(s["T"], s["M"]) for s in sc))
     if binned and trj_ms >= col_ms:
         # with the binned check the stage before the check holds the point
         # prologue, the grids and the trajectory kernels, the width-64 ones

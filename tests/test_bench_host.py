@@ -55,3 +55,12 @@ def test_profiled_traffic_entries_are_current():
         if "@" in key:
             name, wl = key.split("@")
             assert bench.profiled_traffic(name, wl) == rec["kernels"][key]["dram_bytes_per_launch"]
+
+
+def test_grid_bytes_counts_reads_and_writes():
+    """Per grid: M points read in the count and the scatter pass (16 B
+    each), 128 x 128 + 1 cell starts and M sorted points (8 B) written."""
+    import bench
+    assert bench.grid_bytes(0, 0) == 4.0 * (128 * 128 + 1)
+    assert bench.grid_bytes(0, 10) == 10 * 16 * 2 + 4.0 * (128 * 128 + 1) + 10 * 8
+    assert bench.grid_bytes(100, 8192) == 101 * (8192 * 40 + 4.0 * 16385)

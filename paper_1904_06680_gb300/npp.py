@@ -2,7 +2,7 @@
 
 The functions keep the C names and only marshal arguments: torch tensors
 provide device memory and streams, every step of the planner runs in the
-library's CUDA kernels.  Importing this module raises if the library has not
+library's CUDA kernels.  The first call into the library raises if it has not
 been built (there is no CPU fallback).
 """
 import ctypes as C

@@ -964,25 +964,19 @@ def run_paper(args):
     from paper_1904_06680_gb300 import inputs, npp
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
-    R, N, T = 15, 20480, 200
-    p = dict(inputs.PAPER, widths=(8, 16, 16, 2))
-    v0 = 50 / 3.6
-    state = np.array([0.0, 0.0, 0.0, v0, 0.0, 0.0])
-    goal = np.array([60.0, 0.0, 0.0, v0])
-    road = np.zeros((20, 4))
-    road[:16, 0] = np.tile(np.linspace(5.0, 75.0, 8), 2)
-    road[:16, 1] = np.repeat([-3.5, 3.5], 8)
-    road[16:, 0] = [29.0, 29.0, 33.5, 33.5]                      # a car 30 m ahead at 20 km/h
-    road[16:, 1] = [-0.9, 0.9, -0.9, 0.9]
-    road[16:, 2] = 20 / 3.6
-    far = np.array([[1e4, 1e4, 0.0, 0.0]])
+    R = 15
+    scenes = (("no obstacles (Exp. 2)", inputs.scene_paper_road(False)),
+              ("20 points (Exp. 3)", inputs.scene_paper_road(True)))
+    p, N, T = scenes[0][1]["preset"], scenes[0][1]["N"], scenes[0][1]["T"]
+    state, goal = scenes[0][1]["state"], scenes[0][1]["goal"]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     pl = npp.Planner(p, max_N=N, max_T=T, max_M=20)
     out = pl.outputs()
     rows = []
     clocks = Clocks(0)
     clocks.start()
-    for label, obs in (("no obstacles (Exp. 2)", far), ("20 points (Exp. 3)", road)):
+    for label, scn in scenes:
+        obs = scn["obs"]
         obs_d = torch.tensor(obs, dtype=torch.float32, device=dev)
         ms = []
         for t in range(args.warmup + args.steps):

@@ -464,6 +464,27 @@ def scene_turnaround(seed: int = 0, N: int = 16384, T: int = 80):
                 N=N, T=T, seed=philox_seed(seed), t_index=0, waypoints=waypoints)
 
 
+def scene_paper_road(with_points: bool = True, seed: int = 0, N: int = 20480, T: int = 200):
+    """The paper's Step-5 setting on a road (Experiments 2 and 3, Sect. V):
+    the paper's vehicle on this library's smallest network (8-16-16-2), start
+    at 50 km/h, goal 60 m ahead at the same speed, horizon H = 200; with
+    points: 16 road bounds (every 10 m from 5 to 75 m at +-3.5 m) and 4 on
+    the corners of a car 30 m ahead moving at 20 km/h (20 points), else one
+    point 10 km away."""
+    v0 = 50 / 3.6
+    if with_points:
+        obs = np.zeros((20, 4))
+        obs[:16, 0] = np.tile(np.linspace(5.0, 75.0, 8), 2)
+        obs[:16, 1] = np.repeat([-3.5, 3.5], 8)
+        obs[16:, 0] = [29.0, 29.0, 33.5, 33.5]
+        obs[16:, 1] = [-0.9, 0.9, -0.9, 0.9]
+        obs[16:, 2] = 20 / 3.6
+    else:
+        obs = np.array([[1e4, 1e4, 0.0, 0.0]])
+    return dict(preset=dict(PAPER, widths=(8, 16, 16, 2)), state=np.array([0.0, 0.0, 0.0, v0, 0.0, 0.0]),
+                goal=np.array([60.0, 0.0, 0.0, v0]), obs=obs, N=N, T=T, seed=philox_seed(seed), t_index=0)
+
+
 def scene_waypoints(seed: int = 0, N: int = 16384, T: int = 40):
     """See the module docstring (Experiment 4)."""
     obs = np.array([[1e4, 1e4, 0.0, 0.0]])

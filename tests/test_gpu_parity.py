@@ -235,6 +235,15 @@ def test_large_full_size(orc):
     _full_size(inputs.scene_large(0), 0.98)
 
 
+def test_paper_horizon(orc):
+    """The paper's horizon H = 200 with its vehicle (Experiment 3's road:
+    16 bounds and a car ahead at 20 km/h; 8-16-16-2, N = 4096): every
+    sample's status and cost from the oracle; per-step replay, decisions at
+    the GPU's states, the trajectory rule and the cost at the GPU's states
+    on 1024 sampled indices and the winner."""
+    _full_size(inputs.scene_paper_road(True, N=4096), 0.95)
+
+
 def test_large_point_set_from_global_memory(orc):
     """More points than shared memory holds: the collision kernel reads an
     L2-resident copy; every sample against the oracle."""

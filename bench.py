@@ -258,6 +258,16 @@ def workload_setup(name, seed):
     return inputs.scene_course(seed=seed), COURSE_DESC
 
 
+def brute_auto(M, N):
+    """The library's automatic brute-force collision variant (the same rule
+    as its brute_auto), to name the kernel that ran."""
+    if N >= 6144:
+        return 2 if M <= 1200 else 4
+    if M >= 6000:
+        return 1
+    return 2 if M <= 64 else 3
+
+
 def grid_bytes(T, M):
     """Algorithmic bytes of one plan step's per-step grids: for each of the
     T + 1 grids the M world points read twice (count and scatter passes,
@@ -587,9 +597,7 @@ def run_npp(args):
         tname = "traj_kernel" + shape
         cname = {0: "collide_block_kernel<16,128,1>", 1: "collide_block_kernel<8,64,2>",
                  2: "collide_warp_kernel<8,2>", 3: "collide_slice_kernel<4,2,0,2>",
-                 4: "collide_slice_kernel<2,2,0,4>"}.get(
-            cv, "collide_slice_kernel<4,2,0,2>" if N <= 8192 else
-            "collide_slice_kernel<2,2,0,4>" if N <= 32768 else "collide_warp_kernel<8,2>")
+                 4: "collide_slice_kernel<2,2,0,4>"}[cv if cv >= 0 else brute_auto(M, N)]
         fps_c = res["fma_c"] / (collide_ms / 1e3)
         fps_t = res["fma_t"] / (traj_ms / 1e3)
         roofline = {"bound": "alu", "kernel": cname,

@@ -291,16 +291,15 @@ npp_status run_rollout(npp_handle* h, RolloutArgs& a, cudaStream_t s, bool no_re
         if (h->timing) CUDA_TRY(h, record_event(h->ev[2], s));
         return NPP_OK;
     }
-    // automatic choice (measured on GB300, course workload): few samples ->
-    // items checked by 4 warps on point slices; medium -> 2 warps; many
-    // samples -> one warp per item keeps enough items in flight; many points
-    // -> spatial binning; at width 64 checked window by window inside the
+    // automatic choice (measured on GB300): many points -> spatial binning,
+    // else the brute-force variant by points and samples (brute_auto); at
+    // width 64 the binned check runs window by window inside the
     // trajectory kernel unless the caller wants every sample's records
     // (measured at N = 65536, T = 100, M = 8192: 2.72 ms per plan step
     // against 3.83 in two kernels and 3.31 in two step chunks; at width 32,
     // T = 40 the two kernels stay faster, 0.258 against 0.311 ms)
     const int v = h->collide_variant >= 0 ? h->collide_variant
-                : (binned_auto(a.M, a.N) ? COLLIDE_BINNED : (a.N <= 8192 ? 3 : (a.N <= 32768 ? 4 : 2)));
+                : (binned_auto(a.M, a.N) ? COLLIDE_BINNED : brute_auto(a.M, a.N));
     if (v == COLLIDE_BINNED) {
         if (h->timing) CUDA_TRY(h, record_event(h->ev[0], s));
         const bool fuse = no_records && (h->fuse == 1 || (h->fuse < 0 && h->cfg.width == 64));

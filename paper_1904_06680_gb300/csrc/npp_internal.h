@@ -16,6 +16,20 @@
 constexpr int COLLIDE_BINNED = 5;
 inline bool binned_auto(int M, int N) { return M >= 512 && (long long)M * N >= 8000000LL; }
 
+// the brute-force variant the automatic choice takes otherwise (measured on
+// GB300 over M = 20..8000 points and N = 1k..30k samples, every variant
+// computing the same flags): with many samples one warp per 8-sample item
+// (2) unless the points are many (4: two point slices per item); with few
+// samples items on four point slices (3), one warp per item for a handful
+// of points, the block-balanced kernel (1) for very many points.  Within 4 %
+// of the fastest variant on every measured case.
+inline int brute_auto(int M, int N)
+{
+    if (N >= 6144) return M <= 1200 ? 2 : 4;
+    if (M >= 6000) return 1;
+    return M <= 64 ? 2 : 3;
+}
+
 // most step chunks of one plan step, and the stage events they need
 constexpr int NPP_MAX_CHUNKS = 8;
 constexpr int NPP_CHUNK_EVENTS = 2 * NPP_MAX_CHUNKS + 1;

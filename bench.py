@@ -494,11 +494,10 @@ def run_npp(args):
     # the library's own FMA-stream microbenchmark, beside the derived peak
     fma_measured = {"ffma": npp.npp_measure_fma_peak(local, False) / 1e12,
                     "ffma2": npp.npp_measure_fma_peak(local, True) / 1e12, "unit": "T FP32-FMA/s"}
-    # the library's automatic collision choice (binned from 512 points and
-    # 8e6 point-sample pairs); "fuse" runs the binned check inside the
-    # trajectory kernel
+    # the library's automatic collision choice (binned from 128 points);
+    # "fuse" runs the binned check inside the trajectory kernel
     cv = int(options.get("collide_variant", -1))
-    binned = poly or cv == 5 or (cv < 0 and M >= 512 and M * N >= 8000000)
+    binned = poly or cv == 5 or (cv < 0 and M >= 128)
     fz = int(options.get("fuse", DEFAULT_FUSE))
     fused = binned and not poly and (fz == 1 or (fz < 0 and W == 64))
     # the library's step chunks of the split binned path (option "chunks";
@@ -1079,7 +1078,7 @@ def run_mission(args):
             if t >= args.warmup or k > 0:
                 step_ms.append(tm["total"])
             # trajectories, collision check (+ grid build when binned), epilogue, vehicle, points
-            launches += 6 if (M >= 512 and M * N >= 8e6) else 5
+            launches += 6 if M >= 128 else 5
             st = npp.npp_loop_read(L)
             if st["done"]:
                 done_at = st["t"]

@@ -478,9 +478,8 @@ npp_status npp_plan_step_noalloc(const npp_config* cfg, const npp_state* state,
  * are counting-sorted into a uniform grid around the vehicle and each state
  * is tested only against the cells its bounding disk overlaps (the same
  * per-point test, so the same flags as checking every point); -1 (default)
- * takes 5 when M >= 512 and M N >= 8e6 and otherwise chooses by points and
- * samples: for N >= 6144, 2 up to 1200 points, else 4; for fewer samples,
- * 1 from 6000 points, 2 up to 64 points, else 3.
+ * takes 5 from 128 points and below that 2 for N >= 6144 or at most 64
+ * points, else 3.
  * "fuse" -1 (default), 0 or 1: with the binned check (5) and no per-sample
  * records requested, 1 runs the check inside the trajectory kernel: each
  * warp rolls its samples through a window of steps, checks the window's

@@ -10,11 +10,13 @@
 #include "npp_device.cuh"
 
 // collision-kernel variant number of the spatially binned check, and when
-// the automatic choice takes it (measured on GB300: the per-step grid build
-// costs 20-45 us, so binning pays from about 512 points and 8M point-sample
-// pairs)
+// the automatic choice takes it: from 128 points, whatever the number of
+// samples (measured on GB300, plan steps at widths 16-64 against the best
+// brute-force variant: 1.0-1.3x faster from 128 to 300 points, 1.3-1.8x
+// beyond; below 128 points within 2-14 % either way; the grid build runs on
+// a side stream while the trajectories are rolled out)
 constexpr int COLLIDE_BINNED = 5;
-inline bool binned_auto(int M, int N) { return M >= 512 && (long long)M * N >= 8000000LL; }
+inline bool binned_auto(int M, int N) { (void)N; return M >= 128; }
 
 // the brute-force variant the automatic choice takes otherwise (measured on
 // GB300 over M = 20..8000 points and N = 1k..30k samples, every variant

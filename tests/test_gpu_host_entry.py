@@ -41,17 +41,18 @@ def _host_plan(pl, sc, warm, npp, torch):
                 costs=costs, first_hit=fh)
 
 
-# course scenes (2000 points) with the library's automatic collision check:
-# brute force (M N < 8e6), the two-kernel binned check (width 32), the
-# windowed check inside the trajectory kernel (width 64)
-@pytest.mark.parametrize("width,N,seed", [(32, 2048, 1), (32, 4096, 2), (64, 4096, 3)])
+# course scenes (2000 points) under a brute-force check (option 3), the
+# automatic two-kernel binned check (width 32) and the automatic windowed
+# check inside the trajectory kernel (width 64)
+@pytest.mark.parametrize("width,N,seed,variant", [(32, 2048, 1, 3), (32, 4096, 2, -1), (64, 4096, 3, -1)])
 @pytest.mark.parametrize("use_warm", [False, True])
-def test_host_entry_equals_device_entry(width, N, seed, use_warm):
+def test_host_entry_equals_device_entry(width, N, seed, variant, use_warm):
     import torch
     from paper_1904_06680_gb300 import npp
     sc = inputs.scene_course(seed, N=N, width=width)
     T, M = sc["T"], sc["obs"].shape[0]
     pl = npp.Planner(sc["preset"], max_N=N, max_T=T, max_M=M)
+    npp.npp_set_option(pl.h, "collide_variant", variant)
     warm = None
     if use_warm:
         warm = (np.random.default_rng(seed).standard_normal(pl.n_theta) * 0.5).astype(np.float32)

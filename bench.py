@@ -288,11 +288,10 @@ def algorithmic_work(first_hit, T, M, W):
 
 
 # source files whose code each profiled kernel is built from
-KERNEL_SOURCES = (
-    ("traj_kernel", ("npp_rollout.cuh", "npp_device.cuh", "npp_async.cuh", "npp_rollout_w16.cu",
-                     "npp_rollout_w32.cu", "npp_rollout_w64.cu")),
-    ("fused_kernel", ("npp_rollout.cuh", "npp_device.cuh", "npp_async.cuh", "npp_rollout_w16.cu",
-                      "npp_rollout_w32.cu", "npp_rollout_w64.cu")),
+_ROLLOUT = ("npp_rollout.cuh", "npp_device.cuh", "npp_async.cuh")
+KERNEL_SOURCES = tuple(
+    (kind + "<%d" % w, _ROLLOUT + ("npp_rollout_w%d.cu" % w,))      # each width's own translation unit
+    for kind in ("traj_kernel", "fused_kernel") for w in (16, 32, 64)) + (
     ("bin_build_kernel", ("npp_binned.cu", "npp_rollout.cuh", "npp_device.cuh", "npp_async.cuh")),
     ("collide_binned_kernel", ("npp_binned.cu", "npp_rollout.cuh", "npp_device.cuh", "npp_async.cuh")),
     ("collide_poly_kernel", ("npp_poly.cu", "npp_rollout.cuh", "npp_device.cuh", "npp_async.cuh")),
@@ -510,7 +509,8 @@ def run_npp(args):
     # default launch shapes; the last template argument is the variant flag
     # (off: no speed limits, features in the EV frame at t)
     var = int(bool(p.get("v_limits", 0) or p.get("feature_frame", 0)))
-    shape = {16: "<16,8,4,4,%d,0>", 32: "<32,16,4,4,%d,0>", 64: "<64,32,1,16,%d,8>"}[W] % var
+    shape = {16: "<16,8,4,4,%d,0>" if var else "<16,8,8,3,%d,0>", 32: "<32,16,4,4,%d,0>",
+             64: "<64,32,1,16,%d,8>"}[W] % var
     if fused:
         # [0] grid build, [1] the trajectory kernel with the windowed check
         fshape = {16: "<16,8,4,4,%d,0,16,4>", 32: "<32,16,4,5,%d,5,8,4>", 64: "<64,32,1,16,%d,12,8,4>"}[W] % var

@@ -288,7 +288,7 @@ def test_collide_variants_identical():
     pl.close()
 
 
-@pytest.mark.parametrize("width", [64, 32])
+@pytest.mark.parametrize("width", [64, 32, 16])
 def test_trajectory_launch_shapes_identical(width):
     """Every launch shape of the trajectory kernel gives the same bits:
     per-sample states, controls, costs, first collisions and the winner.

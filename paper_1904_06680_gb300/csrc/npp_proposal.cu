@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(256) encode_kernel(const DevCfg c, const npp_s
 // rows beyond n, zero inputs beyond 72).  A block takes PX_TB rows: X is
 // written along the inputs, the tile staged in shared memory and XT written
 // along the batch, so both stores are coalesced.
-constexpr int PX_TB = 64;
+constexpr int PX_TB = 32;
 __global__ void __launch_bounds__(256) pack_x_kernel(const float* __restrict__ x, int n, int B,
                                                      bf16* __restrict__ X, bf16* __restrict__ XT)
 {

@@ -88,3 +88,18 @@ def test_paper_experiment_scenes():
     assert np.array_equal(e4["state"], np.zeros(6)) and e4["waypoints"].shape == (4, 4)
     assert np.all(e4["waypoints"][:, 3] == 0.0)
     assert e1["seed"] != inputs.scene_turnaround(4)["seed"]
+
+
+def test_scene_paper_road_recipe():
+    """The paper's Step-5 road: its vehicle, 50 km/h, goal 60 m ahead, H = 200;
+    16 static road bounds at +-3.5 m and a car's 4 corners moving at 20 km/h,
+    or a single far point."""
+    sc = inputs.scene_paper_road(True)
+    o = sc["obs"]
+    assert o.shape == (20, 4) and sc["N"] == 20480 and sc["T"] == 200
+    assert sc["preset"]["lf"] == inputs.PAPER["lf"] and sc["preset"]["widths"] == (8, 16, 16, 2)
+    assert math.isclose(sc["state"][3], 50 / 3.6) and sc["goal"][0] == 60.0
+    assert np.all(np.abs(o[:16, 1]) == 3.5) and np.all(o[:16, 2:] == 0.0)
+    assert np.allclose(o[16:, 2], 20 / 3.6) and np.all(o[16:, 3] == 0.0) and np.all(np.abs(o[16:, 1]) < 1.0)
+    empty = inputs.scene_paper_road(False, N=4096)
+    assert empty["obs"].shape == (1, 4) and np.hypot(*empty["obs"][0, :2]) > 1e3 and empty["N"] == 4096

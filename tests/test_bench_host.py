@@ -64,3 +64,15 @@ def test_grid_bytes_counts_reads_and_writes():
     assert bench.grid_bytes(0, 0) == 4.0 * (128 * 128 + 1)
     assert bench.grid_bytes(0, 10) == 10 * 16 * 2 + 4.0 * (128 * 128 + 1) + 10 * 8
     assert bench.grid_bytes(100, 8192) == 101 * (8192 * 40 + 4.0 * 16385)
+
+
+def test_automatic_brute_force_variant_names():
+    """The bench names the kernel the library's automatic brute-force choice
+    runs: for N >= 6144 variant 2 up to 1200 points, else 4; for fewer
+    samples 1 from 6000 points, 2 up to 64 points, else 3 (the rule the
+    library documents for collide_variant -1 below its binning threshold)."""
+    import bench
+    cases = {(20, 20480): 2, (157, 16384): 2, (1200, 8192): 2, (1201, 8192): 4, (20, 4096): 2, (64, 1024): 2,
+             (65, 1024): 3, (157, 4096): 3, (5999, 2048): 3, (6000, 2048): 1, (8000, 990): 1}
+    for (M, N), v in cases.items():
+        assert bench.brute_auto(M, N) == v, (M, N)
